@@ -1,0 +1,225 @@
+/*
+ * pcms.h -- C ABI of the GB300 field-transfer library (libpcms.so).
+ *
+ * Implements the data-parallel hot path of the field-mapping method of "PCMS: Parallel
+ * Coupler for Multimodel Simulations" (arXiv 2510.18838):
+ *   - meshless moving-least-squares (local weighted polynomial fitting) transfer with
+ *     compactly supported radial weights (Sec. 3.2.1, Eq. 1, Table 1), behind
+ *     pcms_create_map / pcms_apply_map / pcms_mls_transfer;
+ *   - mesh point localization with lowest-order topological classification and
+ *     barycentric (parametric) interpolation (Sec. 3.3), behind pcms_mesh_create /
+ *     pcms_locate_interp.
+ *
+ * Conventions shared by every entry point:
+ *   - Point arrays are structure-of-arrays float64 [dim][n] (x for all points, then y,
+ *     then z). Every pointer argument named *_pts, fields, out, elem_ids, ... is a DEVICE
+ *     pointer on the current CUDA device unless stated otherwise. The caller owns every
+ *     buffer it passes; the library never frees or retains them past the call (it copies
+ *     what a map or mesh needs into memory it owns).
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Work is enqueued
+ *     asynchronously on it; a call returns once its launches are enqueued, except where a
+ *     sync is documented (a device-to-host read of a size or a status count).
+ *   - Temporary and owned device memory comes from cudaMallocAsync on `stream`.
+ *   - No C++ exception crosses this boundary. Every call returns a pcms_status; on an
+ *     error pcms_last_error() returns a thread-local message. Inputs are validated on the
+ *     host before anything is enqueued (NULL pointers, sizes, dim, degree, radius, NaN
+ *     arguments); invalid arguments return PCMS_ERR_INVALID_ARG and enqueue nothing.
+ *   - There is no CPU fallback: every step runs in the library's CUDA kernels (sm_103a).
+ */
+#ifndef PCMS_H
+#define PCMS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PCMS_OK = 0,
+    PCMS_ERR_INVALID_ARG = 1,
+    /* Sec. 3.2.1: with a user-given radius (min_neighbors == 0) some target has fewer
+     * neighbours than basis terms; the map is still returned for inspection. */
+    PCMS_ERR_UNDERDETERMINED = 2,
+    PCMS_ERR_ILL_CONDITIONED = 3,
+    PCMS_ERR_OUT_OF_MEMORY = 4,
+    PCMS_ERR_TIMEOUT = 5,
+    PCMS_ERR_CUDA = 6,
+    PCMS_ERR_CAPACITY = 7
+} pcms_status;
+
+/* Arithmetic of the MLS path.
+ * PCMS_FP64:  distances, weights, moments, solve and operator in FP64.
+ * PCMS_MIXED: distance filter, weights and moment assembly in FP32 (coordinates as
+ *             FP32 hi/lo pairs), FP64 solve with a conditioning guard (targets that fail
+ *             it are re-assembled in FP64), FP32 operator and apply. Neighbour selection
+ *             is decided in FP64 in both modes, so neighbour lists are identical. */
+typedef enum { PCMS_FP64 = 0, PCMS_MIXED = 1 } pcms_precision;
+
+/* Radial weights phi(q), q = r / r_c (Table 1 with a = 2, plus Wendland C2). */
+typedef enum {
+    PCMS_WENDLAND_C2 = 0, /* (1-q)^4 (4q+1) */
+    PCMS_GAUSSIAN = 1,    /* exp(-(2q)^2) */
+    PCMS_C4 = 2,          /* (5q^5+30q^4+72q^3+82q^2+36q+6)(1-q)^6 */
+    PCMS_CONST = 3,       /* 1 */
+    PCMS_NOOP = 4,        /* 1 (identity weight; selection stays the radius) */
+    PCMS_MQ = 5,          /* sqrt(1+(2q)^2) */
+    PCMS_IMQ = 6,         /* 1/sqrt(1+(2q)^2) */
+    PCMS_TPS = 7,         /* (2q)^2 ln(2q) */
+    PCMS_CUBIC = 8        /* (2q)^3 */
+} pcms_weight;
+
+/* per-target status codes (int8) */
+enum { PCMS_TARGET_OK = 0, PCMS_TARGET_UNDERDETERMINED = 1, PCMS_TARGET_ILL_CONDITIONED = 2 };
+
+typedef struct {
+    pcms_precision precision; /* default PCMS_FP64 */
+    pcms_weight weight;       /* default PCMS_WENDLAND_C2 */
+    double lambda;            /* Tikhonov parameter of Eq. 1 (scaled basis), >= 0; default 0 */
+    /* Sec. 3.2.1 selection modes. 0 (default): the radius is used as given and targets with
+     * fewer than m neighbours are UNDERDETERMINED (value NaN). > 0: per target, the radius
+     * is doubled until at least max(min_neighbors, m) sources are selected. */
+    int min_neighbors;
+    /* Optional: 1 if lo/hi bound every source point; saves one device-to-host read. */
+    int domain_known;
+    double lo[3], hi[3];
+} pcms_map_opts;
+
+typedef struct pcms_map_s* pcms_map;
+typedef struct pcms_mesh_s* pcms_mesh;
+
+typedef struct {
+    int dim, basis_degree, n_terms;
+    pcms_precision precision;
+    int64_t n_src, n_tgt, nnz;
+    int64_t n_underdetermined, n_ill_conditioned; /* per-target status counts */
+    int64_t max_neighbors, max_radius_doublings;
+    int64_t device_bytes; /* memory owned by the map */
+} pcms_map_info_t;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int pcms_version(void);
+
+/* Thread-local message describing the last error returned on this thread. */
+const char* pcms_last_error(void);
+
+/* Fill *opts with the defaults listed above. */
+void pcms_map_opts_default(pcms_map_opts* opts);
+
+/*
+ * pcms_create_map -- build a cached MLS transfer operator (Sec. 3.2.1, Eq. 1).
+ *   For every target point t_i, selects the sources with |s_j - t_i| < r (decided in FP64
+ *   exactly as ((dx*dx + dy*dy) + dz*dz) < r*r, plus phi > 0), fits the weighted polynomial
+ *   of degree `basis_degree` (0, 1 or 2; graded-lex monomials of (s - t)/r) and stores the
+ *   shape functions N_ij so that f(t_i) = sum_j N_ij f(s_j).
+ *   dim: 2 or 3. src_pts: device float64 [dim][n_src]; tgt_pts: device float64 [dim][n_tgt].
+ *   radius > 0. opts may be NULL (defaults). The map copies what it needs; inputs may be
+ *   freed after the call returns and the stream has run.
+ *   Syncs `stream` once to size the operator (and once more for the bounding box unless
+ *   opts->domain_known). Returns PCMS_ERR_UNDERDETERMINED (map still created) when
+ *   min_neighbors == 0 and some target has fewer than m neighbours.
+ */
+pcms_status pcms_create_map(int dim, const double* src_pts, int64_t n_src,
+                            const double* tgt_pts, int64_t n_tgt, int basis_degree,
+                            double radius, const pcms_map_opts* opts, void* stream,
+                            pcms_map* out);
+
+/*
+ * pcms_apply_map -- evaluate out[f][i] = sum_j N_ij fields[f][j] for n_fields fields.
+ *   fields: device [n_fields][n_src] in the caller's source order; out: device
+ *   [n_fields][n_tgt] in the caller's target order. dtype is float64 for PCMS_FP64 maps and
+ *   float32 for PCMS_MIXED maps. 1 <= n_fields <= 16. Targets whose status is not OK get NaN.
+ *   Uses scratch of n_fields*(n_src+n_tgt) elements from cudaMallocAsync on `stream`.
+ */
+pcms_status pcms_apply_map(pcms_map map, const void* fields, int n_fields, void* out,
+                           void* stream);
+
+/*
+ * pcms_mls_transfer -- one-shot MLS transfer of n_fields fields without storing an
+ *   operator (same selection, weights and fit as pcms_create_map; the per-target fit is
+ *   evaluated directly as c_0 = e_1^T G^-1 g). Arguments as pcms_create_map plus fields
+ *   (device [n_fields][n_src], float64 for PCMS_FP64, float32 for PCMS_MIXED), out (device
+ *   [n_fields][n_tgt], same dtype) and target_status (device int8 [n_tgt], may be NULL).
+ *   1 <= n_fields <= 16. Syncs once for the bounding box unless opts->domain_known.
+ *   Returns PCMS_ERR_UNDERDETERMINED only when target_status is non-NULL, min_neighbors
+ *   == 0 and some target is underdetermined (this reads a count back: one more sync).
+ */
+pcms_status pcms_mls_transfer(int dim, const double* src_pts, int64_t n_src,
+                              const double* tgt_pts, int64_t n_tgt, int basis_degree,
+                              double radius, const pcms_map_opts* opts, const void* fields,
+                              int n_fields, void* out, int8_t* target_status, void* stream);
+
+/*
+ * pcms_count_neighbors -- the radius search alone (Sec. 3.2.1 selection function, with the
+ *   same minimum-count radius growth and the same FP64 decision as pcms_create_map).
+ *   counts: device int32 [n_tgt] (caller target order), number of selected sources;
+ *   radius_doublings: device int32 [n_tgt] or NULL; total: host int64 or NULL, the sum of
+ *   counts (reading it syncs `stream`). Other arguments as pcms_create_map (the precision
+ *   only selects the FP32 or FP64 distance filter; the decision is the same).
+ */
+pcms_status pcms_count_neighbors(int dim, const double* src_pts, int64_t n_src,
+                                 const double* tgt_pts, int64_t n_tgt, int basis_degree,
+                                 double radius, const pcms_map_opts* opts, int32_t* counts,
+                                 int32_t* radius_doublings, int64_t* total, void* stream);
+
+/* Sizes and status counts of a map. Syncs the map's stream. */
+pcms_status pcms_map_info(pcms_map map, pcms_map_info_t* info);
+
+/*
+ * pcms_map_export -- copy the operator out in the caller's orders (for tests/inspection).
+ *   offsets: device int64 [n_tgt+1]; cols: device int32 [nnz] (caller source indices);
+ *   vals: device float64 [nnz] or NULL; status: device int8 [n_tgt] or NULL;
+ *   radius_doublings: device int32 [n_tgt] or NULL. Within a row the order of (col, val)
+ *   pairs is unspecified.
+ */
+pcms_status pcms_map_export(pcms_map map, int64_t* offsets, int32_t* cols, double* vals,
+                            int8_t* status, int32_t* radius_doublings, void* stream);
+
+/* Release a map; its memory is freed on `stream` (stream order). NULL is a no-op. */
+void pcms_map_destroy(pcms_map map, void* stream);
+
+/*
+ * pcms_mesh_create -- cache a triangle mesh and its uniform-grid search structure
+ *   (Sec. 3.3). xy: device float64 [2][n_vertices]; tri: device int32 [3][n_tri] vertex
+ *   ids (either orientation; zero-area triangles never contain a point). Syncs once for
+ *   the bounding box and once for the number of (cell, triangle) pairs.
+ */
+pcms_status pcms_mesh_create(const double* xy, int64_t n_vertices, const int32_t* tri,
+                             int64_t n_tri, void* stream, pcms_mesh* out);
+
+/*
+ * pcms_locate_interp -- point localization + barycentric interpolation (Sec. 3.3).
+ *   tgt_pts: device float64 [2][n_pts]. elem_ids: device int32 [n_pts]: the smallest id
+ *   among triangles whose closure contains the point (exact orientation predicates), -1
+ *   if none. entity_dim (device int8 [n_pts] or NULL): dimension of the lowest-order mesh
+ *   entity the point lies on (0 vertex, 1 edge, 2 face), -1 outside. values (device
+ *   float64 [n_pts] or NULL, requires nodal_field device float64 [n_vertices]):
+ *   l0 f0 + l1 f1 + l2 f2 with l0 = A(p,v1,v2)/A(v0,v1,v2), l1 = A(v0,p,v2)/A(v0,v1,v2),
+ *   l2 = 1 - l0 - l1; NaN outside. Asynchronous.
+ */
+pcms_status pcms_locate_interp(pcms_mesh mesh, const double* tgt_pts, int64_t n_pts,
+                               const double* nodal_field, int32_t* elem_ids,
+                               int8_t* entity_dim, double* values, void* stream);
+
+/* Release a mesh (memory freed on `stream`). NULL is a no-op. */
+void pcms_mesh_destroy(pcms_mesh mesh, void* stream);
+
+/*
+ * Kernel tracing (no counterpart in the paper; instrumentation). When enabled, every
+ * library kernel launch is bracketed by a CUDA event pair recorded on the stream it is
+ * launched on, and elapsed times are accumulated per kernel name. pcms_trace_enable(1)
+ * clears the table; pcms_trace_enable(0) stops recording and keeps it. pcms_trace_count
+ * and pcms_trace_get synchronise on the recorded events. Thread-safe. Off by default.
+ */
+pcms_status pcms_trace_enable(int on);
+int pcms_trace_count(void);
+/* Entry `index` (0 <= index < pcms_trace_count()): name (NUL-terminated, truncated to
+ * name_len), number of launches and total milliseconds. PCMS_ERR_INVALID_ARG if out of range. */
+pcms_status pcms_trace_get(int index, char* name, int name_len, int64_t* launches,
+                           double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PCMS_H */

@@ -1,0 +1,241 @@
+// apply.cu -- evaluation of a cached MLS operator on one or many fields (out = N f, the
+// transferred values of Sec. 3.2.1), and export of the operator in the caller's orders.
+//
+// Data flow of one apply (all HBM-streaming kernels):
+//   1. k_fields_to_sorted: fields [F][ns] (caller order) -> fs [ns][FP] (sorted by cell,
+//      fields interleaved, FP = F rounded up to the vector width). Reads are coalesced over
+//      the caller index; each source writes one contiguous FP-element row.
+//   2. k_spmm: one warp per target row (targets sorted by cell), lanes split into
+//      32/NV nnz slots x NV vectors of fields; each slot reads (col, val) once and NV
+//      vectors of the source's field row. Rows of neighbouring targets touch neighbouring
+//      source rows, so the gathered field rows are served mostly from L2.
+//   3. k_stage_to_caller: out[f][i] = stage[inv_t[i]][f], coalesced writes per field.
+#include <algorithm>
+
+#include "pcms_internal.cuh"
+#include "trace.cuh"
+
+namespace pcms {
+
+namespace {
+
+int blocks_for(int64_t n, int threads, int per_sm = 32) {
+    int64_t need = (n + threads - 1) / threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * per_sm));
+}
+
+template <typename T>
+__global__ void k_fields_to_sorted(const T* __restrict__ f, int nf, int fp, int64_t ns,
+                                   const int32_t* __restrict__ inv, T* __restrict__ fs) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ns;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        T* row = fs + (int64_t)inv[i] * fp;
+        for (int k = 0; k < fp; k++) row[k] = k < nf ? f[(int64_t)k * ns + i] : T(0);
+    }
+}
+
+template <typename T> struct Vec;
+template <> struct Vec<float> { using type = float4; static constexpr int W = 4; };
+template <> struct Vec<double> { using type = double2; static constexpr int W = 2; };
+
+template <typename V, typename T>
+__device__ __forceinline__ void fma_vec(V& acc, T a, const V& x);
+template <>
+__device__ __forceinline__ void fma_vec<float4, float>(float4& acc, float a, const float4& x) {
+    acc.x = fmaf(a, x.x, acc.x); acc.y = fmaf(a, x.y, acc.y);
+    acc.z = fmaf(a, x.z, acc.z); acc.w = fmaf(a, x.w, acc.w);
+}
+template <>
+__device__ __forceinline__ void fma_vec<double2, double>(double2& acc, double a, const double2& x) {
+    acc.x = fma(a, x.x, acc.x); acc.y = fma(a, x.y, acc.y);
+}
+__device__ __forceinline__ void shfl_add(float4& v, int o) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o); v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    v.z += __shfl_xor_sync(0xffffffffu, v.z, o); v.w += __shfl_xor_sync(0xffffffffu, v.w, o);
+}
+__device__ __forceinline__ void shfl_add(double2& v, int o) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o); v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+}
+
+// vectorised: NV vectors of W elements per nnz (fp = NV*W)
+template <typename T, int NV>
+__global__ void __launch_bounds__(256) k_spmm_vec(int64_t nt, const int64_t* __restrict__ off,
+                                                  const int32_t* __restrict__ cols,
+                                                  const T* __restrict__ vals,
+                                                  const T* __restrict__ fs, T* __restrict__ stage) {
+    using V = typename Vec<T>::type;
+    constexpr int SLOTS = 32 / NV;
+    const int lane = threadIdx.x & 31;
+    const int slot = lane / NV, vi = lane % NV;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < nt;
+         t += nwarps) {
+        const int64_t a = off[t], b = off[t + 1];
+        V acc{};
+        for (int64_t e = a + slot; e < b; e += SLOTS) {
+            const int32_t j = __ldg(cols + e);
+            const T w = __ldg(vals + e);
+            const V x = *reinterpret_cast<const V*>(fs + (int64_t)j * (NV * Vec<T>::W) + vi * Vec<T>::W);
+            fma_vec<V, T>(acc, w, x);
+        }
+#pragma unroll
+        for (int o = NV; o < 32; o <<= 1) shfl_add(acc, o);
+        if (slot == 0)
+            *reinterpret_cast<V*>(stage + t * (NV * Vec<T>::W) + vi * Vec<T>::W) = acc;
+    }
+}
+
+// scalar: one field
+template <typename T>
+__global__ void __launch_bounds__(256) k_spmm_1(int64_t nt, const int64_t* __restrict__ off,
+                                                const int32_t* __restrict__ cols,
+                                                const T* __restrict__ vals,
+                                                const T* __restrict__ fs, T* __restrict__ stage) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < nt;
+         t += nwarps) {
+        const int64_t a = off[t], b = off[t + 1];
+        T acc = T(0);
+        for (int64_t e = a + lane; e < b; e += 32) acc += __ldg(vals + e) * fs[__ldg(cols + e)];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) stage[t] = acc;
+    }
+}
+
+template <typename T>
+__global__ void k_stage_to_caller(const T* __restrict__ stage, int fp, int nf, int64_t nt,
+                                  const int32_t* __restrict__ inv_t, T* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const T* row = stage + (int64_t)inv_t[i] * fp;
+        for (int f = 0; f < nf; f++) out[(int64_t)f * nt + i] = row[f];
+    }
+}
+
+template <typename T>
+void apply_t(MapImpl& M, const T* fields, int nf, T* out, cudaStream_t s) {
+    const int64_t ns = M.ns, nt = M.nt;
+    constexpr int W = Vec<T>::W;
+    int nvec = 1;
+    while (nvec * W < nf) nvec <<= 1;   // power-of-two vectors per row
+    const int fp = nf == 1 ? 1 : nvec * W;
+    DBuf fs(sizeof(T) * fp * std::max<int64_t>(ns, 1), s);
+    DBuf stage(sizeof(T) * fp * std::max<int64_t>(nt, 1), s);
+    if (ns > 0) {
+        PCMS_TRACE("apply_fields_to_sorted", s);
+        k_fields_to_sorted<T><<<blocks_for(ns, 256), 256, 0, s>>>(fields, nf, fp, ns,
+                                                                  M.src.inv.as<int32_t>(), fs.as<T>());
+    }
+    if (nt > 0) {
+        PCMS_TRACE("apply_spmm", s);
+        const int64_t* off = M.offsets.as<int64_t>();
+        const int32_t* cols = M.cols.as<int32_t>();
+        const T* vals = M.vals.as<T>();
+        int blocks = blocks_for(nt * 32, 256, 16);
+        int nv = fp / W;
+        if (fp == 1) k_spmm_1<T><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs.as<T>(), stage.as<T>());
+        else if (nv == 1) k_spmm_vec<T, 1><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs.as<T>(), stage.as<T>());
+        else if (nv == 2) k_spmm_vec<T, 2><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs.as<T>(), stage.as<T>());
+        else if (nv == 4) k_spmm_vec<T, 4><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs.as<T>(), stage.as<T>());
+        else if (nv == 8) k_spmm_vec<T, 8><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs.as<T>(), stage.as<T>());
+        else {
+            fail(PCMS_ERR_INVALID_ARG, "internal: field padding");
+        }
+        PCMS_LAUNCH_CHECK("k_spmm");
+    }
+    if (nt > 0) {
+        PCMS_TRACE("apply_stage_to_caller", s);
+        k_stage_to_caller<T><<<blocks_for(nt, 256), 256, 0, s>>>(stage.as<T>(), fp, nf, nt,
+                                                                 M.tgt.inv.as<int32_t>(), out);
+    }
+    PCMS_LAUNCH_CHECK("apply");
+}
+
+// export: row lengths in caller order, scan, then a warp per row copies (col, val)
+__global__ void k_export_len(int64_t nt, const int32_t* __restrict__ inv_t,
+                             const int64_t* __restrict__ off, int32_t* __restrict__ len) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t p = inv_t[i];
+        len[i] = (int32_t)(off[p + 1] - off[p]);
+    }
+}
+
+template <typename T>
+__global__ void k_export_rows(int64_t nt, const int32_t* __restrict__ inv_t,
+                              const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
+                              const T* __restrict__ vals, const int32_t* __restrict__ perm_s,
+                              const int8_t* __restrict__ st, const int32_t* __restrict__ kx,
+                              const int64_t* __restrict__ off_out, int32_t* __restrict__ cols_out,
+                              double* __restrict__ vals_out, int8_t* __restrict__ st_out,
+                              int32_t* __restrict__ kx_out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < nt;
+         i += nwarps) {
+        const int64_t p = inv_t[i];
+        const int64_t a = off[p], b = off[p + 1], o = off_out[i];
+        for (int64_t e = a + lane; e < b; e += 32) {
+            cols_out[o + (e - a)] = perm_s[cols[e]];
+            if (vals_out) vals_out[o + (e - a)] = (double)vals[e];
+        }
+        if (lane == 0) {
+            if (st_out) st_out[i] = st[p];
+            if (kx_out) kx_out[i] = kx[p];
+        }
+    }
+}
+
+__global__ void k_export_status(int64_t nt, const int32_t* __restrict__ inv_t,
+                                const int8_t* __restrict__ st, const int32_t* __restrict__ kx,
+                                int8_t* __restrict__ st_out, int32_t* __restrict__ kx_out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = inv_t[i];
+        if (st_out) st_out[i] = st[p];
+        if (kx_out) kx_out[i] = kx[p];
+    }
+}
+
+}  // namespace
+
+void mls_apply(MapImpl& M, const void* fields, int nf, void* out, cudaStream_t s) {
+    if (M.P.prec == PCMS_MIXED) apply_t<float>(M, (const float*)fields, nf, (float*)out, s);
+    else apply_t<double>(M, (const double*)fields, nf, (double*)out, s);
+}
+
+void mls_export(MapImpl& M, int64_t* offsets, int32_t* cols, double* vals, int8_t* status,
+                int32_t* kexp, cudaStream_t s) {
+    const int64_t nt = M.nt;
+    if (offsets == nullptr) {
+        if (nt > 0 && (status || kexp))
+            k_export_status<<<blocks_for(nt, 256), 256, 0, s>>>(nt, M.tgt.inv.as<int32_t>(),
+                                                                M.status.as<int8_t>(),
+                                                                M.kexp.as<int32_t>(), status, kexp);
+        PCMS_LAUNCH_CHECK("export");
+        return;
+    }
+    DBuf len(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
+    if (nt > 0)
+        k_export_len<<<blocks_for(nt, 256), 256, 0, s>>>(nt, M.tgt.inv.as<int32_t>(),
+                                                         M.offsets.as<int64_t>(), len.as<int32_t>());
+    exclusive_scan<int64_t>(len.as<int32_t>(), offsets, nt, s);
+    if (nt > 0) {
+        int blocks = blocks_for(nt * 32, 256, 16);
+        if (M.P.prec == PCMS_MIXED)
+            k_export_rows<float><<<blocks, 256, 0, s>>>(
+                nt, M.tgt.inv.as<int32_t>(), M.offsets.as<int64_t>(), M.cols.as<int32_t>(),
+                M.vals.as<float>(), M.src.perm.as<int32_t>(), M.status.as<int8_t>(),
+                M.kexp.as<int32_t>(), offsets, cols, vals, status, kexp);
+        else
+            k_export_rows<double><<<blocks, 256, 0, s>>>(
+                nt, M.tgt.inv.as<int32_t>(), M.offsets.as<int64_t>(), M.cols.as<int32_t>(),
+                M.vals.as<double>(), M.src.perm.as<int32_t>(), M.status.as<int8_t>(),
+                M.kexp.as<int32_t>(), offsets, cols, vals, status, kexp);
+    }
+    PCMS_LAUNCH_CHECK("export");
+}
+
+}  // namespace pcms

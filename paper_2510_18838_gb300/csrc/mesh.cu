@@ -1,0 +1,329 @@
+// mesh.cu -- point localization in a triangle mesh with lowest-order topological
+// classification, and barycentric (parametric) interpolation (Sec. 3.3).
+//
+// Search structure (Sec. 3.3, single-level uniform grid): every triangle is listed in each
+// cell its bounding box overlaps; lists are sorted by triangle id. Cell coordinates of
+// bounding-box corners and of query points use the same monotone expression
+// floor((x - lo) * inv_h), so a triangle whose closure contains p is always listed in p's
+// cell. Scanning the list in ascending id and stopping at the first triangle whose closure
+// contains p yields the smallest such id, which makes the answer independent of traversal
+// order (the consistency requirement of Sec. 3.3).
+//
+// Orientation signs are exact: a floating-point filter with Shewchuk's error bound
+// (3 + 16 eps) eps (|detleft| + |detright|) decides almost every case; the rest is
+// evaluated exactly by splitting each coordinate difference and each product into
+// non-overlapping double expansions (two-diff, FMA-based two-product, two-sum) and taking
+// the sign of the largest component of their exact sum.
+#include <algorithm>
+#include <cmath>
+
+#include "pcms_internal.cuh"
+#include "trace.cuh"
+
+namespace pcms {
+
+namespace {
+
+int blocks_for(int64_t n, int threads, int per_sm = 32) {
+    int64_t need = (n + threads - 1) / threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * per_sm));
+}
+
+__device__ __forceinline__ int mesh_cell(double x, double lo, double inv_h, int n) {
+    double f = floor((x - lo) * inv_h);
+    f = fmin(fmax(f, 0.0), (double)(n - 1));
+    return (int)f;
+}
+
+// ---------------------------------------------------------------------- exact orientation
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+    s = __dadd_rn(a, b);
+    double bv = __dsub_rn(s, a);
+    double av = __dsub_rn(s, bv);
+    e = __dadd_rn(__dsub_rn(a, av), __dsub_rn(b, bv));
+}
+__device__ __forceinline__ void two_diff(double a, double b, double& s, double& e) {
+    s = __dsub_rn(a, b);
+    double bv = __dsub_rn(a, s);
+    double av = __dadd_rn(s, bv);
+    e = __dadd_rn(__dsub_rn(a, av), __dsub_rn(bv, b));
+}
+__device__ __forceinline__ void two_prod(double a, double b, double& p, double& e) {
+    p = __dmul_rn(a, b);
+    e = fma(a, b, -p);
+}
+
+// exact sign of (ax-cx)(by-cy) - (ay-cy)(bx-cx)
+__device__ __noinline__ int orient_exact(double ax, double ay, double bx, double by, double cx,
+                                         double cy) {
+    double u[2], v[2], w[2], z[2];   // ax-cx, by-cy, ay-cy, bx-cx as hi+lo
+    two_diff(ax, cx, u[0], u[1]);
+    two_diff(by, cy, v[0], v[1]);
+    two_diff(ay, cy, w[0], w[1]);
+    two_diff(bx, cx, z[0], z[1]);
+    double e[17];
+    int n = 0;
+    for (int i = 0; i < 2; i++)
+        for (int j = 0; j < 2; j++)
+            for (int neg = 0; neg < 2; neg++) {
+                double p, q;
+                if (neg == 0) two_prod(u[i], v[j], p, q);
+                else two_prod(-w[i], z[j], p, q);
+                double terms[2] = {q, p};
+                for (int t = 0; t < 2; t++) {
+                    double acc = terms[t];
+                    for (int k = 0; k < n; k++) {
+                        double s, h;
+                        two_sum(acc, e[k], s, h);
+                        e[k] = h;
+                        acc = s;
+                    }
+                    e[n++] = acc;
+                }
+            }
+    for (int k = n - 1; k >= 0; k--) {
+        if (e[k] > 0.0) return 1;
+        if (e[k] < 0.0) return -1;
+    }
+    return 0;
+}
+
+__device__ __forceinline__ int orient_sign(double ax, double ay, double bx, double by, double cx,
+                                           double cy) {
+    const double detleft = __dmul_rn(__dsub_rn(ax, cx), __dsub_rn(by, cy));
+    const double detright = __dmul_rn(__dsub_rn(ay, cy), __dsub_rn(bx, cx));
+    const double det = __dsub_rn(detleft, detright);
+    double detsum;
+    if (detleft > 0.0) {
+        if (detright <= 0.0) return det > 0.0 ? 1 : (det < 0.0 ? -1 : 0);
+        detsum = detleft + detright;
+    } else if (detleft < 0.0) {
+        if (detright >= 0.0) return det > 0.0 ? 1 : (det < 0.0 ? -1 : 0);
+        detsum = -detleft - detright;
+    } else {
+        return det > 0.0 ? 1 : (det < 0.0 ? -1 : 0);
+    }
+    const double errbound = 3.3306690738754716e-16 * detsum;   // (3 + 16 eps) eps, eps = 2^-53
+    if (det >= errbound) return 1;
+    if (-det >= errbound) return -1;
+    return orient_exact(ax, ay, bx, by, cx, cy);
+}
+
+__device__ __forceinline__ double orient_fp(double ax, double ay, double bx, double by, double cx,
+                                            double cy) {
+    return __dsub_rn(__dmul_rn(__dsub_rn(ax, cx), __dsub_rn(by, cy)),
+                     __dmul_rn(__dsub_rn(ay, cy), __dsub_rn(bx, cx)));
+}
+
+// ---------------------------------------------------------------------- build kernels
+__global__ void k_tri_prep(int64_t nv, const double* __restrict__ xy, int64_t nt,
+                           const int32_t* __restrict__ tri, Grid g, int32_t* __restrict__ count,
+                           int8_t* __restrict__ tsign, int4* __restrict__ trect,
+                           unsigned long long* bad_ids) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nt;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int32_t i0 = tri[k], i1 = tri[nt + k], i2 = tri[2 * nt + k];
+        if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= nv || i1 >= nv || i2 >= nv) {
+            atomicAdd(bad_ids, 1ull);
+            tsign[k] = 0;
+            trect[k] = make_int4(1, 1, 0, 0);   // empty
+            continue;
+        }
+        double x0 = xy[i0], y0 = xy[nv + i0], x1 = xy[i1], y1 = xy[nv + i1];
+        double x2 = xy[i2], y2 = xy[nv + i2];
+        int s = orient_sign(x0, y0, x1, y1, x2, y2);
+        tsign[k] = (int8_t)s;
+        if (s == 0) {
+            trect[k] = make_int4(1, 1, 0, 0);
+            continue;
+        }
+        int cx0 = mesh_cell(fmin(x0, fmin(x1, x2)), g.lo[0], g.inv_h, g.n[0]);
+        int cx1 = mesh_cell(fmax(x0, fmax(x1, x2)), g.lo[0], g.inv_h, g.n[0]);
+        int cy0 = mesh_cell(fmin(y0, fmin(y1, y2)), g.lo[1], g.inv_h, g.n[1]);
+        int cy1 = mesh_cell(fmax(y0, fmax(y1, y2)), g.lo[1], g.inv_h, g.n[1]);
+        trect[k] = make_int4(cx0, cy0, cx1, cy1);
+        for (int cy = cy0; cy <= cy1; cy++)
+            for (int cx = cx0; cx <= cx1; cx++) atomicAdd(&count[(int64_t)cy * g.n[0] + cx], 1);
+    }
+}
+
+__global__ void k_tri_fill(int64_t nt, Grid g, const int4* __restrict__ trect,
+                           const int32_t* __restrict__ start, int32_t* __restrict__ fill,
+                           int32_t* __restrict__ items) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nt;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int4 r = trect[k];
+        for (int cy = r.y; cy <= r.w; cy++)
+            for (int cx = r.x; cx <= r.z; cx++) {
+                int64_t c = (int64_t)cy * g.n[0] + cx;
+                int pos = start[c] + atomicAdd(&fill[c], 1);
+                items[pos] = (int32_t)k;
+            }
+    }
+}
+
+__global__ void k_cell_sort(int64_t ncell, const int32_t* __restrict__ start, int32_t* items) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int a = start[c], b = start[c + 1];
+        for (int i = a + 1; i < b; i++) {
+            int32_t v = items[i];
+            int j = i - 1;
+            while (j >= a && items[j] > v) {
+                items[j + 1] = items[j];
+                j--;
+            }
+            items[j + 1] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------- query kernel
+__global__ void __launch_bounds__(256) k_locate(Grid g, double bx0, double by0, double bx1,
+                                                double by1, int64_t nv,
+                                                const double* __restrict__ xy, int64_t ntri,
+                                                const int32_t* __restrict__ tri,
+                                                const int8_t* __restrict__ tsign,
+                                                const int32_t* __restrict__ start,
+                                                const int32_t* __restrict__ items,
+                                                const double* __restrict__ pts, int64_t n,
+                                                const double* __restrict__ field,
+                                                int32_t* __restrict__ elem,
+                                                int8_t* __restrict__ edim,
+                                                double* __restrict__ vals) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double px = pts[i], py = pts[n + i];
+        int32_t found = -1;
+        int nz = 0;
+        int32_t v0 = 0, v1 = 0, v2 = 0;
+        if (px >= bx0 && px <= bx1 && py >= by0 && py <= by1) {
+            const int64_t c = (int64_t)mesh_cell(py, g.lo[1], g.inv_h, g.n[1]) * g.n[0] +
+                              mesh_cell(px, g.lo[0], g.inv_h, g.n[0]);
+            const int a = start[c], b = start[c + 1];
+            for (int it = a; it < b; it++) {
+                const int32_t k = items[it];
+                const int s = tsign[k];
+                const int32_t i0 = tri[k], i1 = tri[ntri + k], i2 = tri[2 * ntri + k];
+                const double x0 = xy[i0], y0 = xy[nv + i0];
+                const double x1 = xy[i1], y1 = xy[nv + i1];
+                const double x2 = xy[i2], y2 = xy[nv + i2];
+                const int o0 = orient_sign(x1, y1, x2, y2, px, py);
+                if (o0 * s < 0) continue;
+                const int o1 = orient_sign(x2, y2, x0, y0, px, py);
+                if (o1 * s < 0) continue;
+                const int o2 = orient_sign(x0, y0, x1, y1, px, py);
+                if (o2 * s < 0) continue;
+                found = k;
+                nz = (o0 == 0) + (o1 == 0) + (o2 == 0);
+                v0 = i0; v1 = i1; v2 = i2;
+                break;
+            }
+        }
+        elem[i] = found;
+        if (edim) edim[i] = (int8_t)(found < 0 ? -1 : 2 - nz);
+        if (vals) {
+            double v = __longlong_as_double(0x7ff8000000000000LL);
+            if (found >= 0) {
+                const double x0 = xy[v0], y0 = xy[nv + v0];
+                const double x1 = xy[v1], y1 = xy[nv + v1];
+                const double x2 = xy[v2], y2 = xy[nv + v2];
+                const double area = orient_fp(x0, y0, x1, y1, x2, y2);
+                const double l0 = __ddiv_rn(orient_fp(px, py, x1, y1, x2, y2), area);
+                const double l1 = __ddiv_rn(orient_fp(x0, y0, px, py, x2, y2), area);
+                const double l2 = __dsub_rn(__dsub_rn(1.0, l0), l1);
+                v = __dadd_rn(__dadd_rn(__dmul_rn(l0, field[v0]), __dmul_rn(l1, field[v1])),
+                              __dmul_rn(l2, field[v2]));
+            }
+            vals[i] = v;
+        }
+    }
+}
+
+}  // namespace
+
+void mesh_create(MeshImpl& M, const double* xy, int64_t nv, const int32_t* tri, int64_t ntri) {
+    cudaStream_t s = M.stream;
+    M.nv = nv;
+    M.ntri = ntri;
+    M.xy.alloc(sizeof(double) * 2 * std::max<int64_t>(nv, 1), s);
+    M.tri.alloc(sizeof(int32_t) * 3 * std::max<int64_t>(ntri, 1), s);
+    if (nv > 0) PCMS_CU(cudaMemcpyAsync(M.xy.p, xy, sizeof(double) * 2 * nv, cudaMemcpyDeviceToDevice, s));
+    if (ntri > 0)
+        PCMS_CU(cudaMemcpyAsync(M.tri.p, tri, sizeof(int32_t) * 3 * ntri, cudaMemcpyDeviceToDevice, s));
+    // bounding box of the vertices
+    DBuf box(sizeof(double) * 6 + sizeof(long long) * 6 + sizeof(unsigned long long) * 2, s);
+    double* dbox = box.as<double>();
+    long long* enc = (long long*)(dbox + 6);
+    unsigned long long* bad = (unsigned long long*)(enc + 6);
+    launch_bbox(2, M.xy.as<double>(), nv, dbox, enc, bad, s);
+    double hb[6];
+    unsigned long long hbad = 0;
+    PCMS_CU(cudaMemcpyAsync(hb, dbox, sizeof(hb), cudaMemcpyDeviceToHost, s));
+    PCMS_CU(cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, s));
+    PCMS_CU(cudaStreamSynchronize(s));
+    if (hbad) fail(PCMS_ERR_INVALID_ARG, "non-finite vertex coordinate");
+    if (nv == 0) { hb[0] = hb[1] = 0.0; hb[3] = hb[4] = 0.0; }
+    M.bbox[0] = hb[0]; M.bbox[1] = hb[1]; M.bbox[2] = hb[3]; M.bbox[3] = hb[4];
+    // about one cell per two triangles
+    double ex = std::max(hb[3] - hb[0], 0.0), ey = std::max(hb[4] - hb[1], 0.0);
+    double area = std::max(ex * ey, 1e-300);
+    double h = std::sqrt(area / (0.5 * (double)std::max<int64_t>(ntri, 1)));
+    if (!(h > 0.0) || !std::isfinite(h)) h = std::max(std::max(ex, ey), 1.0);
+    h = std::max(h, std::max(ex, ey) / 16384.0);
+    if (h == 0.0) h = 1.0;
+    double lo[3] = {hb[0], hb[1], 0.0}, hi[3] = {hb[3], hb[4], 0.0};
+    // make_grid adds the 2^-20 margin used for radius searches; harmless here
+    M.g = make_grid(2, lo, hi, h, int64_t(1) << 26);
+    const Grid& g = M.g;
+    DBuf count(sizeof(int32_t) * (g.ncell + 1), s);
+    PCMS_CU(cudaMemsetAsync(count.p, 0, count.bytes, s));
+    M.tsign.alloc(sizeof(int8_t) * std::max<int64_t>(ntri, 1), s);
+    DBuf trect(sizeof(int4) * std::max<int64_t>(ntri, 1), s);
+    DBuf badid(sizeof(unsigned long long), s);
+    PCMS_CU(cudaMemsetAsync(badid.p, 0, badid.bytes, s));
+    if (ntri > 0) {
+        PCMS_TRACE("mesh_tri_prep", s);
+        k_tri_prep<<<blocks_for(ntri, 256), 256, 0, s>>>(nv, M.xy.as<double>(), ntri,
+                                                         M.tri.as<int32_t>(), g, count.as<int32_t>(),
+                                                         M.tsign.as<int8_t>(), trect.as<int4>(),
+                                                         badid.as<unsigned long long>());
+    }
+    PCMS_LAUNCH_CHECK("k_tri_prep");
+    M.cell_start.alloc(sizeof(int32_t) * (g.ncell + 1), s);
+    exclusive_scan<int32_t>(count.as<int32_t>(), M.cell_start.as<int32_t>(), g.ncell, s);
+    int32_t npairs = 0;
+    unsigned long long hbadid = 0;
+    PCMS_CU(cudaMemcpyAsync(&npairs, M.cell_start.as<int32_t>() + g.ncell, sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, s));
+    PCMS_CU(cudaMemcpyAsync(&hbadid, badid.p, sizeof(hbadid), cudaMemcpyDeviceToHost, s));
+    PCMS_CU(cudaStreamSynchronize(s));
+    if (hbadid) fail(PCMS_ERR_INVALID_ARG, "triangle vertex id out of range");
+    if (npairs < 0) fail(PCMS_ERR_CAPACITY, "too many (cell, triangle) pairs");
+    M.npairs = npairs;
+    M.items.alloc(sizeof(int32_t) * std::max<int32_t>(npairs, 1), s);
+    PCMS_CU(cudaMemsetAsync(count.p, 0, count.bytes, s));
+    if (ntri > 0) {
+        PCMS_TRACE("mesh_tri_fill", s);
+        k_tri_fill<<<blocks_for(ntri, 256), 256, 0, s>>>(ntri, g, trect.as<int4>(),
+                                                         M.cell_start.as<int32_t>(),
+                                                         count.as<int32_t>(), M.items.as<int32_t>());
+    }
+    PCMS_TRACE("mesh_cell_sort", s);
+    k_cell_sort<<<blocks_for(g.ncell, 256), 256, 0, s>>>(g.ncell, M.cell_start.as<int32_t>(),
+                                                         M.items.as<int32_t>());
+    PCMS_LAUNCH_CHECK("mesh build");
+}
+
+void mesh_locate(const MeshImpl& M, const double* pts, int64_t n, const double* field,
+                 int32_t* elem, int8_t* edim, double* vals, cudaStream_t s) {
+    if (n <= 0) return;
+    PCMS_TRACE("mesh_locate_interp", s);
+    k_locate<<<blocks_for(n, 256), 256, 0, s>>>(
+        M.g, M.bbox[0], M.bbox[1], M.bbox[2], M.bbox[3], M.nv, M.xy.as<double>(), M.ntri,
+        M.tri.as<int32_t>(), M.tsign.as<int8_t>(), M.cell_start.as<int32_t>(),
+        M.items.as<int32_t>(), pts, n, field, elem, edim, vals);
+    PCMS_LAUNCH_CHECK("k_locate");
+}
+
+}  // namespace pcms

@@ -1,0 +1,399 @@
+// mls.cu -- host orchestration of the MLS transfer (Sec. 3.2.1): grid build, neighbour
+// count, operator assembly/solve/shape, one-shot transfer, apply and export.
+#include <algorithm>
+#include <cmath>
+
+#include "mls_dispatch.cuh"
+
+namespace pcms {
+
+namespace {
+
+constexpr int64_t MAX_CELLS = int64_t(1) << 24;
+constexpr double TAU_FP64 = 1e-14;   // (1e-7)^2: column-angle rank test of the definition
+constexpr double TAU_MIXED = 1e-4;   // FP32-assembled pivots below this are redone in FP64
+
+int asm_blocks(int64_t nwork, int G) {
+    int64_t groups_per_block = 8 * (32 / G);
+    int64_t need = (nwork + groups_per_block - 1) / groups_per_block;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 16));
+}
+
+int thread_blocks(int64_t n, int threads) {
+    int64_t need = (n + threads - 1) / threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 32));
+}
+
+// lanes per target from the expected neighbour count (ns * ball volume / box volume)
+int choose_group(int dim, int64_t ns, double radius, const double* lo, const double* hi) {
+    double vol = 1.0;
+    for (int d = 0; d < dim; d++) vol *= std::max(hi[d] - lo[d], radius);
+    double ball = dim == 2 ? M_PI * radius * radius : 4.0 / 3.0 * M_PI * radius * radius * radius;
+    double mean = (double)ns * ball / vol;
+    return mean >= 160.0 ? 32 : 8;
+}
+
+__global__ void k_stats(const int8_t* status, const int32_t* counts, const int32_t* kexp,
+                        int64_t n, unsigned long long* out) {
+    unsigned long long under = 0, ill = 0, mc = 0, mk = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int8_t st = status[i];
+        under += st == PCMS_TARGET_UNDERDETERMINED;
+        ill += st == PCMS_TARGET_ILL_CONDITIONED;
+        mc = max(mc, (unsigned long long)counts[i]);
+        mk = max(mk, (unsigned long long)kexp[i]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        under += __shfl_xor_sync(0xffffffffu, under, o);
+        ill += __shfl_xor_sync(0xffffffffu, ill, o);
+        mc = max(mc, __shfl_xor_sync(0xffffffffu, mc, o));
+        mk = max(mk, __shfl_xor_sync(0xffffffffu, mk, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out[0], under);
+        atomicAdd(&out[1], ill);
+        atomicMax(&out[2], mc);
+        atomicMax(&out[3], mk);
+    }
+}
+
+template <typename T>
+__global__ void k_permute_field(const T* __restrict__ f, const int32_t* __restrict__ inv,
+                                int64_t n, T* __restrict__ fs) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        fs[inv[i]] = f[i];
+}
+
+struct BoxResult {
+    double lo[3], hi[3];
+};
+
+// Bounding box of the sources and a finiteness check of sources and targets (one sync),
+// or the caller's box.
+BoxResult source_box(int dim, const double* src, int64_t ns, const double* tgt, int64_t nt,
+                     const pcms_map_opts& o, cudaStream_t s) {
+    BoxResult b;
+    if (o.domain_known) {
+        for (int d = 0; d < 3; d++) { b.lo[d] = o.lo[d]; b.hi[d] = o.hi[d]; }
+        return b;
+    }
+    DBuf box(sizeof(double) * 12 + sizeof(long long) * 12 + sizeof(unsigned long long) * 2, s);
+    double* dbox = box.as<double>();
+    long long* enc = (long long*)(dbox + 12);
+    unsigned long long* bad = (unsigned long long*)(enc + 12);
+    launch_bbox(dim, src, ns, dbox, enc, bad, s);
+    launch_bbox(dim, tgt, nt, dbox + 6, enc + 6, bad + 1, s);
+    double hb[12];
+    unsigned long long hbad[2];
+    PCMS_CU(cudaMemcpyAsync(hb, dbox, sizeof(hb), cudaMemcpyDeviceToHost, s));
+    PCMS_CU(cudaMemcpyAsync(hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, s));
+    PCMS_CU(cudaStreamSynchronize(s));
+    if (hbad[0] || hbad[1])
+        fail(PCMS_ERR_INVALID_ARG, "non-finite point coordinate (" + std::to_string(hbad[0]) +
+                                       " in sources, " + std::to_string(hbad[1]) + " in targets)");
+    for (int d = 0; d < 3; d++) {
+        b.lo[d] = (d < dim && ns > 0) ? hb[d] : 0.0;
+        b.hi[d] = (d < dim && ns > 0) ? hb[3 + d] : 0.0;
+    }
+    return b;
+}
+
+AsmArgs base_args(const Grid& g, const SortedPoints& S, const SortedPoints& Tp,
+                  const MlsParams& P) {
+    AsmArgs a{};
+    a.g = g;
+    a.ns = S.n;
+    a.nt = Tp.n;
+    a.cell_start = S.cell_start.as<int32_t>();
+    a.sx64 = S.x64.as<double>();
+    a.hl0 = S.hl0.as<float4>();
+    a.hl1 = S.hl1.as<float2>();
+    a.tx64 = Tp.x64.as<double>();
+    a.radius = P.radius;
+    a.weight = (int)P.weight;
+    a.need = P.need;
+    return a;
+}
+
+int accp(int dim, int deg, int mode) {
+    int nm = mono_count(dim, 2 * deg), m = mono_count(dim, deg);
+    int nacc = mode == MODE_FUSED ? nm + m : nm;
+    return round_up4(nacc);
+}
+
+}  // namespace
+
+int64_t MapImpl::device_bytes() const {
+    return (int64_t)(src.cell_start.bytes + src.perm.bytes + src.inv.bytes + src.x64.bytes +
+                     src.hl0.bytes + src.hl1.bytes + tgt.perm.bytes + tgt.inv.bytes +
+                     tgt.x64.bytes + counts.bytes + kexp.bytes + status.bytes + offsets.bytes +
+                     cols.bytes + vals.bytes);
+}
+
+// ------------------------------------------------------------------------------------
+// create map
+// ------------------------------------------------------------------------------------
+void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms_map_opts& o) {
+    cudaStream_t s = M.stream;
+    const MlsParams& P = M.P;
+    const int dim = P.dim, deg = P.degree, m = P.m;
+    const bool mixed = P.prec == PCMS_MIXED;
+    const int64_t ns = M.ns, nt = M.nt;
+    BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
+    M.g = make_grid(dim, b.lo, b.hi, P.radius, MAX_CELLS);
+    sort_points(M.g, src, ns, true, mixed, M.src, s);
+    sort_points(M.g, tgt, nt, false, false, M.tgt, s);
+    const int G = choose_group(dim, ns, P.radius, b.lo, b.hi);
+
+    M.counts.alloc(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
+    M.kexp.alloc(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
+    M.status.alloc(sizeof(int8_t) * std::max<int64_t>(nt, 1), s);
+    M.offsets.alloc(sizeof(int64_t) * (nt + 1), s);
+    DBuf err(sizeof(unsigned) * 4, s);
+    PCMS_CU(cudaMemsetAsync(err.p, 0, err.bytes, s));
+
+    AsmArgs a = base_args(M.g, M.src, M.tgt, P);
+    a.err = err.as<unsigned>();
+    a.counts = M.counts.as<int32_t>();
+    a.kexp_out = M.kexp.as<int32_t>();
+    if (nt > 0)
+        assemble_any(dim, 0, mixed, MODE_COUNT, G, false, a, asm_blocks(nt, G), s);
+    exclusive_scan<int64_t>(M.counts.as<int32_t>(), M.offsets.as<int64_t>(), nt, s);
+    int64_t nnz = 0;
+    PCMS_CU(cudaMemcpyAsync(&nnz, M.offsets.as<int64_t>() + nt, sizeof(int64_t),
+                            cudaMemcpyDeviceToHost, s));
+    PCMS_CU(cudaStreamSynchronize(s));
+    M.nnz = nnz;
+    M.cols.alloc(sizeof(int32_t) * std::max<int64_t>(nnz, 1), s);
+    M.vals.alloc((mixed ? sizeof(float) : sizeof(double)) * std::max<int64_t>(nnz, 1), s);
+
+    if (nt > 0) {
+        const int np = accp(dim, deg, MODE_MAP);
+        DBuf mom((mixed ? sizeof(float) : sizeof(double)) * np * nt, s);
+        DBuf y(sizeof(double) * m * nt, s);
+        DBuf redo(sizeof(int32_t) * (nt + 1), s);
+        int32_t* redo_n = redo.as<int32_t>() + nt;
+        PCMS_CU(cudaMemsetAsync(redo_n, 0, sizeof(int32_t), s));
+        a.kexp_in = M.kexp.as<int32_t>();
+        a.kexp_out = nullptr;
+        a.offsets = M.offsets.as<int64_t>();
+        a.cols = M.cols.as<int32_t>();
+        a.mom = mom.p;
+        assemble_any(dim, deg, mixed, MODE_MAP, G, false, a, asm_blocks(nt, G), s);
+
+        SolveArgs sa{};
+        sa.nt = nt;
+        sa.counts = M.counts.as<int32_t>();
+        sa.mom = mom.p;
+        sa.lambda = P.lambda;
+        sa.tau = mixed ? TAU_MIXED : TAU_FP64;
+        sa.redo_on_fail = mixed ? 1 : 0;
+        sa.redo_list = redo.as<int32_t>();
+        sa.redo_n = redo_n;
+        sa.y = y.as<double>();
+        sa.status = M.status.as<int8_t>();
+        solve_any(dim, deg, MODE_MAP, !mixed, sa, thread_blocks(nt, 128), s);
+
+        if (mixed) {
+            int32_t nredo = 0;
+            PCMS_CU(cudaMemcpyAsync(&nredo, redo_n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            PCMS_CU(cudaStreamSynchronize(s));
+            if (nredo > 0) {
+                DBuf mom64(sizeof(double) * np * nredo, s);
+                AsmArgs r = a;
+                r.list = redo.as<int32_t>();
+                r.n_list = redo_n;
+                r.mom = mom64.p;
+                assemble_any(dim, deg, false, MODE_MAP, G, false, r, asm_blocks(nredo, G), s);
+                SolveArgs rs = sa;
+                rs.list = redo.as<int32_t>();
+                rs.n_list = redo_n;
+                rs.mom = mom64.p;
+                rs.tau = TAU_FP64;
+                rs.redo_on_fail = 0;
+                solve_any(dim, deg, MODE_MAP, true, rs, thread_blocks(nredo, 128), s);
+            }
+        }
+        ShapeArgs sh{};
+        sh.g = M.g;
+        sh.ns = ns;
+        sh.nt = nt;
+        sh.sx64 = M.src.x64.as<double>();
+        sh.hl0 = M.src.hl0.as<float4>();
+        sh.hl1 = M.src.hl1.as<float2>();
+        sh.tx64 = M.tgt.x64.as<double>();
+        sh.kexp = M.kexp.as<int32_t>();
+        sh.offsets = M.offsets.as<int64_t>();
+        sh.cols = M.cols.as<int32_t>();
+        sh.y = y.as<double>();
+        sh.radius = P.radius;
+        sh.weight = (int)P.weight;
+        sh.vals = M.vals.p;
+        shape_any(dim, deg, mixed, G, sh, asm_blocks(nt, G), s);
+
+        DBuf st(sizeof(unsigned long long) * 4, s);
+        PCMS_CU(cudaMemsetAsync(st.p, 0, st.bytes, s));
+        {
+        PCMS_TRACE("mls_status_stats", s);
+        k_stats<<<thread_blocks(nt, 256), 256, 0, s>>>(M.status.as<int8_t>(), M.counts.as<int32_t>(),
+                                                      M.kexp.as<int32_t>(), nt,
+                                                      st.as<unsigned long long>());
+        }
+        PCMS_LAUNCH_CHECK("k_stats");
+        unsigned long long hs[4];
+        unsigned herr = 0;
+        PCMS_CU(cudaMemcpyAsync(hs, st.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        PCMS_CU(cudaMemcpyAsync(&herr, err.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        PCMS_CU(cudaStreamSynchronize(s));
+        if (herr) fail(PCMS_ERR_CUDA, "internal: neighbour count mismatch between passes");
+        M.n_under = (int64_t)hs[0];
+        M.n_ill = (int64_t)hs[1];
+        M.max_count = (int64_t)hs[2];
+        M.max_k = (int64_t)hs[3];
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// radius search alone
+// ------------------------------------------------------------------------------------
+__global__ void k_counts_to_caller(int64_t nt, const int32_t* __restrict__ perm_t,
+                                   const int32_t* __restrict__ c, const int32_t* __restrict__ k,
+                                   int32_t* __restrict__ c_out, int32_t* __restrict__ k_out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t o = perm_t[i];
+        c_out[o] = c[i];
+        if (k_out) k_out[o] = k[i];
+    }
+}
+
+void mls_count(const MlsParams& P, const double* src, int64_t ns, const double* tgt, int64_t nt,
+               const pcms_map_opts& o, int32_t* counts, int32_t* kexp, int64_t* total,
+               cudaStream_t s) {
+    const int dim = P.dim;
+    const bool mixed = P.prec == PCMS_MIXED;
+    BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
+    Grid g = make_grid(dim, b.lo, b.hi, P.radius, MAX_CELLS);
+    SortedPoints S, Tp;
+    sort_points(g, src, ns, true, mixed, S, s);
+    sort_points(g, tgt, nt, false, false, Tp, s);
+    const int G = choose_group(dim, ns, P.radius, b.lo, b.hi);
+    DBuf c(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
+    DBuf k(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
+    DBuf off(sizeof(int64_t) * (nt + 1), s);
+    if (nt > 0) {
+        AsmArgs a = base_args(g, S, Tp, P);
+        a.counts = c.as<int32_t>();
+        a.kexp_out = k.as<int32_t>();
+        assemble_any(dim, 0, mixed, MODE_COUNT, G, false, a, asm_blocks(nt, G), s);
+        PCMS_TRACE("mls_counts_to_caller", s);
+        k_counts_to_caller<<<thread_blocks(nt, 256), 256, 0, s>>>(
+            nt, Tp.perm.as<int32_t>(), c.as<int32_t>(), k.as<int32_t>(), counts, kexp);
+        PCMS_LAUNCH_CHECK("counts_to_caller");
+    }
+    if (total) {
+        exclusive_scan<int64_t>(c.as<int32_t>(), off.as<int64_t>(), nt, s);
+        PCMS_CU(cudaMemcpyAsync(total, off.as<int64_t>() + nt, sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, s));
+        PCMS_CU(cudaStreamSynchronize(s));
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// one-shot transfer (no operator)
+// ------------------------------------------------------------------------------------
+void mls_transfer(const MlsParams& P, const double* src, int64_t ns, const double* tgt,
+                  int64_t nt, const pcms_map_opts& o, const void* fields, int nf, void* out,
+                  int8_t* status, cudaStream_t s, int64_t* n_under) {
+    const int dim = P.dim, deg = P.degree;
+    const bool mixed = P.prec == PCMS_MIXED;
+    *n_under = 0;
+    BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
+    Grid g = make_grid(dim, b.lo, b.hi, P.radius, MAX_CELLS);
+    SortedPoints S, Tp;
+    sort_points(g, src, ns, true, mixed, S, s);
+    sort_points(g, tgt, nt, false, false, Tp, s);
+    const int G = choose_group(dim, ns, P.radius, b.lo, b.hi);
+    const size_t fsz = mixed ? sizeof(float) : sizeof(double);
+    DBuf fs(fsz * std::max<int64_t>(ns, 1), s);
+    DBuf counts(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
+    DBuf kexp(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
+    const int np = accp(dim, deg, MODE_FUSED);
+    DBuf mom(fsz * np * std::max<int64_t>(nt, 1), s);
+    DBuf redo(sizeof(int32_t) * (nt + 1), s);
+    int32_t* redo_n = redo.as<int32_t>() + nt;
+    for (int f = 0; f < nf; f++) {
+        if (ns > 0) {
+            PCMS_TRACE("mls_field_to_sorted", s);
+            if (mixed)
+                k_permute_field<float><<<thread_blocks(ns, 256), 256, 0, s>>>(
+                    (const float*)fields + (int64_t)f * ns, S.inv.as<int32_t>(), ns, fs.as<float>());
+            else
+                k_permute_field<double><<<thread_blocks(ns, 256), 256, 0, s>>>(
+                    (const double*)fields + (int64_t)f * ns, S.inv.as<int32_t>(), ns, fs.as<double>());
+            PCMS_LAUNCH_CHECK("permute_field");
+        }
+        if (nt == 0) continue;
+        PCMS_CU(cudaMemsetAsync(redo_n, 0, sizeof(int32_t), s));
+        AsmArgs a = base_args(g, S, Tp, P);
+        a.counts = counts.as<int32_t>();
+        a.kexp_out = kexp.as<int32_t>();
+        a.field = fs.p;
+        a.mom = mom.p;
+        assemble_any(dim, deg, mixed, MODE_FUSED, G, !mixed, a, asm_blocks(nt, G), s);
+        SolveArgs sa{};
+        sa.nt = nt;
+        sa.counts = counts.as<int32_t>();
+        sa.mom = mom.p;
+        sa.lambda = P.lambda;
+        sa.tau = mixed ? TAU_MIXED : TAU_FP64;
+        sa.redo_on_fail = mixed ? 1 : 0;
+        sa.redo_list = redo.as<int32_t>();
+        sa.redo_n = redo_n;
+        sa.perm_t = Tp.perm.as<int32_t>();
+        sa.out = (char*)out + fsz * (size_t)f * nt;
+        sa.out_is_double = !mixed;
+        sa.status = f == 0 ? status : nullptr;
+        solve_any(dim, deg, MODE_FUSED, !mixed, sa, thread_blocks(nt, 128), s);
+        if (mixed) {
+            int32_t nredo = 0;
+            PCMS_CU(cudaMemcpyAsync(&nredo, redo_n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            PCMS_CU(cudaStreamSynchronize(s));
+            if (nredo > 0) {
+                DBuf mom64(sizeof(double) * np * nredo, s);
+                AsmArgs r = a;
+                r.list = redo.as<int32_t>();
+                r.n_list = redo_n;
+                r.kexp_in = kexp.as<int32_t>();
+                r.kexp_out = nullptr;
+                r.mom = mom64.p;
+                assemble_any(dim, deg, false, MODE_FUSED, G, false, r, asm_blocks(nredo, G), s);
+                SolveArgs rs = sa;
+                rs.list = redo.as<int32_t>();
+                rs.n_list = redo_n;
+                rs.mom = mom64.p;
+                rs.tau = TAU_FP64;
+                rs.redo_on_fail = 0;
+                solve_any(dim, deg, MODE_FUSED, true, rs, thread_blocks(nredo, 128), s);
+            }
+        }
+    }
+    if (status && P.min_neighbors == 0 && nt > 0) {
+        DBuf st(sizeof(unsigned long long) * 4, s);
+        PCMS_CU(cudaMemsetAsync(st.p, 0, st.bytes, s));
+        // status is in caller order; counts/kexp only feed the max statistics here
+        PCMS_TRACE("mls_status_stats", s);
+        k_stats<<<thread_blocks(nt, 256), 256, 0, s>>>(status, counts.as<int32_t>(),
+                                                      kexp.as<int32_t>(), nt,
+                                                      st.as<unsigned long long>());
+        PCMS_LAUNCH_CHECK("k_stats");
+        unsigned long long hs[4];
+        PCMS_CU(cudaMemcpyAsync(hs, st.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        PCMS_CU(cudaStreamSynchronize(s));
+        *n_under = (int64_t)hs[0];
+    }
+}
+
+}  // namespace pcms

@@ -1,0 +1,653 @@
+// mls_kernels.cuh -- device code of the meshless MLS transfer (Sec. 3.2.1, Eq. 1).
+//
+// Per target t, the sources s_j with |s_j - t| < r (and phi > 0) are selected; with
+// u_j = (s_j - t)/r, w_j = phi(|u_j|) and the graded-lex basis a(u) of degree k, the normal
+// equations of Eq. 1 are G c = g with
+//     G = sum_j w_j a(u_j) a(u_j)^T + lambda I,   g = sum_j w_j b_j a(u_j),
+// and the transferred value is c_0 (a(0) = e_1). G's entries are moments
+// M_p = sum_j w_j u_j^p over the monomials of degree <= 2k (15 instead of 21 entries in 2D
+// quadratic, 35 instead of 55 in 3D quadratic), so a pair costs one multiply-add per
+// moment. The cached operator stores N_j = w_j a(u_j)^T G^-1 e_1.
+//
+// Work split:
+//   k_assemble  -- a group of G lanes per target walks the candidate cells (rows of
+//                  contiguous cells in the counting-sorted source array), classifies
+//                  candidates (FP32 hi/lo distance filter; pairs within 2^-16 of the
+//                  radius are decided by the exact FP64 predicate), compacts the
+//                  selected pairs through a shared-memory ring so the accumulation runs
+//                  on full lanes, reduces the moments across the group and writes them.
+//   k_solve     -- one thread per target: FP64 LDL^T of G with a pivot guard, then
+//                  y = G^-1 e_1 (operator) or c_0 = e_1^T G^-1 g (one-shot transfer).
+//   k_shape     -- a group per target recomputes w_j a(u_j) and writes N_j.
+#pragma once
+
+#include "pcms_internal.cuh"
+
+namespace pcms {
+
+enum { MODE_COUNT = 0, MODE_MAP = 1, MODE_FUSED = 2 };
+
+constexpr float MIX_BAND = 1.52587890625e-05f;   // 2^-16 relative band around r^2
+constexpr int MAX_DOUBLINGS = 60;
+
+struct AsmArgs {
+    Grid g;
+    int64_t ns, nt;
+    const int32_t* cell_start;
+    const double* sx64;   // [dim][ns] sorted sources
+    const float4* hl0;    // mixed: sorted hi/lo
+    const float2* hl1;
+    const double* tx64;   // [dim][nt] sorted targets
+    const int32_t* list;  // optional target list (length *n_list); moments then indexed by list position
+    const int32_t* n_list;
+    double radius;
+    int weight;
+    int need;
+    const int32_t* kexp_in;  // starting doublings (MAP: exact; FUSED redo: start), or null
+    int32_t* kexp_out;       // COUNT/FUSED
+    int32_t* counts;
+    const int64_t* offsets;  // MAP
+    int32_t* cols;           // MAP
+    const void* field;       // FUSED: sorted field (float or double)
+    void* mom;               // MAP/FUSED: [nt][NACCP]
+    unsigned* err;
+};
+
+struct SolveArgs {
+    int64_t nt;
+    const int32_t* list;
+    const int32_t* n_list;
+    const int32_t* counts;
+    const void* mom;          // [nt][NACCP] (float or double)
+    double lambda;
+    double tau;               // pivot guard: d_k <= tau * G_kk fails
+    int redo_on_fail;         // 1: append to redo list instead of ILL
+    int32_t* redo_list;
+    int32_t* redo_n;
+    double* y;                // MAP: [nt][m]
+    int8_t* status;           // MAP: sorted order; FUSED: caller order (via perm) or null
+    const int32_t* perm_t;    // FUSED: sorted -> caller target index
+    void* out;                // FUSED: caller-order output (float or double)
+    int out_is_double;
+};
+
+struct ShapeArgs {
+    Grid g;
+    int64_t ns, nt;
+    const double* sx64;
+    const float4* hl0;
+    const float2* hl1;
+    const double* tx64;
+    const int32_t* kexp;
+    const int64_t* offsets;
+    const int32_t* cols;
+    const double* y;
+    double radius;
+    int weight;
+    void* vals;
+};
+
+// ------------------------------------------------------------------------------------
+// weights (value only; selection is decided separately)
+// ------------------------------------------------------------------------------------
+template <typename T>
+__host__ __device__ __forceinline__ T weight_value(int kind, T q) {
+    const T one = T(1);
+    switch (kind) {
+    case PCMS_WENDLAND_C2: {
+        T t = one - q;
+        T t2 = t * t;
+        return t2 * t2 * (T(4) * q + one);
+    }
+    case PCMS_GAUSSIAN: return exp(-(T(4) * q * q));
+    case PCMS_C4: {
+        T t = one - q;
+        T t2 = t * t;
+        T t6 = t2 * t2 * t2;
+        T p = ((((T(5) * q + T(30)) * q + T(72)) * q + T(82)) * q + T(36)) * q + T(6);
+        return p * t6;
+    }
+    case PCMS_MQ: return sqrt(one + T(4) * q * q);
+    case PCMS_IMQ: return one / sqrt(one + T(4) * q * q);
+    case PCMS_TPS: {
+        T aq = T(2) * q;
+        return aq == T(0) ? T(0) : aq * aq * log(aq);
+    }
+    case PCMS_CUBIC: {
+        T aq = T(2) * q;
+        return aq * aq * aq;
+    }
+    default: return one;  // CONST, NOOP
+    }
+}
+
+// Exact selection, evaluated as the definition does: d2 < r*r and phi(sqrt(d2)/r) > 0 with
+// IEEE sqrt and division. The sign of phi reduces to a test on q for every kind: Wendland
+// and C4 are positive iff q < 1 (their factors cannot underflow for q < 1); Gaussian, MQ,
+// IMQ, Const and No_Op are positive for every q < 1; TPS (2q)^2 ln(2q) iff 2q > 1; cubic
+// (2q)^3 iff the product does not underflow to zero.
+__device__ __forceinline__ bool select_exact(int kind, double d2, double r, double r2) {
+    if (!(d2 < r2)) return false;
+    double q = __ddiv_rn(__dsqrt_rn(d2), r);
+    switch (kind) {
+    case PCMS_WENDLAND_C2:
+    case PCMS_C4: return q < 1.0;
+    case PCMS_TPS: return __dmul_rn(2.0, q) > 1.0;
+    case PCMS_CUBIC: {
+        double aq = __dmul_rn(2.0, q);
+        return __dmul_rn(__dmul_rn(aq, aq), aq) > 0.0;
+    }
+    default: return true;
+    }
+}
+
+// FP64 selection with shortcuts that never change the decision
+__device__ __forceinline__ bool select64(int kind, double d2, double r, double r2, double r2_in) {
+    if (!(d2 < r2)) return false;
+    if (kind == PCMS_TPS || kind == PCMS_CUBIC) return select_exact(kind, d2, r, r2);
+    if (d2 < r2_in) return true;   // r2_in = r2 (1 - 2^-40): q < 1 certainly
+    return select_exact(kind, d2, r, r2);
+}
+
+// FP32 classification: 1 inside, 0 outside, -1 decide exactly
+__device__ __forceinline__ int classify32(int kind, float d2, float r2) {
+    if (d2 > r2 * (1.0f + MIX_BAND)) return 0;
+    const bool in_up = d2 < r2 * (1.0f - MIX_BAND);
+    if (kind == PCMS_TPS) {
+        const float q2 = 0.25f * r2;
+        if (d2 < q2 * (1.0f - MIX_BAND)) return 0;
+        if (d2 <= q2 * (1.0f + MIX_BAND)) return -1;
+    } else if (kind == PCMS_CUBIC) {
+        if (d2 < r2 * 9.094947e-13f) return -1;   // 2^-40
+    }
+    return in_up ? 1 : -1;
+}
+
+// exact FP64 squared distance, summed left to right without contraction
+template <int DIM>
+__device__ __forceinline__ double dist2_exact(const double* __restrict__ sx64, int64_t ns, int64_t j,
+                                              const double* t) {
+    double dx = __dsub_rn(sx64[j], t[0]);
+    double dy = __dsub_rn(sx64[ns + j], t[1]);
+    double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    if (DIM == 3) {
+        double dz = __dsub_rn(sx64[2 * ns + j], t[2]);
+        d2 = __dadd_rn(d2, __dmul_rn(dz, dz));
+    }
+    return d2;
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// source index carried through the queue's payload slot, bit-exact
+__device__ __forceinline__ float pack_index(int j, float) { return __int_as_float(j); }
+__device__ __forceinline__ double pack_index(int j, double) { return (double)j; }
+__device__ __forceinline__ int unpack_index(float v) { return __float_as_int(v); }
+__device__ __forceinline__ int unpack_index(double v) { return (int)v; }
+
+template <typename T> struct QEntry;
+template <> struct QEntry<float> { using type = float4; };
+template <> struct QEntry<double> { using type = double4; };
+
+template <typename T>
+__device__ __forceinline__ typename QEntry<T>::type make_entry(T a, T b, T c, T d);
+template <>
+__device__ __forceinline__ float4 make_entry<float>(float a, float b, float c, float d) {
+    return make_float4(a, b, c, d);
+}
+template <>
+__device__ __forceinline__ double4 make_entry<double>(double a, double b, double c, double d) {
+    return make_double4(a, b, c, d);
+}
+
+// accumulate one selected pair: dx (target-relative offsets), payload b (field value)
+template <int DIM, int DEG, int MODE, typename T, int NACC>
+__host__ __device__ __forceinline__ void accumulate(T (&acc)[NACC > 0 ? NACC : 1], const T* dx,
+                                                    T b, int kind, T inv_r) {
+    constexpr int NM = mono_count(DIM, 2 * DEG);
+    constexpr int M = mono_count(DIM, DEG);
+    T d2 = dx[0] * dx[0] + dx[1] * dx[1];
+    if (DIM == 3) d2 += dx[2] * dx[2];
+    T q;
+#ifdef __CUDA_ARCH__
+    if constexpr (std::is_same<T, float>::value) q = sqrt_approx(d2) * inv_r;
+    else q = sqrt(d2) * inv_r;
+#else
+    q = sqrt(d2) * inv_r;
+#endif
+    T w = weight_value<T>(kind, q);
+    T u[3];
+    u[0] = dx[0] * inv_r;
+    u[1] = dx[1] * inv_r;
+    u[2] = DIM == 3 ? dx[2] * inv_r : T(0);
+    T wm[NM];
+    wm[0] = w;
+    acc[0] += w;
+    sfor<NM - 1>([&](auto I) {
+        constexpr int p = decltype(I)::value + 1;
+        constexpr int par = mono_parent(DIM, p);
+        constexpr int v = mono_var(DIM, p);
+        wm[p] = wm[par] * u[v];
+        acc[p] += wm[p];
+    });
+    if constexpr (MODE == MODE_FUSED) {
+        T wb[M];
+        wb[0] = w * b;
+        acc[NM] += wb[0];
+        sfor<M - 1>([&](auto I) {
+            constexpr int p = decltype(I)::value + 1;
+            constexpr int par = mono_parent(DIM, p);
+            constexpr int v = mono_var(DIM, p);
+            wb[p] = wb[par] * u[v];
+            acc[NM + p] += wb[p];
+        });
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// k_assemble
+// ------------------------------------------------------------------------------------
+template <int DIM, int DEG, bool MIXED, int MODE, int G, typename FT>
+__global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
+    using T = typename std::conditional<MIXED, float, double>::type;
+    using QE = typename QEntry<T>::type;
+    constexpr int NM = mono_count(DIM, 2 * DEG);
+    constexpr int M = mono_count(DIM, DEG);
+    constexpr int NACC = MODE == MODE_FUSED ? NM + M : (MODE == MODE_MAP ? NM : 0);
+    constexpr int NACCP = round_up4(NACC > 0 ? NACC : 1);
+    constexpr int GPW = 32 / G;
+    constexpr int QCAP = 2 * G;
+    __shared__ QE qbuf[8][64];
+
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int gi = lane / G, gl = lane % G;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (gi * G));
+    const unsigned lt = (1u << lane) - 1u;
+    QE* q = &qbuf[wib][gi * QCAP];
+
+    const int64_t ngroups = (int64_t)gridDim.x * (blockDim.x >> 5) * GPW;
+    const int64_t gid = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * GPW + gi;
+    const int64_t nwork = A.list ? (int64_t)(*A.n_list) : A.nt;
+    const Grid& g = A.g;
+
+    for (int64_t wk = gid; wk < nwork; wk += ngroups) {
+        const int64_t t = A.list ? (int64_t)A.list[wk] : wk;
+        double tx[3] = {0.0, 0.0, 0.0};
+        long long ct[3] = {0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < DIM; d++) {
+            tx[d] = A.tx64[d * A.nt + t];
+            double f = floor((tx[d] - g.lo[d]) * g.inv_h);
+            f = fmin(fmax(f, -1073741824.0), 1073741824.0);
+            ct[d] = (long long)f;
+        }
+        float thi[3] = {0.f, 0.f, 0.f}, tlo[3] = {0.f, 0.f, 0.f};
+        if (MIXED) {
+#pragma unroll
+            for (int d = 0; d < DIM; d++) {
+                double rel = tx[d] - g.lo[d];
+                thi[d] = (float)rel;
+                tlo[d] = (float)(rel - (double)thi[d]);
+            }
+        }
+        int k = A.kexp_in ? A.kexp_in[t] : 0;
+        int cnt = 0;
+        int64_t row_off = 0, row_len = 0;
+        if (MODE == MODE_MAP) {
+            row_off = A.offsets[t];
+            row_len = A.offsets[t + 1] - row_off;
+        }
+        T acc[NACC > 0 ? NACC : 1];
+        for (;;) {
+            const double r = ldexp(A.radius, k);
+            const double r2 = r * r;
+            const double r2_in = r2 * (1.0 - 9.094947017729282e-13);
+            const float r2f = (float)r2;
+            const T inv_r = (T)(1.0 / r);
+            const long long wc = k >= 30 ? (1LL << 30) : (1LL << k);
+            long long lo_[3], hi_[3];
+            bool empty = false;
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                if (d < DIM) {
+                    lo_[d] = max(ct[d] - wc, 0LL);
+                    hi_[d] = min(ct[d] + wc, (long long)g.n[d] - 1);
+                    empty |= lo_[d] > hi_[d];
+                } else {
+                    lo_[d] = hi_[d] = 0;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < (NACC > 0 ? NACC : 1); i++) acc[i] = T(0);
+            cnt = 0;
+            int qn = 0, head = 0;
+            int64_t written = 0;
+            if (!empty) {
+                for (long long cz = lo_[2]; cz <= hi_[2]; ++cz)
+                    for (long long cy = lo_[1]; cy <= hi_[1]; ++cy) {
+                        const int64_t rowbase = (cz * g.n[1] + cy) * (int64_t)g.n[0];
+                        const int a = A.cell_start[rowbase + lo_[0]];
+                        const int b = A.cell_start[rowbase + hi_[0] + 1];
+                        for (int j0 = a; j0 < b; j0 += G) {
+                            const int j = j0 + gl;
+                            bool in = false;
+                            T dx[3] = {T(0), T(0), T(0)};
+                            if (j < b) {
+                                if (MIXED) {
+                                    float4 h0 = A.hl0[j];
+                                    float ddx, ddy, ddz = 0.f;
+                                    if (DIM == 2) {
+                                        ddx = (h0.x - thi[0]) + (h0.z - tlo[0]);
+                                        ddy = (h0.y - thi[1]) + (h0.w - tlo[1]);
+                                    } else {
+                                        float2 h1 = A.hl1[j];
+                                        ddx = (h0.x - thi[0]) + (h0.w - tlo[0]);
+                                        ddy = (h0.y - thi[1]) + (h1.x - tlo[1]);
+                                        ddz = (h0.z - thi[2]) + (h1.y - tlo[2]);
+                                    }
+                                    float d2f = ddx * ddx + ddy * ddy;
+                                    if (DIM == 3) d2f += ddz * ddz;
+                                    int c = classify32(A.weight, d2f, r2f);
+                                    if (c < 0)
+                                        c = select_exact(A.weight, dist2_exact<DIM>(A.sx64, A.ns, j, tx),
+                                                         r, r2);
+                                    in = c != 0;
+                                    dx[0] = (T)ddx;
+                                    dx[1] = (T)ddy;
+                                    dx[2] = (T)ddz;
+                                } else {
+                                    double e0 = __dsub_rn(A.sx64[j], tx[0]);
+                                    double e1 = __dsub_rn(A.sx64[A.ns + j], tx[1]);
+                                    double d2 = __dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1));
+                                    double e2 = 0.0;
+                                    if (DIM == 3) {
+                                        e2 = __dsub_rn(A.sx64[2 * A.ns + j], tx[2]);
+                                        d2 = __dadd_rn(d2, __dmul_rn(e2, e2));
+                                    }
+                                    in = select64(A.weight, d2, r, r2, r2_in);
+                                    dx[0] = (T)e0;
+                                    dx[1] = (T)e1;
+                                    dx[2] = (T)e2;
+                                }
+                            }
+                            const unsigned bal = __ballot_sync(gmask, in) & gmask;
+                            const int nin = __popc(bal);
+                            if (MODE == MODE_COUNT) {
+                                cnt += nin;
+                                continue;
+                            }
+                            if (in) {
+                                T pay;
+                                if (MODE == MODE_MAP) pay = pack_index(j, T(0));
+                                else pay = (T)(((const FT*)A.field)[j]);
+                                const int pos = (head + qn + __popc(bal & lt)) & (QCAP - 1);
+                                q[pos] = make_entry<T>(dx[0], dx[1], dx[2], pay);
+                            }
+                            qn += nin;
+                            cnt += nin;
+                            __syncwarp(gmask);
+                            if (qn >= G) {
+                                QE e = q[(head + gl) & (QCAP - 1)];
+                                T edx[3] = {e.x, e.y, e.z};
+                                accumulate<DIM, DEG, MODE, T, NACC>(acc, edx, e.w, A.weight, inv_r);
+                                if (MODE == MODE_MAP) {
+                                    if (written + gl < row_len) A.cols[row_off + written + gl] = unpack_index(e.w);
+                                    written += G;
+                                }
+                                head = (head + G) & (QCAP - 1);
+                                qn -= G;
+                                __syncwarp(gmask);
+                            }
+                        }
+                    }
+                if (MODE != MODE_COUNT && qn > 0) {
+                    if (gl < qn) {
+                        QE e = q[(head + gl) & (QCAP - 1)];
+                        T edx[3] = {e.x, e.y, e.z};
+                        accumulate<DIM, DEG, MODE, T, NACC>(acc, edx, e.w, A.weight, inv_r);
+                        if (MODE == MODE_MAP && written + gl < row_len)
+                            A.cols[row_off + written + gl] = unpack_index(e.w);
+                    }
+                    __syncwarp(gmask);
+                }
+            }
+            if (MODE != MODE_MAP && A.need > 0 && cnt < A.need && k < MAX_DOUBLINGS && cnt < A.ns) {
+                ++k;
+                continue;
+            }
+            break;
+        }
+        if (NACC > 0) {
+#pragma unroll
+            for (int i = 0; i < (NACC > 0 ? NACC : 1); i++) {
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(gmask, acc[i], o);
+            }
+        }
+        if (gl == 0) {
+            if (NACC > 0) {
+                T* dst = (T*)A.mom + (A.list ? wk : t) * NACCP;   // list mode: by list position
+#pragma unroll
+                for (int i = 0; i < NACCP; i++) dst[i] = i < NACC ? acc[i < NACC ? i : 0] : T(0);
+            }
+            A.counts[t] = cnt;
+            if (A.kexp_out) A.kexp_out[t] = k;
+            if (MODE == MODE_MAP && cnt != row_len) atomicOr(A.err, 1u);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// per-target solve: G from the moments (+ lambda on the diagonal), LDL^T with the pivot
+// guard d_k > tau * G_kk for every k (d_k / G_kk = R_kk^2 / ||column k||^2 of the weighted
+// Vandermonde matrix), then
+//   MODE_MAP:   out[0..m) = G^-1 e_1                 (L w = e_1, z = D^-1 w, L^T y = z)
+//   MODE_FUSED: out[0]    = e_1^T G^-1 g = (L^-1 e_1)^T D^-1 (L^-1 g)
+// mom = [moments of degree <= 2k (graded-lex)] [g (FUSED only)]. Returns false when the
+// guard fails. Host-callable so the algebra can be checked without a GPU.
+// ------------------------------------------------------------------------------------
+template <int DIM, int DEG, int MODE>
+__host__ __device__ __forceinline__ bool solve_moments(const double* mom, double lambda,
+                                                       double tau, double* out) {
+    constexpr int NM = mono_count(DIM, 2 * DEG);
+    constexpr int M = mono_count(DIM, DEG);
+    constexpr int NP = M * (M + 1) / 2;
+    double L[NP];
+    sfor<M>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        sfor<k + 1>([&](auto Lx) {
+            constexpr int l = decltype(Lx)::value;
+            L[k * (k + 1) / 2 + l] = mom[mono_prod(DIM, k, l)] + (k == l ? lambda : 0.0);
+        });
+    });
+    double invd[M];
+    bool ok = true;
+    sfor<M>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        sfor<k>([&](auto Jx) {
+            constexpr int j = decltype(Jx)::value;
+            double s = L[k * (k + 1) / 2 + j];
+            sfor<j>([&](auto Ix) {
+                constexpr int i = decltype(Ix)::value;
+                s -= L[k * (k + 1) / 2 + i] * (L[j * (j + 1) / 2 + i] * L[i * (i + 1) / 2 + i]);
+            });
+            L[k * (k + 1) / 2 + j] = s * invd[j];
+        });
+        const double gkk = L[k * (k + 1) / 2 + k];
+        double dk = gkk;
+        sfor<k>([&](auto Jx) {
+            constexpr int j = decltype(Jx)::value;
+            const double lkj = L[k * (k + 1) / 2 + j];
+            dk -= lkj * lkj * L[j * (j + 1) / 2 + j];
+        });
+        ok = ok && (dk > tau * gkk);
+        L[k * (k + 1) / 2 + k] = dk;
+        invd[k] = 1.0 / dk;
+    });
+    if (!ok) return false;
+    if (MODE == MODE_FUSED) {
+        double z1[M], zg[M];
+        sfor<M>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            double a = k == 0 ? 1.0 : 0.0;
+            double b = mom[NM + k];
+            sfor<k>([&](auto Jx) {
+                constexpr int j = decltype(Jx)::value;
+                a -= L[k * (k + 1) / 2 + j] * z1[j];
+                b -= L[k * (k + 1) / 2 + j] * zg[j];
+            });
+            z1[k] = a;
+            zg[k] = b;
+        });
+        double c0 = 0.0;
+        for (int k = 0; k < M; k++) c0 += z1[k] * invd[k] * zg[k];
+        out[0] = c0;
+    } else {
+        double w[M], z[M];
+        sfor<M>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            double a = k == 0 ? 1.0 : 0.0;
+            sfor<k>([&](auto Jx) {
+                constexpr int j = decltype(Jx)::value;
+                a -= L[k * (k + 1) / 2 + j] * w[j];
+            });
+            w[k] = a;
+            z[k] = a * invd[k];
+        });
+        sfor<M>([&](auto K) {
+            constexpr int k = M - 1 - decltype(K)::value;
+            double a = z[k];
+            sfor<M - 1 - k>([&](auto Jx) {
+                constexpr int j = k + 1 + decltype(Jx)::value;
+                a -= L[j * (j + 1) / 2 + k] * out[j];
+            });
+            out[k] = a;
+        });
+    }
+    return true;
+}
+
+// ------------------------------------------------------------------------------------
+// k_solve: one thread per target
+// ------------------------------------------------------------------------------------
+template <int DIM, int DEG, int MODE, typename MT>
+__global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
+    constexpr int NM = mono_count(DIM, 2 * DEG);
+    constexpr int M = mono_count(DIM, DEG);
+    constexpr int NACC = MODE == MODE_FUSED ? NM + M : NM;
+    constexpr int NACCP = round_up4(NACC);
+    const int64_t nwork = S.list ? (int64_t)(*S.n_list) : S.nt;
+    for (int64_t wk = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; wk < nwork;
+         wk += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = S.list ? (int64_t)S.list[wk] : wk;
+        const int cnt = S.counts[t];
+        int st = PCMS_TARGET_OK;
+        double val = 0.0;
+        double y[M];
+        if (cnt < M) {
+            st = PCMS_TARGET_UNDERDETERMINED;
+        } else {
+            const MT* src = (const MT*)S.mom + (S.list ? wk : t) * NACCP;
+            double mom[NACC];
+#pragma unroll
+            for (int i = 0; i < NACC; i++) mom[i] = (double)src[i];
+            if (!solve_moments<DIM, DEG, MODE>(mom, S.lambda, S.tau, y))
+                st = PCMS_TARGET_ILL_CONDITIONED;
+            val = y[0];
+        }
+        if (st == PCMS_TARGET_ILL_CONDITIONED && S.redo_on_fail) {
+            int pos = atomicAdd(S.redo_n, 1);
+            S.redo_list[pos] = (int32_t)t;
+            continue;   // the FP64 pass writes this target
+        }
+        const double nanv = __longlong_as_double(0x7ff8000000000000LL);
+        if (MODE == MODE_FUSED) {
+            const int64_t o = S.perm_t ? (int64_t)S.perm_t[t] : t;
+            const double v = st == PCMS_TARGET_OK ? val : nanv;
+            if (S.out_is_double) ((double*)S.out)[o] = v;
+            else ((float*)S.out)[o] = (float)v;
+            if (S.status) S.status[o] = (int8_t)st;
+        } else {
+#pragma unroll
+            for (int k = 0; k < M; k++) S.y[t * M + k] = st == PCMS_TARGET_OK ? y[k] : nanv;
+            S.status[t] = (int8_t)st;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// k_shape: N_j = w_j a(u_j)^T y
+// ------------------------------------------------------------------------------------
+template <int DIM, int DEG, bool MIXED, int G>
+__global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
+    using T = typename std::conditional<MIXED, float, double>::type;
+    constexpr int M = mono_count(DIM, DEG);
+    constexpr int GPW = 32 / G;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int gi = lane / G, gl = lane % G;
+    const int64_t ngroups = (int64_t)gridDim.x * (blockDim.x >> 5) * GPW;
+    const int64_t gid = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * GPW + gi;
+    const Grid& g = S.g;
+    for (int64_t t = gid; t < S.nt; t += ngroups) {
+        double tx[3] = {0, 0, 0};
+        float thi[3] = {0.f, 0.f, 0.f}, tlo[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int d = 0; d < DIM; d++) {
+            tx[d] = S.tx64[d * S.nt + t];
+            if (MIXED) {
+                double rel = tx[d] - g.lo[d];
+                thi[d] = (float)rel;
+                tlo[d] = (float)(rel - (double)thi[d]);
+            }
+        }
+        T y[M];
+#pragma unroll
+        for (int k = 0; k < M; k++) y[k] = (T)S.y[t * M + k];
+        const double r = ldexp(S.radius, S.kexp[t]);
+        const T inv_r = (T)(1.0 / r);
+        const int64_t a = S.offsets[t], b = S.offsets[t + 1];
+        for (int64_t i = a + gl; i < b; i += G) {
+            const int j = S.cols[i];
+            T dx[3] = {T(0), T(0), T(0)};
+            if (MIXED) {
+                float4 h0 = S.hl0[j];
+                if (DIM == 2) {
+                    dx[0] = (h0.x - thi[0]) + (h0.z - tlo[0]);
+                    dx[1] = (h0.y - thi[1]) + (h0.w - tlo[1]);
+                } else {
+                    float2 h1 = S.hl1[j];
+                    dx[0] = (h0.x - thi[0]) + (h0.w - tlo[0]);
+                    dx[1] = (h0.y - thi[1]) + (h1.x - tlo[1]);
+                    dx[2] = (h0.z - thi[2]) + (h1.y - tlo[2]);
+                }
+            } else {
+#pragma unroll
+                for (int d = 0; d < DIM; d++) dx[d] = (T)(S.sx64[d * S.ns + j] - tx[d]);
+            }
+            T d2 = dx[0] * dx[0] + dx[1] * dx[1];
+            if (DIM == 3) d2 += dx[2] * dx[2];
+            T qv;
+            if constexpr (MIXED) qv = sqrt_approx(d2) * inv_r;
+            else qv = sqrt(d2) * inv_r;
+            const T w = weight_value<T>(S.weight, qv);
+            T u[3] = {dx[0] * inv_r, dx[1] * inv_r, dx[2] * inv_r};
+            T am[M];
+            am[0] = T(1);
+            T s = y[0];
+            sfor<M - 1>([&](auto I) {
+                constexpr int p = decltype(I)::value + 1;
+                constexpr int par = mono_parent(DIM, p);
+                constexpr int v = mono_var(DIM, p);
+                am[p] = am[par] * u[v];
+                s += am[p] * y[p];
+            });
+            ((T*)S.vals)[i] = w * s;
+        }
+    }
+}
+
+}  // namespace pcms

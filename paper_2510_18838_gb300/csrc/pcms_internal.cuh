@@ -1,0 +1,235 @@
+// pcms_internal.cuh -- shared declarations of the GB300 field-transfer library.
+//
+// Nothing here is visible through the C ABI (include/pcms.h). Internal errors are C++
+// exceptions (PcmsError) that capi.cu converts into a pcms_status at the boundary.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <type_traits>
+#include <utility>
+
+#include "pcms.h"
+
+namespace pcms {
+
+// ------------------------------------------------------------------------------------
+// errors
+// ------------------------------------------------------------------------------------
+struct PcmsError {
+    pcms_status status;
+    std::string msg;
+};
+
+[[noreturn]] void fail(pcms_status st, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+
+#define PCMS_CU(x) ::pcms::check_cuda((x), #x)
+#define PCMS_LAUNCH_CHECK(name) ::pcms::check_cuda(cudaGetLastError(), name)
+
+// ------------------------------------------------------------------------------------
+// stream-ordered device memory (cudaMallocAsync / cudaFreeAsync on one stream)
+// ------------------------------------------------------------------------------------
+void ensure_mempool(int device);
+
+struct DBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaStream_t s = nullptr;
+    DBuf() = default;
+    DBuf(size_t b, cudaStream_t st) { alloc(b, st); }
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept : p(o.p), bytes(o.bytes), s(o.s) { o.p = nullptr; o.bytes = 0; }
+    DBuf& operator=(DBuf&& o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p; bytes = o.bytes; s = o.s;
+            o.p = nullptr; o.bytes = 0;
+        }
+        return *this;
+    }
+    ~DBuf() { release(); }
+    void alloc(size_t b, cudaStream_t st);
+    void release();
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ------------------------------------------------------------------------------------
+// uniform grid (Sec. 3.3 search structure)
+// ------------------------------------------------------------------------------------
+struct Grid {
+    int dim;
+    int n[3];         // cells per axis (1 for unused axes)
+    int64_t ncell;
+    double lo[3];     // origin (bounding-box minimum)
+    double h, inv_h;  // cell edge and its reciprocal
+};
+
+// Cell edge h = r (1 + 2^-20) and cells per axis from a bounding box; h doubles until the
+// grid has at most max_cells cells. Every point within r of a target lies in a cell at
+// most 2^k cells away (per axis) from the target's cell, for radius r 2^k.
+Grid make_grid(int dim, const double* lo, const double* hi, double radius, int64_t max_cells);
+
+// ------------------------------------------------------------------------------------
+// points sorted by cell (counting sort)
+// ------------------------------------------------------------------------------------
+struct SortedPoints {
+    int dim = 0;
+    int64_t n = 0;
+    DBuf cell_start;  // int32 [ncell+1]   (sources only)
+    DBuf perm;        // int32 [n]: sorted position -> caller index
+    DBuf inv;         // int32 [n]: caller index -> sorted position
+    DBuf x64;         // float64 [dim][n] sorted coordinates
+    DBuf hl0;         // float4 [n] (mixed path): 2D {xh,yh,xl,yl}; 3D {xh,yh,zh,xl}
+    DBuf hl1;         // float2 [n] (mixed path, 3D): {yl,zl}
+};
+
+// bounding box of pts (float64 [dim][n]) into dev_box[6] = {lo0,lo1,lo2,hi0,hi1,hi2};
+// *dev_bad counts non-finite coordinates. Both are device buffers zero/initialised here.
+void launch_bbox(int dim, const double* pts, int64_t n, double* dev_box, long long* dev_enc,
+                 unsigned long long* dev_bad, cudaStream_t s);
+
+// Sort points by cell of grid g. with_start: also build cell_start (sources).
+// with_hl: also write FP32 hi/lo coordinates relative to g.lo (mixed path).
+void sort_points(const Grid& g, const double* pts, int64_t n, bool with_start, bool with_hl,
+                 SortedPoints& out, cudaStream_t s);
+
+// exclusive scan of int32 counts into out[0..n] (out[n] = total); T = int32_t or int64_t
+template <typename T>
+void exclusive_scan(const int32_t* in, T* out, int64_t n, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------
+// compile-time monomial tables (graded-lex: by degree, then exponent of x descending,
+// then exponent of y descending). 2D: 1, x, y, x^2, xy, y^2, ...; 3D: 1, x, y, z, x^2, xy,
+// xz, y^2, yz, z^2, ...
+// ------------------------------------------------------------------------------------
+struct Exp3 {
+    int e[3];
+};
+
+__host__ __device__ constexpr int mono_count(int dim, int deg) {
+    return dim == 2 ? (deg + 1) * (deg + 2) / 2 : (deg + 1) * (deg + 2) * (deg + 3) / 6;
+}
+
+__host__ __device__ constexpr Exp3 mono_exp(int dim, int p) {
+    int idx = 0;
+    for (int g = 0; g <= 8; ++g)
+        for (int e0 = g; e0 >= 0; --e0) {
+            if (dim == 2) {
+                if (idx == p) return Exp3{{e0, g - e0, 0}};
+                ++idx;
+            } else {
+                for (int e1 = g - e0; e1 >= 0; --e1) {
+                    if (idx == p) return Exp3{{e0, e1, g - e0 - e1}};
+                    ++idx;
+                }
+            }
+        }
+    return Exp3{{-1, -1, -1}};
+}
+
+__host__ __device__ constexpr int mono_index(int dim, int e0, int e1, int e2) {
+    for (int p = 0; p < mono_count(dim, 8); ++p) {
+        Exp3 x = mono_exp(dim, p);
+        if (x.e[0] == e0 && x.e[1] == e1 && x.e[2] == e2) return p;
+    }
+    return -1;
+}
+
+// first variable with a positive exponent, and the monomial with that exponent lowered
+__host__ __device__ constexpr int mono_var(int dim, int p) {
+    Exp3 x = mono_exp(dim, p);
+    return x.e[0] > 0 ? 0 : (x.e[1] > 0 ? 1 : 2);
+}
+
+__host__ __device__ constexpr int mono_parent(int dim, int p) {
+    Exp3 x = mono_exp(dim, p);
+    int v = mono_var(dim, p);
+    x.e[v] -= 1;
+    return mono_index(dim, x.e[0], x.e[1], x.e[2]);
+}
+
+// index of the product of monomials k and l
+__host__ __device__ constexpr int mono_prod(int dim, int k, int l) {
+    Exp3 a = mono_exp(dim, k), b = mono_exp(dim, l);
+    return mono_index(dim, a.e[0] + b.e[0], a.e[1] + b.e[1], a.e[2] + b.e[2]);
+}
+
+// static_for: calls f(std::integral_constant<int, I>) for I = 0 .. N-1 (indices are
+// compile-time constants, so register arrays indexed by them stay in registers)
+template <class F, int... Is>
+__host__ __device__ __forceinline__ void sfor_impl(F&& f, std::integer_sequence<int, Is...>) {
+    (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, class F>
+__host__ __device__ __forceinline__ void sfor(F&& f) {
+    sfor_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+__host__ __device__ constexpr int round_up4(int x) { return (x + 3) & ~3; }
+
+// ------------------------------------------------------------------------------------
+// MLS entry points (mls.cu)
+// ------------------------------------------------------------------------------------
+struct MlsParams {
+    int dim, degree, m;
+    pcms_precision prec;
+    pcms_weight weight;
+    double radius, lambda;
+    int min_neighbors;
+    int need;  // max(min_neighbors, m) if min_neighbors > 0 else 0
+};
+
+struct MapImpl {
+    MlsParams P;
+    Grid g;
+    int64_t ns = 0, nt = 0, nnz = 0;
+    cudaStream_t stream = nullptr;
+    SortedPoints src, tgt;
+    DBuf counts;     // int32 [nt] (sorted target order)
+    DBuf kexp;       // int32 [nt]
+    DBuf status;     // int8  [nt]
+    DBuf offsets;    // int64 [nt+1]
+    DBuf cols;       // int32 [nnz] sorted source positions
+    DBuf vals;       // float64 or float32 [nnz]
+    int64_t n_under = 0, n_ill = 0, max_count = 0, max_k = 0;
+    int64_t device_bytes() const;
+};
+
+void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms_map_opts& o);
+void mls_apply(MapImpl& M, const void* fields, int nf, void* out, cudaStream_t s);
+void mls_export(MapImpl& M, int64_t* offsets, int32_t* cols, double* vals, int8_t* status,
+                int32_t* kexp, cudaStream_t s);
+void mls_count(const MlsParams& P, const double* src, int64_t ns, const double* tgt, int64_t nt,
+               const pcms_map_opts& o, int32_t* counts, int32_t* kexp, int64_t* total,
+               cudaStream_t s);
+void mls_transfer(const MlsParams& P, const double* src, int64_t ns, const double* tgt,
+                  int64_t nt, const pcms_map_opts& o, const void* fields, int nf, void* out,
+                  int8_t* status, cudaStream_t s, int64_t* n_under);
+
+// ------------------------------------------------------------------------------------
+// mesh (mesh.cu)
+// ------------------------------------------------------------------------------------
+struct MeshImpl {
+    int64_t nv = 0, ntri = 0, npairs = 0;
+    cudaStream_t stream = nullptr;
+    Grid g;
+    double bbox[4];    // lo_x, lo_y, hi_x, hi_y of all vertices
+    DBuf xy;           // float64 [2][nv]
+    DBuf tri;          // int32 [3][ntri]
+    DBuf cell_start;   // int32 [ncell+1]
+    DBuf items;        // int32 [npairs] triangle ids, ascending within a cell
+    DBuf tsign;        // int8 [ntri] orientation sign of each triangle (0 = degenerate)
+};
+
+void mesh_create(MeshImpl& M, const double* xy, int64_t nv, const int32_t* tri, int64_t ntri);
+void mesh_locate(const MeshImpl& M, const double* pts, int64_t n, const double* field,
+                 int32_t* elem, int8_t* edim, double* vals, cudaStream_t s);
+
+// number of SMs of the current device (cached)
+int num_sms();
+
+}  // namespace pcms

@@ -1,0 +1,33 @@
+// trace.cuh -- scope object that times one kernel launch with CUDA events on its stream
+// when tracing is enabled (pcms_trace_enable).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace pcms {
+
+bool trace_on();
+void trace_enable(int on);
+int trace_count();
+int trace_get(int i, char* name, int name_len, int64_t* launches, double* total_ms);
+
+class TraceScope {
+public:
+    TraceScope(const char* name, cudaStream_t s);
+    ~TraceScope();
+    TraceScope(const TraceScope&) = delete;
+    TraceScope& operator=(const TraceScope&) = delete;
+
+private:
+    const char* name_;
+    cudaStream_t s_;
+    cudaEvent_t a_ = nullptr;
+};
+
+}  // namespace pcms
+
+#define PCMS_TRACE_CAT2(a, b) a##b
+#define PCMS_TRACE_CAT(a, b) PCMS_TRACE_CAT2(a, b)
+#define PCMS_TRACE(name, stream) ::pcms::TraceScope PCMS_TRACE_CAT(pcms_trace_, __LINE__)(name, stream)

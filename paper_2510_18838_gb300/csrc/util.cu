@@ -1,0 +1,409 @@
+// util.cu -- errors, device memory, bounding box, prefix scan and the counting sort of
+// points into uniform-grid cells (the search structure of Sec. 3.3).
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+
+#include "pcms_internal.cuh"
+#include "trace.cuh"
+
+namespace pcms {
+
+void fail(pcms_status st, const std::string& msg) { throw PcmsError{st, msg}; }
+
+void check_cuda(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return;
+    (void)cudaGetLastError();
+    fail(e == cudaErrorMemoryAllocation ? PCMS_ERR_OUT_OF_MEMORY : PCMS_ERR_CUDA,
+         std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void ensure_mempool(int device) {
+    // Keep freed stream-ordered memory cached in this process's default pool, so that
+    // repeated calls do not return memory to the driver at every synchronisation.
+    static std::mutex mu;
+    static bool done[64] = {};
+    std::lock_guard<std::mutex> lk(mu);
+    if (device < 0 || device >= 64 || done[device]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    (void)cudaGetLastError();
+    done[device] = true;
+}
+
+void DBuf::alloc(size_t b, cudaStream_t st) {
+    release();
+    s = st;
+    bytes = b;
+    if (b == 0) return;
+    cudaError_t e = cudaMallocAsync(&p, b, st);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        bytes = 0;
+        (void)cudaGetLastError();
+        fail(e == cudaErrorMemoryAllocation ? PCMS_ERR_OUT_OF_MEMORY : PCMS_ERR_CUDA,
+             std::string("cudaMallocAsync(") + std::to_string(b) + " bytes): " +
+                 cudaGetErrorString(e));
+    }
+}
+
+void DBuf::release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    bytes = 0;
+}
+
+int num_sms() {
+    static int cached[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && cached[dev]) return cached[dev];
+    int n = 0;
+    PCMS_CU(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+    if (dev >= 0 && dev < 64) cached[dev] = n;
+    return n;
+}
+
+Grid make_grid(int dim, const double* lo, const double* hi, double radius, int64_t max_cells) {
+    Grid g;
+    g.dim = dim;
+    double h = radius * (1.0 + std::ldexp(1.0, -20));
+    for (int d = 0; d < 3; d++) {
+        g.lo[d] = d < dim ? lo[d] : 0.0;
+        g.n[d] = 1;
+    }
+    for (;;) {
+        double tot = 1.0;
+        for (int d = 0; d < dim; d++) {
+            double ext = hi[d] - lo[d];
+            double nd = std::floor(ext / h) + 1.0;
+            tot *= nd;
+        }
+        if (tot <= (double)max_cells) break;
+        h *= 2.0;
+    }
+    int64_t ncell = 1;
+    for (int d = 0; d < dim; d++) {
+        g.n[d] = (int)(std::floor((hi[d] - lo[d]) / h) + 1.0);
+        ncell *= g.n[d];
+    }
+    g.ncell = ncell;
+    g.h = h;
+    g.inv_h = 1.0 / h;
+    return g;
+}
+
+// ------------------------------------------------------------------------------------
+// bounding box: order-preserving int64 encoding of doubles + atomicMin/Max
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ long long enc_double(double x) {
+    long long b = __double_as_longlong(x);
+    return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFLL);
+}
+__device__ __forceinline__ double dec_double(long long k) {
+    return __longlong_as_double(k >= 0 ? k : (k ^ 0x7FFFFFFFFFFFFFFFLL));
+}
+
+__global__ void k_bbox_init(long long* enc, unsigned long long* bad) {
+    int i = threadIdx.x;
+    if (i < 3) enc[i] = 0x7FFFFFFFFFFFFFFFLL;          // min slots
+    else if (i < 6) enc[i] = (long long)0x8000000000000000ULL;  // max slots
+    if (i == 0) *bad = 0;
+}
+
+__global__ void k_bbox(int dim, const double* __restrict__ pts, int64_t n, long long* enc,
+                       unsigned long long* bad) {
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    unsigned long long nb = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        for (int d = 0; d < dim; d++) {
+            double x = pts[d * n + i];
+            if (!isfinite(x)) { nb++; continue; }
+            lo[d] = fmin(lo[d], x);
+            hi[d] = fmax(hi[d], x);
+        }
+    }
+    for (int d = 0; d < dim; d++) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+            hi[d] = fmax(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) nb += __shfl_xor_sync(0xffffffffu, nb, o);
+    if ((threadIdx.x & 31) == 0) {
+        for (int d = 0; d < dim; d++) {
+            if (lo[d] <= hi[d]) {
+                atomicMin(&enc[d], enc_double(lo[d]));
+                atomicMax(&enc[3 + d], enc_double(hi[d]));
+            }
+        }
+        if (nb) atomicAdd(bad, nb);
+    }
+}
+
+__global__ void k_bbox_decode(const long long* enc, double* box) {
+    int i = threadIdx.x;
+    if (i < 6) box[i] = dec_double(enc[i]);
+}
+
+void launch_bbox(int dim, const double* pts, int64_t n, double* dev_box, long long* dev_enc,
+                 unsigned long long* dev_bad, cudaStream_t s) {
+    {
+        PCMS_TRACE("bbox_init", s);
+        k_bbox_init<<<1, 32, 0, s>>>(dev_enc, dev_bad);
+    }
+    if (n > 0) {
+        PCMS_TRACE("bbox_reduce", s);
+        int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 4);
+        k_bbox<<<blocks, 256, 0, s>>>(dim, pts, n, dev_enc, dev_bad);
+    }
+    {
+        PCMS_TRACE("bbox_decode", s);
+        k_bbox_decode<<<1, 32, 0, s>>>(dev_enc, dev_box);
+    }
+    PCMS_LAUNCH_CHECK("bbox");
+}
+
+// ------------------------------------------------------------------------------------
+// exclusive scan: per-tile reduce -> scan of tile sums -> per-tile scan with offset
+// (no inter-block waiting)
+// ------------------------------------------------------------------------------------
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* warp_tot, T* total) {
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        T t = lane < (SCAN_THREADS / 32) ? warp_tot[lane] : T(0);
+        T u = t;
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, u, o);
+            if (lane >= o) u += y;
+        }
+        if (lane < (SCAN_THREADS / 32)) warp_tot[lane] = u - t;
+        if (lane == 31) *total = u;
+    }
+    __syncthreads();
+    return x - v + warp_tot[wid];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const int32_t* __restrict__ in,
+                                                              int64_t n, T* bsum) {
+    __shared__ T wt[SCAN_THREADS / 32];
+    __shared__ T tot;
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++)
+        if (base + k < n) s += (T)in[base + k];
+    block_exclusive_scan<T>(s, wt, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_scan_bsum(T* bsum, int64_t nb, T* total_out) {
+    __shared__ T wt[32];
+    __shared__ T carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t base = 0; base < nb; base += 1024) {
+        int64_t i = base + threadIdx.x;
+        T v = i < nb ? bsum[i] : T(0);
+        T x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wt[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            T t = wt[lane];
+            T u = t;
+            for (int o = 1; o < 32; o <<= 1) {
+                T y = __shfl_up_sync(0xffffffffu, u, o);
+                if (lane >= o) u += y;
+            }
+            wt[lane] = u - t;
+        }
+        __syncthreads();
+        T excl = x - v + wt[wid] + carry;
+        if (i < nb) bsum[i] = excl;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total_out = carry;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const int32_t* __restrict__ in,
+                                                            int64_t n, const T* bsum, T* out) {
+    __shared__ T wt[SCAN_THREADS / 32];
+    __shared__ T tot;
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    T v[SCAN_ITEMS];
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        v[k] = base + k < n ? (T)in[base + k] : T(0);
+        s += v[k];
+    }
+    T run = block_exclusive_scan<T>(s, wt, &tot) + bsum[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+}
+
+template <typename T>
+void exclusive_scan(const int32_t* in, T* out, int64_t n, cudaStream_t s) {
+    int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb == 0) {
+        PCMS_CU(cudaMemsetAsync(out, 0, sizeof(T), s));
+        return;
+    }
+    DBuf bs(sizeof(T) * nb, s);
+    {
+        PCMS_TRACE("scan_reduce", s);
+        k_scan_reduce<T><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, bs.as<T>());
+    }
+    {
+        PCMS_TRACE("scan_tile_sums", s);
+        k_scan_bsum<T><<<1, 1024, 0, s>>>(bs.as<T>(), nb, out + n);
+    }
+    {
+        PCMS_TRACE("scan_down", s);
+        k_scan_down<T><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, bs.as<T>(), out);
+    }
+    PCMS_LAUNCH_CHECK("exclusive_scan");
+}
+
+template void exclusive_scan<int32_t>(const int32_t*, int32_t*, int64_t, cudaStream_t);
+template void exclusive_scan<int64_t>(const int32_t*, int64_t*, int64_t, cudaStream_t);
+
+// ------------------------------------------------------------------------------------
+// counting sort by cell: key + rank (warp-aggregated atomics), scan, scatter
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ int cell_of(double x, double lo, double inv_h, int n) {
+    double f = floor((x - lo) * inv_h);
+    f = fmin(fmax(f, 0.0), (double)(n - 1));   // NaN -> 0 (fmax/fmin drop NaN)
+    return (int)f;
+}
+
+__global__ void k_cell_keys(Grid g, const double* __restrict__ pts, int64_t n,
+                            int32_t* __restrict__ key, int32_t* __restrict__ rank,
+                            int32_t* __restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = base + threadIdx.x;
+        bool valid = i < n;
+        unsigned active = __ballot_sync(0xffffffffu, valid);
+        if (!valid) continue;
+        int c = cell_of(pts[i], g.lo[0], g.inv_h, g.n[0]);
+        if (g.dim >= 2) c += g.n[0] * cell_of(pts[n + i], g.lo[1], g.inv_h, g.n[1]);
+        if (g.dim == 3)
+            c += g.n[0] * g.n[1] * cell_of(pts[2 * n + i], g.lo[2], g.inv_h, g.n[2]);
+        unsigned peers = __match_any_sync(active, c);
+        int leader = __ffs(peers) - 1;
+        int b = 0;
+        if (lane == leader) b = atomicAdd(&count[c], __popc(peers));
+        b = __shfl_sync(peers, b, leader);
+        key[i] = c;
+        rank[i] = b + __popc(peers & lt);
+    }
+}
+
+__global__ void k_scatter(int dim, Grid g, const double* __restrict__ pts, int64_t n,
+                          const int32_t* __restrict__ key, const int32_t* __restrict__ rank,
+                          const int32_t* __restrict__ start, int32_t* __restrict__ perm,
+                          int32_t* __restrict__ inv, double* __restrict__ x64,
+                          float4* __restrict__ hl0, float2* __restrict__ hl1) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int pos = start[key[i]] + rank[i];
+        perm[pos] = (int32_t)i;
+        inv[i] = pos;
+        double x[3] = {0, 0, 0};
+        for (int d = 0; d < dim; d++) {
+            x[d] = pts[d * n + i];
+            x64[d * n + pos] = x[d];
+        }
+        if (hl0) {
+            float h[3], l[3];
+            for (int d = 0; d < 3; d++) {
+                double rel = x[d] - g.lo[d];
+                h[d] = (float)rel;
+                l[d] = (float)(rel - (double)h[d]);
+            }
+            if (dim == 2) {
+                hl0[pos] = make_float4(h[0], h[1], l[0], l[1]);
+            } else {
+                hl0[pos] = make_float4(h[0], h[1], h[2], l[0]);
+                hl1[pos] = make_float2(l[1], l[2]);
+            }
+        }
+    }
+}
+
+void sort_points(const Grid& g, const double* pts, int64_t n, bool with_start, bool with_hl,
+                 SortedPoints& out, cudaStream_t s) {
+    out.dim = g.dim;
+    out.n = n;
+    int dim = g.dim;
+    DBuf count(sizeof(int32_t) * (g.ncell + 1), s);
+    DBuf key(sizeof(int32_t) * std::max<int64_t>(n, 1), s);
+    DBuf rank(sizeof(int32_t) * std::max<int64_t>(n, 1), s);
+    PCMS_CU(cudaMemsetAsync(count.p, 0, sizeof(int32_t) * (g.ncell + 1), s));
+    out.perm.alloc(sizeof(int32_t) * std::max<int64_t>(n, 1), s);
+    out.inv.alloc(sizeof(int32_t) * std::max<int64_t>(n, 1), s);
+    out.x64.alloc(sizeof(double) * dim * std::max<int64_t>(n, 1), s);
+    if (with_hl) {
+        out.hl0.alloc(sizeof(float4) * std::max<int64_t>(n, 1), s);
+        if (dim == 3) out.hl1.alloc(sizeof(float2) * std::max<int64_t>(n, 1), s);
+    }
+    DBuf start_tmp;
+    int32_t* start;
+    if (with_start) {
+        out.cell_start.alloc(sizeof(int32_t) * (g.ncell + 1), s);
+        start = out.cell_start.as<int32_t>();
+    } else {
+        start_tmp.alloc(sizeof(int32_t) * (g.ncell + 1), s);
+        start = start_tmp.as<int32_t>();
+    }
+    int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8));
+    if (n > 0) {
+        PCMS_TRACE("grid_cell_keys", s);
+        k_cell_keys<<<blocks, 256, 0, s>>>(g, pts, n, key.as<int32_t>(), rank.as<int32_t>(),
+                                           count.as<int32_t>());
+    }
+    PCMS_LAUNCH_CHECK("cell_keys");
+    exclusive_scan<int32_t>(count.as<int32_t>(), start, g.ncell, s);
+    if (n > 0) {
+        PCMS_TRACE("grid_scatter", s);
+        k_scatter<<<blocks, 256, 0, s>>>(dim, g, pts, n, key.as<int32_t>(), rank.as<int32_t>(),
+                                         start, out.perm.as<int32_t>(), out.inv.as<int32_t>(),
+                                         out.x64.as<double>(), with_hl ? out.hl0.as<float4>() : nullptr,
+                                         (with_hl && dim == 3) ? out.hl1.as<float2>() : nullptr);
+    }
+    PCMS_LAUNCH_CHECK("scatter");
+}
+
+}  // namespace pcms

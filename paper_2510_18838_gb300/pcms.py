@@ -1,0 +1,299 @@
+"""Thin Python binding of libpcms.so (include/pcms.h): argument marshalling only.
+
+Every call takes CUDA torch tensors, passes their device pointers and the current torch
+stream to the C ABI, and raises ``PcmsError`` on a non-OK status. There is no CPU
+fallback: if the library has not been built, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libpcms.so")
+
+OK, INVALID_ARG, UNDERDETERMINED, ILL_CONDITIONED, OUT_OF_MEMORY, TIMEOUT, CUDA_ERR, CAPACITY = range(8)
+STATUS_NAMES = ["OK", "INVALID_ARG", "UNDERDETERMINED", "ILL_CONDITIONED", "OUT_OF_MEMORY",
+                "TIMEOUT", "CUDA", "CAPACITY"]
+FP64, MIXED = 0, 1
+WEIGHTS = {"wendland_c2": 0, "gaussian": 1, "c4": 2, "const": 3, "noop": 4, "mq": 5,
+           "imq": 6, "tps": 7, "cubic": 8}
+
+
+class PcmsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"[{STATUS_NAMES[status] if 0 <= status < 8 else status}] {msg}")
+        self.status = status
+
+
+class MapOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("weight", ctypes.c_int),
+                ("lambda_", ctypes.c_double), ("min_neighbors", ctypes.c_int),
+                ("domain_known", ctypes.c_int), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3)]
+
+
+class MapInfo(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("basis_degree", ctypes.c_int), ("n_terms", ctypes.c_int),
+                ("precision", ctypes.c_int), ("n_src", ctypes.c_int64), ("n_tgt", ctypes.c_int64),
+                ("nnz", ctypes.c_int64), ("n_underdetermined", ctypes.c_int64),
+                ("n_ill_conditioned", ctypes.c_int64), ("max_neighbors", ctypes.c_int64),
+                ("max_radius_doublings", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+
+_lib = None
+
+# exported symbol -> (restype, argtypes)
+_P, _I, _I64, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+SIGNATURES = {
+    "pcms_version": (_I, []),
+    "pcms_last_error": (ctypes.c_char_p, []),
+    "pcms_map_opts_default": (None, [_P]),
+    "pcms_create_map": (_I, [_I, _P, _I64, _P, _I64, _I, _D, _P, _P, _P]),
+    "pcms_apply_map": (_I, [_P, _P, _I, _P, _P]),
+    "pcms_mls_transfer": (_I, [_I, _P, _I64, _P, _I64, _I, _D, _P, _P, _I, _P, _P, _P]),
+    "pcms_count_neighbors": (_I, [_I, _P, _I64, _P, _I64, _I, _D, _P, _P, _P, _P, _P]),
+    "pcms_map_info": (_I, [_P, _P]),
+    "pcms_map_export": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "pcms_map_destroy": (None, [_P, _P]),
+    "pcms_mesh_create": (_I, [_P, _I64, _P, _I64, _P, _P]),
+    "pcms_locate_interp": (_I, [_P, _P, _I64, _P, _P, _P, _P, _P]),
+    "pcms_mesh_destroy": (None, [_P, _P]),
+    "pcms_trace_enable": (_I, [_I]),
+    "pcms_trace_count": (_I, []),
+    "pcms_trace_get": (_I, [_I, ctypes.c_char_p, _I, _P, _P]),
+}
+
+
+def trace_enable(on: bool = True) -> None:
+    """Start (clearing the table) or stop per-kernel CUDA-event timing in the library."""
+    _check(lib().pcms_trace_enable(1 if on else 0))
+
+
+def trace_read() -> dict:
+    """{kernel name: (launches, total_ms)} accumulated since the last trace_enable(True)."""
+    L = lib()
+    out = {}
+    for i in range(L.pcms_trace_count()):
+        buf = ctypes.create_string_buffer(128)
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        _check(L.pcms_trace_get(i, buf, 128, ctypes.byref(n), ctypes.byref(ms)))
+        out[buf.value.decode()] = (int(n.value), float(ms.value))
+    return out
+
+
+def lib():
+    """Load libpcms.so (built by ``paper_2510_18838_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libpcms.so not built ({LIB_PATH}); run "
+                          "`python -m paper_2510_18838_gb300.build` or __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(st: int):
+    if st != OK:
+        msg = lib().pcms_last_error()
+        raise PcmsError(st, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.contiguous()
+
+
+def make_opts(precision="fp64", weight="wendland_c2", lam=0.0, min_neighbors=0, domain=None):
+    o = MapOpts()
+    lib().pcms_map_opts_default(ctypes.byref(o))
+    o.precision = FP64 if precision == "fp64" else MIXED
+    o.weight = WEIGHTS[weight]
+    o.lambda_ = float(lam)
+    o.min_neighbors = int(min_neighbors)
+    if domain is not None:
+        lo, hi = domain
+        o.domain_known = 1
+        for d in range(len(lo)):
+            o.lo[d], o.hi[d] = float(lo[d]), float(hi[d])
+    return o
+
+
+@dataclass
+class Map:
+    """Cached MLS operator (pcms_create_map). ``apply`` evaluates it on fields."""
+    handle: ctypes.c_void_p
+    dim: int
+    n_src: int
+    n_tgt: int
+    precision: str
+    status_code: int = OK
+
+    @property
+    def dtype(self):
+        return torch.float64 if self.precision == "fp64" else torch.float32
+
+    def apply(self, fields, out=None, stream=None):
+        f = _dev(fields, self.dtype, "fields")
+        squeeze = f.dim() == 1
+        if squeeze:
+            f = f[None]
+        nf = f.shape[0]
+        if out is None:
+            out = torch.empty((nf, self.n_tgt), dtype=self.dtype, device=f.device)
+        _check(lib().pcms_apply_map(self.handle, _ptr(f), nf, _ptr(out), _stream(stream)))
+        return out[0] if squeeze else out
+
+    def info(self) -> dict:
+        i = MapInfo()
+        _check(lib().pcms_map_info(self.handle, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in MapInfo._fields_}
+
+    def export(self, stream=None):
+        """(offsets int64[nt+1], cols int32[nnz] caller source ids, vals float64[nnz],
+        status int8[nt], radius_doublings int32[nt]), rows in caller target order."""
+        nnz = self.info()["nnz"]
+        dev = torch.device("cuda", torch.cuda.current_device())
+        off = torch.empty(self.n_tgt + 1, dtype=torch.int64, device=dev)
+        cols = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+        vals = torch.empty(max(nnz, 1), dtype=torch.float64, device=dev)
+        st = torch.empty(max(self.n_tgt, 1), dtype=torch.int8, device=dev)
+        kx = torch.empty(max(self.n_tgt, 1), dtype=torch.int32, device=dev)
+        _check(lib().pcms_map_export(self.handle, _ptr(off), _ptr(cols), _ptr(vals), _ptr(st),
+                                     _ptr(kx), _stream(stream)))
+        return off, cols[:nnz], vals[:nnz], st[:self.n_tgt], kx[:self.n_tgt]
+
+    def destroy(self, stream=None):
+        if self.handle:
+            lib().pcms_map_destroy(self.handle, _stream(stream))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            if self.handle and torch.cuda.is_available():
+                self.destroy()
+        except Exception:
+            pass
+
+
+def create_map(src, tgt, degree, radius, precision="fp64", weight="wendland_c2", lam=0.0,
+               min_neighbors=0, domain=None, stream=None, allow_underdetermined=True) -> Map:
+    """pcms_create_map. src/tgt: float64 CUDA tensors [dim, n]."""
+    src = _dev(src, torch.float64, "src")
+    tgt = _dev(tgt, torch.float64, "tgt")
+    dim = src.shape[0]
+    o = make_opts(precision, weight, lam, min_neighbors, domain)
+    h = ctypes.c_void_p()
+    st = lib().pcms_create_map(dim, _ptr(src), src.shape[1], _ptr(tgt), tgt.shape[1], int(degree),
+                               float(radius), ctypes.byref(o), _stream(stream), ctypes.byref(h))
+    if st != OK and not (st == UNDERDETERMINED and allow_underdetermined and h.value):
+        _check(st)
+    return Map(h, dim, src.shape[1], tgt.shape[1], precision, st)
+
+
+def mls_transfer(src, tgt, fields, degree, radius, precision="fp64", weight="wendland_c2",
+                 lam=0.0, min_neighbors=0, domain=None, with_status=True, out=None, stream=None):
+    """pcms_mls_transfer (one shot, no operator kept). Returns (values [F, nt], status)."""
+    src = _dev(src, torch.float64, "src")
+    tgt = _dev(tgt, torch.float64, "tgt")
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    f = _dev(fields, dt, "fields")
+    if f.dim() == 1:
+        f = f[None]
+    nf = f.shape[0]
+    nt = tgt.shape[1]
+    if out is None:
+        out = torch.empty((nf, nt), dtype=dt, device=src.device)
+    status = torch.empty(max(nt, 1), dtype=torch.int8, device=src.device) if with_status else None
+    o = make_opts(precision, weight, lam, min_neighbors, domain)
+    st = lib().pcms_mls_transfer(src.shape[0], _ptr(src), src.shape[1], _ptr(tgt), nt, int(degree),
+                                 float(radius), ctypes.byref(o), _ptr(f), nf, _ptr(out),
+                                 _ptr(status), _stream(stream))
+    if st not in (OK, UNDERDETERMINED):
+        _check(st)
+    return out, (status[:nt] if status is not None else None)
+
+
+def count_neighbors(src, tgt, radius, degree=1, precision="fp64", weight="wendland_c2",
+                    min_neighbors=0, domain=None, with_doublings=False, stream=None):
+    """pcms_count_neighbors: per-target neighbour counts (caller order), optionally with the
+    radius doublings."""
+    src = _dev(src, torch.float64, "src")
+    tgt = _dev(tgt, torch.float64, "tgt")
+    nt = tgt.shape[1]
+    counts = torch.empty(max(nt, 1), dtype=torch.int32, device=src.device)
+    kx = torch.empty(max(nt, 1), dtype=torch.int32, device=src.device) if with_doublings else None
+    o = make_opts(precision, weight, 0.0, min_neighbors, domain)
+    _check(lib().pcms_count_neighbors(src.shape[0], _ptr(src), src.shape[1], _ptr(tgt), nt,
+                                      int(degree), float(radius), ctypes.byref(o), _ptr(counts),
+                                      _ptr(kx), None, _stream(stream)))
+    return (counts[:nt], kx[:nt]) if with_doublings else counts[:nt]
+
+
+class Mesh:
+    """Cached triangle mesh + search grid (pcms_mesh_create)."""
+
+    def __init__(self, xy, tri, stream=None):
+        xy = _dev(xy, torch.float64, "xy")
+        tri = _dev(tri, torch.int32, "tri")
+        self.n_vertices = xy.shape[1]
+        self.n_tri = tri.shape[1]
+        h = ctypes.c_void_p()
+        _check(lib().pcms_mesh_create(_ptr(xy), self.n_vertices, _ptr(tri), self.n_tri,
+                                      _stream(stream), ctypes.byref(h)))
+        self.handle = h
+
+    def locate_interp(self, pts, field=None, with_dim=True, stream=None, elem=None, edim=None,
+                      values=None):
+        """Returns (elem int32[n], entity_dim int8[n] or None, values float64[n] or None)."""
+        pts = _dev(pts, torch.float64, "pts")
+        n = pts.shape[1]
+        dev = pts.device
+        if elem is None:
+            elem = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        if with_dim and edim is None:
+            edim = torch.empty(max(n, 1), dtype=torch.int8, device=dev)
+        if field is not None:
+            field = _dev(field, torch.float64, "field")
+            if values is None:
+                values = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
+        _check(lib().pcms_locate_interp(self.handle, _ptr(pts), n, _ptr(field), _ptr(elem),
+                                        _ptr(edim) if with_dim else None,
+                                        _ptr(values) if field is not None else None,
+                                        _stream(stream)))
+        return (elem[:n], edim[:n] if with_dim else None,
+                values[:n] if field is not None else None)
+
+    def destroy(self, stream=None):
+        if self.handle:
+            lib().pcms_mesh_destroy(self.handle, _stream(stream))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            if self.handle and torch.cuda.is_available():
+                self.destroy()
+        except Exception:
+            pass

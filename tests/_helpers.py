@@ -1,0 +1,47 @@
+"""Shared helpers for the parity tests (no method arithmetic here)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pcms.h")
+
+# tolerances from the stated accuracy targets: FP64 path 1e-12, mixed path 2e-5,
+# measured norm-wise per field (max |gpu - oracle| / max |oracle| over OK targets)
+TOL_FP64 = 1e-12
+TOL_MIXED = 2e-5
+
+
+def normwise_err(got, ref, mask=None):
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    if got.ndim == 1:
+        got, ref = got[None], ref[None]
+    if mask is not None:
+        got, ref = got[:, mask], ref[:, mask]
+    if ref.size == 0:
+        return 0.0
+    den = np.max(np.abs(ref), axis=1)
+    den[den == 0] = 1.0
+    return float(np.max(np.max(np.abs(got - ref), axis=1) / den))
+
+
+def header_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(pcms_[a-z0-9_]+)\s*\(", txt)))
+
+
+def need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def rows_as_sets(off, cols):
+    off = np.asarray(off)
+    cols = np.asarray(cols)
+    return [np.sort(cols[off[i]:off[i + 1]]) for i in range(len(off) - 1)]

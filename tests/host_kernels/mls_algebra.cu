@@ -1,0 +1,52 @@
+// Host-compiled harness for the CPU tests: exposes the library's per-target MLS algebra
+// (the moment accumulation and the guarded LDL^T solve from mls_kernels.cuh, compiled for
+// the host with T = double) so its arithmetic can be checked against numpy without a GPU.
+#include "mls_kernels.cuh"
+
+using namespace pcms;
+
+template <int DIM, int DEG, int MODE>
+static int run(int kind, int n, const double* dx, const double* b, double inv_r, double lambda,
+               double tau, double* mom_out, double* out) {
+    constexpr int NM = mono_count(DIM, 2 * DEG);
+    constexpr int M = mono_count(DIM, DEG);
+    constexpr int NACC = MODE == MODE_FUSED ? NM + M : NM;
+    double acc[NACC];
+    for (int i = 0; i < NACC; i++) acc[i] = 0.0;
+    for (int i = 0; i < n; i++)
+        accumulate<DIM, DEG, MODE, double, NACC>(acc, dx + 3 * i, b ? b[i] : 0.0, kind, inv_r);
+    for (int i = 0; i < NACC; i++) mom_out[i] = acc[i];
+    return solve_moments<DIM, DEG, MODE>(acc, lambda, tau, out) ? 1 : 0;
+}
+
+template <int DIM, int DEG>
+static int run_mode(int fused, int kind, int n, const double* dx, const double* b, double inv_r,
+                    double lambda, double tau, double* mom_out, double* out) {
+    if (fused) return run<DIM, DEG, MODE_FUSED>(kind, n, dx, b, inv_r, lambda, tau, mom_out, out);
+    return run<DIM, DEG, MODE_MAP>(kind, n, dx, b, inv_r, lambda, tau, mom_out, out);
+}
+
+extern "C" int hk_mls(int dim, int deg, int fused, int kind, int n, const double* dx,
+                      const double* b, double inv_r, double lambda, double tau, double* mom_out,
+                      double* out) {
+    if (dim == 2) {
+        if (deg == 0) return run_mode<2, 0>(fused, kind, n, dx, b, inv_r, lambda, tau, mom_out, out);
+        if (deg == 1) return run_mode<2, 1>(fused, kind, n, dx, b, inv_r, lambda, tau, mom_out, out);
+        return run_mode<2, 2>(fused, kind, n, dx, b, inv_r, lambda, tau, mom_out, out);
+    }
+    if (deg == 0) return run_mode<3, 0>(fused, kind, n, dx, b, inv_r, lambda, tau, mom_out, out);
+    if (deg == 1) return run_mode<3, 1>(fused, kind, n, dx, b, inv_r, lambda, tau, mom_out, out);
+    return run_mode<3, 2>(fused, kind, n, dx, b, inv_r, lambda, tau, mom_out, out);
+}
+
+extern "C" int hk_mono(int dim, int p, int* e) {
+    Exp3 x = mono_exp(dim, p);
+    e[0] = x.e[0];
+    e[1] = x.e[1];
+    e[2] = x.e[2];
+    return mono_count(dim, 8);
+}
+
+extern "C" int hk_mono_prod(int dim, int k, int l) { return mono_prod(dim, k, l); }
+
+extern "C" double hk_weight(int kind, double q) { return weight_value<double>(kind, q); }

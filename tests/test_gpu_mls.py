@@ -1,0 +1,257 @@
+"""GPU parity of the MLS transfer (Sec. 3.2.1) against the FP64 CPU oracle.
+
+Neighbour lists and radius doublings are compared bit-exactly; values norm-wise per
+field: <= 1e-12 for the FP64 path and <= 2e-5 for the mixed path; per-target statuses
+must be identical. Every call goes through the C ABI (paper_2510_18838_gb300.pcms).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_18838_gb300 import workloads as W
+from tests._helpers import TOL_FP64, TOL_MIXED, need_gpu, normwise_err, rows_as_sets
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    need_gpu()
+    from paper_2510_18838_gb300 import build, pcms
+    build.build()
+    return pcms
+
+
+def cu(a, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def _case(dim, ns, nt, seed, outside=0.0):
+    src = W.uniform_points(ns, dim, seed)
+    tgt = W.uniform_points(nt, dim, seed + 1, lo=-outside, hi=1.0 + outside)
+    return src, tgt
+
+
+# ------------------------------------------------------------------ neighbour lists
+@pytest.mark.parametrize("dim,prec,min_nb", [(2, "fp64", 0), (2, "mixed", 0), (3, "fp64", 0),
+                                              (3, "mixed", 0), (2, "mixed", 12), (3, "fp64", 15)])
+def test_neighbor_lists_bit_exact(P, dim, prec, min_nb):
+    ns, nt, r = (6000, 1700, 0.03) if dim == 2 else (20000, 1300, 0.06)
+    src, tgt = _case(dim, ns, nt, 100 + dim, outside=0.05)
+    m = P.create_map(cu(src), cu(tgt), 1, r, precision=prec, min_neighbors=min_nb)
+    off, cols, vals, st, kx = (host(x) for x in m.export())
+    o_off, o_cols, o_kx = oracle.neighbors(src, tgt, r, min_neighbors=min_nb, degree=1)
+    assert np.array_equal(kx, o_kx)
+    assert np.array_equal(np.diff(off), np.diff(o_off))
+    for a, b in zip(rows_as_sets(off, cols), rows_as_sets(o_off, o_cols)):
+        assert np.array_equal(a, b)
+    m.destroy()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_neighbor_selection_exact_at_the_radius(P, prec):
+    """Sources exactly at distance r (dyadic) are excluded; one ulp inside is included."""
+    r = 0.0625
+    g = (np.arange(8) + 0.5) / 8.0
+    tx, ty = np.meshgrid(g, g)
+    tgt = np.stack([tx.ravel(), ty.ravel()])
+    offs = [(r, 0.0), (-r, 0.0), (0.0, r), (0.0, -r), (0.0375, 0.05),
+            (np.nextafter(r, 0), 0.0), (0.0, -np.nextafter(r, 0)), (0.0375, np.nextafter(0.05, 0))]
+    src = np.concatenate([tgt + np.array(o)[:, None] for o in offs], axis=1)
+    m = P.create_map(cu(src), cu(tgt), 0, r, precision=prec)
+    off, cols, *_ = (host(x) for x in m.export())
+    o_off, o_cols, _ = oracle.neighbors(src, tgt, r, degree=0)
+    for a, b in zip(rows_as_sets(off, cols), rows_as_sets(o_off, o_cols)):
+        assert np.array_equal(a, b)
+    assert all(len(x) == 3 for x in rows_as_sets(off, cols))
+
+
+# ------------------------------------------------------------------ FP64 operator + values
+@pytest.mark.parametrize("dim,deg", [(2, 0), (2, 1), (2, 2), (3, 1), (3, 2)])
+def test_fp64_map_values_and_shape(P, dim, deg):
+    ns, nt, r = (5000, 1500, 0.05) if dim == 2 else (12000, 900, 0.12)
+    src, tgt = _case(dim, ns, nt, 200 + 10 * dim + deg)
+    f = np.stack([np.sin(3 * src[0]) * np.cos(2 * src[1]), src[0] ** 2 - src[1]])
+    m = P.create_map(cu(src), cu(tgt), deg, r)
+    out = host(m.apply(cu(f)))
+    o = oracle.mls(src, tgt, f, deg, r, shape=True)
+    off, cols, vals, st, kx = (host(x) for x in m.export())
+    assert np.array_equal(st, o["status"])
+    ok = o["status"] == 0
+    assert ok.mean() > 0.9
+    assert normwise_err(out, o["values"], ok) <= TOL_FP64
+    assert np.isnan(out[:, ~ok]).all()
+    # shape functions, row by row (compare sorted by column)
+    err = 0.0
+    scale = np.abs(o["shape"]).max()
+    for i in np.nonzero(ok)[0]:
+        a = slice(off[i], off[i + 1])
+        b = slice(o["offsets"][i], o["offsets"][i + 1])
+        ia, ib = np.argsort(cols[a]), np.argsort(o["cols"][b])
+        assert np.array_equal(cols[a][ia], o["cols"][b][ib])
+        err = max(err, np.abs(vals[a][ia] - o["shape"][b][ib]).max())
+    assert err / scale <= TOL_FP64
+
+
+@pytest.mark.parametrize("dim,deg", [(2, 1), (2, 2), (3, 2)])
+def test_fp64_one_shot_transfer(P, dim, deg):
+    ns, nt, r = (5000, 1500, 0.05) if dim == 2 else (12000, 900, 0.12)
+    src, tgt = _case(dim, ns, nt, 300 + 10 * dim + deg)
+    f = np.cos(4 * src[0]) + src[1] * src[dim - 1]
+    out, st = P.mls_transfer(cu(src), cu(tgt), cu(f), deg, r)
+    o = oracle.mls(src, tgt, f, deg, r)
+    assert np.array_equal(host(st), o["status"])
+    ok = o["status"] == 0
+    assert normwise_err(host(out), o["values"], ok) <= TOL_FP64
+
+
+def test_fp64_small_config_full(P):
+    """10,000 -> 10,000 uniform 2D, linear basis, Wendland C2, r = 0.03."""
+    c = W.mls_2d_small()
+    o = oracle.mls(c.src, c.tgt, c.fields, c.degree, c.radius)
+    out, st = P.mls_transfer(cu(c.src), cu(c.tgt), cu(c.fields), c.degree, c.radius)
+    assert np.array_equal(host(st), o["status"])
+    ok = o["status"] == 0
+    assert normwise_err(host(out), o["values"], ok) <= TOL_FP64
+    m = P.create_map(cu(c.src), cu(c.tgt), c.degree, c.radius)
+    out2 = host(m.apply(cu(c.fields)))
+    assert normwise_err(out2, o["values"], ok) <= TOL_FP64
+
+
+@pytest.mark.parametrize("weight", ["wendland_c2", "gaussian", "c4", "const", "noop", "mq", "imq",
+                                    "tps", "cubic"])
+def test_fp64_every_weight(P, weight):
+    src, tgt = _case(2, 4000, 700, 400)
+    f = np.sin(5 * src[0]) + src[1]
+    out, st = P.mls_transfer(cu(src), cu(tgt), cu(f), 1, 0.06, weight=weight)
+    o = oracle.mls(src, tgt, f, 1, 0.06, weight=weight)
+    assert np.array_equal(host(st), o["status"])
+    ok = o["status"] == 0
+    assert normwise_err(host(out), o["values"], ok) <= TOL_FP64
+
+
+def test_fp64_tikhonov(P):
+    src, tgt = _case(2, 4000, 700, 410)
+    f = np.cos(3 * src[0] + src[1])
+    for lam in (1e-3, 0.5):
+        out, st = P.mls_transfer(cu(src), cu(tgt), cu(f), 2, 0.06, lam=lam)
+        o = oracle.mls(src, tgt, f, 2, 0.06, lam=lam)
+        assert np.array_equal(host(st), o["status"])
+        assert normwise_err(host(out), o["values"], o["status"] == 0) <= TOL_FP64
+
+
+# ------------------------------------------------------------------ mixed precision
+@pytest.mark.parametrize("dim,deg", [(2, 1), (2, 2), (3, 1), (3, 2)])
+def test_mixed_values(P, dim, deg):
+    ns, nt, r = (20000, 3000, 0.03) if dim == 2 else (40000, 2000, 0.08)
+    src, tgt = _case(dim, ns, nt, 500 + 10 * dim + deg)
+    f32 = (np.sin(2 * np.pi * src[0]) * np.cos(2 * np.pi * src[1])).astype(np.float32)
+    out, st = P.mls_transfer(cu(src), cu(tgt), cu(f32), deg, r, precision="mixed")
+    o = oracle.mls(src, tgt, f32.astype(np.float64), deg, r)
+    assert np.array_equal(host(st), o["status"])
+    ok = o["status"] == 0
+    assert normwise_err(host(out), o["values"], ok) <= TOL_MIXED
+    m = P.create_map(cu(src), cu(tgt), deg, r, precision="mixed")
+    out2 = host(m.apply(cu(f32)))
+    assert normwise_err(out2, o["values"], ok) <= TOL_MIXED
+
+
+def test_mixed_multifield_apply_3d(P):
+    src = W.slab_points(60000, seed=401)
+    tgt = W.uniform_points(3000, 3, 402)
+    f = W.trig_fields(src, 16)
+    m = P.create_map(cu(src), cu(tgt), 2, 0.07, precision="mixed")
+    out = host(m.apply(cu(f)))
+    o = oracle.mls(src, tgt, f.astype(np.float64), 2, 0.07)
+    ok = o["status"] == 0
+    assert ok.mean() > 0.95
+    assert normwise_err(out, o["values"], ok) <= TOL_MIXED
+    # 1..16 fields give the same numbers as 16 at once
+    for nf in (1, 3, 5, 9):
+        part = host(m.apply(cu(np.ascontiguousarray(f[:nf]))))
+        np.testing.assert_allclose(part[:, ok], out[:nf, ok], rtol=1e-6, atol=1e-6)
+
+
+def test_mixed_growth_gaussian_mixture(P):
+    src = W.gaussian_mixture_points(60000, 301, 302)
+    tgt = W.uniform_points(3000, 2, 303)
+    f32 = W.sincos_field(src).astype(np.float32)
+    out, st = P.mls_transfer(cu(src), cu(tgt), cu(f32), 2, 0.01, precision="mixed",
+                             min_neighbors=10)
+    o = oracle.mls(src, tgt, f32.astype(np.float64), 2, 0.01, min_neighbors=10, mode="grid")
+    assert np.array_equal(host(st), o["status"])
+    assert normwise_err(host(out), o["values"], o["status"] == 0) <= TOL_MIXED
+    m = P.create_map(cu(src), cu(tgt), 2, 0.01, precision="mixed", min_neighbors=10)
+    *_, kx = (host(x) for x in m.export())
+    assert np.array_equal(kx, o["kexp"])
+    assert kx.max() >= 1
+
+
+# ------------------------------------------------------------------ statuses and edge cases
+def test_strict_mode_reports_underdetermined(P):
+    src, tgt = _case(2, 300, 200, 600, outside=0.5)
+    m = P.create_map(cu(src), cu(tgt), 2, 0.05)
+    assert m.status_code == P.UNDERDETERMINED
+    *_, st, _ = (host(x) for x in m.export())
+    o = oracle.mls(src, tgt, np.ones(300), 2, 0.05)
+    assert np.array_equal(st, o["status"])
+    assert m.info()["n_underdetermined"] == int((o["status"] == 1).sum()) > 0
+    out = host(m.apply(cu(np.ones(300))))
+    assert np.isnan(out[0, o["status"] != 0]).all()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_collinear_neighbours_are_ill_conditioned(P, prec):
+    x = np.linspace(0.45, 0.55, 201)
+    line = np.stack([x, 0.5 + 0.25 * (x - 0.5)])
+    cloud = W.uniform_points(2000, 2, 601)
+    cloud = cloud[:, np.hypot(cloud[0] - 0.5, cloud[1] - 0.5) > 0.02]
+    src = np.concatenate([line, cloud], axis=1)
+    tgt = np.array([[0.5, 0.3], [0.5, 0.3]])
+    f = np.ones(src.shape[1])
+    dt = np.float64 if prec == "fp64" else np.float32
+    out, st = P.mls_transfer(cu(src), cu(tgt), cu(f.astype(dt)), 1, 0.004, precision=prec)
+    o = oracle.mls(src, tgt, f, 1, 0.004)
+    assert o["status"][0] == 2
+    assert np.array_equal(host(st), o["status"])
+    assert np.isnan(host(out)[0, 0])
+
+
+def test_empty_and_tiny_inputs(P):
+    import torch
+    src, tgt = _case(2, 100, 10, 700)
+    out, st = P.mls_transfer(cu(src), cu(tgt[:, :0]), cu(np.ones(100)), 1, 0.1)
+    assert out.shape == (1, 0)
+    out, st = P.mls_transfer(cu(src[:, :0]), cu(tgt), cu(np.ones(0)), 1, 0.1)
+    assert (host(st) == 1).all() and np.isnan(host(out)).all()
+    m = P.create_map(cu(src), cu(tgt[:, :1]), 0, 0.3)
+    assert m.info()["n_tgt"] == 1
+    o = oracle.mls(src, tgt[:, :1], np.arange(100.0), 0, 0.3)
+    assert normwise_err(host(m.apply(cu(np.arange(100.0)))), o["values"]) <= TOL_FP64
+
+
+def test_nonfinite_coordinates_rejected(P):
+    src, tgt = _case(2, 100, 10, 710)
+    src[0, 5] = np.nan
+    with pytest.raises(P.PcmsError) as e:
+        P.create_map(cu(src), cu(tgt), 1, 0.1)
+    assert e.value.status == P.INVALID_ARG
+
+
+def test_ragged_tile_sizes(P):
+    """Target counts that are not multiples of any tile (1, 31, 33, 257, 1031)."""
+    src = W.uniform_points(3000, 2, 720)
+    for nt in (1, 31, 33, 257, 1031):
+        tgt = W.uniform_points(nt, 2, 721 + nt)
+        out, st = P.mls_transfer(cu(src), cu(tgt), cu(src[0].copy()), 1, 0.05)
+        o = oracle.mls(src, tgt, src[0], 1, 0.05)
+        assert np.array_equal(host(st), o["status"])
+        assert normwise_err(host(out), o["values"], o["status"] == 0) <= TOL_FP64
