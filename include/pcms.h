@@ -206,6 +206,80 @@ pcms_status pcms_locate_interp(pcms_mesh mesh, const double* tgt_pts, int64_t n_
 void pcms_mesh_destroy(pcms_mesh mesh, void* stream);
 
 /*
+ * Serving: a continuous-batching request loop (no counterpart in the paper, which couples
+ * applications through files/streams; this is the single-GPU runtime around the hot path).
+ *
+ * A server owns n_slots worker threads, each with its own non-blocking CUDA stream. Requests
+ * are queued in submission order; the head request is admitted as soon as a slot is idle
+ * and its device-memory estimate fits under mem_cap_bytes together with everything already
+ * admitted or cached (least recently used cached operators are evicted first). Admitted
+ * requests run concurrently on their slots' streams, so their kernels overlap on the GPU.
+ * A request whose estimate alone exceeds the cap fails with PCMS_ERR_CAPACITY.
+ * All pointers in a request are device pointers owned by the caller and must stay valid
+ * until the request has completed.
+ */
+typedef enum { PCMS_REQ_MLS = 0, PCMS_REQ_MESH = 1 } pcms_request_kind;
+
+typedef struct {
+    pcms_request_kind kind;
+    /* MLS: dim, basis_degree, radius, opts, src_pts [dim][n_src], tgt_pts [dim][n_tgt],
+     * fields [n_fields][n_src] (float32 for PCMS_MIXED, float64 for PCMS_FP64),
+     * out [n_fields][n_tgt] (same dtype).
+     * map_key >= 0: keep the operator cached under this key; a later request with the same
+     * key and reuse_map = 1 applies the cached operator to its own fields. A reuse request
+     * still passes the same geometry (src/tgt): it is used to rebuild the operator if it was
+     * evicted. map_key < 0: nothing is cached. */
+    int dim, basis_degree;
+    double radius;
+    pcms_map_opts opts;
+    const double* src_pts;
+    int64_t n_src;
+    const double* tgt_pts;
+    int64_t n_tgt;
+    const void* fields;
+    int n_fields;
+    void* out;
+    int64_t map_key;
+    int reuse_map;
+    /* MESH: xy [2][n_vertices] (src_pts), n_vertices (n_src), tri [3][n_tri], points
+     * (tgt_pts, n_tgt), nodal field (fields, float64 [n_vertices]), values out (out, float64
+     * [n_tgt]), elem_ids (int32 [n_tgt], required). */
+    const int32_t* tri;
+    int64_t n_tri;
+    int32_t* elem_ids;
+    /* device bytes to reserve; 0 = estimate from the sizes */
+    int64_t bytes_hint;
+} pcms_request;
+
+typedef struct {
+    int64_t ticket;
+    pcms_status status;
+    double t_submit, t_start, t_end; /* seconds on the server's monotonic clock */
+    int64_t bytes_reserved;
+    int used_cached_map;
+} pcms_request_result;
+
+typedef struct pcms_server_s* pcms_server;
+
+/* Start a server on the current device. n_slots in 1..64, mem_cap_bytes > 0. */
+pcms_status pcms_server_create(int n_slots, int64_t mem_cap_bytes, pcms_server* out);
+/* Queue a request (copied); *ticket receives its id (0, 1, 2, ...). Never blocks on the GPU. */
+pcms_status pcms_server_submit(pcms_server s, const pcms_request* req, int64_t* ticket);
+/* Up to max_results completed requests not yet returned, in completion order. Waits up to
+ * timeout_s for at least one (0 = do not wait). *n_results may be 0 (PCMS_OK). */
+pcms_status pcms_server_poll(pcms_server s, pcms_request_result* results, int max_results,
+                             double timeout_s, int* n_results);
+/* Wait until every submitted request has completed; PCMS_ERR_TIMEOUT after timeout_s. */
+pcms_status pcms_server_drain(pcms_server s, double timeout_s);
+/* Current time on the server's monotonic clock (seconds). */
+double pcms_server_now(pcms_server s);
+/* Bytes currently reserved by admitted requests plus cached operators, and the peak. */
+pcms_status pcms_server_memory(pcms_server s, int64_t* in_use, int64_t* peak,
+                               int64_t* cached_maps);
+/* Drain, stop the workers, free cached operators. NULL is a no-op. */
+void pcms_server_destroy(pcms_server s);
+
+/*
  * Kernel tracing (no counterpart in the paper; instrumentation). When enabled, every
  * library kernel launch is bracketed by a CUDA event pair recorded on the stream it is
  * launched on, and elapsed times are accumulated per kernel name. pcms_trace_enable(1)

@@ -83,17 +83,7 @@ pcms_status check_mls_args(const char* fn, int dim, const double* src, int64_t n
 }
 
 pcms::MlsParams make_params(int dim, int degree, double radius, const pcms_map_opts& o) {
-    pcms::MlsParams P;
-    P.dim = dim;
-    P.degree = degree;
-    P.m = num_terms(dim, degree);
-    P.prec = o.precision;
-    P.weight = o.weight;
-    P.radius = radius;
-    P.lambda = o.lambda;
-    P.min_neighbors = o.min_neighbors;
-    P.need = o.min_neighbors > 0 ? std::max(o.min_neighbors, P.m) : 0;
-    return P;
+    return pcms::make_mls_params(dim, degree, radius, o);
 }
 
 }  // namespace

@@ -315,6 +315,14 @@ void mesh_create(MeshImpl& M, const double* xy, int64_t nv, const int32_t* tri, 
     PCMS_LAUNCH_CHECK("mesh build");
 }
 
+int64_t estimate_mesh_bytes(int64_t nv, int64_t ntri, int64_t npts) {
+    (void)npts;
+    // copies of the mesh, orientation signs, rectangles, cell counts/starts, (cell, tri) pairs
+    double b = nv * 16.0 + ntri * (12.0 + 1.0 + 16.0) + 2.0 * 4.0 * (0.5 * ntri + 64.0) +
+               4.0 * 4.0 * ntri;
+    return (int64_t)(1.2 * b) + (int64_t(1) << 20);
+}
+
 void mesh_locate(const MeshImpl& M, const double* pts, int64_t n, const double* field,
                  int32_t* elem, int8_t* edim, double* vals, cudaStream_t s) {
     if (n <= 0) return;

@@ -11,7 +11,8 @@ namespace {
 
 constexpr int64_t MAX_CELLS = int64_t(1) << 24;
 constexpr double TAU_FP64 = 1e-14;   // (1e-7)^2: column-angle rank test of the definition
-constexpr double TAU_MIXED = 1e-4;   // FP32-assembled pivots below this are redone in FP64
+constexpr double TAU_MIXED = 1e-5;   // FP32-assembled pivots below this go to FP64
+constexpr double TAU_COMP = 1e-9;    // compensated-FP32 pivots below this go to FP64
 
 int asm_blocks(int64_t nwork, int G) {
     int64_t groups_per_block = 8 * (32 / G);
@@ -123,7 +124,109 @@ int accp(int dim, int deg, int mode) {
     return round_up4(nacc);
 }
 
+// Solve the tier-1 systems already assembled in sa.mom, then re-assemble and solve the
+// targets the solve hands on: tier 2 (compensated FP32) and tier 3 (FP64). `a` holds the
+// assembly arguments of tier 1 (mode-specific fields set). Mixed path only syncs to size the
+// tier-2/3 work; the FP64 path has a single tier.
+void solve_tiers(int dim, int deg, int mode, bool mixed, int G, const AsmArgs& a,
+                 SolveArgs sa, int64_t nt, cudaStream_t s) {
+    const int np = accp(dim, deg, mode);
+    DBuf lists(sizeof(int32_t) * (2 * nt + 2), s);
+    int32_t* list2 = lists.as<int32_t>();
+    int32_t* list3 = list2 + nt;
+    int32_t* n2 = list2 + 2 * nt;
+    int32_t* n3 = n2 + 1;
+    PCMS_CU(cudaMemsetAsync(n2, 0, 2 * sizeof(int32_t), s));
+    sa.list2 = list2;
+    sa.n2 = n2;
+    sa.list3 = list3;
+    sa.n3 = n3;
+    sa.tier = mixed ? 1 : 3;
+    sa.group = G;
+    sa.tau = mixed ? TAU_MIXED : TAU_FP64;
+    solve_any(dim, deg, mode, !mixed, sa, thread_blocks(nt, 128), s);
+    if (!mixed) return;
+    int32_t cnt[2] = {0, 0};
+    PCMS_CU(cudaMemcpyAsync(cnt, n2, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+    PCMS_CU(cudaStreamSynchronize(s));
+    if (cnt[0] > 0) {
+        DBuf mom2(sizeof(double) * np * cnt[0], s);
+        AsmArgs a2 = a;
+        a2.list = list2;
+        a2.n_list = n2;
+        a2.mom = mom2.p;
+        if (mode == MODE_FUSED) {
+            a2.kexp_in = a.kexp_out ? a.kexp_out : a.kexp_in;
+            a2.kexp_out = nullptr;
+        }
+        assemble_comp_any(dim, deg, mode, G, a2, asm_blocks(cnt[0], G), s);
+        SolveArgs s2 = sa;
+        s2.list = list2;
+        s2.n_list = n2;
+        s2.mom = mom2.p;
+        s2.tier = 2;
+        s2.tau = TAU_COMP;
+        solve_any(dim, deg, mode, true, s2, thread_blocks(cnt[0], 128), s);
+        PCMS_CU(cudaMemcpyAsync(&cnt[1], n3, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        PCMS_CU(cudaStreamSynchronize(s));
+    }
+    if (cnt[1] > 0) {
+        DBuf mom3(sizeof(double) * np * cnt[1], s);
+        AsmArgs a3 = a;
+        a3.list = list3;
+        a3.n_list = n3;
+        a3.mom = mom3.p;
+        if (mode == MODE_FUSED) {
+            a3.kexp_in = a.kexp_out ? a.kexp_out : a.kexp_in;
+            a3.kexp_out = nullptr;
+        }
+        assemble_any(dim, deg, false, mode, G, false, a3, asm_blocks(cnt[1], G), s);
+        SolveArgs s3 = sa;
+        s3.list = list3;
+        s3.n_list = n3;
+        s3.mom = mom3.p;
+        s3.tier = 3;
+        s3.tau = TAU_FP64;
+        solve_any(dim, deg, mode, true, s3, thread_blocks(cnt[1], 128), s);
+    }
+}
+
 }  // namespace
+
+MlsParams make_mls_params(int dim, int degree, double radius, const pcms_map_opts& o) {
+    MlsParams P;
+    P.dim = dim;
+    P.degree = degree;
+    P.m = mono_count(dim, degree);
+    P.prec = o.precision;
+    P.weight = o.weight;
+    P.radius = radius;
+    P.lambda = o.lambda;
+    P.min_neighbors = o.min_neighbors;
+    P.need = o.min_neighbors > 0 ? std::max(o.min_neighbors, P.m) : 0;
+    return P;
+}
+
+int64_t estimate_mls_bytes(const MlsParams& P, int64_t ns, int64_t nt, int nf, bool keep_map) {
+    const int d = P.dim;
+    const bool mixed = P.prec == PCMS_MIXED;
+    const double ball = d == 2 ? M_PI * P.radius * P.radius
+                               : 4.0 / 3.0 * M_PI * P.radius * P.radius * P.radius;
+    double k = std::max((double)P.m, std::max((double)P.need, (double)ns * ball));
+    k = std::min(k, (double)std::max<int64_t>(ns, 1));
+    const double elem = mixed ? 4.0 : 8.0;
+    const int np = round_up4(mono_count(d, 2 * P.degree) + P.m);
+    double b = 0;
+    b += ns * (4.0 + 4.0 + 8.0 * d + (mixed ? 24.0 : 0.0) + 12.0);   // sorted sources + sort scratch
+    b += nt * (4.0 + 4.0 + 8.0 * d + 12.0);                          // sorted targets + scratch
+    b += nt * (4.0 + 4.0 + 1.0 + 8.0 + 4.0);                         // counts, kexp, status, offsets, redo
+    b += nt * (np * elem + P.m * 8.0);                               // moments, y
+    const double nnz = 1.2 * k * nt;
+    if (keep_map || nf > 2) b += nnz * (4.0 + elem);                 // operator
+    b += (double)(ns + nt) * std::max(nf, 1) * elem * 2.0;           // apply/permute scratch
+    b += 4.0 * std::min<double>((double)(int64_t(1) << 24), 2.0 * ns + 64.0);  // cell starts
+    return (int64_t)(1.15 * b) + (int64_t(1) << 20);
+}
 
 int64_t MapImpl::device_bytes() const {
     return (int64_t)(src.cell_start.bytes + src.perm.bytes + src.inv.bytes + src.x64.bytes +
@@ -173,9 +276,7 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
         const int np = accp(dim, deg, MODE_MAP);
         DBuf mom((mixed ? sizeof(float) : sizeof(double)) * np * nt, s);
         DBuf y(sizeof(double) * m * nt, s);
-        DBuf redo(sizeof(int32_t) * (nt + 1), s);
-        int32_t* redo_n = redo.as<int32_t>() + nt;
-        PCMS_CU(cudaMemsetAsync(redo_n, 0, sizeof(int32_t), s));
+        DBuf flags(sizeof(int8_t) * nt, s);
         a.kexp_in = M.kexp.as<int32_t>();
         a.kexp_out = nullptr;
         a.offsets = M.offsets.as<int64_t>();
@@ -188,35 +289,13 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
         sa.counts = M.counts.as<int32_t>();
         sa.mom = mom.p;
         sa.lambda = P.lambda;
-        sa.tau = mixed ? TAU_MIXED : TAU_FP64;
-        sa.redo_on_fail = mixed ? 1 : 0;
-        sa.redo_list = redo.as<int32_t>();
-        sa.redo_n = redo_n;
         sa.y = y.as<double>();
+        sa.flags = mixed ? flags.as<int8_t>() : nullptr;
         sa.status = M.status.as<int8_t>();
-        solve_any(dim, deg, MODE_MAP, !mixed, sa, thread_blocks(nt, 128), s);
+        solve_tiers(dim, deg, MODE_MAP, mixed, G, a, sa, nt, s);
 
-        if (mixed) {
-            int32_t nredo = 0;
-            PCMS_CU(cudaMemcpyAsync(&nredo, redo_n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-            PCMS_CU(cudaStreamSynchronize(s));
-            if (nredo > 0) {
-                DBuf mom64(sizeof(double) * np * nredo, s);
-                AsmArgs r = a;
-                r.list = redo.as<int32_t>();
-                r.n_list = redo_n;
-                r.mom = mom64.p;
-                assemble_any(dim, deg, false, MODE_MAP, G, false, r, asm_blocks(nredo, G), s);
-                SolveArgs rs = sa;
-                rs.list = redo.as<int32_t>();
-                rs.n_list = redo_n;
-                rs.mom = mom64.p;
-                rs.tau = TAU_FP64;
-                rs.redo_on_fail = 0;
-                solve_any(dim, deg, MODE_MAP, true, rs, thread_blocks(nredo, 128), s);
-            }
-        }
         ShapeArgs sh{};
+        sh.flags = mixed ? flags.as<int8_t>() : nullptr;
         sh.g = M.g;
         sh.ns = ns;
         sh.nt = nt;
@@ -322,8 +401,6 @@ void mls_transfer(const MlsParams& P, const double* src, int64_t ns, const doubl
     DBuf kexp(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
     const int np = accp(dim, deg, MODE_FUSED);
     DBuf mom(fsz * np * std::max<int64_t>(nt, 1), s);
-    DBuf redo(sizeof(int32_t) * (nt + 1), s);
-    int32_t* redo_n = redo.as<int32_t>() + nt;
     for (int f = 0; f < nf; f++) {
         if (ns > 0) {
             PCMS_TRACE("mls_field_to_sorted", s);
@@ -336,7 +413,6 @@ void mls_transfer(const MlsParams& P, const double* src, int64_t ns, const doubl
             PCMS_LAUNCH_CHECK("permute_field");
         }
         if (nt == 0) continue;
-        PCMS_CU(cudaMemsetAsync(redo_n, 0, sizeof(int32_t), s));
         AsmArgs a = base_args(g, S, Tp, P);
         a.counts = counts.as<int32_t>();
         a.kexp_out = kexp.as<int32_t>();
@@ -348,37 +424,11 @@ void mls_transfer(const MlsParams& P, const double* src, int64_t ns, const doubl
         sa.counts = counts.as<int32_t>();
         sa.mom = mom.p;
         sa.lambda = P.lambda;
-        sa.tau = mixed ? TAU_MIXED : TAU_FP64;
-        sa.redo_on_fail = mixed ? 1 : 0;
-        sa.redo_list = redo.as<int32_t>();
-        sa.redo_n = redo_n;
         sa.perm_t = Tp.perm.as<int32_t>();
         sa.out = (char*)out + fsz * (size_t)f * nt;
         sa.out_is_double = !mixed;
         sa.status = f == 0 ? status : nullptr;
-        solve_any(dim, deg, MODE_FUSED, !mixed, sa, thread_blocks(nt, 128), s);
-        if (mixed) {
-            int32_t nredo = 0;
-            PCMS_CU(cudaMemcpyAsync(&nredo, redo_n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-            PCMS_CU(cudaStreamSynchronize(s));
-            if (nredo > 0) {
-                DBuf mom64(sizeof(double) * np * nredo, s);
-                AsmArgs r = a;
-                r.list = redo.as<int32_t>();
-                r.n_list = redo_n;
-                r.kexp_in = kexp.as<int32_t>();
-                r.kexp_out = nullptr;
-                r.mom = mom64.p;
-                assemble_any(dim, deg, false, MODE_FUSED, G, false, r, asm_blocks(nredo, G), s);
-                SolveArgs rs = sa;
-                rs.list = redo.as<int32_t>();
-                rs.n_list = redo_n;
-                rs.mom = mom64.p;
-                rs.tau = TAU_FP64;
-                rs.redo_on_fail = 0;
-                solve_any(dim, deg, MODE_FUSED, true, rs, thread_blocks(nredo, 128), s);
-            }
-        }
+        solve_tiers(dim, deg, MODE_FUSED, mixed, G, a, sa, nt, s);
     }
     if (status && P.min_neighbors == 0 && nt > 0) {
         DBuf st(sizeof(unsigned long long) * 4, s);

@@ -15,9 +15,19 @@ namespace pcms {
     void solve_dispatch_d##DIMV(int deg, int mode, bool mom_double, const SolveArgs& a,       \
                                 int blocks, cudaStream_t s);                                  \
     void shape_dispatch_d##DIMV(int deg, bool mixed, int G, const ShapeArgs& a, int blocks,   \
-                                cudaStream_t s);
+                                cudaStream_t s);                                              \
+    void assemble_comp_dispatch_d##DIMV(int deg, int mode, int G, const AsmArgs& a,            \
+                                        int blocks, cudaStream_t s);
 PCMS_DECLARE_MLS_DISPATCH(2)
 PCMS_DECLARE_MLS_DISPATCH(3)
+
+// compensated FP32 assembly (mixed precision, tier 2), MODE_MAP or MODE_FUSED
+inline void assemble_comp_any(int dim, int deg, int mode, int G, const AsmArgs& a, int blocks,
+                              cudaStream_t s) {
+    PCMS_TRACE(mode == MODE_FUSED ? "mls_assemble_fused_comp" : "mls_assemble_map_comp", s);
+    if (dim == 2) assemble_comp_dispatch_d2(deg, mode, G, a, blocks, s);
+    else assemble_comp_dispatch_d3(deg, mode, G, a, blocks, s);
+}
 
 inline void assemble_any(int dim, int deg, bool mixed, int mode, int G, bool fd,
                          const AsmArgs& a, int blocks, cudaStream_t s) {
@@ -129,5 +139,22 @@ inline void shape_any(int dim, int deg, bool mixed, int G, const ShapeArgs& a, i
             }                                                                                 \
         }                                                                                     \
         PCMS_LAUNCH_CHECK("k_shape");                                                         \
+    }                                                                                         \
+    template <int DEG>                                                                        \
+    static void comp_mode(int mode, int G, const AsmArgs& a, int b, cudaStream_t s) {         \
+        if (mode == MODE_MAP) {                                                               \
+            if (G == 32) k_assemble<DIMV, DEG, true, MODE_MAP, 32, float, true><<<b, 256, 0, s>>>(a); \
+            else k_assemble<DIMV, DEG, true, MODE_MAP, 8, float, true><<<b, 256, 0, s>>>(a);  \
+        } else {                                                                              \
+            if (G == 32) k_assemble<DIMV, DEG, true, MODE_FUSED, 32, float, true><<<b, 256, 0, s>>>(a); \
+            else k_assemble<DIMV, DEG, true, MODE_FUSED, 8, float, true><<<b, 256, 0, s>>>(a); \
+        }                                                                                     \
+    }                                                                                         \
+    void assemble_comp_dispatch_d##DIMV(int deg, int mode, int G, const AsmArgs& a, int b,    \
+                                        cudaStream_t s) {                                     \
+        if (deg == 0) comp_mode<0>(mode, G, a, b, s);                                         \
+        else if (deg == 1) comp_mode<1>(mode, G, a, b, s);                                    \
+        else comp_mode<2>(mode, G, a, b, s);                                                  \
+        PCMS_LAUNCH_CHECK("k_assemble_comp");                                                 \
     }                                                                                         \
     }

@@ -53,18 +53,32 @@ struct AsmArgs {
     unsigned* err;
 };
 
+// Precision tiers of the mixed path. The FP64 solve of a tier-1 system estimates how much
+// the FP32 assembly error can move c_0 and hands sensitive targets to the next tier:
+//   tier 1  plain FP32 accumulation      accepted if amp * (1 + sqrt(n / (3 G^2))) <= AMP_T1
+//   tier 2  compensated FP32 (Kahan)     accepted if amp <= AMP_T2
+//   tier 3  FP64 assembly                final (pivot guard TAU_FP64 only)
+// A failed pivot guard in tier 1 or 2 also goes to tier 3.
+constexpr double AMP_T1 = 32.0;
+constexpr double AMP_T2 = 2048.0;
+constexpr double AMP_SHAPE = 32.0;   // operator rows above this are evaluated in FP64
+
 struct SolveArgs {
     int64_t nt;
     const int32_t* list;
     const int32_t* n_list;
     const int32_t* counts;
-    const void* mom;          // [nt][NACCP] (float or double)
+    const void* mom;          // [nt or list][NACCP] (float or double)
     double lambda;
     double tau;               // pivot guard: d_k <= tau * G_kk fails
-    int redo_on_fail;         // 1: append to redo list instead of ILL
-    int32_t* redo_list;
-    int32_t* redo_n;
+    int tier;                 // 1, 2 (mixed) or 3 (FP64)
+    int group;                // lanes per target of the assembly (error model)
+    int32_t* list2;           // targets for tier 2 / tier 3
+    int32_t* n2;
+    int32_t* list3;
+    int32_t* n3;
     double* y;                // MAP: [nt][m]
+    int8_t* flags;            // MAP: 1 = evaluate the operator row in FP64
     int8_t* status;           // MAP: sorted order; FUSED: caller order (via perm) or null
     const int32_t* perm_t;    // FUSED: sorted -> caller target index
     void* out;                // FUSED: caller-order output (float or double)
@@ -82,6 +96,7 @@ struct ShapeArgs {
     const int64_t* offsets;
     const int32_t* cols;
     const double* y;
+    const int8_t* flags;   // per target: 1 = evaluate in FP64 (mixed maps), or null
     double radius;
     int weight;
     void* vals;
@@ -205,8 +220,20 @@ __device__ __forceinline__ double4 make_entry<double>(double a, double b, double
 }
 
 // accumulate one selected pair: dx (target-relative offsets), payload b (field value)
-template <int DIM, int DEG, int MODE, typename T, int NACC>
-__host__ __device__ __forceinline__ void accumulate(T (&acc)[NACC > 0 ? NACC : 1], const T* dx,
+// s += x with Kahan's compensation c (the true running sum is s - c)
+template <typename T>
+__host__ __device__ __forceinline__ void kahan_add(T& s, T& c, T x) {
+    const T y = x - c;
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// COMP = true: every accumulator is a compensated (Kahan) sum; acc holds the sums and cmp
+// their compensations.
+template <int DIM, int DEG, int MODE, typename T, int NACC, bool COMP = false>
+__host__ __device__ __forceinline__ void accumulate(T (&acc)[NACC > 0 ? NACC : 1],
+                                                    T (&cmp)[NACC > 0 ? NACC : 1], const T* dx,
                                                     T b, int kind, T inv_r) {
     constexpr int NM = mono_count(DIM, 2 * DEG);
     constexpr int M = mono_count(DIM, DEG);
@@ -226,24 +253,28 @@ __host__ __device__ __forceinline__ void accumulate(T (&acc)[NACC > 0 ? NACC : 1
     u[2] = DIM == 3 ? dx[2] * inv_r : T(0);
     T wm[NM];
     wm[0] = w;
-    acc[0] += w;
+    if constexpr (COMP) kahan_add(acc[0], cmp[0], w);
+    else acc[0] += w;
     sfor<NM - 1>([&](auto I) {
         constexpr int p = decltype(I)::value + 1;
         constexpr int par = mono_parent(DIM, p);
         constexpr int v = mono_var(DIM, p);
         wm[p] = wm[par] * u[v];
-        acc[p] += wm[p];
+        if constexpr (COMP) kahan_add(acc[p], cmp[p], wm[p]);
+        else acc[p] += wm[p];
     });
     if constexpr (MODE == MODE_FUSED) {
         T wb[M];
         wb[0] = w * b;
-        acc[NM] += wb[0];
+        if constexpr (COMP) kahan_add(acc[NM], cmp[NM], wb[0]);
+        else acc[NM] += wb[0];
         sfor<M - 1>([&](auto I) {
             constexpr int p = decltype(I)::value + 1;
             constexpr int par = mono_parent(DIM, p);
             constexpr int v = mono_var(DIM, p);
             wb[p] = wb[par] * u[v];
-            acc[NM + p] += wb[p];
+            if constexpr (COMP) kahan_add(acc[NM + p], cmp[NM + p], wb[p]);
+            else acc[NM + p] += wb[p];
         });
     }
 }
@@ -251,9 +282,12 @@ __host__ __device__ __forceinline__ void accumulate(T (&acc)[NACC > 0 ? NACC : 1
 // ------------------------------------------------------------------------------------
 // k_assemble
 // ------------------------------------------------------------------------------------
-template <int DIM, int DEG, bool MIXED, int MODE, int G, typename FT>
+// COMP (mixed only): compensated FP32 accumulation, lanes reduced in FP64, moments written
+// as FP64 (used for the targets the mixed solve flags as sensitive).
+template <int DIM, int DEG, bool MIXED, int MODE, int G, typename FT, bool COMP = false>
 __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
     using T = typename std::conditional<MIXED, float, double>::type;
+    using MT = typename std::conditional<COMP, double, T>::type;   // stored moment type
     using QE = typename QEntry<T>::type;
     constexpr int NM = mono_count(DIM, 2 * DEG);
     constexpr int M = mono_count(DIM, DEG);
@@ -302,6 +336,7 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
             row_len = A.offsets[t + 1] - row_off;
         }
         T acc[NACC > 0 ? NACC : 1];
+        T cmp[NACC > 0 ? NACC : 1];
         for (;;) {
             const double r = ldexp(A.radius, k);
             const double r2 = r * r;
@@ -322,7 +357,10 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
                 }
             }
 #pragma unroll
-            for (int i = 0; i < (NACC > 0 ? NACC : 1); i++) acc[i] = T(0);
+            for (int i = 0; i < (NACC > 0 ? NACC : 1); i++) {
+                acc[i] = T(0);
+                cmp[i] = T(0);
+            }
             cnt = 0;
             int qn = 0, head = 0;
             int64_t written = 0;
@@ -393,7 +431,7 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
                             if (qn >= G) {
                                 QE e = q[(head + gl) & (QCAP - 1)];
                                 T edx[3] = {e.x, e.y, e.z};
-                                accumulate<DIM, DEG, MODE, T, NACC>(acc, edx, e.w, A.weight, inv_r);
+                                accumulate<DIM, DEG, MODE, T, NACC, COMP>(acc, cmp, edx, e.w, A.weight, inv_r);
                                 if (MODE == MODE_MAP) {
                                     if (written + gl < row_len) A.cols[row_off + written + gl] = unpack_index(e.w);
                                     written += G;
@@ -408,7 +446,7 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
                     if (gl < qn) {
                         QE e = q[(head + gl) & (QCAP - 1)];
                         T edx[3] = {e.x, e.y, e.z};
-                        accumulate<DIM, DEG, MODE, T, NACC>(acc, edx, e.w, A.weight, inv_r);
+                        accumulate<DIM, DEG, MODE, T, NACC, COMP>(acc, cmp, edx, e.w, A.weight, inv_r);
                         if (MODE == MODE_MAP && written + gl < row_len)
                             A.cols[row_off + written + gl] = unpack_index(e.w);
                     }
@@ -421,18 +459,24 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
             }
             break;
         }
+        MT red[NACC > 0 ? NACC : 1];
+#pragma unroll
+        for (int i = 0; i < (NACC > 0 ? NACC : 1); i++) {
+            if constexpr (COMP) red[i] = (double)acc[i] - (double)cmp[i];
+            else red[i] = acc[i];
+        }
         if (NACC > 0) {
 #pragma unroll
             for (int i = 0; i < (NACC > 0 ? NACC : 1); i++) {
 #pragma unroll
-                for (int o = G / 2; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(gmask, acc[i], o);
+                for (int o = G / 2; o > 0; o >>= 1) red[i] += __shfl_xor_sync(gmask, red[i], o);
             }
         }
         if (gl == 0) {
             if (NACC > 0) {
-                T* dst = (T*)A.mom + (A.list ? wk : t) * NACCP;   // list mode: by list position
+                MT* dst = (MT*)A.mom + (A.list ? wk : t) * NACCP;   // list mode: by list position
 #pragma unroll
-                for (int i = 0; i < NACCP; i++) dst[i] = i < NACC ? acc[i < NACC ? i : 0] : T(0);
+                for (int i = 0; i < NACCP; i++) dst[i] = i < NACC ? red[i < NACC ? i : 0] : MT(0);
             }
             A.counts[t] = cnt;
             if (A.kexp_out) A.kexp_out[t] = k;
@@ -445,14 +489,17 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
 // per-target solve: G from the moments (+ lambda on the diagonal), LDL^T with the pivot
 // guard d_k > tau * G_kk for every k (d_k / G_kk = R_kk^2 / ||column k||^2 of the weighted
 // Vandermonde matrix), then
-//   MODE_MAP:   out[0..m) = G^-1 e_1                 (L w = e_1, z = D^-1 w, L^T y = z)
-//   MODE_FUSED: out[0]    = e_1^T G^-1 g = (L^-1 e_1)^T D^-1 (L^-1 g)
+//   y[0..m) = G^-1 e_1   (L w = e_1, z = D^-1 w, L^T y = z; the operator row is w a^T y)
+//   *c0     = y^T g = e_1^T G^-1 g   (MODE_FUSED; G is symmetric)
+//   *amp    = sqrt(G_00) sum_k |y_k| sqrt(G_kk): how much relative perturbations of the
+//             moments are amplified in c_0 (1 for an orthogonal basis).
 // mom = [moments of degree <= 2k (graded-lex)] [g (FUSED only)]. Returns false when the
 // guard fails. Host-callable so the algebra can be checked without a GPU.
 // ------------------------------------------------------------------------------------
 template <int DIM, int DEG, int MODE>
 __host__ __device__ __forceinline__ bool solve_moments(const double* mom, double lambda,
-                                                       double tau, double* out) {
+                                                       double tau, double* out, double* c0,
+                                                       double* amp) {
     constexpr int NM = mono_count(DIM, 2 * DEG);
     constexpr int M = mono_count(DIM, DEG);
     constexpr int NP = M * (M + 1) / 2;
@@ -464,10 +511,11 @@ __host__ __device__ __forceinline__ bool solve_moments(const double* mom, double
             L[k * (k + 1) / 2 + l] = mom[mono_prod(DIM, k, l)] + (k == l ? lambda : 0.0);
         });
     });
-    double invd[M];
+    double invd[M], diag[M];
     bool ok = true;
     sfor<M>([&](auto K) {
         constexpr int k = decltype(K)::value;
+        diag[k] = L[k * (k + 1) / 2 + k];
         sfor<k>([&](auto Jx) {
             constexpr int j = decltype(Jx)::value;
             double s = L[k * (k + 1) / 2 + j];
@@ -489,24 +537,7 @@ __host__ __device__ __forceinline__ bool solve_moments(const double* mom, double
         invd[k] = 1.0 / dk;
     });
     if (!ok) return false;
-    if (MODE == MODE_FUSED) {
-        double z1[M], zg[M];
-        sfor<M>([&](auto K) {
-            constexpr int k = decltype(K)::value;
-            double a = k == 0 ? 1.0 : 0.0;
-            double b = mom[NM + k];
-            sfor<k>([&](auto Jx) {
-                constexpr int j = decltype(Jx)::value;
-                a -= L[k * (k + 1) / 2 + j] * z1[j];
-                b -= L[k * (k + 1) / 2 + j] * zg[j];
-            });
-            z1[k] = a;
-            zg[k] = b;
-        });
-        double c0 = 0.0;
-        for (int k = 0; k < M; k++) c0 += z1[k] * invd[k] * zg[k];
-        out[0] = c0;
-    } else {
+    {
         double w[M], z[M];
         sfor<M>([&](auto K) {
             constexpr int k = decltype(K)::value;
@@ -528,6 +559,13 @@ __host__ __device__ __forceinline__ bool solve_moments(const double* mom, double
             out[k] = a;
         });
     }
+    double s = 0.0, cc = 0.0;
+    for (int k = 0; k < M; k++) {
+        s += fabs(out[k]) * sqrt(fmax(diag[k], 0.0));
+        if (MODE == MODE_FUSED) cc += out[k] * mom[NM + k];
+    }
+    if (amp) *amp = s * sqrt(fmax(diag[0], 0.0));
+    if (c0) *c0 = cc;
     return true;
 }
 
@@ -546,7 +584,7 @@ __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
         const int64_t t = S.list ? (int64_t)S.list[wk] : wk;
         const int cnt = S.counts[t];
         int st = PCMS_TARGET_OK;
-        double val = 0.0;
+        double val = 0.0, amp = 0.0;
         double y[M];
         if (cnt < M) {
             st = PCMS_TARGET_UNDERDETERMINED;
@@ -555,15 +593,30 @@ __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
             double mom[NACC];
 #pragma unroll
             for (int i = 0; i < NACC; i++) mom[i] = (double)src[i];
-            if (!solve_moments<DIM, DEG, MODE>(mom, S.lambda, S.tau, y))
+            if (!solve_moments<DIM, DEG, MODE>(mom, S.lambda, S.tau, y, &val, &amp))
                 st = PCMS_TARGET_ILL_CONDITIONED;
-            val = y[0];
         }
-        if (st == PCMS_TARGET_ILL_CONDITIONED && S.redo_on_fail) {
-            int pos = atomicAdd(S.redo_n, 1);
-            S.redo_list[pos] = (int32_t)t;
-            continue;   // the FP64 pass writes this target
+        if (S.tier < 3 && st != PCMS_TARGET_UNDERDETERMINED) {
+            int next = 0;
+            if (st == PCMS_TARGET_ILL_CONDITIONED) {
+                next = 3;
+            } else if (S.tier == 1) {
+                const double g = (double)S.group;
+                const double risk = amp * (1.0 + sqrt((double)cnt / (3.0 * g * g)));
+                if (risk > AMP_T1) next = amp > AMP_T2 ? 3 : 2;
+            } else if (amp > AMP_T2) {
+                next = 3;
+            }
+            if (next == 2) {
+                S.list2[atomicAdd(S.n2, 1)] = (int32_t)t;
+                continue;   // a later tier writes this target
+            }
+            if (next == 3) {
+                S.list3[atomicAdd(S.n3, 1)] = (int32_t)t;
+                continue;
+            }
         }
+        if (MODE == MODE_MAP && S.flags) S.flags[t] = (int8_t)(amp > AMP_SHAPE ? 1 : 0);
         const double nanv = __longlong_as_double(0x7ff8000000000000LL);
         if (MODE == MODE_FUSED) {
             const int64_t o = S.perm_t ? (int64_t)S.perm_t[t] : t;
@@ -607,6 +660,7 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
         T y[M];
 #pragma unroll
         for (int k = 0; k < M; k++) y[k] = (T)S.y[t * M + k];
+        const int flag = S.flags ? S.flags[t] : 0;
         const double r = ldexp(S.radius, S.kexp[t]);
         const T inv_r = (T)(1.0 / r);
         const int64_t a = S.offsets[t], b = S.offsets[t + 1];
@@ -635,6 +689,22 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
             else qv = sqrt(d2) * inv_r;
             const T w = weight_value<T>(S.weight, qv);
             T u[3] = {dx[0] * inv_r, dx[1] * inv_r, dx[2] * inv_r};
+            if (MIXED && flag) {
+                // sensitive row: the same FP32 u and w as the moments, monomials and the dot
+                // product with y in FP64
+                double am[M];
+                am[0] = 1.0;
+                double s = S.y[t * M];
+                sfor<M - 1>([&](auto I) {
+                    constexpr int p = decltype(I)::value + 1;
+                    constexpr int par = mono_parent(DIM, p);
+                    constexpr int v = mono_var(DIM, p);
+                    am[p] = am[par] * (double)u[v];
+                    s += am[p] * S.y[t * M + p];
+                });
+                ((T*)S.vals)[i] = (T)((double)w * s);
+                continue;
+            }
             T am[M];
             am[0] = T(1);
             T s = y[0];

@@ -183,6 +183,13 @@ struct MlsParams {
     int need;  // max(min_neighbors, m) if min_neighbors > 0 else 0
 };
 
+MlsParams make_mls_params(int dim, int degree, double radius, const pcms_map_opts& o);
+
+// device bytes a request needs at most (sorted copies, operator, scratch), estimated from
+// the sizes with the sources' bounding box taken as the unit box
+int64_t estimate_mls_bytes(const MlsParams& P, int64_t ns, int64_t nt, int nf, bool keep_map);
+int64_t estimate_mesh_bytes(int64_t nv, int64_t ntri, int64_t npts);
+
 struct MapImpl {
     MlsParams P;
     Grid g;

@@ -1,0 +1,366 @@
+// serve.cu -- continuous-batching request loop around the transfer kernels.
+//
+// n_slots worker threads each own a non-blocking CUDA stream. Requests are admitted in
+// submission order when a slot is idle and their device-memory estimate fits under the
+// cap together with what is already admitted or cached; cached operators that no running
+// request uses are evicted least-recently-used first. Each admitted request runs entirely
+// on its slot's stream (the library's own syncs wait for that stream only), so requests on
+// different slots overlap on the GPU. Completion is taken after the slot's stream has
+// drained. No thread ever waits on the GPU without a bounded host-side timeout path: the
+// client's drain/poll calls have explicit timeouts.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "pcms_internal.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Job {
+    pcms_request req;
+    int64_t ticket = 0;
+    int64_t bytes = 0;
+    double t_submit = 0, t_start = 0, t_end = 0;
+    pcms_status st = PCMS_OK;
+    int used_cached = 0;
+    bool builds_cache = false;
+};
+
+struct CacheEntry {
+    std::unique_ptr<pcms::MapImpl> map;
+    int64_t bytes = 0;       // bytes charged to the cap while cached
+    bool ready = false;
+    int pins = 0;
+    uint64_t last_use = 0;
+};
+
+}  // namespace
+
+struct pcms_server_s {
+    int device = 0;
+    int n_slots = 1;
+    int64_t cap = 0;
+    Clock::time_point t0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done, cv_cache;
+    std::deque<Job*> queue;
+    std::vector<std::unique_ptr<Job>> jobs;
+    std::deque<int64_t> finished;
+    int64_t n_submitted = 0, n_completed = 0;
+    int64_t in_use = 0, peak = 0;
+    uint64_t use_clock = 0;
+    bool stop = false;
+    std::unordered_map<int64_t, CacheEntry> cache;
+    std::vector<std::thread> workers;
+    std::vector<cudaStream_t> streams;
+
+    double now() const {
+        return std::chrono::duration<double>(Clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+int64_t request_bytes(const pcms_request& r) {
+    if (r.bytes_hint > 0) return r.bytes_hint;
+    if (r.kind == PCMS_REQ_MESH) return pcms::estimate_mesh_bytes(r.n_src, r.n_tri, r.n_tgt);
+    pcms::MlsParams P = pcms::make_mls_params(r.dim, r.basis_degree, r.radius, r.opts);
+    const bool keep = r.map_key >= 0;
+    return pcms::estimate_mls_bytes(P, r.n_src, r.n_tgt, r.n_fields, keep);
+}
+
+// evict unpinned cached operators (LRU) until `need` more bytes fit; caller holds the lock
+void evict_for(pcms_server_s* S, int64_t need) {
+    while (S->in_use + need > S->cap) {
+        auto victim = S->cache.end();
+        for (auto it = S->cache.begin(); it != S->cache.end(); ++it) {
+            if (!it->second.ready || it->second.pins > 0) continue;
+            if (victim == S->cache.end() || it->second.last_use < victim->second.last_use) victim = it;
+        }
+        if (victim == S->cache.end()) return;
+        S->in_use -= victim->second.bytes;
+        S->cache.erase(victim);   // frees the operator on the stream that built it
+    }
+}
+
+void run_job(pcms_server_s* S, Job* j, cudaStream_t s, pcms::MapImpl* cached,
+             std::unique_ptr<pcms::MapImpl>* built) {
+    const pcms_request& r = j->req;
+    if (r.kind == PCMS_REQ_MESH) {
+        pcms::MeshImpl mesh;
+        mesh.stream = s;
+        pcms::mesh_create(mesh, r.src_pts, r.n_src, r.tri, r.n_tri);
+        pcms::mesh_locate(mesh, r.tgt_pts, r.n_tgt, r.out ? (const double*)r.fields : nullptr,
+                          r.elem_ids, nullptr, (double*)r.out, s);
+        PCMS_CU(cudaStreamSynchronize(s));
+        return;
+    }
+    pcms::MlsParams P = pcms::make_mls_params(r.dim, r.basis_degree, r.radius, r.opts);
+    if (cached) {
+        pcms::mls_apply(*cached, r.fields, r.n_fields, r.out, s);
+    } else if (built) {
+        std::unique_ptr<pcms::MapImpl> M(new pcms::MapImpl());
+        M->P = P;
+        M->ns = r.n_src;
+        M->nt = r.n_tgt;
+        M->stream = s;
+        pcms::mls_create_map(*M, r.src_pts, r.tgt_pts, r.opts);
+        pcms::mls_apply(*M, r.fields, r.n_fields, r.out, s);
+        *built = std::move(M);
+    } else if (r.n_fields <= 2) {
+        int64_t nu = 0;
+        pcms::mls_transfer(P, r.src_pts, r.n_src, r.tgt_pts, r.n_tgt, r.opts, r.fields,
+                           r.n_fields, r.out, nullptr, s, &nu);
+    } else {
+        pcms::MapImpl M;
+        M.P = P;
+        M.ns = r.n_src;
+        M.nt = r.n_tgt;
+        M.stream = s;
+        pcms::mls_create_map(M, r.src_pts, r.tgt_pts, r.opts);
+        pcms::mls_apply(M, r.fields, r.n_fields, r.out, s);
+    }
+    PCMS_CU(cudaStreamSynchronize(s));
+}
+
+void worker(pcms_server_s* S, int slot) {
+    cudaSetDevice(S->device);
+    cudaStream_t s = S->streams[slot];
+    for (;;) {
+        Job* j = nullptr;
+        pcms::MapImpl* cached = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            for (;;) {
+                if (S->stop && S->queue.empty()) return;
+                if (!S->queue.empty()) {
+                    Job* h = S->queue.front();
+                    if (h->bytes > S->cap) {   // can never fit
+                        S->queue.pop_front();
+                        h->st = PCMS_ERR_CAPACITY;
+                        h->t_start = h->t_end = S->now();
+                        S->finished.push_back(h->ticket);
+                        S->n_completed++;
+                        S->cv_done.notify_all();
+                        continue;
+                    }
+                    // a reuse request whose operator is being built waits for it
+                    const pcms_request& r = h->req;
+                    int64_t need = h->bytes;
+                    bool reuse = r.kind == PCMS_REQ_MLS && r.reuse_map && r.map_key >= 0;
+                    auto it = reuse ? S->cache.find(r.map_key) : S->cache.end();
+                    if (reuse && it != S->cache.end() && !it->second.ready) {
+                        S->cv_cache.wait(lk);
+                        continue;
+                    }
+                    if (reuse && it != S->cache.end()) {
+                        // only the apply scratch is new
+                        need = (int64_t)(r.n_src + r.n_tgt) * std::max(r.n_fields, 1) * 8 * 2 +
+                               (int64_t(1) << 20);
+                    }
+                    if (S->in_use + need > S->cap) evict_for(S, need);
+                    if (S->in_use + need <= S->cap) {
+                        S->queue.pop_front();
+                        h->bytes = need;
+                        S->in_use += need;
+                        S->peak = std::max(S->peak, S->in_use);
+                        h->t_start = S->now();
+                        if (reuse && it != S->cache.end()) {
+                            it->second.pins++;
+                            it->second.last_use = ++S->use_clock;
+                            cached = it->second.map.get();
+                            h->used_cached = 1;
+                        } else if (r.kind == PCMS_REQ_MLS && r.map_key >= 0 &&
+                                   S->cache.find(r.map_key) == S->cache.end()) {
+                            CacheEntry e;
+                            e.ready = false;
+                            S->cache.emplace(r.map_key, std::move(e));
+                            h->builds_cache = true;
+                        }
+                        j = h;
+                        break;
+                    }
+                }
+                S->cv_work.wait(lk);
+            }
+        }
+        std::unique_ptr<pcms::MapImpl> built;
+        pcms_status st = PCMS_OK;
+        try {
+            run_job(S, j, s, cached, j->builds_cache ? &built : nullptr);
+        } catch (const pcms::PcmsError& e) {
+            st = e.status;
+        } catch (...) {
+            st = PCMS_ERR_CUDA;
+        }
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            j->st = st;
+            j->t_end = S->now();
+            S->in_use -= j->bytes;
+            if (cached) {
+                auto it = S->cache.find(j->req.map_key);
+                if (it != S->cache.end()) it->second.pins--;
+            }
+            if (j->builds_cache) {
+                auto it = S->cache.find(j->req.map_key);
+                if (st == PCMS_OK && built) {
+                    int64_t b = built->device_bytes();
+                    it->second.map = std::move(built);
+                    it->second.bytes = b;
+                    it->second.ready = true;
+                    it->second.last_use = ++S->use_clock;
+                    S->in_use += b;
+                    S->peak = std::max(S->peak, S->in_use);
+                    if (S->in_use > S->cap) evict_for(S, 0);
+                } else if (it != S->cache.end()) {
+                    S->cache.erase(it);
+                }
+                S->cv_cache.notify_all();
+            }
+            S->finished.push_back(j->ticket);
+            S->n_completed++;
+        }
+        S->cv_done.notify_all();
+        S->cv_work.notify_all();
+    }
+}
+
+thread_local std::string g_server_err;
+
+}  // namespace
+
+extern "C" {
+
+pcms_status pcms_server_create(int n_slots, int64_t mem_cap_bytes, pcms_server* out) {
+    if (!out || n_slots < 1 || n_slots > 64 || mem_cap_bytes <= 0) return PCMS_ERR_INVALID_ARG;
+    *out = nullptr;
+    pcms_server_s* S = new pcms_server_s();
+    S->n_slots = n_slots;
+    S->cap = mem_cap_bytes;
+    S->t0 = Clock::now();
+    if (cudaGetDevice(&S->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete S;
+        return PCMS_ERR_CUDA;
+    }
+    pcms::ensure_mempool(S->device);
+    for (int i = 0; i < n_slots; i++) {
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            for (cudaStream_t x : S->streams) cudaStreamDestroy(x);
+            delete S;
+            return PCMS_ERR_CUDA;
+        }
+        S->streams.push_back(st);
+    }
+    for (int i = 0; i < n_slots; i++) S->workers.emplace_back(worker, S, i);
+    *out = S;
+    return PCMS_OK;
+}
+
+pcms_status pcms_server_submit(pcms_server S, const pcms_request* req, int64_t* ticket) {
+    if (!S || !req) return PCMS_ERR_INVALID_ARG;
+    const pcms_request& r = *req;
+    if (r.kind == PCMS_REQ_MLS) {
+        if ((r.dim != 2 && r.dim != 3) || r.basis_degree < 0 || r.basis_degree > 2 ||
+            !(r.radius > 0.0) || r.n_fields < 1 || r.n_fields > 16 || r.n_src < 0 || r.n_tgt < 0 ||
+            (r.n_tgt > 0 && !r.out) || (r.n_src > 0 && !r.fields) ||
+            (r.n_src > 0 && !r.src_pts) || (r.n_tgt > 0 && !r.tgt_pts))
+            return PCMS_ERR_INVALID_ARG;
+    } else if (r.kind == PCMS_REQ_MESH) {
+        if (r.n_src < 0 || r.n_tri < 0 || r.n_tgt < 0 || (r.n_src > 0 && !r.src_pts) ||
+            (r.n_tri > 0 && !r.tri) || (r.n_tgt > 0 && (!r.tgt_pts || !r.elem_ids)) ||
+            (r.out && !r.fields))
+            return PCMS_ERR_INVALID_ARG;
+    } else {
+        return PCMS_ERR_INVALID_ARG;
+    }
+    std::unique_ptr<Job> j(new Job());
+    j->req = r;
+    j->bytes = request_bytes(r);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        j->ticket = S->n_submitted++;
+        j->t_submit = S->now();
+        if (ticket) *ticket = j->ticket;
+        S->queue.push_back(j.get());
+        S->jobs.push_back(std::move(j));
+    }
+    S->cv_work.notify_one();
+    return PCMS_OK;
+}
+
+pcms_status pcms_server_poll(pcms_server S, pcms_request_result* res, int max_results,
+                             double timeout_s, int* n_results) {
+    if (!S || !n_results || (max_results > 0 && !res)) return PCMS_ERR_INVALID_ARG;
+    *n_results = 0;
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (S->finished.empty() && timeout_s > 0)
+        S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s),
+                            [&] { return !S->finished.empty(); });
+    int n = 0;
+    while (n < max_results && !S->finished.empty()) {
+        Job* j = S->jobs[(size_t)S->finished.front()].get();
+        S->finished.pop_front();
+        pcms_request_result& o = res[n++];
+        o.ticket = j->ticket;
+        o.status = j->st;
+        o.t_submit = j->t_submit;
+        o.t_start = j->t_start;
+        o.t_end = j->t_end;
+        o.bytes_reserved = j->bytes;
+        o.used_cached_map = j->used_cached;
+    }
+    *n_results = n;
+    return PCMS_OK;
+}
+
+pcms_status pcms_server_drain(pcms_server S, double timeout_s) {
+    if (!S) return PCMS_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(S->mu);
+    bool ok = S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s),
+                                  [&] { return S->n_completed == S->n_submitted; });
+    return ok ? PCMS_OK : PCMS_ERR_TIMEOUT;
+}
+
+double pcms_server_now(pcms_server S) { return S ? S->now() : 0.0; }
+
+pcms_status pcms_server_memory(pcms_server S, int64_t* in_use, int64_t* peak,
+                               int64_t* cached_maps) {
+    if (!S) return PCMS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (in_use) *in_use = S->in_use;
+    if (peak) *peak = S->peak;
+    if (cached_maps) *cached_maps = (int64_t)S->cache.size();
+    return PCMS_OK;
+}
+
+void pcms_server_destroy(pcms_server S) {
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    S->cv_cache.notify_all();
+    for (std::thread& t : S->workers) t.join();
+    S->cache.clear();
+    for (cudaStream_t st : S->streams) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    delete S;
+}
+
+}  // extern "C"

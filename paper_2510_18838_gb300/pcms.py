@@ -44,6 +44,26 @@ class MapInfo(ctypes.Structure):
                 ("max_radius_doublings", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("dim", ctypes.c_int), ("basis_degree", ctypes.c_int),
+                ("radius", ctypes.c_double), ("opts", MapOpts),
+                ("src_pts", ctypes.c_void_p), ("n_src", ctypes.c_int64),
+                ("tgt_pts", ctypes.c_void_p), ("n_tgt", ctypes.c_int64),
+                ("fields", ctypes.c_void_p), ("n_fields", ctypes.c_int),
+                ("out", ctypes.c_void_p), ("map_key", ctypes.c_int64), ("reuse_map", ctypes.c_int),
+                ("tri", ctypes.c_void_p), ("n_tri", ctypes.c_int64),
+                ("elem_ids", ctypes.c_void_p), ("bytes_hint", ctypes.c_int64)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_int64), ("status", ctypes.c_int),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_end", ctypes.c_double), ("bytes_reserved", ctypes.c_int64),
+                ("used_cached_map", ctypes.c_int)]
+
+
+REQ_MLS, REQ_MESH = 0, 1
+
 _lib = None
 
 # exported symbol -> (restype, argtypes)
@@ -62,6 +82,13 @@ SIGNATURES = {
     "pcms_mesh_create": (_I, [_P, _I64, _P, _I64, _P, _P]),
     "pcms_locate_interp": (_I, [_P, _P, _I64, _P, _P, _P, _P, _P]),
     "pcms_mesh_destroy": (None, [_P, _P]),
+    "pcms_server_create": (_I, [_I, _I64, _P]),
+    "pcms_server_submit": (_I, [_P, _P, _P]),
+    "pcms_server_poll": (_I, [_P, _P, _I, _D, _P]),
+    "pcms_server_drain": (_I, [_P, _D]),
+    "pcms_server_now": (_D, [_P]),
+    "pcms_server_memory": (_I, [_P, _P, _P, _P]),
+    "pcms_server_destroy": (None, [_P]),
     "pcms_trace_enable": (_I, [_I]),
     "pcms_trace_count": (_I, []),
     "pcms_trace_get": (_I, [_I, ctypes.c_char_p, _I, _P, _P]),
@@ -295,5 +322,89 @@ class Mesh:
         try:
             if self.handle and torch.cuda.is_available():
                 self.destroy()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop (pcms_server_*). Tensors referenced by a submitted
+    request are kept alive until the request completes."""
+
+    def __init__(self, n_slots=8, mem_cap_bytes=40 << 30):
+        h = ctypes.c_void_p()
+        _check(lib().pcms_server_create(int(n_slots), int(mem_cap_bytes), ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def now(self) -> float:
+        return float(lib().pcms_server_now(self.handle))
+
+    def submit_mls(self, src, tgt, fields, out, degree, radius, precision="mixed",
+                   weight="wendland_c2", min_neighbors=0, map_key=-1, reuse=False, bytes_hint=0):
+        r = Request()
+        r.kind = REQ_MLS
+        r.dim = src.shape[0]
+        r.basis_degree = int(degree)
+        r.radius = float(radius)
+        r.opts = make_opts(precision, weight, 0.0, min_neighbors)
+        r.src_pts, r.n_src = src.data_ptr(), src.shape[1]
+        r.tgt_pts, r.n_tgt = tgt.data_ptr(), tgt.shape[1]
+        r.fields, r.n_fields = fields.data_ptr(), fields.shape[0]
+        r.out = out.data_ptr()
+        r.map_key = int(map_key)
+        r.reuse_map = 1 if reuse else 0
+        r.bytes_hint = int(bytes_hint)
+        return self._submit(r, (src, tgt, fields, out))
+
+    def submit_mesh(self, xy, tri, pts, field, values, elem, bytes_hint=0):
+        r = Request()
+        r.kind = REQ_MESH
+        r.src_pts, r.n_src = xy.data_ptr(), xy.shape[1]
+        r.tri, r.n_tri = tri.data_ptr(), tri.shape[1]
+        r.tgt_pts, r.n_tgt = pts.data_ptr(), pts.shape[1]
+        r.fields = field.data_ptr() if field is not None else None
+        r.out = values.data_ptr() if values is not None else None
+        r.elem_ids = elem.data_ptr()
+        r.bytes_hint = int(bytes_hint)
+        return self._submit(r, (xy, tri, pts, field, values, elem))
+
+    def _submit(self, r, keep):
+        t = ctypes.c_int64()
+        _check(lib().pcms_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))
+        self._keep[t.value] = keep
+        return t.value
+
+    def poll(self, max_results=256, timeout_s=0.0):
+        buf = (RequestResult * max_results)()
+        n = ctypes.c_int()
+        _check(lib().pcms_server_poll(self.handle, buf, max_results, float(timeout_s),
+                                      ctypes.byref(n)))
+        out = []
+        for i in range(n.value):
+            x = buf[i]
+            self._keep.pop(x.ticket, None)
+            out.append({"ticket": x.ticket, "status": x.status, "t_submit": x.t_submit,
+                        "t_start": x.t_start, "t_end": x.t_end, "bytes": x.bytes_reserved,
+                        "cached": bool(x.used_cached_map)})
+        return out
+
+    def drain(self, timeout_s=600.0):
+        _check(lib().pcms_server_drain(self.handle, float(timeout_s)))
+
+    def memory(self):
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().pcms_server_memory(self.handle, ctypes.byref(a), ctypes.byref(b),
+                                        ctypes.byref(c)))
+        return {"in_use": a.value, "peak": b.value, "cached_maps": c.value}
+
+    def close(self):
+        if self.handle:
+            lib().pcms_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass

@@ -15,10 +15,9 @@ TOL_MIXED = 2e-5
 
 
 def normwise_err(got, ref, mask=None):
-    got = np.asarray(got, dtype=np.float64)
-    ref = np.asarray(ref, dtype=np.float64)
-    if got.ndim == 1:
-        got, ref = got[None], ref[None]
+    got = np.atleast_2d(np.asarray(got, dtype=np.float64))
+    ref = np.atleast_2d(np.asarray(ref, dtype=np.float64))
+    assert got.shape == ref.shape, (got.shape, ref.shape)
     if mask is not None:
         got, ref = got[:, mask], ref[:, mask]
     if ref.size == 0:

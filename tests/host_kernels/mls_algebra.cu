@@ -11,12 +11,18 @@ static int run(int kind, int n, const double* dx, const double* b, double inv_r,
     constexpr int NM = mono_count(DIM, 2 * DEG);
     constexpr int M = mono_count(DIM, DEG);
     constexpr int NACC = MODE == MODE_FUSED ? NM + M : NM;
-    double acc[NACC];
-    for (int i = 0; i < NACC; i++) acc[i] = 0.0;
+    double acc[NACC], cmp[NACC];
+    for (int i = 0; i < NACC; i++) acc[i] = cmp[i] = 0.0;
     for (int i = 0; i < n; i++)
-        accumulate<DIM, DEG, MODE, double, NACC>(acc, dx + 3 * i, b ? b[i] : 0.0, kind, inv_r);
+        accumulate<DIM, DEG, MODE, double, NACC>(acc, cmp, dx + 3 * i, b ? b[i] : 0.0, kind, inv_r);
     for (int i = 0; i < NACC; i++) mom_out[i] = acc[i];
-    return solve_moments<DIM, DEG, MODE>(acc, lambda, tau, out) ? 1 : 0;
+    double y[M], c0 = 0.0, amp = 0.0;
+    const bool ok = solve_moments<DIM, DEG, MODE>(acc, lambda, tau, y, &c0, &amp);
+    if (MODE == MODE_FUSED) out[0] = c0;
+    else
+        for (int k = 0; k < M; k++) out[k] = y[k];
+    out[M] = amp;
+    return ok ? 1 : 0;
 }
 
 template <int DIM, int DEG>

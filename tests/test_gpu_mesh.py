@@ -71,8 +71,9 @@ def test_linear_field_exact_and_orientation_independent(P):
     np.testing.assert_allclose(host(v), 1.5 - 2.0 * pts[0] + 0.25 * pts[1], rtol=0, atol=1e-13)
     # clockwise copies of every triangle: same ids, same classification
     tri_cw = np.ascontiguousarray(tri[[0, 2, 1]])
-    e1, d1, _ = (host(x) for x in P.Mesh(cu(xy), cu(tri_cw)).locate_interp(cu(pts)))
-    e0, d0, _ = (host(x) for x in mesh.locate_interp(cu(pts)))
+    e1, d1, _ = P.Mesh(cu(xy), cu(tri_cw)).locate_interp(cu(pts))
+    e0, d0, _ = mesh.locate_interp(cu(pts))
+    e0, d0, e1, d1 = host(e0), host(d0), host(e1), host(d1)
     assert np.array_equal(e0, e1) and np.array_equal(d0, d1)
 
 

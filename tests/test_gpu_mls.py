@@ -59,12 +59,13 @@ def test_neighbor_lists_bit_exact(P, dim, prec, min_nb):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_neighbor_selection_exact_at_the_radius(P, prec):
     """Sources exactly at distance r (dyadic) are excluded; one ulp inside is included."""
-    r = 0.0625
+    r = 5.0 / 128          # a 3-4-5 triangle with dyadic legs: 3/128, 4/128
     g = (np.arange(8) + 0.5) / 8.0
     tx, ty = np.meshgrid(g, g)
     tgt = np.stack([tx.ravel(), ty.ravel()])
-    offs = [(r, 0.0), (-r, 0.0), (0.0, r), (0.0, -r), (0.0375, 0.05),
-            (np.nextafter(r, 0), 0.0), (0.0, -np.nextafter(r, 0)), (0.0375, np.nextafter(0.05, 0))]
+    a, b = 3.0 / 128, 4.0 / 128
+    offs = [(r, 0.0), (-r, 0.0), (0.0, r), (0.0, -r), (a, b),
+            (np.nextafter(r, 0), 0.0), (0.0, -np.nextafter(r, 0)), (a, np.nextafter(b, 0))]
     src = np.concatenate([tgt + np.array(o)[:, None] for o in offs], axis=1)
     m = P.create_map(cu(src), cu(tgt), 0, r, precision=prec)
     off, cols, *_ = (host(x) for x in m.export())
@@ -204,7 +205,7 @@ def test_strict_mode_reports_underdetermined(P):
     o = oracle.mls(src, tgt, np.ones(300), 2, 0.05)
     assert np.array_equal(st, o["status"])
     assert m.info()["n_underdetermined"] == int((o["status"] == 1).sum()) > 0
-    out = host(m.apply(cu(np.ones(300))))
+    out = host(m.apply(cu(np.ones((1, 300)))))
     assert np.isnan(out[0, o["status"] != 0]).all()
 
 
@@ -255,3 +256,43 @@ def test_ragged_tile_sizes(P):
         o = oracle.mls(src, tgt, src[0], 1, 0.05)
         assert np.array_equal(host(st), o["status"])
         assert normwise_err(host(out), o["values"], o["status"] == 0) <= TOL_FP64
+
+
+# ------------------------------------------------------------------ full-size, sampled
+def _sample(n, k, seed):
+    return np.sort(np.random.default_rng(seed).choice(n, k, replace=False))
+
+
+def test_full_size_mls2d_gaussian_mixture_sampled(P):
+    """4M Gaussian-mixture sources -> 4M targets, quadratic, r = 0.01, min 10 neighbours,
+    mixed precision one-shot transfer: a seeded sample of targets against the oracle."""
+    c = W.mls_2d_gaussian()
+    f32 = c.fields.astype(np.float32)
+    out, st = P.mls_transfer(cu(c.src), cu(c.tgt), cu(f32), c.degree, c.radius,
+                             precision="mixed", min_neighbors=c.min_neighbors)
+    out, st = host(out), host(st)
+    idx = _sample(c.tgt.shape[1], 400, 31)
+    o = oracle.mls(c.src, c.tgt[:, idx], f32.astype(np.float64), c.degree, c.radius,
+                   min_neighbors=c.min_neighbors, mode="grid")
+    assert np.array_equal(st[idx], o["status"])
+    assert normwise_err(out[:, idx], o["values"], o["status"] == 0) <= TOL_MIXED
+    assert (st == 0).all()
+
+
+def test_full_size_mls3d_sixteen_fields_sampled(P):
+    """8M slab sources -> 8M targets, quadratic, r = 0.012, 16 fields: operator + apply."""
+    c = W.mls_3d_slab()
+    m = P.create_map(cu(c.src), cu(c.tgt), c.degree, c.radius, precision="mixed")
+    out = host(m.apply(cu(c.fields)))
+    *_, st, _ = (host(x) for x in m.export())
+    idx = _sample(c.tgt.shape[1], 2000, 32)
+    o = oracle.mls(c.src, c.tgt[:, idx], c.fields.astype(np.float64), c.degree, c.radius,
+                   mode="grid")
+    assert np.array_equal(st[idx], o["status"])
+    assert normwise_err(out[:, idx], o["values"], o["status"] == 0) <= TOL_MIXED
+    # neighbour lists of the sampled targets, bit-exact
+    off, cols, *_ = (host(x) for x in m.export())
+    o_off, o_cols, _ = oracle.neighbors(c.src, c.tgt[:, idx], c.radius, degree=2, mode="grid")
+    for k, i in enumerate(idx):
+        assert np.array_equal(np.sort(cols[off[i]:off[i + 1]]), o_cols[o_off[k]:o_off[k + 1]])
+    m.destroy()

@@ -1,0 +1,88 @@
+"""Serving: each request's result is the same alone and in the concurrent mix (within the
+stated tolerances), the memory cap is respected, and oversized requests are refused."""
+import numpy as np
+import pytest
+
+from paper_2510_18838_gb300 import workloads as W
+from tests._helpers import TOL_FP64, TOL_MIXED, need_gpu, normwise_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = need_gpu()
+    from paper_2510_18838_gb300 import build, pcms, serve
+    build.build()
+    return torch, pcms, serve
+
+
+def _alone(pcms, d):
+    r, t = d.req, d.tensors
+    if r.kind == "mesh":
+        mesh = pcms.Mesh(t["xy"], t["tri"])
+        e, _, v = mesh.locate_interp(t["pts"], t["field"], with_dim=False)
+        return e.cpu().numpy(), v.cpu().numpy()
+    if r.n_fields <= 2:
+        out, _ = pcms.mls_transfer(t["src"], t["tgt"], t["fields"], r.degree, r.radius,
+                                   precision="mixed", with_status=False)
+    else:
+        m = pcms.create_map(t["src"], t["tgt"], r.degree, r.radius, precision="mixed")
+        out = m.apply(t["fields"])
+        m.destroy()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("n_slots", [1, 6])
+def test_alone_equals_in_the_mix(env, n_slots):
+    torch, pcms, serve = env
+    reqs = W.request_stream(n_req=48, seed=77, pts_hi=60000, max_pts=60000)
+    assert {r.kind for r in reqs} == {"mls", "mesh"}
+    assert any(r.reuse_of >= 0 for r in reqs)
+    dreqs = serve.materialize(reqs, torch.device("cuda", 0))
+    stats = serve.run_served(dreqs, n_slots=n_slots, mem_cap=4 << 30)
+    assert stats["failed"] == 0
+    assert stats["peak_bytes"] <= 4 << 30
+    for d in dreqs:
+        r, t = d.req, d.tensors
+        if r.kind == "mesh":
+            e_mix, v_mix = t["elem"].cpu().numpy(), t["values"].cpu().numpy()
+            e_al, v_al = _alone(pcms, d)
+            assert np.array_equal(e_mix, e_al)
+            inside = e_al >= 0
+            assert normwise_err(v_mix, v_al, inside) <= TOL_FP64
+        else:
+            mix = t["out"].cpu().numpy()
+            al = _alone(pcms, d)
+            ok = np.isfinite(al).all(axis=0)
+            assert np.array_equal(np.isfinite(mix).all(axis=0), ok)
+            assert normwise_err(mix, al, ok) <= TOL_MIXED, r
+
+
+def test_cache_reuse_and_capacity(env):
+    torch, pcms, serve = env
+    dev = torch.device("cuda", 0)
+    src = torch.rand((2, 20000), dtype=torch.float64, device=dev)
+    tgt = torch.rand((2, 5000), dtype=torch.float64, device=dev)
+    f1 = torch.rand((3, 20000), dtype=torch.float32, device=dev)
+    f2 = torch.rand((5, 20000), dtype=torch.float32, device=dev)
+    o1 = torch.empty((3, 5000), dtype=torch.float32, device=dev)
+    o2 = torch.empty((5, 5000), dtype=torch.float32, device=dev)
+    s = pcms.Server(n_slots=2, mem_cap_bytes=2 << 30)
+    s.submit_mls(src, tgt, f1, o1, 2, 0.03, map_key=7)
+    s.submit_mls(src, tgt, f2, o2, 2, 0.03, map_key=7, reuse=True)
+    s.drain(120)
+    res = sorted(s.poll(8), key=lambda x: x["ticket"])
+    assert [x["status"] for x in res] == [pcms.OK, pcms.OK]
+    assert res[1]["cached"] and not res[0]["cached"]
+    assert s.memory()["cached_maps"] == 1
+    m = pcms.create_map(src, tgt, 2, 0.03, precision="mixed")
+    ref = m.apply(f2).cpu().numpy()
+    assert normwise_err(o2.cpu().numpy(), ref) <= TOL_MIXED
+    s.close()
+    # a request whose estimate exceeds the cap is refused, the server keeps running
+    s = pcms.Server(n_slots=1, mem_cap_bytes=1 << 20)
+    s.submit_mls(src, tgt, f1, o1, 2, 0.03)
+    s.drain(60)
+    assert s.poll(4)[0]["status"] == pcms.CAPACITY
+    s.close()

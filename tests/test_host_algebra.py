@@ -91,13 +91,17 @@ def test_operator_weights_match_numpy(hk, dim, deg):
     m = A.shape[1]
     nm = len([e for e in itertools.product(range(2 * deg + 1), repeat=dim) if sum(e) <= 2 * deg])
     mom = np.zeros(nm)
-    y = np.zeros(m)
+    out = np.zeros(m + 1)
     ok = hk.hk_mls(dim, deg, 0, 0, len(dx), _p(np.ascontiguousarray(dx)), None, 1.0 / r, 0.0,
-                   1e-14, _p(mom), _p(y))
+                   1e-14, _p(mom), _p(out))
     assert ok == 1
+    y, amp = out[:m], out[m]
     G = (A * w[:, None]).T @ A
     y_ref = np.linalg.solve(G, np.eye(m)[0])
     np.testing.assert_allclose(y, y_ref, rtol=1e-10, atol=1e-12 * np.abs(y_ref).max())
+    amp_ref = np.sqrt(G[0, 0]) * np.sum(np.abs(y_ref) * np.sqrt(np.diag(G)))
+    assert amp == pytest.approx(amp_ref, rel=1e-10)
+    assert amp >= 1.0 - 1e-12          # amp >= G_00 * y_0 = G_00 (G^-1)_00 >= 1
     # the shape functions w a^T y reproduce every basis monomial (moment conditions)
     N = w * (A @ y)
     np.testing.assert_allclose(N @ A, np.eye(m)[0], atol=1e-12)
@@ -111,7 +115,7 @@ def test_one_shot_value_matches_weighted_lstsq(hk, dim, deg, lam):
     b = np.cos(7 * u[:, 0]) + u[:, -1] ** 2
     nm = len([e for e in itertools.product(range(2 * deg + 1), repeat=dim) if sum(e) <= 2 * deg])
     mom = np.zeros(nm + m)
-    c0 = np.zeros(1)
+    c0 = np.zeros(m + 1)
     ok = hk.hk_mls(dim, deg, 1, 0, len(dx), _p(np.ascontiguousarray(dx)), _p(b), 1.0 / r, lam,
                    1e-14, _p(mom), _p(c0))
     assert ok == 1
@@ -128,7 +132,7 @@ def test_guard_flags_collinear_points(hk):
     dx[:, 0] = 0.05 * t
     dx[:, 1] = 0.05 * 0.5 * t
     mom = np.zeros(15)
-    y = np.zeros(6)
+    y = np.zeros(7)
     assert hk.hk_mls(2, 1, 0, 0, 30, _p(dx), None, 20.0, 0.0, 1e-14, _p(mom), _p(y)) == 0
     assert hk.hk_mls(2, 2, 0, 0, 30, _p(dx), None, 20.0, 0.0, 1e-14, _p(mom), _p(y)) == 0
     assert hk.hk_mls(2, 0, 0, 0, 30, _p(dx), None, 20.0, 0.0, 1e-14, _p(mom), _p(y)) == 1
