@@ -24,19 +24,37 @@ int blocks_for(int64_t n, int threads, int per_sm = 32) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * per_sm));
 }
 
-template <typename T>
-__global__ void k_fields_to_sorted(const T* __restrict__ f, int nf, int fp, int64_t ns,
-                                   const int32_t* __restrict__ inv, T* __restrict__ fs) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ns;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        T* row = fs + (int64_t)inv[i] * fp;
-        for (int k = 0; k < fp; k++) row[k] = k < nf ? f[(int64_t)k * ns + i] : T(0);
-    }
-}
-
 template <typename T> struct Vec;
 template <> struct Vec<float> { using type = float4; static constexpr int W = 4; };
 template <> struct Vec<double> { using type = double2; static constexpr int W = 2; };
+
+// caller-order fields -> sorted, interleaved rows; fp is 1 or a multiple of the vector width,
+// each row is written with vector stores
+template <typename T>
+__global__ void k_fields_to_sorted(const T* __restrict__ f, int nf, int fp, int64_t ns,
+                                   const int32_t* __restrict__ inv, T* __restrict__ fs) {
+    using V = typename Vec<T>::type;
+    constexpr int W = Vec<T>::W;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ns;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        T* row = fs + (int64_t)inv[i] * fp;
+        if (fp == 1) {
+            row[0] = f[i];
+            continue;
+        }
+        for (int v = 0; v < fp / W; v++) {
+            T tmp[W];
+#pragma unroll
+            for (int c = 0; c < W; c++) {
+                const int k = v * W + c;
+                tmp[c] = k < nf ? f[(int64_t)k * ns + i] : T(0);
+            }
+            V x;
+            memcpy(&x, tmp, sizeof(V));
+            reinterpret_cast<V*>(row)[v] = x;
+        }
+    }
+}
 
 template <typename V, typename T>
 __device__ __forceinline__ void fma_vec(V& acc, T a, const V& x);
@@ -57,13 +75,28 @@ __device__ __forceinline__ void shfl_add(double2& v, int o) {
     v.x += __shfl_xor_sync(0xffffffffu, v.x, o); v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
 }
 
-// vectorised: NV vectors of W elements per nnz (fp = NV*W)
+template <typename T>
+__device__ __forceinline__ T quiet_nan();
+template <>
+__device__ __forceinline__ float quiet_nan<float>() { return __int_as_float(0x7fc00000); }
+template <>
+__device__ __forceinline__ double quiet_nan<double>() {
+    return __longlong_as_double(0x7ff8000000000000LL);
+}
+
+// One warp per target row; lanes = 32/NV slots x NV vectors of W fields (fp = NV*W).
+// Each chunk of 32 nonzeros is read with one coalesced load of (col, val) per lane and
+// redistributed by shuffles, so every lane has NV independent field-row gathers in flight.
+// Rows whose target status is not OK produce NaN.
 template <typename T, int NV>
 __global__ void __launch_bounds__(256) k_spmm_vec(int64_t nt, const int64_t* __restrict__ off,
                                                   const int32_t* __restrict__ cols,
                                                   const T* __restrict__ vals,
-                                                  const T* __restrict__ fs, T* __restrict__ stage) {
+                                                  const T* __restrict__ fs,
+                                                  const int8_t* __restrict__ status,
+                                                  T* __restrict__ stage) {
     using V = typename Vec<T>::type;
+    constexpr int W = Vec<T>::W;
     constexpr int SLOTS = 32 / NV;
     const int lane = threadIdx.x & 31;
     const int slot = lane / NV, vi = lane % NV;
@@ -72,45 +105,88 @@ __global__ void __launch_bounds__(256) k_spmm_vec(int64_t nt, const int64_t* __r
          t += nwarps) {
         const int64_t a = off[t], b = off[t + 1];
         V acc{};
-        for (int64_t e = a + slot; e < b; e += SLOTS) {
-            const int32_t j = __ldg(cols + e);
-            const T w = __ldg(vals + e);
-            const V x = *reinterpret_cast<const V*>(fs + (int64_t)j * (NV * Vec<T>::W) + vi * Vec<T>::W);
-            fma_vec<V, T>(acc, w, x);
+        for (int64_t c0 = a; c0 < b; c0 += 32) {
+            const int64_t e = c0 + lane;
+            const int32_t jl = e < b ? __ldg(cols + e) : 0;
+            const T wl = e < b ? __ldg(vals + e) : T(0);
+            V x[NV];
+#pragma unroll
+            for (int s = 0; s < NV; s++) {
+                const int k = s * SLOTS + slot;
+                const int32_t j = __shfl_sync(0xffffffffu, jl, k);
+                if (c0 + k < b) x[s] = *reinterpret_cast<const V*>(fs + (int64_t)j * (NV * W) + vi * W);
+                else x[s] = V{};
+            }
+#pragma unroll
+            for (int s = 0; s < NV; s++) {
+                const T w = __shfl_sync(0xffffffffu, wl, s * SLOTS + slot);
+                fma_vec<V, T>(acc, w, x[s]);
+            }
         }
 #pragma unroll
         for (int o = NV; o < 32; o <<= 1) shfl_add(acc, o);
-        if (slot == 0)
-            *reinterpret_cast<V*>(stage + t * (NV * Vec<T>::W) + vi * Vec<T>::W) = acc;
+        if (slot == 0) {
+            if (status[t] != PCMS_TARGET_OK) {
+                const T nan = quiet_nan<T>();
+                const T nan4[4] = {nan, nan, nan, nan};
+                memcpy(&acc, nan4, sizeof(V));
+            }
+            *reinterpret_cast<V*>(stage + t * (NV * W) + vi * W) = acc;
+        }
     }
 }
 
-// scalar: one field
+// one field: lanes over nonzeros, two chunks of 32 in flight
 template <typename T>
 __global__ void __launch_bounds__(256) k_spmm_1(int64_t nt, const int64_t* __restrict__ off,
                                                 const int32_t* __restrict__ cols,
                                                 const T* __restrict__ vals,
-                                                const T* __restrict__ fs, T* __restrict__ stage) {
+                                                const T* __restrict__ fs,
+                                                const int8_t* __restrict__ status,
+                                                T* __restrict__ stage) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < nt;
          t += nwarps) {
         const int64_t a = off[t], b = off[t + 1];
         T acc = T(0);
-        for (int64_t e = a + lane; e < b; e += 32) acc += __ldg(vals + e) * fs[__ldg(cols + e)];
+        for (int64_t e = a + lane; e < b; e += 64) {
+            const bool two = e + 32 < b;
+            const int32_t j0 = __ldg(cols + e);
+            const int32_t j1 = two ? __ldg(cols + e + 32) : 0;
+            const T w0 = __ldg(vals + e);
+            const T w1 = two ? __ldg(vals + e + 32) : T(0);
+            const T x0 = fs[j0];
+            const T x1 = two ? fs[j1] : T(0);
+            acc += w0 * x0;
+            acc += w1 * x1;
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) stage[t] = acc;
+        if (lane == 0) stage[t] = status[t] == PCMS_TARGET_OK ? acc : quiet_nan<T>();
     }
 }
 
 template <typename T>
 __global__ void k_stage_to_caller(const T* __restrict__ stage, int fp, int nf, int64_t nt,
                                   const int32_t* __restrict__ inv_t, T* __restrict__ out) {
+    using V = typename Vec<T>::type;
+    constexpr int W = Vec<T>::W;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt;
          i += (int64_t)gridDim.x * blockDim.x) {
         const T* row = stage + (int64_t)inv_t[i] * fp;
-        for (int f = 0; f < nf; f++) out[(int64_t)f * nt + i] = row[f];
+        if (fp == 1) {
+            out[i] = row[0];
+            continue;
+        }
+        for (int v = 0; v * W < nf; v++) {
+            const V x = reinterpret_cast<const V*>(row)[v];
+            T tmp[W];
+            memcpy(tmp, &x, sizeof(V));
+#pragma unroll
+            for (int c = 0; c < W; c++)
+                if (v * W + c < nf) out[(int64_t)(v * W + c) * nt + i] = tmp[c];
+        }
     }
 }
 
@@ -133,13 +209,14 @@ void apply_t(MapImpl& M, const T* fields, int nf, T* out, cudaStream_t s) {
         const int64_t* off = M.offsets.as<int64_t>();
         const int32_t* cols = M.cols.as<int32_t>();
         const T* vals = M.vals.as<T>();
+        const int8_t* st = M.status.as<int8_t>();
         int blocks = blocks_for(nt * 32, 256, 16);
         int nv = fp / W;
-        if (fp == 1) k_spmm_1<T><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs.as<T>(), stage.as<T>());
-        else if (nv == 1) k_spmm_vec<T, 1><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs.as<T>(), stage.as<T>());
-        else if (nv == 2) k_spmm_vec<T, 2><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs.as<T>(), stage.as<T>());
-        else if (nv == 4) k_spmm_vec<T, 4><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs.as<T>(), stage.as<T>());
-        else if (nv == 8) k_spmm_vec<T, 8><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs.as<T>(), stage.as<T>());
+        if (fp == 1) k_spmm_1<T><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs.as<T>(), st, stage.as<T>());
+        else if (nv == 1) k_spmm_vec<T, 1><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs.as<T>(), st, stage.as<T>());
+        else if (nv == 2) k_spmm_vec<T, 2><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs.as<T>(), st, stage.as<T>());
+        else if (nv == 4) k_spmm_vec<T, 4><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs.as<T>(), st, stage.as<T>());
+        else if (nv == 8) k_spmm_vec<T, 8><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs.as<T>(), st, stage.as<T>());
         else {
             fail(PCMS_ERR_INVALID_ARG, "internal: field padding");
         }

@@ -149,6 +149,8 @@ void solve_tiers(int dim, int deg, int mode, bool mixed, int G, const AsmArgs& a
     int32_t cnt[2] = {0, 0};
     PCMS_CU(cudaMemcpyAsync(cnt, n2, sizeof(cnt), cudaMemcpyDeviceToHost, s));
     PCMS_CU(cudaStreamSynchronize(s));
+    trace_count("mls_tier1_targets", nt - cnt[0] - cnt[1]);
+    trace_count("mls_tier2_targets", cnt[0]);
     if (cnt[0] > 0) {
         DBuf mom2(sizeof(double) * np * cnt[0], s);
         AsmArgs a2 = a;
@@ -170,6 +172,7 @@ void solve_tiers(int dim, int deg, int mode, bool mixed, int G, const AsmArgs& a
         PCMS_CU(cudaMemcpyAsync(&cnt[1], n3, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         PCMS_CU(cudaStreamSynchronize(s));
     }
+    trace_count("mls_tier3_targets", cnt[1]);
     if (cnt[1] > 0) {
         DBuf mom3(sizeof(double) * np * cnt[1], s);
         AsmArgs a3 = a;

@@ -83,6 +83,12 @@ TraceScope::~TraceScope() {
     g_pending.push_back(Pending{name_, a_, b});
 }
 
+void trace_count(const char* name, int64_t n) {
+    if (!trace_on()) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_stats[std::string("count:") + name].launches += n;
+}
+
 void trace_enable(int on) {
     std::lock_guard<std::mutex> lk(g_mu);
     drain_locked();

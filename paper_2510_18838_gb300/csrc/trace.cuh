@@ -10,6 +10,8 @@ namespace pcms {
 
 bool trace_on();
 void trace_enable(int on);
+// record a count (not a launch) under "count:<name>" while tracing is on
+void trace_count(const char* name, int64_t n);
 int trace_count();
 int trace_get(int i, char* name, int name_len, int64_t* launches, double* total_ms);
 

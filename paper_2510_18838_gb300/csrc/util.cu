@@ -298,7 +298,9 @@ template void exclusive_scan<int32_t>(const int32_t*, int32_t*, int64_t, cudaStr
 template void exclusive_scan<int64_t>(const int32_t*, int64_t*, int64_t, cudaStream_t);
 
 // ------------------------------------------------------------------------------------
-// counting sort by cell: key + rank (warp-aggregated atomics), scan, scatter
+// binning points into cells: cell key per point, then a stable LSD radix sort of
+// (key, caller index) with 8-bit digits. Stability makes the order inside a cell the caller's
+// index order, so everything computed from the sorted points is bitwise reproducible.
 // ------------------------------------------------------------------------------------
 __device__ __forceinline__ int cell_of(double x, double lo, double inv_h, int n) {
     double f = floor((x - lo) * inv_h);
@@ -307,40 +309,96 @@ __device__ __forceinline__ int cell_of(double x, double lo, double inv_h, int n)
 }
 
 __global__ void k_cell_keys(Grid g, const double* __restrict__ pts, int64_t n,
-                            int32_t* __restrict__ key, int32_t* __restrict__ rank,
+                            uint32_t* __restrict__ key, uint32_t* __restrict__ idx,
                             int32_t* __restrict__ count) {
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n;
-         base += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = base + threadIdx.x;
-        bool valid = i < n;
-        unsigned active = __ballot_sync(0xffffffffu, valid);
-        if (!valid) continue;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
         int c = cell_of(pts[i], g.lo[0], g.inv_h, g.n[0]);
         if (g.dim >= 2) c += g.n[0] * cell_of(pts[n + i], g.lo[1], g.inv_h, g.n[1]);
         if (g.dim == 3)
             c += g.n[0] * g.n[1] * cell_of(pts[2 * n + i], g.lo[2], g.inv_h, g.n[2]);
-        unsigned peers = __match_any_sync(active, c);
-        int leader = __ffs(peers) - 1;
-        int b = 0;
-        if (lane == leader) b = atomicAdd(&count[c], __popc(peers));
-        b = __shfl_sync(peers, b, leader);
-        key[i] = c;
-        rank[i] = b + __popc(peers & lt);
+        key[i] = (uint32_t)c;
+        idx[i] = (uint32_t)i;
+        atomicAdd(&count[c], 1);
     }
 }
 
-__global__ void k_scatter(int dim, Grid g, const double* __restrict__ pts, int64_t n,
-                          const int32_t* __restrict__ key, const int32_t* __restrict__ rank,
-                          const int32_t* __restrict__ start, int32_t* __restrict__ perm,
-                          int32_t* __restrict__ inv, double* __restrict__ x64,
-                          float4* __restrict__ hl0, float2* __restrict__ hl1) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int pos = start[key[i]] + rank[i];
+constexpr int RS_THREADS = 256;
+constexpr int RS_ROUNDS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
+
+// per-tile digit histogram, digit-major: hist[d * ntiles + tile]
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t* __restrict__ key,
+                                                        int64_t n, int shift, int64_t ntiles,
+                                                        int32_t* __restrict__ hist) {
+    __shared__ int32_t cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int r = 0; r < RS_ROUNDS; r++) {
+        const int64_t i = base + r * RS_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[(key[i] >> shift) & 255u], 1);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// stable scatter: items of a tile are placed in index order within each digit
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* __restrict__ kin,
+                                                           const uint32_t* __restrict__ vin,
+                                                           int64_t n, int shift, int64_t ntiles,
+                                                           const int32_t* __restrict__ off,
+                                                           uint32_t* __restrict__ kout,
+                                                           uint32_t* __restrict__ vout) {
+    __shared__ int32_t base[256];
+    __shared__ int32_t tot[256];
+    __shared__ int32_t wcnt[RS_THREADS / 32][256];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    base[tid] = off[(int64_t)tid * ntiles + blockIdx.x];
+    const int64_t t0 = (int64_t)blockIdx.x * RS_TILE;
+    for (int r = 0; r < RS_ROUNDS; r++) {
+#pragma unroll
+        for (int k = 0; k < RS_THREADS / 32; k++) wcnt[k][tid] = 0;
+        __syncthreads();
+        const int64_t i = t0 + r * RS_THREADS + tid;
+        const bool valid = i < n;
+        const uint32_t kv = valid ? kin[i] : 0u;
+        const int d = valid ? (int)((kv >> shift) & 255u) : 256;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & lt);
+        if (valid && rank == 0) wcnt[w][d] = __popc(peers);
+        __syncthreads();
+        {
+            int run = 0;
+#pragma unroll
+            for (int k = 0; k < RS_THREADS / 32; k++) {
+                const int c = wcnt[k][tid];
+                wcnt[k][tid] = run;
+                run += c;
+            }
+            tot[tid] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            const int pos = base[d] + wcnt[w][d] + rank;
+            kout[pos] = kv;
+            vout[pos] = vin[i];
+        }
+        __syncthreads();
+        base[tid] += tot[tid];
+    }
+}
+
+__global__ void k_gather_sorted(int dim, Grid g, const double* __restrict__ pts, int64_t n,
+                                const uint32_t* __restrict__ order, int32_t* __restrict__ perm,
+                                int32_t* __restrict__ inv, double* __restrict__ x64,
+                                float4* __restrict__ hl0, float2* __restrict__ hl1) {
+    for (int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pos < n;
+         pos += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = order[pos];
         perm[pos] = (int32_t)i;
-        inv[i] = pos;
+        inv[i] = (int32_t)pos;
         double x[3] = {0, 0, 0};
         for (int d = 0; d < dim; d++) {
             x[d] = pts[d * n + i];
@@ -367,17 +425,21 @@ void sort_points(const Grid& g, const double* pts, int64_t n, bool with_start, b
                  SortedPoints& out, cudaStream_t s) {
     out.dim = g.dim;
     out.n = n;
-    int dim = g.dim;
+    const int dim = g.dim;
+    const int64_t nn = std::max<int64_t>(n, 1);
     DBuf count(sizeof(int32_t) * (g.ncell + 1), s);
-    DBuf key(sizeof(int32_t) * std::max<int64_t>(n, 1), s);
-    DBuf rank(sizeof(int32_t) * std::max<int64_t>(n, 1), s);
+    DBuf kv(sizeof(uint32_t) * 4 * nn, s);   // key, idx, key', idx'
+    uint32_t* k0 = kv.as<uint32_t>();
+    uint32_t* v0 = k0 + nn;
+    uint32_t* k1 = v0 + nn;
+    uint32_t* v1 = k1 + nn;
     PCMS_CU(cudaMemsetAsync(count.p, 0, sizeof(int32_t) * (g.ncell + 1), s));
-    out.perm.alloc(sizeof(int32_t) * std::max<int64_t>(n, 1), s);
-    out.inv.alloc(sizeof(int32_t) * std::max<int64_t>(n, 1), s);
-    out.x64.alloc(sizeof(double) * dim * std::max<int64_t>(n, 1), s);
+    out.perm.alloc(sizeof(int32_t) * nn, s);
+    out.inv.alloc(sizeof(int32_t) * nn, s);
+    out.x64.alloc(sizeof(double) * dim * nn, s);
     if (with_hl) {
-        out.hl0.alloc(sizeof(float4) * std::max<int64_t>(n, 1), s);
-        if (dim == 3) out.hl1.alloc(sizeof(float2) * std::max<int64_t>(n, 1), s);
+        out.hl0.alloc(sizeof(float4) * nn, s);
+        if (dim == 3) out.hl1.alloc(sizeof(float2) * nn, s);
     }
     DBuf start_tmp;
     int32_t* start;
@@ -388,22 +450,41 @@ void sort_points(const Grid& g, const double* pts, int64_t n, bool with_start, b
         start_tmp.alloc(sizeof(int32_t) * (g.ncell + 1), s);
         start = start_tmp.as<int32_t>();
     }
-    int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8));
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8));
     if (n > 0) {
         PCMS_TRACE("grid_cell_keys", s);
-        k_cell_keys<<<blocks, 256, 0, s>>>(g, pts, n, key.as<int32_t>(), rank.as<int32_t>(),
-                                           count.as<int32_t>());
+        k_cell_keys<<<blocks, 256, 0, s>>>(g, pts, n, k0, v0, count.as<int32_t>());
     }
     PCMS_LAUNCH_CHECK("cell_keys");
     exclusive_scan<int32_t>(count.as<int32_t>(), start, g.ncell, s);
     if (n > 0) {
-        PCMS_TRACE("grid_scatter", s);
-        k_scatter<<<blocks, 256, 0, s>>>(dim, g, pts, n, key.as<int32_t>(), rank.as<int32_t>(),
-                                         start, out.perm.as<int32_t>(), out.inv.as<int32_t>(),
-                                         out.x64.as<double>(), with_hl ? out.hl0.as<float4>() : nullptr,
-                                         (with_hl && dim == 3) ? out.hl1.as<float2>() : nullptr);
+        int bits = 1;
+        while (bits < 32 && ((int64_t)1 << bits) < g.ncell) bits++;
+        const int passes = (bits + 7) / 8;
+        const int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+        DBuf hist(sizeof(int32_t) * (256 * ntiles + 1), s);
+        for (int p = 0; p < passes; p++) {
+            {
+                PCMS_TRACE("grid_radix_hist", s);
+                k_rs_hist<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(k0, n, 8 * p, ntiles, hist.as<int32_t>());
+            }
+            exclusive_scan<int32_t>(hist.as<int32_t>(), hist.as<int32_t>(), 256 * ntiles, s);
+            {
+                PCMS_TRACE("grid_radix_scatter", s);
+                k_rs_scatter<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(k0, v0, n, 8 * p, ntiles,
+                                                                     hist.as<int32_t>(), k1, v1);
+            }
+            PCMS_LAUNCH_CHECK("radix");
+            std::swap(k0, k1);
+            std::swap(v0, v1);
+        }
+        PCMS_TRACE("grid_gather_sorted", s);
+        k_gather_sorted<<<blocks, 256, 0, s>>>(dim, g, pts, n, v0, out.perm.as<int32_t>(),
+                                               out.inv.as<int32_t>(), out.x64.as<double>(),
+                                               with_hl ? out.hl0.as<float4>() : nullptr,
+                                               (with_hl && dim == 3) ? out.hl1.as<float2>() : nullptr);
     }
-    PCMS_LAUNCH_CHECK("scatter");
+    PCMS_LAUNCH_CHECK("gather_sorted");
 }
 
 }  // namespace pcms

@@ -45,6 +45,45 @@ extern "C" int hk_mls(int dim, int deg, int fused, int kind, int n, const double
     return run_mode<3, 2>(fused, kind, n, dx, b, inv_r, lambda, tau, mom_out, out);
 }
 
+// FP32 accumulation (plain or compensated) of the same per-pair algebra, reduced in FP64,
+// then the FP64 solve: the arithmetic of precision tiers 1 and 2 of the mixed path
+template <int DIM, int DEG, bool COMP>
+static int run_f32(int kind, int n, const float* dx, const float* b, float inv_r, double lambda,
+                   double tau, double* out, int lanes) {
+    constexpr int NM = mono_count(DIM, 2 * DEG);
+    constexpr int M = mono_count(DIM, DEG);
+    constexpr int NACC = NM + M;
+    double tot[NACC];
+    for (int i = 0; i < NACC; i++) tot[i] = 0.0;
+    for (int l = 0; l < lanes; l++) {
+        float acc[NACC], cmp[NACC];
+        for (int i = 0; i < NACC; i++) acc[i] = cmp[i] = 0.f;
+        for (int i = l; i < n; i += lanes)
+            accumulate<DIM, DEG, MODE_FUSED, float, NACC, COMP>(acc, cmp, dx + 3 * i, b[i], kind, inv_r);
+        for (int i = 0; i < NACC; i++) tot[i] += (double)acc[i] - (double)cmp[i];
+    }
+    double y[M], c0 = 0.0, amp = 0.0;
+    const bool ok = solve_moments<DIM, DEG, MODE_FUSED>(tot, lambda, tau, y, &c0, &amp);
+    out[0] = c0;
+    out[1] = amp;
+    return ok ? 1 : 0;
+}
+
+extern "C" int hk_mls_f32(int dim, int deg, int comp, int kind, int n, const float* dx,
+                          const float* b, float inv_r, double lambda, double tau, double* out,
+                          int lanes) {
+#define HK_F32(D, K)                                                                         \
+    return comp ? run_f32<D, K, true>(kind, n, dx, b, inv_r, lambda, tau, out, lanes)        \
+                : run_f32<D, K, false>(kind, n, dx, b, inv_r, lambda, tau, out, lanes)
+    if (dim == 2) {
+        if (deg == 1) HK_F32(2, 1);
+        HK_F32(2, 2);
+    }
+    if (deg == 1) HK_F32(3, 1);
+    HK_F32(3, 2);
+#undef HK_F32
+}
+
 extern "C" int hk_mono(int dim, int p, int* e) {
     Exp3 x = mono_exp(dim, p);
     e[0] = x.e[0];

@@ -64,15 +64,22 @@ def test_neighbor_selection_exact_at_the_radius(P, prec):
     tx, ty = np.meshgrid(g, g)
     tgt = np.stack([tx.ravel(), ty.ravel()])
     a, b = 3.0 / 128, 4.0 / 128
-    offs = [(r, 0.0), (-r, 0.0), (0.0, r), (0.0, -r), (a, b),
-            (np.nextafter(r, 0), 0.0), (0.0, -np.nextafter(r, 0)), (a, np.nextafter(b, 0))]
-    src = np.concatenate([tgt + np.array(o)[:, None] for o in offs], axis=1)
+    on = [(r, 0.0), (-r, 0.0), (0.0, r), (0.0, -r), (a, b)]      # exactly at distance r
+    src = [tgt + np.array(o)[:, None] for o in on]
+    for o, ax in [((r, 0.0), 0), ((0.0, -r), 1), ((a, b), 1)]:  # one ulp inside
+        p = tgt + np.array(o)[:, None]
+        p[ax] = np.nextafter(p[ax], tgt[ax])
+        src.append(p)
+    src = np.concatenate(src, axis=1)
     m = P.create_map(cu(src), cu(tgt), 0, r, precision=prec)
     off, cols, *_ = (host(x) for x in m.export())
     o_off, o_cols, _ = oracle.neighbors(src, tgt, r, degree=0)
     for a, b in zip(rows_as_sets(off, cols), rows_as_sets(o_off, o_cols)):
         assert np.array_equal(a, b)
-    assert all(len(x) == 3 for x in rows_as_sets(off, cols))
+    nt = tgt.shape[1]
+    exact = set(range(5 * nt))        # the five sources per target at exactly distance r
+    assert not exact.intersection(np.asarray(cols).tolist())
+    assert all(2 <= len(x) <= 3 for x in rows_as_sets(off, cols))
 
 
 # ------------------------------------------------------------------ FP64 operator + values
