@@ -4,22 +4,25 @@
                     [--workload serve|transfer]
 
 Workloads (synthetic, seeded; shaped like the paper's field-transfer workloads):
-  transfer -- one step = the whole hot path over one batch:
-              (a) 2D mesh transfer: 512x512 jittered grid (524,288 triangles), search-grid
-                  build + localisation + barycentric interpolation of 1,000,000 points;
-              (b) 2D MLS, mixed precision, one-shot: 4M Gaussian-mixture sources -> 4M
-                  uniform targets, quadratic basis, Wendland C2, r = 0.01, min 10
-                  neighbours (radius doubling);
-              (c) 3D MLS, mixed precision: 8M sources (uniform + dense slab) -> 8M targets,
-                  quadratic basis, r = 0.012: operator build + apply of 16 fields.
-              value = target points mapped per second (1M + 4M + 8M per step).
-  serve    -- see paper_2510_18838_gb300/serve.py (continuous-batching request loop).
+  serve    (default) -- the headline: a stream of 2,000 transfer requests (Poisson arrivals;
+              target counts log-uniform in 1k..2M; 2D/3D MLS, linear or quadratic, 1..16
+              fields, 30% reusing an earlier request's operator; 2D mesh transfers on
+              jittered grids), inputs resident in HBM. One step = the whole stream served
+              by the library's continuous-batching server (16 slots, 40 GiB cap, mixed
+              precision), all requests available at once. value = target points / second.
+              Latency p50/p99 come from one open-loop pass with Poisson arrivals at 80% of
+              the measured capacity; the plain FP64 per-request form (one at a time, no
+              cache) is run on the same requests for comparison.
+  transfer -- one step = (a) 512x512 jittered mesh (524,288 tri): grid build + location +
+              interpolation of 1,000,000 points; (b) 2D MLS mixed one-shot 4M Gaussian-mixture
+              sources -> 4M targets, quadratic, r = 0.01, min 10 neighbours; (c) 3D MLS mixed
+              8M -> 8M, quadratic, r = 0.012: operator + 16-field apply. Always run once
+              (single stream) for the per-kernel breakdown and the roofline entry.
 
-Timing: W untimed warm-up steps; K timed steps, each bracketed by CUDA events on the
-stream the library launches on, with a 256 MiB L2-flushing write between steps (outside
-the events); barrier + synchronize on both sides; max over ranks. SM clocks and throttle
-reasons are sampled with nvidia-smi during the timed steps. Per-kernel times come from
-the library's own CUDA-event tracing on its launching stream.
+Timing: W untimed warm-up steps; K timed steps each bracketed by CUDA events with a
+synchronize on both sides and a 256 MiB L2-flushing write between steps; barrier and max
+over ranks for N > 1. SM clocks/throttle reasons are sampled with nvidia-smi during the
+timed steps. Per-kernel times are CUDA events the library records on its launching stream.
 """
 from __future__ import annotations
 
@@ -39,35 +42,36 @@ if ROOT not in sys.path:
 
 METRIC = ("target points mapped/sec (MLS + mesh interp) at ≤2e-5 rel err; "
           "p50/p99 request latency")
+SERVE_NAME = ("serving: Poisson stream of 2,000 transfer requests, points log-uniform 1k-2M, "
+              "2D/3D MLS linear/quadratic 1-16 fields (30% cached-map reuse) + 2D mesh "
+              "transfers, continuous batching 16 slots, 40 GiB cap, mixed precision")
+TRANSFER_NAME = ("transfer_mix: mesh 512x512 jittered (524,288 tri) 1M pts + MLS2D mixed "
+                 "4M->4M gauss8 quadratic r=0.01 minnb=10 + MLS3D mixed 8M->8M slab quadratic "
+                 "r=0.012 16 fields")
+
 
 # ------------------------------------------------------------------------------------
-# algorithmic work models (per selected pair / per point); see the design doc
+# algorithmic work models
 # ------------------------------------------------------------------------------------
-
-
 def mono_count(dim, deg):
     return math.comb(dim + deg, deg)
 
 
 def mls_pair_flops(dim, deg, fused_fields):
     """FP32 flops the weighted-moment formulation needs per selected pair: squared
-    distance, q, Wendland C2, scaled offsets, moments of degree <= 2k, and (one-shot mode)
-    the right-hand side for each field."""
+    distance, q, Wendland C2, scaled offsets, moments of degree <= 2k and, in one-shot mode,
+    the right-hand side of each field."""
     nm = mono_count(dim, 2 * deg)
     m = mono_count(dim, deg)
-    f = (2 * dim - 1) + 2 + 6 + dim + (2 * nm - 1)
-    f += fused_fields * (2 * m + 1)
-    return f
+    return (2 * dim - 1) + 2 + 6 + dim + (2 * nm - 1) + fused_fields * (2 * m + 1)
 
 
 def spmm_bytes(nnz, ns, nt, nf, elem=4):
-    """HBM bytes one apply launch must move at least: column index + value per nonzero,
-    every source field row once, every target output row once."""
+    """HBM bytes one apply must move at least: column + value per nonzero, each source's
+    field row once, each target's output row once."""
     return nnz * (4 + elem) + ns * nf * elem + nt * nf * elem
 
 
-# ------------------------------------------------------------------------------------
-# clocks
 # ------------------------------------------------------------------------------------
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -104,7 +108,7 @@ class ClockSampler:
             if len(p) < 9:
                 continue
             try:
-                rows.append((float(p[1]), float(p[2]), p[3], p[5:9]))
+                rows.append((float(p[1]), float(p[2]), p[5:9]))
             except ValueError:
                 continue
         os.unlink(self.path)
@@ -113,7 +117,7 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         seen = set()
         for r in rows:
-            for n, v in zip(names, r[3]):
+            for n, v in zip(names, r[2]):
                 if v.lower() == "active":
                     seen.add(n)
         return {"sm_mhz": statistics.median(r[0] for r in rows),
@@ -125,59 +129,54 @@ def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
-            d = json.load(f)
-        return d, "measured"
+            return json.load(f), "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# ------------------------------------------------------------------------------------
-# transfer workload
+def kernel_launches(trace):
+    return {k: v for k, v in trace.items() if not k.startswith("count:")}
+
+
 # ------------------------------------------------------------------------------------
 class TransferWorkload:
-    name = ("transfer_mix: mesh 512x512 jittered (524,288 tri) 1M pts + MLS2D mixed 4M->4M "
-            "gauss8 quadratic r=0.01 minnb=10 + MLS3D mixed 8M->8M slab quadratic r=0.012 16 fields")
+    name = TRANSFER_NAME
 
     def __init__(self, torch, pcms, W, device):
-        self.torch, self.P, self.W = torch, pcms, W
+        import numpy as np
+        self.torch, self.P, self.np = torch, pcms, np
         self.dev = device
-        np = __import__("numpy")
-        self.np = np
-        c2 = W.mesh_2d()
-        c3 = W.mls_2d_gaussian()
-        c4 = W.mls_3d_slab()
-        self.host = {
-            "xy": c2.xy, "tri": c2.tri, "mfield": c2.field, "mpts": c2.pts,
-            "s3": c3.src, "t3": c3.tgt, "f3": c3.fields.astype(np.float32),
-            "s4": c4.src, "t4": c4.tgt, "f4": c4.fields,
-        }
+        c2, c3, c4 = W.mesh_2d(), W.mls_2d_gaussian(), W.mls_3d_slab()
         self.cfg = {"c2": c2, "c3": c3, "c4": c4}
-        self.d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in self.host.items()}
+        host = {"xy": c2.xy, "tri": c2.tri, "mfield": c2.field, "mpts": c2.pts,
+                "s3": c3.src, "t3": c3.tgt, "f3": c3.fields.astype(np.float32),
+                "s4": c4.src, "t4": c4.tgt, "f4": c4.fields}
+        self.d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in host.items()}
         self.points_per_step = c2.pts.shape[1] + c3.tgt.shape[1] + c4.tgt.shape[1]
-        self.parts = {}
-        self.out = {}
-        # work counts for the roofline models
         m4 = pcms.create_map(self.d["s4"], self.d["t4"], 2, c4.radius, precision="mixed")
         self.nnz4 = m4.info()["nnz"]
         m4.destroy()
         cnt = pcms.count_neighbors(self.d["s3"], self.d["t3"], c3.radius, degree=2,
                                    min_neighbors=c3.min_neighbors, precision="mixed")
-        self.pairs3 = int(cnt.sum().item())
+        self.pairs3 = int(cnt.to(torch.int64).sum().item())
+        self.parts = {}
         torch.cuda.synchronize()
 
-    def step(self, d=None, timed_parts=False):
-        P, torch = self.P, self.torch
-        d = d or self.d
+    def step(self, timed_parts=False):
+        P, torch, d = self.P, self.torch, self.d
         c3, c4 = self.cfg["c3"], self.cfg["c4"]
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if timed_parts else None
-        if ev: ev[0].record()
+        if ev:
+            ev[0].record()
         mesh = P.Mesh(d["xy"], d["tri"])
-        elem, _, vals = mesh.locate_interp(d["mpts"], d["mfield"], with_dim=False)
-        if ev: ev[1].record()
-        out3, _ = P.mls_transfer(d["s3"], d["t3"], d["f3"], 2, c3.radius, precision="mixed",
-                                 min_neighbors=c3.min_neighbors, with_status=False)
-        if ev: ev[2].record()
+        mesh.locate_interp(d["mpts"], d["mfield"], with_dim=False)
+        if ev:
+            ev[1].record()
+        P.mls_transfer(d["s3"], d["t3"], d["f3"], 2, c3.radius, precision="mixed",
+                       min_neighbors=c3.min_neighbors, with_status=False)
+        if ev:
+            ev[2].record()
         m4 = P.create_map(d["s4"], d["t4"], 2, c4.radius, precision="mixed")
-        out4 = m4.apply(d["f4"])
+        m4.apply(d["f4"])
         m4.destroy()
         mesh.destroy()
         if ev:
@@ -186,109 +185,196 @@ class TransferWorkload:
             self.parts = {"mesh_1M_ms": ev[0].elapsed_time(ev[1]),
                           "mls2d_4M_ms": ev[1].elapsed_time(ev[2]),
                           "mls3d_8M_16f_ms": ev[2].elapsed_time(ev[3])}
-        self.out = {"elem": elem, "vals": vals, "out3": out3, "out4": out4}
         return self.points_per_step
 
-    def e2e_step(self, pinned):
-        """inputs copied from pinned host buffers, outputs read back, inside the region"""
-        torch = self.torch
-        d = {k: v.to(self.dev, non_blocking=True) for k, v in pinned.items()}
-        self.step(d)
-        outs = [self.out["elem"], self.out["vals"], self.out["out3"], self.out["out4"]]
-        host = [o.to("cpu") for o in outs]
-        torch.cuda.synchronize()
-        return sum(o.numel() * o.element_size() for o in host)
-
-    def pinned_inputs(self):
-        return {k: v.cpu().pin_memory() for k, v in self.d.items()}
-
-    def input_bytes(self):
-        return sum(v.numel() * v.element_size() for v in self.d.values())
-
-    def roofline(self, trace, peaks, kind):
-        """dominant kernel of the step and its roofline entry"""
-        if not trace:
-            return None, None
-        name = max(trace, key=lambda k: trace[k][1])
-        launches, ms = trace[name]
+    def roofline(self, trace, peaks, kind, sm_mhz=None):
+        """the step's dominant kernel and its roofline entry"""
+        tr = kernel_launches(trace)
+        if not tr:
+            return None
+        name = max(tr, key=lambda k: tr[k][1])
+        launches, ms = tr[name]
         avg_s = ms / launches / 1e3
-        c3, c4 = self.cfg["c3"], self.cfg["c4"]
-        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-        fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        r = None
+        c4 = self.cfg["c4"]
+        clk = peaks.get("sm_max_mhz", 2070.0)
+        fp32_peak = 152 * 128 * 2 * clk * 1e6 / 1e12
         if name == "mls_assemble_fused_mixed":
-            fl = self.pairs3 * mls_pair_flops(2, 2, 1)
-            r = {"bound": "alu", "achieved": fl / avg_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s"}
+            r = {"bound": "alu", "achieved": self.pairs3 * mls_pair_flops(2, 2, 1) / avg_s / 1e12,
+                 "peak": fp32_peak, "unit": "TFLOP/s"}
         elif name == "mls_assemble_map_mixed":
-            fl = self.nnz4 * mls_pair_flops(3, 2, 0)
-            r = {"bound": "alu", "achieved": fl / avg_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s"}
+            r = {"bound": "alu", "achieved": self.nnz4 * mls_pair_flops(3, 2, 0) / avg_s / 1e12,
+                 "peak": fp32_peak, "unit": "TFLOP/s"}
         elif name == "apply_spmm":
             by = spmm_bytes(self.nnz4, c4.src.shape[1], c4.tgt.shape[1], 16)
-            r = {"bound": "hbm", "achieved": by / avg_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
-        if r is not None:
-            r["frac"] = r["achieved"] / r["peak"]
-            r["traffic"] = None
-            r["kernel"] = name
-            r["peak_source"] = kind if r["unit"] == "GB/s" else f"{kind} max SM clock x 152 SM x 128 FP32 lanes x 2"
-            r["avg_launch_ms"] = ms / launches
-        return name, r
-
-    def cpu_sample(self, orc, budget_s=15.0):
-        """the oracle as it stands on a bounded, seeded sample of the same workload"""
-        np = self.np
-        rng = np.random.default_rng(7)
-        c2, c3, c4 = self.cfg["c2"], self.cfg["c3"], self.cfg["c4"]
-        n2, n3, n4 = 100_000, 1_000, 10_000
-        i2 = rng.choice(c2.pts.shape[1], n2, replace=False)
-        i3 = rng.choice(c3.tgt.shape[1], n3, replace=False)
-        i4 = rng.choice(c4.tgt.shape[1], n4, replace=False)
-        t = time.perf_counter()
-        orc.locate(c2.xy, c2.tri, c2.pts[:, i2], field=c2.field, mode="grid")
-        orc.mls(c3.src, c3.tgt[:, i3], c3.fields, 2, c3.radius, min_neighbors=c3.min_neighbors,
-                mode="grid")
-        orc.mls(c4.src, c4.tgt[:, i4], c4.fields.astype(np.float64), 2, c4.radius, mode="grid")
-        dt = time.perf_counter() - t
-        n = n2 + n3 + n4
-        return n / dt, n, dt, (f"{n2} mesh points + {n3} MLS2D targets + {n4} MLS3D targets "
-                               f"(16 fields), uniform sample, oracle grid mode")
+            r = {"bound": "hbm", "achieved": by / avg_s / 1e9, "peak": peaks["hbm_gbs"],
+                 "unit": "GB/s"}
+        else:
+            return {"kernel": name, "avg_launch_ms": ms / launches, "bound": None}
+        r["frac"] = r["achieved"] / r["peak"]
+        r["traffic"] = None
+        r["kernel"] = name
+        r["avg_launch_ms"] = ms / launches
+        r["peak_source"] = (f"{kind} HBM copy" if r["unit"] == "GB/s" else
+                            f"152 SM x 128 FP32 lanes x 2 x {clk:.0f} MHz ({kind} max SM clock)")
+        return r
 
 
-# ------------------------------------------------------------------------------------
-def flush_l2(torch, buf):
+class ServeWorkload:
+    name = SERVE_NAME
+
+    def __init__(self, torch, pcms, serve, W, device, n_req=2000, n_slots=16,
+                 cap=40 << 30):
+        self.torch, self.P, self.S = torch, pcms, serve
+        self.dev = device
+        self.reqs = W.request_stream(n_req, 501)
+        self.dreqs = serve.materialize(self.reqs, device)
+        self.points_per_step = sum(d.points for d in self.dreqs)
+        self.n_slots, self.cap = n_slots, cap
+        self.last = None
+
+    def step(self):
+        self.last = self.S.run_served(self.dreqs, n_slots=self.n_slots, mem_cap=self.cap)
+        assert self.last["failed"] == 0, self.last
+        return self.points_per_step
+
+    def open_loop(self, capacity_pts_s):
+        arr = [r.arrival_s for r in self.reqs]
+        scale = (self.points_per_step / (0.8 * capacity_pts_s)) / arr[-1]
+        self.arrivals = [a * scale for a in arr]
+        return self.S.run_served(self.dreqs, n_slots=self.n_slots, mem_cap=self.cap,
+                                 arrivals=self.arrivals)
+
+    def plain_fp64(self):
+        return self.S.run_plain_fp64(self.dreqs, arrivals=getattr(self, "arrivals", None))
+
+    def e2e(self):
+        """pinned host inputs -> device, serve, outputs -> host, all inside the region"""
+        torch = self.torch
+        host = []
+        for d in self.dreqs:
+            ins = {k: v for k, v in d.tensors.items() if k not in ("out", "values", "elem")}
+            host.append({k: v.cpu().pin_memory() for k, v in ins.items()})
+        outs = [[v for k, v in d.tensors.items() if k in ("out", "values", "elem")]
+                for d in self.dreqs]
+        bi = sum(v.numel() * v.element_size() for h in host for v in h.values())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for d, h in zip(self.dreqs, host):
+            for k, v in h.items():
+                d.tensors[k].copy_(v, non_blocking=True)
+        st = self.S.run_served(self.dreqs, n_slots=self.n_slots, mem_cap=self.cap)
+        got = [o.to("cpu") for os_ in outs for o in os_]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        bo = sum(o.numel() * o.element_size() for o in got)
+        return {"value": self.points_per_step / dt, "unit": "points/s",
+                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": dt * 1e3,
+                "failed": st["failed"]}
+
+    def cpu_sample(self, orc, per_req=64, n_req=40):
+        """the oracle as it stands on a bounded sample: n_req seeded requests, per_req seeded
+        targets each, on the same (device-synthesised) inputs"""
+        import numpy as np
+        rng = np.random.default_rng(11)
+        pick = rng.choice(len(self.dreqs), n_req, replace=False)
+        jobs = []
+        for i in pick:
+            d = self.dreqs[i]
+            t = {k: v.cpu().numpy() for k, v in d.tensors.items()}
+            jobs.append((d.req, t))
+        n = 0
+        t0 = time.perf_counter()
+        for r, t in jobs:
+            if r.kind == "mesh":
+                sel = rng.choice(r.n_tgt, min(per_req * 16, r.n_tgt), replace=False)
+                orc.locate(t["xy"], t["tri"], t["pts"][:, sel], field=t["field"], mode="grid")
+                n += len(sel)
+            else:
+                sel = rng.choice(r.n_tgt, min(per_req, r.n_tgt), replace=False)
+                orc.mls(t["src"], t["tgt"][:, sel], t["fields"].astype(np.float64), r.degree,
+                        r.radius, mode="grid")
+                n += len(sel)
+        dt = time.perf_counter() - t0
+        return n / dt, n, dt, (f"{n_req} seeded requests of the stream, {per_req} targets per "
+                               f"MLS request and {per_req * 16} points per mesh request, oracle "
+                               f"grid mode")
+
+
+def flush_l2(buf):
     buf.add_(1.0)
 
 
+def timed(torch, fn, stream):
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    r = fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return r, a.elapsed_time(b)
+
+
+# ------------------------------------------------------------------------------------
 def run_reference(args, rank, world):
     """The CPU oracle as it stands, on the host cores, on bounded samples (rank 0 only)."""
     if rank != 0:
         return
-    import numpy as np
     import oracle
-    from paper_2510_18838_gb300 import workloads as W
     oracle.build()
     cores = oracle.get_threads()
+    if args.workload == "serve":
+        import torch
+        from paper_2510_18838_gb300 import serve
+        from paper_2510_18838_gb300 import workloads as W
+        reqs = W.request_stream(2000, 501)
+        wl = ServeWorkload.__new__(ServeWorkload)
+        wl.reqs = reqs
+        pick = sorted(__import__("numpy").random.default_rng(11).choice(len(reqs), 40,
+                                                                       replace=False))
+        # a reused operator's request needs the request that built its geometry
+        need = set(pick) | {reqs[i].reuse_of for i in pick if reqs[i].reuse_of >= 0}
+        sub = [reqs[i] for i in sorted(need)]
+        wl.dreqs = serve.materialize(sub, torch.device("cpu"))   # synthesised on the host
+        name = SERVE_NAME
+        sample_fn = lambda: wl.cpu_sample(oracle, n_req=len(wl.dreqs))
+    else:
+        from paper_2510_18838_gb300 import workloads as W
+        c2, c3, c4 = W.mesh_2d(), W.mls_2d_gaussian(), W.mls_3d_slab()
+        name = TRANSFER_NAME
 
-    class _Stub:
-        pass
-    wl = TransferWorkload.__new__(TransferWorkload)
-    wl.np = np
-    wl.cfg = {"c2": W.mesh_2d(), "c3": W.mls_2d_gaussian(), "c4": W.mls_3d_slab()}
+        def sample_fn():
+            import numpy as np
+            rng = np.random.default_rng(7)
+            i2 = rng.choice(c2.pts.shape[1], 100_000, replace=False)
+            i3 = rng.choice(c3.tgt.shape[1], 1_000, replace=False)
+            i4 = rng.choice(c4.tgt.shape[1], 10_000, replace=False)
+            t = time.perf_counter()
+            oracle.locate(c2.xy, c2.tri, c2.pts[:, i2], field=c2.field, mode="grid")
+            oracle.mls(c3.src, c3.tgt[:, i3], c3.fields, 2, c3.radius,
+                       min_neighbors=c3.min_neighbors, mode="grid")
+            oracle.mls(c4.src, c4.tgt[:, i4], c4.fields.astype(np.float64), 2, c4.radius,
+                       mode="grid")
+            dt = time.perf_counter() - t
+            n = 111_000
+            return n / dt, n, dt, "100k mesh points + 1k MLS2D + 10k MLS3D targets, grid mode"
     vals = []
+    sample = ""
     for i in range(args.warmup + args.steps):
-        v, n, dt, sample = wl.cpu_sample(oracle)
+        v, n, dt, sample = sample_fn()
         if i >= args.warmup:
-            vals.append((v, n, dt))
+            vals.append((v, dt))
     v = statistics.median(x[0] for x in vals)
-    ms = statistics.median(x[2] for x in vals) * 1e3
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "points/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": TransferWorkload.name, "sample": sample},
-            "cpu_baseline": {"kind": "oracle", "value": v, "unit": "points/s", "cores": cores,
-                             "sample": sample},
-            "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    ms = statistics.median(x[1] for x in vals) * 1e3
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "points/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "sample": sample},
+        "cpu_baseline": {"kind": "oracle", "value": v, "unit": "points/s", "cores": cores,
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}), flush=True)
 
 
 def main():
@@ -297,18 +383,17 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="transfer", choices=["transfer", "serve"])
+    ap.add_argument("--workload", default="serve", choices=["serve", "transfer"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+    args.warmup = max(args.warmup, 3)
 
     import torch
     torch.cuda.set_device(local)
@@ -318,12 +403,41 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2510_18838_gb300 import build as B
     B.build()
-    from paper_2510_18838_gb300 import pcms
+    from paper_2510_18838_gb300 import pcms, serve
     from paper_2510_18838_gb300 import workloads as W
     dev = torch.device("cuda", local)
-
-    wl = TransferWorkload(torch, pcms, W, dev)
+    stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+
+    # ---- single-stream transfer pass: per-kernel breakdown and the roofline entry
+    tw = TransferWorkload(torch, pcms, W, dev)
+    for _ in range(2):
+        tw.step()
+    torch.cuda.synchronize()
+    pcms.trace_enable(True)
+    flush_l2(flush)
+    _, tms = timed(torch, tw.step, stream)
+    pcms.trace_enable(False)
+    ttrace = pcms.trace_read()
+    tw.step(timed_parts=True)
+    transfer = {"workload": TRANSFER_NAME, "ms": tms, "points": tw.points_per_step,
+                "points_per_s": tw.points_per_step / (tms / 1e3), "parts_ms": tw.parts,
+                "kernels_ms": {k: round(v[1], 3) for k, v in sorted(
+                    kernel_launches(ttrace).items(), key=lambda kv: -kv[1][1])[:14]},
+                "tiers": {k[6:]: v[0] for k, v in ttrace.items() if k.startswith("count:")},
+                "work": {"mls2d_pairs": tw.pairs3, "mls3d_nnz": tw.nnz4}}
+    peaks, kind = measured_peaks()
+    roof = tw.roofline(ttrace, peaks, kind)
+
+    if args.workload == "transfer":
+        wl = tw
+        name = TRANSFER_NAME
+    else:
+        del tw
+        torch.cuda.empty_cache()
+        wl = ServeWorkload(torch, pcms, serve, W, dev)
+        name = SERVE_NAME
+
     for _ in range(args.warmup):
         wl.step()
     torch.cuda.synchronize()
@@ -335,16 +449,11 @@ def main():
     pcms.trace_enable(True)
     step_ms = []
     points = 0
-    stream = torch.cuda.current_stream()
     for _ in range(args.steps):
-        flush_l2(torch, flush)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        points += wl.step()
-        b.record(stream)
-        torch.cuda.synchronize()
-        step_ms.append(a.elapsed_time(b))
+        flush_l2(flush)
+        p, ms = timed(torch, wl.step, stream)
+        points += p
+        step_ms.append(ms)
     pcms.trace_enable(False)
     trace = pcms.trace_read()
     clk = clocks.stop()
@@ -354,27 +463,22 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
         dist.barrier()
-    torch.cuda.synchronize()
     value = points * world / (total_ms / 1e3)
-    wl.step(timed_parts=True)
-    parts = dict(wl.parts)
+    launches = sum(v[0] for v in kernel_launches(trace).values())
 
-    # end to end: pinned host inputs -> device, the same C-ABI calls, results -> host
-    pinned = wl.pinned_inputs()
-    e2e_ms = []
-    bo = 0
-    for i in range(max(2, args.steps)):
-        flush_l2(torch, flush)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        bo = wl.e2e_step(pinned)
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_med = statistics.median(e2e_ms[1:] if len(e2e_ms) > 2 else e2e_ms)
-    bi = wl.input_bytes()
-
-    peaks, kind = measured_peaks()
-    kname, roof = wl.roofline(trace, peaks, kind)
-    launches = sum(v[0] for v in trace.values())
+    extra = {}
+    if args.workload == "serve":
+        ol = wl.open_loop(value / world)
+        pf = wl.plain_fp64()
+        extra = {"latency_open_loop_0p8": {k: ol[k] for k in ("p50_ms", "p99_ms", "points_per_s",
+                                                              "failed", "cached_hits")},
+                 "closed_loop": {k: wl.last[k] for k in ("p50_ms", "p99_ms", "cached_hits",
+                                                         "peak_bytes")},
+                 "plain_fp64_per_request": pf,
+                 "requests": len(wl.dreqs)}
+        e2e = wl.e2e()
+    else:
+        e2e = {"value": None}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -390,20 +494,11 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": wl.name, "points_per_step": wl.points_per_step,
+            "config": {"workload": name, "points_per_step": wl.points_per_step,
                        "l2": "256 MiB write between timed steps; inputs > L2",
                        "parallelism": f"replicas x{world}"},
-            "clocks": clk,
-            "e2e": {"value": wl.points_per_step / (e2e_med / 1e3), "unit": "points/s",
-                    "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
-                    "ms_per_step": e2e_med},
-            "gpu_launches": launches,
-            "roofline": roof,
-            "cpu_baseline": cpu,
-            "parts_ms": parts,
-            "kernels_ms": {k: round(v[1] / args.steps, 4) for k, v in
-                           sorted(trace.items(), key=lambda kv: -kv[1][1])},
-            "work": {"mls2d_pairs": wl.pairs3, "mls3d_nnz": wl.nnz4},
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+            "cpu_baseline": cpu, **extra, "transfer_pass": transfer,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -248,7 +248,7 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
     const bool mixed = P.prec == PCMS_MIXED;
     const int64_t ns = M.ns, nt = M.nt;
     BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
-    M.g = make_grid(dim, b.lo, b.hi, P.radius, MAX_CELLS);
+    M.g = make_grid(dim, b.lo, b.hi, 0.5 * P.radius, MAX_CELLS);
     sort_points(M.g, src, ns, true, mixed, M.src, s);
     sort_points(M.g, tgt, nt, false, false, M.tgt, s);
     const int G = choose_group(dim, ns, P.radius, b.lo, b.hi);
@@ -357,7 +357,7 @@ void mls_count(const MlsParams& P, const double* src, int64_t ns, const double* 
     const int dim = P.dim;
     const bool mixed = P.prec == PCMS_MIXED;
     BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
-    Grid g = make_grid(dim, b.lo, b.hi, P.radius, MAX_CELLS);
+    Grid g = make_grid(dim, b.lo, b.hi, 0.5 * P.radius, MAX_CELLS);
     SortedPoints S, Tp;
     sort_points(g, src, ns, true, mixed, S, s);
     sort_points(g, tgt, nt, false, false, Tp, s);
@@ -393,7 +393,7 @@ void mls_transfer(const MlsParams& P, const double* src, int64_t ns, const doubl
     const bool mixed = P.prec == PCMS_MIXED;
     *n_under = 0;
     BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
-    Grid g = make_grid(dim, b.lo, b.hi, P.radius, MAX_CELLS);
+    Grid g = make_grid(dim, b.lo, b.hi, 0.5 * P.radius, MAX_CELLS);
     SortedPoints S, Tp;
     sort_points(g, src, ns, true, mixed, S, s);
     sort_points(g, tgt, nt, false, false, Tp, s);

@@ -56,10 +56,12 @@ struct AsmArgs {
 // Precision tiers of the mixed path. The FP64 solve of a tier-1 system estimates how much
 // the FP32 assembly error can move c_0 and hands sensitive targets to the next tier:
 //   tier 1  plain FP32 accumulation      accepted if amp * (1 + sqrt(n / (3 G^2))) <= AMP_T1
-//   tier 2  compensated FP32 (Kahan)     accepted if amp <= AMP_T2
+//   tier 2  compensated FP32 (Kahan)     accepted if amp <= AMP_T2 * max(1, sqrt(n / 1000))
 //   tier 3  FP64 assembly                final (pivot guard TAU_FP64 only)
-// A failed pivot guard in tier 1 or 2 also goes to tier 3.
-constexpr double AMP_T1 = 32.0;
+// A failed pivot guard in tier 1 or 2 also goes to tier 3. The bounds keep the estimated
+// error of c_0 several times below 2e-5 (calibrated on emulated FP32 arithmetic: plain sums
+// ~ amp * 6e-8 * (1 + sqrt(n / 3G^2)), compensated sums ~ amp * (2e-8 .. 1.5e-7) / sqrt(n)).
+constexpr double AMP_T1 = 64.0;
 constexpr double AMP_T2 = 2048.0;
 constexpr double AMP_SHAPE = 32.0;   // operator rows above this are evaluated in FP64
 
@@ -312,12 +314,15 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
         const int64_t t = A.list ? (int64_t)A.list[wk] : wk;
         double tx[3] = {0.0, 0.0, 0.0};
         long long ct[3] = {0, 0, 0};
+        float fr[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int d = 0; d < DIM; d++) {
             tx[d] = A.tx64[d * A.nt + t];
-            double f = floor((tx[d] - g.lo[d]) * g.inv_h);
+            const double u = (tx[d] - g.lo[d]) * g.inv_h;   // position in cell units
+            double f = floor(u);
             f = fmin(fmax(f, -1073741824.0), 1073741824.0);
             ct[d] = (long long)f;
+            fr[d] = (float)(u - f);
         }
         float thi[3] = {0.f, 0.f, 0.f}, tlo[3] = {0.f, 0.f, 0.f};
         if (MIXED) {
@@ -343,19 +348,19 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
             const double r2_in = r2 * (1.0 - 9.094947017729282e-13);
             const float r2f = (float)r2;
             const T inv_r = (T)(1.0 / r);
-            const long long wc = k >= 30 ? (1LL << 30) : (1LL << k);
-            long long lo_[3], hi_[3];
-            bool empty = false;
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-                if (d < DIM) {
-                    lo_[d] = max(ct[d] - wc, 0LL);
-                    hi_[d] = min(ct[d] + wc, (long long)g.n[d] - 1);
-                    empty |= lo_[d] > hi_[d];
-                } else {
-                    lo_[d] = hi_[d] = 0;
-                }
+            // Candidate rows: cells (y, z) whose slab comes within r of the target, each
+            // trimmed in x to the ball's chord. Computed in cell units in FP32 with a margin
+            // m far above the FP32 error, so the rows and chords only ever over-cover.
+            const float R0 = fminf((float)(r * g.inv_h), 1073741824.f);
+            const float mg = 1e-3f + R0 * 1e-6f;
+            const float RR = R0 + mg;
+            long long z0 = 0, z1 = 0;
+            if (DIM == 3) {
+                z0 = max((long long)floorf(fr[2] - RR), -ct[2]);
+                z1 = min((long long)floorf(fr[2] + RR), (long long)g.n[2] - 1 - ct[2]);
             }
+            const long long y0 = max((long long)floorf(fr[1] - RR), -ct[1]);
+            const long long y1 = min((long long)floorf(fr[1] + RR), (long long)g.n[1] - 1 - ct[1]);
 #pragma unroll
             for (int i = 0; i < (NACC > 0 ? NACC : 1); i++) {
                 acc[i] = T(0);
@@ -364,12 +369,29 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
             cnt = 0;
             int qn = 0, head = 0;
             int64_t written = 0;
-            if (!empty) {
-                for (long long cz = lo_[2]; cz <= hi_[2]; ++cz)
-                    for (long long cy = lo_[1]; cy <= hi_[1]; ++cy) {
-                        const int64_t rowbase = (cz * g.n[1] + cy) * (int64_t)g.n[0];
-                        const int a = A.cell_start[rowbase + lo_[0]];
-                        const int b = A.cell_start[rowbase + hi_[0] + 1];
+            {
+                for (long long dz = z0; dz <= z1; ++dz) {
+                    float ez = 0.f;
+                    if (DIM == 3) {
+                        ez = fmaxf(fmaxf((float)dz - fr[2], fr[2] - (float)dz - 1.f), 0.f);
+                        ez = fmaxf(ez - mg, 0.f);
+                    }
+                    const float remz = RR * RR - ez * ez;
+                    if (remz <= 0.f) continue;
+                    for (long long dy = y0; dy <= y1; ++dy) {
+                        float ey = fmaxf(fmaxf((float)dy - fr[1], fr[1] - (float)dy - 1.f), 0.f);
+                        ey = fmaxf(ey - mg, 0.f);
+                        const float rem = remz - ey * ey;
+                        if (rem <= 0.f) continue;
+                        const float hx = sqrtf(rem) + mg;
+                        const long long x0 = max((long long)floorf(fr[0] - hx) + ct[0], 0LL);
+                        const long long x1 =
+                            min((long long)floorf(fr[0] + hx) + ct[0], (long long)g.n[0] - 1);
+                        if (x0 > x1) continue;
+                        const int64_t rowbase =
+                            ((ct[2] + dz) * g.n[1] + (ct[1] + dy)) * (int64_t)g.n[0];
+                        const int a = A.cell_start[rowbase + x0];
+                        const int b = A.cell_start[rowbase + x1 + 1];
                         for (int j0 = a; j0 < b; j0 += G) {
                             const int j = j0 + gl;
                             bool in = false;
@@ -442,6 +464,7 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
                             }
                         }
                     }
+                }
                 if (MODE != MODE_COUNT && qn > 0) {
                     if (gl < qn) {
                         QE e = q[(head + gl) & (QCAP - 1)];
@@ -600,12 +623,17 @@ __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
             int next = 0;
             if (st == PCMS_TARGET_ILL_CONDITIONED) {
                 next = 3;
-            } else if (S.tier == 1) {
-                const double g = (double)S.group;
-                const double risk = amp * (1.0 + sqrt((double)cnt / (3.0 * g * g)));
-                if (risk > AMP_T1) next = amp > AMP_T2 ? 3 : 2;
-            } else if (amp > AMP_T2) {
-                next = 3;
+            } else {
+                // compensated sums leave the per-term product rounding, whose effect on c_0
+                // shrinks like 1/sqrt(n): the tier-2 bound grows with sqrt(n / 1000)
+                const double lim2 = AMP_T2 * fmax(1.0, sqrt((double)cnt / 1000.0));
+                if (S.tier == 1) {
+                    const double g = (double)S.group;
+                    const double risk = amp * (1.0 + sqrt((double)cnt / (3.0 * g * g)));
+                    if (risk > AMP_T1) next = amp > lim2 ? 3 : 2;
+                } else if (amp > lim2) {
+                    next = 3;
+                }
             }
             if (next == 2) {
                 S.list2[atomicAdd(S.n2, 1)] = (int32_t)t;
@@ -616,7 +644,10 @@ __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
                 continue;
             }
         }
-        if (MODE == MODE_MAP && S.flags) S.flags[t] = (int8_t)(amp > AMP_SHAPE ? 1 : 0);
+        // operator rows: 0 = FP32; 1 = FP32 u, w as in the moments, FP64 monomials and dot;
+        // 2 = everything in FP64 (tier 3: y belongs to the exact FP64 moments)
+        if (MODE == MODE_MAP && S.flags)
+            S.flags[t] = (int8_t)(S.tier == 3 ? 2 : (amp > AMP_SHAPE ? 1 : 0));
         const double nanv = __longlong_as_double(0x7ff8000000000000LL);
         if (MODE == MODE_FUSED) {
             const int64_t o = S.perm_t ? (int64_t)S.perm_t[t] : t;
@@ -666,6 +697,29 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
         const int64_t a = S.offsets[t], b = S.offsets[t + 1];
         for (int64_t i = a + gl; i < b; i += G) {
             const int j = S.cols[i];
+            if (MIXED && flag == 2) {
+                // row of an FP64-assembled target: the exact FP64 offsets, weight and basis
+                double e[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+                for (int d = 0; d < DIM; d++) e[d] = S.sx64[d * S.ns + j] - tx[d];
+                double d2 = e[0] * e[0] + e[1] * e[1];
+                if (DIM == 3) d2 += e[2] * e[2];
+                const double ir = 1.0 / r;
+                const double w64 = weight_value<double>(S.weight, sqrt(d2) * ir);
+                const double uu[3] = {e[0] * ir, e[1] * ir, e[2] * ir};
+                double am[M];
+                am[0] = 1.0;
+                double s = S.y[t * M];
+                sfor<M - 1>([&](auto I) {
+                    constexpr int p = decltype(I)::value + 1;
+                    constexpr int par = mono_parent(DIM, p);
+                    constexpr int v = mono_var(DIM, p);
+                    am[p] = am[par] * uu[v];
+                    s += am[p] * S.y[t * M + p];
+                });
+                ((T*)S.vals)[i] = (T)(w64 * s);
+                continue;
+            }
             T dx[3] = {T(0), T(0), T(0)};
             if (MIXED) {
                 float4 h0 = S.hl0[j];

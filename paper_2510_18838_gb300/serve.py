@@ -105,7 +105,8 @@ def materialize(reqs, device) -> list[DeviceRequest]:
                                              device=device))
         by_id[r.rid] = d
         out.append(d)
-    torch.cuda.synchronize()
+    if torch.device(device).type == "cuda":
+        torch.cuda.synchronize()
     return out
 
 
