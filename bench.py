@@ -223,10 +223,10 @@ class ServeWorkload:
     name = SERVE_NAME
 
     def __init__(self, torch, pcms, serve, W, device, n_req=2000, n_slots=16,
-                 cap=40 << 30):
+                 cap=40 << 30, seed=501):
         self.torch, self.P, self.S = torch, pcms, serve
         self.dev = device
-        self.reqs = W.request_stream(n_req, 501)
+        self.reqs = W.request_stream(n_req, seed)
         self.dreqs = serve.materialize(self.reqs, device)
         self.points_per_step = sum(d.points for d in self.dreqs)
         self.n_slots, self.cap = n_slots, cap
@@ -271,7 +271,7 @@ class ServeWorkload:
                 "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": dt * 1e3,
                 "failed": st["failed"]}
 
-    def cpu_sample(self, orc, per_req=64, n_req=40):
+    def cpu_sample(self, orc, per_req=1024, n_req=40):
         """the oracle as it stands on a bounded sample: n_req seeded requests, per_req seeded
         targets each, on the same (device-synthesised) inputs"""
         import numpy as np
@@ -403,7 +403,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2510_18838_gb300 import build as B
     B.build()
-    from paper_2510_18838_gb300 import pcms, serve
+    from paper_2510_18838_gb300 import pcms, serve, shard
     from paper_2510_18838_gb300 import workloads as W
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
@@ -435,7 +435,7 @@ def main():
     else:
         del tw
         torch.cuda.empty_cache()
-        wl = ServeWorkload(torch, pcms, serve, W, dev)
+        wl = ServeWorkload(torch, pcms, serve, W, dev, seed=shard.rank_seed(501, rank))
         name = SERVE_NAME
 
     for _ in range(args.warmup):
@@ -459,11 +459,10 @@ def main():
     clk = clocks.stop()
     total_ms = sum(step_ms)
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms, points, value = shard.aggregate(total_ms, points)
         dist.barrier()
-    value = points * world / (total_ms / 1e3)
+    else:
+        value = points / (total_ms / 1e3)
     launches = sum(v[0] for v in kernel_launches(trace).values())
 
     extra = {}

@@ -256,8 +256,9 @@ def request_stream(n_req: int = 2000, seed: int = 501, rate_hz: float = 2000.0,
             continue
         if mls_ids and u[3] < reuse_frac:
             src_req = out[mls_ids[int(rng.integers(0, len(mls_ids)))]]
+            root = src_req.reuse_of if src_req.reuse_of >= 0 else src_req.rid
             out.append(dataclasses.replace(src_req, rid=i, arrival_s=float(t[i]),
-                                           n_fields=n_fields, reuse_of=src_req.rid))
+                                           n_fields=n_fields, reuse_of=root))
             mls_ids.append(i)
             continue
         dim = 2 if u[4] < 0.5 else 3

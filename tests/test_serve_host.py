@@ -41,7 +41,7 @@ def test_reuse_points_to_an_earlier_mls_request_with_the_same_geometry():
     for r in reqs:
         if r.kind == "mls" and r.reuse_of >= 0:
             b = by[r.reuse_of]
-            assert b.rid < r.rid and b.kind == "mls"
+            assert b.rid < r.rid and b.kind == "mls" and b.reuse_of < 0   # the root request
             assert (b.dim, b.degree, b.radius, b.n_src, b.n_tgt, b.seed) == \
                    (r.dim, r.degree, r.radius, r.n_src, r.n_tgt, r.seed)
 
