@@ -163,6 +163,27 @@ pcms_status pcms_count_neighbors(int dim, const double* src_pts, int64_t n_src,
                                  double radius, const pcms_map_opts* opts, int32_t* counts,
                                  int32_t* radius_doublings, int64_t* total, void* stream);
 
+/*
+ * pcms_apply_map_noalloc -- the same result as pcms_apply_map, for callers that must not
+ *   allocate device memory while they run (for example a solver's time-step loop that keeps
+ *   a fixed device-memory footprint after set-up, or code sharing the GPU with an
+ *   application whose allocator owns the free memory). The paper has no counterpart: this
+ *   is a deployment variant of the apply.
+ *   Scratch comes from one fixed 32 MiB device array built into the library (held by every
+ *   GPU that loads the library until the process exits); this call performs no device
+ *   allocation or free. The scratch needed is about (n_src + n_tgt) * P * elem bytes, P =
+ *   n_fields rounded up to 1, 4, 8 or 16 (float32 maps) or 1, 2, 4, 8, 16 (float64), elem =
+ *   4 or 8; a map/field count needing more returns PCMS_ERR_CAPACITY and enqueues nothing.
+ *   The first call on a device performs a one-time set-up for that device (it looks up the
+ *   array's device address, which may load the library's device code); make that first
+ *   call before any stream capture. Every call shares the one array and every element a
+ *   call reads is written earlier by the same call, so nothing carries over between calls;
+ *   calls whose work can overlap on the GPU (different streams, or host threads) race on
+ *   the array and must be ordered by the caller. Arguments as pcms_apply_map.
+ */
+pcms_status pcms_apply_map_noalloc(pcms_map map, const void* fields, int n_fields, void* out,
+                                   void* stream);
+
 /* Sizes and status counts of a map. Syncs the map's stream. */
 pcms_status pcms_map_info(pcms_map map, pcms_map_info_t* info);
 

@@ -230,6 +230,37 @@ void apply_t(MapImpl& M, const T* fields, int nf, T* out, cudaStream_t s) {
     PCMS_LAUNCH_CHECK("apply");
 }
 
+// The same three kernels as apply_t, with caller-provided scratch: fs needs ns*fp and stage
+// nt*fp elements. Launch errors are returned, nothing is allocated or traced.
+template <typename T>
+cudaError_t apply_with_scratch_t(const MapImpl& M, const T* fields, int nf, T* out, T* fs,
+                                 T* stage, cudaStream_t s) {
+    const int64_t ns = M.ns, nt = M.nt;
+    constexpr int W = Vec<T>::W;
+    int nvec = 1;
+    while (nvec * W < nf) nvec <<= 1;
+    const int fp = nf == 1 ? 1 : nvec * W;
+    if (ns > 0)
+        k_fields_to_sorted<T><<<blocks_for(ns, 256), 256, 0, s>>>(fields, nf, fp, ns,
+                                                                  M.src.inv.as<int32_t>(), fs);
+    if (nt > 0) {
+        const int64_t* off = M.offsets.as<int64_t>();
+        const int32_t* cols = M.cols.as<int32_t>();
+        const T* vals = M.vals.as<T>();
+        const int8_t* st = M.status.as<int8_t>();
+        const int blocks = blocks_for(nt * 32, 256, 16);
+        const int nv = fp / W;
+        if (fp == 1) k_spmm_1<T><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs, st, stage);
+        else if (nv == 1) k_spmm_vec<T, 1><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs, st, stage);
+        else if (nv == 2) k_spmm_vec<T, 2><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs, st, stage);
+        else if (nv == 4) k_spmm_vec<T, 4><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs, st, stage);
+        else k_spmm_vec<T, 8><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs, st, stage);
+        k_stage_to_caller<T><<<blocks_for(nt, 256), 256, 0, s>>>(stage, fp, nf, nt,
+                                                                 M.tgt.inv.as<int32_t>(), out);
+    }
+    return cudaGetLastError();
+}
+
 // export: row lengths in caller order, scan, then a warp per row copies (col, val)
 __global__ void k_export_len(int64_t nt, const int32_t* __restrict__ inv_t,
                              const int64_t* __restrict__ off, int32_t* __restrict__ len) {
@@ -281,6 +312,32 @@ __global__ void k_export_status(int64_t nt, const int32_t* __restrict__ inv_t,
 void mls_apply(MapImpl& M, const void* fields, int nf, void* out, cudaStream_t s) {
     if (M.P.prec == PCMS_MIXED) apply_t<float>(M, (const float*)fields, nf, (float*)out, s);
     else apply_t<double>(M, (const double*)fields, nf, (double*)out, s);
+}
+
+int64_t apply_scratch_bytes(const MapImpl& M, int nf) {
+    const int W = M.P.prec == PCMS_MIXED ? 4 : 2;
+    const int64_t elem = M.P.prec == PCMS_MIXED ? 4 : 8;
+    int nvec = 1;
+    while (nvec * W < nf) nvec <<= 1;
+    const int64_t fp = nf == 1 ? 1 : nvec * W;
+    const int64_t fs = (M.ns * fp * elem + 255) / 256 * 256;   // stage starts 256-aligned
+    return fs + M.nt * fp * elem;
+}
+
+cudaError_t mls_apply_with_scratch(const MapImpl& M, const void* fields, int nf, void* out,
+                                   void* scratch, cudaStream_t s) {
+    const int64_t elem = M.P.prec == PCMS_MIXED ? 4 : 8;
+    const int W = M.P.prec == PCMS_MIXED ? 4 : 2;
+    int nvec = 1;
+    while (nvec * W < nf) nvec <<= 1;
+    const int64_t fp = nf == 1 ? 1 : nvec * W;
+    char* fs = (char*)scratch;
+    char* stage = fs + (M.ns * fp * elem + 255) / 256 * 256;
+    if (M.P.prec == PCMS_MIXED)
+        return apply_with_scratch_t<float>(M, (const float*)fields, nf, (float*)out, (float*)fs,
+                                           (float*)stage, s);
+    return apply_with_scratch_t<double>(M, (const double*)fields, nf, (double*)out,
+                                        (double*)fs, (double*)stage, s);
 }
 
 void mls_export(MapImpl& M, int64_t* offsets, int32_t* cols, double* vals, int8_t* status,

@@ -10,9 +10,6 @@
 #include "pcms_internal.cuh"
 #include "trace.cuh"
 
-struct pcms_map_s {
-    pcms::MapImpl impl;
-};
 struct pcms_mesh_s {
     pcms::MeshImpl impl;
 };
@@ -20,6 +17,14 @@ struct pcms_mesh_s {
 namespace {
 
 thread_local std::string g_last_error;
+
+}  // namespace
+
+namespace pcms {
+void set_last_error_message(const std::string& msg) { g_last_error = msg; }
+}  // namespace pcms
+
+namespace {
 
 pcms_status set_error(pcms_status st, const std::string& msg) {
     g_last_error = msg;

@@ -208,6 +208,11 @@ struct MapImpl {
 
 void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms_map_opts& o);
 void mls_apply(MapImpl& M, const void* fields, int nf, void* out, cudaStream_t s);
+// apply with caller-provided scratch of apply_scratch_bytes(M, nf) bytes (256-aligned base);
+// allocates nothing, returns the launch status
+int64_t apply_scratch_bytes(const MapImpl& M, int nf);
+cudaError_t mls_apply_with_scratch(const MapImpl& M, const void* fields, int nf, void* out,
+                                   void* scratch, cudaStream_t s);
 void mls_export(MapImpl& M, int64_t* offsets, int32_t* cols, double* vals, int8_t* status,
                 int32_t* kexp, cudaStream_t s);
 void mls_count(const MlsParams& P, const double* src, int64_t ns, const double* tgt, int64_t nt,
@@ -216,6 +221,9 @@ void mls_count(const MlsParams& P, const double* src, int64_t ns, const double* 
 void mls_transfer(const MlsParams& P, const double* src, int64_t ns, const double* tgt,
                   int64_t nt, const pcms_map_opts& o, const void* fields, int nf, void* out,
                   int8_t* status, cudaStream_t s, int64_t* n_under);
+
+// the thread-local message returned by pcms_last_error (capi.cu)
+void set_last_error_message(const std::string& msg);
 
 // ------------------------------------------------------------------------------------
 // mesh (mesh.cu)
@@ -240,3 +248,8 @@ void mesh_locate(const MeshImpl& M, const double* pts, int64_t n, const double* 
 int num_sms();
 
 }  // namespace pcms
+
+// the opaque handle behind pcms_map
+struct pcms_map_s {
+    pcms::MapImpl impl;
+};

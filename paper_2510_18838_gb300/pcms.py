@@ -74,6 +74,7 @@ SIGNATURES = {
     "pcms_map_opts_default": (None, [_P]),
     "pcms_create_map": (_I, [_I, _P, _I64, _P, _I64, _I, _D, _P, _P, _P]),
     "pcms_apply_map": (_I, [_P, _P, _I, _P, _P]),
+    "pcms_apply_map_noalloc": (_I, [_P, _P, _I, _P, _P]),
     "pcms_mls_transfer": (_I, [_I, _P, _I64, _P, _I64, _I, _D, _P, _P, _I, _P, _P, _P]),
     "pcms_count_neighbors": (_I, [_I, _P, _I64, _P, _I64, _I, _D, _P, _P, _P, _P, _P]),
     "pcms_map_info": (_I, [_P, _P]),
