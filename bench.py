@@ -141,11 +141,18 @@ def kernel_launches(trace):
 class TransferWorkload:
     name = TRANSFER_NAME
 
-    def __init__(self, torch, pcms, W, device):
+    def __init__(self, torch, pcms, W, device, small=False):
         import numpy as np
         self.torch, self.P, self.np = torch, pcms, np
         self.dev = device
-        c2, c3, c4 = W.mesh_2d(), W.mls_2d_gaussian(), W.mls_3d_slab()
+        if small:   # the same three parts at about 1/8 of the sizes (profiling captures)
+            self.name = TRANSFER_NAME.replace("512x512", "256x256").replace(
+                "1M pts", "250k pts").replace("4M->4M", "500k->500k").replace("8M->8M", "1M->1M")
+            c2 = W.mesh_2d(n=256, n_pts=250_000)
+            c3 = W.mls_2d_gaussian(500_000, 500_000)
+            c4 = W.mls_3d_slab(1_000_000, 1_000_000)
+        else:
+            c2, c3, c4 = W.mesh_2d(), W.mls_2d_gaussian(), W.mls_3d_slab()
         self.cfg = {"c2": c2, "c3": c3, "c4": c4}
         host = {"xy": c2.xy, "tri": c2.tri, "mfield": c2.field, "mpts": c2.pts,
                 "s3": c3.src, "t3": c3.tgt, "f3": c3.fields.astype(np.float32),
@@ -186,6 +193,25 @@ class TransferWorkload:
                           "mls2d_4M_ms": ev[1].elapsed_time(ev[2]),
                           "mls3d_8M_16f_ms": ev[2].elapsed_time(ev[3])}
         return self.points_per_step
+
+    def cpu_sample(self, orc):
+        """the oracle as it stands on a bounded, seeded sample of the same three parts"""
+        np = self.np
+        rng = np.random.default_rng(7)
+        c2, c3, c4 = self.cfg["c2"], self.cfg["c3"], self.cfg["c4"]
+        n2, n3, n4 = min(100_000, c2.pts.shape[1]), 1_000, 10_000
+        i2 = rng.choice(c2.pts.shape[1], n2, replace=False)
+        i3 = rng.choice(c3.tgt.shape[1], n3, replace=False)
+        i4 = rng.choice(c4.tgt.shape[1], n4, replace=False)
+        t = time.perf_counter()
+        orc.locate(c2.xy, c2.tri, c2.pts[:, i2], field=c2.field, mode="grid")
+        orc.mls(c3.src, c3.tgt[:, i3], c3.fields, 2, c3.radius, min_neighbors=c3.min_neighbors,
+                mode="grid")
+        orc.mls(c4.src, c4.tgt[:, i4], c4.fields.astype(np.float64), 2, c4.radius, mode="grid")
+        dt = time.perf_counter() - t
+        n = n2 + n3 + n4
+        return n / dt, n, dt, (f"{n2} mesh points + {n3} MLS2D + {n4} MLS3D (16 fields) "
+                               f"targets, seeded uniform sample, oracle grid mode")
 
     def roofline(self, trace, peaks, kind, sm_mhz=None):
         """the step's dominant kernel and its roofline entry"""
@@ -383,7 +409,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="serve", choices=["serve", "transfer"])
+    ap.add_argument("--workload", default="serve", choices=["serve", "transfer", "transfer_small"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -410,7 +436,7 @@ def main():
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
 
     # ---- single-stream transfer pass: per-kernel breakdown and the roofline entry
-    tw = TransferWorkload(torch, pcms, W, dev)
+    tw = TransferWorkload(torch, pcms, W, dev, small=args.workload == "transfer_small")
     for _ in range(2):
         tw.step()
     torch.cuda.synchronize()
@@ -429,9 +455,9 @@ def main():
     peaks, kind = measured_peaks()
     roof = tw.roofline(ttrace, peaks, kind)
 
-    if args.workload == "transfer":
+    if args.workload in ("transfer", "transfer_small"):
         wl = tw
-        name = TRANSFER_NAME
+        name = tw.name
     else:
         del tw
         torch.cuda.empty_cache()
