@@ -213,35 +213,49 @@ class TransferWorkload:
         return n / dt, n, dt, (f"{n2} mesh points + {n3} MLS2D + {n4} MLS3D (16 fields) "
                                f"targets, seeded uniform sample, oracle grid mode")
 
-    def roofline(self, trace, peaks, kind, sm_mhz=None):
-        """the step's dominant kernel and its roofline entry"""
+    def roofline(self, trace, peaks, kind):
+        """The step's dominant kernel and its roofline entry. Work per launch comes from the
+        workload (selected pairs, operator nonzeros) or from the library's work counts of the
+        traced step (pairs re-assembled by the second and third precision tiers)."""
         tr = kernel_launches(trace)
         if not tr:
             return None
+        cnt = {k[6:]: v[0] for k, v in trace.items() if k.startswith("count:")}
         name = max(tr, key=lambda k: tr[k][1])
         launches, ms = tr[name]
-        avg_s = ms / launches / 1e3
         c4 = self.cfg["c4"]
         clk = peaks.get("sm_max_mhz", 2070.0)
-        fp32_peak = 152 * 128 * 2 * clk * 1e6 / 1e12
-        if name == "mls_assemble_fused_mixed":
-            r = {"bound": "alu", "achieved": self.pairs3 * mls_pair_flops(2, 2, 1) / avg_s / 1e12,
-                 "peak": fp32_peak, "unit": "TFLOP/s"}
-        elif name == "mls_assemble_map_mixed":
-            r = {"bound": "alu", "achieved": self.nnz4 * mls_pair_flops(3, 2, 0) / avg_s / 1e12,
-                 "peak": fp32_peak, "unit": "TFLOP/s"}
+        fp32 = 152 * 128 * 2 * clk * 1e6 / 1e12      # FFMA lanes x 2 flops
+        fp64 = 152 * 2 * 2 * clk * 1e6 / 1e12        # DFMA lanes x 2 flops
+        f2, f3 = mls_pair_flops(2, 2, 1), mls_pair_flops(3, 2, 0)
+        flops = {   # kernel: (units in the traced step, flops per unit, peak TFLOP/s, peak name)
+            "mls_assemble_fused_mixed": (self.pairs3, f2, fp32, "FP32"),
+            "mls_assemble_fused_bk": (self.pairs3, f2, fp32, "FP32"),
+            "mls_assemble_fused_tier2": (cnt.get("mls_fused_tier2_pairs"), f2, fp32, "FP32"),
+            "mls_assemble_fused_tier3": (cnt.get("mls_fused_tier3_pairs"), f2, fp64, "FP64"),
+            "mls_assemble_map_mixed": (self.nnz4, f3, fp32, "FP32"),
+            "mls_assemble_map_bk": (self.nnz4, f3, fp32, "FP32"),
+            "mls_assemble_map_tier2": (cnt.get("mls_map_tier2_pairs"), f3, fp32, "FP32"),
+            "mls_assemble_map_tier3": (cnt.get("mls_map_tier3_pairs"), f3, fp64, "FP64"),
+        }
+        if name in flops and flops[name][0]:
+            units, per, peak, pk = flops[name]
+            r = {"bound": "alu", "achieved": units * per / (ms / 1e3) / 1e12, "peak": peak,
+                 "unit": "TFLOP/s",
+                 "peak_source": f"derived: 152 SM x {128 if pk == 'FP32' else 2} {pk} FMA lanes "
+                                f"x 2 flops x {clk:.0f} MHz ({kind} max SM clock)",
+                 "work": f"{units} selected pairs x {per} flops"}
         elif name == "apply_spmm":
-            by = spmm_bytes(self.nnz4, c4.src.shape[1], c4.tgt.shape[1], 16)
-            r = {"bound": "hbm", "achieved": by / avg_s / 1e9, "peak": peaks["hbm_gbs"],
-                 "unit": "GB/s"}
+            by = spmm_bytes(self.nnz4, c4.src.shape[1], c4.tgt.shape[1], 16) * launches
+            r = {"bound": "hbm", "achieved": by / (ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+                 "unit": "GB/s", "peak_source": f"{kind} HBM copy",
+                 "work": "nnz x (4 B column + 4 B value) + fields in + outputs out"}
         else:
             return {"kernel": name, "avg_launch_ms": ms / launches, "bound": None}
         r["frac"] = r["achieved"] / r["peak"]
         r["traffic"] = None
         r["kernel"] = name
         r["avg_launch_ms"] = ms / launches
-        r["peak_source"] = (f"{kind} HBM copy" if r["unit"] == "GB/s" else
-                            f"152 SM x 128 FP32 lanes x 2 x {clk:.0f} MHz ({kind} max SM clock)")
         return r
 
 
@@ -472,7 +486,7 @@ def main():
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    pcms.trace_enable(True)
+    pcms.trace_enable(True, count_only=True)   # launch counts only: no events, no extra work
     step_ms = []
     points = 0
     for _ in range(args.steps):

@@ -301,13 +301,16 @@ pcms_status pcms_server_memory(pcms_server s, int64_t* in_use, int64_t* peak,
 void pcms_server_destroy(pcms_server s);
 
 /*
- * Kernel tracing (no counterpart in the paper; instrumentation). When enabled, every
+ * Kernel tracing (no counterpart in the paper; instrumentation). mode 1 (timing): every
  * library kernel launch is bracketed by a CUDA event pair recorded on the stream it is
- * launched on, and elapsed times are accumulated per kernel name. pcms_trace_enable(1)
- * clears the table; pcms_trace_enable(0) stops recording and keeps it. pcms_trace_count
- * and pcms_trace_get synchronise on the recorded events. Thread-safe. Off by default.
+ * launched on, elapsed times are accumulated per kernel name, and work counts are recorded
+ * as "count:<name>" entries (some of which cost a small extra kernel and a sync: pairs per
+ * precision tier). mode 2 (count): launches are only counted per kernel name (total_ms 0),
+ * with no events and no extra work. Any other non-zero mode is mode 1. A non-zero mode
+ * clears the table; 0 stops recording and keeps it. pcms_trace_count and pcms_trace_get
+ * synchronise on the recorded events. Thread-safe. Off by default.
  */
-pcms_status pcms_trace_enable(int on);
+pcms_status pcms_trace_enable(int mode);
 int pcms_trace_count(void);
 /* Entry `index` (0 <= index < pcms_trace_count()): name (NUL-terminated, truncated to
  * name_len), number of launches and total milliseconds. PCMS_ERR_INVALID_ARG if out of range. */

@@ -302,8 +302,8 @@ pcms_status pcms_locate_interp(pcms_mesh mesh, const double* tgt_pts, int64_t n_
     });
 }
 
-pcms_status pcms_trace_enable(int on) {
-    pcms::trace_enable(on);
+pcms_status pcms_trace_enable(int mode) {
+    pcms::trace_enable(mode);
     return PCMS_OK;
 }
 

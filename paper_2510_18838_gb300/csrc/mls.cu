@@ -11,8 +11,14 @@ namespace {
 
 constexpr int64_t MAX_CELLS = int64_t(1) << 24;
 constexpr double TAU_FP64 = 1e-14;   // (1e-7)^2: column-angle rank test of the definition
-constexpr double TAU_MIXED = 1e-5;   // FP32-assembled pivots below this go to FP64
-constexpr double TAU_COMP = 1e-9;    // compensated-FP32 pivots below this go to FP64
+constexpr double TAU_MIXED = 1e-5;   // plain-FP32 pivots below this go to the next tier
+constexpr double TAU_BK = 1e-7;      // blocked-compensated pivots below this go on (noise ~1e-8)
+
+// stored moment type of a first-pass assembly
+int mom_kind(bool mixed, int mode, int G) {
+    return !mixed ? MOM_F64 : (assembles_bk(mixed, mode, G) ? MOM_F32PAIR : MOM_F32);
+}
+size_t mom_elem_bytes(int kind) { return kind == MOM_F32 ? sizeof(float) : sizeof(double); }
 
 int asm_blocks(int64_t nwork, int G) {
     int64_t groups_per_block = 8 * (32 / G);
@@ -65,6 +71,32 @@ __global__ void k_permute_field(const T* __restrict__ f, const int32_t* __restri
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         fs[inv[i]] = f[i];
+}
+
+// sum of the neighbour counts of the targets on a list (tracing only: pairs per tier)
+__global__ void k_list_pairs(const int32_t* __restrict__ list, const int32_t* __restrict__ n_list,
+                             const int32_t* __restrict__ counts, unsigned long long* out) {
+    unsigned long long s = 0;
+    const int64_t n = *n_list;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        s += (unsigned long long)counts[list[i]];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+void trace_list_pairs(const char* name, const int32_t* list, const int32_t* n_list,
+                      const int32_t* counts, int64_t n, cudaStream_t s) {
+    if (!trace_timing() || n <= 0) return;
+    DBuf acc(sizeof(unsigned long long), s);
+    PCMS_CU(cudaMemsetAsync(acc.p, 0, acc.bytes, s));
+    k_list_pairs<<<thread_blocks(n, 256), 256, 0, s>>>(list, n_list, counts,
+                                                       acc.as<unsigned long long>());
+    PCMS_LAUNCH_CHECK("k_list_pairs");
+    unsigned long long h = 0;
+    PCMS_CU(cudaMemcpyAsync(&h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PCMS_CU(cudaStreamSynchronize(s));
+    trace_count(name, (int64_t)h);
 }
 
 struct BoxResult {
@@ -125,17 +157,20 @@ int accp(int dim, int deg, int mode) {
 }
 
 // Solve the tier-1 systems already assembled in sa.mom, then re-assemble and solve the
-// targets the solve hands on: tier 2 (compensated FP32) and tier 3 (FP64). `a` holds the
-// assembly arguments of tier 1 (mode-specific fields set). Mixed path only syncs to size the
-// tier-2/3 work; the FP64 path has a single tier.
+// targets the solve hands on: tier 2 (blocked-compensated FP32, 32 lanes, re-centred basis
+// when lambda = 0) and tier 3 (FP64). `a` holds the assembly arguments of tier 1
+// (mode-specific fields set). The mixed path syncs to size the tier-2/3 work; the FP64 path
+// has a single tier. rc: MAP only, per-target basis of re-centred operator rows.
 void solve_tiers(int dim, int deg, int mode, bool mixed, int G, const AsmArgs& a,
-                 SolveArgs sa, int64_t nt, cudaStream_t s) {
+                 SolveArgs sa, int64_t nt, float4* rc, cudaStream_t s) {
     const int np = accp(dim, deg, mode);
+    const int mk1 = mom_kind(mixed, mode, G);
     DBuf lists(sizeof(int32_t) * (2 * nt + 2), s);
     int32_t* list2 = lists.as<int32_t>();
     int32_t* list3 = list2 + nt;
     int32_t* n2 = list2 + 2 * nt;
     int32_t* n3 = n2 + 1;
+    DBuf basis2(mixed ? sizeof(float4) * nt : 0, s);
     PCMS_CU(cudaMemsetAsync(n2, 0, 2 * sizeof(int32_t), s));
     sa.list2 = list2;
     sa.n2 = n2;
@@ -143,45 +178,63 @@ void solve_tiers(int dim, int deg, int mode, bool mixed, int G, const AsmArgs& a
     sa.n3 = n3;
     sa.tier = mixed ? 1 : 3;
     sa.group = G;
-    sa.tau = mixed ? TAU_MIXED : TAU_FP64;
-    solve_any(dim, deg, mode, !mixed, sa, thread_blocks(nt, 128), s);
+    sa.acc = mk1 == MOM_F32PAIR ? ACC_BK : ACC_PLAIN;
+    sa.recentre = mixed && deg >= 1 && sa.lambda == 0.0;
+    sa.tau = !mixed ? TAU_FP64 : (sa.acc == ACC_BK ? TAU_BK : TAU_MIXED);
+    sa.basis_in = nullptr;
+    sa.basis2 = mixed ? basis2.as<float4>() : nullptr;
+    sa.rc = rc;
+    solve_any(dim, deg, mode, mk1, sa, thread_blocks(nt, 128), s);
     if (!mixed) return;
     int32_t cnt[2] = {0, 0};
     PCMS_CU(cudaMemcpyAsync(cnt, n2, sizeof(cnt), cudaMemcpyDeviceToHost, s));
     PCMS_CU(cudaStreamSynchronize(s));
     trace_count("mls_tier1_targets", nt - cnt[0] - cnt[1]);
     trace_count("mls_tier2_targets", cnt[0]);
+    trace_list_pairs(mode == MODE_FUSED ? "mls_fused_tier2_pairs" : "mls_map_tier2_pairs", list2,
+                     n2, sa.counts, cnt[0], s);
     if (cnt[0] > 0) {
-        DBuf mom2(sizeof(double) * np * cnt[0], s);
+        DBuf mom2(sizeof(float2) * np * cnt[0], s);
         AsmArgs a2 = a;
         a2.list = list2;
         a2.n_list = n2;
         a2.mom = mom2.p;
+        a2.basis = basis2.as<float4>();
         if (mode == MODE_FUSED) {
             a2.kexp_in = a.kexp_out ? a.kexp_out : a.kexp_in;
             a2.kexp_out = nullptr;
+        } else {
+            a2.cols = nullptr;   // the operator's columns are already written
         }
-        assemble_comp_any(dim, deg, mode, G, a2, asm_blocks(cnt[0], G), s);
+        assemble_any(dim, deg, true, mode, 32, false, a2, asm_blocks(cnt[0], 32), s);
         SolveArgs s2 = sa;
         s2.list = list2;
         s2.n_list = n2;
         s2.mom = mom2.p;
         s2.tier = 2;
-        s2.tau = TAU_COMP;
-        solve_any(dim, deg, mode, true, s2, thread_blocks(cnt[0], 128), s);
+        s2.acc = ACC_BK;
+        s2.tau = TAU_BK;
+        s2.basis_in = basis2.as<float4>();
+        s2.basis2 = nullptr;
+        solve_any(dim, deg, mode, MOM_F32PAIR, s2, thread_blocks(cnt[0], 128), s);
         PCMS_CU(cudaMemcpyAsync(&cnt[1], n3, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         PCMS_CU(cudaStreamSynchronize(s));
     }
     trace_count("mls_tier3_targets", cnt[1]);
+    trace_list_pairs(mode == MODE_FUSED ? "mls_fused_tier3_pairs" : "mls_map_tier3_pairs", list3,
+                     n3, sa.counts, cnt[1], s);
     if (cnt[1] > 0) {
         DBuf mom3(sizeof(double) * np * cnt[1], s);
         AsmArgs a3 = a;
         a3.list = list3;
         a3.n_list = n3;
         a3.mom = mom3.p;
+        a3.basis = nullptr;
         if (mode == MODE_FUSED) {
             a3.kexp_in = a.kexp_out ? a.kexp_out : a.kexp_in;
             a3.kexp_out = nullptr;
+        } else {
+            a3.cols = nullptr;
         }
         assemble_any(dim, deg, false, mode, G, false, a3, asm_blocks(cnt[1], G), s);
         SolveArgs s3 = sa;
@@ -189,8 +242,11 @@ void solve_tiers(int dim, int deg, int mode, bool mixed, int G, const AsmArgs& a
         s3.n_list = n3;
         s3.mom = mom3.p;
         s3.tier = 3;
+        s3.acc = ACC_PLAIN;
         s3.tau = TAU_FP64;
-        solve_any(dim, deg, mode, true, s3, thread_blocks(cnt[1], 128), s);
+        s3.basis_in = nullptr;
+        s3.basis2 = nullptr;
+        solve_any(dim, deg, mode, MOM_F64, s3, thread_blocks(cnt[1], 128), s);
     }
 }
 
@@ -223,7 +279,8 @@ int64_t estimate_mls_bytes(const MlsParams& P, int64_t ns, int64_t nt, int nf, b
     b += ns * (4.0 + 4.0 + 8.0 * d + (mixed ? 24.0 : 0.0) + 12.0);   // sorted sources + sort scratch
     b += nt * (4.0 + 4.0 + 8.0 * d + 12.0);                          // sorted targets + scratch
     b += nt * (4.0 + 4.0 + 1.0 + 8.0 + 4.0);                         // counts, kexp, status, offsets, redo
-    b += nt * (np * elem + P.m * 8.0);                               // moments, y
+    b += nt * (np * 8.0 + P.m * 8.0);                                // moments, y
+    if (mixed) b += nt * 32.0;                                       // tier-2 bases
     const double nnz = 1.2 * k * nt;
     if (keep_map || nf > 2) b += nnz * (4.0 + elem);                 // operator
     b += (double)(ns + nt) * std::max(nf, 1) * elem * 2.0;           // apply/permute scratch
@@ -277,9 +334,10 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
 
     if (nt > 0) {
         const int np = accp(dim, deg, MODE_MAP);
-        DBuf mom((mixed ? sizeof(float) : sizeof(double)) * np * nt, s);
+        DBuf mom(mom_elem_bytes(mom_kind(mixed, MODE_MAP, G)) * np * nt, s);
         DBuf y(sizeof(double) * m * nt, s);
         DBuf flags(sizeof(int8_t) * nt, s);
+        DBuf rc(mixed ? sizeof(float4) * nt : 0, s);
         a.kexp_in = M.kexp.as<int32_t>();
         a.kexp_out = nullptr;
         a.offsets = M.offsets.as<int64_t>();
@@ -295,10 +353,11 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
         sa.y = y.as<double>();
         sa.flags = mixed ? flags.as<int8_t>() : nullptr;
         sa.status = M.status.as<int8_t>();
-        solve_tiers(dim, deg, MODE_MAP, mixed, G, a, sa, nt, s);
+        solve_tiers(dim, deg, MODE_MAP, mixed, G, a, sa, nt, mixed ? rc.as<float4>() : nullptr, s);
 
         ShapeArgs sh{};
         sh.flags = mixed ? flags.as<int8_t>() : nullptr;
+        sh.rc = mixed ? rc.as<float4>() : nullptr;
         sh.g = M.g;
         sh.ns = ns;
         sh.nt = nt;
@@ -403,7 +462,7 @@ void mls_transfer(const MlsParams& P, const double* src, int64_t ns, const doubl
     DBuf counts(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
     DBuf kexp(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
     const int np = accp(dim, deg, MODE_FUSED);
-    DBuf mom(fsz * np * std::max<int64_t>(nt, 1), s);
+    DBuf mom(mom_elem_bytes(mom_kind(mixed, MODE_FUSED, G)) * np * std::max<int64_t>(nt, 1), s);
     for (int f = 0; f < nf; f++) {
         if (ns > 0) {
             PCMS_TRACE("mls_field_to_sorted", s);
@@ -431,7 +490,7 @@ void mls_transfer(const MlsParams& P, const double* src, int64_t ns, const doubl
         sa.out = (char*)out + fsz * (size_t)f * nt;
         sa.out_is_double = !mixed;
         sa.status = f == 0 ? status : nullptr;
-        solve_tiers(dim, deg, MODE_FUSED, mixed, G, a, sa, nt, s);
+        solve_tiers(dim, deg, MODE_FUSED, mixed, G, a, sa, nt, nullptr, s);
     }
     if (status && P.min_neighbors == 0 && nt > 0) {
         DBuf st(sizeof(unsigned long long) * 4, s);

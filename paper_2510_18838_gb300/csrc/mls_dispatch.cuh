@@ -12,37 +12,43 @@ namespace pcms {
 #define PCMS_DECLARE_MLS_DISPATCH(DIMV)                                                       \
     void assemble_dispatch_d##DIMV(int deg, bool mixed, int mode, int G, bool field_double,   \
                                    const AsmArgs& a, int blocks, cudaStream_t s);             \
-    void solve_dispatch_d##DIMV(int deg, int mode, bool mom_double, const SolveArgs& a,       \
+    void solve_dispatch_d##DIMV(int deg, int mode, int mom_kind, const SolveArgs& a,          \
                                 int blocks, cudaStream_t s);                                  \
     void shape_dispatch_d##DIMV(int deg, bool mixed, int G, const ShapeArgs& a, int blocks,   \
-                                cudaStream_t s);                                              \
-    void assemble_comp_dispatch_d##DIMV(int deg, int mode, int G, const AsmArgs& a,            \
-                                        int blocks, cudaStream_t s);
+                                cudaStream_t s);
 PCMS_DECLARE_MLS_DISPATCH(2)
 PCMS_DECLARE_MLS_DISPATCH(3)
 
-// compensated FP32 assembly (mixed precision, tier 2), MODE_MAP or MODE_FUSED
-inline void assemble_comp_any(int dim, int deg, int mode, int G, const AsmArgs& a, int blocks,
-                              cudaStream_t s) {
-    PCMS_TRACE(mode == MODE_FUSED ? "mls_assemble_fused_comp" : "mls_assemble_map_comp", s);
-    if (dim == 2) assemble_comp_dispatch_d2(deg, mode, G, a, blocks, s);
-    else assemble_comp_dispatch_d3(deg, mode, G, a, blocks, s);
+// stored moment types of the solve
+enum { MOM_F32 = 0, MOM_F32PAIR = 1, MOM_F64 = 2 };
+
+// Mixed MAP/FUSED assembly with 32 lanes per target uses blocked compensation (ACC_BK,
+// float2 moments): tier 1 of large neighbourhoods, and tier 2 (a target list). Everything
+// else accumulates plainly (float moments on the mixed path, double on the FP64 path).
+inline bool assembles_bk(bool mixed, int mode, int G) {
+    return mixed && mode != MODE_COUNT && G == 32;
 }
 
 inline void assemble_any(int dim, int deg, bool mixed, int mode, int G, bool fd,
                          const AsmArgs& a, int blocks, cudaStream_t s) {
-    static const char* names[2][3] = {
+    // a target list means a later tier of the mixed path (tier 2: blocked FP32, tier 3: FP64)
+    static const char* names[5][3] = {
         {"mls_count_fp64", "mls_assemble_map_fp64", "mls_assemble_fused_fp64"},
-        {"mls_count_mixed", "mls_assemble_map_mixed", "mls_assemble_fused_mixed"}};
-    PCMS_TRACE(names[mixed ? 1 : 0][mode], s);
+        {"mls_count_mixed", "mls_assemble_map_mixed", "mls_assemble_fused_mixed"},
+        {"mls_count_mixed", "mls_assemble_map_bk", "mls_assemble_fused_bk"},
+        {"mls_count_mixed", "mls_assemble_map_tier2", "mls_assemble_fused_tier2"},
+        {"mls_count_fp64", "mls_assemble_map_tier3", "mls_assemble_fused_tier3"}};
+    const int row = !mixed ? (a.list ? 4 : 0)
+                           : (!assembles_bk(mixed, mode, G) ? 1 : (a.list ? 3 : 2));
+    PCMS_TRACE(names[row][mode], s);
     if (dim == 2) assemble_dispatch_d2(deg, mixed, mode, G, fd, a, blocks, s);
     else assemble_dispatch_d3(deg, mixed, mode, G, fd, a, blocks, s);
 }
-inline void solve_any(int dim, int deg, int mode, bool md, const SolveArgs& a, int blocks,
+inline void solve_any(int dim, int deg, int mode, int mom_kind, const SolveArgs& a, int blocks,
                       cudaStream_t s) {
     PCMS_TRACE(mode == MODE_FUSED ? "mls_solve_fused" : "mls_solve_map", s);
-    if (dim == 2) solve_dispatch_d2(deg, mode, md, a, blocks, s);
-    else solve_dispatch_d3(deg, mode, md, a, blocks, s);
+    if (dim == 2) solve_dispatch_d2(deg, mode, mom_kind, a, blocks, s);
+    else solve_dispatch_d3(deg, mode, mom_kind, a, blocks, s);
 }
 inline void shape_any(int dim, int deg, bool mixed, int G, const ShapeArgs& a, int blocks,
                       cudaStream_t s) {
@@ -63,15 +69,16 @@ inline void shape_any(int dim, int deg, bool mixed, int G, const ShapeArgs& a, i
             if (G == 32) k_assemble<DIMV, 0, MIXED, MODE_COUNT, 32, float><<<b, 256, 0, s>>>(a); \
             else k_assemble<DIMV, 0, MIXED, MODE_COUNT, 8, float><<<b, 256, 0, s>>>(a);       \
         } else if (mode == MODE_MAP) {                                                        \
-            if (G == 32) k_assemble<DIMV, DEG, MIXED, MODE_MAP, 32, float><<<b, 256, 0, s>>>(a); \
+            if (G == 32) k_assemble<DIMV, DEG, MIXED, MODE_MAP, 32, float, MIXED ? ACC_BK : ACC_PLAIN><<<b, 256, 0, s>>>(a); \
             else k_assemble<DIMV, DEG, MIXED, MODE_MAP, 8, float><<<b, 256, 0, s>>>(a);       \
         } else {                                                                              \
             if (fd) {                                                                         \
-                if (MIXED) return;                                                            \
-                if (G == 32) k_assemble<DIMV, DEG, MIXED, MODE_FUSED, 32, double><<<b, 256, 0, s>>>(a); \
-                else k_assemble<DIMV, DEG, MIXED, MODE_FUSED, 8, double><<<b, 256, 0, s>>>(a); \
+                if constexpr (!MIXED) {                                                       \
+                    if (G == 32) k_assemble<DIMV, DEG, MIXED, MODE_FUSED, 32, double><<<b, 256, 0, s>>>(a); \
+                    else k_assemble<DIMV, DEG, MIXED, MODE_FUSED, 8, double><<<b, 256, 0, s>>>(a); \
+                }                                                                             \
             } else {                                                                          \
-                if (G == 32) k_assemble<DIMV, DEG, MIXED, MODE_FUSED, 32, float><<<b, 256, 0, s>>>(a); \
+                if (G == 32) k_assemble<DIMV, DEG, MIXED, MODE_FUSED, 32, float, MIXED ? ACC_BK : ACC_PLAIN><<<b, 256, 0, s>>>(a); \
                 else k_assemble<DIMV, DEG, MIXED, MODE_FUSED, 8, float><<<b, 256, 0, s>>>(a);  \
             }                                                                                 \
         }                                                                                     \
@@ -90,28 +97,22 @@ inline void shape_any(int dim, int deg, bool mixed, int G, const ShapeArgs& a, i
         }                                                                                     \
         PCMS_LAUNCH_CHECK("k_assemble");                                                      \
     }                                                                                         \
-    void solve_dispatch_d##DIMV(int deg, int mode, bool md, const SolveArgs& a, int b,          \
+    template <int DEG, int MODE>                                                              \
+    static void solve_deg(int mk, const SolveArgs& a, int b, cudaStream_t s) {                \
+        if (mk == MOM_F64) k_solve<DIMV, DEG, MODE, double><<<b, 128, 0, s>>>(a);            \
+        else if (mk == MOM_F32PAIR) k_solve<DIMV, DEG, MODE, float2><<<b, 128, 0, s>>>(a);   \
+        else k_solve<DIMV, DEG, MODE, float><<<b, 128, 0, s>>>(a);                           \
+    }                                                                                         \
+    void solve_dispatch_d##DIMV(int deg, int mode, int mk, const SolveArgs& a, int b,           \
                               cudaStream_t s) {                                               \
         if (mode == MODE_FUSED) {                                                             \
-            if (md) {                                                                         \
-                if (deg == 0) k_solve<DIMV, 0, MODE_FUSED, double><<<b, 128, 0, s>>>(a);     \
-                else if (deg == 1) k_solve<DIMV, 1, MODE_FUSED, double><<<b, 128, 0, s>>>(a); \
-                else k_solve<DIMV, 2, MODE_FUSED, double><<<b, 128, 0, s>>>(a);              \
-            } else {                                                                          \
-                if (deg == 0) k_solve<DIMV, 0, MODE_FUSED, float><<<b, 128, 0, s>>>(a);      \
-                else if (deg == 1) k_solve<DIMV, 1, MODE_FUSED, float><<<b, 128, 0, s>>>(a); \
-                else k_solve<DIMV, 2, MODE_FUSED, float><<<b, 128, 0, s>>>(a);               \
-            }                                                                                 \
+            if (deg == 0) solve_deg<0, MODE_FUSED>(mk, a, b, s);                              \
+            else if (deg == 1) solve_deg<1, MODE_FUSED>(mk, a, b, s);                         \
+            else solve_deg<2, MODE_FUSED>(mk, a, b, s);                                       \
         } else {                                                                              \
-            if (md) {                                                                         \
-                if (deg == 0) k_solve<DIMV, 0, MODE_MAP, double><<<b, 128, 0, s>>>(a);       \
-                else if (deg == 1) k_solve<DIMV, 1, MODE_MAP, double><<<b, 128, 0, s>>>(a);  \
-                else k_solve<DIMV, 2, MODE_MAP, double><<<b, 128, 0, s>>>(a);                \
-            } else {                                                                          \
-                if (deg == 0) k_solve<DIMV, 0, MODE_MAP, float><<<b, 128, 0, s>>>(a);        \
-                else if (deg == 1) k_solve<DIMV, 1, MODE_MAP, float><<<b, 128, 0, s>>>(a);   \
-                else k_solve<DIMV, 2, MODE_MAP, float><<<b, 128, 0, s>>>(a);                 \
-            }                                                                                 \
+            if (deg == 0) solve_deg<0, MODE_MAP>(mk, a, b, s);                                \
+            else if (deg == 1) solve_deg<1, MODE_MAP>(mk, a, b, s);                           \
+            else solve_deg<2, MODE_MAP>(mk, a, b, s);                                         \
         }                                                                                     \
         PCMS_LAUNCH_CHECK("k_solve");                                                         \
     }                                                                                         \
@@ -139,22 +140,5 @@ inline void shape_any(int dim, int deg, bool mixed, int G, const ShapeArgs& a, i
             }                                                                                 \
         }                                                                                     \
         PCMS_LAUNCH_CHECK("k_shape");                                                         \
-    }                                                                                         \
-    template <int DEG>                                                                        \
-    static void comp_mode(int mode, int G, const AsmArgs& a, int b, cudaStream_t s) {         \
-        if (mode == MODE_MAP) {                                                               \
-            if (G == 32) k_assemble<DIMV, DEG, true, MODE_MAP, 32, float, true><<<b, 256, 0, s>>>(a); \
-            else k_assemble<DIMV, DEG, true, MODE_MAP, 8, float, true><<<b, 256, 0, s>>>(a);  \
-        } else {                                                                              \
-            if (G == 32) k_assemble<DIMV, DEG, true, MODE_FUSED, 32, float, true><<<b, 256, 0, s>>>(a); \
-            else k_assemble<DIMV, DEG, true, MODE_FUSED, 8, float, true><<<b, 256, 0, s>>>(a); \
-        }                                                                                     \
-    }                                                                                         \
-    void assemble_comp_dispatch_d##DIMV(int deg, int mode, int G, const AsmArgs& a, int b,    \
-                                        cudaStream_t s) {                                     \
-        if (deg == 0) comp_mode<0>(mode, G, a, b, s);                                         \
-        else if (deg == 1) comp_mode<1>(mode, G, a, b, s);                                    \
-        else comp_mode<2>(mode, G, a, b, s);                                                  \
-        PCMS_LAUNCH_CHECK("k_assemble_comp");                                                 \
     }                                                                                         \
     }

@@ -17,7 +17,8 @@
 //                  selected pairs through a shared-memory ring so the accumulation runs
 //                  on full lanes, reduces the moments across the group and writes them.
 //   k_solve     -- one thread per target: FP64 LDL^T of G with a pivot guard, then
-//                  y = G^-1 e_1 (operator) or c_0 = e_1^T G^-1 g (one-shot transfer).
+//                  y = G^-1 e_1 (operator) or c_0 = e_1^T G^-1 g (one-shot transfer), and
+//                  the routing of the mixed path's precision tiers (below).
 //   k_shape     -- a group per target recomputes w_j a(u_j) and writes N_j.
 #pragma once
 
@@ -26,6 +27,18 @@
 namespace pcms {
 
 enum { MODE_COUNT = 0, MODE_MAP = 1, MODE_FUSED = 2 };
+
+// How a group accumulates its moments.
+//   ACC_PLAIN  one running sum per lane (FP32 on the mixed path, FP64 on the FP64 path),
+//              lanes reduced in the same type.
+//   ACC_BK     mixed path, blocked compensation: each lane adds BK_BLOCK selected pairs
+//              into a plain FP32 block sum, then adds the block sum into a Kahan-compensated
+//              FP32 total; lanes are reduced error-free (two-sum) and each moment is written
+//              as an unevaluated FP32 pair (hi, lo). Everything stays on the FP32 pipe; the
+//              summation error no longer grows with the neighbour count, so what is left is
+//              the rounding of the individual terms, which averages out like 1/sqrt(n).
+enum { ACC_PLAIN = 0, ACC_BK = 1 };
+constexpr int BK_BLOCK = 4;
 
 constexpr float MIX_BAND = 1.52587890625e-05f;   // 2^-16 relative band around r^2
 constexpr int MAX_DOUBLINGS = 60;
@@ -49,20 +62,35 @@ struct AsmArgs {
     const int64_t* offsets;  // MAP
     int32_t* cols;           // MAP
     const void* field;       // FUSED: sorted field (float or double)
-    void* mom;               // MAP/FUSED: [nt][NACCP]
+    void* mom;               // MAP/FUSED: [nt][NACCP] (float, float2 for ACC_BK, or double)
+    const float4* basis;     // ACC_BK list mode: per list position (c_x, c_y, c_z, 1/s), or null
     unsigned* err;
 };
 
 // Precision tiers of the mixed path. The FP64 solve of a tier-1 system estimates how much
-// the FP32 assembly error can move c_0 and hands sensitive targets to the next tier:
-//   tier 1  plain FP32 accumulation      accepted if amp * (1 + sqrt(n / (3 G^2))) <= AMP_T1
-//   tier 2  compensated FP32 (Kahan)     accepted if amp <= AMP_T2 * max(1, sqrt(n / 1000))
-//   tier 3  FP64 assembly                final (pivot guard TAU_FP64 only)
+// the FP32 assembly error can move c_0 (amp, below) and hands sensitive targets on:
+//   tier 1  plain FP32 (8-lane groups)      accepted if amp * (1 + sqrt(n / (3 G^2))) <= AMP_T1
+//           blocked compensation (32 lanes) accepted if amp <= AMP_BK * sqrt(n)
+//   tier 2  blocked compensation in a re-centred, re-scaled basis (lambda = 0; see below),
+//           accepted if amp' <= AMP_BK * sqrt(n)
+//   tier 3  FP64 assembly                   final (pivot guard TAU_FP64 only)
 // A failed pivot guard in tier 1 or 2 also goes to tier 3. The bounds keep the estimated
-// error of c_0 several times below 2e-5 (calibrated on emulated FP32 arithmetic: plain sums
-// ~ amp * 6e-8 * (1 + sqrt(n / 3G^2)), compensated sums ~ amp * (2e-8 .. 1.5e-7) / sqrt(n)).
+// error of c_0 several times below 2e-5. They are calibrated on emulated FP32 arithmetic
+// over the 2D Gaussian-mixture targets (field of unit size):
+//   plain sums          err ~ amp * 6e-8 * (1 + sqrt(n / 3G^2));
+//   blocked compensated err <= 3.4 * amp * 6e-8 / sqrt(n) (largest over 500 targets with
+//                       up to 5e5 neighbours), so AMP_BK = 32 leaves a factor 3.
+//
+// Re-centred basis. Far targets (radius doubled until min_neighbors sources are inside)
+// often see their neighbours on one side, at offsets u = (s - t)/r of size ~1 with a small
+// spread. In the target-centred basis the normal equations are then badly scaled and amp is
+// large, although the fit itself is not sensitive. At lambda = 0 the MLS value does not
+// depend on the basis of the polynomial space, so tier 2 uses u' = (u - c)/s with c the
+// weighted centroid and s the weighted spread of the tier-1 neighbours, and evaluates the
+// fitted polynomial at u'_t = -c/s: G' y = a(u'_t), c_0 = y^T g'. (c, 1/s) are rounded to
+// FP32 once and define the basis exactly for assembly, solve and operator rows.
 constexpr double AMP_T1 = 64.0;
-constexpr double AMP_T2 = 2048.0;
+constexpr double AMP_BK = 32.0;
 constexpr double AMP_SHAPE = 32.0;   // operator rows above this are evaluated in FP64
 
 struct SolveArgs {
@@ -75,12 +103,17 @@ struct SolveArgs {
     double tau;               // pivot guard: d_k <= tau * G_kk fails
     int tier;                 // 1, 2 (mixed) or 3 (FP64)
     int group;                // lanes per target of the assembly (error model)
+    int acc;                  // ACC_PLAIN or ACC_BK: how these moments were accumulated
+    int recentre;             // tier 1 -> 2: hand on a re-centred basis (lambda = 0, degree >= 1)
+    const float4* basis_in;   // tier 2: basis of these moments, per list position
+    float4* basis2;           // tier 1: basis for tier 2, per list2 position
+    float4* rc;               // MAP: basis of the accepted tier-2 rows, per sorted target
     int32_t* list2;           // targets for tier 2 / tier 3
     int32_t* n2;
     int32_t* list3;
     int32_t* n3;
     double* y;                // MAP: [nt][m]
-    int8_t* flags;            // MAP: 1 = evaluate the operator row in FP64
+    int8_t* flags;            // MAP: how to evaluate the operator row (k_shape)
     int8_t* status;           // MAP: sorted order; FUSED: caller order (via perm) or null
     const int32_t* perm_t;    // FUSED: sorted -> caller target index
     void* out;                // FUSED: caller-order output (float or double)
@@ -98,7 +131,8 @@ struct ShapeArgs {
     const int64_t* offsets;
     const int32_t* cols;
     const double* y;
-    const int8_t* flags;   // per target: 1 = evaluate in FP64 (mixed maps), or null
+    const int8_t* flags;   // per target (mixed maps), or null: see k_shape
+    const float4* rc;      // per target: re-centred basis of flag-3 rows
     double radius;
     int weight;
     void* vals;
@@ -208,7 +242,7 @@ __device__ __forceinline__ int unpack_index(double v) { return (int)v; }
 
 template <typename T> struct QEntry;
 template <> struct QEntry<float> { using type = float4; };
-template <> struct QEntry<double> { using type = double4; };
+template <> struct QEntry<double> { using type = double4_32a; };
 
 template <typename T>
 __device__ __forceinline__ typename QEntry<T>::type make_entry(T a, T b, T c, T d);
@@ -217,8 +251,8 @@ __device__ __forceinline__ float4 make_entry<float>(float a, float b, float c, f
     return make_float4(a, b, c, d);
 }
 template <>
-__device__ __forceinline__ double4 make_entry<double>(double a, double b, double c, double d) {
-    return make_double4(a, b, c, d);
+__device__ __forceinline__ double4_32a make_entry<double>(double a, double b, double c, double d) {
+    return make_double4_32a(a, b, c, d);
 }
 
 // accumulate one selected pair: dx (target-relative offsets), payload b (field value)
@@ -231,12 +265,32 @@ __host__ __device__ __forceinline__ void kahan_add(T& s, T& c, T x) {
     s = t;
 }
 
-// COMP = true: every accumulator is a compensated (Kahan) sum; acc holds the sums and cmp
-// their compensations.
-template <int DIM, int DEG, int MODE, typename T, int NACC, bool COMP = false>
-__host__ __device__ __forceinline__ void accumulate(T (&acc)[NACC > 0 ? NACC : 1],
-                                                    T (&cmp)[NACC > 0 ? NACC : 1], const T* dx,
-                                                    T b, int kind, T inv_r) {
+// Error-free sum of two FP32 values (Knuth's TwoSum): s + e == a + b exactly.
+__host__ __device__ __forceinline__ void two_sum32(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Offsets u = dx / r of one selected pair in the assembly basis: target-centred, or with
+// bc = {c_x, c_y, c_z, 1/s} the re-centred basis u' = (u - c) / s.
+template <int DIM, typename T>
+__host__ __device__ __forceinline__ void basis_offsets(const T* dx, T inv_r, const T* bc, T* u) {
+    u[0] = dx[0] * inv_r;
+    u[1] = dx[1] * inv_r;
+    u[2] = DIM == 3 ? dx[2] * inv_r : T(0);
+    if (bc) {
+#pragma unroll
+        for (int d = 0; d < DIM; d++) u[d] = (u[d] - bc[d]) * bc[3];
+    }
+}
+
+// Adds one selected pair to the running sums: moments w u^p of degree <= 2k, and in fused
+// mode the right-hand side w b u^p of degree <= k. dx = target-relative offsets (the weight
+// is always a function of |dx| / r), b = field value, bc = re-centred basis or null.
+template <int DIM, int DEG, int MODE, typename T, int NACC>
+__host__ __device__ __forceinline__ void accumulate(T (&acc)[NACC > 0 ? NACC : 1], const T* dx,
+                                                    T b, int kind, T inv_r, const T* bc) {
     constexpr int NM = mono_count(DIM, 2 * DEG);
     constexpr int M = mono_count(DIM, DEG);
     T d2 = dx[0] * dx[0] + dx[1] * dx[1];
@@ -250,46 +304,55 @@ __host__ __device__ __forceinline__ void accumulate(T (&acc)[NACC > 0 ? NACC : 1
 #endif
     T w = weight_value<T>(kind, q);
     T u[3];
-    u[0] = dx[0] * inv_r;
-    u[1] = dx[1] * inv_r;
-    u[2] = DIM == 3 ? dx[2] * inv_r : T(0);
+    basis_offsets<DIM, T>(dx, inv_r, bc, u);
     T wm[NM];
     wm[0] = w;
-    if constexpr (COMP) kahan_add(acc[0], cmp[0], w);
-    else acc[0] += w;
+    acc[0] += w;
     sfor<NM - 1>([&](auto I) {
         constexpr int p = decltype(I)::value + 1;
         constexpr int par = mono_parent(DIM, p);
         constexpr int v = mono_var(DIM, p);
         wm[p] = wm[par] * u[v];
-        if constexpr (COMP) kahan_add(acc[p], cmp[p], wm[p]);
-        else acc[p] += wm[p];
+        acc[p] += wm[p];
     });
     if constexpr (MODE == MODE_FUSED) {
         T wb[M];
         wb[0] = w * b;
-        if constexpr (COMP) kahan_add(acc[NM], cmp[NM], wb[0]);
-        else acc[NM] += wb[0];
+        acc[NM] += wb[0];
         sfor<M - 1>([&](auto I) {
             constexpr int p = decltype(I)::value + 1;
             constexpr int par = mono_parent(DIM, p);
             constexpr int v = mono_var(DIM, p);
             wb[p] = wb[par] * u[v];
-            if constexpr (COMP) kahan_add(acc[NM + p], cmp[NM + p], wb[p]);
-            else acc[NM + p] += wb[p];
+            acc[NM + p] += wb[p];
         });
+    }
+}
+
+// Blocked compensation: the block sums acc are added into the Kahan totals (sum, cmp) and
+// cleared.
+template <int NACC>
+__host__ __device__ __forceinline__ void bk_flush(float (&acc)[NACC], float (&sum)[NACC],
+                                                  float (&cmp)[NACC]) {
+#pragma unroll
+    for (int i = 0; i < NACC; i++) {
+        kahan_add(sum[i], cmp[i], acc[i]);
+        acc[i] = 0.f;
     }
 }
 
 // ------------------------------------------------------------------------------------
 // k_assemble
 // ------------------------------------------------------------------------------------
-// COMP (mixed only): compensated FP32 accumulation, lanes reduced in FP64, moments written
-// as FP64 (used for the targets the mixed solve flags as sensitive).
-template <int DIM, int DEG, bool MIXED, int MODE, int G, typename FT, bool COMP = false>
+// Stored moment type: T for ACC_PLAIN, an unevaluated FP32 pair for ACC_BK.
+template <typename T, int ACC>
+using MomT = typename std::conditional<ACC == ACC_BK, float2, T>::type;
+
+template <int DIM, int DEG, bool MIXED, int MODE, int G, typename FT, int ACC = ACC_PLAIN>
 __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
+    static_assert(ACC == ACC_PLAIN || (MIXED && MODE != MODE_COUNT), "blocked compensation: mixed moments only");
     using T = typename std::conditional<MIXED, float, double>::type;
-    using MT = typename std::conditional<COMP, double, T>::type;   // stored moment type
+    using MT = MomT<T, ACC>;
     using QE = typename QEntry<T>::type;
     constexpr int NM = mono_count(DIM, 2 * DEG);
     constexpr int M = mono_count(DIM, DEG);
@@ -340,8 +403,24 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
             row_off = A.offsets[t];
             row_len = A.offsets[t + 1] - row_off;
         }
-        T acc[NACC > 0 ? NACC : 1];
-        T cmp[NACC > 0 ? NACC : 1];
+        // re-centred basis (blocked tier 2 only)
+        T bcv[4] = {T(0), T(0), T(0), T(1)};
+        const T* bc = nullptr;
+        if constexpr (ACC == ACC_BK) {
+            if (A.basis) {
+                const float4 bb = A.basis[wk];
+                bcv[0] = bb.x;
+                bcv[1] = bb.y;
+                bcv[2] = bb.z;
+                bcv[3] = bb.w;
+                bc = bcv;
+            }
+        }
+        constexpr int NA = NACC > 0 ? NACC : 1;
+        constexpr int NB = ACC == ACC_BK ? NA : 1;   // Kahan totals (blocked compensation)
+        T acc[NA];
+        float sum[NB], cmp[NB];
+        int pops = 0;
         for (;;) {
             const double r = ldexp(A.radius, k);
             const double r2 = r * r;
@@ -362,10 +441,13 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
             const long long y0 = max((long long)floorf(fr[1] - RR), -ct[1]);
             const long long y1 = min((long long)floorf(fr[1] + RR), (long long)g.n[1] - 1 - ct[1]);
 #pragma unroll
-            for (int i = 0; i < (NACC > 0 ? NACC : 1); i++) {
-                acc[i] = T(0);
-                cmp[i] = T(0);
+            for (int i = 0; i < NA; i++) acc[i] = T(0);
+#pragma unroll
+            for (int i = 0; i < NB; i++) {
+                sum[i] = 0.f;
+                cmp[i] = 0.f;
             }
+            pops = 0;
             cnt = 0;
             int qn = 0, head = 0;
             int64_t written = 0;
@@ -453,9 +535,16 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
                             if (qn >= G) {
                                 QE e = q[(head + gl) & (QCAP - 1)];
                                 T edx[3] = {e.x, e.y, e.z};
-                                accumulate<DIM, DEG, MODE, T, NACC, COMP>(acc, cmp, edx, e.w, A.weight, inv_r);
+                                accumulate<DIM, DEG, MODE, T, NACC>(acc, edx, e.w, A.weight, inv_r, bc);
+                                if constexpr (ACC == ACC_BK) {
+                                    if (++pops == BK_BLOCK) {
+                                        bk_flush<NA>(acc, sum, cmp);
+                                        pops = 0;
+                                    }
+                                }
                                 if (MODE == MODE_MAP) {
-                                    if (written + gl < row_len) A.cols[row_off + written + gl] = unpack_index(e.w);
+                                    if (A.cols && written + gl < row_len)
+                                        A.cols[row_off + written + gl] = unpack_index(e.w);
                                     written += G;
                                 }
                                 head = (head + G) & (QCAP - 1);
@@ -469,8 +558,8 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
                     if (gl < qn) {
                         QE e = q[(head + gl) & (QCAP - 1)];
                         T edx[3] = {e.x, e.y, e.z};
-                        accumulate<DIM, DEG, MODE, T, NACC, COMP>(acc, cmp, edx, e.w, A.weight, inv_r);
-                        if (MODE == MODE_MAP && written + gl < row_len)
+                        accumulate<DIM, DEG, MODE, T, NACC>(acc, edx, e.w, A.weight, inv_r, bc);
+                        if (MODE == MODE_MAP && A.cols && written + gl < row_len)
                             A.cols[row_off + written + gl] = unpack_index(e.w);
                     }
                     __syncwarp(gmask);
@@ -482,24 +571,43 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
             }
             break;
         }
-        MT red[NACC > 0 ? NACC : 1];
+        MT red[NA];
+        if constexpr (ACC == ACC_BK) {
+            // the lane's total is sum - cmp; reduce the pairs (hi, lo) = (sum, -cmp) with
+            // TwoSum on the leading parts and plain sums of the trailing parts
+            bk_flush<NA>(acc, sum, cmp);
 #pragma unroll
-        for (int i = 0; i < (NACC > 0 ? NACC : 1); i++) {
-            if constexpr (COMP) red[i] = (double)acc[i] - (double)cmp[i];
-            else red[i] = acc[i];
-        }
-        if (NACC > 0) {
+            for (int i = 0; i < NA; i++) {
+                float hi = sum[i], lo = -cmp[i];
 #pragma unroll
-            for (int i = 0; i < (NACC > 0 ? NACC : 1); i++) {
+                for (int o = G / 2; o > 0; o >>= 1) {
+                    const float ho = __shfl_xor_sync(gmask, hi, o);
+                    const float lw = __shfl_xor_sync(gmask, lo, o);
+                    float s, e;
+                    two_sum32(hi, ho, s, e);
+                    lo = (lo + lw) + e;
+                    hi = s;
+                }
+                red[i] = make_float2(hi, lo);
+            }
+        } else {
 #pragma unroll
-                for (int o = G / 2; o > 0; o >>= 1) red[i] += __shfl_xor_sync(gmask, red[i], o);
+            for (int i = 0; i < NA; i++) {
+                red[i] = acc[i];
+                if (NACC > 0) {
+#pragma unroll
+                    for (int o = G / 2; o > 0; o >>= 1) red[i] += __shfl_xor_sync(gmask, red[i], o);
+                }
             }
         }
         if (gl == 0) {
             if (NACC > 0) {
                 MT* dst = (MT*)A.mom + (A.list ? wk : t) * NACCP;   // list mode: by list position
 #pragma unroll
-                for (int i = 0; i < NACCP; i++) dst[i] = i < NACC ? red[i < NACC ? i : 0] : MT(0);
+                for (int i = 0; i < NACCP; i++) {
+                    if (i < NACC) dst[i] = red[i < NACC ? i : 0];
+                    else dst[i] = MT{};
+                }
             }
             A.counts[t] = cnt;
             if (A.kexp_out) A.kexp_out[t] = k;
@@ -512,8 +620,10 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
 // per-target solve: G from the moments (+ lambda on the diagonal), LDL^T with the pivot
 // guard d_k > tau * G_kk for every k (d_k / G_kk = R_kk^2 / ||column k||^2 of the weighted
 // Vandermonde matrix), then
-//   y[0..m) = G^-1 e_1   (L w = e_1, z = D^-1 w, L^T y = z; the operator row is w a^T y)
-//   *c0     = y^T g = e_1^T G^-1 g   (MODE_FUSED; G is symmetric)
+//   y[0..m) = G^-1 a_t   (L w = a_t, z = D^-1 w, L^T y = z; the operator row is w a^T y)
+//   *c0     = y^T g = a_t^T G^-1 g   (MODE_FUSED; G is symmetric)
+// with a_t = a(u_t) the basis at the target: e_1 in the target-centred basis (at = null),
+// or a(-c/s) in a re-centred one.
 //   *amp    = sqrt(G_00) sum_k |y_k| sqrt(G_kk): how much relative perturbations of the
 //             moments are amplified in c_0 (1 for an orthogonal basis).
 // mom = [moments of degree <= 2k (graded-lex)] [g (FUSED only)]. Returns false when the
@@ -522,7 +632,7 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
 template <int DIM, int DEG, int MODE>
 __host__ __device__ __forceinline__ bool solve_moments(const double* mom, double lambda,
                                                        double tau, double* out, double* c0,
-                                                       double* amp) {
+                                                       double* amp, const double* at = nullptr) {
     constexpr int NM = mono_count(DIM, 2 * DEG);
     constexpr int M = mono_count(DIM, DEG);
     constexpr int NP = M * (M + 1) / 2;
@@ -564,7 +674,7 @@ __host__ __device__ __forceinline__ bool solve_moments(const double* mom, double
         double w[M], z[M];
         sfor<M>([&](auto K) {
             constexpr int k = decltype(K)::value;
-            double a = k == 0 ? 1.0 : 0.0;
+            double a = at ? at[k] : (k == 0 ? 1.0 : 0.0);
             sfor<k>([&](auto Jx) {
                 constexpr int j = decltype(Jx)::value;
                 a -= L[k * (k + 1) / 2 + j] * w[j];
@@ -595,6 +705,47 @@ __host__ __device__ __forceinline__ bool solve_moments(const double* mom, double
 // ------------------------------------------------------------------------------------
 // k_solve: one thread per target
 // ------------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ double mom_value(float v) { return (double)v; }
+__host__ __device__ __forceinline__ double mom_value(double v) { return v; }
+__host__ __device__ __forceinline__ double mom_value(float2 v) { return (double)v.x + (double)v.y; }
+
+__host__ __device__ __forceinline__ bool is_target_centred(float4 b) {
+    return b.x == 0.f && b.y == 0.f && b.z == 0.f && b.w == 1.f;
+}
+
+// Re-centred basis from target-centred moments (offsets in units of r): c = weighted
+// centroid, s = weighted root-mean-square distance from c per coordinate; returned as
+// (c, 1/s) rounded to FP32. Falls back to the target-centred basis when the spread is zero.
+template <int DIM>
+__host__ __device__ inline float4 recentre_basis(const double* mom) {
+    const double w0 = mom[0];
+    double c[3] = {0.0, 0.0, 0.0};
+    double var = 0.0;
+    sfor<DIM>([&](auto D) {
+        constexpr int d = decltype(D)::value;
+        constexpr int i1 = mono_index(DIM, d == 0, d == 1, d == 2);
+        constexpr int i2 = mono_index(DIM, 2 * (d == 0), 2 * (d == 1), 2 * (d == 2));
+        c[d] = mom[i1] / w0;
+        var += mom[i2] / w0 - c[d] * c[d];
+    });
+    const double s2 = var / DIM;
+    if (!(w0 > 0.0) || !(s2 > 1e-12)) return make_float4(0.f, 0.f, 0.f, 1.f);
+    return make_float4((float)c[0], (float)c[1], (float)c[2], (float)(1.0 / sqrt(s2)));
+}
+
+// a(u'_t), the basis at the target in the basis b: u'_t = (0 - c) / s with the FP32 (c, 1/s)
+template <int DIM, int DEG>
+__host__ __device__ inline void basis_at_target(float4 b, double* at) {
+    constexpr int M = mono_count(DIM, DEG);
+    const double ut[3] = {-(double)b.x * (double)b.w, -(double)b.y * (double)b.w,
+                          -(double)b.z * (double)b.w};
+    at[0] = 1.0;
+    sfor<M - 1>([&](auto I) {
+        constexpr int p = decltype(I)::value + 1;
+        at[p] = at[mono_parent(DIM, p)] * ut[mono_var(DIM, p)];
+    });
+}
+
 template <int DIM, int DEG, int MODE, typename MT>
 __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
     constexpr int NM = mono_count(DIM, 2 * DEG);
@@ -609,45 +760,60 @@ __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
         int st = PCMS_TARGET_OK;
         double val = 0.0, amp = 0.0;
         double y[M];
+        double mom[NACC];
+        float4 bas = make_float4(0.f, 0.f, 0.f, 1.f);
+        bool recentred = false;
         if (cnt < M) {
             st = PCMS_TARGET_UNDERDETERMINED;
         } else {
             const MT* src = (const MT*)S.mom + (S.list ? wk : t) * NACCP;
-            double mom[NACC];
 #pragma unroll
-            for (int i = 0; i < NACC; i++) mom[i] = (double)src[i];
-            if (!solve_moments<DIM, DEG, MODE>(mom, S.lambda, S.tau, y, &val, &amp))
+            for (int i = 0; i < NACC; i++) mom[i] = mom_value(src[i]);
+            double at[M];
+            if (S.basis_in) {
+                bas = S.basis_in[wk];
+                recentred = !is_target_centred(bas);
+                if (recentred) basis_at_target<DIM, DEG>(bas, at);
+            }
+            if (!solve_moments<DIM, DEG, MODE>(mom, S.lambda, S.tau, y, &val, &amp,
+                                               recentred ? at : nullptr))
                 st = PCMS_TARGET_ILL_CONDITIONED;
         }
         if (S.tier < 3 && st != PCMS_TARGET_UNDERDETERMINED) {
-            int next = 0;
-            if (st == PCMS_TARGET_ILL_CONDITIONED) {
-                next = 3;
-            } else {
-                // compensated sums leave the per-term product rounding, whose effect on c_0
-                // shrinks like 1/sqrt(n): the tier-2 bound grows with sqrt(n / 1000)
-                const double lim2 = AMP_T2 * fmax(1.0, sqrt((double)cnt / 1000.0));
-                if (S.tier == 1) {
+            bool ok = st == PCMS_TARGET_OK;
+            if (ok) {
+                const double n = (double)cnt;
+                if (S.acc == ACC_PLAIN) {
                     const double g = (double)S.group;
-                    const double risk = amp * (1.0 + sqrt((double)cnt / (3.0 * g * g)));
-                    if (risk > AMP_T1) next = amp > lim2 ? 3 : 2;
-                } else if (amp > lim2) {
-                    next = 3;
+                    ok = amp * (1.0 + sqrt(n / (3.0 * g * g))) <= AMP_T1;
+                } else {
+                    ok = amp <= AMP_BK * sqrt(n);
                 }
             }
-            if (next == 2) {
-                S.list2[atomicAdd(S.n2, 1)] = (int32_t)t;
+            if (!ok) {
+                // tier 2 only helps if it differs from this pass: a plain tier 1, or a
+                // re-centred basis
+                const bool to2 = S.tier == 1 && (S.acc == ACC_PLAIN || S.recentre);
+                if (to2) {
+                    const int pos = atomicAdd(S.n2, 1);
+                    S.list2[pos] = (int32_t)t;
+                    if (S.basis2)
+                        S.basis2[pos] = S.recentre ? recentre_basis<DIM>(mom)
+                                                   : make_float4(0.f, 0.f, 0.f, 1.f);
+                } else {
+                    S.list3[atomicAdd(S.n3, 1)] = (int32_t)t;
+                }
                 continue;   // a later tier writes this target
-            }
-            if (next == 3) {
-                S.list3[atomicAdd(S.n3, 1)] = (int32_t)t;
-                continue;
             }
         }
         // operator rows: 0 = FP32; 1 = FP32 u, w as in the moments, FP64 monomials and dot;
-        // 2 = everything in FP64 (tier 3: y belongs to the exact FP64 moments)
-        if (MODE == MODE_MAP && S.flags)
-            S.flags[t] = (int8_t)(S.tier == 3 ? 2 : (amp > AMP_SHAPE ? 1 : 0));
+        // 2 = everything in FP64 (tier 3: y belongs to the exact FP64 moments);
+        // 3 = as 1 in the re-centred basis rc[t]
+        if (MODE == MODE_MAP && S.flags) {
+            const int flag = S.tier == 3 ? 2 : (recentred ? 3 : (amp > AMP_SHAPE ? 1 : 0));
+            S.flags[t] = (int8_t)flag;
+            if (recentred && S.rc) S.rc[t] = bas;
+        }
         const double nanv = __longlong_as_double(0x7ff8000000000000LL);
         if (MODE == MODE_FUSED) {
             const int64_t o = S.perm_t ? (int64_t)S.perm_t[t] : t;
@@ -692,6 +858,14 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
 #pragma unroll
         for (int k = 0; k < M; k++) y[k] = (T)S.y[t * M + k];
         const int flag = S.flags ? S.flags[t] : 0;
+        T bcv[4] = {T(0), T(0), T(0), T(1)};
+        if (MIXED && flag == 3) {
+            const float4 b4 = S.rc[t];
+            bcv[0] = b4.x;
+            bcv[1] = b4.y;
+            bcv[2] = b4.z;
+            bcv[3] = b4.w;
+        }
         const double r = ldexp(S.radius, S.kexp[t]);
         const T inv_r = (T)(1.0 / r);
         const int64_t a = S.offsets[t], b = S.offsets[t + 1];
@@ -742,10 +916,11 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
             if constexpr (MIXED) qv = sqrt_approx(d2) * inv_r;
             else qv = sqrt(d2) * inv_r;
             const T w = weight_value<T>(S.weight, qv);
-            T u[3] = {dx[0] * inv_r, dx[1] * inv_r, dx[2] * inv_r};
+            T u[3];
+            basis_offsets<DIM, T>(dx, inv_r, (MIXED && flag == 3) ? bcv : nullptr, u);
             if (MIXED && flag) {
-                // sensitive row: the same FP32 u and w as the moments, monomials and the dot
-                // product with y in FP64
+                // sensitive row (1), or a row in a re-centred basis (3): the same FP32 u and w
+                // as the moments, monomials and the dot product with y in FP64
                 double am[M];
                 am[0] = 1.0;
                 double s = S.y[t * M];

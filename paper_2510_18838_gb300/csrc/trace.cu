@@ -1,6 +1,7 @@
 // trace.cu -- optional per-kernel timing: a CUDA event pair recorded on the launching
-// stream around each traced launch, accumulated per kernel name. Off by default; when off
-// a trace scope costs one relaxed atomic load.
+// stream around each traced launch, accumulated per kernel name (mode 1), or launch counts
+// alone with no events and no extra work (mode 2). Off by default; when off a trace scope
+// costs one relaxed atomic load.
 #include <atomic>
 #include <cstring>
 #include <map>
@@ -63,10 +64,16 @@ void drain_locked() {
 }  // namespace
 
 bool trace_on() { return g_on.load(std::memory_order_relaxed) != 0; }
+bool trace_timing() { return g_on.load(std::memory_order_relaxed) == 1; }
 
 TraceScope::TraceScope(const char* name, cudaStream_t s) : name_(name), s_(s) {
-    if (!trace_on()) return;
+    const int mode = g_on.load(std::memory_order_relaxed);
+    if (!mode) return;
     std::lock_guard<std::mutex> lk(g_mu);
+    if (mode == 2) {
+        g_stats[name_].launches += 1;
+        return;
+    }
     a_ = get_event();
     if (a_) cudaEventRecord(a_, s_);
 }
@@ -89,11 +96,11 @@ void trace_count(const char* name, int64_t n) {
     g_stats[std::string("count:") + name].launches += n;
 }
 
-void trace_enable(int on) {
+void trace_enable(int mode) {
     std::lock_guard<std::mutex> lk(g_mu);
     drain_locked();
-    if (on) g_stats.clear();
-    g_on.store(on ? 1 : 0);
+    if (mode) g_stats.clear();
+    g_on.store(mode == 2 ? 2 : (mode ? 1 : 0));
 }
 
 int trace_count() {

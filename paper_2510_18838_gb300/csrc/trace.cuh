@@ -1,5 +1,5 @@
 // trace.cuh -- scope object that times one kernel launch with CUDA events on its stream
-// when tracing is enabled (pcms_trace_enable).
+// (or only counts it) when tracing is enabled (pcms_trace_enable).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -8,8 +8,9 @@
 
 namespace pcms {
 
-bool trace_on();
-void trace_enable(int on);
+bool trace_on();       // mode 1 or 2
+bool trace_timing();   // mode 1: events, and work counts that cost extra launches
+void trace_enable(int mode);
 // record a count (not a launch) under "count:<name>" while tracing is on
 void trace_count(const char* name, int64_t n);
 int trace_count();

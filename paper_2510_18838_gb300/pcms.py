@@ -96,9 +96,11 @@ SIGNATURES = {
 }
 
 
-def trace_enable(on: bool = True) -> None:
-    """Start (clearing the table) or stop per-kernel CUDA-event timing in the library."""
-    _check(lib().pcms_trace_enable(1 if on else 0))
+def trace_enable(on: bool = True, count_only: bool = False) -> None:
+    """Start (clearing the table) or stop tracing in the library: per-kernel CUDA-event
+    timing plus work counts, or with ``count_only`` launch counts alone (no events, no
+    extra work, for timed regions)."""
+    _check(lib().pcms_trace_enable(0 if not on else (2 if count_only else 1)))
 
 
 def trace_read() -> dict:

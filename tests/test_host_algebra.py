@@ -1,5 +1,6 @@
 """CPU check of the CUDA library's per-target MLS algebra (moment accumulation, monomial
-tables, guarded LDL^T solve) compiled for the host. Compares with numpy on the same
+tables, guarded LDL^T solve, the re-centred basis of the second precision tier and the
+mixed path's FP32 lane arithmetic) compiled for the host. Compares with numpy on the same
 weighted systems; no GPU and no oracle involved."""
 import ctypes
 import itertools
@@ -27,7 +28,11 @@ def hk(tmp_path_factory):
     L = ctypes.CDLL(out)
     P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
     L.hk_mls.restype = I
-    L.hk_mls.argtypes = [I, I, I, I, I, P, P, D, D, D, P, P]
+    L.hk_mls.argtypes = [I, I, I, I, I, P, P, D, D, D, P, P, I, P]
+    L.hk_mls_f32.restype = I
+    L.hk_mls_f32.argtypes = [I, I, I, I, I, P, P, ctypes.c_float, D, D, P, P, I]
+    L.hk_recentre_basis.restype = None
+    L.hk_recentre_basis.argtypes = [I, P, P]
     L.hk_mono.restype = I
     L.hk_mono.argtypes = [I, I, P]
     L.hk_mono_prod.restype = I
@@ -91,9 +96,9 @@ def test_operator_weights_match_numpy(hk, dim, deg):
     m = A.shape[1]
     nm = len([e for e in itertools.product(range(2 * deg + 1), repeat=dim) if sum(e) <= 2 * deg])
     mom = np.zeros(nm)
-    out = np.zeros(m + 1)
+    out = np.zeros(m + 5)
     ok = hk.hk_mls(dim, deg, 0, 0, len(dx), _p(np.ascontiguousarray(dx)), None, 1.0 / r, 0.0,
-                   1e-14, _p(mom), _p(out))
+                   1e-14, _p(mom), _p(out), 0, None)
     assert ok == 1
     y, amp = out[:m], out[m]
     G = (A * w[:, None]).T @ A
@@ -115,9 +120,9 @@ def test_one_shot_value_matches_weighted_lstsq(hk, dim, deg, lam):
     b = np.cos(7 * u[:, 0]) + u[:, -1] ** 2
     nm = len([e for e in itertools.product(range(2 * deg + 1), repeat=dim) if sum(e) <= 2 * deg])
     mom = np.zeros(nm + m)
-    c0 = np.zeros(m + 1)
+    c0 = np.zeros(m + 5)
     ok = hk.hk_mls(dim, deg, 1, 0, len(dx), _p(np.ascontiguousarray(dx)), _p(b), 1.0 / r, lam,
-                   1e-14, _p(mom), _p(c0))
+                   1e-14, _p(mom), _p(c0), 0, None)
     assert ok == 1
     sw = np.sqrt(w)
     Aa = np.vstack([sw[:, None] * A, np.sqrt(lam) * np.eye(m)])
@@ -132,7 +137,147 @@ def test_guard_flags_collinear_points(hk):
     dx[:, 0] = 0.05 * t
     dx[:, 1] = 0.05 * 0.5 * t
     mom = np.zeros(15)
-    y = np.zeros(7)
-    assert hk.hk_mls(2, 1, 0, 0, 30, _p(dx), None, 20.0, 0.0, 1e-14, _p(mom), _p(y)) == 0
-    assert hk.hk_mls(2, 2, 0, 0, 30, _p(dx), None, 20.0, 0.0, 1e-14, _p(mom), _p(y)) == 0
-    assert hk.hk_mls(2, 0, 0, 0, 30, _p(dx), None, 20.0, 0.0, 1e-14, _p(mom), _p(y)) == 1
+    y = np.zeros(11)
+    for deg, ok in ((1, 0), (2, 0), (0, 1)):
+        for rc in (0, 1):
+            assert hk.hk_mls(2, deg, 0, 0, 30, _p(dx), None, 20.0, 0.0, 1e-14, _p(mom), _p(y),
+                             rc, None) == ok
+
+
+def _lopsided(dim, deg, n, seed, centre=0.62, spread=0.12):
+    """A far target's neighbourhood: the selected sources lie in a blob on one side of the
+    target (offsets in units of r around (centre, 0.3 centre, ..), spread `spread`), as after
+    the radius doubling at the edge of a source cluster."""
+    rng = np.random.default_rng(seed)
+    r = 0.05
+    c = np.zeros(dim)
+    c[0], c[1] = centre, 0.3 * centre
+    u = c + spread * rng.standard_normal((n * 3, dim))
+    u = u[np.linalg.norm(u, axis=1) < 0.999][:n]
+    dx = np.zeros((len(u), 3))
+    dx[:, :dim] = u * r
+    q = np.linalg.norm(u, axis=1)
+    w = (1 - q) ** 4 * (4 * q + 1)
+    ex = sorted((e for e in itertools.product(range(deg + 1), repeat=dim) if sum(e) <= deg),
+                key=lambda e: (sum(e), tuple(-x for x in e)))
+    A = np.stack([np.prod(u ** np.array(e), axis=1) for e in ex], axis=1)
+    return dx, u, w, A, r
+
+
+def _n_moments(dim, deg):
+    return len([e for e in itertools.product(range(2 * deg + 1), repeat=dim) if sum(e) <= 2 * deg])
+
+
+@pytest.mark.parametrize("dim,deg", [(2, 1), (2, 2), (3, 2)])
+def test_recentred_basis_gives_the_same_fit(hk, dim, deg):
+    """At lambda = 0 the fitted value does not depend on the polynomial basis: the second
+    tier's re-centred, re-scaled basis must give the target-centred weighted least-squares
+    value and the same operator row, while its amplification factor is much smaller."""
+    dx, u, w, A, r = _lopsided(dim, deg, 400, 7 + dim + deg)
+    m = A.shape[1]
+    nm = _n_moments(dim, deg)
+    b = np.cos(3 * u[:, 0]) + u[:, 1] ** 2
+    dxc = np.ascontiguousarray(dx)
+    sw = np.sqrt(w)
+    c, *_ = np.linalg.lstsq(sw[:, None] * A, sw * b, rcond=None)
+    out0, out1 = np.zeros(m + 5), np.zeros(m + 5)
+    mom = np.zeros(nm + m)
+    assert hk.hk_mls(dim, deg, 1, 0, len(dx), _p(dxc), _p(b), 1.0 / r, 0.0, 1e-14, _p(mom),
+                     _p(out0), 0, None) == 1
+    assert hk.hk_mls(dim, deg, 1, 0, len(dx), _p(dxc), _p(b), 1.0 / r, 0.0, 1e-14, _p(mom),
+                     _p(out1), 1, None) == 1
+    assert out1[0] == pytest.approx(c[0], rel=1e-9, abs=1e-12)
+    assert out0[0] == pytest.approx(c[0], rel=1e-9, abs=1e-12)
+    bas = out1[m + 1:m + 5]
+    assert not np.allclose(bas, [0, 0, 0, 1])          # the basis did move
+    assert out1[m] < out0[m] / 4                        # and the amplification dropped
+    # operator rows N_j = w_j a(u'_j)^T y' equal the target-centred ones
+    G = (A * w[:, None]).T @ A
+    N_ref = w * (A @ np.linalg.solve(G, np.eye(m)[0]))
+    rows = np.zeros(len(dx))
+    out = np.zeros(m + 5)
+    assert hk.hk_mls(dim, deg, 0, 0, len(dx), _p(dxc), None, 1.0 / r, 0.0, 1e-14, _p(mom[:nm]),
+                     _p(out), 1, _p(rows)) == 1
+    np.testing.assert_allclose(rows, N_ref, rtol=1e-8, atol=1e-10 * np.abs(N_ref).max())
+    np.testing.assert_allclose(rows @ A, np.eye(m)[0], atol=1e-9)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_recentre_basis_is_weighted_centroid_and_spread(hk, dim):
+    dx, u, w, A, r = _lopsided(dim, 2, 300, 40 + dim)
+    nm = _n_moments(dim, 2)
+    mom = np.zeros(nm + 10)
+    out = np.zeros(15)
+    hk.hk_mls(dim, 2, 0, 0, len(dx), _p(np.ascontiguousarray(dx)), None, 1.0 / r, 0.0, 1e-14,
+              _p(mom), _p(out), 0, None)
+    got = np.zeros(4, np.float32)
+    hk.hk_recentre_basis(dim, _p(mom), _p(got))
+    c = (w[:, None] * u).sum(0) / w.sum()
+    s = np.sqrt((w * ((u - c) ** 2).sum(1)).sum() / (dim * w.sum()))
+    np.testing.assert_allclose(got[:dim], c, rtol=1e-6, atol=1e-7)
+    assert got[3] == pytest.approx(1.0 / s, rel=1e-6)
+    # zero spread (all neighbours at one point): no re-centring
+    one = np.zeros(nm)
+    one[0] = 2.0
+    hk.hk_recentre_basis(dim, _p(one), _p(got))
+    assert list(got) == [0.0, 0.0, 0.0, 1.0]
+
+
+def _f32_case(kind_of, n, seed):
+    if kind_of == "ball":
+        dx, u, w, A, r = _system(2, 2, n, seed)
+    else:
+        dx, u, w, A, r = _lopsided(2, 2, n, seed)
+    dx32 = dx.astype(np.float32)
+    u64 = dx32[:, :2].astype(np.float64) / np.float64(np.float32(r))
+    b32 = (np.cos(3 * u64[:, 0]) * np.sin(2 * u64[:, 1]) + 0.5).astype(np.float32)
+    # the exact fit of the FP32 data (the values the mixed path receives)
+    inv_r = np.float32(1.0 / r)
+    u = dx32[:, :2].astype(np.float64) * np.float64(inv_r)
+    q = np.linalg.norm(u, axis=1)
+    w = (1 - q) ** 4 * (4 * q + 1)
+    ex = [(0, 0), (1, 0), (0, 1), (2, 0), (1, 1), (0, 2)]
+    A = np.stack([u[:, 0] ** a * u[:, 1] ** c for a, c in ex], axis=1)
+    sw = np.sqrt(w)
+    c, *_ = np.linalg.lstsq(sw[:, None] * A, sw * b32.astype(np.float64), rcond=None)
+    return np.ascontiguousarray(dx32), b32, inv_r, c[0]
+
+
+@pytest.mark.parametrize("case,n", [("ball", 20000), ("lopsided", 20000), ("lopsided", 3000)])
+def test_fp32_blocked_compensation_error_model(hk, case, n):
+    """The mixed path's FP32 lane arithmetic (32 lanes) against the exact fit of the same FP32
+    data: blocked compensation stays within the bound the tier routing relies on
+    (|err| <= 3.4 amp 2^-24 / sqrt(n), checked with a factor 2), and beats plain sums."""
+    dx32, b32, inv_r, ref = _f32_case(case, n, 900 + n)
+    nn = len(dx32)
+    res = {}
+    for scheme in (0, 1):
+        out = np.zeros(2)
+        assert hk.hk_mls_f32(2, 2, scheme, 0, nn, _p(dx32), _p(b32), float(inv_r), 0.0, 1e-14,
+                             None, _p(out), 32) == 1
+        res[scheme] = (abs(out[0] - ref), out[1])
+    err_bk, amp = res[1]
+    assert err_bk <= 2 * 3.4 * amp * 2.0 ** -24 / np.sqrt(nn)
+    assert err_bk < res[0][0] / 4
+
+
+def test_fp32_recentred_tier_accuracy(hk):
+    """The second tier: blocked compensation in the re-centred basis of a lopsided
+    neighbourhood is within the error model with the (smaller) re-centred amplification."""
+    dx32, b32, inv_r, ref = _f32_case("lopsided", 8000, 77)
+    nn = len(dx32)
+    # basis from the target-centred FP64 moments, as k_solve derives it
+    nm = _n_moments(2, 2)
+    mom = np.zeros(nm + 6)
+    out = np.zeros(11)
+    hk.hk_mls(2, 2, 0, 0, nn, _p(dx32.astype(np.float64)), None, float(inv_r), 0.0, 1e-14,
+              _p(mom), _p(out), 0, None)
+    amp_tc = out[6]
+    bas = np.zeros(4, np.float32)
+    hk.hk_recentre_basis(2, _p(mom), _p(bas))
+    res = np.zeros(2)
+    assert hk.hk_mls_f32(2, 2, 1, 0, nn, _p(dx32), _p(b32), float(inv_r), 0.0, 1e-14, _p(bas),
+                         _p(res), 32) == 1
+    err, amp_rc = abs(res[0] - ref), res[1]
+    assert amp_rc < amp_tc / 10
+    assert err <= 2 * 3.4 * amp_rc * 2.0 ** -24 / np.sqrt(nn)
