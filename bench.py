@@ -507,6 +507,15 @@ def main():
 
     extra = {}
     if args.workload == "serve":
+        # one more step with event timing: where the serving step spends device time
+        # (kernels overlap across slots, so these are summed busy times, not a partition)
+        pcms.trace_enable(True)
+        wl.step()
+        torch.cuda.synchronize()
+        pcms.trace_enable(False)
+        st = kernel_launches(pcms.trace_read())
+        extra["serve_kernels_ms"] = {k: [v[0], round(v[1], 2)] for k, v in sorted(
+            st.items(), key=lambda kv: -kv[1][1])[:16]}
         ol = wl.open_loop(value / world)
         pf = wl.plain_fp64()
         extra = {"latency_open_loop_0p8": {k: ol[k] for k in ("p50_ms", "p99_ms", "points_per_s",

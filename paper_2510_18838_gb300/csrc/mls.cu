@@ -144,6 +144,9 @@ AsmArgs base_args(const Grid& g, const SortedPoints& S, const SortedPoints& Tp,
     a.hl0 = S.hl0.as<float4>();
     a.hl1 = S.hl1.as<float2>();
     a.tx64 = Tp.x64.as<double>();
+    a.thl0 = Tp.hl0.as<float4>();
+    a.thl1 = Tp.hl1.as<float2>();
+    a.lv = make_radius_levels(P.radius);
     a.radius = P.radius;
     a.weight = (int)P.weight;
     a.need = P.need;
@@ -307,7 +310,7 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
     BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
     M.g = make_grid(dim, b.lo, b.hi, 0.5 * P.radius, MAX_CELLS);
     sort_points(M.g, src, ns, true, mixed, M.src, s);
-    sort_points(M.g, tgt, nt, false, false, M.tgt, s);
+    sort_points(M.g, tgt, nt, false, mixed, M.tgt, s);
     const int G = choose_group(dim, ns, P.radius, b.lo, b.hi);
 
     M.counts.alloc(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
@@ -365,6 +368,9 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
         sh.hl0 = M.src.hl0.as<float4>();
         sh.hl1 = M.src.hl1.as<float2>();
         sh.tx64 = M.tgt.x64.as<double>();
+        sh.thl0 = M.tgt.hl0.as<float4>();
+        sh.thl1 = M.tgt.hl1.as<float2>();
+        sh.lv = a.lv;
         sh.kexp = M.kexp.as<int32_t>();
         sh.offsets = M.offsets.as<int64_t>();
         sh.cols = M.cols.as<int32_t>();
@@ -373,6 +379,8 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
         sh.weight = (int)P.weight;
         sh.vals = M.vals.p;
         shape_any(dim, deg, mixed, G, sh, asm_blocks(nt, G), s);
+        M.tgt.hl0.release();   // the targets' hi/lo coordinates only serve the assembly
+        M.tgt.hl1.release();
 
         DBuf st(sizeof(unsigned long long) * 4, s);
         PCMS_CU(cudaMemsetAsync(st.p, 0, st.bytes, s));
@@ -419,7 +427,7 @@ void mls_count(const MlsParams& P, const double* src, int64_t ns, const double* 
     Grid g = make_grid(dim, b.lo, b.hi, 0.5 * P.radius, MAX_CELLS);
     SortedPoints S, Tp;
     sort_points(g, src, ns, true, mixed, S, s);
-    sort_points(g, tgt, nt, false, false, Tp, s);
+    sort_points(g, tgt, nt, false, mixed, Tp, s);
     const int G = choose_group(dim, ns, P.radius, b.lo, b.hi);
     DBuf c(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
     DBuf k(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
@@ -455,7 +463,7 @@ void mls_transfer(const MlsParams& P, const double* src, int64_t ns, const doubl
     Grid g = make_grid(dim, b.lo, b.hi, 0.5 * P.radius, MAX_CELLS);
     SortedPoints S, Tp;
     sort_points(g, src, ns, true, mixed, S, s);
-    sort_points(g, tgt, nt, false, false, Tp, s);
+    sort_points(g, tgt, nt, false, mixed, Tp, s);
     const int G = choose_group(dim, ns, P.radius, b.lo, b.hi);
     const size_t fsz = mixed ? sizeof(float) : sizeof(double);
     DBuf fs(fsz * std::max<int64_t>(ns, 1), s);

@@ -22,6 +22,8 @@
 //   k_shape     -- a group per target recomputes w_j a(u_j) and writes N_j.
 #pragma once
 
+#include <cmath>
+
 #include "pcms_internal.cuh"
 
 namespace pcms {
@@ -43,6 +45,31 @@ constexpr int BK_BLOCK = 4;
 constexpr float MIX_BAND = 1.52587890625e-05f;   // 2^-16 relative band around r^2
 constexpr int MAX_DOUBLINGS = 60;
 
+// The radius after k doublings and what the kernels derive from it, computed once on the
+// host. Kernels read these instead of deriving them in FP64: under register pressure the
+// register allocator would otherwise recompute such values inside the candidate loop, and
+// every FP64 instruction there costs 64 FP32 ones on this GPU.
+struct RadiusLevels {
+    double r[MAX_DOUBLINGS + 1];       // radius * 2^k
+    double r2[MAX_DOUBLINGS + 1];      // r * r
+    double inv_r[MAX_DOUBLINGS + 1];   // 1 / r
+    float r2f[MAX_DOUBLINGS + 1];      // (float)(r * r)
+    float inv_rf[MAX_DOUBLINGS + 1];   // (float)(1 / r)
+};
+
+inline RadiusLevels make_radius_levels(double radius) {
+    RadiusLevels L;
+    for (int k = 0; k <= MAX_DOUBLINGS; k++) {
+        const double r = std::ldexp(radius, k);
+        L.r[k] = r;
+        L.r2[k] = r * r;
+        L.inv_r[k] = 1.0 / r;
+        L.r2f[k] = (float)(r * r);
+        L.inv_rf[k] = (float)(1.0 / r);
+    }
+    return L;
+}
+
 struct AsmArgs {
     Grid g;
     int64_t ns, nt;
@@ -51,6 +78,9 @@ struct AsmArgs {
     const float4* hl0;    // mixed: sorted hi/lo
     const float2* hl1;
     const double* tx64;   // [dim][nt] sorted targets
+    const float4* thl0;   // mixed: sorted targets' hi/lo (same layout as hl0/hl1)
+    const float2* thl1;
+    RadiusLevels lv;
     const int32_t* list;  // optional target list (length *n_list); moments then indexed by list position
     const int32_t* n_list;
     double radius;
@@ -127,6 +157,9 @@ struct ShapeArgs {
     const float4* hl0;
     const float2* hl1;
     const double* tx64;
+    const float4* thl0;
+    const float2* thl1;
+    RadiusLevels lv;
     const int32_t* kexp;
     const int64_t* offsets;
     const int32_t* cols;
@@ -344,12 +377,59 @@ __host__ __device__ __forceinline__ void bk_flush(float (&acc)[NACC], float (&su
 // ------------------------------------------------------------------------------------
 // k_assemble
 // ------------------------------------------------------------------------------------
+// FP32 hi/lo coordinates of point i (relative to the grid origin) in the sorted hi/lo layout
+template <int DIM>
+__device__ __forceinline__ void load_hilo(const float4* h0, const float2* h1, int64_t i,
+                                          float* hi, float* lo) {
+    const float4 a = h0[i];
+    if (DIM == 2) {
+        hi[0] = a.x;
+        hi[1] = a.y;
+        lo[0] = a.z;
+        lo[1] = a.w;
+    } else {
+        const float2 b = h1[i];
+        hi[0] = a.x;
+        hi[1] = a.y;
+        hi[2] = a.z;
+        lo[0] = a.w;
+        lo[1] = b.x;
+        lo[2] = b.y;
+    }
+}
+
+// One candidate's data as the assembly walk loads it a step ahead: the hi/lo FP32
+// coordinates (mixed) or the FP64 coordinates, and in fused mode the field value.
+template <bool MIXED, int DIM, typename FT, bool LOADF>
+struct Cand {
+    float4 h0;
+    float2 h1;
+    double x[3];
+    FT f;
+    __device__ __forceinline__ void load(const AsmArgs& A, int j) {
+        if constexpr (MIXED) {
+            h0 = A.hl0[j];
+            if constexpr (DIM == 3) h1 = A.hl1[j];
+        } else {
+            x[0] = A.sx64[j];
+            x[1] = A.sx64[A.ns + j];
+            if constexpr (DIM == 3) x[2] = A.sx64[2 * A.ns + j];
+        }
+        if constexpr (LOADF) f = ((const FT*)A.field)[j];
+    }
+};
+
 // Stored moment type: T for ACC_PLAIN, an unevaluated FP32 pair for ACC_BK.
 template <typename T, int ACC>
 using MomT = typename std::conditional<ACC == ACC_BK, float2, T>::type;
 
+// Two blocks per SM (at most 128 registers) except the blocked 3D quadratic form, whose
+// three accumulator sets of 35-45 moments would spill heavily at that size.
+template <int DIM, int DEG, int ACC>
+constexpr int asm_min_blocks() { return (ACC == ACC_BK && DIM == 3 && DEG == 2) ? 1 : 2; }
+
 template <int DIM, int DEG, bool MIXED, int MODE, int G, typename FT, int ACC = ACC_PLAIN>
-__global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
+__global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemble(AsmArgs A) {
     static_assert(ACC == ACC_PLAIN || (MIXED && MODE != MODE_COUNT), "blocked compensation: mixed moments only");
     using T = typename std::conditional<MIXED, float, double>::type;
     using MT = MomT<T, ACC>;
@@ -361,12 +441,16 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
     constexpr int GPW = 32 / G;
     constexpr int QCAP = 2 * G;
     __shared__ QE qbuf[8][64];
+    __shared__ int rowa_s[8][32], rowe_s[8][32];   // per group: G rows' source start, stream end
 
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int gi = lane / G, gl = lane % G;
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (gi * G));
     const unsigned lt = (1u << lane) - 1u;
     QE* q = &qbuf[wib][gi * QCAP];
+    int* rA = &rowa_s[wib][gi * G];
+    int* rE = &rowe_s[wib][gi * G];
+    using CandT = Cand<MIXED, DIM, FT, MODE == MODE_FUSED>;
 
     const int64_t ngroups = (int64_t)gridDim.x * (blockDim.x >> 5) * GPW;
     const int64_t gid = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * GPW + gi;
@@ -388,14 +472,7 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
             fr[d] = (float)(u - f);
         }
         float thi[3] = {0.f, 0.f, 0.f}, tlo[3] = {0.f, 0.f, 0.f};
-        if (MIXED) {
-#pragma unroll
-            for (int d = 0; d < DIM; d++) {
-                double rel = tx[d] - g.lo[d];
-                thi[d] = (float)rel;
-                tlo[d] = (float)(rel - (double)thi[d]);
-            }
-        }
+        if constexpr (MIXED) load_hilo<DIM>(A.thl0, A.thl1, t, thi, tlo);
         int k = A.kexp_in ? A.kexp_in[t] : 0;
         int cnt = 0;
         int64_t row_off = 0, row_len = 0;
@@ -422,11 +499,13 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
         float sum[NB], cmp[NB];
         int pops = 0;
         for (;;) {
-            const double r = ldexp(A.radius, k);
-            const double r2 = r * r;
+            const double r = A.lv.r[k];
+            const double r2 = A.lv.r2[k];
             const double r2_in = r2 * (1.0 - 9.094947017729282e-13);
-            const float r2f = (float)r2;
-            const T inv_r = (T)(1.0 / r);
+            const float r2f = A.lv.r2f[k];
+            T inv_r;
+            if constexpr (MIXED) inv_r = A.lv.inv_rf[k];
+            else inv_r = A.lv.inv_r[k];
             // Candidate rows: cells (y, z) whose slab comes within r of the target, each
             // trimmed in x to the ball's chord. Computed in cell units in FP32 with a margin
             // m far above the FP32 error, so the rows and chords only ever over-cover.
@@ -451,119 +530,163 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
             cnt = 0;
             int qn = 0, head = 0;
             int64_t written = 0;
-            {
-                for (long long dz = z0; dz <= z1; ++dz) {
+            // The rows are taken G at a time: each lane sets up one row (its chord and the
+            // range [a, a + len) of cell-sorted sources it covers), a prefix sum over the
+            // group lays those ranges end to end, and the group streams the concatenated
+            // candidates G per step, so steps are full across row ends. The loads of the
+            // next step are issued before the current one is classified.
+            const long long ny = y1 >= y0 ? y1 - y0 + 1 : 0;
+            const long long nrows = ny * (DIM == 3 ? (z1 >= z0 ? z1 - z0 + 1 : 0) : 1);
+            for (long long row0 = 0; row0 < nrows; row0 += G) {
+                int ra = 0, rlen = 0;
+                const long long rho = row0 + gl;
+                if (rho < nrows) {
+                    long long dz = 0, dy = y0 + rho;
+                    if (DIM == 3) {   // row counts are bounded by the grid's <= 2^24 cells
+                        const int q = (int)rho / (int)ny;
+                        dz = z0 + q;
+                        dy = y0 + ((int)rho - q * (int)ny);
+                    }
                     float ez = 0.f;
                     if (DIM == 3) {
                         ez = fmaxf(fmaxf((float)dz - fr[2], fr[2] - (float)dz - 1.f), 0.f);
                         ez = fmaxf(ez - mg, 0.f);
                     }
+                    float ey = fmaxf(fmaxf((float)dy - fr[1], fr[1] - (float)dy - 1.f), 0.f);
+                    ey = fmaxf(ey - mg, 0.f);
                     const float remz = RR * RR - ez * ez;
-                    if (remz <= 0.f) continue;
-                    for (long long dy = y0; dy <= y1; ++dy) {
-                        float ey = fmaxf(fmaxf((float)dy - fr[1], fr[1] - (float)dy - 1.f), 0.f);
-                        ey = fmaxf(ey - mg, 0.f);
-                        const float rem = remz - ey * ey;
-                        if (rem <= 0.f) continue;
+                    const float rem = remz - ey * ey;
+                    if (remz > 0.f && rem > 0.f) {
                         const float hx = sqrtf(rem) + mg;
                         const long long x0 = max((long long)floorf(fr[0] - hx) + ct[0], 0LL);
                         const long long x1 =
                             min((long long)floorf(fr[0] + hx) + ct[0], (long long)g.n[0] - 1);
-                        if (x0 > x1) continue;
-                        const int64_t rowbase =
-                            ((ct[2] + dz) * g.n[1] + (ct[1] + dy)) * (int64_t)g.n[0];
-                        const int a = A.cell_start[rowbase + x0];
-                        const int b = A.cell_start[rowbase + x1 + 1];
-                        for (int j0 = a; j0 < b; j0 += G) {
-                            const int j = j0 + gl;
-                            bool in = false;
-                            T dx[3] = {T(0), T(0), T(0)};
-                            if (j < b) {
-                                if (MIXED) {
-                                    float4 h0 = A.hl0[j];
-                                    float ddx, ddy, ddz = 0.f;
-                                    if (DIM == 2) {
-                                        ddx = (h0.x - thi[0]) + (h0.z - tlo[0]);
-                                        ddy = (h0.y - thi[1]) + (h0.w - tlo[1]);
-                                    } else {
-                                        float2 h1 = A.hl1[j];
-                                        ddx = (h0.x - thi[0]) + (h0.w - tlo[0]);
-                                        ddy = (h0.y - thi[1]) + (h1.x - tlo[1]);
-                                        ddz = (h0.z - thi[2]) + (h1.y - tlo[2]);
-                                    }
-                                    float d2f = ddx * ddx + ddy * ddy;
-                                    if (DIM == 3) d2f += ddz * ddz;
-                                    int c = classify32(A.weight, d2f, r2f);
-                                    if (c < 0)
-                                        c = select_exact(A.weight, dist2_exact<DIM>(A.sx64, A.ns, j, tx),
-                                                         r, r2);
-                                    in = c != 0;
-                                    dx[0] = (T)ddx;
-                                    dx[1] = (T)ddy;
-                                    dx[2] = (T)ddz;
-                                } else {
-                                    double e0 = __dsub_rn(A.sx64[j], tx[0]);
-                                    double e1 = __dsub_rn(A.sx64[A.ns + j], tx[1]);
-                                    double d2 = __dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1));
-                                    double e2 = 0.0;
-                                    if (DIM == 3) {
-                                        e2 = __dsub_rn(A.sx64[2 * A.ns + j], tx[2]);
-                                        d2 = __dadd_rn(d2, __dmul_rn(e2, e2));
-                                    }
-                                    in = select64(A.weight, d2, r, r2, r2_in);
-                                    dx[0] = (T)e0;
-                                    dx[1] = (T)e1;
-                                    dx[2] = (T)e2;
-                                }
-                            }
-                            const unsigned bal = __ballot_sync(gmask, in) & gmask;
-                            const int nin = __popc(bal);
-                            if (MODE == MODE_COUNT) {
-                                cnt += nin;
-                                continue;
-                            }
-                            if (in) {
-                                T pay;
-                                if (MODE == MODE_MAP) pay = pack_index(j, T(0));
-                                else pay = (T)(((const FT*)A.field)[j]);
-                                const int pos = (head + qn + __popc(bal & lt)) & (QCAP - 1);
-                                q[pos] = make_entry<T>(dx[0], dx[1], dx[2], pay);
-                            }
-                            qn += nin;
-                            cnt += nin;
-                            __syncwarp(gmask);
-                            if (qn >= G) {
-                                QE e = q[(head + gl) & (QCAP - 1)];
-                                T edx[3] = {e.x, e.y, e.z};
-                                accumulate<DIM, DEG, MODE, T, NACC>(acc, edx, e.w, A.weight, inv_r, bc);
-                                if constexpr (ACC == ACC_BK) {
-                                    if (++pops == BK_BLOCK) {
-                                        bk_flush<NA>(acc, sum, cmp);
-                                        pops = 0;
-                                    }
-                                }
-                                if (MODE == MODE_MAP) {
-                                    if (A.cols && written + gl < row_len)
-                                        A.cols[row_off + written + gl] = unpack_index(e.w);
-                                    written += G;
-                                }
-                                head = (head + G) & (QCAP - 1);
-                                qn -= G;
-                                __syncwarp(gmask);
-                            }
+                        if (x0 <= x1) {
+                            const int64_t rowbase =
+                                ((ct[2] + dz) * g.n[1] + (ct[1] + dy)) * (int64_t)g.n[0];
+                            ra = A.cell_start[rowbase + x0];
+                            rlen = A.cell_start[rowbase + x1 + 1] - ra;
                         }
                     }
                 }
-                if (MODE != MODE_COUNT && qn > 0) {
-                    if (gl < qn) {
+                int incl = rlen;
+#pragma unroll
+                for (int o = 1; o < G; o <<= 1) {
+                    const int v = __shfl_up_sync(gmask, incl, o, G);
+                    if (gl >= o) incl += v;
+                }
+                const int total = __shfl_sync(gmask, incl, G - 1, G);
+                rA[gl] = ra;
+                rE[gl] = incl;
+                __syncwarp(gmask);
+                // stream position p -> source index; positions only grow, so the row cursor
+                // only moves forward (p < total keeps it inside the G rows)
+                int rcur = 0;
+                auto locate = [&](int p) -> int {
+                    while (rE[rcur] <= p) ++rcur;
+                    return rA[rcur] + (p - (rcur ? rE[rcur - 1] : 0));
+                };
+                CandT cn;
+                int jn = 0;
+                bool vn = gl < total;
+                if (vn) {
+                    jn = locate(gl);
+                    cn.load(A, jn);
+                }
+                for (int p0 = 0; p0 < total; p0 += G) {
+                    const bool v = vn;
+                    const int j = jn;
+                    const CandT c = cn;
+                    const int pn = p0 + G + gl;
+                    vn = pn < total;
+                    if (vn) {
+                        jn = locate(pn);
+                        cn.load(A, jn);
+                    }
+                    bool in = false;
+                    T dx[3] = {T(0), T(0), T(0)};
+                    if (v) {
+                        if constexpr (MIXED) {
+                            float ddx, ddy, ddz = 0.f;
+                            if (DIM == 2) {
+                                ddx = (c.h0.x - thi[0]) + (c.h0.z - tlo[0]);
+                                ddy = (c.h0.y - thi[1]) + (c.h0.w - tlo[1]);
+                            } else {
+                                ddx = (c.h0.x - thi[0]) + (c.h0.w - tlo[0]);
+                                ddy = (c.h0.y - thi[1]) + (c.h1.x - tlo[1]);
+                                ddz = (c.h0.z - thi[2]) + (c.h1.y - tlo[2]);
+                            }
+                            float d2f = ddx * ddx + ddy * ddy;
+                            if (DIM == 3) d2f += ddz * ddz;
+                            int cl = classify32(A.weight, d2f, r2f);
+                            if (cl < 0)
+                                cl = select_exact(A.weight, dist2_exact<DIM>(A.sx64, A.ns, j, tx), r, r2);
+                            in = cl != 0;
+                            dx[0] = (T)ddx;
+                            dx[1] = (T)ddy;
+                            dx[2] = (T)ddz;
+                        } else {
+                            const double e0 = __dsub_rn(c.x[0], tx[0]);
+                            const double e1 = __dsub_rn(c.x[1], tx[1]);
+                            double d2 = __dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1));
+                            double e2 = 0.0;
+                            if (DIM == 3) {
+                                e2 = __dsub_rn(c.x[2], tx[2]);
+                                d2 = __dadd_rn(d2, __dmul_rn(e2, e2));
+                            }
+                            in = select64(A.weight, d2, r, r2, r2_in);
+                            dx[0] = (T)e0;
+                            dx[1] = (T)e1;
+                            dx[2] = (T)e2;
+                        }
+                    }
+                    const unsigned bal = __ballot_sync(gmask, in) & gmask;
+                    const int nin = __popc(bal);
+                    if (MODE == MODE_COUNT) {
+                        cnt += nin;
+                        continue;
+                    }
+                    if (in) {
+                        T pay;
+                        if constexpr (MODE == MODE_MAP) pay = pack_index(j, T(0));
+                        else pay = (T)c.f;
+                        const int pos = (head + qn + __popc(bal & lt)) & (QCAP - 1);
+                        q[pos] = make_entry<T>(dx[0], dx[1], dx[2], pay);
+                    }
+                    qn += nin;
+                    cnt += nin;
+                    __syncwarp(gmask);
+                    if (qn >= G) {
                         QE e = q[(head + gl) & (QCAP - 1)];
                         T edx[3] = {e.x, e.y, e.z};
                         accumulate<DIM, DEG, MODE, T, NACC>(acc, edx, e.w, A.weight, inv_r, bc);
-                        if (MODE == MODE_MAP && A.cols && written + gl < row_len)
-                            A.cols[row_off + written + gl] = unpack_index(e.w);
+                        if constexpr (ACC == ACC_BK) {
+                            if (++pops == BK_BLOCK) {
+                                bk_flush<NA>(acc, sum, cmp);
+                                pops = 0;
+                            }
+                        }
+                        if (MODE == MODE_MAP) {
+                            if (A.cols && written + gl < row_len)
+                                A.cols[row_off + written + gl] = unpack_index(e.w);
+                            written += G;
+                        }
+                        head = (head + G) & (QCAP - 1);
+                        qn -= G;
+                        __syncwarp(gmask);
                     }
-                    __syncwarp(gmask);
                 }
+                __syncwarp(gmask);   // the row table is rewritten by the next G rows
+            }
+            if (MODE != MODE_COUNT && qn > 0) {
+                if (gl < qn) {
+                    QE e = q[(head + gl) & (QCAP - 1)];
+                    T edx[3] = {e.x, e.y, e.z};
+                    accumulate<DIM, DEG, MODE, T, NACC>(acc, edx, e.w, A.weight, inv_r, bc);
+                    if (MODE == MODE_MAP && A.cols && written + gl < row_len)
+                        A.cols[row_off + written + gl] = unpack_index(e.w);
+                }
+                __syncwarp(gmask);
             }
             if (MODE != MODE_MAP && A.need > 0 && cnt < A.need && k < MAX_DOUBLINGS && cnt < A.ns) {
                 ++k;
@@ -846,14 +969,8 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
         double tx[3] = {0, 0, 0};
         float thi[3] = {0.f, 0.f, 0.f}, tlo[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int d = 0; d < DIM; d++) {
-            tx[d] = S.tx64[d * S.nt + t];
-            if (MIXED) {
-                double rel = tx[d] - g.lo[d];
-                thi[d] = (float)rel;
-                tlo[d] = (float)(rel - (double)thi[d]);
-            }
-        }
+        for (int d = 0; d < DIM; d++) tx[d] = S.tx64[d * S.nt + t];
+        if constexpr (MIXED) load_hilo<DIM>(S.thl0, S.thl1, t, thi, tlo);
         T y[M];
 #pragma unroll
         for (int k = 0; k < M; k++) y[k] = (T)S.y[t * M + k];
@@ -866,8 +983,11 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
             bcv[2] = b4.z;
             bcv[3] = b4.w;
         }
-        const double r = ldexp(S.radius, S.kexp[t]);
-        const T inv_r = (T)(1.0 / r);
+        const int kx = S.kexp[t];
+        const double r = S.lv.r[kx];
+        T inv_r;
+        if constexpr (MIXED) inv_r = S.lv.inv_rf[kx];
+        else inv_r = S.lv.inv_r[kx];
         const int64_t a = S.offsets[t], b = S.offsets[t + 1];
         for (int64_t i = a + gl; i < b; i += G) {
             const int j = S.cols[i];
@@ -878,7 +998,7 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
                 for (int d = 0; d < DIM; d++) e[d] = S.sx64[d * S.ns + j] - tx[d];
                 double d2 = e[0] * e[0] + e[1] * e[1];
                 if (DIM == 3) d2 += e[2] * e[2];
-                const double ir = 1.0 / r;
+                const double ir = S.lv.inv_r[kx];
                 const double w64 = weight_value<double>(S.weight, sqrt(d2) * ir);
                 const double uu[3] = {e[0] * ir, e[1] * ir, e[2] * ir};
                 double am[M];
