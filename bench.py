@@ -145,12 +145,14 @@ class TransferWorkload:
         import numpy as np
         self.torch, self.P, self.np = torch, pcms, np
         self.dev = device
-        if small:   # the same three parts at about 1/8 of the sizes (profiling captures)
+        if small:   # the same three parts at 1/8 of the points, radii scaled so that the
+            # neighbour counts per target match the full sizes (profiling captures)
             self.name = TRANSFER_NAME.replace("512x512", "256x256").replace(
-                "1M pts", "250k pts").replace("4M->4M", "500k->500k").replace("8M->8M", "1M->1M")
+                "1M pts", "250k pts").replace("4M->4M", "500k->500k").replace(
+                "r=0.01 ", "r=0.02828 ").replace("8M->8M", "1M->1M").replace("r=0.012", "r=0.024")
             c2 = W.mesh_2d(n=256, n_pts=250_000)
-            c3 = W.mls_2d_gaussian(500_000, 500_000)
-            c4 = W.mls_3d_slab(1_000_000, 1_000_000)
+            c3 = W.mls_2d_gaussian(500_000, 500_000, radius=0.01 * math.sqrt(8.0))
+            c4 = W.mls_3d_slab(1_000_000, 1_000_000, radius=0.024)
         else:
             c2, c3, c4 = W.mesh_2d(), W.mls_2d_gaussian(), W.mls_3d_slab()
         self.cfg = {"c2": c2, "c3": c3, "c4": c4}
@@ -189,9 +191,9 @@ class TransferWorkload:
         if ev:
             ev[3].record()
             torch.cuda.synchronize()
-            self.parts = {"mesh_1M_ms": ev[0].elapsed_time(ev[1]),
-                          "mls2d_4M_ms": ev[1].elapsed_time(ev[2]),
-                          "mls3d_8M_16f_ms": ev[2].elapsed_time(ev[3])}
+            self.parts = {"mesh_ms": ev[0].elapsed_time(ev[1]),
+                          "mls2d_ms": ev[1].elapsed_time(ev[2]),
+                          "mls3d_16f_ms": ev[2].elapsed_time(ev[3])}
         return self.points_per_step
 
     def cpu_sample(self, orc):
@@ -460,7 +462,7 @@ def main():
     pcms.trace_enable(False)
     ttrace = pcms.trace_read()
     tw.step(timed_parts=True)
-    transfer = {"workload": TRANSFER_NAME, "ms": tms, "points": tw.points_per_step,
+    transfer = {"workload": tw.name, "ms": tms, "points": tw.points_per_step,
                 "points_per_s": tw.points_per_step / (tms / 1e3), "parts_ms": tw.parts,
                 "kernels_ms": {k: round(v[1], 3) for k, v in sorted(
                     kernel_launches(ttrace).items(), key=lambda kv: -kv[1][1])[:14]},
@@ -518,12 +520,12 @@ def main():
             st.items(), key=lambda kv: -kv[1][1])[:16]}
         ol = wl.open_loop(value / world)
         pf = wl.plain_fp64()
-        extra = {"latency_open_loop_0p8": {k: ol[k] for k in ("p50_ms", "p99_ms", "points_per_s",
-                                                              "failed", "cached_hits")},
+        extra.update({"latency_open_loop_0p8": {k: ol[k] for k in ("p50_ms", "p99_ms", "points_per_s",
+                                                                   "failed", "cached_hits")},
                  "closed_loop": {k: wl.last[k] for k in ("p50_ms", "p99_ms", "cached_hits",
                                                          "peak_bytes")},
                  "plain_fp64_per_request": pf,
-                 "requests": len(wl.dreqs)}
+                 "requests": len(wl.dreqs)})
         e2e = wl.e2e()
     else:
         e2e = {"value": None}

@@ -7,8 +7,9 @@
 //      the caller index; each source writes one contiguous FP-element row.
 //   2. k_spmm: one warp per target row (targets sorted by cell), lanes split into
 //      32/NV nnz slots x NV vectors of fields; each slot reads (col, val) once and NV
-//      vectors of the source's field row. Rows of neighbouring targets touch neighbouring
-//      source rows, so the gathered field rows are served mostly from L2.
+//      vectors of the source's field row. Blocks take chunks of consecutive rows, so
+//      neighbouring targets, which share most sources, are in flight together and the
+//      gathered field rows are served mostly from L1/L2.
 //   3. k_stage_to_caller: out[f][i] = stage[inv_t[i]][f], coalesced writes per field.
 #include <algorithm>
 
@@ -22,6 +23,25 @@ namespace {
 int blocks_for(int64_t n, int threads, int per_sm = 32) {
     int64_t need = (n + threads - 1) / threads;
     return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * per_sm));
+}
+
+// Rows are handed out in chunks of SPMM_ROWS consecutive targets (an atomic counter), so a
+// block's warps work on neighbouring targets at the same time and share their gathered field
+// rows in L1; chunks also balance rows of uneven length (the denser slab of the 3D case).
+constexpr int SPMM_ROWS = 128;
+
+// persistent grid of the apply: as many 256-thread blocks as fit on the GPU at once (they
+// take chunks of rows from a counter), at most one per chunk
+template <typename K>
+int spmm_blocks(K kernel, int64_t nt) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess ||
+        per_sm < 1) {
+        (void)cudaGetLastError();
+        per_sm = 1;
+    }
+    const int64_t chunks = (nt + SPMM_ROWS - 1) / SPMM_ROWS;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)num_sms() * per_sm));
 }
 
 template <typename T> struct Vec;
@@ -84,86 +104,140 @@ __device__ __forceinline__ double quiet_nan<double>() {
     return __longlong_as_double(0x7ff8000000000000LL);
 }
 
+__device__ __forceinline__ int64_t spmm_next_chunk(unsigned long long* next) {
+    __shared__ long long chunk_s;
+    __syncthreads();   // the previous chunk's start has been read by every thread
+    if (threadIdx.x == 0) chunk_s = (long long)atomicAdd(next, (unsigned long long)SPMM_ROWS);
+    __syncthreads();
+    return chunk_s;
+}
+
 // One warp per target row; lanes = 32/NV slots x NV vectors of W fields (fp = NV*W).
-// Each chunk of 32 nonzeros is read with one coalesced load of (col, val) per lane and
-// redistributed by shuffles, so every lane has NV independent field-row gathers in flight.
-// Rows whose target status is not OK produce NaN.
+// Nonzeros are taken 32 at a time: each lane loads one (col, val) pair with a coalesced load,
+// the columns are redistributed by shuffles, and every lane then has NV independent
+// field-row gathers in flight. A row's first 64 (col, val) pairs are loaded together, and the
+// next row's offsets and first 32 pairs while the current row is gathered. Rows whose target
+// status is not OK produce NaN.
 template <typename T, int NV>
 __global__ void __launch_bounds__(256) k_spmm_vec(int64_t nt, const int64_t* __restrict__ off,
                                                   const int32_t* __restrict__ cols,
                                                   const T* __restrict__ vals,
                                                   const T* __restrict__ fs,
                                                   const int8_t* __restrict__ status,
-                                                  T* __restrict__ stage) {
+                                                  T* __restrict__ stage,
+                                                  unsigned long long* next) {
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
     constexpr int SLOTS = 32 / NV;
     const int lane = threadIdx.x & 31;
     const int slot = lane / NV, vi = lane % NV;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < nt;
-         t += nwarps) {
-        const int64_t a = off[t], b = off[t + 1];
-        V acc{};
-        for (int64_t c0 = a; c0 < b; c0 += 32) {
-            const int64_t e = c0 + lane;
-            const int32_t jl = e < b ? __ldg(cols + e) : 0;
-            const T wl = e < b ? __ldg(vals + e) : T(0);
-            V x[NV];
-#pragma unroll
-            for (int s = 0; s < NV; s++) {
-                const int k = s * SLOTS + slot;
-                const int32_t j = __shfl_sync(0xffffffffu, jl, k);
-                if (c0 + k < b) x[s] = *reinterpret_cast<const V*>(fs + (int64_t)j * (NV * W) + vi * W);
-                else x[s] = V{};
-            }
-#pragma unroll
-            for (int s = 0; s < NV; s++) {
-                const T w = __shfl_sync(0xffffffffu, wl, s * SLOTS + slot);
-                fma_vec<V, T>(acc, w, x[s]);
+    const int nwb = blockDim.x >> 5, wib = threadIdx.x >> 5;
+    for (;;) {
+        const int64_t c0 = spmm_next_chunk(next);
+        if (c0 >= nt) break;
+        const int64_t c1 = min(c0 + (int64_t)SPMM_ROWS, nt);
+        int64_t t = c0 + wib;
+        int64_t a = 0, b = 0;
+        int32_t jA = 0;
+        T wA = T(0);
+        if (t < c1) {
+            a = off[t];
+            b = off[t + 1];
+            if (a + lane < b) {
+                jA = __ldg(cols + a + lane);
+                wA = __ldg(vals + a + lane);
             }
         }
-#pragma unroll
-        for (int o = NV; o < 32; o <<= 1) shfl_add(acc, o);
-        if (slot == 0) {
-            if (status[t] != PCMS_TARGET_OK) {
-                const T nan = quiet_nan<T>();
-                const T nan4[4] = {nan, nan, nan, nan};
-                memcpy(&acc, nan4, sizeof(V));
+        for (; t < c1; t += nwb) {
+            // the row's second 32 pairs, and the next row's offsets
+            int32_t jB = 0;
+            T wB = T(0);
+            if (a + 32 + lane < b) {
+                jB = __ldg(cols + a + 32 + lane);
+                wB = __ldg(vals + a + 32 + lane);
             }
-            *reinterpret_cast<V*>(stage + t * (NV * W) + vi * W) = acc;
+            const int64_t tn = t + nwb;
+            int64_t an = 0, bn = 0;
+            if (tn < c1) {
+                an = off[tn];
+                bn = off[tn + 1];
+            }
+            V acc{};
+            for (int64_t e0 = a; e0 < b; e0 += 32) {
+                if (e0 >= a + 64) {   // rows longer than 64 nonzeros
+                    jB = e0 + lane < b ? __ldg(cols + e0 + lane) : 0;
+                    wB = e0 + lane < b ? __ldg(vals + e0 + lane) : T(0);
+                }
+                const bool first = e0 == a;
+                const int32_t jl = first ? jA : jB;
+                const T wl = first ? wA : wB;
+                V x[NV];
+#pragma unroll
+                for (int s = 0; s < NV; s++) {
+                    const int k = s * SLOTS + slot;
+                    const int32_t j = __shfl_sync(0xffffffffu, jl, k);
+                    x[s] = e0 + k < b ? *reinterpret_cast<const V*>(fs + (int64_t)j * (NV * W) + vi * W)
+                                      : V{};
+                }
+#pragma unroll
+                for (int s = 0; s < NV; s++)
+                    fma_vec<V, T>(acc, __shfl_sync(0xffffffffu, wl, s * SLOTS + slot), x[s]);
+            }
+            jA = 0;
+            wA = T(0);
+            if (an + lane < bn) {   // the next row's first 32 pairs
+                jA = __ldg(cols + an + lane);
+                wA = __ldg(vals + an + lane);
+            }
+#pragma unroll
+            for (int o = NV; o < 32; o <<= 1) shfl_add(acc, o);
+            if (slot == 0) {
+                if (status[t] != PCMS_TARGET_OK) {
+                    const T nan = quiet_nan<T>();
+                    const T nan4[4] = {nan, nan, nan, nan};
+                    memcpy(&acc, nan4, sizeof(V));
+                }
+                *reinterpret_cast<V*>(stage + t * (NV * W) + vi * W) = acc;
+            }
+            a = an;
+            b = bn;
         }
     }
 }
 
-// one field: lanes over nonzeros, two chunks of 32 in flight
+// one field: lanes over nonzeros, 64 in flight, rows in chunks as above
 template <typename T>
 __global__ void __launch_bounds__(256) k_spmm_1(int64_t nt, const int64_t* __restrict__ off,
                                                 const int32_t* __restrict__ cols,
                                                 const T* __restrict__ vals,
                                                 const T* __restrict__ fs,
                                                 const int8_t* __restrict__ status,
-                                                T* __restrict__ stage) {
+                                                T* __restrict__ stage,
+                                                unsigned long long* next) {
     const int lane = threadIdx.x & 31;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < nt;
-         t += nwarps) {
-        const int64_t a = off[t], b = off[t + 1];
-        T acc = T(0);
-        for (int64_t e = a + lane; e < b; e += 64) {
-            const bool two = e + 32 < b;
-            const int32_t j0 = __ldg(cols + e);
-            const int32_t j1 = two ? __ldg(cols + e + 32) : 0;
-            const T w0 = __ldg(vals + e);
-            const T w1 = two ? __ldg(vals + e + 32) : T(0);
-            const T x0 = fs[j0];
-            const T x1 = two ? fs[j1] : T(0);
-            acc += w0 * x0;
-            acc += w1 * x1;
-        }
+    const int nwb = blockDim.x >> 5, wib = threadIdx.x >> 5;
+    for (;;) {
+        const int64_t c0 = spmm_next_chunk(next);
+        if (c0 >= nt) break;
+        const int64_t c1 = min(c0 + (int64_t)SPMM_ROWS, nt);
+        for (int64_t t = c0 + wib; t < c1; t += nwb) {
+            const int64_t a = off[t], b = off[t + 1];
+            T acc = T(0);
+            for (int64_t e = a + lane; e < b; e += 64) {
+                const bool two = e + 32 < b;
+                const int32_t j0 = __ldg(cols + e);
+                const int32_t j1 = two ? __ldg(cols + e + 32) : 0;
+                const T w0 = __ldg(vals + e);
+                const T w1 = two ? __ldg(vals + e + 32) : T(0);
+                const T x0 = fs[j0];
+                const T x1 = two ? fs[j1] : T(0);
+                acc += w0 * x0;
+                acc += w1 * x1;
+            }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) stage[t] = status[t] == PCMS_TARGET_OK ? acc : quiet_nan<T>();
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) stage[t] = status[t] == PCMS_TARGET_OK ? acc : quiet_nan<T>();
+        }
     }
 }
 
@@ -210,13 +284,17 @@ void apply_t(MapImpl& M, const T* fields, int nf, T* out, cudaStream_t s) {
         const int32_t* cols = M.cols.as<int32_t>();
         const T* vals = M.vals.as<T>();
         const int8_t* st = M.status.as<int8_t>();
-        int blocks = blocks_for(nt * 32, 256, 16);
+        DBuf ctr(sizeof(unsigned long long), s);
+        unsigned long long* next = ctr.as<unsigned long long>();
+        PCMS_CU(cudaMemsetAsync(next, 0, sizeof(unsigned long long), s));
         int nv = fp / W;
-        if (fp == 1) k_spmm_1<T><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs.as<T>(), st, stage.as<T>());
-        else if (nv == 1) k_spmm_vec<T, 1><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs.as<T>(), st, stage.as<T>());
-        else if (nv == 2) k_spmm_vec<T, 2><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs.as<T>(), st, stage.as<T>());
-        else if (nv == 4) k_spmm_vec<T, 4><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs.as<T>(), st, stage.as<T>());
-        else if (nv == 8) k_spmm_vec<T, 8><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs.as<T>(), st, stage.as<T>());
+        T* fsp = fs.as<T>();
+        T* stp = stage.as<T>();
+        if (fp == 1) k_spmm_1<T><<<spmm_blocks(k_spmm_1<T>, nt), 256, 0, s>>>(nt, off, cols, vals, fsp, st, stp, next);
+        else if (nv == 1) k_spmm_vec<T, 1><<<spmm_blocks(k_spmm_vec<T, 1>, nt), 256, 0, s>>>(nt, off, cols, vals, fsp, st, stp, next);
+        else if (nv == 2) k_spmm_vec<T, 2><<<spmm_blocks(k_spmm_vec<T, 2>, nt), 256, 0, s>>>(nt, off, cols, vals, fsp, st, stp, next);
+        else if (nv == 4) k_spmm_vec<T, 4><<<spmm_blocks(k_spmm_vec<T, 4>, nt), 256, 0, s>>>(nt, off, cols, vals, fsp, st, stp, next);
+        else if (nv == 8) k_spmm_vec<T, 8><<<spmm_blocks(k_spmm_vec<T, 8>, nt), 256, 0, s>>>(nt, off, cols, vals, fsp, st, stp, next);
         else {
             fail(PCMS_ERR_INVALID_ARG, "internal: field padding");
         }
@@ -234,7 +312,7 @@ void apply_t(MapImpl& M, const T* fields, int nf, T* out, cudaStream_t s) {
 // nt*fp elements. Launch errors are returned, nothing is allocated or traced.
 template <typename T>
 cudaError_t apply_with_scratch_t(const MapImpl& M, const T* fields, int nf, T* out, T* fs,
-                                 T* stage, cudaStream_t s) {
+                                 T* stage, unsigned long long* next, cudaStream_t s) {
     const int64_t ns = M.ns, nt = M.nt;
     constexpr int W = Vec<T>::W;
     int nvec = 1;
@@ -248,13 +326,14 @@ cudaError_t apply_with_scratch_t(const MapImpl& M, const T* fields, int nf, T* o
         const int32_t* cols = M.cols.as<int32_t>();
         const T* vals = M.vals.as<T>();
         const int8_t* st = M.status.as<int8_t>();
-        const int blocks = blocks_for(nt * 32, 256, 16);
+        const cudaError_t me = cudaMemsetAsync(next, 0, sizeof(unsigned long long), s);
+        if (me != cudaSuccess) return me;
         const int nv = fp / W;
-        if (fp == 1) k_spmm_1<T><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs, st, stage);
-        else if (nv == 1) k_spmm_vec<T, 1><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs, st, stage);
-        else if (nv == 2) k_spmm_vec<T, 2><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs, st, stage);
-        else if (nv == 4) k_spmm_vec<T, 4><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs, st, stage);
-        else k_spmm_vec<T, 8><<<blocks, 256, 0, s>>>(nt, off, cols, vals, fs, st, stage);
+        if (fp == 1) k_spmm_1<T><<<spmm_blocks(k_spmm_1<T>, nt), 256, 0, s>>>(nt, off, cols, vals, fs, st, stage, next);
+        else if (nv == 1) k_spmm_vec<T, 1><<<spmm_blocks(k_spmm_vec<T, 1>, nt), 256, 0, s>>>(nt, off, cols, vals, fs, st, stage, next);
+        else if (nv == 2) k_spmm_vec<T, 2><<<spmm_blocks(k_spmm_vec<T, 2>, nt), 256, 0, s>>>(nt, off, cols, vals, fs, st, stage, next);
+        else if (nv == 4) k_spmm_vec<T, 4><<<spmm_blocks(k_spmm_vec<T, 4>, nt), 256, 0, s>>>(nt, off, cols, vals, fs, st, stage, next);
+        else k_spmm_vec<T, 8><<<spmm_blocks(k_spmm_vec<T, 8>, nt), 256, 0, s>>>(nt, off, cols, vals, fs, st, stage, next);
         k_stage_to_caller<T><<<blocks_for(nt, 256), 256, 0, s>>>(stage, fp, nf, nt,
                                                                  M.tgt.inv.as<int32_t>(), out);
     }
@@ -321,7 +400,8 @@ int64_t apply_scratch_bytes(const MapImpl& M, int nf) {
     while (nvec * W < nf) nvec <<= 1;
     const int64_t fp = nf == 1 ? 1 : nvec * W;
     const int64_t fs = (M.ns * fp * elem + 255) / 256 * 256;   // stage starts 256-aligned
-    return fs + M.nt * fp * elem;
+    const int64_t st = (M.nt * fp * elem + 255) / 256 * 256;   // then the row-chunk counter
+    return fs + st + 256;
 }
 
 cudaError_t mls_apply_with_scratch(const MapImpl& M, const void* fields, int nf, void* out,
@@ -333,11 +413,12 @@ cudaError_t mls_apply_with_scratch(const MapImpl& M, const void* fields, int nf,
     const int64_t fp = nf == 1 ? 1 : nvec * W;
     char* fs = (char*)scratch;
     char* stage = fs + (M.ns * fp * elem + 255) / 256 * 256;
+    auto* next = (unsigned long long*)(stage + (M.nt * fp * elem + 255) / 256 * 256);
     if (M.P.prec == PCMS_MIXED)
         return apply_with_scratch_t<float>(M, (const float*)fields, nf, (float*)out, (float*)fs,
-                                           (float*)stage, s);
+                                           (float*)stage, next, s);
     return apply_with_scratch_t<double>(M, (const double*)fields, nf, (double*)out,
-                                        (double*)fs, (double*)stage, s);
+                                        (double*)fs, (double*)stage, next, s);
 }
 
 void mls_export(MapImpl& M, int64_t* offsets, int32_t* cols, double* vals, int8_t* status,

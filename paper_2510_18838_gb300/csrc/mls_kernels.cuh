@@ -323,7 +323,8 @@ __host__ __device__ __forceinline__ void basis_offsets(const T* dx, T inv_r, con
 // is always a function of |dx| / r), b = field value, bc = re-centred basis or null.
 template <int DIM, int DEG, int MODE, typename T, int NACC>
 __host__ __device__ __forceinline__ void accumulate(T (&acc)[NACC > 0 ? NACC : 1], const T* dx,
-                                                    T b, int kind, T inv_r, const T* bc) {
+                                                    T b, int kind, T inv_r, const T* bc,
+                                                    bool selected = true) {
     constexpr int NM = mono_count(DIM, 2 * DEG);
     constexpr int M = mono_count(DIM, DEG);
     T d2 = dx[0] * dx[0] + dx[1] * dx[1];
@@ -336,6 +337,7 @@ __host__ __device__ __forceinline__ void accumulate(T (&acc)[NACC > 0 ? NACC : 1
     q = sqrt(d2) * inv_r;
 #endif
     T w = weight_value<T>(kind, q);
+    if (!selected) w = T(0);   // adds exact zeros: an unselected candidate leaves the sums as they are
     T u[3];
     basis_offsets<DIM, T>(dx, inv_r, bc, u);
     T wm[NM];
@@ -451,6 +453,10 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemb
     int* rA = &rowa_s[wib][gi * G];
     int* rE = &rowe_s[wib][gi * G];
     using CandT = Cand<MIXED, DIM, FT, MODE == MODE_FUSED>;
+    // Dense one-shot targets (warp per target, blocked compensation): about 3 in 4 candidates
+    // are selected, so every lane accumulates its own candidate with the weight zeroed when it
+    // is not selected, instead of compacting selected pairs through the shared-memory ring.
+    constexpr bool PRED = MODE == MODE_FUSED && ACC == ACC_BK;
 
     const int64_t ngroups = (int64_t)gridDim.x * (blockDim.x >> 5) * GPW;
     const int64_t gid = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * GPW + gi;
@@ -644,6 +650,17 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemb
                     const int nin = __popc(bal);
                     if (MODE == MODE_COUNT) {
                         cnt += nin;
+                        continue;
+                    }
+                    if constexpr (PRED) {
+                        cnt += nin;
+                        if (nin == 0) continue;
+                        accumulate<DIM, DEG, MODE, T, NACC>(acc, dx, v ? (T)c.f : T(0), A.weight,
+                                                            inv_r, bc, in);
+                        if (++pops == BK_BLOCK) {
+                            bk_flush<NA>(acc, sum, cmp);
+                            pops = 0;
+                        }
                         continue;
                     }
                     if (in) {
