@@ -86,3 +86,32 @@ def test_cache_reuse_and_capacity(env):
     s.drain(60)
     assert s.poll(4)[0]["status"] == pcms.CAPACITY
     s.close()
+
+
+def test_a_failing_request_does_not_disturb_the_others(env):
+    """A request that fails while running (a non-finite source coordinate, found by the
+    library's bounding-box pass) comes back with its error status; requests around it, in
+    other slots and after it in the same slot, complete with correct results."""
+    torch, pcms, serve = env
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev).manual_seed(11)
+    src = torch.rand((2, 30000), dtype=torch.float64, device=dev, generator=g)
+    tgt = torch.rand((2, 8000), dtype=torch.float64, device=dev, generator=g)
+    f = torch.rand((2, 30000), dtype=torch.float32, device=dev, generator=g)
+    bad = src.clone()
+    bad[0, 1234] = float("nan")
+    outs = [torch.empty((2, 8000), dtype=torch.float32, device=dev) for _ in range(5)]
+    s = pcms.Server(n_slots=2, mem_cap_bytes=2 << 30)
+    tickets = []
+    for i in range(5):
+        tickets.append(s.submit_mls(bad if i == 2 else src, tgt, f, outs[i], 2, 0.03))
+    s.drain(120)
+    res = {x["ticket"]: x["status"] for x in s.poll(16)}
+    s.close()
+    assert res[tickets[2]] == pcms.INVALID_ARG
+    ref, _ = pcms.mls_transfer(src, tgt, f, 2, 0.03, precision="mixed", with_status=False)
+    ref = ref.cpu().numpy()
+    ok = np.isfinite(ref).all(axis=0)
+    for i in (0, 1, 3, 4):
+        assert res[tickets[i]] == pcms.OK
+        assert normwise_err(outs[i].cpu().numpy(), ref, ok) <= TOL_MIXED
