@@ -109,6 +109,41 @@ __device__ __forceinline__ int orient_sign(double ax, double ay, double bx, doub
     return orient_exact(ax, ay, bx, by, cx, cy);
 }
 
+// FP32 filter for orient_sign(a, b, p): +1 or -1 when the sign is certain, 0 when it is not.
+// Points are FP32 hi/lo pairs relative to a common origin (a = (A.x, A.y) + (A.z, A.w)), so
+// each difference a - p, formed as (a_hi - p_hi) + (a_lo - p_lo), is within 2u|d| + delta of
+// the exact one (u = 2^-24; delta = 2^-44 x the extent covers the split of the FP64 inputs
+// and the lo parts' rounding). Propagating that through the two products and the
+// subtraction gives |det - det_exact| <= 6.01u (|l| + |r|) + 1.01 delta (|X|+|Y|+|Z|+|W|)
+// + 2 delta^2; the bound below has at least 25% to spare on every term, and 1e-37 covers
+// underflow. Points on an edge (det_exact = 0) always fail the test and are decided by the
+// FP64 filter and the exact expansion.
+__device__ __forceinline__ int orient_filter32(float4 A, float4 B, float phx, float phy,
+                                               float plx, float ply, float delta) {
+    const float X = __fadd_rn(__fsub_rn(A.x, phx), __fsub_rn(A.z, plx));   // ax - px
+    const float Z = __fadd_rn(__fsub_rn(A.y, phy), __fsub_rn(A.w, ply));   // ay - py
+    const float W = __fadd_rn(__fsub_rn(B.x, phx), __fsub_rn(B.z, plx));   // bx - px
+    const float Y = __fadd_rn(__fsub_rn(B.y, phy), __fsub_rn(B.w, ply));   // by - py
+    const float l = __fmul_rn(X, Y), r = __fmul_rn(Z, W);
+    const float det = __fsub_rn(l, r);
+    const float bound = 4.76837158e-07f * (fabsf(l) + fabsf(r)) +
+                        2.0f * delta * (fabsf(X) + fabsf(Y) + fabsf(Z) + fabsf(W)) +
+                        3.0f * delta * delta + 1e-37f;
+    if (det > bound) return 1;
+    if (det < -bound) return -1;
+    return 0;
+}
+
+__global__ void k_vertex_hilo(int64_t nv, const double* __restrict__ xy, double ox, double oy,
+                              float4* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double rx = xy[i] - ox, ry = xy[nv + i] - oy;
+        const float hx = (float)rx, hy = (float)ry;
+        out[i] = make_float4(hx, hy, (float)(rx - (double)hx), (float)(ry - (double)hy));
+    }
+}
+
 __device__ __forceinline__ double orient_fp(double ax, double ay, double bx, double by, double cx,
                                             double cy) {
     return __dsub_rn(__dmul_rn(__dsub_rn(ax, cx), __dsub_rn(by, cy)),
@@ -186,6 +221,8 @@ __global__ void __launch_bounds__(256) k_locate(Grid g, double bx0, double by0, 
                                                 const int8_t* __restrict__ tsign,
                                                 const int32_t* __restrict__ start,
                                                 const int32_t* __restrict__ items,
+                                                const float4* __restrict__ vhl, double ox,
+                                                double oy, float delta, int use32,
                                                 const double* __restrict__ pts, int64_t n,
                                                 const double* __restrict__ field,
                                                 int32_t* __restrict__ elem,
@@ -201,19 +238,35 @@ __global__ void __launch_bounds__(256) k_locate(Grid g, double bx0, double by0, 
             const int64_t c = (int64_t)mesh_cell(py, g.lo[1], g.inv_h, g.n[1]) * g.n[0] +
                               mesh_cell(px, g.lo[0], g.inv_h, g.n[0]);
             const int a = start[c], b = start[c + 1];
+            // the point in the FP32 filter's frame
+            const double rx = px - ox, ry = py - oy;
+            const float phx = (float)rx, phy = (float)ry;
+            const float plx = (float)(rx - (double)phx), ply = (float)(ry - (double)phy);
             for (int it = a; it < b; it++) {
                 const int32_t k = items[it];
                 const int s = tsign[k];
                 const int32_t i0 = tri[k], i1 = tri[ntri + k], i2 = tri[2 * ntri + k];
-                const double x0 = xy[i0], y0 = xy[nv + i0];
-                const double x1 = xy[i1], y1 = xy[nv + i1];
-                const double x2 = xy[i2], y2 = xy[nv + i2];
-                const int o0 = orient_sign(x1, y1, x2, y2, px, py);
-                if (o0 * s < 0) continue;
-                const int o1 = orient_sign(x2, y2, x0, y0, px, py);
-                if (o1 * s < 0) continue;
-                const int o2 = orient_sign(x0, y0, x1, y1, px, py);
-                if (o2 * s < 0) continue;
+                int o0 = 0, o1 = 0, o2 = 0;
+                if (use32) {
+                    const float4 A = vhl[i0], B = vhl[i1], C = vhl[i2];
+                    o0 = orient_filter32(B, C, phx, phy, plx, ply, delta);
+                    if (o0 * s < 0) continue;
+                    o1 = orient_filter32(C, A, phx, phy, plx, ply, delta);
+                    if (o1 * s < 0) continue;
+                    o2 = orient_filter32(A, B, phx, phy, plx, ply, delta);
+                    if (o2 * s < 0) continue;
+                }
+                if (o0 == 0 || o1 == 0 || o2 == 0) {   // undecided in FP32: FP64 filter, then exact
+                    const double x0 = xy[i0], y0 = xy[nv + i0];
+                    const double x1 = xy[i1], y1 = xy[nv + i1];
+                    const double x2 = xy[i2], y2 = xy[nv + i2];
+                    if (o0 == 0) o0 = orient_sign(x1, y1, x2, y2, px, py);
+                    if (o0 * s < 0) continue;
+                    if (o1 == 0) o1 = orient_sign(x2, y2, x0, y0, px, py);
+                    if (o1 * s < 0) continue;
+                    if (o2 == 0) o2 = orient_sign(x0, y0, x1, y1, px, py);
+                    if (o2 * s < 0) continue;
+                }
                 found = k;
                 nz = (o0 == 0) + (o1 == 0) + (o2 == 0);
                 v0 = i0; v1 = i1; v2 = i2;
@@ -276,6 +329,18 @@ void mesh_create(MeshImpl& M, const double* xy, int64_t nv, const int32_t* tri, 
     // make_grid adds the 2^-20 margin used for radius searches; harmless here
     M.g = make_grid(2, lo, hi, h, int64_t(1) << 26);
     const Grid& g = M.g;
+    // FP32 orientation filter frame: origin at the box corner, error allowance from the extent
+    M.origin[0] = hb[0];
+    M.origin[1] = hb[1];
+    const double ext = std::max(ex, ey);
+    M.use32 = ext > 1e-30 && ext < 1e18;
+    M.delta = M.use32 ? (float)(std::ldexp(ext, -44) * (1.0 + 1e-6)) : 0.f;
+    M.vhl.alloc(sizeof(float4) * std::max<int64_t>(nv, 1), s);
+    if (nv > 0) {
+        PCMS_TRACE("mesh_vertex_hilo", s);
+        k_vertex_hilo<<<blocks_for(nv, 256), 256, 0, s>>>(nv, M.xy.as<double>(), M.origin[0],
+                                                          M.origin[1], M.vhl.as<float4>());
+    }
     DBuf count(sizeof(int32_t) * (g.ncell + 1), s);
     PCMS_CU(cudaMemsetAsync(count.p, 0, count.bytes, s));
     M.tsign.alloc(sizeof(int8_t) * std::max<int64_t>(ntri, 1), s);
@@ -318,7 +383,7 @@ void mesh_create(MeshImpl& M, const double* xy, int64_t nv, const int32_t* tri, 
 int64_t estimate_mesh_bytes(int64_t nv, int64_t ntri, int64_t npts) {
     (void)npts;
     // copies of the mesh, orientation signs, rectangles, cell counts/starts, (cell, tri) pairs
-    double b = nv * 16.0 + ntri * (12.0 + 1.0 + 16.0) + 2.0 * 4.0 * (0.5 * ntri + 64.0) +
+    double b = nv * 32.0 + ntri * (12.0 + 1.0 + 16.0) + 2.0 * 4.0 * (0.5 * ntri + 64.0) +
                4.0 * 4.0 * ntri;
     return (int64_t)(1.2 * b) + (int64_t(1) << 20);
 }
@@ -330,7 +395,8 @@ void mesh_locate(const MeshImpl& M, const double* pts, int64_t n, const double* 
     k_locate<<<blocks_for(n, 256), 256, 0, s>>>(
         M.g, M.bbox[0], M.bbox[1], M.bbox[2], M.bbox[3], M.nv, M.xy.as<double>(), M.ntri,
         M.tri.as<int32_t>(), M.tsign.as<int8_t>(), M.cell_start.as<int32_t>(),
-        M.items.as<int32_t>(), pts, n, field, elem, edim, vals);
+        M.items.as<int32_t>(), M.vhl.as<float4>(), M.origin[0], M.origin[1], M.delta, M.use32,
+        pts, n, field, elem, edim, vals);
     PCMS_LAUNCH_CHECK("k_locate");
 }
 

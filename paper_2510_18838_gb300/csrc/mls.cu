@@ -14,9 +14,9 @@ constexpr double TAU_FP64 = 1e-14;   // (1e-7)^2: column-angle rank test of the 
 constexpr double TAU_MIXED = 1e-5;   // plain-FP32 pivots below this go to the next tier
 constexpr double TAU_BK = 1e-7;      // blocked-compensated pivots below this go on (noise ~1e-8)
 
-// stored moment type of a first-pass assembly
-int mom_kind(bool mixed, int mode, int G) {
-    return !mixed ? MOM_F64 : (assembles_bk(mixed, mode, G) ? MOM_F32PAIR : MOM_F32);
+// stored moment type of an assembly
+int mom_kind(bool mixed, int acc) {
+    return !mixed ? MOM_F64 : (acc == ACC_BK ? MOM_F32PAIR : MOM_F32);
 }
 size_t mom_elem_bytes(int kind) { return kind == MOM_F32 ? sizeof(float) : sizeof(double); }
 
@@ -31,13 +31,25 @@ int thread_blocks(int64_t n, int threads) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 32));
 }
 
-// lanes per target from the expected neighbour count (ns * ball volume / box volume)
-int choose_group(int dim, int64_t ns, double radius, const double* lo, const double* hi) {
+// Lanes per target and the first pass's accumulation, from the expected neighbour count
+// (ns * ball volume / box volume): 32 lanes from 160 neighbours on; blocked compensation
+// (mixed path) from 1000 on, where plain FP32 sums over n / 32 pairs per lane stop meeting
+// the error bound for ordinary targets. Below that plain sums pass for almost every target
+// and the blocked form would only cost registers.
+struct AsmPlan {
+    int G;
+    int acc;
+};
+AsmPlan choose_plan(int dim, int64_t ns, double radius, const double* lo, const double* hi,
+                    bool mixed) {
     double vol = 1.0;
     for (int d = 0; d < dim; d++) vol *= std::max(hi[d] - lo[d], radius);
     double ball = dim == 2 ? M_PI * radius * radius : 4.0 / 3.0 * M_PI * radius * radius * radius;
     double mean = (double)ns * ball / vol;
-    return mean >= 160.0 ? 32 : 8;
+    AsmPlan p;
+    p.G = mean >= 160.0 ? 32 : 8;
+    p.acc = (mixed && p.G == 32 && mean >= 1000.0) ? ACC_BK : ACC_PLAIN;
+    return p;
 }
 
 __global__ void k_stats(const int8_t* status, const int32_t* counts, const int32_t* kexp,
@@ -164,10 +176,11 @@ int accp(int dim, int deg, int mode) {
 // when lambda = 0) and tier 3 (FP64). `a` holds the assembly arguments of tier 1
 // (mode-specific fields set). The mixed path syncs to size the tier-2/3 work; the FP64 path
 // has a single tier. rc: MAP only, per-target basis of re-centred operator rows.
-void solve_tiers(int dim, int deg, int mode, bool mixed, int G, const AsmArgs& a,
+void solve_tiers(int dim, int deg, int mode, bool mixed, AsmPlan plan, const AsmArgs& a,
                  SolveArgs sa, int64_t nt, float4* rc, cudaStream_t s) {
     const int np = accp(dim, deg, mode);
-    const int mk1 = mom_kind(mixed, mode, G);
+    const int G = plan.G;
+    const int mk1 = mom_kind(mixed, plan.acc);
     DBuf lists(sizeof(int32_t) * (2 * nt + 2), s);
     int32_t* list2 = lists.as<int32_t>();
     int32_t* list3 = list2 + nt;
@@ -209,7 +222,7 @@ void solve_tiers(int dim, int deg, int mode, bool mixed, int G, const AsmArgs& a
         } else {
             a2.cols = nullptr;   // the operator's columns are already written
         }
-        assemble_any(dim, deg, true, mode, 32, false, a2, asm_blocks(cnt[0], 32), s);
+        assemble_any(dim, deg, true, mode, 32, ACC_BK, false, a2, asm_blocks(cnt[0], 32), s);
         SolveArgs s2 = sa;
         s2.list = list2;
         s2.n_list = n2;
@@ -239,7 +252,7 @@ void solve_tiers(int dim, int deg, int mode, bool mixed, int G, const AsmArgs& a
         } else {
             a3.cols = nullptr;
         }
-        assemble_any(dim, deg, false, mode, G, false, a3, asm_blocks(cnt[1], G), s);
+        assemble_any(dim, deg, false, mode, G, ACC_PLAIN, false, a3, asm_blocks(cnt[1], G), s);
         SolveArgs s3 = sa;
         s3.list = list3;
         s3.n_list = n3;
@@ -311,7 +324,8 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
     M.g = make_grid(dim, b.lo, b.hi, 0.5 * P.radius, MAX_CELLS);
     sort_points(M.g, src, ns, true, mixed, M.src, s);
     sort_points(M.g, tgt, nt, false, mixed, M.tgt, s);
-    const int G = choose_group(dim, ns, P.radius, b.lo, b.hi);
+    const AsmPlan plan = choose_plan(dim, ns, P.radius, b.lo, b.hi, mixed);
+    const int G = plan.G;
 
     M.counts.alloc(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
     M.kexp.alloc(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
@@ -325,7 +339,7 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
     a.counts = M.counts.as<int32_t>();
     a.kexp_out = M.kexp.as<int32_t>();
     if (nt > 0)
-        assemble_any(dim, 0, mixed, MODE_COUNT, G, false, a, asm_blocks(nt, G), s);
+        assemble_any(dim, 0, mixed, MODE_COUNT, G, ACC_PLAIN, false, a, asm_blocks(nt, G), s);
     exclusive_scan<int64_t>(M.counts.as<int32_t>(), M.offsets.as<int64_t>(), nt, s);
     int64_t nnz = 0;
     PCMS_CU(cudaMemcpyAsync(&nnz, M.offsets.as<int64_t>() + nt, sizeof(int64_t),
@@ -337,7 +351,7 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
 
     if (nt > 0) {
         const int np = accp(dim, deg, MODE_MAP);
-        DBuf mom(mom_elem_bytes(mom_kind(mixed, MODE_MAP, G)) * np * nt, s);
+        DBuf mom(mom_elem_bytes(mom_kind(mixed, plan.acc)) * np * nt, s);
         DBuf y(sizeof(double) * m * nt, s);
         DBuf flags(sizeof(int8_t) * nt, s);
         DBuf rc(mixed ? sizeof(float4) * nt : 0, s);
@@ -346,7 +360,7 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
         a.offsets = M.offsets.as<int64_t>();
         a.cols = M.cols.as<int32_t>();
         a.mom = mom.p;
-        assemble_any(dim, deg, mixed, MODE_MAP, G, false, a, asm_blocks(nt, G), s);
+        assemble_any(dim, deg, mixed, MODE_MAP, G, plan.acc, false, a, asm_blocks(nt, G), s);
 
         SolveArgs sa{};
         sa.nt = nt;
@@ -356,7 +370,7 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
         sa.y = y.as<double>();
         sa.flags = mixed ? flags.as<int8_t>() : nullptr;
         sa.status = M.status.as<int8_t>();
-        solve_tiers(dim, deg, MODE_MAP, mixed, G, a, sa, nt, mixed ? rc.as<float4>() : nullptr, s);
+        solve_tiers(dim, deg, MODE_MAP, mixed, plan, a, sa, nt, mixed ? rc.as<float4>() : nullptr, s);
 
         ShapeArgs sh{};
         sh.flags = mixed ? flags.as<int8_t>() : nullptr;
@@ -428,7 +442,7 @@ void mls_count(const MlsParams& P, const double* src, int64_t ns, const double* 
     SortedPoints S, Tp;
     sort_points(g, src, ns, true, mixed, S, s);
     sort_points(g, tgt, nt, false, mixed, Tp, s);
-    const int G = choose_group(dim, ns, P.radius, b.lo, b.hi);
+    const int G = choose_plan(dim, ns, P.radius, b.lo, b.hi, mixed).G;
     DBuf c(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
     DBuf k(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
     DBuf off(sizeof(int64_t) * (nt + 1), s);
@@ -436,7 +450,7 @@ void mls_count(const MlsParams& P, const double* src, int64_t ns, const double* 
         AsmArgs a = base_args(g, S, Tp, P);
         a.counts = c.as<int32_t>();
         a.kexp_out = k.as<int32_t>();
-        assemble_any(dim, 0, mixed, MODE_COUNT, G, false, a, asm_blocks(nt, G), s);
+        assemble_any(dim, 0, mixed, MODE_COUNT, G, ACC_PLAIN, false, a, asm_blocks(nt, G), s);
         PCMS_TRACE("mls_counts_to_caller", s);
         k_counts_to_caller<<<thread_blocks(nt, 256), 256, 0, s>>>(
             nt, Tp.perm.as<int32_t>(), c.as<int32_t>(), k.as<int32_t>(), counts, kexp);
@@ -464,13 +478,14 @@ void mls_transfer(const MlsParams& P, const double* src, int64_t ns, const doubl
     SortedPoints S, Tp;
     sort_points(g, src, ns, true, mixed, S, s);
     sort_points(g, tgt, nt, false, mixed, Tp, s);
-    const int G = choose_group(dim, ns, P.radius, b.lo, b.hi);
+    const AsmPlan plan = choose_plan(dim, ns, P.radius, b.lo, b.hi, mixed);
+    const int G = plan.G;
     const size_t fsz = mixed ? sizeof(float) : sizeof(double);
     DBuf fs(fsz * std::max<int64_t>(ns, 1), s);
     DBuf counts(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
     DBuf kexp(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
     const int np = accp(dim, deg, MODE_FUSED);
-    DBuf mom(mom_elem_bytes(mom_kind(mixed, MODE_FUSED, G)) * np * std::max<int64_t>(nt, 1), s);
+    DBuf mom(mom_elem_bytes(mom_kind(mixed, plan.acc)) * np * std::max<int64_t>(nt, 1), s);
     for (int f = 0; f < nf; f++) {
         if (ns > 0) {
             PCMS_TRACE("mls_field_to_sorted", s);
@@ -488,7 +503,7 @@ void mls_transfer(const MlsParams& P, const double* src, int64_t ns, const doubl
         a.kexp_out = kexp.as<int32_t>();
         a.field = fs.p;
         a.mom = mom.p;
-        assemble_any(dim, deg, mixed, MODE_FUSED, G, !mixed, a, asm_blocks(nt, G), s);
+        assemble_any(dim, deg, mixed, MODE_FUSED, G, plan.acc, !mixed, a, asm_blocks(nt, G), s);
         SolveArgs sa{};
         sa.nt = nt;
         sa.counts = counts.as<int32_t>();
@@ -498,7 +513,7 @@ void mls_transfer(const MlsParams& P, const double* src, int64_t ns, const doubl
         sa.out = (char*)out + fsz * (size_t)f * nt;
         sa.out_is_double = !mixed;
         sa.status = f == 0 ? status : nullptr;
-        solve_tiers(dim, deg, MODE_FUSED, mixed, G, a, sa, nt, nullptr, s);
+        solve_tiers(dim, deg, MODE_FUSED, mixed, plan, a, sa, nt, nullptr, s);
     }
     if (status && P.min_neighbors == 0 && nt > 0) {
         DBuf st(sizeof(unsigned long long) * 4, s);

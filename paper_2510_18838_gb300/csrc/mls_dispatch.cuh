@@ -10,8 +10,9 @@ namespace pcms {
 // assemble: mode MODE_COUNT / MODE_MAP / MODE_FUSED; G = lanes per target (8 or 32);
 // field_double: FUSED field type (float or double)
 #define PCMS_DECLARE_MLS_DISPATCH(DIMV)                                                       \
-    void assemble_dispatch_d##DIMV(int deg, bool mixed, int mode, int G, bool field_double,   \
-                                   const AsmArgs& a, int blocks, cudaStream_t s);             \
+    void assemble_dispatch_d##DIMV(int deg, bool mixed, int mode, int G, int acc,             \
+                                   bool field_double, const AsmArgs& a, int blocks,           \
+                                   cudaStream_t s);                                           \
     void solve_dispatch_d##DIMV(int deg, int mode, int mom_kind, const SolveArgs& a,          \
                                 int blocks, cudaStream_t s);                                  \
     void shape_dispatch_d##DIMV(int deg, bool mixed, int G, const ShapeArgs& a, int blocks,   \
@@ -22,15 +23,11 @@ PCMS_DECLARE_MLS_DISPATCH(3)
 // stored moment types of the solve
 enum { MOM_F32 = 0, MOM_F32PAIR = 1, MOM_F64 = 2 };
 
-// Mixed MAP/FUSED assembly with 32 lanes per target uses blocked compensation (ACC_BK,
-// float2 moments): tier 1 of large neighbourhoods, and tier 2 (a target list). Everything
-// else accumulates plainly (float moments on the mixed path, double on the FP64 path).
-inline bool assembles_bk(bool mixed, int mode, int G) {
-    return mixed && mode != MODE_COUNT && G == 32;
-}
-
-inline void assemble_any(int dim, int deg, bool mixed, int mode, int G, bool fd,
+// acc: ACC_PLAIN, or ACC_BK (mixed MAP/FUSED with 32 lanes per target only: blocked
+// compensation, float2 moments) for tier 1 of very large neighbourhoods and for tier 2.
+inline void assemble_any(int dim, int deg, bool mixed, int mode, int G, int acc, bool fd,
                          const AsmArgs& a, int blocks, cudaStream_t s) {
+    const bool bk = mixed && mode != MODE_COUNT && G == 32 && acc == ACC_BK;
     // a target list means a later tier of the mixed path (tier 2: blocked FP32, tier 3: FP64)
     static const char* names[5][3] = {
         {"mls_count_fp64", "mls_assemble_map_fp64", "mls_assemble_fused_fp64"},
@@ -38,11 +35,10 @@ inline void assemble_any(int dim, int deg, bool mixed, int mode, int G, bool fd,
         {"mls_count_mixed", "mls_assemble_map_bk", "mls_assemble_fused_bk"},
         {"mls_count_mixed", "mls_assemble_map_tier2", "mls_assemble_fused_tier2"},
         {"mls_count_fp64", "mls_assemble_map_tier3", "mls_assemble_fused_tier3"}};
-    const int row = !mixed ? (a.list ? 4 : 0)
-                           : (!assembles_bk(mixed, mode, G) ? 1 : (a.list ? 3 : 2));
+    const int row = !mixed ? (a.list ? 4 : 0) : (!bk ? 1 : (a.list ? 3 : 2));
     PCMS_TRACE(names[row][mode], s);
-    if (dim == 2) assemble_dispatch_d2(deg, mixed, mode, G, fd, a, blocks, s);
-    else assemble_dispatch_d3(deg, mixed, mode, G, fd, a, blocks, s);
+    if (dim == 2) assemble_dispatch_d2(deg, mixed, mode, G, bk ? ACC_BK : ACC_PLAIN, fd, a, blocks, s);
+    else assemble_dispatch_d3(deg, mixed, mode, G, bk ? ACC_BK : ACC_PLAIN, fd, a, blocks, s);
 }
 inline void solve_any(int dim, int deg, int mode, int mom_kind, const SolveArgs& a, int blocks,
                       cudaStream_t s) {
@@ -63,13 +59,16 @@ inline void shape_any(int dim, int deg, bool mixed, int G, const ShapeArgs& a, i
 #define PCMS_DEFINE_MLS_DISPATCH(DIMV)                                                        \
     namespace pcms {                                                                          \
     template <int DEG, bool MIXED>                                                            \
-    static void asm_mode(int mode, int G, bool fd, const AsmArgs& a, int b, cudaStream_t s) { \
+    static void asm_mode(int mode, int G, int acc, bool fd, const AsmArgs& a, int b,          \
+                         cudaStream_t s) {                                                    \
         if (mode == MODE_COUNT) {                                                             \
             if (DEG != 0) return;                                                             \
             if (G == 32) k_assemble<DIMV, 0, MIXED, MODE_COUNT, 32, float><<<b, 256, 0, s>>>(a); \
             else k_assemble<DIMV, 0, MIXED, MODE_COUNT, 8, float><<<b, 256, 0, s>>>(a);       \
         } else if (mode == MODE_MAP) {                                                        \
-            if (G == 32) k_assemble<DIMV, DEG, MIXED, MODE_MAP, 32, float, MIXED ? ACC_BK : ACC_PLAIN><<<b, 256, 0, s>>>(a); \
+            if (G == 32 && MIXED && acc == ACC_BK)                                            \
+                k_assemble<DIMV, DEG, MIXED, MODE_MAP, 32, float, MIXED ? ACC_BK : ACC_PLAIN><<<b, 256, 0, s>>>(a); \
+            else if (G == 32) k_assemble<DIMV, DEG, MIXED, MODE_MAP, 32, float><<<b, 256, 0, s>>>(a); \
             else k_assemble<DIMV, DEG, MIXED, MODE_MAP, 8, float><<<b, 256, 0, s>>>(a);       \
         } else {                                                                              \
             if (fd) {                                                                         \
@@ -78,22 +77,24 @@ inline void shape_any(int dim, int deg, bool mixed, int G, const ShapeArgs& a, i
                     else k_assemble<DIMV, DEG, MIXED, MODE_FUSED, 8, double><<<b, 256, 0, s>>>(a); \
                 }                                                                             \
             } else {                                                                          \
-                if (G == 32) k_assemble<DIMV, DEG, MIXED, MODE_FUSED, 32, float, MIXED ? ACC_BK : ACC_PLAIN><<<b, 256, 0, s>>>(a); \
+                if (G == 32 && MIXED && acc == ACC_BK)                                        \
+                    k_assemble<DIMV, DEG, MIXED, MODE_FUSED, 32, float, MIXED ? ACC_BK : ACC_PLAIN><<<b, 256, 0, s>>>(a); \
+                else if (G == 32) k_assemble<DIMV, DEG, MIXED, MODE_FUSED, 32, float><<<b, 256, 0, s>>>(a); \
                 else k_assemble<DIMV, DEG, MIXED, MODE_FUSED, 8, float><<<b, 256, 0, s>>>(a);  \
             }                                                                                 \
         }                                                                                     \
     }                                                                                         \
-    void assemble_dispatch_d##DIMV(int deg, bool mixed, int mode, int G, bool fd,               \
+    void assemble_dispatch_d##DIMV(int deg, bool mixed, int mode, int G, int acc, bool fd,      \
                                  const AsmArgs& a, int b, cudaStream_t s) {                   \
         if (mode == MODE_COUNT) deg = 0;                                                      \
         if (mixed) {                                                                          \
-            if (deg == 0) asm_mode<0, true>(mode, G, fd, a, b, s);                            \
-            else if (deg == 1) asm_mode<1, true>(mode, G, fd, a, b, s);                       \
-            else asm_mode<2, true>(mode, G, fd, a, b, s);                                     \
+            if (deg == 0) asm_mode<0, true>(mode, G, acc, fd, a, b, s);                       \
+            else if (deg == 1) asm_mode<1, true>(mode, G, acc, fd, a, b, s);                  \
+            else asm_mode<2, true>(mode, G, acc, fd, a, b, s);                                \
         } else {                                                                              \
-            if (deg == 0) asm_mode<0, false>(mode, G, fd, a, b, s);                           \
-            else if (deg == 1) asm_mode<1, false>(mode, G, fd, a, b, s);                      \
-            else asm_mode<2, false>(mode, G, fd, a, b, s);                                    \
+            if (deg == 0) asm_mode<0, false>(mode, G, acc, fd, a, b, s);                      \
+            else if (deg == 1) asm_mode<1, false>(mode, G, acc, fd, a, b, s);                 \
+            else asm_mode<2, false>(mode, G, acc, fd, a, b, s);                               \
         }                                                                                     \
         PCMS_LAUNCH_CHECK("k_assemble");                                                      \
     }                                                                                         \

@@ -238,6 +238,10 @@ struct MeshImpl {
     DBuf cell_start;   // int32 [ncell+1]
     DBuf items;        // int32 [npairs] triangle ids, ascending within a cell
     DBuf tsign;        // int8 [ntri] orientation sign of each triangle (0 = degenerate)
+    DBuf vhl;          // float4 [nv] vertex (x_hi, y_hi, x_lo, y_lo) relative to `origin`
+    double origin[2];  // lower corner of the vertex box: the FP32 filter's frame
+    float delta = 0.f; // absolute error allowance of the FP32 differences (2^-44 x extent)
+    int use32 = 0;     // FP32 orientation filter usable (extent within [1e-30, 1e18])
 };
 
 void mesh_create(MeshImpl& M, const double* xy, int64_t nv, const int32_t* tri, int64_t ntri);

@@ -100,3 +100,26 @@ def test_full_mesh_config(P):
     """512 x 512 jittered grid (524,288 triangles), 1,000,000 uniform points, f = x^2+3xy."""
     c = W.mesh_2d()
     _check(P, c.xy, c.tri, c.pts, c.field, mode="grid")
+
+
+@pytest.mark.parametrize("scale", [1.0, 1e-5, 3e4])
+def test_points_a_hair_off_the_edges(P, scale):
+    """Points displaced from edge midpoints by 1e-16 .. 1e-6 of the edge length, on both sides
+    (and exactly on, up to rounding): the orientation signs there are far below what FP32
+    resolves, so location must defer to the FP64 filter and the exact expansion and still
+    give the oracle's element ids. Meshes at several coordinate scales exercise the FP32
+    filter's error allowance, which is proportional to the extent."""
+    xy, tri = W.jittered_grid_mesh(48, 0.3, seed=31)
+    xy = xy * scale + np.array([[0.25 * scale], [-0.5 * scale]])
+    rng = np.random.default_rng(32)
+    k = rng.integers(0, tri.shape[1], 3000)
+    e = rng.integers(0, 3, 3000)
+    a = xy[:, tri[e, k]]
+    b = xy[:, tri[(e + 1) % 3, k]]
+    t = rng.uniform(0.05, 0.95, 3000)
+    base = a + t * (b - a)
+    nrm = np.stack([-(b - a)[1], (b - a)[0]])
+    eps = 10.0 ** rng.uniform(-16, -6, 3000) * rng.choice([-1.0, 0.0, 1.0], 3000)
+    pts = np.concatenate([base + eps * nrm, W.uniform_points(3000, 2, 33) * scale * 0.9], axis=1)
+    f = xy[0] / scale + 2 * xy[1] / scale
+    _check(P, xy, tri, pts, f, mode="grid")
