@@ -120,6 +120,7 @@ __device__ __forceinline__ int64_t spmm_next_chunk(unsigned long long* next) {
 // status is not OK produce NaN.
 template <typename T, int NV>
 __global__ void __launch_bounds__(256) k_spmm_vec(int64_t nt, const int64_t* __restrict__ off,
+                                                  const int32_t* __restrict__ cnt,
                                                   const int32_t* __restrict__ cols,
                                                   const T* __restrict__ vals,
                                                   const T* __restrict__ fs,
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(256) k_spmm_vec(int64_t nt, const int64_t* __r
         T wA = T(0);
         if (t < c1) {
             a = off[t];
-            b = off[t + 1];
+            b = a + cnt[t];
             if (a + lane < b) {
                 jA = __ldg(cols + a + lane);
                 wA = __ldg(vals + a + lane);
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(256) k_spmm_vec(int64_t nt, const int64_t* __r
             int64_t an = 0, bn = 0;
             if (tn < c1) {
                 an = off[tn];
-                bn = off[tn + 1];
+                bn = an + cnt[tn];
             }
             V acc{};
             for (int64_t e0 = a; e0 < b; e0 += 32) {
@@ -208,6 +209,7 @@ __global__ void __launch_bounds__(256) k_spmm_vec(int64_t nt, const int64_t* __r
 // one field: lanes over nonzeros, 64 in flight, rows in chunks as above
 template <typename T>
 __global__ void __launch_bounds__(256) k_spmm_1(int64_t nt, const int64_t* __restrict__ off,
+                                                const int32_t* __restrict__ cnt,
                                                 const int32_t* __restrict__ cols,
                                                 const T* __restrict__ vals,
                                                 const T* __restrict__ fs,
@@ -221,7 +223,7 @@ __global__ void __launch_bounds__(256) k_spmm_1(int64_t nt, const int64_t* __res
         if (c0 >= nt) break;
         const int64_t c1 = min(c0 + (int64_t)SPMM_ROWS, nt);
         for (int64_t t = c0 + wib; t < c1; t += nwb) {
-            const int64_t a = off[t], b = off[t + 1];
+            const int64_t a = off[t], b = a + cnt[t];
             T acc = T(0);
             for (int64_t e = a + lane; e < b; e += 64) {
                 const bool two = e + 32 < b;
@@ -281,6 +283,7 @@ void apply_t(MapImpl& M, const T* fields, int nf, T* out, cudaStream_t s) {
     if (nt > 0) {
         PCMS_TRACE("apply_spmm", s);
         const int64_t* off = M.offsets.as<int64_t>();
+        const int32_t* rc = M.counts.as<int32_t>();
         const int32_t* cols = M.cols.as<int32_t>();
         const T* vals = M.vals.as<T>();
         const int8_t* st = M.status.as<int8_t>();
@@ -290,11 +293,11 @@ void apply_t(MapImpl& M, const T* fields, int nf, T* out, cudaStream_t s) {
         int nv = fp / W;
         T* fsp = fs.as<T>();
         T* stp = stage.as<T>();
-        if (fp == 1) k_spmm_1<T><<<spmm_blocks(k_spmm_1<T>, nt), 256, 0, s>>>(nt, off, cols, vals, fsp, st, stp, next);
-        else if (nv == 1) k_spmm_vec<T, 1><<<spmm_blocks(k_spmm_vec<T, 1>, nt), 256, 0, s>>>(nt, off, cols, vals, fsp, st, stp, next);
-        else if (nv == 2) k_spmm_vec<T, 2><<<spmm_blocks(k_spmm_vec<T, 2>, nt), 256, 0, s>>>(nt, off, cols, vals, fsp, st, stp, next);
-        else if (nv == 4) k_spmm_vec<T, 4><<<spmm_blocks(k_spmm_vec<T, 4>, nt), 256, 0, s>>>(nt, off, cols, vals, fsp, st, stp, next);
-        else if (nv == 8) k_spmm_vec<T, 8><<<spmm_blocks(k_spmm_vec<T, 8>, nt), 256, 0, s>>>(nt, off, cols, vals, fsp, st, stp, next);
+        if (fp == 1) k_spmm_1<T><<<spmm_blocks(k_spmm_1<T>, nt), 256, 0, s>>>(nt, off, rc, cols, vals, fsp, st, stp, next);
+        else if (nv == 1) k_spmm_vec<T, 1><<<spmm_blocks(k_spmm_vec<T, 1>, nt), 256, 0, s>>>(nt, off, rc, cols, vals, fsp, st, stp, next);
+        else if (nv == 2) k_spmm_vec<T, 2><<<spmm_blocks(k_spmm_vec<T, 2>, nt), 256, 0, s>>>(nt, off, rc, cols, vals, fsp, st, stp, next);
+        else if (nv == 4) k_spmm_vec<T, 4><<<spmm_blocks(k_spmm_vec<T, 4>, nt), 256, 0, s>>>(nt, off, rc, cols, vals, fsp, st, stp, next);
+        else if (nv == 8) k_spmm_vec<T, 8><<<spmm_blocks(k_spmm_vec<T, 8>, nt), 256, 0, s>>>(nt, off, rc, cols, vals, fsp, st, stp, next);
         else {
             fail(PCMS_ERR_INVALID_ARG, "internal: field padding");
         }
@@ -323,17 +326,18 @@ cudaError_t apply_with_scratch_t(const MapImpl& M, const T* fields, int nf, T* o
                                                                   M.src.inv.as<int32_t>(), fs);
     if (nt > 0) {
         const int64_t* off = M.offsets.as<int64_t>();
+        const int32_t* rc = M.counts.as<int32_t>();
         const int32_t* cols = M.cols.as<int32_t>();
         const T* vals = M.vals.as<T>();
         const int8_t* st = M.status.as<int8_t>();
         const cudaError_t me = cudaMemsetAsync(next, 0, sizeof(unsigned long long), s);
         if (me != cudaSuccess) return me;
         const int nv = fp / W;
-        if (fp == 1) k_spmm_1<T><<<spmm_blocks(k_spmm_1<T>, nt), 256, 0, s>>>(nt, off, cols, vals, fs, st, stage, next);
-        else if (nv == 1) k_spmm_vec<T, 1><<<spmm_blocks(k_spmm_vec<T, 1>, nt), 256, 0, s>>>(nt, off, cols, vals, fs, st, stage, next);
-        else if (nv == 2) k_spmm_vec<T, 2><<<spmm_blocks(k_spmm_vec<T, 2>, nt), 256, 0, s>>>(nt, off, cols, vals, fs, st, stage, next);
-        else if (nv == 4) k_spmm_vec<T, 4><<<spmm_blocks(k_spmm_vec<T, 4>, nt), 256, 0, s>>>(nt, off, cols, vals, fs, st, stage, next);
-        else k_spmm_vec<T, 8><<<spmm_blocks(k_spmm_vec<T, 8>, nt), 256, 0, s>>>(nt, off, cols, vals, fs, st, stage, next);
+        if (fp == 1) k_spmm_1<T><<<spmm_blocks(k_spmm_1<T>, nt), 256, 0, s>>>(nt, off, rc, cols, vals, fs, st, stage, next);
+        else if (nv == 1) k_spmm_vec<T, 1><<<spmm_blocks(k_spmm_vec<T, 1>, nt), 256, 0, s>>>(nt, off, rc, cols, vals, fs, st, stage, next);
+        else if (nv == 2) k_spmm_vec<T, 2><<<spmm_blocks(k_spmm_vec<T, 2>, nt), 256, 0, s>>>(nt, off, rc, cols, vals, fs, st, stage, next);
+        else if (nv == 4) k_spmm_vec<T, 4><<<spmm_blocks(k_spmm_vec<T, 4>, nt), 256, 0, s>>>(nt, off, rc, cols, vals, fs, st, stage, next);
+        else k_spmm_vec<T, 8><<<spmm_blocks(k_spmm_vec<T, 8>, nt), 256, 0, s>>>(nt, off, rc, cols, vals, fs, st, stage, next);
         k_stage_to_caller<T><<<blocks_for(nt, 256), 256, 0, s>>>(stage, fp, nf, nt,
                                                                  M.tgt.inv.as<int32_t>(), out);
     }
@@ -342,17 +346,16 @@ cudaError_t apply_with_scratch_t(const MapImpl& M, const T* fields, int nf, T* o
 
 // export: row lengths in caller order, scan, then a warp per row copies (col, val)
 __global__ void k_export_len(int64_t nt, const int32_t* __restrict__ inv_t,
-                             const int64_t* __restrict__ off, int32_t* __restrict__ len) {
+                             const int32_t* __restrict__ cnt, int32_t* __restrict__ len) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t p = inv_t[i];
-        len[i] = (int32_t)(off[p + 1] - off[p]);
-    }
+         i += (int64_t)gridDim.x * blockDim.x)
+        len[i] = cnt[inv_t[i]];
 }
 
 template <typename T>
 __global__ void k_export_rows(int64_t nt, const int32_t* __restrict__ inv_t,
-                              const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
+                              const int64_t* __restrict__ off, const int32_t* __restrict__ cnt,
+                              const int32_t* __restrict__ cols,
                               const T* __restrict__ vals, const int32_t* __restrict__ perm_s,
                               const int8_t* __restrict__ st, const int32_t* __restrict__ kx,
                               const int64_t* __restrict__ off_out, int32_t* __restrict__ cols_out,
@@ -363,7 +366,7 @@ __global__ void k_export_rows(int64_t nt, const int32_t* __restrict__ inv_t,
     for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < nt;
          i += nwarps) {
         const int64_t p = inv_t[i];
-        const int64_t a = off[p], b = off[p + 1], o = off_out[i];
+        const int64_t a = off[p], b = a + cnt[p], o = off_out[i];
         for (int64_t e = a + lane; e < b; e += 32) {
             cols_out[o + (e - a)] = perm_s[cols[e]];
             if (vals_out) vals_out[o + (e - a)] = (double)vals[e];
@@ -435,19 +438,19 @@ void mls_export(MapImpl& M, int64_t* offsets, int32_t* cols, double* vals, int8_
     DBuf len(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
     if (nt > 0)
         k_export_len<<<blocks_for(nt, 256), 256, 0, s>>>(nt, M.tgt.inv.as<int32_t>(),
-                                                         M.offsets.as<int64_t>(), len.as<int32_t>());
+                                                         M.counts.as<int32_t>(), len.as<int32_t>());
     exclusive_scan<int64_t>(len.as<int32_t>(), offsets, nt, s);
     if (nt > 0) {
         int blocks = blocks_for(nt * 32, 256, 16);
         if (M.P.prec == PCMS_MIXED)
             k_export_rows<float><<<blocks, 256, 0, s>>>(
-                nt, M.tgt.inv.as<int32_t>(), M.offsets.as<int64_t>(), M.cols.as<int32_t>(),
-                M.vals.as<float>(), M.src.perm.as<int32_t>(), M.status.as<int8_t>(),
+                nt, M.tgt.inv.as<int32_t>(), M.offsets.as<int64_t>(), M.counts.as<int32_t>(),
+                M.cols.as<int32_t>(), M.vals.as<float>(), M.src.perm.as<int32_t>(), M.status.as<int8_t>(),
                 M.kexp.as<int32_t>(), offsets, cols, vals, status, kexp);
         else
             k_export_rows<double><<<blocks, 256, 0, s>>>(
-                nt, M.tgt.inv.as<int32_t>(), M.offsets.as<int64_t>(), M.cols.as<int32_t>(),
-                M.vals.as<double>(), M.src.perm.as<int32_t>(), M.status.as<int8_t>(),
+                nt, M.tgt.inv.as<int32_t>(), M.offsets.as<int64_t>(), M.counts.as<int32_t>(),
+                M.cols.as<int32_t>(), M.vals.as<double>(), M.src.perm.as<int32_t>(), M.status.as<int8_t>(),
                 M.kexp.as<int32_t>(), offsets, cols, vals, status, kexp);
     }
     PCMS_LAUNCH_CHECK("export");

@@ -39,6 +39,7 @@ int thread_blocks(int64_t n, int threads) {
 struct AsmPlan {
     int G;
     int acc;
+    double mean;   // expected neighbours per target
 };
 AsmPlan choose_plan(int dim, int64_t ns, double radius, const double* lo, const double* hi,
                     bool mixed) {
@@ -47,14 +48,17 @@ AsmPlan choose_plan(int dim, int64_t ns, double radius, const double* lo, const 
     double ball = dim == 2 ? M_PI * radius * radius : 4.0 / 3.0 * M_PI * radius * radius * radius;
     double mean = (double)ns * ball / vol;
     AsmPlan p;
+    p.mean = mean;
     p.G = mean >= 160.0 ? 32 : 8;
     p.acc = (mixed && p.G == 32 && mean >= 1000.0) ? ACC_BK : ACC_PLAIN;
     return p;
 }
 
+// out: [0] underdetermined, [1] ill-conditioned, [2] max count, [3] max doublings,
+//      [4] sum of counts (the operator's nonzeros)
 __global__ void k_stats(const int8_t* status, const int32_t* counts, const int32_t* kexp,
                         int64_t n, unsigned long long* out) {
-    unsigned long long under = 0, ill = 0, mc = 0, mk = 0;
+    unsigned long long under = 0, ill = 0, mc = 0, mk = 0, sc = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         int8_t st = status[i];
@@ -62,18 +66,21 @@ __global__ void k_stats(const int8_t* status, const int32_t* counts, const int32
         ill += st == PCMS_TARGET_ILL_CONDITIONED;
         mc = max(mc, (unsigned long long)counts[i]);
         mk = max(mk, (unsigned long long)kexp[i]);
+        sc += (unsigned long long)counts[i];
     }
     for (int o = 16; o > 0; o >>= 1) {
         under += __shfl_xor_sync(0xffffffffu, under, o);
         ill += __shfl_xor_sync(0xffffffffu, ill, o);
         mc = max(mc, __shfl_xor_sync(0xffffffffu, mc, o));
         mk = max(mk, __shfl_xor_sync(0xffffffffu, mk, o));
+        sc += __shfl_xor_sync(0xffffffffu, sc, o);
     }
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&out[0], under);
         atomicAdd(&out[1], ill);
         atomicMax(&out[2], mc);
         atomicMax(&out[3], mk);
+        atomicAdd(&out[4], sc);
     }
 }
 
@@ -297,7 +304,7 @@ int64_t estimate_mls_bytes(const MlsParams& P, int64_t ns, int64_t nt, int nf, b
     b += nt * (4.0 + 4.0 + 1.0 + 8.0 + 4.0);                         // counts, kexp, status, offsets, redo
     b += nt * (np * 8.0 + P.m * 8.0);                                // moments, y
     if (mixed) b += nt * 32.0;                                       // tier-2 bases
-    const double nnz = 1.2 * k * nt;
+    const double nnz = 1.3 * k * nt;
     if (keep_map || nf > 2) b += nnz * (4.0 + elem);                 // operator
     b += (double)(ns + nt) * std::max(nf, 1) * elem * 2.0;           // apply/permute scratch
     b += 4.0 * std::min<double>((double)(int64_t(1) << 24), 2.0 * ns + 64.0);  // cell starts
@@ -338,29 +345,81 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
     a.err = err.as<unsigned>();
     a.counts = M.counts.as<int32_t>();
     a.kexp_out = M.kexp.as<int32_t>();
-    if (nt > 0)
-        assemble_any(dim, 0, mixed, MODE_COUNT, G, ACC_PLAIN, false, a, asm_blocks(nt, G), s);
-    exclusive_scan<int64_t>(M.counts.as<int32_t>(), M.offsets.as<int64_t>(), nt, s);
+    // Rows. With a fixed radius the assembly stages each target's columns, reserves its row
+    // with one atomic add and writes it (one pass; the rare rows that do not fit are walked
+    // again). When the radius may grow, a count pass finds the doublings and the row sizes.
+    const bool one_pass = P.need == 0;
     int64_t nnz = 0;
-    PCMS_CU(cudaMemcpyAsync(&nnz, M.offsets.as<int64_t>() + nt, sizeof(int64_t),
-                            cudaMemcpyDeviceToHost, s));
-    PCMS_CU(cudaStreamSynchronize(s));
-    M.nnz = nnz;
-    M.cols.alloc(sizeof(int32_t) * std::max<int64_t>(nnz, 1), s);
-    M.vals.alloc((mixed ? sizeof(float) : sizeof(double)) * std::max<int64_t>(nnz, 1), s);
+    if (!one_pass) {
+        if (nt > 0)
+            assemble_any(dim, 0, mixed, MODE_COUNT, G, ACC_PLAIN, false, a, asm_blocks(nt, G), s);
+        exclusive_scan<int64_t>(M.counts.as<int32_t>(), M.offsets.as<int64_t>(), nt, s);
+        PCMS_CU(cudaMemcpyAsync(&nnz, M.offsets.as<int64_t>() + nt, sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, s));
+        PCMS_CU(cudaStreamSynchronize(s));
+        M.cols.alloc(sizeof(int32_t) * std::max<int64_t>(nnz, 1), s);
+    }
 
     if (nt > 0) {
         const int np = accp(dim, deg, MODE_MAP);
-        DBuf mom(mom_elem_bytes(mom_kind(mixed, plan.acc)) * np * nt, s);
+        const size_t melem = mom_elem_bytes(mom_kind(mixed, plan.acc));
+        DBuf mom(melem * np * nt, s);
         DBuf y(sizeof(double) * m * nt, s);
         DBuf flags(sizeof(int8_t) * nt, s);
         DBuf rc(mixed ? sizeof(float4) * nt : 0, s);
-        a.kexp_in = M.kexp.as<int32_t>();
-        a.kexp_out = nullptr;
         a.offsets = M.offsets.as<int64_t>();
-        a.cols = M.cols.as<int32_t>();
         a.mom = mom.p;
-        assemble_any(dim, deg, mixed, MODE_MAP, G, plan.acc, false, a, asm_blocks(nt, G), s);
+        if (one_pass) {
+            const int64_t est = (int64_t)(1.3 * std::min(plan.mean, (double)ns) * (double)nt) + 4096;
+            M.cols.alloc(sizeof(int32_t) * est, s);
+            DBuf ctl(sizeof(unsigned long long) + sizeof(int32_t) * (nt + 2), s);
+            auto* ctr = ctl.as<unsigned long long>();
+            int32_t* n_redo = (int32_t*)(ctr + 1);
+            int32_t* redo = n_redo + 2;
+            PCMS_CU(cudaMemsetAsync(ctl.p, 0, sizeof(unsigned long long) + 2 * sizeof(int32_t), s));
+            a.one_pass = 1;
+            a.nnz_ctr = ctr;
+            a.cols_cap = est;
+            a.redo = redo;
+            a.n_redo = n_redo;
+            a.cols = M.cols.as<int32_t>();
+            a.kexp_in = nullptr;
+            a.kexp_out = M.kexp.as<int32_t>();
+            assemble_any(dim, deg, mixed, MODE_MAP, G, plan.acc, false, a, asm_blocks(nt, G), s);
+            unsigned long long hctr = 0;
+            int32_t hredo = 0;
+            PCMS_CU(cudaMemcpyAsync(&hctr, ctr, sizeof(hctr), cudaMemcpyDeviceToHost, s));
+            PCMS_CU(cudaMemcpyAsync(&hredo, n_redo, sizeof(hredo), cudaMemcpyDeviceToHost, s));
+            PCMS_CU(cudaStreamSynchronize(s));
+            nnz = (int64_t)hctr;
+            if (nnz > est) {   // rows reserved past the buffer: grow it, keep what was written
+                DBuf grown(sizeof(int32_t) * nnz, s);
+                PCMS_CU(cudaMemcpyAsync(grown.p, M.cols.p, sizeof(int32_t) * est,
+                                        cudaMemcpyDeviceToDevice, s));
+                M.cols = std::move(grown);
+            }
+            trace_count("mls_map_rows_walked_again", hredo);
+            a.one_pass = 0;
+            a.kexp_in = M.kexp.as<int32_t>();
+            a.kexp_out = nullptr;
+            if (hredo > 0) {   // rows that did not fit: walk again, writing at the reserved start
+                DBuf mom2(melem * np * hredo, s);
+                AsmArgs a2 = a;
+                a2.list = redo;
+                a2.n_list = n_redo;
+                a2.mom = mom2.p;
+                a2.cols = M.cols.as<int32_t>();
+                assemble_any(dim, deg, mixed, MODE_MAP, G, plan.acc, false, a2,
+                             asm_blocks(hredo, G), s);
+            }
+        } else {
+            a.kexp_in = M.kexp.as<int32_t>();
+            a.kexp_out = nullptr;
+            a.cols = M.cols.as<int32_t>();
+            assemble_any(dim, deg, mixed, MODE_MAP, G, plan.acc, false, a, asm_blocks(nt, G), s);
+        }
+        M.nnz = nnz;
+        M.vals.alloc((mixed ? sizeof(float) : sizeof(double)) * std::max<int64_t>(nnz, 1), s);
 
         SolveArgs sa{};
         sa.nt = nt;
@@ -387,6 +446,7 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
         sh.lv = a.lv;
         sh.kexp = M.kexp.as<int32_t>();
         sh.offsets = M.offsets.as<int64_t>();
+        sh.counts = M.counts.as<int32_t>();
         sh.cols = M.cols.as<int32_t>();
         sh.y = y.as<double>();
         sh.radius = P.radius;
@@ -396,7 +456,7 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
         M.tgt.hl0.release();   // the targets' hi/lo coordinates only serve the assembly
         M.tgt.hl1.release();
 
-        DBuf st(sizeof(unsigned long long) * 4, s);
+        DBuf st(sizeof(unsigned long long) * 5, s);
         PCMS_CU(cudaMemsetAsync(st.p, 0, st.bytes, s));
         {
         PCMS_TRACE("mls_status_stats", s);
@@ -405,16 +465,17 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
                                                       st.as<unsigned long long>());
         }
         PCMS_LAUNCH_CHECK("k_stats");
-        unsigned long long hs[4];
+        unsigned long long hs[5];
         unsigned herr = 0;
         PCMS_CU(cudaMemcpyAsync(hs, st.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
         PCMS_CU(cudaMemcpyAsync(&herr, err.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         PCMS_CU(cudaStreamSynchronize(s));
-        if (herr) fail(PCMS_ERR_CUDA, "internal: neighbour count mismatch between passes");
+        if (herr) fail(PCMS_ERR_CUDA, "internal: neighbour count above the row size");
         M.n_under = (int64_t)hs[0];
         M.n_ill = (int64_t)hs[1];
         M.max_count = (int64_t)hs[2];
         M.max_k = (int64_t)hs[3];
+        M.nnz = (int64_t)hs[4];
     }
 }
 

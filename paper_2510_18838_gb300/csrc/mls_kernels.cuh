@@ -89,8 +89,16 @@ struct AsmArgs {
     const int32_t* kexp_in;  // starting doublings (MAP: exact; FUSED redo: start), or null
     int32_t* kexp_out;       // COUNT/FUSED
     int32_t* counts;
-    const int64_t* offsets;  // MAP
-    int32_t* cols;           // MAP
+    int64_t* offsets;        // MAP: row starts (written in one-pass mode, read otherwise)
+    int32_t* cols;           // MAP: column indices, or null (tiers 2/3 only need moments)
+    // one-pass MAP (fixed radius): each group stages its target's columns in shared memory,
+    // then reserves exact space with one atomic add on nnz_ctr; targets whose columns did
+    // not fit the stage or the buffer (cols_cap) are listed in redo for a second walk
+    int one_pass;
+    unsigned long long* nnz_ctr;
+    int64_t cols_cap;
+    int32_t* redo;
+    int32_t* n_redo;
     const void* field;       // FUSED: sorted field (float or double)
     void* mom;               // MAP/FUSED: [nt][NACCP] (float, float2 for ACC_BK, or double)
     const float4* basis;     // ACC_BK list mode: per list position (c_x, c_y, c_z, 1/s), or null
@@ -161,7 +169,8 @@ struct ShapeArgs {
     const float2* thl1;
     RadiusLevels lv;
     const int32_t* kexp;
-    const int64_t* offsets;
+    const int64_t* offsets;   // row starts
+    const int32_t* counts;    // row lengths
     const int32_t* cols;
     const double* y;
     const int8_t* flags;   // per target (mixed maps), or null: see k_shape
@@ -452,6 +461,10 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemb
     QE* q = &qbuf[wib][gi * QCAP];
     int* rA = &rowa_s[wib][gi * G];
     int* rE = &rowe_s[wib][gi * G];
+    // one-pass MAP: staged column indices, STG per group (24 KB per block)
+    constexpr int STG = MODE == MODE_MAP ? (G == 32 ? 768 : 192) : 1;
+    __shared__ int32_t stg_s[MODE == MODE_MAP ? 8 * GPW * STG : 1];
+    int32_t* stg = &stg_s[MODE == MODE_MAP ? (wib * GPW + gi) * STG : 0];
     using CandT = Cand<MIXED, DIM, FT, MODE == MODE_FUSED>;
     // Dense one-shot targets (warp per target, blocked compensation): about 3 in 4 candidates
     // are selected, so every lane accumulates its own candidate with the weight zeroed when it
@@ -482,9 +495,10 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemb
         int k = A.kexp_in ? A.kexp_in[t] : 0;
         int cnt = 0;
         int64_t row_off = 0, row_len = 0;
-        if (MODE == MODE_MAP) {
+        const bool one_pass = MODE == MODE_MAP && A.one_pass;
+        if (MODE == MODE_MAP && !one_pass && A.cols) {   // a previous pass fixed the row
             row_off = A.offsets[t];
-            row_len = A.offsets[t + 1] - row_off;
+            row_len = A.counts[t];
         }
         // re-centred basis (blocked tier 2 only)
         T bcv[4] = {T(0), T(0), T(0), T(1)};
@@ -684,8 +698,11 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemb
                             }
                         }
                         if (MODE == MODE_MAP) {
-                            if (A.cols && written + gl < row_len)
+                            if (one_pass) {
+                                if (written + gl < STG) stg[written + gl] = unpack_index(e.w);
+                            } else if (A.cols && written + gl < row_len) {
                                 A.cols[row_off + written + gl] = unpack_index(e.w);
+                            }
                             written += G;
                         }
                         head = (head + G) & (QCAP - 1);
@@ -700,8 +717,13 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemb
                     QE e = q[(head + gl) & (QCAP - 1)];
                     T edx[3] = {e.x, e.y, e.z};
                     accumulate<DIM, DEG, MODE, T, NACC>(acc, edx, e.w, A.weight, inv_r, bc);
-                    if (MODE == MODE_MAP && A.cols && written + gl < row_len)
-                        A.cols[row_off + written + gl] = unpack_index(e.w);
+                    if (MODE == MODE_MAP) {
+                        if (one_pass) {
+                            if (written + gl < STG) stg[written + gl] = unpack_index(e.w);
+                        } else if (A.cols && written + gl < row_len) {
+                            A.cols[row_off + written + gl] = unpack_index(e.w);
+                        }
+                    }
                 }
                 __syncwarp(gmask);
             }
@@ -751,7 +773,22 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemb
             }
             A.counts[t] = cnt;
             if (A.kexp_out) A.kexp_out[t] = k;
-            if (MODE == MODE_MAP && cnt != row_len) atomicOr(A.err, 1u);
+            if (MODE == MODE_MAP && !one_pass && A.cols && cnt != row_len) atomicOr(A.err, 1u);
+        }
+        if (MODE == MODE_MAP && one_pass) {
+            // reserve the row, then copy the staged columns (or leave the row to the second walk)
+            unsigned long long base = 0;
+            if (gl == 0) base = atomicAdd(A.nnz_ctr, (unsigned long long)cnt);
+            base = __shfl_sync(gmask, base, 0, G);
+            const bool fits = cnt <= STG && (int64_t)(base + cnt) <= A.cols_cap;
+            __syncwarp(gmask);
+            if (fits)
+                for (int i = gl; i < cnt; i += G) A.cols[base + i] = stg[i];
+            if (gl == 0) {
+                A.offsets[t] = (int64_t)base;
+                if (!fits) A.redo[atomicAdd(A.n_redo, 1)] = (int32_t)t;
+            }
+            __syncwarp(gmask);   // the stage is reused by the group's next target
         }
     }
 }
@@ -1005,7 +1042,7 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
         T inv_r;
         if constexpr (MIXED) inv_r = S.lv.inv_rf[kx];
         else inv_r = S.lv.inv_r[kx];
-        const int64_t a = S.offsets[t], b = S.offsets[t + 1];
+        const int64_t a = S.offsets[t], b = a + S.counts[t];
         for (int64_t i = a + gl; i < b; i += G) {
             const int j = S.cols[i];
             if (MIXED && flag == 2) {

@@ -199,7 +199,7 @@ struct MapImpl {
     DBuf counts;     // int32 [nt] (sorted target order)
     DBuf kexp;       // int32 [nt]
     DBuf status;     // int8  [nt]
-    DBuf offsets;    // int64 [nt+1]
+    DBuf offsets;    // int64 [nt+1] row starts; row t is [offsets[t], offsets[t] + counts[t])
     DBuf cols;       // int32 [nnz] sorted source positions
     DBuf vals;       // float64 or float32 [nnz]
     int64_t n_under = 0, n_ill = 0, max_count = 0, max_k = 0;
