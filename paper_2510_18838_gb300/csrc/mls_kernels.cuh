@@ -806,6 +806,23 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemb
 // mom = [moments of degree <= 2k (graded-lex)] [g (FUSED only)]. Returns false when the
 // guard fails. Host-callable so the algebra can be checked without a GPU.
 // ------------------------------------------------------------------------------------
+// 1/x. On the device: Newton-Raphson from the FP32 reciprocal, two steps (2^-23 -> 2^-46 ->
+// below FP64 rounding), about half the FP64 instructions of an IEEE division; IEEE division
+// outside [1e-30, 1e30] and on the host.
+__host__ __device__ __forceinline__ double recip64(double x) {
+#ifdef __CUDA_ARCH__
+    const double ax = fabs(x);
+    if (ax > 1e-30 && ax < 1e30) {
+        double r = (double)__frcp_rn((float)x);
+        double e = fma(-x, r, 1.0);
+        r = fma(r, e, r);
+        e = fma(-x, r, 1.0);
+        return fma(r, e, r);
+    }
+#endif
+    return 1.0 / x;
+}
+
 template <int DIM, int DEG, int MODE>
 __host__ __device__ __forceinline__ bool solve_moments(const double* mom, double lambda,
                                                        double tau, double* out, double* c0,
@@ -844,7 +861,7 @@ __host__ __device__ __forceinline__ bool solve_moments(const double* mom, double
         });
         ok = ok && (dk > tau * gkk);
         L[k * (k + 1) / 2 + k] = dk;
-        invd[k] = 1.0 / dk;
+        invd[k] = recip64(dk);
     });
     if (!ok) return false;
     {
@@ -869,13 +886,21 @@ __host__ __device__ __forceinline__ bool solve_moments(const double* mom, double
             out[k] = a;
         });
     }
-    double s = 0.0, cc = 0.0;
-    for (int k = 0; k < M; k++) {
-        s += fabs(out[k]) * sqrt(fmax(diag[k], 0.0));
+    double cc = 0.0;
+    for (int k = 0; k < M; k++)
         if (MODE == MODE_FUSED) cc += out[k] * mom[NM + k];
-    }
-    if (amp) *amp = s * sqrt(fmax(diag[0], 0.0));
     if (c0) *c0 = cc;
+    if (amp) {   // an error estimate for routing: FP32 on the device (overflow gives inf: routed on)
+#ifdef __CUDA_ARCH__
+        float sf = 0.f;
+        for (int k = 0; k < M; k++) sf += fabsf((float)out[k]) * sqrtf(fmaxf((float)diag[k], 0.f));
+        *amp = (double)(sf * sqrtf(fmaxf((float)diag[0], 0.f)));
+#else
+        double sd = 0.0;
+        for (int k = 0; k < M; k++) sd += fabs(out[k]) * sqrt(fmax(diag[k], 0.0));
+        *amp = sd * sqrt(fmax(diag[0], 0.0));
+#endif
+    }
     return true;
 }
 
@@ -1011,6 +1036,7 @@ __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
 // ------------------------------------------------------------------------------------
 template <int DIM, int DEG, bool MIXED, int G>
 __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
+    static_assert(DEG <= 2, "operator rows: exact double-FP32 monomials need degree <= 2");
     using T = typename std::conditional<MIXED, float, double>::type;
     constexpr int M = mono_count(DIM, DEG);
     constexpr int GPW = 32 / G;
@@ -1025,9 +1051,15 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
 #pragma unroll
         for (int d = 0; d < DIM; d++) tx[d] = S.tx64[d * S.nt + t];
         if constexpr (MIXED) load_hilo<DIM>(S.thl0, S.thl1, t, thi, tlo);
+        // y as T, and for mixed maps also as an unevaluated FP32 pair (y = yh + yl to ~2^-48)
         T y[M];
+        float yl[M];
 #pragma unroll
-        for (int k = 0; k < M; k++) y[k] = (T)S.y[t * M + k];
+        for (int k = 0; k < M; k++) {
+            const double yk = S.y[t * M + k];
+            y[k] = (T)yk;
+            yl[k] = MIXED ? (float)(yk - (double)(float)yk) : 0.f;
+        }
         const int flag = S.flags ? S.flags[t] : 0;
         T bcv[4] = {T(0), T(0), T(0), T(1)};
         if (MIXED && flag == 3) {
@@ -1092,21 +1124,41 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
             const T w = weight_value<T>(S.weight, qv);
             T u[3];
             basis_offsets<DIM, T>(dx, inv_r, (MIXED && flag == 3) ? bcv : nullptr, u);
-            if (MIXED && flag) {
-                // sensitive row (1), or a row in a re-centred basis (3): the same FP32 u and w
-                // as the moments, monomials and the dot product with y in FP64
-                double am[M];
-                am[0] = 1.0;
-                double s = S.y[t * M];
-                sfor<M - 1>([&](auto I) {
-                    constexpr int p = decltype(I)::value + 1;
-                    constexpr int par = mono_parent(DIM, p);
-                    constexpr int v = mono_var(DIM, p);
-                    am[p] = am[par] * (double)u[v];
-                    s += am[p] * S.y[t * M + p];
-                });
-                ((T*)S.vals)[i] = (T)((double)w * s);
-                continue;
+            if constexpr (MIXED) {
+                if (flag) {
+                    // sensitive row (1), or a row in a re-centred basis (3): the same FP32 u
+                    // and w as the moments; the monomials (degree <= 2) as exact FP32 pairs
+                    // (TwoProduct by FMA) and the dot product with y in double-FP32
+                    // arithmetic (TwoProduct terms, TwoSum accumulation, ~2^-48), since y's
+                    // entries cancel when amp is large
+                    float ah[M], al[M];
+                    ah[0] = 1.f;
+                    al[0] = 0.f;
+                    sfor<M - 1>([&](auto I) {
+                        constexpr int p = decltype(I)::value + 1;
+                        constexpr int par = mono_parent(DIM, p);
+                        constexpr int v = mono_var(DIM, p);
+                        if constexpr (par == 0) {
+                            ah[p] = u[v];
+                            al[p] = 0.f;
+                        } else {   // degree 2: parent of degree 1 is an exact FP32 value
+                            ah[p] = __fmul_rn(ah[par], u[v]);
+                            al[p] = __fmaf_rn(ah[par], u[v], -ah[p]);
+                        }
+                    });
+                    float sh = 0.f, sl = 0.f;
+#pragma unroll
+                    for (int k = 0; k < M; k++) {
+                        const float ph = __fmul_rn(ah[k], y[k]);
+                        const float pl = __fmaf_rn(ah[k], y[k], -ph) + (ah[k] * yl[k] + al[k] * y[k]);
+                        float s2, e2;
+                        two_sum32(sh, ph, s2, e2);
+                        sl = (sl + pl) + e2;
+                        sh = s2;
+                    }
+                    ((T*)S.vals)[i] = (T)(w * sh + w * sl);
+                    continue;
+                }
             }
             T am[M];
             am[0] = T(1);
