@@ -236,8 +236,13 @@ void pcms_mesh_destroy(pcms_mesh mesh, void* stream);
  * admitted or cached (least recently used cached operators are evicted first). Admitted
  * requests run concurrently on their slots' streams, so their kernels overlap on the GPU.
  * A request whose estimate alone exceeds the cap fails with PCMS_ERR_CAPACITY.
- * All pointers in a request are device pointers owned by the caller and must stay valid
- * until the request has completed.
+ * All pointers in a request are owned by the caller and must stay valid until the request
+ * has completed. They are device pointers, or with host_io = 1 host pointers: the server
+ * then copies the inputs the request needs to device memory on the slot's stream, runs it,
+ * and copies the outputs back before reporting completion, so a request's copies overlap
+ * other slots' kernels. Host buffers should be page-locked (cudaHostAlloc or
+ * cudaHostRegister); pageable memory works but its copies do not overlap. The staging
+ * memory is part of the request's reservation.
  */
 typedef enum { PCMS_REQ_MLS = 0, PCMS_REQ_MESH = 1 } pcms_request_kind;
 
@@ -270,6 +275,8 @@ typedef struct {
     int32_t* elem_ids;
     /* device bytes to reserve; 0 = estimate from the sizes */
     int64_t bytes_hint;
+    /* 1: all buffers above are host memory, staged through the device by the server */
+    int host_io;
 } pcms_request;
 
 typedef struct {

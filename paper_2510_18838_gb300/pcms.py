@@ -52,7 +52,17 @@ class Request(ctypes.Structure):
                 ("fields", ctypes.c_void_p), ("n_fields", ctypes.c_int),
                 ("out", ctypes.c_void_p), ("map_key", ctypes.c_int64), ("reuse_map", ctypes.c_int),
                 ("tri", ctypes.c_void_p), ("n_tri", ctypes.c_int64),
-                ("elem_ids", ctypes.c_void_p), ("bytes_hint", ctypes.c_int64)]
+                ("elem_ids", ctypes.c_void_p), ("bytes_hint", ctypes.c_int64),
+                ("host_io", ctypes.c_int)]
+
+
+def _host_io(*tensors) -> int:
+    """1 if a request's tensors are all host tensors (the server stages them; pin them with
+    Tensor.pin_memory() so the copies overlap other requests), 0 if all are CUDA tensors."""
+    dev = {t.is_cuda for t in tensors if t is not None}
+    if len(dev) != 1:
+        raise ValueError("a request's tensors must be all CUDA or all host tensors")
+    return 0 if dev.pop() else 1
 
 
 class RequestResult(ctypes.Structure):
@@ -357,6 +367,7 @@ class Server:
         r.map_key = int(map_key)
         r.reuse_map = 1 if reuse else 0
         r.bytes_hint = int(bytes_hint)
+        r.host_io = _host_io(src, tgt, fields, out)
         return self._submit(r, (src, tgt, fields, out))
 
     def submit_mesh(self, xy, tri, pts, field, values, elem, bytes_hint=0):
@@ -369,6 +380,7 @@ class Server:
         r.out = values.data_ptr() if values is not None else None
         r.elem_ids = elem.data_ptr()
         r.bytes_hint = int(bytes_hint)
+        r.host_io = _host_io(xy, tri, pts, field, values, elem)
         return self._submit(r, (xy, tri, pts, field, values, elem))
 
     def _submit(self, r, keep):

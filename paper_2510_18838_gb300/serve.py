@@ -79,6 +79,31 @@ def _mesh_dev(n, seed, device):
     return xy, tri
 
 
+OUTPUT_KEYS = ("out", "values", "elem")
+
+
+def to_host(dreqs, pin: bool = False) -> list[DeviceRequest]:
+    """The same requests with host copies of their inputs and host output buffers:
+    submitted as they are, the server stages every copy on the request's slot stream (host
+    I/O requests). Ordinary (pageable) memory by default, as a caller's arrays usually are;
+    pin=True page-locks them. Requests sharing a geometry share its host copy."""
+    copies = {}
+    out = []
+    for d in dreqs:
+        h = {}
+        for k, v in d.tensors.items():
+            if k in OUTPUT_KEYS:
+                h[k] = torch.empty(v.shape, dtype=v.dtype, pin_memory=pin)
+            else:
+                key = (v.data_ptr(), v.numel(), v.dtype)
+                if key not in copies:
+                    c = v.to("cpu")
+                    copies[key] = c.pin_memory() if pin else c
+                h[k] = copies[key]
+        out.append(DeviceRequest(d.req, h))
+    return out
+
+
 def materialize(reqs, device) -> list[DeviceRequest]:
     """Synthesise every request's inputs and outputs on the device (seeded)."""
     out: list[DeviceRequest] = []
@@ -164,7 +189,7 @@ def run_served(dreqs, n_slots=8, mem_cap=40 << 30, arrivals=None, timeout_s=900.
     return dict(points=pts, seconds=wall, points_per_s=pts / wall,
                 p50_ms=1e3 * statistics.median(lat), p99_ms=1e3 * _pct(lat, 99),
                 failed=bad, cached_hits=sum(1 for r in results.values() if r["cached"]),
-                peak_bytes=mem["peak"])
+                peak_bytes=mem["peak"], results=[results[i] for i in range(n)])
 
 
 def run_plain_fp64(dreqs, arrivals=None):

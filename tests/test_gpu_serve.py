@@ -115,3 +115,23 @@ def test_a_failing_request_does_not_disturb_the_others(env):
     for i in (0, 1, 3, 4):
         assert res[tickets[i]] == pcms.OK
         assert normwise_err(outs[i].cpu().numpy(), ref, ok) <= TOL_MIXED
+
+
+@pytest.mark.parametrize("pin", [False, True])
+def test_host_io_requests_match_device_requests(env, pin):
+    """Requests whose buffers are host memory, ordinary or page-locked (the server stages the
+    copies on each slot's stream), give bit-identical results to the same requests on
+    device buffers."""
+    torch, pcms, serve = env
+    reqs = W.request_stream(n_req=40, seed=78, pts_hi=40000, max_pts=40000)
+    dreqs = serve.materialize(reqs, torch.device("cuda", 0))
+    host = serve.to_host(dreqs, pin=pin)
+    assert all(not v.is_cuda for d in host for v in d.tensors.values())
+    st_d = serve.run_served(dreqs, n_slots=4, mem_cap=2 << 30)
+    st_h = serve.run_served(host, n_slots=4, mem_cap=2 << 30)
+    assert st_d["failed"] == 0 and st_h["failed"] == 0
+    for d, h in zip(dreqs, host):
+        for k in serve.OUTPUT_KEYS:
+            if k in d.tensors:
+                a, b = d.tensors[k].cpu().numpy(), h.tensors[k].numpy()
+                assert np.array_equal(a, b, equal_nan=True), (d.req, k)
