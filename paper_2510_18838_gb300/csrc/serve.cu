@@ -10,6 +10,7 @@
 // client's drain/poll calls have explicit timeouts.
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -34,6 +35,17 @@ struct Job {
     pcms_status st = PCMS_OK;
     int used_cached = 0;
     bool builds_cache = false;
+};
+
+// Page-locked bounce buffers of one slot: host-I/O requests whose buffers are ordinary
+// (pageable) memory are copied through them in chunks, the slot's thread copying one chunk
+// on the CPU while the GPU transfers the other. Allocated on first use.
+constexpr size_t BOUNCE_BYTES = size_t(16) << 20;
+struct Bounce {
+    char* h[2] = {nullptr, nullptr};
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    bool used[2] = {false, false};
+    int cur = 0;
 };
 
 struct CacheEntry {
@@ -63,6 +75,7 @@ struct pcms_server_s {
     std::unordered_map<int64_t, CacheEntry> cache;
     std::vector<std::thread> workers;
     std::vector<cudaStream_t> streams;
+    std::vector<Bounce> bounce;   // per slot
 
     double now() const {
         return std::chrono::duration<double>(Clock::now() - t0).count();
@@ -94,17 +107,87 @@ int64_t request_bytes(const pcms_request& r) {
            staged_bytes(r, true);
 }
 
+bool page_locked(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+void bounce_init(Bounce& b) {
+    if (b.h[0]) return;
+    for (int i = 0; i < 2; i++) {
+        PCMS_CU(cudaHostAlloc((void**)&b.h[i], BOUNCE_BYTES, cudaHostAllocDefault));
+        PCMS_CU(cudaEventCreateWithFlags(&b.ev[i], cudaEventDisableTiming));
+    }
+}
+
+// host -> device on stream s: directly from page-locked memory, else through the bounce
+// buffers (the CPU fills one while the GPU reads the other)
+void copy_in(Bounce& b, void* dst, const void* src, size_t n, cudaStream_t s) {
+    if (page_locked(src)) {
+        PCMS_CU(cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s));
+        return;
+    }
+    bounce_init(b);
+    for (size_t off = 0; off < n; off += BOUNCE_BYTES) {
+        const size_t len = std::min(BOUNCE_BYTES, n - off);
+        const int c = b.cur;
+        if (b.used[c]) PCMS_CU(cudaEventSynchronize(b.ev[c]));
+        std::memcpy(b.h[c], (const char*)src + off, len);
+        PCMS_CU(cudaMemcpyAsync((char*)dst + off, b.h[c], len, cudaMemcpyHostToDevice, s));
+        PCMS_CU(cudaEventRecord(b.ev[c], s));
+        b.used[c] = true;
+        b.cur = c ^ 1;
+    }
+}
+
+// device -> host after the work queued on s: chunk k is transferred while chunk k-1 is
+// copied out of the other buffer
+void copy_out(Bounce& b, void* dst, const void* src, size_t n, cudaStream_t s) {
+    if (page_locked(dst)) {
+        PCMS_CU(cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, s));
+        return;
+    }
+    bounce_init(b);
+    int cp = -1;
+    size_t op = 0, lp = 0;
+    for (size_t off = 0; off < n; off += BOUNCE_BYTES) {
+        const size_t len = std::min(BOUNCE_BYTES, n - off);
+        const int c = b.cur;
+        if (b.used[c]) PCMS_CU(cudaEventSynchronize(b.ev[c]));
+        PCMS_CU(cudaMemcpyAsync(b.h[c], (const char*)src + off, len, cudaMemcpyDeviceToHost, s));
+        PCMS_CU(cudaEventRecord(b.ev[c], s));
+        b.used[c] = true;
+        if (cp >= 0) {
+            PCMS_CU(cudaEventSynchronize(b.ev[cp]));
+            std::memcpy((char*)dst + op, b.h[cp], lp);
+        }
+        cp = c;
+        op = off;
+        lp = len;
+        b.cur = c ^ 1;
+    }
+    if (cp >= 0) {
+        PCMS_CU(cudaEventSynchronize(b.ev[cp]));
+        std::memcpy((char*)dst + op, b.h[cp], lp);
+    }
+}
+
 // Device staging of a host_io request: copies in, on the slot's stream, what the chosen
 // path reads; outputs are copied back by unstage().
 struct Staging {
     pcms::DBuf buf;
     char* next = nullptr;
+    Bounce* bounce = nullptr;
     pcms_request d;   // the request with device pointers
     const void* take(const void* host, int64_t bytes, cudaStream_t s) {
         if (!host || bytes <= 0) return nullptr;
         void* p = next;
         next += (bytes + 255) / 256 * 256;
-        PCMS_CU(cudaMemcpyAsync(p, host, (size_t)bytes, cudaMemcpyHostToDevice, s));
+        copy_in(*bounce, p, host, (size_t)bytes, s);
         return p;
     }
     void* room(const void* host, int64_t bytes) {
@@ -139,12 +222,11 @@ void stage(const pcms_request& r, bool geometry, Staging& st, cudaStream_t s) {
 
 void unstage(const pcms_request& r, const Staging& st, cudaStream_t s) {
     if (r.kind == PCMS_REQ_MESH) {
-        if (r.out) PCMS_CU(cudaMemcpyAsync(r.out, st.d.out, 8 * r.n_tgt, cudaMemcpyDeviceToHost, s));
-        PCMS_CU(cudaMemcpyAsync(r.elem_ids, st.d.elem_ids, 4 * r.n_tgt, cudaMemcpyDeviceToHost, s));
+        if (r.out) copy_out(*st.bounce, r.out, st.d.out, 8 * r.n_tgt, s);
+        copy_out(*st.bounce, r.elem_ids, st.d.elem_ids, 4 * r.n_tgt, s);
         return;
     }
-    PCMS_CU(cudaMemcpyAsync(r.out, st.d.out, (size_t)r.n_fields * mls_elem(r) * r.n_tgt,
-                            cudaMemcpyDeviceToHost, s));
+    copy_out(*st.bounce, r.out, st.d.out, (size_t)r.n_fields * mls_elem(r) * r.n_tgt, s);
 }
 
 // evict unpinned cached operators (LRU) until `need` more bytes fit; caller holds the lock
@@ -161,9 +243,10 @@ void evict_for(pcms_server_s* S, int64_t need) {
     }
 }
 
-void run_job(pcms_server_s* S, Job* j, cudaStream_t s, pcms::MapImpl* cached,
+void run_job(pcms_server_s* S, Job* j, cudaStream_t s, Bounce& bounce, pcms::MapImpl* cached,
              std::unique_ptr<pcms::MapImpl>* built) {
     Staging st;
+    st.bounce = &bounce;
     if (j->req.host_io) stage(j->req, cached == nullptr, st, s);
     const pcms_request& r = j->req.host_io ? st.d : j->req;
     if (r.kind == PCMS_REQ_MESH) {
@@ -269,7 +352,7 @@ void worker(pcms_server_s* S, int slot) {
         std::unique_ptr<pcms::MapImpl> built;
         pcms_status st = PCMS_OK;
         try {
-            run_job(S, j, s, cached, j->builds_cache ? &built : nullptr);
+            run_job(S, j, s, S->bounce[slot], cached, j->builds_cache ? &built : nullptr);
         } catch (const pcms::PcmsError& e) {
             st = e.status;
             // a CUDA error ends the context for every later request: say where it surfaced
@@ -342,6 +425,7 @@ pcms_status pcms_server_create(int n_slots, int64_t mem_cap_bytes, pcms_server* 
         }
         S->streams.push_back(st);
     }
+    S->bounce.resize(n_slots);
     for (int i = 0; i < n_slots; i++) S->workers.emplace_back(worker, S, i);
     *out = S;
     return PCMS_OK;
@@ -438,6 +522,11 @@ void pcms_server_destroy(pcms_server S) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     }
+    for (Bounce& b : S->bounce)
+        for (int i = 0; i < 2; i++) {
+            if (b.h[i]) cudaFreeHost(b.h[i]);
+            if (b.ev[i]) cudaEventDestroy(b.ev[i]);
+        }
     delete S;
 }
 
