@@ -70,6 +70,9 @@ typedef enum {
     PCMS_CUBIC = 8        /* (2q)^3 */
 } pcms_weight;
 
+/* Readings of the Sec. 3.2.1 minimum-count rule (pcms_map_opts.growth, min_neighbors > 0). */
+typedef enum { PCMS_GROWTH_PER_TARGET = 0, PCMS_GROWTH_GLOBAL = 1 } pcms_growth;
+
 /* per-target status codes (int8) */
 enum { PCMS_TARGET_OK = 0, PCMS_TARGET_UNDERDETERMINED = 1, PCMS_TARGET_ILL_CONDITIONED = 2 };
 
@@ -84,6 +87,12 @@ typedef struct {
     /* Optional: 1 if lo/hi bound every source point; saves one device-to-host read. */
     int domain_known;
     double lo[3], hi[3];
+    /* How the radius grows when min_neighbors > 0. PCMS_GROWTH_PER_TARGET (default): each
+     * target doubles its own radius. PCMS_GROWTH_GLOBAL: one radius, radius * 2^K, for every
+     * target, with K the fewest doublings after which no target is short (K is also the
+     * largest per-target doubling count, as counts only grow with the radius). The
+     * reported radius doublings are then K for every target. */
+    int growth;
 } pcms_map_opts;
 
 typedef struct pcms_map_s* pcms_map;
@@ -222,6 +231,25 @@ pcms_status pcms_mesh_create(const double* xy, int64_t n_vertices, const int32_t
 pcms_status pcms_locate_interp(pcms_mesh mesh, const double* tgt_pts, int64_t n_pts,
                                const double* nodal_field, int32_t* elem_ids,
                                int8_t* entity_dim, double* values, void* stream);
+
+/*
+ * pcms_mesh_centroids -- triangle centroids ((v0 + v1) + v2) / 3, written to centroids
+ *   (device float64 [2][n_tri]): the element-centred points of the vertex <-> centroid
+ *   round trip that measures accuracy and conservation (Sec. 3.2.1, Eq. 2 and Eq. 3).
+ *   Asynchronous.
+ */
+pcms_status pcms_mesh_centroids(pcms_mesh mesh, double* centroids, void* stream);
+
+/*
+ * pcms_mesh_integrate -- integral over the mesh of the piecewise-linear interpolant of a
+ *   nodal field (the integral of Eq. 3): the sum over triangles of |area| (f0 + f1 + f2) / 3,
+ *   area = ((x1-x0)(y2-y0) - (y1-y0)(x2-x0)) / 2, in FP64 without contraction. The sum runs
+ *   in a fixed order (per-block partial sums, then one block), so it is reproducible.
+ *   nodal_field: device float64 [n_vertices]; *integral: host double, written after the
+ *   call synchronises `stream`.
+ */
+pcms_status pcms_mesh_integrate(pcms_mesh mesh, const double* nodal_field, double* integral,
+                                void* stream);
 
 /* Release a mesh (memory freed on `stream`). NULL is a no-op. */
 void pcms_mesh_destroy(pcms_mesh mesh, void* stream);

@@ -72,6 +72,8 @@ def _load():
         lib.orc_count_neighbors.restype = i64
         lib.orc_count_neighbors.argtypes = [i32, P, i64, P, i64, f64, i32, i32, i32, P, P]
         lib.orc_fill_neighbors.argtypes = [i32, P, i64, P, i64, f64, i32, i32, P, P, P]
+        lib.orc_global_doublings.restype = i32
+        lib.orc_global_doublings.argtypes = [i32, P, i64, P, i64, f64, i32, i32, i32]
         lib.orc_mls.argtypes = [i32, i32, i32, f64, P, i64, P, i64, P, i32, f64, i32, i32,
                                 P, P, P, P, P, P]
         lib.orc_orient2d_sign.restype = i32
@@ -111,11 +113,34 @@ def _need(dim, degree, min_neighbors):
     return max(int(min_neighbors), num_terms(dim, degree)) if min_neighbors > 0 else 0
 
 
+GROWTH = ("target", "global")
+
+
+def global_doublings(src, tgt, radius, weight="wendland_c2", min_neighbors=0, degree=1,
+                     mode="brute") -> int:
+    """Global reading of the Sec. 3.2.1 minimum-count rule: the number of times one radius
+    shared by all targets is doubled until every target selects max(min_neighbors, m)
+    sources (or all of them). 0 without min_neighbors."""
+    lib = _load()
+    src, tgt = _f64(src), _f64(tgt)
+    dim, ns = src.shape
+    need = _need(dim, degree, min_neighbors)
+    return int(lib.orc_global_doublings(dim, _p(src), ns, _p(tgt), tgt.shape[1], float(radius),
+                                        WEIGHTS[weight], need, 1 if mode == "grid" else 0))
+
+
 def neighbors(src, tgt, radius, weight="wendland_c2", min_neighbors=0, degree=1,
-              mode="brute"):
+              mode="brute", growth="target"):
     """Neighbour lists (Sec. 3.2.1 radius selection, ascending source index).
     Returns (offsets int64[nt+1], cols int32[nnz], kexp int32[nt]); kexp[i] is the
-    number of radius doublings target i needed (0 without min_neighbors)."""
+    number of radius doublings target i needed (0 without min_neighbors). growth="global"
+    uses the single radius radius * 2^K of global_doublings for every target (kexp = K)."""
+    if growth not in GROWTH:
+        raise ValueError(f"growth must be one of {GROWTH}")
+    if growth == "global" and min_neighbors > 0:
+        k = global_doublings(src, tgt, radius, weight, min_neighbors, degree, mode)
+        off, cols, _ = neighbors(src, tgt, np.ldexp(float(radius), k), weight, 0, degree, mode)
+        return off, cols, np.full(np.shape(tgt)[1], k, np.int32)
     lib = _load()
     src, tgt = _f64(src), _f64(tgt)
     dim, ns = src.shape
@@ -135,10 +160,19 @@ def neighbors(src, tgt, radius, weight="wendland_c2", min_neighbors=0, degree=1,
 
 
 def mls(src, tgt, fields, degree, radius, weight="wendland_c2", lam=0.0, min_neighbors=0,
-        mode="brute", shape=False):
+        mode="brute", shape=False, growth="target"):
     """MLS transfer by QR (Sec. 3.2.1, Eq. 1). fields: [F, ns] (or [ns]).
     Returns dict(values float64[F, nt], status int8[nt], kexp int32[nt]) and, with
-    shape=True, also offsets, cols (ascending) and shape float64[nnz]."""
+    shape=True, also offsets, cols (ascending) and shape float64[nnz]. growth="global":
+    every target is fitted at the shared radius radius * 2^K of global_doublings."""
+    if growth not in GROWTH:
+        raise ValueError(f"growth must be one of {GROWTH}")
+    if growth == "global" and min_neighbors > 0:
+        k = global_doublings(src, tgt, radius, weight, min_neighbors, degree, mode)
+        out = mls(src, tgt, fields, degree, np.ldexp(float(radius), k), weight, lam, 0, mode,
+                  shape)
+        out["kexp"][:] = k
+        return out
     lib = _load()
     src, tgt = _f64(src), _f64(tgt)
     fields = _f64(fields)
@@ -201,3 +235,6 @@ def locate(xy, tri, pts, field=None, mode="exhaustive"):
     lib.orc_locate(_p(xy), nv, _p(tri), ntri, _p(pts), q, 1 if mode == "grid" else 0,
                    _p(fld), _p(elem), _p(dimc), _p(vals))
     return elem, dimc, vals
+
+
+from oracle.roundtrip import centroids, p1_integral, round_trip  # noqa: E402,F401

@@ -15,12 +15,12 @@
  *        d2 = ((sx-tx)*(sx-tx) + (sy-ty)*(sy-ty)) [+ (sz-tz)*(sz-tz)]  <  r*r
  *    evaluated left to right in FP64, and phi(sqrt(d2)/r) > 0.
  *    Lists are returned in ascending source index.
- *  - Minimum-count radius growth (Sec. 3.2.1, "the cutoff radius will be iteratively
- *    increased until every target point meets the user constraint"): read per target,
- *    r <- 2 r until the count reaches max(min_neighbors, m).
- *  - Underdetermined check (Sec. 3.2.1, "an error is thrown if the resulting
- *    minimization problem will be underdetermined"): fewer neighbours than basis terms
- *    -> status UNDERDETERMINED, value NaN.
+ *  - Minimum-count radius growth (Sec. 3.2.1: with a minimum neighbour count the radius
+ *    grows until the targets have enough sources). Per target (default): r <- 2 r until
+ *    the count reaches max(min_neighbors, m). Global (option): one radius for every
+ *    target, doubled until all of them reach that count.
+ *  - Underdetermined check (Sec. 3.2.1: a fit with fewer equations than unknowns is an
+ *    error): fewer neighbours than basis terms -> status UNDERDETERMINED, value NaN.
  *  - Local weighted polynomial fit (Sec. 3.2.1, Eq. 1): min_c ||Phi^(1/2)(A c - b)||^2 +
  *    lambda ||c||^2 with A the Vandermonde matrix of the basis centred at the target and
  *    scaled by 1/r, solved by unpivoted Householder QR of [diag(sqrt w) A; sqrt(lambda) I].
@@ -311,6 +311,36 @@ int64_t orc_count_neighbors(int dim, const double* src, int64_t ns, const double
     }
     if (gp) grid_free(&g);
     return total;
+}
+
+/* Global reading of the growth rule (Sec. 3.2.1): one radius for all targets, doubled
+ * until every target has at least `need` neighbours (or already selects all ns sources),
+ * at most ORC_MAX_GROW times. Returns the number of doublings; 0 when need <= 0. */
+int orc_global_doublings(int dim, const double* src, int64_t ns, const double* tgt,
+                         int64_t nt, double radius, int wkind, int need, int mode) {
+    if (need <= 0 || nt <= 0) return 0;
+    grid_t g;
+    const grid_t* gp = NULL;
+    if (mode == 1) {
+        grid_build(&g, dim, src, ns, radius);
+        gp = &g;
+    }
+    int k = 0;
+    for (;;) {
+        const double r = ldexp(radius, k);
+        int64_t short_of = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : short_of)
+        for (int64_t i = 0; i < nt; i++) {
+            double t[3];
+            load_target(dim, tgt, nt, i, t);
+            int64_t c = target_neighbors(dim, src, ns, t, r, wkind, mode, gp, NULL);
+            if (c < need && c < ns) short_of++;
+        }
+        if (short_of == 0 || k >= ORC_MAX_GROW) break;
+        k++;
+    }
+    if (gp) grid_free(&g);
+    return k;
 }
 
 /* Fill neighbour lists (ascending) given offsets from counts and the growth exponents. */

@@ -87,12 +87,35 @@ template <>
 __device__ __forceinline__ void fma_vec<double2, double>(double2& acc, double a, const double2& x) {
     acc.x = fma(a, x.x, acc.x); acc.y = fma(a, x.y, acc.y);
 }
-__device__ __forceinline__ void shfl_add(float4& v, int o) {
-    v.x += __shfl_xor_sync(0xffffffffu, v.x, o); v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-    v.z += __shfl_xor_sync(0xffffffffu, v.z, o); v.w += __shfl_xor_sync(0xffffffffu, v.w, o);
+// Sum over the slots of a row's partial vectors (lane = slot * NV + vi), with the vector's
+// components spread over the lanes instead of reduced whole: the first exchange (lanes 16
+// apart) halves the components a lane keeps, the second (8 apart, float4 only) halves them
+// again, the rest are plain. On return the lane holds the total of component *comp of vector
+// vi; the lanes that hold distinct totals are those with (lane & writer_mask) == 0.
+template <int NV>
+__device__ __forceinline__ float slot_total(const float4& a, int lane, int* comp) {
+    static_assert(NV <= 8, "lanes 8 and 16 apart must hold different slots");
+    const bool h = lane & 16, q = lane & 8;
+    const float k0 = (h ? a.z : a.x) + __shfl_xor_sync(0xffffffffu, h ? a.x : a.z, 16);
+    const float k1 = (h ? a.w : a.y) + __shfl_xor_sync(0xffffffffu, h ? a.y : a.w, 16);
+    float k = (q ? k1 : k0) + __shfl_xor_sync(0xffffffffu, q ? k0 : k1, 8);
+#pragma unroll
+    for (int o = NV; o < 8; o <<= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+    *comp = (h ? 2 : 0) + (q ? 1 : 0);
+    return k;
 }
-__device__ __forceinline__ void shfl_add(double2& v, int o) {
-    v.x += __shfl_xor_sync(0xffffffffu, v.x, o); v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+template <int NV>
+__device__ __forceinline__ double slot_total(const double2& a, int lane, int* comp) {
+    const bool h = lane & 16;
+    double k = (h ? a.y : a.x) + __shfl_xor_sync(0xffffffffu, h ? a.x : a.y, 16);
+#pragma unroll
+    for (int o = NV; o < 16; o <<= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+    *comp = h ? 1 : 0;
+    return k;
+}
+template <typename T, int NV>
+constexpr int writer_mask() {
+    return sizeof(T) == 4 ? 8 - NV : 16 - NV;
 }
 
 template <typename T>
@@ -190,16 +213,11 @@ __global__ void __launch_bounds__(256) k_spmm_vec(int64_t nt, const int64_t* __r
                 jA = __ldg(cols + an + lane);
                 wA = __ldg(vals + an + lane);
             }
-#pragma unroll
-            for (int o = NV; o < 32; o <<= 1) shfl_add(acc, o);
-            if (slot == 0) {
-                if (status[t] != PCMS_TARGET_OK) {
-                    const T nan = quiet_nan<T>();
-                    const T nan4[4] = {nan, nan, nan, nan};
-                    memcpy(&acc, nan4, sizeof(V));
-                }
-                *reinterpret_cast<V*>(stage + t * (NV * W) + vi * W) = acc;
-            }
+            int comp;
+            const T tot = slot_total<NV>(acc, lane, &comp);
+            if ((lane & writer_mask<T, NV>()) == 0)
+                stage[t * (NV * W) + vi * W + comp] =
+                    status[t] == PCMS_TARGET_OK ? tot : quiet_nan<T>();
             a = an;
             b = bn;
         }
@@ -360,7 +378,7 @@ __global__ void k_export_rows(int64_t nt, const int32_t* __restrict__ inv_t,
                               const int8_t* __restrict__ st, const int32_t* __restrict__ kx,
                               const int64_t* __restrict__ off_out, int32_t* __restrict__ cols_out,
                               double* __restrict__ vals_out, int8_t* __restrict__ st_out,
-                              int32_t* __restrict__ kx_out) {
+                              int32_t* __restrict__ kx_out, int kadd) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < nt;
@@ -373,19 +391,20 @@ __global__ void k_export_rows(int64_t nt, const int32_t* __restrict__ inv_t,
         }
         if (lane == 0) {
             if (st_out) st_out[i] = st[p];
-            if (kx_out) kx_out[i] = kx[p];
+            if (kx_out) kx_out[i] = kx[p] + kadd;
         }
     }
 }
 
 __global__ void k_export_status(int64_t nt, const int32_t* __restrict__ inv_t,
                                 const int8_t* __restrict__ st, const int32_t* __restrict__ kx,
-                                int8_t* __restrict__ st_out, int32_t* __restrict__ kx_out) {
+                                int8_t* __restrict__ st_out, int32_t* __restrict__ kx_out,
+                                int kadd) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t p = inv_t[i];
         if (st_out) st_out[i] = st[p];
-        if (kx_out) kx_out[i] = kx[p];
+        if (kx_out) kx_out[i] = kx[p] + kadd;
     }
 }
 
@@ -431,7 +450,8 @@ void mls_export(MapImpl& M, int64_t* offsets, int32_t* cols, double* vals, int8_
         if (nt > 0 && (status || kexp))
             k_export_status<<<blocks_for(nt, 256), 256, 0, s>>>(nt, M.tgt.inv.as<int32_t>(),
                                                                 M.status.as<int8_t>(),
-                                                                M.kexp.as<int32_t>(), status, kexp);
+                                                                M.kexp.as<int32_t>(), status, kexp,
+                                                                M.P.kbase);
         PCMS_LAUNCH_CHECK("export");
         return;
     }
@@ -446,12 +466,12 @@ void mls_export(MapImpl& M, int64_t* offsets, int32_t* cols, double* vals, int8_
             k_export_rows<float><<<blocks, 256, 0, s>>>(
                 nt, M.tgt.inv.as<int32_t>(), M.offsets.as<int64_t>(), M.counts.as<int32_t>(),
                 M.cols.as<int32_t>(), M.vals.as<float>(), M.src.perm.as<int32_t>(), M.status.as<int8_t>(),
-                M.kexp.as<int32_t>(), offsets, cols, vals, status, kexp);
+                M.kexp.as<int32_t>(), offsets, cols, vals, status, kexp, M.P.kbase);
         else
             k_export_rows<double><<<blocks, 256, 0, s>>>(
                 nt, M.tgt.inv.as<int32_t>(), M.offsets.as<int64_t>(), M.counts.as<int32_t>(),
                 M.cols.as<int32_t>(), M.vals.as<double>(), M.src.perm.as<int32_t>(), M.status.as<int8_t>(),
-                M.kexp.as<int32_t>(), offsets, cols, vals, status, kexp);
+                M.kexp.as<int32_t>(), offsets, cols, vals, status, kexp, M.P.kbase);
     }
     PCMS_LAUNCH_CHECK("export");
 }

@@ -79,6 +79,8 @@ pcms_status check_mls_args(const char* fn, int dim, const double* src, int64_t n
     REQUIRE((int)o.weight >= 0 && (int)o.weight <= 8, f + ": bad weight kind");
     REQUIRE(std::isfinite(o.lambda) && o.lambda >= 0.0, f + ": lambda must be finite and >= 0");
     REQUIRE(o.min_neighbors >= 0, f + ": min_neighbors must be >= 0");
+    REQUIRE(o.growth == PCMS_GROWTH_PER_TARGET || o.growth == PCMS_GROWTH_GLOBAL,
+            f + ": growth must be PCMS_GROWTH_PER_TARGET or PCMS_GROWTH_GLOBAL");
     if (o.domain_known) {
         for (int d = 0; d < dim; d++)
             REQUIRE(std::isfinite(o.lo[d]) && std::isfinite(o.hi[d]) && o.lo[d] <= o.hi[d],
@@ -107,6 +109,7 @@ void pcms_map_opts_default(pcms_map_opts* o) {
     o->lambda = 0.0;
     o->min_neighbors = 0;
     o->domain_known = 0;
+    o->growth = PCMS_GROWTH_PER_TARGET;
 }
 
 pcms_status pcms_create_map(int dim, const double* src_pts, int64_t n_src, const double* tgt_pts,
@@ -228,7 +231,7 @@ pcms_status pcms_map_info(pcms_map map, pcms_map_info_t* info) {
         info->n_underdetermined = M.n_under;
         info->n_ill_conditioned = M.n_ill;
         info->max_neighbors = M.max_count;
-        info->max_radius_doublings = M.max_k;
+        info->max_radius_doublings = M.max_k + M.P.kbase;
         info->device_bytes = M.device_bytes();
         return PCMS_OK;
     });
@@ -302,6 +305,25 @@ pcms_status pcms_locate_interp(pcms_mesh mesh, const double* tgt_pts, int64_t n_
     });
 }
 
+pcms_status pcms_mesh_centroids(pcms_mesh mesh, double* centroids, void* stream) {
+    REQUIRE(mesh != nullptr, "pcms_mesh_centroids: mesh is NULL");
+    REQUIRE(mesh->impl.ntri == 0 || centroids != nullptr, "pcms_mesh_centroids: centroids is NULL");
+    return guarded("pcms_mesh_centroids", [&]() -> pcms_status {
+        pcms::mesh_centroids(mesh->impl, centroids, (cudaStream_t)stream);
+        return PCMS_OK;
+    });
+}
+
+pcms_status pcms_mesh_integrate(pcms_mesh mesh, const double* nodal_field, double* integral,
+                                void* stream) {
+    REQUIRE(mesh != nullptr && integral != nullptr, "pcms_mesh_integrate: NULL argument");
+    REQUIRE(mesh->impl.nv == 0 || nodal_field != nullptr, "pcms_mesh_integrate: nodal_field is NULL");
+    return guarded("pcms_mesh_integrate", [&]() -> pcms_status {
+        *integral = pcms::mesh_integrate(mesh->impl, nodal_field, (cudaStream_t)stream);
+        return PCMS_OK;
+    });
+}
+
 pcms_status pcms_trace_enable(int mode) {
     pcms::trace_enable(mode);
     return PCMS_OK;
@@ -320,7 +342,7 @@ void pcms_mesh_destroy(pcms_mesh mesh, void* stream) {
     if (!mesh) return;
     cudaStream_t s = (cudaStream_t)stream;
     pcms::MeshImpl& M = mesh->impl;
-    pcms::DBuf* bufs[] = {&M.xy, &M.tri, &M.cell_start, &M.items, &M.tsign};
+    pcms::DBuf* bufs[] = {&M.xy, &M.tri, &M.cell_start, &M.items, &M.tsign, &M.vhl};
     for (pcms::DBuf* b : bufs) {
         b->s = s;
         b->release();

@@ -197,10 +197,47 @@ __global__ void k_tri_fill(int64_t nt, Grid g, const int4* __restrict__ trect,
     }
 }
 
+// odd-even transposition sort of N registers (N rounds of compare-exchanges)
+template <int N>
+__device__ __forceinline__ void sort_regs(int32_t (&v)[N]) {
+#pragma unroll
+    for (int r = 0; r < N; r++) {
+#pragma unroll
+        for (int j = r & 1; j + 1 < N; j += 2) {
+            const int32_t lo = min(v[j], v[j + 1]), hi = max(v[j], v[j + 1]);
+            v[j] = lo;
+            v[j + 1] = hi;
+        }
+    }
+}
+
+// the cell's n <= N items loaded together, sorted in registers (padding sorts last), stored
+template <int N>
+__device__ __forceinline__ void sort_cell_regs(int32_t* items, int a, int n) {
+    int32_t v[N];
+#pragma unroll
+    for (int i = 0; i < N; i++) v[i] = i < n ? items[a + i] : INT32_MAX;
+    sort_regs<N>(v);
+#pragma unroll
+    for (int i = 0; i < N; i++)
+        if (i < n) items[a + i] = v[i];
+}
+
+// Each cell's triangle IDs ascending (the fill order is that of atomics): one thread per cell;
+// up to 16 items are sorted in registers, longer cells by insertion in place.
 __global__ void k_cell_sort(int64_t ncell, const int32_t* __restrict__ start, int32_t* items) {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
          c += (int64_t)gridDim.x * blockDim.x) {
-        const int a = start[c], b = start[c + 1];
+        const int a = start[c], b = start[c + 1], n = b - a;
+        if (n <= 1) continue;
+        if (n <= 8) {
+            sort_cell_regs<8>(items, a, n);
+            continue;
+        }
+        if (n <= 16) {
+            sort_cell_regs<16>(items, a, n);
+            continue;
+        }
         for (int i = a + 1; i < b; i++) {
             int32_t v = items[i];
             int j = i - 1;
@@ -378,6 +415,90 @@ void mesh_create(MeshImpl& M, const double* xy, int64_t nv, const int32_t* tri, 
     k_cell_sort<<<blocks_for(g.ncell, 256), 256, 0, s>>>(g.ncell, M.cell_start.as<int32_t>(),
                                                          M.items.as<int32_t>());
     PCMS_LAUNCH_CHECK("mesh build");
+}
+
+// ---------------------------------------------------------------------- centroids, P1 integral
+__global__ void k_tri_centroid(int64_t nv, const double* __restrict__ xy, int64_t nt,
+                               const int32_t* __restrict__ tri, double* __restrict__ out) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nt;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = tri[k], b = tri[nt + k], c = tri[2 * nt + k];
+        out[k] = __ddiv_rn(__dadd_rn(__dadd_rn(xy[a], xy[b]), xy[c]), 3.0);
+        out[nt + k] = __ddiv_rn(__dadd_rn(__dadd_rn(xy[nv + a], xy[nv + b]), xy[nv + c]), 3.0);
+    }
+}
+
+constexpr int INTEGRAL_THREADS = 256;
+constexpr int INTEGRAL_BLOCKS = 1024;
+
+// fixed-order sum of one value per thread over the block (tree in shared memory)
+__device__ __forceinline__ double block_sum_fixed(double v, double* sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = INTEGRAL_THREADS / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] = __dadd_rn(sh[threadIdx.x], sh[threadIdx.x + o]);
+        __syncthreads();
+    }
+    return sh[0];
+}
+
+// per-block partial sums of |area| (f0 + f1 + f2) / 3, each thread over a fixed stride
+__global__ void __launch_bounds__(INTEGRAL_THREADS) k_tri_integral(
+    int64_t nv, const double* __restrict__ xy, int64_t nt, const int32_t* __restrict__ tri,
+    const double* __restrict__ f, double* __restrict__ partial) {
+    __shared__ double sh[INTEGRAL_THREADS];
+    double acc = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nt;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = tri[k], b = tri[nt + k], c = tri[2 * nt + k];
+        const double x0 = xy[a], y0 = xy[nv + a];
+        const double cr = __dsub_rn(__dmul_rn(__dsub_rn(xy[b], x0), __dsub_rn(xy[nv + c], y0)),
+                                    __dmul_rn(__dsub_rn(xy[nv + b], y0), __dsub_rn(xy[c], x0)));
+        const double area = __dmul_rn(fabs(cr), 0.5);
+        const double mean = __ddiv_rn(__dadd_rn(__dadd_rn(f[a], f[b]), f[c]), 3.0);
+        acc = __dadd_rn(acc, __dmul_rn(area, mean));
+    }
+    const double s = block_sum_fixed(acc, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(INTEGRAL_THREADS) k_sum_partials(const double* __restrict__ partial,
+                                                                    int n, double* __restrict__ out) {
+    __shared__ double sh[INTEGRAL_THREADS];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc = __dadd_rn(acc, partial[i]);
+    const double s = block_sum_fixed(acc, sh);
+    if (threadIdx.x == 0) *out = s;
+}
+
+void mesh_centroids(const MeshImpl& M, double* out, cudaStream_t s) {
+    if (M.ntri <= 0) return;
+    PCMS_TRACE("mesh_centroids", s);
+    k_tri_centroid<<<blocks_for(M.ntri, 256), 256, 0, s>>>(M.nv, M.xy.as<double>(), M.ntri,
+                                                           M.tri.as<int32_t>(), out);
+    PCMS_LAUNCH_CHECK("k_tri_centroid");
+}
+
+double mesh_integrate(const MeshImpl& M, const double* field, cudaStream_t s) {
+    if (M.ntri <= 0) return 0.0;
+    const int blocks = (int)std::min<int64_t>(INTEGRAL_BLOCKS, (M.ntri + INTEGRAL_THREADS - 1) / INTEGRAL_THREADS);
+    DBuf part(sizeof(double) * (blocks + 1), s);
+    {
+        PCMS_TRACE("mesh_integrate", s);
+        k_tri_integral<<<blocks, INTEGRAL_THREADS, 0, s>>>(M.nv, M.xy.as<double>(), M.ntri,
+                                                           M.tri.as<int32_t>(), field,
+                                                           part.as<double>());
+    }
+    {
+        PCMS_TRACE("mesh_integrate_sum", s);
+        k_sum_partials<<<1, INTEGRAL_THREADS, 0, s>>>(part.as<double>(), blocks,
+                                                      part.as<double>() + blocks);
+    }
+    PCMS_LAUNCH_CHECK("k_tri_integral");
+    double h = 0.0;
+    PCMS_CU(cudaMemcpyAsync(&h, part.as<double>() + blocks, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PCMS_CU(cudaStreamSynchronize(s));
+    return h;
 }
 
 int64_t estimate_mesh_bytes(int64_t nv, int64_t ntri, int64_t npts) {

@@ -170,7 +170,9 @@ AsmArgs base_args(const Grid& g, const SortedPoints& S, const SortedPoints& Tp,
     a.tx64 = Tp.x64.as<double>();
     a.thl0 = Tp.hl0.as<float4>();
     a.thl1 = Tp.hl1.as<float2>();
-    a.lv = make_radius_levels(P.radius);
+    a.tcell = Tp.cell.as<int4>();
+    a.tfrac = Tp.frac.as<float4>();
+    a.lv = make_radius_levels(P.radius, g.inv_h);
     a.radius = P.radius;
     a.weight = (int)P.weight;
     a.need = P.need;
@@ -198,7 +200,7 @@ void solve_tiers(int dim, int deg, int mode, bool mixed, AsmPlan plan, const Asm
     int32_t* list3 = list2 + nt;
     int32_t* n2 = list2 + 2 * nt;
     int32_t* n3 = n2 + 1;
-    DBuf basis2(mixed ? sizeof(float4) * nt : 0, s);
+    DBuf basis2(sizeof(float4) * nt, s);
     PCMS_CU(cudaMemsetAsync(n2, 0, 2 * sizeof(int32_t), s));
     sa.list2 = list2;
     sa.n2 = n2;
@@ -208,12 +210,47 @@ void solve_tiers(int dim, int deg, int mode, bool mixed, AsmPlan plan, const Asm
     sa.group = G;
     sa.acc = mk1 == MOM_F32PAIR ? ACC_BK : ACC_PLAIN;
     sa.recentre = mixed && deg >= 1 && sa.lambda == 0.0;
+    sa.refine64 = !mixed && deg >= 1 && sa.lambda == 0.0;
     sa.tau = !mixed ? TAU_FP64 : (sa.acc == ACC_BK ? TAU_BK : TAU_MIXED);
     sa.basis_in = nullptr;
-    sa.basis2 = mixed ? basis2.as<float4>() : nullptr;
+    sa.basis2 = basis2.as<float4>();
     sa.rc = rc;
     solve_any(dim, deg, mode, mk1, sa, thread_blocks(nt, 128), s);
-    if (!mixed) return;
+    if (!mixed) {
+        if (!sa.refine64) return;
+        // FP64 refine pass: the listed targets again, in their re-centred bases
+        int32_t n_ref = 0;
+        PCMS_CU(cudaMemcpyAsync(&n_ref, n2, sizeof(n_ref), cudaMemcpyDeviceToHost, s));
+        PCMS_CU(cudaStreamSynchronize(s));
+        trace_count("mls_fp64_refine_targets", n_ref);
+        if (n_ref == 0) return;
+        DBuf mom4(sizeof(double) * np * n_ref, s);
+        AsmArgs a4 = a;
+        a4.list = list2;
+        a4.n_list = n2;
+        a4.mom = mom4.p;
+        a4.basis = basis2.as<float4>();
+        if (mode == MODE_FUSED) {
+            a4.kexp_in = a.kexp_out ? a.kexp_out : a.kexp_in;
+            a4.kexp_out = nullptr;
+        } else {
+            a4.cols = nullptr;   // the operator's columns are already written
+        }
+        // the FP64 path's fields are double (fd)
+        assemble_any(dim, deg, false, mode, G, ACC_PLAIN, true, a4, asm_blocks(n_ref, G), s);
+        SolveArgs s4 = sa;
+        s4.list = list2;
+        s4.n_list = n2;
+        s4.mom = mom4.p;
+        s4.tier = 4;
+        s4.acc = ACC_PLAIN;
+        s4.tau = TAU_FP64;
+        s4.refine64 = 0;
+        s4.basis_in = basis2.as<float4>();
+        s4.basis2 = nullptr;
+        solve_any(dim, deg, mode, MOM_F64, s4, thread_blocks(n_ref, 128), s);
+        return;
+    }
     int32_t cnt[2] = {0, 0};
     PCMS_CU(cudaMemcpyAsync(cnt, n2, sizeof(cnt), cudaMemcpyDeviceToHost, s));
     PCMS_CU(cudaStreamSynchronize(s));
@@ -278,6 +315,55 @@ void solve_tiers(int dim, int deg, int mode, bool mixed, AsmPlan plan, const Asm
     }
 }
 
+__global__ void k_max_i32(const int32_t* __restrict__ v, int64_t n, unsigned long long* out) {
+    unsigned long long m = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, (unsigned long long)max(v[i], 0));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+// Global reading of the minimum-count rule (Sec. 3.2.1): one count pass with per-target
+// growth gives every target's doublings k_t. A target's count only grows with the radius,
+// so the fewest shared doublings after which no target is short is K = max_t k_t. The
+// request then runs at the fixed radius radius * 2^K (exact in FP64), and K is added to
+// the exponents it reports.
+MlsParams settle_growth(const MlsParams& P, const double* src, int64_t ns, const double* tgt,
+                        int64_t nt, const pcms_map_opts& o, cudaStream_t s) {
+    if (P.need == 0 || P.growth != PCMS_GROWTH_GLOBAL || nt == 0) return P;
+    const int dim = P.dim;
+    const bool mixed = P.prec == PCMS_MIXED;
+    BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
+    Grid g = make_grid(dim, b.lo, b.hi, cell_edge(dim, P.radius), MAX_CELLS);
+    SortedPoints S, Tp;
+    sort_points(g, src, ns, true, mixed, S, s);
+    sort_points(g, tgt, nt, false, mixed, Tp, s, true);
+    const int G = choose_plan(dim, ns, P.radius, b.lo, b.hi, mixed).G;
+    DBuf c(sizeof(int32_t) * nt, s);
+    DBuf k(sizeof(int32_t) * nt, s);
+    DBuf mx(sizeof(unsigned long long), s);
+    PCMS_CU(cudaMemsetAsync(mx.p, 0, mx.bytes, s));
+    AsmArgs a = base_args(g, S, Tp, P);
+    a.counts = c.as<int32_t>();
+    a.kexp_out = k.as<int32_t>();
+    assemble_any(dim, 0, mixed, MODE_COUNT, G, ACC_PLAIN, false, a, asm_blocks(nt, G), s);
+    {
+        PCMS_TRACE("mls_global_doublings", s);
+        k_max_i32<<<thread_blocks(nt, 256), 256, 0, s>>>(k.as<int32_t>(), nt,
+                                                        mx.as<unsigned long long>());
+    }
+    PCMS_LAUNCH_CHECK("k_max_i32");
+    unsigned long long K = 0;
+    PCMS_CU(cudaMemcpyAsync(&K, mx.p, sizeof(K), cudaMemcpyDeviceToHost, s));
+    PCMS_CU(cudaStreamSynchronize(s));
+    MlsParams Q = P;
+    Q.radius = std::ldexp(P.radius, (int)K);
+    Q.need = 0;
+    Q.kbase = (int)K;
+    return Q;
+}
+
 }  // namespace
 
 MlsParams make_mls_params(int dim, int degree, double radius, const pcms_map_opts& o) {
@@ -291,6 +377,8 @@ MlsParams make_mls_params(int dim, int degree, double radius, const pcms_map_opt
     P.lambda = o.lambda;
     P.min_neighbors = o.min_neighbors;
     P.need = o.min_neighbors > 0 ? std::max(o.min_neighbors, P.m) : 0;
+    P.growth = o.growth;
+    P.kbase = 0;
     return P;
 }
 
@@ -308,7 +396,7 @@ int64_t estimate_mls_bytes(const MlsParams& P, int64_t ns, int64_t nt, int nf, b
     b += nt * (4.0 + 4.0 + 8.0 * d + 12.0);                          // sorted targets + scratch
     b += nt * (4.0 + 4.0 + 1.0 + 8.0 + 4.0);                         // counts, kexp, status, offsets, redo
     b += nt * (np * 8.0 + P.m * 8.0);                                // moments, y
-    if (mixed) b += nt * 32.0;                                       // tier-2 bases
+    b += nt * 33.0;                                                  // re-centred bases, row flags
     const double nnz = 1.3 * k * nt;
     if (keep_map || nf > 2) b += nnz * (4.0 + elem);                 // operator
     b += (double)(ns + nt) * std::max(nf, 1) * elem * 2.0;           // apply/permute scratch
@@ -328,6 +416,7 @@ int64_t MapImpl::device_bytes() const {
 // ------------------------------------------------------------------------------------
 void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms_map_opts& o) {
     cudaStream_t s = M.stream;
+    M.P = settle_growth(M.P, src, M.ns, tgt, M.nt, o, s);
     const MlsParams& P = M.P;
     const int dim = P.dim, deg = P.degree, m = P.m;
     const bool mixed = P.prec == PCMS_MIXED;
@@ -335,7 +424,7 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
     BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
     M.g = make_grid(dim, b.lo, b.hi, cell_edge(dim, P.radius), MAX_CELLS);
     sort_points(M.g, src, ns, true, mixed, M.src, s);
-    sort_points(M.g, tgt, nt, false, mixed, M.tgt, s);
+    sort_points(M.g, tgt, nt, false, mixed, M.tgt, s, true);
     const AsmPlan plan = choose_plan(dim, ns, P.radius, b.lo, b.hi, mixed);
     const int G = plan.G;
 
@@ -370,8 +459,9 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
         const size_t melem = mom_elem_bytes(mom_kind(mixed, plan.acc));
         DBuf mom(melem * np * nt, s);
         DBuf y(sizeof(double) * m * nt, s);
+        DBuf yf(mixed ? sizeof(float2) * m * nt : 0, s);
         DBuf flags(sizeof(int8_t) * nt, s);
-        DBuf rc(mixed ? sizeof(float4) * nt : 0, s);
+        DBuf rc(sizeof(float4) * nt, s);
         a.offsets = M.offsets.as<int64_t>();
         a.mom = mom.p;
         if (one_pass) {
@@ -432,13 +522,14 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
         sa.mom = mom.p;
         sa.lambda = P.lambda;
         sa.y = y.as<double>();
-        sa.flags = mixed ? flags.as<int8_t>() : nullptr;
+        sa.yf = mixed ? yf.as<float2>() : nullptr;
+        sa.flags = flags.as<int8_t>();
         sa.status = M.status.as<int8_t>();
-        solve_tiers(dim, deg, MODE_MAP, mixed, plan, a, sa, nt, mixed ? rc.as<float4>() : nullptr, s);
+        solve_tiers(dim, deg, MODE_MAP, mixed, plan, a, sa, nt, rc.as<float4>(), s);
 
         ShapeArgs sh{};
-        sh.flags = mixed ? flags.as<int8_t>() : nullptr;
-        sh.rc = mixed ? rc.as<float4>() : nullptr;
+        sh.flags = flags.as<int8_t>();
+        sh.rc = rc.as<float4>();
         sh.g = M.g;
         sh.ns = ns;
         sh.nt = nt;
@@ -454,6 +545,7 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
         sh.counts = M.counts.as<int32_t>();
         sh.cols = M.cols.as<int32_t>();
         sh.y = y.as<double>();
+        sh.yf = mixed ? yf.as<float2>() : nullptr;
         sh.radius = P.radius;
         sh.weight = (int)P.weight;
         sh.vals = M.vals.p;
@@ -489,25 +581,27 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
 // ------------------------------------------------------------------------------------
 __global__ void k_counts_to_caller(int64_t nt, const int32_t* __restrict__ perm_t,
                                    const int32_t* __restrict__ c, const int32_t* __restrict__ k,
-                                   int32_t* __restrict__ c_out, int32_t* __restrict__ k_out) {
+                                   int32_t* __restrict__ c_out, int32_t* __restrict__ k_out,
+                                   int kadd) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t o = perm_t[i];
         c_out[o] = c[i];
-        if (k_out) k_out[o] = k[i];
+        if (k_out) k_out[o] = k[i] + kadd;
     }
 }
 
-void mls_count(const MlsParams& P, const double* src, int64_t ns, const double* tgt, int64_t nt,
+void mls_count(const MlsParams& P0, const double* src, int64_t ns, const double* tgt, int64_t nt,
                const pcms_map_opts& o, int32_t* counts, int32_t* kexp, int64_t* total,
                cudaStream_t s) {
+    const MlsParams P = settle_growth(P0, src, ns, tgt, nt, o, s);
     const int dim = P.dim;
     const bool mixed = P.prec == PCMS_MIXED;
     BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
     Grid g = make_grid(dim, b.lo, b.hi, cell_edge(dim, P.radius), MAX_CELLS);
     SortedPoints S, Tp;
     sort_points(g, src, ns, true, mixed, S, s);
-    sort_points(g, tgt, nt, false, mixed, Tp, s);
+    sort_points(g, tgt, nt, false, mixed, Tp, s, true);
     const int G = choose_plan(dim, ns, P.radius, b.lo, b.hi, mixed).G;
     DBuf c(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
     DBuf k(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
@@ -519,7 +613,7 @@ void mls_count(const MlsParams& P, const double* src, int64_t ns, const double* 
         assemble_any(dim, 0, mixed, MODE_COUNT, G, ACC_PLAIN, false, a, asm_blocks(nt, G), s);
         PCMS_TRACE("mls_counts_to_caller", s);
         k_counts_to_caller<<<thread_blocks(nt, 256), 256, 0, s>>>(
-            nt, Tp.perm.as<int32_t>(), c.as<int32_t>(), k.as<int32_t>(), counts, kexp);
+            nt, Tp.perm.as<int32_t>(), c.as<int32_t>(), k.as<int32_t>(), counts, kexp, P.kbase);
         PCMS_LAUNCH_CHECK("counts_to_caller");
     }
     if (total) {
@@ -533,9 +627,10 @@ void mls_count(const MlsParams& P, const double* src, int64_t ns, const double* 
 // ------------------------------------------------------------------------------------
 // one-shot transfer (no operator)
 // ------------------------------------------------------------------------------------
-void mls_transfer(const MlsParams& P, const double* src, int64_t ns, const double* tgt,
+void mls_transfer(const MlsParams& P0, const double* src, int64_t ns, const double* tgt,
                   int64_t nt, const pcms_map_opts& o, const void* fields, int nf, void* out,
                   int8_t* status, cudaStream_t s, int64_t* n_under) {
+    const MlsParams P = settle_growth(P0, src, ns, tgt, nt, o, s);
     const int dim = P.dim, deg = P.degree;
     const bool mixed = P.prec == PCMS_MIXED;
     *n_under = 0;
@@ -543,7 +638,7 @@ void mls_transfer(const MlsParams& P, const double* src, int64_t ns, const doubl
     Grid g = make_grid(dim, b.lo, b.hi, cell_edge(dim, P.radius), MAX_CELLS);
     SortedPoints S, Tp;
     sort_points(g, src, ns, true, mixed, S, s);
-    sort_points(g, tgt, nt, false, mixed, Tp, s);
+    sort_points(g, tgt, nt, false, mixed, Tp, s, true);
     const AsmPlan plan = choose_plan(dim, ns, P.radius, b.lo, b.hi, mixed);
     const int G = plan.G;
     const size_t fsz = mixed ? sizeof(float) : sizeof(double);

@@ -29,13 +29,15 @@ inline void assemble_any(int dim, int deg, bool mixed, int mode, int G, int acc,
                          const AsmArgs& a, int blocks, cudaStream_t s) {
     const bool bk = mixed && mode != MODE_COUNT && G == 32 && acc == ACC_BK;
     // a target list means a later tier of the mixed path (tier 2: blocked FP32, tier 3: FP64)
-    static const char* names[5][3] = {
+    // or the FP64 path's refine pass (a list with a re-centred basis)
+    static const char* names[6][3] = {
         {"mls_count_fp64", "mls_assemble_map_fp64", "mls_assemble_fused_fp64"},
         {"mls_count_mixed", "mls_assemble_map_mixed", "mls_assemble_fused_mixed"},
         {"mls_count_mixed", "mls_assemble_map_bk", "mls_assemble_fused_bk"},
         {"mls_count_mixed", "mls_assemble_map_tier2", "mls_assemble_fused_tier2"},
-        {"mls_count_fp64", "mls_assemble_map_tier3", "mls_assemble_fused_tier3"}};
-    const int row = !mixed ? (a.list ? 4 : 0) : (!bk ? 1 : (a.list ? 3 : 2));
+        {"mls_count_fp64", "mls_assemble_map_tier3", "mls_assemble_fused_tier3"},
+        {"mls_count_fp64", "mls_assemble_map_fp64_refine", "mls_assemble_fused_fp64_refine"}};
+    const int row = !mixed ? (a.list ? (a.basis ? 5 : 4) : 0) : (!bk ? 1 : (a.list ? 3 : 2));
     PCMS_TRACE(names[row][mode], s);
     if (dim == 2) assemble_dispatch_d2(deg, mixed, mode, G, bk ? ACC_BK : ACC_PLAIN, fd, a, blocks, s);
     else assemble_dispatch_d3(deg, mixed, mode, G, bk ? ACC_BK : ACC_PLAIN, fd, a, blocks, s);

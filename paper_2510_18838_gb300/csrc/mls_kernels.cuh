@@ -55,9 +55,10 @@ struct RadiusLevels {
     double inv_r[MAX_DOUBLINGS + 1];   // 1 / r
     float r2f[MAX_DOUBLINGS + 1];      // (float)(r * r)
     float inv_rf[MAX_DOUBLINGS + 1];   // (float)(1 / r)
+    float rcell[MAX_DOUBLINGS + 1];    // the radius in cell units, (float)(r / h), at most 2^30
 };
 
-inline RadiusLevels make_radius_levels(double radius) {
+inline RadiusLevels make_radius_levels(double radius, double inv_h) {
     RadiusLevels L;
     for (int k = 0; k <= MAX_DOUBLINGS; k++) {
         const double r = std::ldexp(radius, k);
@@ -66,6 +67,7 @@ inline RadiusLevels make_radius_levels(double radius) {
         L.inv_r[k] = 1.0 / r;
         L.r2f[k] = (float)(r * r);
         L.inv_rf[k] = (float)(1.0 / r);
+        L.rcell[k] = std::fmin((float)(r * inv_h), 1073741824.f);
     }
     return L;
 }
@@ -80,6 +82,8 @@ struct AsmArgs {
     const double* tx64;   // [dim][nt] sorted targets
     const float4* thl0;   // mixed: sorted targets' hi/lo (same layout as hl0/hl1)
     const float2* thl1;
+    const int4* tcell;    // sorted targets' cell coordinates and positions in the cell
+    const float4* tfrac;  // (point_cell)
     RadiusLevels lv;
     const int32_t* list;  // optional target list (length *n_list); moments then indexed by list position
     const int32_t* n_list;
@@ -101,7 +105,7 @@ struct AsmArgs {
     int32_t* n_redo;
     const void* field;       // FUSED: sorted field (float or double)
     void* mom;               // MAP/FUSED: [nt][NACCP] (float, float2 for ACC_BK, or double)
-    const float4* basis;     // ACC_BK list mode: per list position (c_x, c_y, c_z, 1/s), or null
+    const float4* basis;     // list mode (ACC_BK, or FP64): per list position (c_x, c_y, c_z, 1/s), or null
     unsigned* err;
 };
 
@@ -127,9 +131,17 @@ struct AsmArgs {
 // weighted centroid and s the weighted spread of the tier-1 neighbours, and evaluates the
 // fitted polynomial at u'_t = -c/s: G' y = a(u'_t), c_0 = y^T g'. (c, 1/s) are rounded to
 // FP32 once and define the basis exactly for assembly, solve and operator rows.
+//
+// The FP64 path has the same sensitivity, 2^29 times smaller: FP64 normal equations give
+// c_0 to about 15 * amp * 2^-53 (numpy on extrapolating 3D quadratic targets, amp up to
+// 2e6). Its targets with amp > AMP_FP64 keep their target-centred status and values, and are
+// assembled and solved once more in FP64 in the re-centred basis (the "refine" pass); if
+// that solve passes its pivot guard its values replace the first ones. On extrapolating
+// targets this cuts amp and the error by factors of 50 to 300.
 constexpr double AMP_T1 = 64.0;
 constexpr double AMP_BK = 32.0;
 constexpr double AMP_SHAPE = 32.0;   // operator rows above this are evaluated in FP64
+constexpr double AMP_FP64 = 256.0;   // FP64 path: above this the error may pass 4e-13
 
 struct SolveArgs {
     int64_t nt;
@@ -143,6 +155,7 @@ struct SolveArgs {
     int group;                // lanes per target of the assembly (error model)
     int acc;                  // ACC_PLAIN or ACC_BK: how these moments were accumulated
     int recentre;             // tier 1 -> 2: hand on a re-centred basis (lambda = 0, degree >= 1)
+    int refine64;             // FP64 path: list targets with amp > AMP_FP64 for the refine pass
     const float4* basis_in;   // tier 2: basis of these moments, per list position
     float4* basis2;           // tier 1: basis for tier 2, per list2 position
     float4* rc;               // MAP: basis of the accepted tier-2 rows, per sorted target
@@ -151,6 +164,7 @@ struct SolveArgs {
     int32_t* list3;
     int32_t* n3;
     double* y;                // MAP: [nt][m]
+    float2* yf;               // mixed MAP: y as FP32 pairs {hi, lo} (y = hi + lo to ~2^-48)
     int8_t* flags;            // MAP: how to evaluate the operator row (k_shape)
     int8_t* status;           // MAP: sorted order; FUSED: caller order (via perm) or null
     const int32_t* perm_t;    // FUSED: sorted -> caller target index
@@ -173,6 +187,7 @@ struct ShapeArgs {
     const int32_t* counts;    // row lengths
     const int32_t* cols;
     const double* y;
+    const float2* yf;   // mixed: y as FP32 pairs (written by the solve)
     const int8_t* flags;   // per target (mixed maps), or null: see k_shape
     const float4* rc;      // per target: re-centred basis of flag-3 rows
     double radius;
@@ -478,17 +493,26 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemb
 
     for (int64_t wk = gid; wk < nwork; wk += ngroups) {
         const int64_t t = A.list ? (int64_t)A.list[wk] : wk;
+        // The target's cell and position in it were computed once when the targets were
+        // sorted; its FP64 coordinates are only read by the FP64 path (and, on the mixed
+        // path, by the rare exact decision), which keeps FP64 work out of the target set-up
+        // that all G lanes of the group repeat.
         double tx[3] = {0.0, 0.0, 0.0};
         long long ct[3] = {0, 0, 0};
         float fr[3] = {0.f, 0.f, 0.f};
+        {
+            const int4 c4 = A.tcell[t];
+            const float4 f4 = A.tfrac[t];
+            ct[0] = c4.x;
+            ct[1] = c4.y;
+            ct[2] = c4.z;
+            fr[0] = f4.x;
+            fr[1] = f4.y;
+            fr[2] = f4.z;
+        }
+        if constexpr (!MIXED) {
 #pragma unroll
-        for (int d = 0; d < DIM; d++) {
-            tx[d] = A.tx64[d * A.nt + t];
-            const double u = (tx[d] - g.lo[d]) * g.inv_h;   // position in cell units
-            double f = floor(u);
-            f = fmin(fmax(f, -1073741824.0), 1073741824.0);
-            ct[d] = (long long)f;
-            fr[d] = (float)(u - f);
+            for (int d = 0; d < DIM; d++) tx[d] = A.tx64[d * A.nt + t];
         }
         float thi[3] = {0.f, 0.f, 0.f}, tlo[3] = {0.f, 0.f, 0.f};
         if constexpr (MIXED) load_hilo<DIM>(A.thl0, A.thl1, t, thi, tlo);
@@ -500,10 +524,10 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemb
             row_off = A.offsets[t];
             row_len = A.counts[t];
         }
-        // re-centred basis (blocked tier 2 only)
+        // re-centred basis (blocked tier 2, FP64 refine pass)
         T bcv[4] = {T(0), T(0), T(0), T(1)};
         const T* bc = nullptr;
-        if constexpr (ACC == ACC_BK) {
+        if constexpr (ACC == ACC_BK || !MIXED) {
             if (A.basis) {
                 const float4 bb = A.basis[wk];
                 bcv[0] = bb.x;
@@ -529,7 +553,7 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemb
             // Candidate rows: cells (y, z) whose slab comes within r of the target, each
             // trimmed in x to the ball's chord. Computed in cell units in FP32 with a margin
             // m far above the FP32 error, so the rows and chords only ever over-cover.
-            const float R0 = fminf((float)(r * g.inv_h), 1073741824.f);
+            const float R0 = A.lv.rcell[k];
             const float mg = 1e-3f + R0 * 1e-6f;
             const float RR = R0 + mg;
             long long z0 = 0, z1 = 0;
@@ -639,8 +663,12 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemb
                             float d2f = ddx * ddx + ddy * ddy;
                             if (DIM == 3) d2f += ddz * ddz;
                             int cl = classify32(A.weight, d2f, r2f);
-                            if (cl < 0)
-                                cl = select_exact(A.weight, dist2_exact<DIM>(A.sx64, A.ns, j, tx), r, r2);
+                            if (cl < 0) {
+                                double te[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+                                for (int d = 0; d < DIM; d++) te[d] = A.tx64[d * A.nt + t];
+                                cl = select_exact(A.weight, dist2_exact<DIM>(A.sx64, A.ns, j, te), r, r2);
+                            }
                             in = cl != 0;
                             dx[0] = (T)ddx;
                             dx[1] = (T)ddy;
@@ -981,6 +1009,12 @@ __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
                                                recentred ? at : nullptr))
                 st = PCMS_TARGET_ILL_CONDITIONED;
         }
+        if (S.tier == 4 && st != PCMS_TARGET_OK) continue;   // keep the first FP64 solve
+        if (S.tier == 3 && S.refine64 && st == PCMS_TARGET_OK && amp > AMP_FP64) {
+            const int pos = atomicAdd(S.n2, 1);
+            S.list2[pos] = (int32_t)t;
+            S.basis2[pos] = recentre_basis<DIM>(mom);
+        }
         if (S.tier < 3 && st != PCMS_TARGET_UNDERDETERMINED) {
             bool ok = st == PCMS_TARGET_OK;
             if (ok) {
@@ -1012,7 +1046,7 @@ __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
         // 2 = everything in FP64 (tier 3: y belongs to the exact FP64 moments);
         // 3 = as 1 in the re-centred basis rc[t]
         if (MODE == MODE_MAP && S.flags) {
-            const int flag = S.tier == 3 ? 2 : (recentred ? 3 : (amp > AMP_SHAPE ? 1 : 0));
+            const int flag = recentred ? 3 : (S.tier == 3 ? 2 : (amp > AMP_SHAPE ? 1 : 0));
             S.flags[t] = (int8_t)flag;
             if (recentred && S.rc) S.rc[t] = bas;
         }
@@ -1025,7 +1059,14 @@ __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
             if (S.status) S.status[o] = (int8_t)st;
         } else {
 #pragma unroll
-            for (int k = 0; k < M; k++) S.y[t * M + k] = st == PCMS_TARGET_OK ? y[k] : nanv;
+            for (int k = 0; k < M; k++) {
+                const double yk = st == PCMS_TARGET_OK ? y[k] : nanv;
+                S.y[t * M + k] = yk;
+                if (S.yf) {
+                    const float hi = (float)yk;
+                    S.yf[t * M + k] = make_float2(hi, (float)(yk - (double)hi));
+                }
+            }
             S.status[t] = (int8_t)st;
         }
     }
@@ -1046,23 +1087,32 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
     const int64_t gid = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * GPW + gi;
     const Grid& g = S.g;
     for (int64_t t = gid; t < S.nt; t += ngroups) {
+        // the FP64 target coordinates serve the FP64 rows only; the FP32 pairs of y come from
+        // the solve (one conversion per target instead of one per lane)
         double tx[3] = {0, 0, 0};
         float thi[3] = {0.f, 0.f, 0.f}, tlo[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int d = 0; d < DIM; d++) tx[d] = S.tx64[d * S.nt + t];
         if constexpr (MIXED) load_hilo<DIM>(S.thl0, S.thl1, t, thi, tlo);
         // y as T, and for mixed maps also as an unevaluated FP32 pair (y = yh + yl to ~2^-48)
         T y[M];
         float yl[M];
 #pragma unroll
         for (int k = 0; k < M; k++) {
-            const double yk = S.y[t * M + k];
-            y[k] = (T)yk;
-            yl[k] = MIXED ? (float)(yk - (double)(float)yk) : 0.f;
+            if constexpr (MIXED) {
+                const float2 v = S.yf[t * M + k];
+                y[k] = v.x;
+                yl[k] = v.y;
+            } else {
+                y[k] = S.y[t * M + k];
+                yl[k] = 0.f;
+            }
         }
         const int flag = S.flags ? S.flags[t] : 0;
+        if (!MIXED || flag == 2) {
+#pragma unroll
+            for (int d = 0; d < DIM; d++) tx[d] = S.tx64[d * S.nt + t];
+        }
         T bcv[4] = {T(0), T(0), T(0), T(1)};
-        if (MIXED && flag == 3) {
+        if (flag == 3) {   // re-centred basis (mixed tier 2, FP64 refine pass)
             const float4 b4 = S.rc[t];
             bcv[0] = b4.x;
             bcv[1] = b4.y;
@@ -1123,7 +1173,7 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
             else qv = sqrt(d2) * inv_r;
             const T w = weight_value<T>(S.weight, qv);
             T u[3];
-            basis_offsets<DIM, T>(dx, inv_r, (MIXED && flag == 3) ? bcv : nullptr, u);
+            basis_offsets<DIM, T>(dx, inv_r, flag == 3 ? bcv : nullptr, u);
             if constexpr (MIXED) {
                 if (flag) {
                     // sensitive row (1), or a row in a re-centred basis (3): the same FP32 u

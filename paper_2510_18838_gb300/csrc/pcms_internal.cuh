@@ -73,6 +73,26 @@ struct Grid {
 // most 2^k cells away (per axis) from the target's cell, for radius r 2^k.
 Grid make_grid(int dim, const double* lo, const double* hi, double radius, int64_t max_cells);
 
+// Where a point sits in the grid, in cell units: the cell coordinates (the floor, clamped
+// to +-2^30, points outside the box included) and the FP32 position inside that cell. The
+// radius-search walk starts from these. Unused axes give 0.
+#ifdef __CUDACC__
+__device__ __forceinline__ void point_cell(const Grid& g, int dim, const double* x, int4* cell,
+                                           float4* frac) {
+    int c[3] = {0, 0, 0};
+    float f[3] = {0.f, 0.f, 0.f};
+    for (int d = 0; d < dim; d++) {
+        const double u = (x[d] - g.lo[d]) * g.inv_h;
+        double fl = floor(u);
+        fl = fmin(fmax(fl, -1073741824.0), 1073741824.0);
+        c[d] = (int)fl;
+        f[d] = (float)(u - fl);
+    }
+    *cell = make_int4(c[0], c[1], c[2], 0);
+    *frac = make_float4(f[0], f[1], f[2], 0.f);
+}
+#endif
+
 // ------------------------------------------------------------------------------------
 // points sorted by cell (counting sort)
 // ------------------------------------------------------------------------------------
@@ -85,6 +105,8 @@ struct SortedPoints {
     DBuf x64;         // float64 [dim][n] sorted coordinates
     DBuf hl0;         // float4 [n] (mixed path): 2D {xh,yh,xl,yl}; 3D {xh,yh,zh,xl}
     DBuf hl1;         // float2 [n] (mixed path, 3D): {yl,zl}
+    DBuf cell;        // int4 [n] (targets): point_cell's cell coordinates
+    DBuf frac;        // float4 [n] (targets): point_cell's position inside the cell
 };
 
 // bounding box of pts (float64 [dim][n]) into dev_box[6] = {lo0,lo1,lo2,hi0,hi1,hi2};
@@ -95,7 +117,7 @@ void launch_bbox(int dim, const double* pts, int64_t n, double* dev_box, long lo
 // Sort points by cell of grid g. with_start: also build cell_start (sources).
 // with_hl: also write FP32 hi/lo coordinates relative to g.lo (mixed path).
 void sort_points(const Grid& g, const double* pts, int64_t n, bool with_start, bool with_hl,
-                 SortedPoints& out, cudaStream_t s);
+                 SortedPoints& out, cudaStream_t s, bool with_cell = false);
 
 // exclusive scan of int32 counts into out[0..n] (out[n] = total); T = int32_t or int64_t
 template <typename T>
@@ -180,7 +202,9 @@ struct MlsParams {
     pcms_weight weight;
     double radius, lambda;
     int min_neighbors;
-    int need;  // max(min_neighbors, m) if min_neighbors > 0 else 0
+    int need;    // max(min_neighbors, m) if min_neighbors > 0 else 0
+    int growth;  // pcms_growth
+    int kbase;   // doublings already in radius (global growth), added to reported exponents
 };
 
 MlsParams make_mls_params(int dim, int degree, double radius, const pcms_map_opts& o);
@@ -247,6 +271,8 @@ struct MeshImpl {
 void mesh_create(MeshImpl& M, const double* xy, int64_t nv, const int32_t* tri, int64_t ntri);
 void mesh_locate(const MeshImpl& M, const double* pts, int64_t n, const double* field,
                  int32_t* elem, int8_t* edim, double* vals, cudaStream_t s);
+void mesh_centroids(const MeshImpl& M, double* out, cudaStream_t s);
+double mesh_integrate(const MeshImpl& M, const double* field, cudaStream_t s);
 
 // number of SMs of the current device (cached)
 int num_sms();

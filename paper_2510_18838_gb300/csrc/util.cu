@@ -393,7 +393,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* __res
 __global__ void k_gather_sorted(int dim, Grid g, const double* __restrict__ pts, int64_t n,
                                 const uint32_t* __restrict__ order, int32_t* __restrict__ perm,
                                 int32_t* __restrict__ inv, double* __restrict__ x64,
-                                float4* __restrict__ hl0, float2* __restrict__ hl1) {
+                                float4* __restrict__ hl0, float2* __restrict__ hl1,
+                                int4* __restrict__ cell, float4* __restrict__ frac) {
     for (int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pos < n;
          pos += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = order[pos];
@@ -404,6 +405,7 @@ __global__ void k_gather_sorted(int dim, Grid g, const double* __restrict__ pts,
             x[d] = pts[d * n + i];
             x64[d * n + pos] = x[d];
         }
+        if (cell) point_cell(g, dim, x, &cell[pos], &frac[pos]);
         if (hl0) {
             float h[3], l[3];
             for (int d = 0; d < 3; d++) {
@@ -422,7 +424,7 @@ __global__ void k_gather_sorted(int dim, Grid g, const double* __restrict__ pts,
 }
 
 void sort_points(const Grid& g, const double* pts, int64_t n, bool with_start, bool with_hl,
-                 SortedPoints& out, cudaStream_t s) {
+                 SortedPoints& out, cudaStream_t s, bool with_cell) {
     out.dim = g.dim;
     out.n = n;
     const int dim = g.dim;
@@ -440,6 +442,10 @@ void sort_points(const Grid& g, const double* pts, int64_t n, bool with_start, b
     if (with_hl) {
         out.hl0.alloc(sizeof(float4) * nn, s);
         if (dim == 3) out.hl1.alloc(sizeof(float2) * nn, s);
+    }
+    if (with_cell) {
+        out.cell.alloc(sizeof(int4) * nn, s);
+        out.frac.alloc(sizeof(float4) * nn, s);
     }
     DBuf start_tmp;
     int32_t* start;
@@ -482,7 +488,9 @@ void sort_points(const Grid& g, const double* pts, int64_t n, bool with_start, b
         k_gather_sorted<<<blocks, 256, 0, s>>>(dim, g, pts, n, v0, out.perm.as<int32_t>(),
                                                out.inv.as<int32_t>(), out.x64.as<double>(),
                                                with_hl ? out.hl0.as<float4>() : nullptr,
-                                               (with_hl && dim == 3) ? out.hl1.as<float2>() : nullptr);
+                                               (with_hl && dim == 3) ? out.hl1.as<float2>() : nullptr,
+                                               with_cell ? out.cell.as<int4>() : nullptr,
+                                               with_cell ? out.frac.as<float4>() : nullptr);
     }
     PCMS_LAUNCH_CHECK("gather_sorted");
 }

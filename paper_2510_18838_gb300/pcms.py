@@ -33,7 +33,7 @@ class MapOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("weight", ctypes.c_int),
                 ("lambda_", ctypes.c_double), ("min_neighbors", ctypes.c_int),
                 ("domain_known", ctypes.c_int), ("lo", ctypes.c_double * 3),
-                ("hi", ctypes.c_double * 3)]
+                ("hi", ctypes.c_double * 3), ("growth", ctypes.c_int)]
 
 
 class MapInfo(ctypes.Structure):
@@ -92,6 +92,8 @@ SIGNATURES = {
     "pcms_map_destroy": (None, [_P, _P]),
     "pcms_mesh_create": (_I, [_P, _I64, _P, _I64, _P, _P]),
     "pcms_locate_interp": (_I, [_P, _P, _I64, _P, _P, _P, _P, _P]),
+    "pcms_mesh_centroids": (_I, [_P, _P, _P]),
+    "pcms_mesh_integrate": (_I, [_P, _P, _P, _P]),
     "pcms_mesh_destroy": (None, [_P, _P]),
     "pcms_server_create": (_I, [_I, _I64, _P]),
     "pcms_server_submit": (_I, [_P, _P, _P]),
@@ -166,13 +168,20 @@ def _dev(t, dtype, name):
     return t.contiguous()
 
 
-def make_opts(precision="fp64", weight="wendland_c2", lam=0.0, min_neighbors=0, domain=None):
+GROWTH = {"target": 0, "global": 1}
+
+
+def make_opts(precision="fp64", weight="wendland_c2", lam=0.0, min_neighbors=0, domain=None,
+              growth="target"):
+    """pcms_map_opts. growth: "target" (each target doubles its radius) or "global" (one
+    shared radius for all targets), used when min_neighbors > 0."""
     o = MapOpts()
     lib().pcms_map_opts_default(ctypes.byref(o))
     o.precision = FP64 if precision == "fp64" else MIXED
     o.weight = WEIGHTS[weight]
     o.lambda_ = float(lam)
     o.min_neighbors = int(min_neighbors)
+    o.growth = GROWTH[growth]
     if domain is not None:
         lo, hi = domain
         o.domain_known = 1
@@ -205,6 +214,19 @@ class Map:
             out = torch.empty((nf, self.n_tgt), dtype=self.dtype, device=f.device)
         _check(lib().pcms_apply_map(self.handle, _ptr(f), nf, _ptr(out), _stream(stream)))
         return out[0] if squeeze else out
+
+    def apply_noalloc(self, fields, out, stream=None):
+        """pcms_apply_map_noalloc into a caller tensor (no allocation on any side; usable
+        inside CUDA-graph capture). fields [F, n_src] or [n_src], out [F, n_tgt] or [n_tgt],
+        both contiguous CUDA tensors of the map's dtype."""
+        for t, name in ((fields, "fields"), (out, "out")):
+            if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != self.dtype \
+                    or not t.is_contiguous():
+                raise TypeError(f"{name} must be a contiguous CUDA {self.dtype} tensor")
+        nf = 1 if fields.dim() == 1 else fields.shape[0]
+        _check(lib().pcms_apply_map_noalloc(self.handle, _ptr(fields), nf, _ptr(out),
+                                            _stream(stream)))
+        return out
 
     def info(self) -> dict:
         i = MapInfo()
@@ -239,12 +261,13 @@ class Map:
 
 
 def create_map(src, tgt, degree, radius, precision="fp64", weight="wendland_c2", lam=0.0,
-               min_neighbors=0, domain=None, stream=None, allow_underdetermined=True) -> Map:
+               min_neighbors=0, domain=None, stream=None, allow_underdetermined=True,
+               growth="target") -> Map:
     """pcms_create_map. src/tgt: float64 CUDA tensors [dim, n]."""
     src = _dev(src, torch.float64, "src")
     tgt = _dev(tgt, torch.float64, "tgt")
     dim = src.shape[0]
-    o = make_opts(precision, weight, lam, min_neighbors, domain)
+    o = make_opts(precision, weight, lam, min_neighbors, domain, growth)
     h = ctypes.c_void_p()
     st = lib().pcms_create_map(dim, _ptr(src), src.shape[1], _ptr(tgt), tgt.shape[1], int(degree),
                                float(radius), ctypes.byref(o), _stream(stream), ctypes.byref(h))
@@ -254,7 +277,8 @@ def create_map(src, tgt, degree, radius, precision="fp64", weight="wendland_c2",
 
 
 def mls_transfer(src, tgt, fields, degree, radius, precision="fp64", weight="wendland_c2",
-                 lam=0.0, min_neighbors=0, domain=None, with_status=True, out=None, stream=None):
+                 lam=0.0, min_neighbors=0, domain=None, with_status=True, out=None, stream=None,
+                 growth="target"):
     """pcms_mls_transfer (one shot, no operator kept). Returns (values [F, nt], status)."""
     src = _dev(src, torch.float64, "src")
     tgt = _dev(tgt, torch.float64, "tgt")
@@ -267,7 +291,7 @@ def mls_transfer(src, tgt, fields, degree, radius, precision="fp64", weight="wen
     if out is None:
         out = torch.empty((nf, nt), dtype=dt, device=src.device)
     status = torch.empty(max(nt, 1), dtype=torch.int8, device=src.device) if with_status else None
-    o = make_opts(precision, weight, lam, min_neighbors, domain)
+    o = make_opts(precision, weight, lam, min_neighbors, domain, growth)
     st = lib().pcms_mls_transfer(src.shape[0], _ptr(src), src.shape[1], _ptr(tgt), nt, int(degree),
                                  float(radius), ctypes.byref(o), _ptr(f), nf, _ptr(out),
                                  _ptr(status), _stream(stream))
@@ -277,7 +301,8 @@ def mls_transfer(src, tgt, fields, degree, radius, precision="fp64", weight="wen
 
 
 def count_neighbors(src, tgt, radius, degree=1, precision="fp64", weight="wendland_c2",
-                    min_neighbors=0, domain=None, with_doublings=False, stream=None):
+                    min_neighbors=0, domain=None, with_doublings=False, stream=None,
+                    growth="target"):
     """pcms_count_neighbors: per-target neighbour counts (caller order), optionally with the
     radius doublings."""
     src = _dev(src, torch.float64, "src")
@@ -285,7 +310,7 @@ def count_neighbors(src, tgt, radius, degree=1, precision="fp64", weight="wendla
     nt = tgt.shape[1]
     counts = torch.empty(max(nt, 1), dtype=torch.int32, device=src.device)
     kx = torch.empty(max(nt, 1), dtype=torch.int32, device=src.device) if with_doublings else None
-    o = make_opts(precision, weight, 0.0, min_neighbors, domain)
+    o = make_opts(precision, weight, 0.0, min_neighbors, domain, growth)
     _check(lib().pcms_count_neighbors(src.shape[0], _ptr(src), src.shape[1], _ptr(tgt), nt,
                                       int(degree), float(radius), ctypes.byref(o), _ptr(counts),
                                       _ptr(kx), None, _stream(stream)))
@@ -325,6 +350,22 @@ class Mesh:
                                         _stream(stream)))
         return (elem[:n], edim[:n] if with_dim else None,
                 values[:n] if field is not None else None)
+
+    def centroids(self, stream=None, out=None):
+        """pcms_mesh_centroids: float64 [2, n_tri] triangle centroids."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if out is None:
+            out = torch.empty((2, max(self.n_tri, 1)), dtype=torch.float64, device=dev)
+        _check(lib().pcms_mesh_centroids(self.handle, _ptr(out), _stream(stream)))
+        return out[:, :self.n_tri]
+
+    def integrate(self, field, stream=None) -> float:
+        """pcms_mesh_integrate: integral of the piecewise-linear interpolant of a nodal field
+        (float64 [n_vertices]) over the mesh; synchronises the stream."""
+        f = _dev(field, torch.float64, "field")
+        v = ctypes.c_double()
+        _check(lib().pcms_mesh_integrate(self.handle, _ptr(f), ctypes.byref(v), _stream(stream)))
+        return float(v.value)
 
     def destroy(self, stream=None):
         if self.handle:

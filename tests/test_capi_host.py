@@ -35,7 +35,7 @@ def test_version_and_defaults(lib):
     o = pcms.MapOpts()
     lib.pcms_map_opts_default(ctypes.byref(o))
     assert o.precision == pcms.FP64 and o.weight == 0 and o.lambda_ == 0.0
-    assert o.min_neighbors == 0 and o.domain_known == 0
+    assert o.min_neighbors == 0 and o.domain_known == 0 and o.growth == 0
 
 
 @pytest.mark.parametrize("dim,deg,radius,ns,nt", [
@@ -62,7 +62,8 @@ def test_null_pointers_and_bad_opts_rejected(lib):
     o = pcms.MapOpts()
     lib.pcms_map_opts_default(ctypes.byref(o))
     fake = ctypes.c_void_p(0x1000)
-    for field, val in [("precision", 7), ("weight", 42), ("lambda_", -1.0), ("min_neighbors", -3)]:
+    for field, val in [("precision", 7), ("weight", 42), ("lambda_", -1.0), ("min_neighbors", -3),
+                       ("growth", 2), ("growth", -1)]:
         bad = pcms.MapOpts.from_buffer_copy(o)
         setattr(bad, field, val)
         assert lib.pcms_create_map(2, fake, 5, fake, 5, 1, 0.1, ctypes.byref(bad), None,

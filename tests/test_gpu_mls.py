@@ -203,6 +203,41 @@ def test_mixed_growth_gaussian_mixture(P):
     assert kx.max() >= 1
 
 
+@pytest.mark.parametrize("dim,prec,deg", [(2, "fp64", 1), (2, "mixed", 2), (3, "mixed", 1),
+                                          (3, "fp64", 2)])
+def test_global_growth_matches_oracle(P, dim, prec, deg):
+    """Global reading of the minimum-count rule: one shared radius r 2^K for every target.
+    Neighbour lists, doublings (K everywhere), values and statuses against the oracle's
+    global mode, through the operator, the one-shot transfer and the count entry point."""
+    ns, nt, r, need = (5000, 1500, 0.01, 12) if dim == 2 else (12000, 900, 0.03, 20)
+    src, tgt = _case(dim, ns, nt, 700 + dim, outside=0.25)
+    f = np.sin(3 * src[0]) + src[1] * src[-1]
+    o = oracle.mls(src, tgt, f, deg, r, min_neighbors=need, mode="grid", growth="global",
+                   shape=True)
+    K = int(o["kexp"][0])
+    assert K >= 2 and (o["kexp"] == K).all()
+    dt = np.float64 if prec == "fp64" else np.float32
+    tol = TOL_FP64 if prec == "fp64" else TOL_MIXED
+    m = P.create_map(cu(src), cu(tgt), deg, r, precision=prec, min_neighbors=need,
+                     growth="global")
+    off, cols, vals, st, kx = (host(x) for x in m.export())
+    assert (kx == K).all() and m.info()["max_radius_doublings"] == K
+    assert np.array_equal(st, o["status"])
+    for a, b in zip(rows_as_sets(off, cols), rows_as_sets(o["offsets"], o["cols"])):
+        assert np.array_equal(a, b)
+    ok = o["status"] == 0
+    out = host(m.apply(cu(f.astype(dt))))
+    assert normwise_err(out[None], o["values"], ok) <= tol
+    v, st2 = P.mls_transfer(cu(src), cu(tgt), cu(f.astype(dt)), deg, r, precision=prec,
+                            min_neighbors=need, growth="global")
+    assert np.array_equal(host(st2), o["status"])
+    assert normwise_err(host(v), o["values"], ok) <= tol
+    c, k = P.count_neighbors(cu(src), cu(tgt), r, degree=deg, precision=prec,
+                             min_neighbors=need, with_doublings=True, growth="global")
+    assert np.array_equal(host(c), np.diff(o["offsets"])) and (host(k) == K).all()
+    m.destroy()
+
+
 # ------------------------------------------------------------------ statuses and edge cases
 def test_strict_mode_reports_underdetermined(P):
     src, tgt = _case(2, 300, 200, 600, outside=0.5)

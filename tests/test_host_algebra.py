@@ -281,3 +281,37 @@ def test_fp32_recentred_tier_accuracy(hk):
     err, amp_rc = abs(res[0] - ref), res[1]
     assert amp_rc < amp_tc / 10
     assert err <= 2 * 3.4 * amp_rc * 2.0 ** -24 / np.sqrt(nn)
+
+
+@pytest.mark.parametrize("t", [(-0.2, -0.2, -0.2), (-0.25, -0.25, 0.2), (-0.3, -0.1, 0.5)])
+def test_fp64_refine_pass_on_extrapolating_targets(hk, t):
+    """The FP64 path's refine pass. A 3D quadratic fit at a target outside the sources
+    reproduces a quadratic field exactly in exact arithmetic, so the error of c_0 is pure
+    rounding. In the target-centred basis amp is far above AMP_FP64 = 256 and the FP64
+    normal equations lose digits (error ~ amp 2^-53, here up to 2e-10 of the field's size);
+    the re-centred basis cuts amp and the error by a factor of more than 50, to below 1e-12."""
+    rng = np.random.default_rng(5)
+    src = rng.uniform(size=(3, 12000))
+    tgt = np.array(t)
+    r = 0.48
+    d = src - tgt[:, None]
+    sel = (d ** 2).sum(0) < r * r
+    dx = np.ascontiguousarray(d[:, sel].T)
+    s = src[:, sel]
+    f = lambda x, y, z: 1.0 + 2.0 * x - y + 0.5 * z + x * x - 0.7 * x * y + 0.3 * z * z + y * z
+    b = f(*s)
+    exact = f(*tgt)
+    scale = np.abs(b).max()
+    n = len(b)
+    res = {}
+    for rc in (0, 1):
+        mom = np.zeros(_n_moments(3, 2) + 10)
+        out = np.zeros(16)
+        assert hk.hk_mls(3, 2, 1, 0, n, _p(dx), _p(b), 1.0 / r, 0.0, 1e-14, _p(mom), _p(out),
+                         rc, None) == 1
+        res[rc] = (abs(out[0] - exact) / scale, out[10])
+    (err_tc, amp_tc), (err_rc, amp_rc) = res[0], res[1]
+    assert amp_tc > 256 * 100
+    assert amp_rc < amp_tc / 50
+    assert err_rc <= 1e-12
+    assert err_rc < err_tc / 50

@@ -100,6 +100,54 @@ def test_min_neighbor_growth_is_minimal_doubling(orc):
         assert off[i + 1] - off[i] == counts[k_ref]
 
 
+@pytest.mark.parametrize("mode", ["brute", "grid"])
+def test_global_growth_is_the_smallest_shared_doubling(orc, mode):
+    """Global reading of the growth rule: brute-force counts (numpy) at r 2^k for every
+    target; K is the first k at which no target is short, and it equals the largest
+    per-target doubling (counts only grow with the radius)."""
+    src = W.uniform_points(400, 2, 31)
+    tgt = W.uniform_points(50, 2, 32, lo=-0.4, hi=1.4)
+    r, need = 0.015, 9
+    K = orc.global_doublings(src, tgt, r, min_neighbors=need, degree=1, mode=mode)
+    counts = np.array([[len(_numpy_neighbors(src, tgt[:, i:i + 1], r * 2.0 ** k)[0])
+                        for i in range(tgt.shape[1])] for k in range(K + 1)])
+    assert (counts[K] >= need).all()
+    assert K > 0 and (counts[K - 1] < need).any()
+    _, _, kexp = orc.neighbors(src, tgt, r, min_neighbors=need, degree=1, mode=mode)
+    assert K == kexp.max()
+    off, cols, kg = orc.neighbors(src, tgt, r, min_neighbors=need, degree=1, mode=mode,
+                                  growth="global")
+    assert (kg == K).all()
+    for i in range(tgt.shape[1]):
+        ref = _numpy_neighbors(src, tgt[:, i:i + 1], r * 2.0 ** K)[0]
+        assert np.array_equal(cols[off[i]:off[i + 1]], ref)
+
+
+def test_global_growth_fit_uses_the_shared_radius(orc):
+    """A global-growth fit of a quadratic field with a linear basis equals the per-target
+    fit at the shared radius (the basis scale and the weights follow that radius), and
+    differs from the per-target growth fit where a target needed fewer doublings."""
+    src = W.uniform_points(300, 2, 41)
+    tgt = W.uniform_points(40, 2, 42, lo=-0.3, hi=1.3)
+    f = (src[0] ** 2 + src[0] * src[1])[None]
+    r, need = 0.02, 8
+    K = orc.global_doublings(src, tgt, r, min_neighbors=need, degree=1)
+    g = orc.mls(src, tgt, f, 1, r, min_neighbors=need, growth="global")
+    fixed = orc.mls(src, tgt, f, 1, r * 2.0 ** K)
+    assert (g["kexp"] == K).all()
+    assert np.array_equal(g["values"], fixed["values"])
+    per = orc.mls(src, tgt, f, 1, r, min_neighbors=need)
+    lower = per["kexp"] < K
+    assert lower.any()
+    assert not np.allclose(g["values"][0, lower], per["values"][0, lower])
+
+
+def test_growth_mode_is_checked(orc):
+    src = W.uniform_points(20, 2, 1)
+    with pytest.raises(ValueError):
+        orc.neighbors(src, src, 0.1, min_neighbors=3, growth="sometimes")
+
+
 # ---------------------------------------------------------------- the fit (Eq. 1)
 def _monomials(dim, degree):
     return [e for e in itertools.product(range(degree + 1), repeat=dim) if sum(e) <= degree]
