@@ -358,6 +358,49 @@ def timed(torch, fn, stream):
 
 
 # ------------------------------------------------------------------------------------
+def roundtrip_study(torch, W, iterations=100, n=553):
+    """The vertex <-> centroid round trip (Sec. 3.2.1, Eq. 2 and Eq. 3) on a synthetic
+    stand-in for the paper's 611k-element WEST mesh: a jittered n x n grid split into
+    triangles (n = 553: 611,618 triangles, 306,916 vertices) stretched to a tokamak-like R-Z
+    box [1.8, 3.2] x [-0.8, 0.8], field sin(x)cos(y) + 2, C4 weights, r = 3 mesh spacings.
+    One iteration (two operator applies) is captured in a CUDA graph; the iterations are
+    timed with CUDA events, and the errors are read after 1, 10 and all iterations."""
+    import numpy as np
+    from paper_2510_18838_gb300 import roundtrip as RT
+    xy, tri = W.jittered_grid_mesh(n, 0.3, 611)
+    xy = np.stack([1.8 + 1.4 * xy[0], -0.8 + 1.6 * xy[1]])
+    f = RT.sincos_plus_two(xy)
+    r = 3.0 * 1.6 / n
+    out = {"mesh": f"jittered {n}x{n} grid on [1.8,3.2]x[-0.8,0.8]: {tri.shape[1]} triangles, "
+                   f"{xy.shape[1]} vertices (stand-in for the 611,359-element WEST mesh)",
+           "field": "sin(x)cos(y)+2", "weight": "c4", "radius": r, "iterations": iterations}
+    for degree in (1, 2):
+        t0 = time.perf_counter()
+        rt = RT.RoundTrip(xy, tri, degree, r, weight="c4")
+        rt.load(f)
+        torch.cuda.synchronize()
+        build_ms = (time.perf_counter() - t0) * 1e3
+        fstar = rt.fv.clone()
+        i_star = rt.integral(fstar)
+        rt.capture()
+        errs = {}
+        done = 0
+        total = 0.0
+        for upto in (1, 10, iterations):
+            _, ms = timed(torch, lambda: rt.replay(upto - done), torch.cuda.current_stream())
+            total += ms
+            done = upto
+            fv = rt.fv.cpu().numpy()
+            errs[upto] = {"accuracy_l2": float(np.linalg.norm(fv - f) / np.linalg.norm(f)),
+                          "conservation": abs(rt.integral() - i_star) / abs(i_star)}
+        out[f"degree{degree}"] = {"build_ms": build_ms, "ms_per_iteration": total / iterations,
+                                  "errors_after": errs,
+                                  "nnz": rt.v2c.info()["nnz"] + rt.c2v.info()["nnz"]}
+        rt.destroy()
+    return out
+
+
+# ------------------------------------------------------------------------------------
 def run_reference(args, rank, world):
     """The CPU oracle as it stands, on the host cores, on bounded samples (rank 0 only)."""
     if rank != 0:
@@ -470,6 +513,7 @@ def main():
                 "work": {"mls2d_pairs": tw.pairs3, "mls3d_nnz": tw.nnz4}}
     peaks, kind = measured_peaks()
     roof = tw.roofline(ttrace, peaks, kind)
+    study = roundtrip_study(torch, W) if args.workload == "serve" and rank == 0 else None
 
     if args.workload in ("transfer", "transfer_small"):
         wl = tw
@@ -550,6 +594,8 @@ def main():
             "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
             "cpu_baseline": cpu, **extra, "transfer_pass": transfer,
         }
+        if study is not None:
+            line["roundtrip_study"] = study
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
