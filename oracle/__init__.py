@@ -6,6 +6,10 @@ code with the CUDA library. The arithmetic lives in ``pcms_oracle.c`` (plain C, 
 compiled with -ffp-contract=off); this module compiles it with gcc on first use and wraps
 it with numpy.
 
+Dimensions: MLS in 2 to 5 dimensions (the paper maps fields in up to five, Sec. 1 and
+Sec. 4's 5D distribution function); the cell-list search (mode="grid") covers 2D and 3D
+and falls back to brute force above. Meshes are 2D.
+
 Definitions followed (see the C file for details):
   * radius selection and minimum-count growth -- Sec. 3.2.1, Table 1 (``r > r_c -> 0``);
   * weighted polynomial fit, Tikhonov term, value = c_0 -- Sec. 3.2.1, Eq. 1;

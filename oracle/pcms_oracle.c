@@ -66,6 +66,8 @@
  * when |R_kk| <= ORC_RANK_TOL * ||column k of the (weighted, augmented) matrix||. */
 #define ORC_RANK_TOL 1e-7
 #define ORC_MAX_GROW 60
+#define ORC_MAX_DIM 5     /* MLS in up to five dimensions (brute-force search above 3D) */
+#define ORC_MAX_TERMS 21  /* quadratic basis in 5D */
 
 int orc_version(void) { return 3; }
 
@@ -114,15 +116,19 @@ double orc_weight(int kind, double q) {
     }
 }
 
+/* Number of monomials of degree <= 2 in dim (2..5) variables: 1, dim + 1, or
+ * 1 + dim + dim (dim + 1) / 2. */
 int orc_num_terms(int dim, int degree) {
+    if (dim < 2 || dim > ORC_MAX_DIM) return -1;
     if (degree == 0) return 1;
     if (degree == 1) return dim + 1;
-    if (degree == 2) return dim == 2 ? 6 : 10;
+    if (degree == 2) return 1 + dim + dim * (dim + 1) / 2;
     return -1;
 }
 
-/* Graded-lex monomials of u (degree <= 2):
- * 2D [1, x, y, x^2, xy, y^2]; 3D [1, x, y, z, x^2, xy, xz, y^2, yz, z^2]. */
+/* Graded-lex monomials of u (degree <= 2): 1, then u_d, then u_d u_e (d <= e).
+ * 2D [1, x, y, x^2, xy, y^2]; 3D [1, x, y, z, x^2, xy, xz, y^2, yz, z^2]; the same
+ * rule in 4D and 5D. */
 static void basis(int dim, int degree, const double* u, double* a) {
     int k = 0;
     a[k++] = 1.0;
@@ -136,12 +142,13 @@ static void basis(int dim, int degree, const double* u, double* a) {
 /* ------------------------------------------------------------------------------------ */
 /* Radius selection                                                                      */
 /* ------------------------------------------------------------------------------------ */
+/* ((dx*dx + dy*dy) + dz*dz) + ... summed left to right over the dimensions */
 static double dist2(int dim, const double* src, int64_t ns, int64_t j, const double* t) {
     double dx = src[j] - t[0];
     double dy = src[ns + j] - t[1];
     double d2 = dx * dx + dy * dy;
-    if (dim == 3) {
-        double dz = src[2 * ns + j] - t[2];
+    for (int d = 2; d < dim; d++) {
+        double dz = src[d * ns + j] - t[d];
         d2 = d2 + dz * dz;
     }
     return d2;
@@ -268,7 +275,7 @@ static int64_t target_neighbors(int dim, const double* src, int64_t ns, const do
 
 static void load_target(int dim, const double* tgt, int64_t nt, int64_t i, double* t) {
     for (int d = 0; d < dim; d++) t[d] = tgt[d * nt + i];
-    for (int d = dim; d < 3; d++) t[d] = 0.0;
+    for (int d = dim; d < ORC_MAX_DIM; d++) t[d] = 0.0;
 }
 
 /* Per-target radius growth (Sec. 3.2.1). need <= 0: no growth. Returns count at the
@@ -292,6 +299,7 @@ static int64_t grow_radius(int dim, const double* src, int64_t ns, const double*
 int64_t orc_count_neighbors(int dim, const double* src, int64_t ns, const double* tgt,
                             int64_t nt, double radius, int wkind, int need, int mode,
                             int32_t* counts, int32_t* kexp) {
+    if (dim > 3) mode = 0; /* the grid is 2D/3D: brute force above */
     grid_t g;
     const grid_t* gp = NULL;
     if (mode == 1) {
@@ -301,7 +309,7 @@ int64_t orc_count_neighbors(int dim, const double* src, int64_t ns, const double
     int64_t total = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : total)
     for (int64_t i = 0; i < nt; i++) {
-        double t[3];
+        double t[ORC_MAX_DIM];
         load_target(dim, tgt, nt, i, t);
         int32_t k = 0;
         int64_t c = grow_radius(dim, src, ns, t, radius, wkind, need, mode, gp, &k);
@@ -318,6 +326,7 @@ int64_t orc_count_neighbors(int dim, const double* src, int64_t ns, const double
  * at most ORC_MAX_GROW times. Returns the number of doublings; 0 when need <= 0. */
 int orc_global_doublings(int dim, const double* src, int64_t ns, const double* tgt,
                          int64_t nt, double radius, int wkind, int need, int mode) {
+    if (dim > 3) mode = 0; /* the grid is 2D/3D: brute force above */
     if (need <= 0 || nt <= 0) return 0;
     grid_t g;
     const grid_t* gp = NULL;
@@ -331,7 +340,7 @@ int orc_global_doublings(int dim, const double* src, int64_t ns, const double* t
         int64_t short_of = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : short_of)
         for (int64_t i = 0; i < nt; i++) {
-            double t[3];
+            double t[ORC_MAX_DIM];
             load_target(dim, tgt, nt, i, t);
             int64_t c = target_neighbors(dim, src, ns, t, r, wkind, mode, gp, NULL);
             if (c < need && c < ns) short_of++;
@@ -347,6 +356,7 @@ int orc_global_doublings(int dim, const double* src, int64_t ns, const double* t
 void orc_fill_neighbors(int dim, const double* src, int64_t ns, const double* tgt,
                         int64_t nt, double radius, int wkind, int mode,
                         const int32_t* kexp, const int64_t* offsets, int32_t* cols) {
+    if (dim > 3) mode = 0; /* the grid is 2D/3D: brute force above */
     grid_t g;
     const grid_t* gp = NULL;
     if (mode == 1) {
@@ -355,7 +365,7 @@ void orc_fill_neighbors(int dim, const double* src, int64_t ns, const double* tg
     }
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < nt; i++) {
-        double t[3];
+        double t[ORC_MAX_DIM];
         load_target(dim, tgt, nt, i, t);
         target_neighbors(dim, src, ns, t, ldexp(radius, kexp[i]), wkind, mode, gp,
                          cols + offsets[i]);
@@ -414,7 +424,7 @@ static int solve_target(int dim, int degree, int wkind, double lambda, const dou
     /* B = [diag(sqrt w) A ; sqrt(lambda) I], column-major rows x m */
     for (int64_t i = 0; i < n; i++) {
         int64_t j = nbr[i];
-        double u[3] = {0, 0, 0}, a[10];
+        double u[ORC_MAX_DIM] = {0, 0, 0, 0, 0}, a[ORC_MAX_TERMS];
         for (int d = 0; d < dim; d++) u[d] = (src[d * ns + j] - t[d]) / r;
         double d2 = dist2(dim, src, ns, j, t);
         double wt = orc_weight(wkind, sqrt(d2) / r);
@@ -512,6 +522,7 @@ void orc_mls(int dim, int degree, int wkind, double lambda, const double* src, i
              const double* tgt, int64_t nt, const double* fields, int nf, double radius,
              int need, int mode, double* values, int8_t* status, int32_t* kexp,
              const int64_t* offsets, int32_t* cols, double* shape) {
+    if (dim > 3) mode = 0; /* the grid is 2D/3D: brute force above */
     grid_t g;
     const grid_t* gp = NULL;
     if (mode == 1) {
@@ -525,7 +536,7 @@ void orc_mls(int dim, int degree, int wkind, double lambda, const double* src, i
         w.cap_nbr = 0;
 #pragma omp for schedule(dynamic, 8)
         for (int64_t i = 0; i < nt; i++) {
-            double t[3];
+            double t[ORC_MAX_DIM];
             load_target(dim, tgt, nt, i, t);
             int32_t k = 0;
             int64_t cnt = grow_radius(dim, src, ns, t, radius, wkind, need, mode, gp, &k);

@@ -132,8 +132,86 @@ struct Exp3 {
     int e[3];
 };
 
+__host__ __device__ constexpr int binom(int n, int k) {
+    int r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+// monomials of degree <= deg in dim variables: C(dim + deg, deg)
 __host__ __device__ constexpr int mono_count(int dim, int deg) {
-    return dim == 2 ? (deg + 1) * (deg + 2) / 2 : (deg + 1) * (deg + 2) * (deg + 3) / 6;
+    return deg < 0 ? 0 : binom(dim + deg, deg);
+}
+
+// Four and five variables (the FP64 path above 3D): the same graded-lex order, from a table
+// of exponent vectors. Within a degree, vectors follow reverse-lexicographic order (e0
+// descending, then e1, ...): from e, take the last i < dim-1 with e[i] > 0, lower e[i] by
+// one, put the sum of e[i+1..] plus one into e[i+1] and clear the rest.
+constexpr int ND_MAX_DIM = 5;
+constexpr int ND_MAX_MOMENT_DEG = 4;   // moments of a quadratic basis
+struct Exp5 {
+    int e[ND_MAX_DIM];
+};
+template <int D>
+struct MonoTab {
+    static constexpr int N = binom(D + ND_MAX_MOMENT_DEG, ND_MAX_MOMENT_DEG);
+    Exp5 x[N];
+};
+template <int D>
+__host__ __device__ constexpr MonoTab<D> make_mono_tab() {
+    MonoTab<D> t{};
+    int idx = 0;
+    for (int g = 0; g <= ND_MAX_MOMENT_DEG; ++g) {
+        Exp5 e{};
+        e.e[0] = g;
+        for (;;) {
+            t.x[idx++] = e;
+            int i = -1;
+            for (int j = 0; j < D - 1; ++j)
+                if (e.e[j] > 0) i = j;
+            if (i < 0) break;
+            int rest = 0;
+            for (int j = i + 1; j < D; ++j) rest += e.e[j];
+            e.e[i] -= 1;
+            e.e[i + 1] = rest + 1;
+            for (int j = i + 2; j < D; ++j) e.e[j] = 0;
+        }
+    }
+    return t;
+}
+template <int D>
+__host__ __device__ constexpr Exp5 mono_exp_nd(int p) {
+    return make_mono_tab<D>().x[p];
+}
+template <int D>
+__host__ __device__ constexpr int mono_index_nd(const Exp5& e) {
+    const MonoTab<D> t = make_mono_tab<D>();
+    for (int p = 0; p < MonoTab<D>::N; ++p) {
+        bool eq = true;
+        for (int d = 0; d < D; ++d) eq = eq && t.x[p].e[d] == e.e[d];
+        if (eq) return p;
+    }
+    return -1;
+}
+template <int D>
+__host__ __device__ constexpr int mono_var_nd(int p) {
+    const Exp5 x = mono_exp_nd<D>(p);
+    for (int d = 0; d < D; ++d)
+        if (x.e[d] > 0) return d;
+    return 0;
+}
+template <int D>
+__host__ __device__ constexpr int mono_parent_nd(int p) {
+    Exp5 x = mono_exp_nd<D>(p);
+    x.e[mono_var_nd<D>(p)] -= 1;
+    return mono_index_nd<D>(x);
+}
+template <int D>
+__host__ __device__ constexpr int mono_prod_nd(int k, int l) {
+    const Exp5 a = mono_exp_nd<D>(k), b = mono_exp_nd<D>(l);
+    Exp5 c{};
+    for (int d = 0; d < D; ++d) c.e[d] = a.e[d] + b.e[d];
+    return mono_index_nd<D>(c);
 }
 
 __host__ __device__ constexpr Exp3 mono_exp(int dim, int p) {
@@ -176,6 +254,8 @@ __host__ __device__ constexpr int mono_parent(int dim, int p) {
 
 // index of the product of monomials k and l
 __host__ __device__ constexpr int mono_prod(int dim, int k, int l) {
+    if (dim == 4) return mono_prod_nd<4>(k, l);
+    if (dim == 5) return mono_prod_nd<5>(k, l);
     Exp3 a = mono_exp(dim, k), b = mono_exp(dim, l);
     return mono_index(dim, a.e[0] + b.e[0], a.e[1] + b.e[1], a.e[2] + b.e[2]);
 }

@@ -52,11 +52,11 @@ def _numpy_neighbors(src, tgt, r):
     return out
 
 
-@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("dim", [2, 3, 4, 5])
 def test_neighbors_brute_force_tiny(orc, dim):
     src = W.uniform_points(300, dim, 7)
     tgt = W.uniform_points(40, dim, 8)
-    r = 0.2
+    r = {2: 0.2, 3: 0.2, 4: 0.35, 5: 0.45}[dim]
     off, cols, kexp = orc.neighbors(src, tgt, r)
     ref = _numpy_neighbors(src, tgt, r)
     assert (kexp == 0).all()
@@ -160,13 +160,14 @@ def _poly(pts, expo, centre):
     return v
 
 
-@pytest.mark.parametrize("dim,degree", [(2, 0), (2, 1), (2, 2), (3, 1), (3, 2)])
+@pytest.mark.parametrize("dim,degree", [(2, 0), (2, 1), (2, 2), (3, 1), (3, 2), (4, 1), (4, 2),
+                                        (5, 1), (5, 2)])
 def test_polynomial_reproduction(orc, dim, degree):
     """Every polynomial of degree <= k is reproduced exactly (lambda = 0)."""
-    src = W.uniform_points(2500 if dim == 2 else 6000, dim, 31)
-    tgt = W.uniform_points(200, dim, 32, lo=0.1, hi=0.9)
-    r = 0.12 if dim == 2 else 0.25
-    centre = [0.3, 0.6, 0.45][:dim]
+    src = W.uniform_points({2: 2500, 3: 6000, 4: 6000, 5: 6000}[dim], dim, 31)
+    tgt = W.uniform_points(200 if dim <= 3 else 60, dim, 32, lo=0.1, hi=0.9)
+    r = {2: 0.12, 3: 0.25, 4: 0.4, 5: 0.5}[dim]
+    centre = [0.3, 0.6, 0.45, 0.55, 0.4][:dim]
     fields = np.stack([_poly(src, e, centre) for e in _monomials(dim, degree)])
     o = orc.mls(src, tgt, fields, degree, r)
     assert (o["status"] == 0).all()
@@ -182,12 +183,12 @@ def test_linear_basis_does_not_reproduce_quadratics(orc):
     assert np.abs(o["values"][0] - (tgt[0] - 0.5) ** 2).max() > 1e-4
 
 
-@pytest.mark.parametrize("dim,degree", [(2, 1), (2, 2), (3, 2)])
+@pytest.mark.parametrize("dim,degree", [(2, 1), (2, 2), (3, 2), (5, 2)])
 def test_partition_of_unity_and_moments(orc, dim, degree):
     """Shape functions satisfy sum_j N_j p(s_j - t) = e_1 for the whole basis."""
-    src = W.uniform_points(2000 if dim == 2 else 5000, dim, 41)
-    tgt = W.uniform_points(80, dim, 42)
-    r = 0.12 if dim == 2 else 0.25
+    src = W.uniform_points({2: 2000, 3: 5000, 5: 5000}[dim], dim, 41)
+    tgt = W.uniform_points(80 if dim <= 3 else 30, dim, 42)
+    r = {2: 0.12, 3: 0.25, 5: 0.5}[dim]
     o = orc.mls(src, tgt, np.zeros((1, src.shape[1])), degree, r, shape=True, min_neighbors=15)
     off, cols, shp = o["offsets"], o["cols"], o["shape"]
     for i in range(tgt.shape[1]):
@@ -225,14 +226,14 @@ def test_degree0_is_shepard(orc):
         assert o["values"][0, i] == pytest.approx(np.sum(w * f[nb[i]]) / np.sum(w), rel=1e-13)
 
 
-@pytest.mark.parametrize("dim,degree", [(2, 1), (2, 2), (3, 2)])
+@pytest.mark.parametrize("dim,degree", [(2, 1), (2, 2), (3, 2), (4, 2), (5, 1), (5, 2)])
 def test_const_weight_equals_plain_lstsq_uncentred(orc, dim, degree):
     """Constant weight -> ordinary least squares; evaluated with the raw, uncentred
     monomials (numpy lstsq), which also pins the centring/scaling of the basis."""
-    src = W.uniform_points(1500 if dim == 2 else 4000, dim, 61)
-    tgt = W.uniform_points(50, dim, 62, lo=0.2, hi=0.8)
+    src = W.uniform_points({2: 1500, 3: 4000, 4: 4000, 5: 4000}[dim], dim, 61)
+    tgt = W.uniform_points(50 if dim <= 3 else 20, dim, 62, lo=0.2, hi=0.8)
     f = np.exp(src[0]) * np.sin(2 * src[1])
-    r = 0.1 if dim == 2 else 0.2
+    r = {2: 0.1, 3: 0.2, 4: 0.35, 5: 0.45}[dim]
     o = orc.mls(src, tgt, f, degree, r, weight="const")
     nb = _numpy_neighbors(src, tgt, r)
     mons = _monomials(dim, degree)
