@@ -67,7 +67,10 @@ pcms_status check_mls_args(const char* fn, int dim, const double* src, int64_t n
                            const double* tgt, int64_t nt, int degree, double radius,
                            const pcms_map_opts& o) {
     std::string f(fn);
-    REQUIRE(dim == 2 || dim == 3, f + ": dim must be 2 or 3");
+    REQUIRE(dim >= 2 && dim <= 5, f + ": dim must be 2, 3, 4 or 5");
+    REQUIRE(dim <= 3 || o.precision == PCMS_FP64,
+            f + ": above 3D only the FP64 path exists (precision must be PCMS_FP64)");
+    REQUIRE(dim <= 3 || !o.domain_known, f + ": domain_known covers at most 3 dimensions");
     REQUIRE(degree >= 0 && degree <= 2, f + ": basis_degree must be 0, 1 or 2");
     REQUIRE(std::isfinite(radius) && radius > 0.0, f + ": radius must be finite and > 0");
     REQUIRE(ns >= 0 && nt >= 0, f + ": negative point count");

@@ -385,8 +385,8 @@ MlsParams make_mls_params(int dim, int degree, double radius, const pcms_map_opt
 int64_t estimate_mls_bytes(const MlsParams& P, int64_t ns, int64_t nt, int nf, bool keep_map) {
     const int d = P.dim;
     const bool mixed = P.prec == PCMS_MIXED;
-    const double ball = d == 2 ? M_PI * P.radius * P.radius
-                               : 4.0 / 3.0 * M_PI * P.radius * P.radius * P.radius;
+    // volume of the d-ball of radius r: pi^(d/2) r^d / Gamma(d/2 + 1)
+    const double ball = std::pow(M_PI, 0.5 * d) * std::pow(P.radius, d) / std::tgamma(0.5 * d + 1.0);
     double k = std::max((double)P.m, std::max((double)P.need, (double)ns * ball));
     k = std::min(k, (double)std::max<int64_t>(ns, 1));
     const double elem = mixed ? 4.0 : 8.0;
@@ -415,6 +415,7 @@ int64_t MapImpl::device_bytes() const {
 // create map
 // ------------------------------------------------------------------------------------
 void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms_map_opts& o) {
+    if (M.P.dim >= 4) return mls_nd_create_map(M, src, tgt);
     cudaStream_t s = M.stream;
     M.P = settle_growth(M.P, src, M.ns, tgt, M.nt, o, s);
     const MlsParams& P = M.P;
@@ -594,6 +595,7 @@ __global__ void k_counts_to_caller(int64_t nt, const int32_t* __restrict__ perm_
 void mls_count(const MlsParams& P0, const double* src, int64_t ns, const double* tgt, int64_t nt,
                const pcms_map_opts& o, int32_t* counts, int32_t* kexp, int64_t* total,
                cudaStream_t s) {
+    if (P0.dim >= 4) return mls_nd_count(P0, src, ns, tgt, nt, counts, kexp, total, s);
     const MlsParams P = settle_growth(P0, src, ns, tgt, nt, o, s);
     const int dim = P.dim;
     const bool mixed = P.prec == PCMS_MIXED;
@@ -630,6 +632,9 @@ void mls_count(const MlsParams& P0, const double* src, int64_t ns, const double*
 void mls_transfer(const MlsParams& P0, const double* src, int64_t ns, const double* tgt,
                   int64_t nt, const pcms_map_opts& o, const void* fields, int nf, void* out,
                   int8_t* status, cudaStream_t s, int64_t* n_under) {
+    if (P0.dim >= 4)
+        return mls_nd_transfer(P0, src, ns, tgt, nt, (const double*)fields, nf, (double*)out,
+                               status, s, n_under);
     const MlsParams P = settle_growth(P0, src, ns, tgt, nt, o, s);
     const int dim = P.dim, deg = P.degree;
     const bool mixed = P.prec == PCMS_MIXED;

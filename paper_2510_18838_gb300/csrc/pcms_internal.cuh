@@ -119,6 +119,11 @@ void launch_bbox(int dim, const double* pts, int64_t n, double* dev_box, long lo
 void sort_points(const Grid& g, const double* pts, int64_t n, bool with_start, bool with_hl,
                  SortedPoints& out, cudaStream_t s, bool with_cell = false);
 
+// Stable LSD radix sort (8-bit digits) of (key, value) pairs with keys < nkeys; k1/v1 are
+// scratch of n entries. Returns the buffer (v0 or v1) holding the values in key order.
+uint32_t* radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t n,
+                           int64_t nkeys, cudaStream_t s);
+
 // exclusive scan of int32 counts into out[0..n] (out[n] = total); T = int32_t or int64_t
 template <typename T>
 void exclusive_scan(const int32_t* in, T* out, int64_t n, cudaStream_t s);
@@ -325,6 +330,14 @@ void mls_count(const MlsParams& P, const double* src, int64_t ns, const double* 
 void mls_transfer(const MlsParams& P, const double* src, int64_t ns, const double* tgt,
                   int64_t nt, const pcms_map_opts& o, const void* fields, int nf, void* out,
                   int8_t* status, cudaStream_t s, int64_t* n_under);
+
+// four and five dimensions, FP64 (mls_nd.cu); the MLS entry points above dispatch here
+void mls_nd_create_map(MapImpl& M, const double* src, const double* tgt);
+void mls_nd_transfer(const MlsParams& P, const double* src, int64_t ns, const double* tgt,
+                     int64_t nt, const double* fields, int nf, double* out, int8_t* status,
+                     cudaStream_t s, int64_t* n_under);
+void mls_nd_count(const MlsParams& P, const double* src, int64_t ns, const double* tgt, int64_t nt,
+                  int32_t* counts, int32_t* kexp, int64_t* total, cudaStream_t s);
 
 // the thread-local message returned by pcms_last_error (capi.cu)
 void set_last_error_message(const std::string& msg);

@@ -423,6 +423,32 @@ __global__ void k_gather_sorted(int dim, Grid g, const double* __restrict__ pts,
     }
 }
 
+uint32_t* radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t n,
+                           int64_t nkeys, cudaStream_t s) {
+    if (n <= 0) return v0;
+    int bits = 1;
+    while (bits < 32 && ((int64_t)1 << bits) < nkeys) bits++;
+    const int passes = (bits + 7) / 8;
+    const int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+    DBuf hist(sizeof(int32_t) * (256 * ntiles + 1), s);
+    for (int p = 0; p < passes; p++) {
+        {
+            PCMS_TRACE("grid_radix_hist", s);
+            k_rs_hist<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(k0, n, 8 * p, ntiles, hist.as<int32_t>());
+        }
+        exclusive_scan<int32_t>(hist.as<int32_t>(), hist.as<int32_t>(), 256 * ntiles, s);
+        {
+            PCMS_TRACE("grid_radix_scatter", s);
+            k_rs_scatter<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(k0, v0, n, 8 * p, ntiles,
+                                                                 hist.as<int32_t>(), k1, v1);
+        }
+        PCMS_LAUNCH_CHECK("radix");
+        std::swap(k0, k1);
+        std::swap(v0, v1);
+    }
+    return v0;
+}
+
 void sort_points(const Grid& g, const double* pts, int64_t n, bool with_start, bool with_hl,
                  SortedPoints& out, cudaStream_t s, bool with_cell) {
     out.dim = g.dim;
@@ -464,26 +490,7 @@ void sort_points(const Grid& g, const double* pts, int64_t n, bool with_start, b
     PCMS_LAUNCH_CHECK("cell_keys");
     exclusive_scan<int32_t>(count.as<int32_t>(), start, g.ncell, s);
     if (n > 0) {
-        int bits = 1;
-        while (bits < 32 && ((int64_t)1 << bits) < g.ncell) bits++;
-        const int passes = (bits + 7) / 8;
-        const int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
-        DBuf hist(sizeof(int32_t) * (256 * ntiles + 1), s);
-        for (int p = 0; p < passes; p++) {
-            {
-                PCMS_TRACE("grid_radix_hist", s);
-                k_rs_hist<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(k0, n, 8 * p, ntiles, hist.as<int32_t>());
-            }
-            exclusive_scan<int32_t>(hist.as<int32_t>(), hist.as<int32_t>(), 256 * ntiles, s);
-            {
-                PCMS_TRACE("grid_radix_scatter", s);
-                k_rs_scatter<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(k0, v0, n, 8 * p, ntiles,
-                                                                     hist.as<int32_t>(), k1, v1);
-            }
-            PCMS_LAUNCH_CHECK("radix");
-            std::swap(k0, k1);
-            std::swap(v0, v1);
-        }
+        v0 = radix_sort_pairs(k0, v0, k1, v1, n, g.ncell, s);
         PCMS_TRACE("grid_gather_sorted", s);
         k_gather_sorted<<<blocks, 256, 0, s>>>(dim, g, pts, n, v0, out.perm.as<int32_t>(),
                                                out.inv.as<int32_t>(), out.x64.as<double>(),

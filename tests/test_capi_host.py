@@ -39,7 +39,7 @@ def test_version_and_defaults(lib):
 
 
 @pytest.mark.parametrize("dim,deg,radius,ns,nt", [
-    (4, 1, 0.1, 10, 10), (1, 1, 0.1, 10, 10), (2, 3, 0.1, 10, 10), (2, -1, 0.1, 10, 10),
+    (6, 1, 0.1, 10, 10), (1, 1, 0.1, 10, 10), (2, 3, 0.1, 10, 10), (2, -1, 0.1, 10, 10),
     (2, 1, 0.0, 10, 10), (2, 1, -1.0, 10, 10), (2, 1, float("nan"), 10, 10),
     (2, 1, float("inf"), 10, 10), (2, 1, 0.1, -1, 10), (2, 1, 0.1, 10, -5),
     (2, 1, 0.1, 1 << 31, 10),
@@ -52,6 +52,25 @@ def test_create_map_rejects_bad_arguments(lib, dim, deg, radius, ns, nt):
     assert st == pcms.INVALID_ARG
     assert h.value is None
     assert b"pcms_create_map" in lib.pcms_last_error()
+
+
+def test_dimensions_above_three_are_fp64_only(lib):
+    from paper_2510_18838_gb300 import pcms
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(0x1000)
+    o = pcms.MapOpts()
+    lib.pcms_map_opts_default(ctypes.byref(o))
+    for dim in (4, 5):
+        bad = pcms.MapOpts.from_buffer_copy(o)
+        bad.precision = pcms.MIXED
+        assert lib.pcms_create_map(dim, fake, 5, fake, 5, 1, 0.1, ctypes.byref(bad), None,
+                                   ctypes.byref(h)) == pcms.INVALID_ARG
+        bad = pcms.MapOpts.from_buffer_copy(o)
+        bad.domain_known = 1
+        assert lib.pcms_create_map(dim, fake, 5, fake, 5, 1, 0.1, ctypes.byref(bad), None,
+                                   ctypes.byref(h)) == pcms.INVALID_ARG
+    assert lib.pcms_create_map(6, fake, 5, fake, 5, 1, 0.1, None, None,
+                               ctypes.byref(h)) == pcms.INVALID_ARG
 
 
 def test_null_pointers_and_bad_opts_rejected(lib):

@@ -338,3 +338,70 @@ def test_full_size_mls3d_sixteen_fields_sampled(P):
     for k, i in enumerate(idx):
         assert np.array_equal(np.sort(cols[off[i]:off[i + 1]]), o_cols[o_off[k]:o_off[k + 1]])
     m.destroy()
+
+
+# ------------------------------------------------------------------ four and five dimensions
+def _case_nd(dim, ns, nt, seed):
+    src = W.uniform_points(ns, dim, seed)
+    tgt = W.uniform_points(nt, dim, seed + 1, lo=0.05, hi=0.95)
+    return src, tgt
+
+
+@pytest.mark.parametrize("dim,deg,min_nb", [(4, 1, 0), (4, 2, 0), (5, 1, 0), (5, 2, 0),
+                                            (5, 2, 40), (4, 0, 25)])
+def test_nd_map_matches_oracle(P, dim, deg, min_nb):
+    """4D/5D (FP64): neighbour lists and doublings bit-exact, statuses identical, operator
+    applied to three fields within 1e-12 of the oracle's fit."""
+    ns, nt, r = (6000, 700, 0.32) if dim == 4 else (8000, 500, 0.42)
+    if min_nb:
+        r *= 0.5
+    src, tgt = _case_nd(dim, ns, nt, 900 + 10 * dim + deg)
+    f = np.stack([np.cos(3 * src[0]) + src[1] * src[dim - 1],
+                  src[2] ** 2 - src[3],
+                  np.exp(-src[dim - 1]) * src[0]])
+    o = oracle.mls(src, tgt, f, deg, r, min_neighbors=min_nb, shape=True)
+    m = P.create_map(cu(src), cu(tgt), deg, r, min_neighbors=min_nb)
+    off, cols, vals, st, kx = (host(x) for x in m.export())
+    assert np.array_equal(kx, o["kexp"])
+    assert np.array_equal(st, o["status"])
+    for a, b in zip(rows_as_sets(off, cols), rows_as_sets(o["offsets"], o["cols"])):
+        assert np.array_equal(a, b)
+    ok = o["status"] == 0
+    assert ok.mean() > 0.9
+    out = host(m.apply(cu(f)))
+    assert normwise_err(out, o["values"], ok) <= TOL_FP64
+    if min_nb:
+        assert kx.max() >= 1
+    m.destroy()
+
+
+@pytest.mark.parametrize("dim,weight,lam", [(4, "wendland_c2", 0.0), (5, "c4", 0.0),
+                                            (5, "gaussian", 1e-3), (4, "imq", 0.0)])
+def test_nd_one_shot_transfer(P, dim, weight, lam):
+    ns, nt, r = (5000, 600, 0.35) if dim == 4 else (7000, 400, 0.45)
+    src, tgt = _case_nd(dim, ns, nt, 950 + dim)
+    f = np.sin(2 * src[0]) * np.cos(src[1]) + src[dim - 1]
+    out, st = P.mls_transfer(cu(src), cu(tgt), cu(f), 2, r, weight=weight, lam=lam)
+    o = oracle.mls(src, tgt, f, 2, r, weight=weight, lam=lam)
+    assert np.array_equal(host(st), o["status"])
+    assert normwise_err(host(out), o["values"], o["status"] == 0) <= TOL_FP64
+    c = P.count_neighbors(cu(src), cu(tgt), r, degree=2, weight=weight)
+    off, _, _ = oracle.neighbors(src, tgt, r, weight=weight, degree=2)
+    assert np.array_equal(host(c), np.diff(off))
+
+
+def test_nd_global_growth_and_strict_mode(P):
+    src, tgt = _case_nd(5, 4000, 300, 977)
+    tgt = np.ascontiguousarray(tgt * 1.3 - 0.15)   # some targets outside the sources' box
+    f = src[0] + 2 * src[4]
+    o = oracle.mls(src, tgt, f, 1, 0.15, min_neighbors=12, growth="global")
+    K = int(o["kexp"][0])
+    m = P.create_map(cu(src), cu(tgt), 1, 0.15, min_neighbors=12, growth="global")
+    *_, st, kx = (host(x) for x in m.export())
+    assert (kx == K).all() and K >= 1
+    assert np.array_equal(st, o["status"])
+    assert normwise_err(host(m.apply(cu(f))), o["values"], o["status"] == 0) <= TOL_FP64
+    m.destroy()
+    m2 = P.create_map(cu(src), cu(tgt), 2, 0.15)     # user radius: underdetermined targets
+    assert m2.status_code == P.UNDERDETERMINED
+    m2.destroy()
