@@ -122,7 +122,9 @@ void pcms_map_opts_default(pcms_map_opts* opts);
  *   exactly as ((dx*dx + dy*dy) + dz*dz) < r*r, plus phi > 0), fits the weighted polynomial
  *   of degree `basis_degree` (0, 1 or 2; graded-lex monomials of (s - t)/r) and stores the
  *   shape functions N_ij so that f(t_i) = sum_j N_ij f(s_j).
- *   dim: 2 or 3. src_pts: device float64 [dim][n_src]; tgt_pts: device float64 [dim][n_tgt].
+ *   dim: 2, 3, 4 or 5 (fields in up to five dimensions; above 3D only PCMS_FP64 and no
+ *   domain_known; the squared distance is summed left to right over all dimensions).
+ *   src_pts: device float64 [dim][n_src]; tgt_pts: device float64 [dim][n_tgt].
  *   radius > 0. opts may be NULL (defaults). The map copies what it needs; inputs may be
  *   freed after the call returns and the stream has run.
  *   Syncs `stream` once to size the operator (and once more for the bounding box unless

@@ -552,17 +552,19 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemb
             else inv_r = A.lv.inv_r[k];
             // Candidate rows: cells (y, z) whose slab comes within r of the target, each
             // trimmed in x to the ball's chord. Computed in cell units in FP32 with a margin
-            // m far above the FP32 error, so the rows and chords only ever over-cover.
+            // m far above the FP32 error, so the rows and chords only ever over-cover. The
+            // floors are 32-bit conversions rounding down (|argument| < 2^31 since the radius
+            // is capped at 2^30 cells): a 64-bit conversion would run on the FP64 pipe.
             const float R0 = A.lv.rcell[k];
             const float mg = 1e-3f + R0 * 1e-6f;
             const float RR = R0 + mg;
             long long z0 = 0, z1 = 0;
             if (DIM == 3) {
-                z0 = max((long long)floorf(fr[2] - RR), -ct[2]);
-                z1 = min((long long)floorf(fr[2] + RR), (long long)g.n[2] - 1 - ct[2]);
+                z0 = max((long long)__float2int_rd(fr[2] - RR), -ct[2]);
+                z1 = min((long long)__float2int_rd(fr[2] + RR), (long long)g.n[2] - 1 - ct[2]);
             }
-            const long long y0 = max((long long)floorf(fr[1] - RR), -ct[1]);
-            const long long y1 = min((long long)floorf(fr[1] + RR), (long long)g.n[1] - 1 - ct[1]);
+            const long long y0 = max((long long)__float2int_rd(fr[1] - RR), -ct[1]);
+            const long long y1 = min((long long)__float2int_rd(fr[1] + RR), (long long)g.n[1] - 1 - ct[1]);
 #pragma unroll
             for (int i = 0; i < NA; i++) acc[i] = T(0);
 #pragma unroll
@@ -602,9 +604,9 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemb
                     const float rem = remz - ey * ey;
                     if (remz > 0.f && rem > 0.f) {
                         const float hx = sqrtf(rem) + mg;
-                        const long long x0 = max((long long)floorf(fr[0] - hx) + ct[0], 0LL);
+                        const long long x0 = max((long long)__float2int_rd(fr[0] - hx) + ct[0], 0LL);
                         const long long x1 =
-                            min((long long)floorf(fr[0] + hx) + ct[0], (long long)g.n[0] - 1);
+                            min((long long)__float2int_rd(fr[0] + hx) + ct[0], (long long)g.n[0] - 1);
                         if (x0 <= x1) {
                             const int64_t rowbase =
                                 ((ct[2] + dz) * g.n[1] + (ct[1] + dy)) * (int64_t)g.n[0];
@@ -863,7 +865,8 @@ __host__ __device__ __forceinline__ bool solve_moments(const double* mom, double
         constexpr int k = decltype(K)::value;
         sfor<k + 1>([&](auto Lx) {
             constexpr int l = decltype(Lx)::value;
-            L[k * (k + 1) / 2 + l] = mom[mono_prod(DIM, k, l)] + (k == l ? lambda : 0.0);
+            constexpr int kl = mono_prod(DIM, k, l);   // evaluated at compile time
+            L[k * (k + 1) / 2 + l] = mom[kl] + (k == l ? lambda : 0.0);
         });
     });
     double invd[M], diag[M];
@@ -1125,8 +1128,28 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
         if constexpr (MIXED) inv_r = S.lv.inv_rf[kx];
         else inv_r = S.lv.inv_r[kx];
         const int64_t a = S.offsets[t], b = a + S.counts[t];
-        for (int64_t i = a + gl; i < b; i += G) {
-            const int j = S.cols[i];
+        // Software pipeline over the row (mixed path): the column two pairs ahead and the
+        // coordinates of the next pair are loaded before the current pair is evaluated, so
+        // the gathers overlap the arithmetic instead of stalling on it.
+        int64_t i = a + gl;
+        int jc = i < b ? S.cols[i] : 0;
+        int jn = i + G < b ? S.cols[i + G] : 0;
+        float4 hc0 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 hc1 = make_float2(0.f, 0.f);
+        if (MIXED && i < b) {
+            hc0 = S.hl0[jc];
+            if (DIM == 3) hc1 = S.hl1[jc];
+        }
+        for (; i < b; i += G) {
+            const int j = jc;
+            const float4 cur0 = hc0;
+            const float2 cur1 = hc1;
+            if (MIXED && i + G < b) {
+                hc0 = S.hl0[jn];
+                if (DIM == 3) hc1 = S.hl1[jn];
+            }
+            jc = jn;
+            jn = i + 2 * G < b ? S.cols[i + 2 * G] : 0;
             if (MIXED && flag == 2) {
                 // row of an FP64-assembled target: the exact FP64 offsets, weight and basis
                 double e[3] = {0.0, 0.0, 0.0};
@@ -1152,12 +1175,12 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
             }
             T dx[3] = {T(0), T(0), T(0)};
             if (MIXED) {
-                float4 h0 = S.hl0[j];
+                const float4 h0 = cur0;
                 if (DIM == 2) {
                     dx[0] = (h0.x - thi[0]) + (h0.z - tlo[0]);
                     dx[1] = (h0.y - thi[1]) + (h0.w - tlo[1]);
                 } else {
-                    float2 h1 = S.hl1[j];
+                    const float2 h1 = cur1;
                     dx[0] = (h0.x - thi[0]) + (h0.w - tlo[0]);
                     dx[1] = (h0.y - thi[1]) + (h1.x - tlo[1]);
                     dx[2] = (h0.z - thi[2]) + (h1.y - tlo[2]);

@@ -6,9 +6,10 @@
 // doubling; weighted normal equations in the target-centred basis scaled by 1/r; guarded
 // LDL^T solve; operator rows N_j = w_j a(u_j)^T y; apply by the shared sparse kernels.
 // What differs is the search and the split of the work:
-//   * a uniform grid in D dimensions with cell edge h >= r (1 + 2^-20) (doubled until the
-//     grid has at most max(2^16, 8 n_src) cells); the box of (2R+1)^D cells around a
-//     target, R = floor(r / h) + 1, is walked as (2R+1)^(D-1) rows of cells contiguous in x;
+//   * a uniform grid in D dimensions with cell edge h >= (r/2)(1 + 2^-20) (doubled until
+//     the grid has at most max(2^16, 8 n_src) cells); the box of (2R+1)^D cells around a
+//     target, R = floor(r / h) + 1, is walked as (2R+1)^(D-1) rows of cells contiguous in x,
+//     and each candidate is screened in FP32 before the exact FP64 test (walk_nd);
 //   * one thread per target. The FP64 pipe is the bound (a quadratic basis in 5D has 126
 //     moments per pair, 1/64 of the FP32 rate on this GPU), and a thread per target needs no
 //     cross-lane reduction of the moments, which would cost more FP64 instructions than the
@@ -185,16 +186,21 @@ __global__ void k_permute_nd(const double* __restrict__ f, const int32_t* __rest
 }
 
 template <int D>
-__global__ void k_gather_nd(const double* __restrict__ pts, int64_t n,
+__global__ void k_gather_nd(GridN g, const double* __restrict__ pts, int64_t n,
                             const uint32_t* __restrict__ order, int32_t* __restrict__ perm,
-                            int32_t* __restrict__ inv, double* __restrict__ x64) {
+                            int32_t* __restrict__ inv, double* __restrict__ x64,
+                            float* __restrict__ xf) {
     for (int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pos < n;
          pos += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = order[pos];
         perm[pos] = (int32_t)i;
         inv[i] = (int32_t)pos;
 #pragma unroll
-        for (int d = 0; d < D; d++) x64[d * n + pos] = pts[d * n + i];
+        for (int d = 0; d < D; d++) {
+            const double x = pts[d * n + i];
+            x64[d * n + pos] = x;
+            if (xf) xf[d * n + pos] = (float)(x - g.lo[d]);
+        }
     }
 }
 
@@ -208,6 +214,7 @@ void sort_nd(const GridN& g, const double* pts, int64_t n, bool with_start, Sort
     out.perm.alloc(sizeof(int32_t) * nn, s);
     out.inv.alloc(sizeof(int32_t) * nn, s);
     out.x64.alloc(sizeof(double) * D * nn, s);
+    if (with_start) out.xf.alloc(sizeof(float) * D * nn, s);
     DBuf kv(sizeof(uint32_t) * 4 * nn, s);
     uint32_t* k0 = kv.as<uint32_t>();
     uint32_t* v0 = k0 + nn;
@@ -229,8 +236,9 @@ void sort_nd(const GridN& g, const double* pts, int64_t n, bool with_start, Sort
     if (n > 0) {
         const uint32_t* order = radix_sort_pairs(k0, v0, k1, v1, n, g.ncell, s);
         PCMS_TRACE("nd_gather_sorted", s);
-        k_gather_nd<D><<<grid_blocks(n, 256), 256, 0, s>>>(pts, n, order, out.perm.as<int32_t>(),
-                                                            out.inv.as<int32_t>(), out.x64.as<double>());
+        k_gather_nd<D><<<grid_blocks(n, 256), 256, 0, s>>>(g, pts, n, order, out.perm.as<int32_t>(),
+                                                            out.inv.as<int32_t>(), out.x64.as<double>(),
+                                                            with_start ? out.xf.as<float>() : nullptr);
     }
     PCMS_LAUNCH_CHECK("nd_gather");
 }
@@ -240,6 +248,8 @@ struct NdArgs {
     int64_t ns, nt;
     const int32_t* cell_start;
     const double* sx64;   // [D][ns] sorted sources
+    const float* sxf;     // [D][ns] the same as FP32 offsets from the grid origin (filter)
+    float src_extent;     // max over d and sources of |s_d - lo_d|
     const double* tx64;   // [D][nt] sorted targets
     RadiusLevels lv;
     int weight;
@@ -254,12 +264,39 @@ struct NdArgs {
 
 // Calls f(j, d2) for every source j selected at radius level k of target t (coordinates tt),
 // in cell order.
+//
+// Candidates are first screened in FP32 (most of the box lies outside the ball: the ball
+// fills 5.3 r^5 of the (5r)^5 / 32 box in 5D with cells of r/2), and only those that may be
+// inside get the exact FP64 test. The screen rejects d2f > r^2 (1 + band), which is sound:
+// with the offsets from the grid origin rounded to FP32 (error <= 2^-24 |x - lo| each, so
+// <= eta = (ds + dt)(1 + 2^-24) + 2^-24 r per coordinate of s - t near the ball, ds and dt
+// the sources' and the target's 2^-24 max |x_d - lo_d|), a source within r has
+// sum e_f^2 < (r + sqrt(D) eta)^2 (Minkowski) and d2f <= (1 + D 2^-23)(r + sqrt(D) eta)^2.
+// band is that bound relative to r^2, and r2 (1 + band) is rounded up by a further 2^-20.
+// The screen is off (band > 1/4) when the FP32 offsets are too coarse for the radius.
 template <int D, typename F>
 __device__ __forceinline__ void walk_nd(const NdArgs& A, const double* tt, int k, F&& f) {
     const GridN& g = A.g;
     const double r = A.lv.r[k], r2 = A.lv.r2[k];
     const double r2_in = r2 * (1.0 - 9.094947017729282e-13);
     const int R = (int)fmin(floor(r * g.inv_h) + 1.0, 1073741824.0);
+    float tf[D];
+    float tmax = 0.f;
+#pragma unroll
+    for (int d = 0; d < D; d++) {
+        tf[d] = (float)(tt[d] - g.lo[d]);
+        tmax = fmaxf(tmax, fabsf(tf[d]));
+    }
+    float r2hi = INFINITY;
+    if (A.sxf) {
+        const float rf = A.lv.r2f[k] > 0.f ? sqrtf(A.lv.r2f[k]) : 0.f;
+        const float ds = 5.9604645e-08f * A.src_extent * (1.f + 1e-6f);
+        const float dt = 5.9604645e-08f * tmax * (1.f + 1e-6f);
+        const float eta = (ds + dt) * (1.f + 5.9604645e-08f) + 5.9604645e-08f * rf;
+        const float grow = 1.f + sqrtf((float)D) * eta / rf;
+        const float band = (1.f + (float)D * 1.1920929e-07f) * grow * grow - 1.f;
+        if (rf > 0.f && band < 0.25f) r2hi = A.lv.r2f[k] * (1.f + band) * (1.f + 9.5367432e-07f);
+    }
     int lo_c[D], hi_c[D], idx[D];
 #pragma unroll
     for (int d = 0; d < D; d++) {
@@ -280,6 +317,15 @@ __device__ __forceinline__ void walk_nd(const NdArgs& A, const double* tt, int k
         }
         const int a = A.cell_start[base + lo_c[0]], b = A.cell_start[base + hi_c[0] + 1];
         for (int j = a; j < b; j++) {
+            if (A.sxf) {
+                float d2f = 0.f;
+#pragma unroll
+                for (int d = 0; d < D; d++) {
+                    const float e = A.sxf[d * A.ns + j] - tf[d];
+                    d2f = fmaf(e, e, d2f);
+                }
+                if (d2f > r2hi) continue;
+            }
             double e = __dsub_rn(A.sx64[j], tt[0]);
             double d2 = __dmul_rn(e, e);
             e = __dsub_rn(A.sx64[A.ns + j], tt[1]);
@@ -370,8 +416,8 @@ __device__ __forceinline__ void accumulate_nd(double (&acc)[NACC], const double*
     }
 }
 
-// operator columns (MAP) and moments at the target's level kexp[t]
-template <int D, int DEG, int MODE>
+// operator columns (MAP) and, with MOMENTS, the moments at the target's level kexp[t]
+template <int D, int DEG, int MODE, bool MOMENTS = true>
 __global__ void __launch_bounds__(ND_THREADS) k_assemble_nd(NdArgs A) {
     constexpr int NM = mono_count(D, 2 * DEG);
     constexpr int M = mono_count(D, DEG);
@@ -389,16 +435,128 @@ __global__ void __launch_bounds__(ND_THREADS) k_assemble_nd(NdArgs A) {
         int64_t w_at = MODE == MODE_MAP ? A.offsets[t] : 0;
         const int64_t w_end = MODE == MODE_MAP ? w_at + A.counts[t] : 0;
         walk_nd<D>(A, tt, k, [&](int j, double d2) {
-            double u[D];
+            if constexpr (MOMENTS) {
+                double u[D];
 #pragma unroll
-            for (int d = 0; d < D; d++) u[d] = (A.sx64[d * A.ns + j] - tt[d]) * inv_r;
-            const double w = weight_value<double>(A.weight, sqrt(d2) * inv_r);
-            accumulate_nd<D, DEG, MODE, NACC>(acc, u, w, MODE == MODE_FUSED ? A.field[j] : 0.0);
+                for (int d = 0; d < D; d++) u[d] = (A.sx64[d * A.ns + j] - tt[d]) * inv_r;
+                const double w = weight_value<double>(A.weight, sqrt(d2) * inv_r);
+                accumulate_nd<D, DEG, MODE, NACC>(acc, u, w, MODE == MODE_FUSED ? A.field[j] : 0.0);
+            }
             if (MODE == MODE_MAP && w_at < w_end) A.cols[w_at++] = j;
         });
-        double* dst = A.mom + t * NACCP;
+        if constexpr (MOMENTS) {
+            double* dst = A.mom + t * NACCP;
 #pragma unroll
-        for (int i = 0; i < NACCP; i++) dst[i] = i < NACC ? acc[i < NACC ? i : 0] : 0.0;
+            for (int i = 0; i < NACCP; i++) dst[i] = i < NACC ? acc[i < NACC ? i : 0] : 0.0;
+        }
+    }
+}
+
+// The moments of a quadratic basis (degree <= 4) as products of two monomials of degree
+// <= 2: moment p = alpha(p) beta(p), alpha = its first min(deg, 2) variable occurrences in
+// variable order, beta = the rest. `order` lists the moments grouped by alpha.
+template <int D>
+struct SplitTab {
+    static constexpr int N = MonoTab<D>::N;
+    int alpha[N], beta[N], order[N];
+};
+template <int D>
+constexpr SplitTab<D> make_split_tab() {
+    SplitTab<D> t{};
+    constexpr int N = SplitTab<D>::N;
+    for (int p = 0; p < N; ++p) {
+        const Exp5 e = mono_exp_nd<D>(p);
+        Exp5 ea{}, eb{};
+        int seen = 0;
+        for (int d = 0; d < D; ++d)
+            for (int c = 0; c < e.e[d]; ++c) {
+                if (seen < 2) ea.e[d] += 1;
+                else eb.e[d] += 1;
+                ++seen;
+            }
+        if (seen <= 2) {   // degree <= 2: the monomial itself times 1
+            ea = e;
+            eb = Exp5{};
+        }
+        t.alpha[p] = mono_index_nd<D>(ea);
+        t.beta[p] = mono_index_nd<D>(eb);
+        t.order[p] = p;
+    }
+    for (int i = 1; i < N; ++i)   // stable insertion sort by alpha
+        for (int k = i; k > 0 && t.alpha[t.order[k - 1]] > t.alpha[t.order[k]]; --k) {
+            const int x = t.order[k];
+            t.order[k] = t.order[k - 1];
+            t.order[k - 1] = x;
+        }
+    return t;
+}
+
+constexpr int ND_PASS = 64;   // moments accumulated per pass over a row
+
+// Moments of a quadratic basis from the operator's row: the 126 (5D) accumulators do not fit
+// one thread's registers, so the row is read in passes of ND_PASS moments. Per pair and pass:
+// squared distance, weight and offsets, the degree <= 2 monomials a2 of u, then for each
+// moment one FMA, (w a2[alpha]) a2[beta], with w a2[alpha] formed once per alpha group.
+template <int D>
+__global__ void __launch_bounds__(ND_THREADS) k_moments_nd(NdArgs A) {
+    constexpr int NM = mono_count(D, 4);
+    constexpr int M2 = mono_count(D, 2);
+    constexpr int NACCP = round_up4(NM);
+    constexpr int NPASS = (NM + ND_PASS - 1) / ND_PASS;
+    constexpr SplitTab<D> tab = make_split_tab<D>();
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < A.nt;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        double tt[D];
+        load_target_nd<D>(A, t, tt);
+        const int k = A.kexp[t];
+        const double inv_r = A.lv.inv_r[k];
+        const int64_t a = A.offsets[t], b = a + A.counts[t];
+        double* dst = A.mom + t * NACCP;
+        sfor<NPASS>([&](auto PI) {
+            constexpr int q0 = decltype(PI)::value * ND_PASS;
+            constexpr int nq = NM - q0 < ND_PASS ? NM - q0 : ND_PASS;
+            double acc[nq];
+#pragma unroll
+            for (int q = 0; q < nq; q++) acc[q] = 0.0;
+            for (int64_t i = a; i < b; i++) {
+                const int j = A.cols[i];
+                double u[D];
+                double e = __dsub_rn(A.sx64[j], tt[0]);
+                double d2 = __dmul_rn(e, e);
+                u[0] = e * inv_r;
+#pragma unroll
+                for (int d = 1; d < D; d++) {
+                    e = __dsub_rn(A.sx64[d * A.ns + j], tt[d]);
+                    d2 = __dadd_rn(d2, __dmul_rn(e, e));
+                    u[d] = e * inv_r;
+                }
+                const double w = weight_value<double>(A.weight, sqrt(d2) * inv_r);
+                double a2[M2];
+                a2[0] = 1.0;
+                sfor<M2 - 1>([&](auto I) {
+                    constexpr int p = decltype(I)::value + 1;
+                    constexpr int par = mono_parent_nd<D>(p);
+                    constexpr int v = mono_var_nd<D>(p);
+                    a2[p] = a2[par] * u[v];
+                });
+                double wa = 0.0;
+                sfor<nq>([&](auto Q) {
+                    constexpr int q = q0 + decltype(Q)::value;
+                    constexpr int p = tab.order[q];
+                    constexpr int al = tab.alpha[p];
+                    constexpr int be = tab.beta[p];
+                    constexpr bool fresh = decltype(Q)::value == 0 || tab.alpha[tab.order[q - 1]] != al;
+                    if constexpr (fresh) wa = w * a2[al];
+                    acc[decltype(Q)::value] = fma(wa, a2[be], acc[decltype(Q)::value]);
+                });
+            }
+            sfor<nq>([&](auto Q) {
+                constexpr int p = tab.order[q0 + decltype(Q)::value];
+                dst[p] = acc[decltype(Q)::value];
+            });
+        });
+#pragma unroll
+        for (int i = NM; i < NACCP; i++) dst[i] = 0.0;
     }
 }
 
@@ -542,7 +700,7 @@ NdSearch<D> search_nd(const MlsParams& P, const double* src, int64_t ns, const d
     double lo[ND_MAX_DIM], hi[ND_MAX_DIM];
     box_nd(D, src, ns, tgt, nt, lo, hi, s);
     NdSearch<D> r;
-    r.g = make_grid_nd(D, lo, hi, P.radius,
+    r.g = make_grid_nd(D, lo, hi, 0.5 * P.radius,
                        std::min<int64_t>(int64_t(1) << 26, std::max<int64_t>(int64_t(1) << 16, 8 * ns)));
     sort_nd<D>(r.g, src, ns, true, S, s);
     sort_nd<D>(r.g, tgt, nt, false, T, s);
@@ -555,6 +713,12 @@ NdSearch<D> search_nd(const MlsParams& P, const double* src, int64_t ns, const d
     a.nt = nt;
     a.cell_start = S.cell_start.as<int32_t>();
     a.sx64 = S.x64.as<double>();
+    a.sxf = S.xf.as<float>();
+    {
+        double ext = 0.0;
+        for (int d = 0; d < D; d++) ext = std::max(ext, std::max(std::fabs(hi[d] - lo[d]), 0.0));
+        a.src_extent = (float)(ext * (1.0 + 1e-6));
+    }
     a.tx64 = T.x64.as<double>();
     a.lv = make_radius_levels(P.radius, r.g.inv_h);
     a.weight = (int)P.weight;
@@ -614,7 +778,16 @@ void create_map_nd(MapImpl& M, const double* src, const double* tgt) {
         a.offsets = M.offsets.as<int64_t>();
         a.cols = M.cols.as<int32_t>();
         a.mom = mom.as<double>();
-        {
+        if constexpr (DEG == 2) {   // columns first, then the moments in passes over the rows
+            {
+                PCMS_TRACE("nd_assemble_map", s);
+                k_assemble_nd<D, DEG, MODE_MAP, false><<<nd_blocks(nt), ND_THREADS, 0, s>>>(a);
+            }
+            {
+                PCMS_TRACE("nd_moments", s);
+                k_moments_nd<D><<<nd_blocks(nt), ND_THREADS, 0, s>>>(a);
+            }
+        } else {
             PCMS_TRACE("nd_assemble_map", s);
             k_assemble_nd<D, DEG, MODE_MAP><<<nd_blocks(nt), ND_THREADS, 0, s>>>(a);
         }
@@ -746,10 +919,24 @@ void mls_nd_transfer(const MlsParams& P, const double* src, int64_t ns, const do
                      int64_t nt, const double* fields, int nf, double* out, int8_t* status,
                      cudaStream_t s, int64_t* n_under) {
     const int D = P.dim, deg = P.degree;
+    if (deg == 2) {
+        // quadratic: through a transient operator (its moments are accumulated in passes
+        // over the rows, which needs the rows)
+        MapImpl M;
+        M.P = P;
+        M.ns = ns;
+        M.nt = nt;
+        M.stream = s;
+        mls_nd_create_map(M, src, tgt);
+        mls_apply(M, fields, nf, out, s);
+        if (status) mls_export(M, nullptr, nullptr, nullptr, status, nullptr, s);
+        *n_under = P.min_neighbors == 0 ? M.n_under : 0;
+        return;
+    }
 #define PCMS_ND_TR(DV, KV) \
     if (D == DV && deg == KV) return transfer_nd<DV, KV>(P, src, ns, tgt, nt, fields, nf, out, status, s, n_under)
-    PCMS_ND_TR(4, 0); PCMS_ND_TR(4, 1); PCMS_ND_TR(4, 2);
-    PCMS_ND_TR(5, 0); PCMS_ND_TR(5, 1); PCMS_ND_TR(5, 2);
+    PCMS_ND_TR(4, 0); PCMS_ND_TR(4, 1);
+    PCMS_ND_TR(5, 0); PCMS_ND_TR(5, 1);
 #undef PCMS_ND_TR
     fail(PCMS_ERR_INVALID_ARG, "MLS above 3D: dim must be 4 or 5");
 }

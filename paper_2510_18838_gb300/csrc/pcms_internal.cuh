@@ -107,6 +107,7 @@ struct SortedPoints {
     DBuf hl1;         // float2 [n] (mixed path, 3D): {yl,zl}
     DBuf cell;        // int4 [n] (targets): point_cell's cell coordinates
     DBuf frac;        // float4 [n] (targets): point_cell's position inside the cell
+    DBuf xf;          // float32 [dim][n] (4D/5D sources): offsets from the grid origin
 };
 
 // bounding box of pts (float64 [dim][n]) into dev_box[6] = {lo0,lo1,lo2,hi0,hi1,hi2};

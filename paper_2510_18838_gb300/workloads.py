@@ -212,6 +212,43 @@ def mls_3d_slab(n_src: int = 8_000_000, n_tgt: int = 8_000_000, radius: float = 
 
 
 # ---------------------------------------------------------------------------------------
+# 5D distribution function (stand-in for the paper's GNET energetic-particle distribution)
+# ---------------------------------------------------------------------------------------
+def slowing_down_points(n: int, seed: int, vc: float = 0.3) -> np.ndarray:
+    """float64 [5, n] phase-space points (x, y, z, v_par, v_perp): positions uniform in the
+    unit cube; speeds v in (0, 1] from the classical slowing-down shape, density in 3D velocity
+    space ~ 1 / (v^3 + vc^3), i.e. speed density ~ v^2 / (v^3 + vc^3), with CDF
+    F(v) = ln(1 + v^3/vc^3) / ln(1 + 1/vc^3), sampled by inversion:
+    v = vc (exp(u ln(1 + 1/vc^3)) - 1)^(1/3); the pitch xi is uniform in [-1, 1] (isotropic):
+    v_par = v xi, v_perp = v sqrt(1 - xi^2)."""
+    rng = np.random.default_rng(seed)
+    pos = rng.uniform(0.0, 1.0, size=(3, n))
+    u = rng.uniform(0.0, 1.0, size=n)
+    v = np.cbrt(vc ** 3 * np.expm1(u * np.log1p(1.0 / vc ** 3)))
+    xi = rng.uniform(-1.0, 1.0, size=n)
+    vel = np.stack([v * xi, v * np.sqrt(1.0 - xi * xi)])
+    return np.ascontiguousarray(np.concatenate([pos, vel]))
+
+
+def distribution_5d_field(pts: np.ndarray, vc: float = 0.3) -> np.ndarray:
+    """A smooth 5D distribution value: a Gaussian radial profile times a slowing-down speed
+    factor 1 / (v^3 + vc^3) and a mild pitch anisotropy."""
+    x, y, z, vpar, vperp = pts
+    v2 = vpar * vpar + vperp * vperp
+    radial = np.exp(-((x - 0.5) ** 2 + (y - 0.5) ** 2) / 0.08) * (1.0 + 0.3 * np.cos(2 * np.pi * z))
+    return radial / (v2 * np.sqrt(v2) + vc ** 3) * (1.0 + 0.2 * vpar / np.sqrt(v2 + 1e-12))
+
+
+def mls_5d_distribution(n_src: int = 400_000, n_tgt: int = 200_000, radius: float = 0.17,
+                        degree: int = 2, min_neighbors: int = 30) -> MLSCase:
+    src = slowing_down_points(n_src, 501)
+    tgt = slowing_down_points(n_tgt, 502)
+    f = distribution_5d_field(src)[None, :].copy()
+    return MLSCase(src, tgt, f, degree, radius, min_neighbors,
+                   f"mls5d_slowing_down_{n_src}_to_{n_tgt}_quadratic_r{radius}_fp64")
+
+
+# ---------------------------------------------------------------------------------------
 # Serving: Poisson stream of mixed transfer requests
 # ---------------------------------------------------------------------------------------
 @dataclasses.dataclass
