@@ -1,7 +1,7 @@
 """Benchmark of the GB300 field-transfer hot path (one JSON line on stdout).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload serve|transfer]
+                    [--workload serve|transfer|transfer_small|mls5d]
 
 Workloads (synthetic, seeded; shaped like the paper's field-transfer workloads):
   serve    (default) -- the headline: a stream of 2,000 transfer requests (Poisson arrivals;
@@ -18,6 +18,12 @@ Workloads (synthetic, seeded; shaped like the paper's field-transfer workloads):
               sources -> 4M targets, quadratic, r = 0.01, min 10 neighbours; (c) 3D MLS mixed
               8M -> 8M, quadratic, r = 0.012: operator + 16-field apply. Always run once
               (single stream) for the per-kernel breakdown and the roofline entry.
+  transfer_small -- the transfer step at about 1/8 of the points, radii scaled to keep the
+              neighbour counts (the case the ncu captures use).
+  mls5d    -- the 5D distribution-function leg alone (FP64 path above 3D): 400k -> 200k
+              phase-space points, quadratic; also part of the default run's JSON line.
+The default run's line also carries the vertex <-> centroid round-trip study on a
+WEST-sized synthetic mesh (Sec. 3.2.1, Eq. 2 and Eq. 3) and the 5D leg.
 
 Timing: W untimed warm-up steps; K timed steps each bracketed by CUDA events with a
 synchronize on both sides and a 256 MiB L2-flushing write between steps; barrier and max
@@ -515,7 +521,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="serve", choices=["serve", "transfer", "transfer_small"])
+    ap.add_argument("--workload", default="serve",
+                    choices=["serve", "transfer", "transfer_small", "mls5d"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -540,6 +547,16 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+
+    if args.workload == "mls5d":   # the 5D leg alone (profiling and parity helper)
+        st = mls5d_study(torch, pcms, W, reps=args.steps)
+        if rank == 0:
+            print(json.dumps({"metric": "5D target points mapped/sec (FP64 MLS create + apply)",
+                              "value": st["points_per_s"], "unit": "points/s", "n_gpus": world,
+                              "steps": args.steps, "warmup": 1, "ms_per_step": st["ms"],
+                              "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                              "config": {"workload": st["workload"]}, "mls5d": st}), flush=True)
+        return
 
     # ---- single-stream transfer pass: per-kernel breakdown and the roofline entry
     tw = TransferWorkload(torch, pcms, W, dev, small=args.workload == "transfer_small")

@@ -7,7 +7,7 @@ compiled with -ffp-contract=off); this module compiles it with gcc on first use 
 it with numpy.
 
 Dimensions: MLS in 2 to 5 dimensions (the paper maps fields in up to five, Sec. 1 and
-Sec. 4's 5D distribution function); the cell-list search (mode="grid") covers 2D and 3D
+Sec. 5.2's 5D distribution function); the cell-list search (mode="grid") covers 2D and 3D
 and falls back to brute force above. Meshes are 2D.
 
 Definitions followed (see the C file for details):
@@ -242,3 +242,4 @@ def locate(xy, tri, pts, field=None, mode="exhaustive"):
 
 
 from oracle.roundtrip import centroids, p1_integral, round_trip  # noqa: E402,F401
+from oracle.projection import l2_projection  # noqa: E402,F401

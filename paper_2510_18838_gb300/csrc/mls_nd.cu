@@ -1,5 +1,5 @@
 // mls_nd.cu -- the MLS transfer in four and five dimensions (the paper maps fields in up to
-// five dimensions: abstract, and Sec. 4's 5D distribution function), in FP64.
+// five dimensions: abstract, and Sec. 5.2's 5D distribution function), in FP64.
 //
 // The definitions are those of 2D and 3D (Sec. 3.2.1): selection d2 < r^2 with phi > 0,
 // d2 summed left to right in FP64 without contraction; per-target (or global) radius
