@@ -253,6 +253,28 @@ pcms_status pcms_mesh_centroids(pcms_mesh mesh, double* centroids, void* stream)
 pcms_status pcms_mesh_integrate(pcms_mesh mesh, const double* nodal_field, double* integral,
                                 void* stream);
 
+/*
+ * pcms_l2_project -- conservative L2 projection of a piecewise-linear field (Sec. 3.2.2):
+ *   f_t solves M f_t = b, M_AB = integral of N_A N_B (the target's consistent P1 mass matrix),
+ *   b_A = integral of N_A f_s over the supermesh of the two meshes (each overlapping pair of
+ *   triangles clipped to its common polygon, integrated exactly for P1 x P1). The integral
+ *   of f_t equals that of f_s over the region both meshes cover, up to the solve's residual.
+ *   src_field: device float64 [source vertices]; tgt_field: device float64 [target
+ *   vertices] (written). M f = b is solved by Jacobi-preconditioned conjugate gradients to
+ *   ||b - M f|| <= tol ||b|| (tol > 0, e.g. 1e-14) or max_iter iterations. info (host, may
+ *   be NULL) receives the pair count, iterations, final relative residual and the area of
+ *   the supermesh. Syncs `stream`. The target mesh caches its vertex-to-triangle lists.
+ */
+typedef struct {
+    int64_t intersecting_pairs;
+    int iterations;
+    double relative_residual;
+    double supermesh_area;
+} pcms_projection_info;
+pcms_status pcms_l2_project(pcms_mesh src_mesh, const double* src_field, pcms_mesh tgt_mesh,
+                            double* tgt_field, double tol, int max_iter,
+                            pcms_projection_info* info, void* stream);
+
 /* Release a mesh (memory freed on `stream`). NULL is a no-op. */
 void pcms_mesh_destroy(pcms_mesh mesh, void* stream);
 

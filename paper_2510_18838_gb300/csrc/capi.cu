@@ -327,6 +327,28 @@ pcms_status pcms_mesh_integrate(pcms_mesh mesh, const double* nodal_field, doubl
     });
 }
 
+pcms_status pcms_l2_project(pcms_mesh src_mesh, const double* src_field, pcms_mesh tgt_mesh,
+                            double* tgt_field, double tol, int max_iter,
+                            pcms_projection_info* info, void* stream) {
+    REQUIRE(src_mesh != nullptr && tgt_mesh != nullptr, "pcms_l2_project: mesh is NULL");
+    REQUIRE(src_mesh->impl.nv == 0 || src_field != nullptr, "pcms_l2_project: src_field is NULL");
+    REQUIRE(tgt_mesh->impl.nv == 0 || tgt_field != nullptr, "pcms_l2_project: tgt_field is NULL");
+    REQUIRE(std::isfinite(tol) && tol > 0.0, "pcms_l2_project: tol must be finite and > 0");
+    REQUIRE(max_iter >= 1, "pcms_l2_project: max_iter must be >= 1");
+    return guarded("pcms_l2_project", [&]() -> pcms_status {
+        const pcms::ProjectionResult r = pcms::l2_project(src_mesh->impl, src_field, tgt_mesh->impl,
+                                                          tgt_field, tol, max_iter,
+                                                          (cudaStream_t)stream);
+        if (info) {
+            info->intersecting_pairs = (int64_t)r.pairs;
+            info->iterations = r.iterations;
+            info->relative_residual = r.rel_residual;
+            info->supermesh_area = r.supermesh_area;
+        }
+        return PCMS_OK;
+    });
+}
+
 pcms_status pcms_trace_enable(int mode) {
     pcms::trace_enable(mode);
     return PCMS_OK;
@@ -345,7 +367,8 @@ void pcms_mesh_destroy(pcms_mesh mesh, void* stream) {
     if (!mesh) return;
     cudaStream_t s = (cudaStream_t)stream;
     pcms::MeshImpl& M = mesh->impl;
-    pcms::DBuf* bufs[] = {&M.xy, &M.tri, &M.cell_start, &M.items, &M.tsign, &M.vhl};
+    pcms::DBuf* bufs[] = {&M.xy, &M.tri, &M.cell_start, &M.items, &M.tsign, &M.vhl,
+                          &M.adj_start, &M.adj, &M.tri_w};
     for (pcms::DBuf* b : bufs) {
         b->s = s;
         b->release();

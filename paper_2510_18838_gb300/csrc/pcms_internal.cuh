@@ -360,6 +360,10 @@ struct MeshImpl {
     double origin[2];  // lower corner of the vertex box: the FP32 filter's frame
     float delta = 0.f; // absolute error allowance of the FP32 differences (2^-44 x extent)
     int use32 = 0;     // FP32 orientation filter usable (extent within [1e-30, 1e18])
+    // built on first use by an L2 projection onto this mesh (mesh_adjacency)
+    DBuf adj_start;    // int32 [nv+1]
+    DBuf adj;          // int32 [3 ntri] entries 3 k + corner, ascending within a vertex
+    DBuf tri_w;        // float64 [ntri] |T| / 12
 };
 
 void mesh_create(MeshImpl& M, const double* xy, int64_t nv, const int32_t* tri, int64_t ntri);
@@ -367,6 +371,17 @@ void mesh_locate(const MeshImpl& M, const double* pts, int64_t n, const double* 
                  int32_t* elem, int8_t* edim, double* vals, cudaStream_t s);
 void mesh_centroids(const MeshImpl& M, double* out, cudaStream_t s);
 double mesh_integrate(const MeshImpl& M, const double* field, cudaStream_t s);
+
+// conservative L2 projection of a P1 field between two meshes (projection.cu)
+struct ProjectionResult {
+    unsigned long long pairs;   // intersecting (source, target) triangle pairs
+    int iterations;             // conjugate-gradient iterations
+    double rel_residual;        // ||b - M f|| / ||b|| at the end
+    double supermesh_area;
+};
+void mesh_adjacency(MeshImpl& M, cudaStream_t s);   // vertex -> triangles, |T| / 12 (cached)
+ProjectionResult l2_project(const MeshImpl& S, const double* fs, MeshImpl& T, double* ft,
+                            double tol, int max_iter, cudaStream_t s);
 
 // number of SMs of the current device (cached)
 int num_sms();

@@ -94,6 +94,7 @@ SIGNATURES = {
     "pcms_locate_interp": (_I, [_P, _P, _I64, _P, _P, _P, _P, _P]),
     "pcms_mesh_centroids": (_I, [_P, _P, _P]),
     "pcms_mesh_integrate": (_I, [_P, _P, _P, _P]),
+    "pcms_l2_project": (_I, [_P, _P, _P, _P, _D, _I, _P, _P]),
     "pcms_mesh_destroy": (None, [_P, _P]),
     "pcms_server_create": (_I, [_I, _I64, _P]),
     "pcms_server_submit": (_I, [_P, _P, _P]),
@@ -315,6 +316,23 @@ def count_neighbors(src, tgt, radius, degree=1, precision="fp64", weight="wendla
                                       int(degree), float(radius), ctypes.byref(o), _ptr(counts),
                                       _ptr(kx), None, _stream(stream)))
     return (counts[:nt], kx[:nt]) if with_doublings else counts[:nt]
+
+
+class ProjectionInfo(ctypes.Structure):
+    _fields_ = [("intersecting_pairs", ctypes.c_int64), ("iterations", ctypes.c_int),
+                ("relative_residual", ctypes.c_double), ("supermesh_area", ctypes.c_double)]
+
+
+def l2_project(src_mesh, src_field, tgt_mesh, tol=1e-14, max_iter=500, out=None, stream=None):
+    """pcms_l2_project: conservative L2 projection of a P1 field (float64 [src vertices])
+    onto tgt_mesh's P1 space. Returns (values float64 [tgt vertices], info dict)."""
+    f = _dev(src_field, torch.float64, "src_field")
+    if out is None:
+        out = torch.empty(max(tgt_mesh.n_vertices, 1), dtype=torch.float64, device=f.device)
+    info = ProjectionInfo()
+    _check(lib().pcms_l2_project(src_mesh.handle, _ptr(f), tgt_mesh.handle, _ptr(out),
+                                 float(tol), int(max_iter), ctypes.byref(info), _stream(stream)))
+    return out[:tgt_mesh.n_vertices], {k: getattr(info, k) for k, _ in ProjectionInfo._fields_}
 
 
 class Mesh:
