@@ -8,7 +8,7 @@ f_s on mesh S and P1 shape functions N_A on mesh T:
   * the supermesh: every intersecting pair (source triangle, target triangle) clipped to its
     common convex polygon (Sutherland-Hodgman against the target triangle's three edges),
     found by brute force over all pairs whose bounding boxes overlap;
-  * the right-hand side b_A = integral of N_A f_s: each polygon split into a fan of triangles,
+  * the load vector, entry A the integral of N_A f_s: each polygon split into a fan of triangles,
     each integrated with the three-point edge-midpoint rule (exact for quadratics, so for the
     product of two linear functions);
   * the consistent mass matrix M_AB = integral of N_A N_B (per triangle |T|/12 [2 1 1; 1 2 1;

@@ -16,6 +16,7 @@
 // the sign of the largest component of their exact sum.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "pcms_internal.cuh"
 #include "trace.cuh"
@@ -342,16 +343,16 @@ void mesh_create(MeshImpl& M, const double* xy, int64_t nv, const int32_t* tri, 
     if (ntri > 0)
         PCMS_CU(cudaMemcpyAsync(M.tri.p, tri, sizeof(int32_t) * 3 * ntri, cudaMemcpyDeviceToDevice, s));
     // bounding box of the vertices
-    DBuf box(sizeof(double) * 6 + sizeof(long long) * 6 + sizeof(unsigned long long) * 2, s);
-    double* dbox = box.as<double>();
-    long long* enc = (long long*)(dbox + 6);
-    unsigned long long* bad = (unsigned long long*)(enc + 6);
-    launch_bbox(2, M.xy.as<double>(), nv, dbox, enc, bad, s);
-    double hb[6];
-    unsigned long long hbad = 0;
-    PCMS_CU(cudaMemcpyAsync(hb, dbox, sizeof(hb), cudaMemcpyDeviceToHost, s));
-    PCMS_CU(cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, s));
+    const int nbb = bbox_blocks(nv);
+    DBuf part(sizeof(double) * 8 * nbb, s);
+    launch_bbox_partials(2, M.xy.as<double>(), nv, part.as<double>(), s);
+    std::vector<double> hp(8 * (size_t)nbb);
+    if (nv > 0)
+        PCMS_CU(cudaMemcpyAsync(hp.data(), part.p, sizeof(double) * 8 * nbb, cudaMemcpyDeviceToHost, s));
     PCMS_CU(cudaStreamSynchronize(s));
+    double hb[6];
+    uint64_t hbad = 0;
+    bbox_combine(hp.data(), nv, hb, hb + 3, &hbad);
     if (hbad) fail(PCMS_ERR_INVALID_ARG, "non-finite vertex coordinate");
     if (nv == 0) { hb[0] = hb[1] = 0.0; hb[3] = hb[4] = 0.0; }
     M.bbox[0] = hb[0]; M.bbox[1] = hb[1]; M.bbox[2] = hb[3]; M.bbox[3] = hb[4];

@@ -2,6 +2,7 @@
 // count, operator assembly/solve/shape, one-shot transfer, apply and export.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "mls_dispatch.cuh"
 
@@ -136,23 +137,28 @@ BoxResult source_box(int dim, const double* src, int64_t ns, const double* tgt, 
         for (int d = 0; d < 3; d++) { b.lo[d] = o.lo[d]; b.hi[d] = o.hi[d]; }
         return b;
     }
-    DBuf box(sizeof(double) * 12 + sizeof(long long) * 12 + sizeof(unsigned long long) * 2, s);
-    double* dbox = box.as<double>();
-    long long* enc = (long long*)(dbox + 12);
-    unsigned long long* bad = (unsigned long long*)(enc + 12);
-    launch_bbox(dim, src, ns, dbox, enc, bad, s);
-    launch_bbox(dim, tgt, nt, dbox + 6, enc + 6, bad + 1, s);
-    double hb[12];
-    unsigned long long hbad[2];
-    PCMS_CU(cudaMemcpyAsync(hb, dbox, sizeof(hb), cudaMemcpyDeviceToHost, s));
-    PCMS_CU(cudaMemcpyAsync(hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, s));
+    // per-block partial boxes of both point sets, one copy back, combined here
+    const int bs = bbox_blocks(ns), bt = bbox_blocks(nt);
+    DBuf part(sizeof(double) * 8 * (bs + bt), s);
+    launch_bbox_partials(dim, src, ns, part.as<double>(), s);
+    launch_bbox_partials(dim, tgt, nt, part.as<double>() + 8 * bs, s);
+    std::vector<double> hp(8 * (size_t)(bs + bt));
+    if (ns > 0)
+        PCMS_CU(cudaMemcpyAsync(hp.data(), part.p, sizeof(double) * 8 * bs, cudaMemcpyDeviceToHost, s));
+    if (nt > 0)
+        PCMS_CU(cudaMemcpyAsync(hp.data() + 8 * bs, part.as<double>() + 8 * bs,
+                                sizeof(double) * 8 * bt, cudaMemcpyDeviceToHost, s));
     PCMS_CU(cudaStreamSynchronize(s));
-    if (hbad[0] || hbad[1])
-        fail(PCMS_ERR_INVALID_ARG, "non-finite point coordinate (" + std::to_string(hbad[0]) +
-                                       " in sources, " + std::to_string(hbad[1]) + " in targets)");
+    double slo[3], shi[3], tlo[3], thi[3];
+    uint64_t sbad = 0, tbad = 0;
+    bbox_combine(hp.data(), ns, slo, shi, &sbad);
+    bbox_combine(hp.data() + 8 * bs, nt, tlo, thi, &tbad);
+    if (sbad || tbad)
+        fail(PCMS_ERR_INVALID_ARG, "non-finite point coordinate (" + std::to_string(sbad) +
+                                       " in sources, " + std::to_string(tbad) + " in targets)");
     for (int d = 0; d < 3; d++) {
-        b.lo[d] = (d < dim && ns > 0) ? hb[d] : 0.0;
-        b.hi[d] = (d < dim && ns > 0) ? hb[3 + d] : 0.0;
+        b.lo[d] = (d < dim && ns > 0) ? slo[d] : 0.0;
+        b.hi[d] = (d < dim && ns > 0) ? shi[d] : 0.0;
     }
     return b;
 }

@@ -110,11 +110,11 @@ struct SortedPoints {
     DBuf xf;          // float32 [dim][n] (4D/5D sources): offsets from the grid origin
 };
 
-// bounding box of pts (float64 [dim][n]) into dev_box[6] = {lo0,lo1,lo2,hi0,hi1,hi2};
-// *dev_bad counts non-finite coordinates. Both are device buffers zero/initialised here.
-void launch_bbox(int dim, const double* pts, int64_t n, double* dev_box, long long* dev_enc,
-                 unsigned long long* dev_bad, cudaStream_t s);
-
+// Bounding boxes of pts (float64 [dim][n], dim <= 3) in one launch: per-block partial boxes (8 doubles per block, bbox_blocks(n)
+// blocks) that the host combines after copying them back.
+int bbox_blocks(int64_t n);
+void launch_bbox_partials(int dim, const double* pts, int64_t n, double* part, cudaStream_t s);
+void bbox_combine(const double* hpart, int64_t n, double* lo, double* hi, uint64_t* bad);
 // Sort points by cell of grid g. with_start: also build cell_start (sources).
 // with_hl: also write FP32 hi/lo coordinates relative to g.lo (mixed path).
 void sort_points(const Grid& g, const double* pts, int64_t n, bool with_start, bool with_hl,

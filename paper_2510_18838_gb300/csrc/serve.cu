@@ -261,6 +261,11 @@ void run_job(pcms_server_s* S, Job* j, cudaStream_t s, Bounce& bounce, pcms::Map
     }
     pcms::MlsParams P = pcms::make_mls_params(r.dim, r.basis_degree, r.radius, r.opts);
     if (cached) {
+        // the operator's sizes bound every access of the apply: they must be the request's
+        if (cached->ns != r.n_src || cached->nt != r.n_tgt || cached->P.dim != r.dim ||
+            cached->P.prec != r.opts.precision)
+            pcms::fail(PCMS_ERR_INVALID_ARG,
+                       "reuse_map: the cached operator under this map_key has other sizes");
         pcms::mls_apply(*cached, r.fields, r.n_fields, r.out, s);
     } else if (built) {
         std::unique_ptr<pcms::MapImpl> M(new pcms::MapImpl());

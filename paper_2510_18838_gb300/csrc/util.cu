@@ -97,75 +97,79 @@ Grid make_grid(int dim, const double* lo, const double* hi, double radius, int64
 }
 
 // ------------------------------------------------------------------------------------
-// bounding box: order-preserving int64 encoding of doubles + atomicMin/Max
+// bounding box
 // ------------------------------------------------------------------------------------
-__device__ __forceinline__ long long enc_double(double x) {
-    long long b = __double_as_longlong(x);
-    return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFLL);
-}
-__device__ __forceinline__ double dec_double(long long k) {
-    return __longlong_as_double(k >= 0 ? k : (k ^ 0x7FFFFFFFFFFFFFFFLL));
-}
-
-__global__ void k_bbox_init(long long* enc, unsigned long long* bad) {
-    int i = threadIdx.x;
-    if (i < 3) enc[i] = 0x7FFFFFFFFFFFFFFFLL;          // min slots
-    else if (i < 6) enc[i] = (long long)0x8000000000000000ULL;  // max slots
-    if (i == 0) *bad = 0;
-}
-
-__global__ void k_bbox(int dim, const double* __restrict__ pts, int64_t n, long long* enc,
-                       unsigned long long* bad) {
+// Per-block boxes: block b writes part[8 b + {0..2}] = minima, [3..5] = maxima, [6] = the
+// number of non-finite coordinates it saw. One launch, no initialisation; the host combines
+// the partial boxes after its copy (bbox_combine).
+__global__ void __launch_bounds__(256) k_bbox_partial(int dim, const double* __restrict__ pts,
+                                                      int64_t n, double* __restrict__ part) {
+    __shared__ double sh[8][7];
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    unsigned long long nb = 0;
+    double nb = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         for (int d = 0; d < dim; d++) {
-            double x = pts[d * n + i];
-            if (!isfinite(x)) { nb++; continue; }
+            const double x = pts[d * n + i];
+            if (!isfinite(x)) {
+                nb += 1.0;
+                continue;
+            }
             lo[d] = fmin(lo[d], x);
             hi[d] = fmax(hi[d], x);
         }
     }
-    for (int d = 0; d < dim; d++) {
-        for (int o = 16; o > 0; o >>= 1) {
+    for (int o = 16; o > 0; o >>= 1) {
+        for (int d = 0; d < 3; d++) {
             lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
             hi[d] = fmax(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
         }
+        nb += __shfl_xor_sync(0xffffffffu, nb, o);
     }
-    for (int o = 16; o > 0; o >>= 1) nb += __shfl_xor_sync(0xffffffffu, nb, o);
+    const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
-        for (int d = 0; d < dim; d++) {
-            if (lo[d] <= hi[d]) {
-                atomicMin(&enc[d], enc_double(lo[d]));
-                atomicMax(&enc[3 + d], enc_double(hi[d]));
-            }
+        for (int d = 0; d < 3; d++) {
+            sh[w][d] = lo[d];
+            sh[w][3 + d] = hi[d];
         }
-        if (nb) atomicAdd(bad, nb);
+        sh[w][6] = nb;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        const int k = threadIdx.x;
+        double v = sh[0][k];
+        for (int j = 1; j < (int)(blockDim.x >> 5); j++)
+            v = k < 3 ? fmin(v, sh[j][k]) : (k < 6 ? fmax(v, sh[j][k]) : v + sh[j][k]);
+        part[8 * blockIdx.x + k] = v;
     }
 }
 
-__global__ void k_bbox_decode(const long long* enc, double* box) {
-    int i = threadIdx.x;
-    if (i < 6) box[i] = dec_double(enc[i]);
+int bbox_blocks(int64_t n) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms()));
 }
 
-void launch_bbox(int dim, const double* pts, int64_t n, double* dev_box, long long* dev_enc,
-                 unsigned long long* dev_bad, cudaStream_t s) {
-    {
-        PCMS_TRACE("bbox_init", s);
-        k_bbox_init<<<1, 32, 0, s>>>(dev_enc, dev_bad);
+void launch_bbox_partials(int dim, const double* pts, int64_t n, double* part, cudaStream_t s) {
+    if (n <= 0) return;
+    PCMS_TRACE("bbox_partial", s);
+    k_bbox_partial<<<bbox_blocks(n), 256, 0, s>>>(dim, pts, n, part);
+    PCMS_LAUNCH_CHECK("bbox_partial");
+}
+
+void bbox_combine(const double* hpart, int64_t n, double* lo, double* hi, uint64_t* bad) {
+    for (int d = 0; d < 3; d++) {
+        lo[d] = INFINITY;
+        hi[d] = -INFINITY;
     }
-    if (n > 0) {
-        PCMS_TRACE("bbox_reduce", s);
-        int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 4);
-        k_bbox<<<blocks, 256, 0, s>>>(dim, pts, n, dev_enc, dev_bad);
-    }
-    {
-        PCMS_TRACE("bbox_decode", s);
-        k_bbox_decode<<<1, 32, 0, s>>>(dev_enc, dev_box);
-    }
-    PCMS_LAUNCH_CHECK("bbox");
+    double nb = 0.0;
+    if (n > 0)
+        for (int b = 0; b < bbox_blocks(n); b++) {
+            for (int d = 0; d < 3; d++) {
+                lo[d] = std::fmin(lo[d], hpart[8 * b + d]);
+                hi[d] = std::fmax(hi[d], hpart[8 * b + 3 + d]);
+            }
+            nb += hpart[8 * b + 6];
+        }
+    *bad = (uint64_t)nb;
 }
 
 // ------------------------------------------------------------------------------------
@@ -271,11 +275,69 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const int32_t* __res
     }
 }
 
+// Small inputs in one block (one launch instead of three): 1024 threads scan tiles of
+// 1024 x SCAN_ITEMS entries in order, carrying the running total.
+constexpr int SCAN1_THREADS = 1024;
+constexpr int64_t SCAN1_MAX = 32768;
+
+template <typename T>
+__global__ void __launch_bounds__(SCAN1_THREADS) k_scan_single(const int32_t* __restrict__ in,
+                                                              int64_t n, T* __restrict__ out) {
+    __shared__ T wt[32];
+    __shared__ T carry_s;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += (int64_t)SCAN1_THREADS * SCAN_ITEMS) {
+        const int64_t i0 = base + (int64_t)threadIdx.x * SCAN_ITEMS;
+        T v[SCAN_ITEMS];
+        T sum = 0;
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; k++) {
+            v[k] = i0 + k < n ? (T)in[i0 + k] : T(0);
+            sum += v[k];
+        }
+        T x = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const T y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wt[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            const T t = wt[lane];
+            T u = t;
+            for (int o = 1; o < 32; o <<= 1) {
+                const T y = __shfl_up_sync(0xffffffffu, u, o);
+                if (lane >= o) u += y;
+            }
+            wt[lane] = u - t;
+        }
+        __syncthreads();
+        T run = carry_s + wt[wid] + (x - sum);
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; k++) {
+            if (i0 + k < n) out[i0 + k] = run;
+            run += v[k];
+        }
+        __syncthreads();
+        if (threadIdx.x == SCAN1_THREADS - 1) carry_s = run;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = carry_s;
+}
+
 template <typename T>
 void exclusive_scan(const int32_t* in, T* out, int64_t n, cudaStream_t s) {
     int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (nb == 0) {
         PCMS_CU(cudaMemsetAsync(out, 0, sizeof(T), s));
+        return;
+    }
+    if (n <= SCAN1_MAX) {   // also in place: a tile is read before any of it is written
+        PCMS_TRACE("scan_single", s);
+        k_scan_single<T><<<1, SCAN1_THREADS, 0, s>>>(in, n, out);
+        PCMS_LAUNCH_CHECK("scan_single");
         return;
     }
     DBuf bs(sizeof(T) * nb, s);
@@ -319,7 +381,7 @@ __global__ void k_cell_keys(Grid g, const double* __restrict__ pts, int64_t n,
             c += g.n[0] * g.n[1] * cell_of(pts[2 * n + i], g.lo[2], g.inv_h, g.n[2]);
         key[i] = (uint32_t)c;
         idx[i] = (uint32_t)i;
-        atomicAdd(&count[c], 1);
+        if (count) atomicAdd(&count[c], 1);
     }
 }
 
@@ -455,13 +517,17 @@ void sort_points(const Grid& g, const double* pts, int64_t n, bool with_start, b
     out.n = n;
     const int dim = g.dim;
     const int64_t nn = std::max<int64_t>(n, 1);
-    DBuf count(sizeof(int32_t) * (g.ncell + 1), s);
+    // cell counts and starts only where they are needed (sources); targets are only ordered
+    DBuf count;
     DBuf kv(sizeof(uint32_t) * 4 * nn, s);   // key, idx, key', idx'
     uint32_t* k0 = kv.as<uint32_t>();
     uint32_t* v0 = k0 + nn;
     uint32_t* k1 = v0 + nn;
     uint32_t* v1 = k1 + nn;
-    PCMS_CU(cudaMemsetAsync(count.p, 0, sizeof(int32_t) * (g.ncell + 1), s));
+    if (with_start) {
+        count.alloc(sizeof(int32_t) * (g.ncell + 1), s);
+        PCMS_CU(cudaMemsetAsync(count.p, 0, sizeof(int32_t) * (g.ncell + 1), s));
+    }
     out.perm.alloc(sizeof(int32_t) * nn, s);
     out.inv.alloc(sizeof(int32_t) * nn, s);
     out.x64.alloc(sizeof(double) * dim * nn, s);
@@ -473,22 +539,16 @@ void sort_points(const Grid& g, const double* pts, int64_t n, bool with_start, b
         out.cell.alloc(sizeof(int4) * nn, s);
         out.frac.alloc(sizeof(float4) * nn, s);
     }
-    DBuf start_tmp;
-    int32_t* start;
-    if (with_start) {
-        out.cell_start.alloc(sizeof(int32_t) * (g.ncell + 1), s);
-        start = out.cell_start.as<int32_t>();
-    } else {
-        start_tmp.alloc(sizeof(int32_t) * (g.ncell + 1), s);
-        start = start_tmp.as<int32_t>();
-    }
+    if (with_start) out.cell_start.alloc(sizeof(int32_t) * (g.ncell + 1), s);
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8));
     if (n > 0) {
         PCMS_TRACE("grid_cell_keys", s);
-        k_cell_keys<<<blocks, 256, 0, s>>>(g, pts, n, k0, v0, count.as<int32_t>());
+        k_cell_keys<<<blocks, 256, 0, s>>>(g, pts, n, k0, v0,
+                                           with_start ? count.as<int32_t>() : nullptr);
     }
     PCMS_LAUNCH_CHECK("cell_keys");
-    exclusive_scan<int32_t>(count.as<int32_t>(), start, g.ncell, s);
+    if (with_start)
+        exclusive_scan<int32_t>(count.as<int32_t>(), out.cell_start.as<int32_t>(), g.ncell, s);
     if (n > 0) {
         v0 = radix_sort_pairs(k0, v0, k1, v1, n, g.ncell, s);
         PCMS_TRACE("grid_gather_sorted", s);

@@ -169,6 +169,20 @@ def _dev(t, dtype, name):
     return t.contiguous()
 
 
+def _req_tensor(t, dtype, shape, name):
+    """A serving request's tensor, used in place: the server reads and writes it after
+    submit returns, so a copy (to fix its dtype or layout) would not be the caller's."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
 GROWTH = {"target": 0, "global": 1}
 
 
@@ -413,6 +427,14 @@ class Server:
 
     def submit_mls(self, src, tgt, fields, out, degree, radius, precision="mixed",
                    weight="wendland_c2", min_neighbors=0, map_key=-1, reuse=False, bytes_hint=0):
+        if src.dim() != 2 or tgt.dim() != 2 or fields.dim() != 2:
+            raise ValueError("src, tgt: [dim, n]; fields: [n_fields, n_src]")
+        dim, ns, nt, nf = src.shape[0], src.shape[1], tgt.shape[1], fields.shape[0]
+        fdt = torch.float32 if precision == "mixed" else torch.float64
+        _req_tensor(src, torch.float64, (dim, ns), "src")
+        _req_tensor(tgt, torch.float64, (dim, nt), "tgt")
+        _req_tensor(fields, fdt, (nf, ns), "fields")
+        _req_tensor(out, fdt, (nf, nt), "out")
         r = Request()
         r.kind = REQ_MLS
         r.dim = src.shape[0]
@@ -430,6 +452,18 @@ class Server:
         return self._submit(r, (src, tgt, fields, out))
 
     def submit_mesh(self, xy, tri, pts, field, values, elem, bytes_hint=0):
+        if xy.dim() != 2 or tri.dim() != 2 or pts.dim() != 2:
+            raise ValueError("xy: [2, n_vertices]; tri: [3, n_triangles]; pts: [2, n]")
+        nv, ntri, nt = xy.shape[1], tri.shape[1], pts.shape[1]
+        _req_tensor(xy, torch.float64, (2, nv), "xy")
+        _req_tensor(tri, torch.int32, (3, ntri), "tri")
+        _req_tensor(pts, torch.float64, (2, nt), "pts")
+        _req_tensor(elem, torch.int32, (nt,), "elem")
+        if (field is None) != (values is None):
+            raise ValueError("field and values go together")
+        if field is not None:
+            _req_tensor(field, torch.float64, (nv,), "field")
+            _req_tensor(values, torch.float64, (nt,), "values")
         r = Request()
         r.kind = REQ_MESH
         r.src_pts, r.n_src = xy.data_ptr(), xy.shape[1]

@@ -1,7 +1,7 @@
 """Vertex <-> centroid round trips on a triangle mesh: the accuracy (Eq. 2) and conservation
 (Eq. 3) study of Sec. 3.2.1, run through the library.
 
-One iteration maps a nodal field from the mesh vertices to the element centroids and back
+One iteration takes a nodal field vertices -> centroids, then centroids -> vertices,
 with two cached MLS operators (pcms_create_map), applied without allocation
 (pcms_apply_map_noalloc) so that an iteration can be captured once in a CUDA graph and
 replayed. The centroids (pcms_mesh_centroids) and the integral of the piecewise-linear

@@ -50,3 +50,45 @@ def test_max_pts_caps_sizes():
     reqs = W.request_stream(n_req=200, seed=3, max_pts=5000)
     assert max(r.n_tgt for r in reqs) <= 5000
     assert max(r.n_src for r in reqs if r.kind == "mls") <= 5000
+
+
+def test_server_requests_are_checked_before_submission():
+    """A serving request's tensors are used in place after submit returns, so a wrong dtype,
+    shape or layout is refused in the binding instead of being copied or misread."""
+    import types
+
+    import pytest
+    import torch
+
+    from paper_2510_18838_gb300 import pcms
+    fake = types.SimpleNamespace()          # never reached: the checks come first
+    src = torch.zeros((2, 10), dtype=torch.float64)
+    tgt = torch.zeros((2, 4), dtype=torch.float64)
+    f = torch.zeros((3, 10), dtype=torch.float32)
+    out = torch.zeros((3, 4), dtype=torch.float32)
+    cases = [
+        dict(src=src.float()),                                    # coordinates not FP64
+        dict(fields=f.double()),                                  # mixed maps take FP32 fields
+        dict(out=torch.zeros((3, 5), dtype=torch.float32)),       # wrong target count
+        dict(fields=torch.zeros((10, 3), dtype=torch.float32).t()),   # not contiguous
+        dict(tgt=torch.zeros((3, 4), dtype=torch.float64)),       # other dimension
+    ]
+    for c in cases:
+        a = dict(src=src, tgt=tgt, fields=f, out=out)
+        a.update(c)
+        with pytest.raises((TypeError, ValueError)):
+            pcms.Server.submit_mls(fake, a["src"], a["tgt"], a["fields"], a["out"], 1, 0.1)
+    with pytest.raises(TypeError):
+        pcms.Server.submit_mls(fake, src, tgt, f, out, 1, 0.1, precision="fp64")
+    xy = torch.zeros((2, 9), dtype=torch.float64)
+    tri = torch.zeros((3, 8), dtype=torch.int32)
+    pts = torch.zeros((2, 5), dtype=torch.float64)
+    elem = torch.zeros(5, dtype=torch.int32)
+    with pytest.raises(TypeError):
+        pcms.Server.submit_mesh(fake, xy, tri.long(), pts, None, None, elem)
+    with pytest.raises(ValueError):
+        pcms.Server.submit_mesh(fake, xy, tri, pts, torch.zeros(9, dtype=torch.float64), None,
+                                elem)
+    with pytest.raises(ValueError):
+        pcms.Server.submit_mesh(fake, xy, tri, pts, torch.zeros(8, dtype=torch.float64),
+                                torch.zeros(5, dtype=torch.float64), elem)
