@@ -185,6 +185,37 @@ AsmArgs base_args(const Grid& g, const SortedPoints& S, const SortedPoints& Tp,
     return a;
 }
 
+// Tier-1 basis estimates (estimate_basis): blocked-compensated mixed plans at lambda = 0
+// and degree >= 1 assemble targets whose estimated neighbour centroid lies more than
+// RECENTRE_MIN radii away in that re-centred basis, so that they pass in tier 1 instead of
+// being walked again in tier 2. Returns the buffers (per-cell means, per-target basis).
+constexpr float RECENTRE_MIN = 0.5f;
+
+struct BasisEstimate {
+    DBuf pyr, basis;
+    int levels = 0;
+    int64_t off[PYR_MAX] = {};
+    void enable(bool mixed, const AsmPlan& plan, const MlsParams& P, const Grid& g,
+                const SortedPoints& S, int64_t nt, cudaStream_t s) {
+        if (!(mixed && plan.acc == ACC_BK && P.degree >= 1 && P.lambda == 0.0) || nt <= 0 ||
+            g.ncell <= 0)
+            return;
+        levels = pyramid_levels(g);
+        pyr.alloc(sizeof(float4) * pyramid_size(g, levels, off), s);
+        basis.alloc(sizeof(float4) * nt, s);
+        cell_pyramid(g, S, levels, off, pyr.as<float4>(), s);
+    }
+    void apply(AsmArgs& a) const {
+        if (!basis.p) return;
+        a.cpyr = pyr.as<float4>();
+        for (int j = 0; j < PYR_MAX; j++) a.pyr_off[j] = off[j];
+        a.pyr_levels = levels;
+        a.basis_out = basis.as<float4>();
+        a.recentre_min2 = RECENTRE_MIN * RECENTRE_MIN;
+    }
+    void apply(SolveArgs& sa) const { sa.basis_in = basis.p ? basis.as<float4>() : nullptr; }
+};
+
 int accp(int dim, int deg, int mode) {
     int nm = mono_count(dim, 2 * deg), m = mono_count(dim, deg);
     int nacc = mode == MODE_FUSED ? nm + m : nm;
@@ -201,13 +232,14 @@ void solve_tiers(int dim, int deg, int mode, bool mixed, AsmPlan plan, const Asm
     const int np = accp(dim, deg, mode);
     const int G = plan.G;
     const int mk1 = mom_kind(mixed, plan.acc);
-    DBuf lists(sizeof(int32_t) * (2 * nt + 2), s);
+    DBuf lists(sizeof(int32_t) * (2 * nt + 3), s);
     int32_t* list2 = lists.as<int32_t>();
     int32_t* list3 = list2 + nt;
     int32_t* n2 = list2 + 2 * nt;
     int32_t* n3 = n2 + 1;
+    int32_t* n_rc = n2 + 2;
     DBuf basis2(sizeof(float4) * nt, s);
-    PCMS_CU(cudaMemsetAsync(n2, 0, 2 * sizeof(int32_t), s));
+    PCMS_CU(cudaMemsetAsync(n2, 0, 3 * sizeof(int32_t), s));
     sa.list2 = list2;
     sa.n2 = n2;
     sa.list3 = list3;
@@ -218,7 +250,8 @@ void solve_tiers(int dim, int deg, int mode, bool mixed, AsmPlan plan, const Asm
     sa.recentre = mixed && deg >= 1 && sa.lambda == 0.0;
     sa.refine64 = !mixed && deg >= 1 && sa.lambda == 0.0;
     sa.tau = !mixed ? TAU_FP64 : (sa.acc == ACC_BK ? TAU_BK : TAU_MIXED);
-    sa.basis_in = nullptr;
+    // sa.basis_in: the caller's tier-1 basis estimates (BasisEstimate), or null
+    sa.n_recentred = sa.basis_in ? n_rc : nullptr;
     sa.basis2 = basis2.as<float4>();
     sa.rc = rc;
     solve_any(dim, deg, mode, mk1, sa, thread_blocks(nt, 128), s);
@@ -232,6 +265,8 @@ void solve_tiers(int dim, int deg, int mode, bool mixed, AsmPlan plan, const Asm
         if (n_ref == 0) return;
         DBuf mom4(sizeof(double) * np * n_ref, s);
         AsmArgs a4 = a;
+        a4.cpyr = nullptr;
+        a4.basis_out = nullptr;
         a4.list = list2;
         a4.n_list = n2;
         a4.mom = mom4.p;
@@ -245,6 +280,7 @@ void solve_tiers(int dim, int deg, int mode, bool mixed, AsmPlan plan, const Asm
         // the FP64 path's fields are double (fd)
         assemble_any(dim, deg, false, mode, G, ACC_PLAIN, true, a4, asm_blocks(n_ref, G), s);
         SolveArgs s4 = sa;
+        s4.n_recentred = nullptr;
         s4.list = list2;
         s4.n_list = n2;
         s4.mom = mom4.p;
@@ -257,16 +293,19 @@ void solve_tiers(int dim, int deg, int mode, bool mixed, AsmPlan plan, const Asm
         solve_any(dim, deg, mode, MOM_F64, s4, thread_blocks(n_ref, 128), s);
         return;
     }
-    int32_t cnt[2] = {0, 0};
+    int32_t cnt[3] = {0, 0, 0};
     PCMS_CU(cudaMemcpyAsync(cnt, n2, sizeof(cnt), cudaMemcpyDeviceToHost, s));
     PCMS_CU(cudaStreamSynchronize(s));
     trace_count("mls_tier1_targets", nt - cnt[0] - cnt[1]);
+    trace_count("mls_tier1_recentred_solves", cnt[2]);
     trace_count("mls_tier2_targets", cnt[0]);
     trace_list_pairs(mode == MODE_FUSED ? "mls_fused_tier2_pairs" : "mls_map_tier2_pairs", list2,
                      n2, sa.counts, cnt[0], s);
     if (cnt[0] > 0) {
         DBuf mom2(sizeof(float2) * np * cnt[0], s);
         AsmArgs a2 = a;
+        a2.cpyr = nullptr;
+        a2.basis_out = nullptr;
         a2.list = list2;
         a2.n_list = n2;
         a2.mom = mom2.p;
@@ -279,6 +318,7 @@ void solve_tiers(int dim, int deg, int mode, bool mixed, AsmPlan plan, const Asm
         }
         assemble_any(dim, deg, true, mode, 32, ACC_BK, false, a2, asm_blocks(cnt[0], 32), s);
         SolveArgs s2 = sa;
+        s2.n_recentred = nullptr;
         s2.list = list2;
         s2.n_list = n2;
         s2.mom = mom2.p;
@@ -297,6 +337,8 @@ void solve_tiers(int dim, int deg, int mode, bool mixed, AsmPlan plan, const Asm
     if (cnt[1] > 0) {
         DBuf mom3(sizeof(double) * np * cnt[1], s);
         AsmArgs a3 = a;
+        a3.cpyr = nullptr;
+        a3.basis_out = nullptr;
         a3.list = list3;
         a3.n_list = n3;
         a3.mom = mom3.p;
@@ -309,6 +351,7 @@ void solve_tiers(int dim, int deg, int mode, bool mixed, AsmPlan plan, const Asm
         }
         assemble_any(dim, deg, false, mode, G, ACC_PLAIN, false, a3, asm_blocks(cnt[1], G), s);
         SolveArgs s3 = sa;
+        s3.n_recentred = nullptr;
         s3.list = list3;
         s3.n_list = n3;
         s3.mom = mom3.p;
@@ -406,7 +449,9 @@ int64_t estimate_mls_bytes(const MlsParams& P, int64_t ns, int64_t nt, int nf, b
     const double nnz = 1.3 * k * nt;
     if (keep_map || nf > 2) b += nnz * (4.0 + elem);                 // operator
     b += (double)(ns + nt) * std::max(nf, 1) * elem * 2.0;           // apply/permute scratch
-    b += 4.0 * std::min<double>((double)(int64_t(1) << 24), 2.0 * ns + 64.0);  // cell starts
+    b += (mixed ? 26.0 : 4.0) * std::min<double>((double)(int64_t(1) << 24), 2.0 * ns + 64.0);
+    // cell starts (and, mixed, the cell-sum pyramid of the tier-1 basis estimates)
+    if (mixed) b += nt * 16.0;                                       // estimated bases
     return (int64_t)(1.15 * b) + (int64_t(1) << 20);
 }
 
@@ -446,6 +491,7 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
     a.err = err.as<unsigned>();
     a.counts = M.counts.as<int32_t>();
     a.kexp_out = M.kexp.as<int32_t>();
+    BasisEstimate bases;   // used by the row assembly (MODE_MAP), not by the count pass
     // Rows. With a fixed radius the assembly stages each target's columns, reserves its row
     // with one atomic add and writes it (one pass; the rare rows that do not fit are walked
     // again). When the radius may grow, a count pass finds the doublings and the row sizes.
@@ -471,6 +517,8 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
         DBuf rc(sizeof(float4) * nt, s);
         a.offsets = M.offsets.as<int64_t>();
         a.mom = mom.p;
+        bases.enable(mixed, plan, P, M.g, M.src, nt, s);
+        bases.apply(a);
         if (one_pass) {
             const int64_t est = (int64_t)(1.3 * std::min(plan.mean, (double)ns) * (double)nt) + 4096;
             M.cols.alloc(sizeof(int32_t) * est, s);
@@ -506,7 +554,9 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
             a.kexp_out = nullptr;
             if (hredo > 0) {   // rows that did not fit: walk again, writing at the reserved start
                 DBuf mom2(melem * np * hredo, s);
-                AsmArgs a2 = a;
+                AsmArgs a2 = a;   // columns only: the first pass's moments and bases stand
+                a2.cpyr = nullptr;
+                a2.basis_out = nullptr;
                 a2.list = redo;
                 a2.n_list = n_redo;
                 a2.mom = mom2.p;
@@ -524,6 +574,7 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
         M.vals.alloc((mixed ? sizeof(float) : sizeof(double)) * std::max<int64_t>(nnz, 1), s);
 
         SolveArgs sa{};
+        bases.apply(sa);
         sa.nt = nt;
         sa.counts = M.counts.as<int32_t>();
         sa.mom = mom.p;
@@ -658,6 +709,8 @@ void mls_transfer(const MlsParams& P0, const double* src, int64_t ns, const doub
     DBuf kexp(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
     const int np = accp(dim, deg, MODE_FUSED);
     DBuf mom(mom_elem_bytes(mom_kind(mixed, plan.acc)) * np * std::max<int64_t>(nt, 1), s);
+    BasisEstimate est;
+    est.enable(mixed, plan, P, g, S, nt, s);
     for (int f = 0; f < nf; f++) {
         if (ns > 0) {
             PCMS_TRACE("mls_field_to_sorted", s);
@@ -675,8 +728,10 @@ void mls_transfer(const MlsParams& P0, const double* src, int64_t ns, const doub
         a.kexp_out = kexp.as<int32_t>();
         a.field = fs.p;
         a.mom = mom.p;
+        est.apply(a);
         assemble_any(dim, deg, mixed, MODE_FUSED, G, plan.acc, !mixed, a, asm_blocks(nt, G), s);
         SolveArgs sa{};
+        est.apply(sa);
         sa.nt = nt;
         sa.counts = counts.as<int32_t>();
         sa.mom = mom.p;

@@ -106,6 +106,17 @@ struct AsmArgs {
     const void* field;       // FUSED: sorted field (float or double)
     void* mom;               // MAP/FUSED: [nt][NACCP] (float, float2 for ACC_BK, or double)
     const float4* basis;     // list mode (ACC_BK, or FP64): per list position (c_x, c_y, c_z, 1/s), or null
+    // tier 1, blocked compensation: the sources' cell-sum pyramid (cell_pyramid: level j
+    // starts at pyr_off[j]), from which a target whose radius grew, or whose ball reaches
+    // past the grid, estimates its neighbours' weighted centroid and spread before it walks;
+    // if the estimated centroid lies more than sqrt(recentre_min2) (offsets in units of the
+    // radius) from the target, it is assembled in that re-centred basis. The basis used is
+    // written to basis_out[t] (the identity when none). Null: target-centred.
+    const float4* cpyr;
+    int64_t pyr_off[PYR_MAX];
+    int pyr_levels;
+    float4* basis_out;
+    float recentre_min2;
     unsigned* err;
 };
 
@@ -156,7 +167,9 @@ struct SolveArgs {
     int acc;                  // ACC_PLAIN or ACC_BK: how these moments were accumulated
     int recentre;             // tier 1 -> 2: hand on a re-centred basis (lambda = 0, degree >= 1)
     int refine64;             // FP64 path: list targets with amp > AMP_FP64 for the refine pass
-    const float4* basis_in;   // tier 2: basis of these moments, per list position
+    const float4* basis_in;   // basis of these moments: per list position (list mode), else
+                              // per target (tier 1 with an estimated basis), or null
+    int32_t* n_recentred;     // tier 1: targets solved in an estimated re-centred basis, or null
     float4* basis2;           // tier 1: basis for tier 2, per list2 position
     float4* rc;               // MAP: basis of the accepted tier-2 rows, per sorted target
     int32_t* list2;           // targets for tier 2 / tier 3
@@ -454,6 +467,110 @@ using MomT = typename std::conditional<ACC == ACC_BK, float2, T>::type;
 template <int DIM, int DEG, int ACC>
 constexpr int asm_min_blocks() { return (ACC == ACC_BK && DIM == 3 && DEG == 2) ? 1 : 2; }
 
+// Candidate row rho of a target (cell (ct) and position in it (fr), cell units): the cells
+// (dz, dy) in row-major order over [z0, z0 + nz) x [y0, y0 + ny), trimmed in x to the chord of
+// the ball of radius RR (which includes the margin mg). Returns false for an empty row, else
+// the row's first cell index and its x range [x0, x1], clamped to the grid.
+template <int DIM>
+__device__ __forceinline__ bool row_chord(const Grid& g, const long long* ct, const float* fr,
+                                          float RR, float mg, long long y0, long long z0,
+                                          long long ny, long long rho, int64_t& rowbase,
+                                          long long& x0, long long& x1) {
+    long long dz = 0, dy = y0 + rho;
+    if (DIM == 3) {   // row counts are bounded by the grid's <= 2^24 cells
+        const int q = (int)rho / (int)ny;
+        dz = z0 + q;
+        dy = y0 + ((int)rho - q * (int)ny);
+    }
+    float ez = 0.f;
+    if (DIM == 3) {
+        ez = fmaxf(fmaxf((float)dz - fr[2], fr[2] - (float)dz - 1.f), 0.f);
+        ez = fmaxf(ez - mg, 0.f);
+    }
+    float ey = fmaxf(fmaxf((float)dy - fr[1], fr[1] - (float)dy - 1.f), 0.f);
+    ey = fmaxf(ey - mg, 0.f);
+    const float remz = RR * RR - ez * ez;
+    const float rem = remz - ey * ey;
+    if (!(remz > 0.f && rem > 0.f)) return false;
+    const float hx = sqrtf(rem) + mg;
+    x0 = max((long long)__float2int_rd(fr[0] - hx) + ct[0], 0LL);
+    x1 = min((long long)__float2int_rd(fr[0] + hx) + ct[0], (long long)g.n[0] - 1);
+    if (x0 > x1) return false;
+    rowbase = ((ct[2] + dz) * g.n[1] + (ct[1] + dy)) * (int64_t)g.n[0];
+    return true;
+}
+
+// The target's re-centred basis estimated from the sources' cell-sum pyramid (all G lanes of
+// the group call this together). At radius level k it reads level j = min(k, top), whose
+// entries span 2^j cells per axis, so the ball (3 or 2 cells per radius at k = 0) covers a
+// few entries per axis at every k: the entries of the ball's bounding box, split over the
+// lanes. Each entry contributes its count times the weight at its sources' mean position,
+// u = (mean - t) / r. c = the weighted mean of u; s^2 = the weighted variance per axis plus
+// that of a uniform entry, (2^j / cells per radius)^2 / 12. Returns (c, 1/s) rounded to
+// FP32, or the identity (0, 0, 0, 1) when |c|^2 <= recentre_min2 or the estimate is
+// degenerate: only markedly one-sided neighbourhoods change basis.
+template <int DIM, int G>
+__device__ __forceinline__ float4 estimate_basis(const AsmArgs& A, const long long* ct,
+                                                 const float* fr, const float* thi, float RR,
+                                                 float R0, float inv_r, int k, int gl,
+                                                 unsigned gmask) {
+    const float4 ident = make_float4(0.f, 0.f, 0.f, 1.f);
+    const int j = min(k, A.pyr_levels - 1);
+    const float4* lev = A.cpyr + A.pyr_off[j];
+    int lo[3] = {0, 0, 0}, ext[3] = {1, 1, 1}, nb[3] = {1, 1, 1};
+    bool empty = false;
+#pragma unroll
+    for (int d = 0; d < DIM; d++) {
+        nb[d] = (int)(((long long)A.g.n[d] + (1LL << j) - 1) >> j);
+        const float p = (float)ct[d] + fr[d];
+        // floor(x / 2^j) of the floored cell coordinates (arithmetic shifts floor negatives)
+        const int a = max(__float2int_rd(p - RR) >> j, 0);
+        const int b = min(__float2int_rd(p + RR) >> j, nb[d] - 1);
+        empty = empty || a > b;
+        lo[d] = a;
+        ext[d] = b - a + 1;
+    }
+    if (empty) return ident;
+    float s0 = 0.f, s1[3] = {0.f, 0.f, 0.f}, s2 = 0.f;
+    const int total = ext[0] * ext[1] * ext[2];
+    for (int i = gl; i < total; i += G) {
+        const int ix = i % ext[0], r = i / ext[0], iy = r % ext[1], iz = r / ext[1];
+        const int64_t idx =
+            ((int64_t)(lo[2] + iz) * nb[1] + (lo[1] + iy)) * (int64_t)nb[0] + (lo[0] + ix);
+        const float4 cs = lev[idx];
+        if (!(cs.w > 0.f)) continue;
+        const float inv_n = 1.f / cs.w;
+        float u[3] = {(cs.x * inv_n - thi[0]) * inv_r, (cs.y * inv_n - thi[1]) * inv_r,
+                      DIM == 3 ? (cs.z * inv_n - thi[2]) * inv_r : 0.f};
+        const float q2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        if (!(q2 < 1.f)) continue;
+        const float w = cs.w * weight_value<float>(A.weight, sqrtf(q2));
+        s0 += w;
+#pragma unroll
+        for (int d = 0; d < DIM; d++) s1[d] += w * u[d];
+        s2 += w * q2;
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(gmask, s0, o);
+#pragma unroll
+        for (int d = 0; d < DIM; d++) s1[d] += __shfl_xor_sync(gmask, s1[d], o);
+        s2 += __shfl_xor_sync(gmask, s2, o);
+    }
+    if (!(s0 > 0.f)) return ident;
+    float c[3] = {0.f, 0.f, 0.f}, cc = 0.f;
+#pragma unroll
+    for (int d = 0; d < DIM; d++) {
+        c[d] = s1[d] / s0;
+        cc += c[d] * c[d];
+    }
+    if (!(cc > A.recentre_min2)) return ident;
+    const float e = (float)(1 << j) / R0;
+    const float var = (s2 / s0 - cc) / (float)DIM + e * e / 12.f;
+    if (!(var > 1e-12f)) return ident;
+    return make_float4(c[0], c[1], c[2], 1.f / sqrtf(var));
+}
+
 template <int DIM, int DEG, bool MIXED, int MODE, int G, typename FT, int ACC = ACC_PLAIN>
 __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemble(AsmArgs A) {
     static_assert(ACC == ACC_PLAIN || (MIXED && MODE != MODE_COUNT), "blocked compensation: mixed moments only");
@@ -565,6 +682,30 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemb
             }
             const long long y0 = max((long long)__float2int_rd(fr[1] - RR), -ct[1]);
             const long long y1 = min((long long)__float2int_rd(fr[1] + RR), (long long)g.n[1] - 1 - ct[1]);
+            const long long ny = y1 >= y0 ? y1 - y0 + 1 : 0;
+            const long long nrows = ny * (DIM == 3 ? (z1 >= z0 ? z1 - z0 + 1 : 0) : 1);
+            // (before the sums are cleared, so that they are not live across it)
+            if constexpr (MIXED && ACC == ACC_BK && MODE != MODE_COUNT) {
+                // tier 1: this level's estimated basis, for the targets whose neighbourhood
+                // can be one-sided: a grown radius, or a ball that reaches past the grid
+                bool want = k > 0;
+#pragma unroll
+                for (int d = 0; d < DIM; d++) {
+                    const float p = (float)ct[d] + fr[d];
+                    want = want || p - RR < 0.f || p + RR > (float)g.n[d];
+                }
+                if (A.cpyr && !A.list) {
+                    const float4 eb =
+                        want ? estimate_basis<DIM, G>(A, ct, fr, thi, RR, R0, inv_r, k, gl, gmask)
+                             : make_float4(0.f, 0.f, 0.f, 1.f);
+                    bcv[0] = eb.x;
+                    bcv[1] = eb.y;
+                    bcv[2] = eb.z;
+                    bcv[3] = eb.w;
+                    const bool ident = eb.x == 0.f && eb.y == 0.f && eb.z == 0.f && eb.w == 1.f;
+                    bc = ident ? nullptr : bcv;
+                }
+            }
 #pragma unroll
             for (int i = 0; i < NA; i++) acc[i] = T(0);
 #pragma unroll
@@ -581,39 +722,15 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemb
             // group lays those ranges end to end, and the group streams the concatenated
             // candidates G per step, so steps are full across row ends. The loads of the
             // next step are issued before the current one is classified.
-            const long long ny = y1 >= y0 ? y1 - y0 + 1 : 0;
-            const long long nrows = ny * (DIM == 3 ? (z1 >= z0 ? z1 - z0 + 1 : 0) : 1);
             for (long long row0 = 0; row0 < nrows; row0 += G) {
                 int ra = 0, rlen = 0;
                 const long long rho = row0 + gl;
-                if (rho < nrows) {
-                    long long dz = 0, dy = y0 + rho;
-                    if (DIM == 3) {   // row counts are bounded by the grid's <= 2^24 cells
-                        const int q = (int)rho / (int)ny;
-                        dz = z0 + q;
-                        dy = y0 + ((int)rho - q * (int)ny);
-                    }
-                    float ez = 0.f;
-                    if (DIM == 3) {
-                        ez = fmaxf(fmaxf((float)dz - fr[2], fr[2] - (float)dz - 1.f), 0.f);
-                        ez = fmaxf(ez - mg, 0.f);
-                    }
-                    float ey = fmaxf(fmaxf((float)dy - fr[1], fr[1] - (float)dy - 1.f), 0.f);
-                    ey = fmaxf(ey - mg, 0.f);
-                    const float remz = RR * RR - ez * ez;
-                    const float rem = remz - ey * ey;
-                    if (remz > 0.f && rem > 0.f) {
-                        const float hx = sqrtf(rem) + mg;
-                        const long long x0 = max((long long)__float2int_rd(fr[0] - hx) + ct[0], 0LL);
-                        const long long x1 =
-                            min((long long)__float2int_rd(fr[0] + hx) + ct[0], (long long)g.n[0] - 1);
-                        if (x0 <= x1) {
-                            const int64_t rowbase =
-                                ((ct[2] + dz) * g.n[1] + (ct[1] + dy)) * (int64_t)g.n[0];
-                            ra = A.cell_start[rowbase + x0];
-                            rlen = A.cell_start[rowbase + x1 + 1] - ra;
-                        }
-                    }
+                int64_t rowbase;
+                long long x0, x1;
+                if (rho < nrows &&
+                    row_chord<DIM>(g, ct, fr, RR, mg, y0, z0, ny, rho, rowbase, x0, x1)) {
+                    ra = A.cell_start[rowbase + x0];
+                    rlen = A.cell_start[rowbase + x1 + 1] - ra;
                 }
                 int incl = rlen;
 #pragma unroll
@@ -803,6 +920,10 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemb
             }
             A.counts[t] = cnt;
             if (A.kexp_out) A.kexp_out[t] = k;
+            if constexpr (MIXED && ACC == ACC_BK && MODE != MODE_COUNT) {
+                if (A.basis_out && !A.list)
+                    A.basis_out[t] = make_float4(bcv[0], bcv[1], bcv[2], bcv[3]);
+            }
             if (MODE == MODE_MAP && !one_pass && A.cols && cnt != row_len) atomicOr(A.err, 1u);
         }
         if (MODE == MODE_MAP && one_pass) {
@@ -966,6 +1087,20 @@ __host__ __device__ inline float4 recentre_basis(const double* mom) {
     return make_float4((float)c[0], (float)c[1], (float)c[2], (float)(1.0 / sqrt(s2)));
 }
 
+// The re-centred basis for moments that were assembled in the basis b = (c_b, 1/s_b): their
+// weighted centroid c' and spread s' (offsets in b) give c = c_b + s_b c' and
+// 1/s = (1/s_b) (1/s'), rounded to FP32. From the identity this is recentre_basis itself.
+template <int DIM>
+__host__ __device__ inline float4 recentre_from(float4 b, const double* mom) {
+    const float4 r = recentre_basis<DIM>(mom);
+    if (is_target_centred(b)) return r;
+    if (is_target_centred(r)) return b;   // no usable spread in b: keep b
+    const double sb = 1.0 / (double)b.w;
+    return make_float4((float)((double)b.x + sb * (double)r.x),
+                       (float)((double)b.y + sb * (double)r.y),
+                       (float)((double)b.z + sb * (double)r.z), (float)((double)b.w * (double)r.w));
+}
+
 // a(u'_t), the basis at the target in the basis b: u'_t = (0 - c) / s with the FP32 (c, 1/s)
 template <int DIM, int DEG>
 __host__ __device__ inline void basis_at_target(float4 b, double* at) {
@@ -1007,6 +1142,7 @@ __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
                 bas = S.basis_in[wk];
                 recentred = !is_target_centred(bas);
                 if (recentred) basis_at_target<DIM, DEG>(bas, at);
+                if (recentred && S.n_recentred) atomicAdd(S.n_recentred, 1);
             }
             if (!solve_moments<DIM, DEG, MODE>(mom, S.lambda, S.tau, y, &val, &amp,
                                                recentred ? at : nullptr))
@@ -1037,7 +1173,7 @@ __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
                     const int pos = atomicAdd(S.n2, 1);
                     S.list2[pos] = (int32_t)t;
                     if (S.basis2)
-                        S.basis2[pos] = S.recentre ? recentre_basis<DIM>(mom)
+                        S.basis2[pos] = S.recentre ? recentre_from<DIM>(bas, mom)
                                                    : make_float4(0.f, 0.f, 0.f, 1.f);
                 } else {
                     S.list3[atomicAdd(S.n3, 1)] = (int32_t)t;
@@ -1047,9 +1183,10 @@ __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
         }
         // operator rows: 0 = FP32; 1 = FP32 u, w as in the moments, FP64 monomials and dot;
         // 2 = everything in FP64 (tier 3: y belongs to the exact FP64 moments);
-        // 3 = as 1 in the re-centred basis rc[t]
+        // 3 = as 1 in the re-centred basis rc[t]; 4 = as 0 in the re-centred basis rc[t]
         if (MODE == MODE_MAP && S.flags) {
-            const int flag = recentred ? 3 : (S.tier == 3 ? 2 : (amp > AMP_SHAPE ? 1 : 0));
+            const int flag = recentred ? (amp > AMP_SHAPE ? 3 : 4)
+                                       : (S.tier == 3 ? 2 : (amp > AMP_SHAPE ? 1 : 0));
             S.flags[t] = (int8_t)flag;
             if (recentred && S.rc) S.rc[t] = bas;
         }
@@ -1115,7 +1252,7 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
             for (int d = 0; d < DIM; d++) tx[d] = S.tx64[d * S.nt + t];
         }
         T bcv[4] = {T(0), T(0), T(0), T(1)};
-        if (flag == 3) {   // re-centred basis (mixed tier 2, FP64 refine pass)
+        if (flag >= 3) {   // re-centred basis (mixed tiers 1 and 2, FP64 refine pass)
             const float4 b4 = S.rc[t];
             bcv[0] = b4.x;
             bcv[1] = b4.y;
@@ -1196,9 +1333,9 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
             else qv = sqrt(d2) * inv_r;
             const T w = weight_value<T>(S.weight, qv);
             T u[3];
-            basis_offsets<DIM, T>(dx, inv_r, flag == 3 ? bcv : nullptr, u);
+            basis_offsets<DIM, T>(dx, inv_r, flag >= 3 ? bcv : nullptr, u);
             if constexpr (MIXED) {
-                if (flag) {
+                if (flag == 1 || flag == 3) {
                     // sensitive row (1), or a row in a re-centred basis (3): the same FP32 u
                     // and w as the moments; the monomials (degree <= 2) as exact FP32 pairs
                     // (TwoProduct by FMA) and the dot product with y in double-FP32

@@ -120,6 +120,18 @@ void bbox_combine(const double* hpart, int64_t n, double* lo, double* hi, uint64
 void sort_points(const Grid& g, const double* pts, int64_t n, bool with_start, bool with_hl,
                  SortedPoints& out, cudaStream_t s, bool with_cell = false);
 
+// Cell-sum pyramid of the sorted sources S (built with_start and with_hl). Level 0 holds per
+// grid cell (sum of the sources' FP32 hi coordinates per axis, relative to g.lo; count);
+// level j + 1 holds the sums over blocks of 2 x 2 (x 2) level-j entries, so an entry of level
+// j covers 2^j cells per axis; level j has ceil(n_d / 2^j) entries along axis d, row-major,
+// and starts at off[j]. pyramid_levels(g) levels, the last a single entry; pyramid_size
+// gives the total entries (and fills off). Sums run in a fixed order (reproducible).
+constexpr int PYR_MAX = 26;
+int pyramid_levels(const Grid& g);
+int64_t pyramid_size(const Grid& g, int levels, int64_t* off);
+void cell_pyramid(const Grid& g, const SortedPoints& S, int levels, const int64_t* off,
+                  float4* out, cudaStream_t s);
+
 // Stable LSD radix sort (8-bit digits) of (key, value) pairs with keys < nkeys; k1/v1 are
 // scratch of n entries. Returns the buffer (v0 or v1) holding the values in key order.
 uint32_t* radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t n,

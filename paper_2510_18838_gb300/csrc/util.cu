@@ -101,22 +101,40 @@ Grid make_grid(int dim, const double* lo, const double* hi, double radius, int64
 // ------------------------------------------------------------------------------------
 // Per-block boxes: block b writes part[8 b + {0..2}] = minima, [3..5] = maxima, [6] = the
 // number of non-finite coordinates it saw. One launch, no initialisation; the host combines
-// the partial boxes after its copy (bbox_combine).
-__global__ void __launch_bounds__(256) k_bbox_partial(int dim, const double* __restrict__ pts,
-                                                      int64_t n, double* __restrict__ part) {
+// the partial boxes after its copy (bbox_combine). Each thread loads BB_UNROLL points per
+// coordinate plane before it reduces them, so that enough loads are in flight for the
+// kernel to stream at HBM speed with one block per SM.
+constexpr int BB_UNROLL = 4;
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_bbox_partial(const double* __restrict__ pts, int64_t n,
+                                                      double* __restrict__ part) {
     __shared__ double sh[8][7];
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     double nb = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        for (int d = 0; d < dim; d++) {
-            const double x = pts[d * n + i];
-            if (!isfinite(x)) {
-                nb += 1.0;
-                continue;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n;
+         i0 += BB_UNROLL * stride) {
+        double x[DIM][BB_UNROLL];
+#pragma unroll
+        for (int d = 0; d < DIM; d++)
+#pragma unroll
+            for (int u = 0; u < BB_UNROLL; u++) {
+                const int64_t i = i0 + u * stride;
+                x[d][u] = i < n ? pts[d * n + i] : 0.0;
             }
-            lo[d] = fmin(lo[d], x);
-            hi[d] = fmax(hi[d], x);
+#pragma unroll
+        for (int u = 0; u < BB_UNROLL; u++) {
+            if (i0 + u * stride >= n) break;
+#pragma unroll
+            for (int d = 0; d < DIM; d++) {
+                if (!isfinite(x[d][u])) {
+                    nb += 1.0;
+                    continue;
+                }
+                lo[d] = fmin(lo[d], x[d][u]);
+                hi[d] = fmax(hi[d], x[d][u]);
+            }
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -145,13 +163,19 @@ __global__ void __launch_bounds__(256) k_bbox_partial(int dim, const double* __r
 }
 
 int bbox_blocks(int64_t n) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms()));
+    const int64_t per_block = 256 * BB_UNROLL;
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + per_block - 1) / per_block,
+                                                       (int64_t)num_sms()));
 }
 
 void launch_bbox_partials(int dim, const double* pts, int64_t n, double* part, cudaStream_t s) {
     if (n <= 0) return;
+    if (dim < 1 || dim > 3) fail(PCMS_ERR_INVALID_ARG, "internal: bounding box of dim > 3");
     PCMS_TRACE("bbox_partial", s);
-    k_bbox_partial<<<bbox_blocks(n), 256, 0, s>>>(dim, pts, n, part);
+    const int nb = bbox_blocks(n);
+    if (dim == 1) k_bbox_partial<1><<<nb, 256, 0, s>>>(pts, n, part);
+    else if (dim == 2) k_bbox_partial<2><<<nb, 256, 0, s>>>(pts, n, part);
+    else k_bbox_partial<3><<<nb, 256, 0, s>>>(pts, n, part);
     PCMS_LAUNCH_CHECK("bbox_partial");
 }
 
@@ -483,6 +507,92 @@ __global__ void k_gather_sorted(int dim, Grid g, const double* __restrict__ pts,
             }
         }
     }
+}
+
+// one warp per cell: lanes take the cell's sources in strides of 32, then a fixed
+// butterfly reduction
+__global__ void k_cell_sums(int dim, int64_t ncell, const int32_t* __restrict__ start,
+                            const float4* __restrict__ hl0, float4* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < ncell;
+         c += nwarps) {
+        const int a = start[c], b = start[c + 1];
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+        for (int i = a + lane; i < b; i += 32) {
+            const float4 h = hl0[i];
+            sx += h.x;
+            sy += h.y;
+            if (dim == 3) sz += h.z;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        }
+        if (lane == 0) out[c] = make_float4(sx, sy, sz, (float)(b - a));
+    }
+}
+
+// level j + 1 from level j: each block sums its (up to) 2^dim children in a fixed order
+__global__ void k_pyr_up(int dim, int64_t nx, int64_t ny, int64_t nz, int64_t mx, int64_t my,
+                         int64_t mz, const float4* __restrict__ in, float4* __restrict__ out) {
+    const int64_t nout = mx * my * mz;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nout;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t bx = i % mx, byz = i / mx, by = byz % my, bz = byz / my;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int c = 0; c < (1 << dim); c++) {
+            const int64_t x = 2 * bx + (c & 1), y = 2 * by + ((c >> 1) & 1),
+                          z = 2 * bz + ((c >> 2) & 1);
+            if (x >= nx || y >= ny || z >= nz) continue;
+            const float4 v = in[(z * ny + y) * nx + x];
+            acc.x += v.x;
+            acc.y += v.y;
+            acc.z += v.z;
+            acc.w += v.w;
+        }
+        out[i] = acc;
+    }
+}
+
+int pyramid_levels(const Grid& g) {
+    int64_t m = std::max<int64_t>(g.n[0], std::max<int64_t>(g.n[1], g.n[2]));
+    int L = 1;
+    while (L < PYR_MAX && m > 1) {
+        m = (m + 1) / 2;
+        L++;
+    }
+    return L;
+}
+
+int64_t pyramid_size(const Grid& g, int levels, int64_t* off) {
+    int64_t n[3] = {g.n[0], g.n[1], g.n[2]}, tot = 0;
+    for (int j = 0; j < levels; j++) {
+        if (off) off[j] = tot;
+        tot += n[0] * n[1] * n[2];
+        for (int d = 0; d < g.dim; d++) n[d] = (n[d] + 1) / 2;
+    }
+    return tot;
+}
+
+void cell_pyramid(const Grid& g, const SortedPoints& S, int levels, const int64_t* off,
+                  float4* out, cudaStream_t s) {
+    if (g.ncell <= 0) return;
+    PCMS_TRACE("grid_cell_pyramid", s);
+    const int64_t blocks = std::min<int64_t>((g.ncell + 7) / 8, (int64_t)num_sms() * 16);
+    k_cell_sums<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(
+        g.dim, g.ncell, S.cell_start.as<int32_t>(), S.hl0.as<float4>(), out);
+    int64_t n[3] = {g.n[0], g.n[1], g.n[2]};
+    for (int j = 1; j < levels; j++) {
+        int64_t m[3] = {n[0], n[1], n[2]};
+        for (int d = 0; d < g.dim; d++) m[d] = (n[d] + 1) / 2;
+        const int64_t nout = m[0] * m[1] * m[2];
+        k_pyr_up<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((nout + 255) / 256, 4096)), 256, 0,
+                   s>>>(g.dim, n[0], n[1], n[2], m[0], m[1], m[2], out + off[j - 1], out + off[j]);
+        for (int d = 0; d < 3; d++) n[d] = m[d];
+    }
+    PCMS_LAUNCH_CHECK("cell_pyramid");
 }
 
 uint32_t* radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t n,

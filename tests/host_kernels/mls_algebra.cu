@@ -187,6 +187,13 @@ extern "C" void hk_recentre_basis(int dim, const double* mom, float* out) {
     out[0] = b.x; out[1] = b.y; out[2] = b.z; out[3] = b.w;
 }
 
+// the tier-2 basis k_solve derives from moments assembled in the basis b (tier 1's estimate)
+extern "C" void hk_recentre_from(int dim, const float* b, const double* mom, float* out) {
+    const float4 bb = make_float4(b[0], b[1], b[2], b[3]);
+    const float4 r = dim == 2 ? recentre_from<2>(bb, mom) : recentre_from<3>(bb, mom);
+    out[0] = r.x; out[1] = r.y; out[2] = r.z; out[3] = r.w;
+}
+
 extern "C" int hk_mono(int dim, int p, int* e) {
     Exp3 x = mono_exp(dim, p);
     e[0] = x.e[0];

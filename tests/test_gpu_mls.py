@@ -203,6 +203,36 @@ def test_mixed_growth_gaussian_mixture(P):
     assert kx.max() >= 1
 
 
+def test_mixed_dense_targets_in_an_estimated_basis(P):
+    """The blocked-compensation plan (mean count ~1250): one-sided targets (grown radii at the
+    edge of a cluster, the domain boundary) are assembled in tier 1 in a re-centred basis
+    estimated from the source cells. Values, statuses and doublings against the oracle, for
+    the one-shot transfer and the operator; the estimate takes the place of most tier-2
+    walks."""
+    src = W.gaussian_mixture_points(400_000, 301, 302)
+    tgt = W.uniform_points(3000, 2, 303)
+    r = 0.01 * np.sqrt(10.0)
+    f32 = W.sincos_field(src).astype(np.float32)
+    o = oracle.mls(src, tgt, f32.astype(np.float64), 2, r, min_neighbors=10, mode="grid")
+    ok = o["status"] == 0
+    P.trace_enable(True, count_only=True)
+    out, st = P.mls_transfer(cu(src), cu(tgt), cu(f32), 2, r, precision="mixed",
+                             min_neighbors=10)
+    tr = P.trace_read()
+    P.trace_enable(False)
+    assert np.array_equal(host(st), o["status"])
+    assert normwise_err(host(out), o["values"], ok) <= TOL_MIXED
+    n_rc = tr.get("count:mls_tier1_recentred_solves", (0, 0))[0]
+    n_t2 = tr.get("count:mls_tier2_targets", (0, 0))[0]
+    assert n_rc >= 50 and n_t2 < n_rc
+    m = P.create_map(cu(src), cu(tgt), 2, r, precision="mixed", min_neighbors=10)
+    *_, kx = (host(x) for x in m.export())
+    assert np.array_equal(kx, o["kexp"])
+    v = host(m.apply(cu(f32[None]))).reshape(o["values"].shape)
+    assert normwise_err(v, o["values"], ok) <= TOL_MIXED
+    m.destroy()
+
+
 @pytest.mark.parametrize("dim,prec,deg", [(2, "fp64", 1), (2, "mixed", 2), (3, "mixed", 1),
                                           (3, "fp64", 2)])
 def test_global_growth_matches_oracle(P, dim, prec, deg):

@@ -33,6 +33,8 @@ def hk(tmp_path_factory):
     L.hk_mls_f32.argtypes = [I, I, I, I, I, P, P, ctypes.c_float, D, D, P, P, I]
     L.hk_recentre_basis.restype = None
     L.hk_recentre_basis.argtypes = [I, P, P]
+    L.hk_recentre_from.restype = None
+    L.hk_recentre_from.argtypes = [I, P, P, P]
     L.hk_mono.restype = I
     L.hk_mono.argtypes = [I, I, P]
     L.hk_mono_prod.restype = I
@@ -221,6 +223,46 @@ def test_recentre_basis_is_weighted_centroid_and_spread(hk, dim):
     one[0] = 2.0
     hk.hk_recentre_basis(dim, _p(one), _p(got))
     assert list(got) == [0.0, 0.0, 0.0, 1.0]
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_recentre_from_an_estimated_basis(hk, dim):
+    """Tier 1 may assemble in an estimated basis b = (c_b, 1/s_b); the basis handed on to
+    tier 2 is then the weighted centroid and spread of the neighbours in the original
+    offsets, composed from the moments in b. From the identity it is recentre_basis
+    bit for bit."""
+    dx, u, w, A, r = _lopsided(dim, 2, 300, 60 + dim)
+    nm = _n_moments(dim, 2)
+    mom = np.zeros(nm + 10)
+    out = np.zeros(15)
+    hk.hk_mls(dim, 2, 0, 0, len(dx), _p(np.ascontiguousarray(dx)), None, 1.0 / r, 0.0, 1e-14,
+              _p(mom), _p(out), 0, None)
+    ident = np.array([0, 0, 0, 1], np.float32)
+    a = np.zeros(4, np.float32)
+    b = np.zeros(4, np.float32)
+    hk.hk_recentre_basis(dim, _p(mom), _p(a))
+    hk.hk_recentre_from(dim, _p(ident), _p(mom), _p(b))
+    assert np.array_equal(a, b)
+    # moments of the same neighbours in a rough estimate of the basis
+    c = (w[:, None] * u).sum(0) / w.sum()
+    s = np.sqrt((w * ((u - c) ** 2).sum(1)).sum() / (dim * w.sum()))
+    est = np.zeros(4, np.float32)
+    est[:dim] = (c + 0.07 * np.arange(1, dim + 1)).astype(np.float32)
+    est[3] = np.float32(1.0 / (1.6 * s))
+    up = (u - est[:dim].astype(np.float64)) * np.float64(est[3])
+    exps_ = [e for e in itertools.product(range(5), repeat=dim) if sum(e) <= 4]
+    exps_.sort(key=lambda e: (sum(e), tuple(-x for x in e)))
+    mom_b = np.array([(w * np.prod(up ** np.array(e), axis=1)).sum() for e in exps_])
+    assert len(mom_b) == nm
+    got = np.zeros(4, np.float32)
+    hk.hk_recentre_from(dim, _p(est), _p(mom_b), _p(got))
+    np.testing.assert_allclose(got[:dim], c, rtol=1e-5, atol=1e-6)
+    assert got[3] == pytest.approx(1.0 / s, rel=1e-5)
+    # a degenerate spread in b keeps b
+    one = np.zeros(nm)
+    one[0] = 2.0
+    hk.hk_recentre_from(dim, _p(est), _p(one), _p(got))
+    assert np.array_equal(got, est)
 
 
 def _f32_case(kind_of, n, seed):
