@@ -1181,7 +1181,8 @@ __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
                 continue;   // a later tier writes this target
             }
         }
-        // operator rows: 0 = FP32; 1 = FP32 u, w as in the moments, FP64 monomials and dot;
+        // operator rows: 0 = FP32; 1 = FP32 u, w as in the moments, exact FP32 monomial
+        // products and a double-FP32 dot product with y;
         // 2 = everything in FP64 (tier 3: y belongs to the exact FP64 moments);
         // 3 = as 1 in the re-centred basis rc[t]; 4 = as 0 in the re-centred basis rc[t]
         if (MODE == MODE_MAP && S.flags) {
