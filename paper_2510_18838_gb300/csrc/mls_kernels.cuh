@@ -1114,6 +1114,194 @@ __host__ __device__ inline void basis_at_target(float4 b, double* at) {
     });
 }
 
+// The mixed tiers' solve without the FP64 pipe. G y = a_t is solved by iterative refinement:
+// an FP32 LDL^T of G's leading FP32 parts gives each correction, and every residual
+// a_t - G y is formed in double-FP32 arithmetic (TwoProduct by FMA, TwoSum) from the moments
+// as stored (plain FP32 sums are exact FP32 values; blocked sums are FP32 pairs), with y kept
+// as an FP32 pair. An error e in y moves c_0 (and an operator row's value) by about e amp, so
+// the refinement runs until a correction is below 2^-27 / amp of y, far below the moments'
+// own FP32 error (about 2^-24 amp). The attainable accuracy is about kappa 2^-48.
+// Returns
+//   1  solved: y = yh + yl, *c0 (FUSED) and *amp as solve_moments;
+//   2  not refined, because amp (from the FP32 solve) exceeds amp_accept, the tier's
+//      acceptance bound, by more than the FP32 solve's error: the caller hands the target on;
+//   0  declined: a pivot of the FP32 factorization is not above 1e-4 G_kk, which exceeds every
+//      guard's threshold by more than the FP32 factorization's error (about 2 m 2^-24 G_kk),
+//      or REFINE_STEPS steps do not converge. The caller then solves in FP64, so a target
+//      accepted here is one the FP64 guard accepts, and decisions near a threshold are the
+//      FP64 factorization's.
+__host__ __device__ __forceinline__ float mom_hi(float v) { return v; }
+__host__ __device__ __forceinline__ float mom_lo(float) { return 0.f; }
+__host__ __device__ __forceinline__ float mom_hi(float2 v) { return v.x; }
+__host__ __device__ __forceinline__ float mom_lo(float2 v) { return v.y; }
+__host__ __device__ __forceinline__ float rcp32(float x) {
+#ifdef __CUDA_ARCH__
+    return __frcp_rn(x);
+#else
+    return 1.f / x;
+#endif
+}
+
+constexpr int REFINE_STEPS = 6;
+constexpr float REFINE_PIVOT = 1e-4f;
+
+template <int DIM, int DEG, int MODE, typename MT>
+__host__ __device__ __forceinline__ int solve_moments_refined(const MT* mt, const double* at,
+                                                              double amp_accept, float* yh,
+                                                              float* yl, double* c0,
+                                                              double* amp) {
+    constexpr int NM = mono_count(DIM, 2 * DEG);
+    constexpr int M = mono_count(DIM, DEG);
+    constexpr int NP = M * (M + 1) / 2;
+    float L[NP];
+    sfor<M>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        sfor<k + 1>([&](auto Lx) {
+            constexpr int l = decltype(Lx)::value;
+            constexpr int kl = mono_prod(DIM, k, l);
+            L[k * (k + 1) / 2 + l] = mom_hi(mt[kl]);
+        });
+    });
+    float invd[M], diag[M];
+    bool ok = true;
+    sfor<M>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        diag[k] = L[k * (k + 1) / 2 + k];
+        sfor<k>([&](auto Jx) {
+            constexpr int j = decltype(Jx)::value;
+            float sv = L[k * (k + 1) / 2 + j];
+            sfor<j>([&](auto Ix) {
+                constexpr int i = decltype(Ix)::value;
+                sv -= L[k * (k + 1) / 2 + i] * (L[j * (j + 1) / 2 + i] * L[i * (i + 1) / 2 + i]);
+            });
+            L[k * (k + 1) / 2 + j] = sv * invd[j];
+        });
+        float dk = L[k * (k + 1) / 2 + k];
+        sfor<k>([&](auto Jx) {
+            constexpr int j = decltype(Jx)::value;
+            const float lkj = L[k * (k + 1) / 2 + j];
+            dk -= lkj * lkj * L[j * (j + 1) / 2 + j];
+        });
+        ok = ok && (dk > REFINE_PIVOT * diag[k]);
+        L[k * (k + 1) / 2 + k] = dk;
+        invd[k] = rcp32(dk);
+    });
+    if (!ok) return 0;
+    // x = (L D L^T)^-1 b in FP32
+    auto ldl_solve = [&](const float* b, float* x) {
+        float w[M];
+        sfor<M>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            float a = b[k];
+            sfor<k>([&](auto Jx) {
+                constexpr int j = decltype(Jx)::value;
+                a -= L[k * (k + 1) / 2 + j] * w[j];
+            });
+            w[k] = a;
+        });
+        sfor<M>([&](auto K) {
+            constexpr int k = M - 1 - decltype(K)::value;
+            float a = w[k] * invd[k];
+            sfor<M - 1 - k>([&](auto Jx) {
+                constexpr int j = k + 1 + decltype(Jx)::value;
+                a -= L[j * (j + 1) / 2 + k] * x[j];
+            });
+            x[k] = a;
+        });
+    };
+    float ah[M], al[M];
+#pragma unroll
+    for (int k = 0; k < M; k++) {
+        if (at) {
+            ah[k] = (float)at[k];
+            al[k] = (float)(at[k] - (double)ah[k]);
+        } else {
+            ah[k] = k == 0 ? 1.f : 0.f;
+            al[k] = 0.f;
+        }
+    }
+    ldl_solve(ah, yh);
+    auto amp_of = [&]() {
+        float sf = 0.f;
+#pragma unroll
+        for (int k = 0; k < M; k++) sf += fabsf(yh[k]) * sqrtf(fmaxf(diag[k], 0.f));
+        return sf * sqrtf(fmaxf(diag[0], 0.f));
+    };
+    const float amp0 = amp_of();
+    if (!(amp0 <= 1e30f)) return 0;
+    if ((double)amp0 > 1.01 * amp_accept) {
+        *amp = (double)amp0;
+        return 2;
+    }
+    const float tol = 7.450580596923828e-09f / fmaxf(amp0, 1.f);   // 2^-27 / amp
+#pragma unroll
+    for (int k = 0; k < M; k++) yl[k] = 0.f;
+    bool conv = false;
+    for (int it = 0; it < REFINE_STEPS && !conv; it++) {
+        float rh[M];
+        sfor<M>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            float sh = ah[k], sl = al[k];
+            sfor<M>([&](auto Lx) {
+                constexpr int l = decltype(Lx)::value;
+                constexpr int kl = mono_prod(DIM, k, l);
+                const MT g = mt[kl];
+                const float gh = mom_hi(g), gll = mom_lo(g);
+                const float ph = gh * yh[l];
+                const float pl = fmaf(gh, yh[l], -ph) + (gh * yl[l] + gll * yh[l]);
+                float s2, e2;
+                two_sum32(sh, -ph, s2, e2);
+                sl = (sl - pl) + e2;
+                sh = s2;
+            });
+            rh[k] = sh + sl;
+        });
+        float dy[M];
+        ldl_solve(rh, dy);
+        float dmax = 0.f, ymax = 0.f;
+#pragma unroll
+        for (int k = 0; k < M; k++) {
+            float s2, e2;
+            two_sum32(yh[k], dy[k], s2, e2);
+            const float lo = yl[k] + e2;
+            yh[k] = s2 + lo;
+            yl[k] = lo - (yh[k] - s2);
+            dmax = fmaxf(dmax, fabsf(dy[k]));
+            ymax = fmaxf(ymax, fabsf(yh[k]));
+        }
+        conv = dmax <= tol * ymax;
+    }
+    if (!conv) return 0;
+    if (MODE == MODE_FUSED) {   // c_0 = y^T g, g the right-hand side moments, as a pair
+        float ch = 0.f, cl = 0.f;
+#pragma unroll
+        for (int k = 0; k < M; k++) {
+            const MT g = mt[NM + k];
+            const float gh = mom_hi(g), gll = mom_lo(g);
+            const float ph = gh * yh[k];
+            const float pl = fmaf(gh, yh[k], -ph) + (gh * yl[k] + gll * yh[k]);
+            float s2, e2;
+            two_sum32(ch, ph, s2, e2);
+            cl = (cl + pl) + e2;
+            ch = s2;
+        }
+        *c0 = (double)ch + (double)cl;
+    }
+    *amp = (double)amp_of();
+    return 1;
+}
+
+// A tier's acceptance bound on amp for a target of n neighbours (the tier table above),
+// evaluated in FP32: the bound is a calibrated constant, not a precision-critical quantity.
+__host__ __device__ __forceinline__ double amp_bound(int acc, int n, int group) {
+    const float nf = (float)n;
+    if (acc == ACC_PLAIN) {
+        const float g = (float)group;
+        return (double)((float)AMP_T1 / (1.f + sqrtf(nf / (3.f * g * g))));
+    }
+    return (double)((float)AMP_BK * sqrtf(nf));
+}
+
 template <int DIM, int DEG, int MODE, typename MT>
 __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
     constexpr int NM = mono_count(DIM, 2 * DEG);
@@ -1129,14 +1317,14 @@ __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
         double val = 0.0, amp = 0.0;
         double y[M];
         double mom[NACC];
+        float yh[M], yl[M];   // the refined FP32 solve's y (mixed tiers), as pairs
+        bool refined = false;
         float4 bas = make_float4(0.f, 0.f, 0.f, 1.f);
         bool recentred = false;
+        const MT* src = (const MT*)S.mom + (S.list ? wk : t) * NACCP;
         if (cnt < M) {
             st = PCMS_TARGET_UNDERDETERMINED;
         } else {
-            const MT* src = (const MT*)S.mom + (S.list ? wk : t) * NACCP;
-#pragma unroll
-            for (int i = 0; i < NACC; i++) mom[i] = mom_value(src[i]);
             double at[M];
             if (S.basis_in) {
                 bas = S.basis_in[wk];
@@ -1144,9 +1332,21 @@ __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
                 if (recentred) basis_at_target<DIM, DEG>(bas, at);
                 if (recentred && S.n_recentred) atomicAdd(S.n_recentred, 1);
             }
-            if (!solve_moments<DIM, DEG, MODE>(mom, S.lambda, S.tau, y, &val, &amp,
-                                               recentred ? at : nullptr))
-                st = PCMS_TARGET_ILL_CONDITIONED;
+            if constexpr (!std::is_same<MT, double>::value) {
+                if (S.lambda == 0.0) {
+                    const double acc_amp = amp_bound(S.acc, cnt, S.group);
+                    const int rs = solve_moments_refined<DIM, DEG, MODE, MT>(
+                        src, recentred ? at : nullptr, acc_amp, yh, yl, &val, &amp);
+                    refined = rs != 0;
+                }
+            }
+            if (!refined) {
+#pragma unroll
+                for (int i = 0; i < NACC; i++) mom[i] = mom_value(src[i]);
+                if (!solve_moments<DIM, DEG, MODE>(mom, S.lambda, S.tau, y, &val, &amp,
+                                                   recentred ? at : nullptr))
+                    st = PCMS_TARGET_ILL_CONDITIONED;
+            }
         }
         if (S.tier == 4 && st != PCMS_TARGET_OK) continue;   // keep the first FP64 solve
         if (S.tier == 3 && S.refine64 && st == PCMS_TARGET_OK && amp > AMP_FP64) {
@@ -1156,15 +1356,7 @@ __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
         }
         if (S.tier < 3 && st != PCMS_TARGET_UNDERDETERMINED) {
             bool ok = st == PCMS_TARGET_OK;
-            if (ok) {
-                const double n = (double)cnt;
-                if (S.acc == ACC_PLAIN) {
-                    const double g = (double)S.group;
-                    ok = amp * (1.0 + sqrt(n / (3.0 * g * g))) <= AMP_T1;
-                } else {
-                    ok = amp <= AMP_BK * sqrt(n);
-                }
-            }
+            if (ok) ok = amp <= amp_bound(S.acc, cnt, S.group);
             if (!ok) {
                 // tier 2 only helps if it differs from this pass: a plain tier 1, or a
                 // re-centred basis
@@ -1172,6 +1364,10 @@ __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
                 if (to2) {
                     const int pos = atomicAdd(S.n2, 1);
                     S.list2[pos] = (int32_t)t;
+                    if (refined) {
+#pragma unroll
+                        for (int i = 0; i < NACC; i++) mom[i] = mom_value(src[i]);
+                    }
                     if (S.basis2)
                         S.basis2[pos] = S.recentre ? recentre_from<DIM>(bas, mom)
                                                    : make_float4(0.f, 0.f, 0.f, 1.f);
@@ -1198,6 +1394,11 @@ __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
             if (S.out_is_double) ((double*)S.out)[o] = v;
             else ((float*)S.out)[o] = (float)v;
             if (S.status) S.status[o] = (int8_t)st;
+        } else if (refined) {
+            // mixed rows of flags 0, 1, 3 and 4 read y as pairs only (k_shape)
+#pragma unroll
+            for (int k = 0; k < M; k++) S.yf[t * M + k] = make_float2(yh[k], yl[k]);
+            S.status[t] = (int8_t)st;
         } else {
 #pragma unroll
             for (int k = 0; k < M; k++) {

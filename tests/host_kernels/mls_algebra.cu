@@ -187,6 +187,41 @@ extern "C" void hk_recentre_basis(int dim, const double* mom, float* out) {
     out[0] = b.x; out[1] = b.y; out[2] = b.z; out[3] = b.w;
 }
 
+// The mixed tiers' refined FP32 solve on stored moments: pairs = 0 takes mom_hi as FP32
+// sums, 1 as (hi, lo) pairs from mom_hi and mom_lo. at = a_t or null (e_1).
+template <int DIM, int DEG, int MODE, typename MT>
+static int refined_t(const MT* mt, const double* at, double amp_accept, float* yh, float* yl,
+                     double* c0, double* amp) {
+    return solve_moments_refined<DIM, DEG, MODE, MT>(mt, at, amp_accept, yh, yl, c0, amp);
+}
+
+extern "C" int hk_solve_refined(int dim, int deg, int fused, int pairs, int nacc,
+                                const float* mom_hi, const float* mom_lo, const double* at,
+                                double amp_accept, float* yh, float* yl, double* c0,
+                                double* amp) {
+    float m1[64];
+    float2 m2[64];
+    if (nacc > 64) return -1;
+    for (int i = 0; i < nacc; i++) {
+        m1[i] = mom_hi[i];
+        m2[i] = make_float2(mom_hi[i], mom_lo[i]);
+    }
+#define HK_R(D, K, MODE)                                                       \
+    return pairs ? refined_t<D, K, MODE, float2>(m2, at, amp_accept, yh, yl, c0, amp)      \
+                 : refined_t<D, K, MODE, float>(m1, at, amp_accept, yh, yl, c0, amp)
+#define HK_RM(D, K)                          \
+    if (fused) { HK_R(D, K, MODE_FUSED); }   \
+    HK_R(D, K, MODE_MAP)
+    if (dim == 2) {
+        if (deg == 1) { HK_RM(2, 1); }
+        HK_RM(2, 2);
+    }
+    if (deg == 1) { HK_RM(3, 1); }
+    HK_RM(3, 2);
+#undef HK_RM
+#undef HK_R
+}
+
 // the tier-2 basis k_solve derives from moments assembled in the basis b (tier 1's estimate)
 extern "C" void hk_recentre_from(int dim, const float* b, const double* mom, float* out) {
     const float4 bb = make_float4(b[0], b[1], b[2], b[3]);

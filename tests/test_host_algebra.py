@@ -33,6 +33,8 @@ def hk(tmp_path_factory):
     L.hk_mls_f32.argtypes = [I, I, I, I, I, P, P, ctypes.c_float, D, D, P, P, I]
     L.hk_recentre_basis.restype = None
     L.hk_recentre_basis.argtypes = [I, P, P]
+    L.hk_solve_refined.restype = I
+    L.hk_solve_refined.argtypes = [I, I, I, I, I, P, P, P, D, P, P, P, P]
     L.hk_recentre_from.restype = None
     L.hk_recentre_from.argtypes = [I, P, P, P]
     L.hk_mono.restype = I
@@ -263,6 +265,114 @@ def test_recentre_from_an_estimated_basis(hk, dim):
     one[0] = 2.0
     hk.hk_recentre_from(dim, _p(est), _p(one), _p(got))
     assert np.array_equal(got, est)
+
+
+def _gram(dim, deg, mom):
+    """The moment matrix G_kl = mom[index of monomial k * monomial l] (graded-lex order)."""
+    ex = sorted((e for e in itertools.product(range(2 * deg + 1), repeat=dim) if sum(e) <= 2 * deg),
+                key=lambda e: (sum(e), tuple(-x for x in e)))
+    basis = [e for e in ex if sum(e) <= deg]
+    idx = {e: i for i, e in enumerate(ex)}
+    return np.array([[mom[idx[tuple(np.add(a, b))]] for b in basis] for a in basis])
+
+
+def _refined(hk, dim, deg, fused, pairs, mom, at=None, amp_accept=1e30):
+    m = mono = len([e for e in itertools.product(range(deg + 1), repeat=dim) if sum(e) <= deg])
+    nm = _n_moments(dim, deg)
+    nacc = nm + m if fused else nm
+    hi = np.asarray(mom[:nacc], np.float64).astype(np.float32)
+    lo = (np.asarray(mom[:nacc]) - hi.astype(np.float64)).astype(np.float32) if pairs \
+        else np.zeros(nacc, np.float32)
+    yh, yl = np.zeros(m, np.float32), np.zeros(m, np.float32)
+    c0, amp = np.zeros(1), np.zeros(1)
+    atp = None if at is None else _p(np.ascontiguousarray(at, np.float64))
+    rc = hk.hk_solve_refined(dim, deg, fused, pairs, nacc, _p(hi), _p(lo), atp,
+                             float(amp_accept), _p(yh), _p(yl), _p(c0), _p(amp))
+    stored = hi.astype(np.float64) + lo.astype(np.float64)
+    return rc, yh.astype(np.float64) + yl.astype(np.float64), c0[0], amp[0], stored
+
+
+@pytest.mark.parametrize("dim,deg,fused,pairs",
+                         [(2, 2, 1, 1), (2, 2, 0, 0), (3, 2, 0, 0), (3, 2, 1, 1), (2, 1, 0, 0),
+                          (3, 1, 1, 0), (2, 1, 1, 1)])
+def test_refined_fp32_solve_reaches_the_exact_solution(hk, dim, deg, fused, pairs):
+    """The mixed tiers solve the stored FP32 moments with an FP32 factorization and
+    double-FP32 refinement. On well-spread neighbourhoods y must reach the exact solution of
+    that FP32-valued system to 2^-27 / amp relative (what moves c_0 by at most 2^-27 of the
+    field; an FP32 solve alone is ~kappa 2^-24 off), c_0 likewise, amp the exact one's to
+    FP32 rounding. With amp above the caller's acceptance bound it stops after the FP32 solve
+    and reports amp (code 2)."""
+    dx, u, w, A, r = _system(dim, deg, 400, 90 + 7 * dim + deg + pairs)
+    m = A.shape[1]
+    nm = _n_moments(dim, deg)
+    b = np.cos(3 * u[:, 0]) + u[:, 1] ** 2
+    mom = np.zeros(nm + m)
+    out = np.zeros(m + 5)
+    hk.hk_mls(dim, deg, 1, 0, len(dx), _p(np.ascontiguousarray(dx)), _p(b), 1.0 / r, 0.0,
+              1e-14, _p(mom), _p(out), 0, None)
+    rc, y, c0, amp, stored = _refined(hk, dim, deg, fused, pairs, mom)
+    assert rc == 1
+    G = _gram(dim, deg, stored[:nm])
+    y_ex = np.linalg.solve(G, np.eye(m)[0])
+    d = np.sqrt(np.diag(G))
+    amp_ex = d[0] * np.sum(np.abs(y_ex) * d)
+    assert amp == pytest.approx(amp_ex, rel=1e-5)
+    assert np.abs(y - y_ex).max() <= 2.0 ** -27 / max(amp_ex, 1.0) * np.abs(y_ex).max()
+    y32 = np.linalg.solve(G.astype(np.float32), np.eye(m, dtype=np.float32)[0]).astype(np.float64)
+    assert np.abs(y - y_ex).max() < np.abs(y32 - y_ex).max()        # better than FP32 alone
+    if fused:
+        assert c0 == pytest.approx(y_ex @ stored[nm:nm + m], rel=1e-9, abs=1e-12)
+    rc2, _, _, amp2, _ = _refined(hk, dim, deg, fused, pairs, mom, amp_accept=amp_ex / 2)
+    assert rc2 == 2 and amp2 == pytest.approx(amp_ex, rel=1e-3)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_refined_fp32_solve_in_a_recentred_basis(hk, dim):
+    """A one-sided neighbourhood: in the target-centred basis amp is large and the refined
+    solve may decline (the FP64 solve then runs); in the re-centred basis, with a_t = a(-c/s),
+    it converges and c_0 is the weighted least-squares value."""
+    dx, u, w, A, r = _lopsided(dim, 2, 400, 70 + dim)
+    m = A.shape[1]
+    nm = _n_moments(dim, 2)
+    b = np.cos(3 * u[:, 0]) + u[:, 1] ** 2
+    sw = np.sqrt(w)
+    c_ls, *_ = np.linalg.lstsq(sw[:, None] * A, sw * b, rcond=None)
+    mom = np.zeros(nm + m)
+    out = np.zeros(m + 5)
+    hk.hk_mls(dim, 2, 1, 0, len(dx), _p(np.ascontiguousarray(dx)), _p(b), 1.0 / r, 0.0, 1e-14,
+              _p(mom), _p(out), 0, None)
+    rc, y, c0, amp, _ = _refined(hk, dim, 2, 1, 1, mom)
+    assert rc in (0, 1)
+    if rc == 1:
+        assert c0 == pytest.approx(c_ls[0], rel=1e-6)
+    bas = np.zeros(4, np.float32)
+    hk.hk_recentre_basis(dim, _p(mom), _p(bas))
+    c, ws = bas[:dim].astype(np.float64), np.float64(bas[3])
+    up = (u - c) * ws
+    ex = sorted((e for e in itertools.product(range(5), repeat=dim) if sum(e) <= 4),
+                key=lambda e: (sum(e), tuple(-x for x in e)))
+    ex2 = [e for e in ex if sum(e) <= 2]
+    mom_c = np.array([(w * np.prod(up ** np.array(e), axis=1)).sum() for e in ex] +
+                     [(w * b * np.prod(up ** np.array(e), axis=1)).sum() for e in ex2])
+    at = np.array([np.prod((-c * ws) ** np.array(e)) for e in ex2])
+    rc, y, c0, amp_c, _ = _refined(hk, dim, 2, 1, 1, mom_c, at=at)
+    assert rc == 1
+    assert c0 == pytest.approx(c_ls[0], rel=1e-7)
+    assert amp_c < out[m] / 4
+
+
+def test_refined_fp32_solve_hands_singular_systems_to_fp64(hk):
+    """Collinear neighbours make a quadratic system singular: the refined FP32 solve must
+    decline (the FP64 solve and its guard then decide), never return a value."""
+    rng = np.random.default_rng(3)
+    t = rng.uniform(-0.9, 0.9, 200)
+    u = np.stack([t, 0.5 * t], 1)
+    w = (1 - np.abs(t)) ** 4 * (4 * np.abs(t) + 1)
+    ex = [(0, 0), (1, 0), (0, 1), (2, 0), (1, 1), (0, 2), (3, 0), (2, 1), (1, 2), (0, 3),
+          (4, 0), (3, 1), (2, 2), (1, 3), (0, 4)]
+    mom = np.array([(w * u[:, 0] ** a * u[:, 1] ** c).sum() for a, c in ex])
+    rc, *_ = _refined(hk, 2, 2, 0, 0, mom)
+    assert rc == 0
 
 
 def _f32_case(kind_of, n, seed):
