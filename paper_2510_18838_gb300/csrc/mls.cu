@@ -62,8 +62,9 @@ AsmPlan choose_plan(int dim, int64_t ns, double radius, const double* lo, const 
 
 // out: [0] underdetermined, [1] ill-conditioned, [2] max count, [3] max doublings,
 //      [4] sum of counts (the operator's nonzeros)
-__global__ void k_stats(const int8_t* status, const int32_t* counts, const int32_t* kexp,
-                        int64_t n, unsigned long long* out) {
+__global__ void __launch_bounds__(256) k_stats(const int8_t* status, const int32_t* counts,
+                                               const int32_t* kexp, int64_t n,
+                                               unsigned long long* out) {
     unsigned long long under = 0, ill = 0, mc = 0, mk = 0, sc = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -81,13 +82,35 @@ __global__ void k_stats(const int8_t* status, const int32_t* counts, const int32
         mk = max(mk, __shfl_xor_sync(0xffffffffu, mk, o));
         sc += __shfl_xor_sync(0xffffffffu, sc, o);
     }
+    // one set of atomics per block: per-warp atomics on five addresses serialise in L2
+    __shared__ unsigned long long sh[8][5];
+    const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
+        sh[w][0] = under;
+        sh[w][1] = ill;
+        sh[w][2] = mc;
+        sh[w][3] = mk;
+        sh[w][4] = sc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int j = 1; j < (int)(blockDim.x >> 5); j++) {
+            under += sh[j][0];
+            ill += sh[j][1];
+            mc = max(mc, sh[j][2]);
+            mk = max(mk, sh[j][3]);
+            sc += sh[j][4];
+        }
         atomicAdd(&out[0], under);
         atomicAdd(&out[1], ill);
         atomicMax(&out[2], mc);
         atomicMax(&out[3], mk);
         atomicAdd(&out[4], sc);
     }
+}
+
+int stats_blocks(int64_t n) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, 2 * (int64_t)num_sms()));
 }
 
 template <typename T>
@@ -316,7 +339,9 @@ void solve_tiers(int dim, int deg, int mode, bool mixed, AsmPlan plan, const Asm
         } else {
             a2.cols = nullptr;   // the operator's columns are already written
         }
-        assemble_any(dim, deg, true, mode, 32, ACC_BK, false, a2, asm_blocks(cnt[0], 32), s);
+        // tier 2 keeps tier 1's lanes per target: its targets are mostly small, badly
+        // conditioned neighbourhoods, which 32 lanes would spend on reductions
+        assemble_any(dim, deg, true, mode, G, ACC_BK, false, a2, asm_blocks(cnt[0], G), s);
         SolveArgs s2 = sa;
         s2.n_recentred = nullptr;
         s2.list = list2;
@@ -615,7 +640,7 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
         PCMS_CU(cudaMemsetAsync(st.p, 0, st.bytes, s));
         {
         PCMS_TRACE("mls_status_stats", s);
-        k_stats<<<thread_blocks(nt, 256), 256, 0, s>>>(M.status.as<int8_t>(), M.counts.as<int32_t>(),
+        k_stats<<<stats_blocks(nt), 256, 0, s>>>(M.status.as<int8_t>(), M.counts.as<int32_t>(),
                                                       M.kexp.as<int32_t>(), nt,
                                                       st.as<unsigned long long>());
         }
@@ -747,7 +772,7 @@ void mls_transfer(const MlsParams& P0, const double* src, int64_t ns, const doub
         PCMS_CU(cudaMemsetAsync(st.p, 0, st.bytes, s));
         // status is in caller order; counts/kexp only feed the max statistics here
         PCMS_TRACE("mls_status_stats", s);
-        k_stats<<<thread_blocks(nt, 256), 256, 0, s>>>(status, counts.as<int32_t>(),
+        k_stats<<<stats_blocks(nt), 256, 0, s>>>(status, counts.as<int32_t>(),
                                                       kexp.as<int32_t>(), nt,
                                                       st.as<unsigned long long>());
         PCMS_LAUNCH_CHECK("k_stats");

@@ -23,11 +23,11 @@ PCMS_DECLARE_MLS_DISPATCH(3)
 // stored moment types of the solve
 enum { MOM_F32 = 0, MOM_F32PAIR = 1, MOM_F64 = 2 };
 
-// acc: ACC_PLAIN, or ACC_BK (mixed MAP/FUSED with 32 lanes per target only: blocked
-// compensation, float2 moments) for tier 1 of very large neighbourhoods and for tier 2.
+// acc: ACC_PLAIN, or ACC_BK (mixed MAP/FUSED: blocked compensation, float2 moments) for
+// tier 1 of very large neighbourhoods (32 lanes) and for tier 2 (8 or 32 lanes, as tier 1).
 inline void assemble_any(int dim, int deg, bool mixed, int mode, int G, int acc, bool fd,
                          const AsmArgs& a, int blocks, cudaStream_t s) {
-    const bool bk = mixed && mode != MODE_COUNT && G == 32 && acc == ACC_BK;
+    const bool bk = mixed && mode != MODE_COUNT && (G == 32 || G == 8) && acc == ACC_BK;
     // a target list means a later tier of the mixed path (tier 2: blocked FP32, tier 3: FP64)
     // or the FP64 path's refine pass (a list with a re-centred basis)
     static const char* names[6][3] = {
@@ -70,6 +70,8 @@ inline void shape_any(int dim, int deg, bool mixed, int G, const ShapeArgs& a, i
         } else if (mode == MODE_MAP) {                                                        \
             if (G == 32 && MIXED && acc == ACC_BK)                                            \
                 k_assemble<DIMV, DEG, MIXED, MODE_MAP, 32, float, MIXED ? ACC_BK : ACC_PLAIN><<<b, 256, 0, s>>>(a); \
+            else if (MIXED && acc == ACC_BK)                                                  \
+                k_assemble<DIMV, DEG, MIXED, MODE_MAP, 8, float, MIXED ? ACC_BK : ACC_PLAIN><<<b, 256, 0, s>>>(a); \
             else if (G == 32) k_assemble<DIMV, DEG, MIXED, MODE_MAP, 32, float><<<b, 256, 0, s>>>(a); \
             else k_assemble<DIMV, DEG, MIXED, MODE_MAP, 8, float><<<b, 256, 0, s>>>(a);       \
         } else {                                                                              \
@@ -81,6 +83,8 @@ inline void shape_any(int dim, int deg, bool mixed, int G, const ShapeArgs& a, i
             } else {                                                                          \
                 if (G == 32 && MIXED && acc == ACC_BK)                                        \
                     k_assemble<DIMV, DEG, MIXED, MODE_FUSED, 32, float, MIXED ? ACC_BK : ACC_PLAIN><<<b, 256, 0, s>>>(a); \
+                else if (MIXED && acc == ACC_BK)                                              \
+                    k_assemble<DIMV, DEG, MIXED, MODE_FUSED, 8, float, MIXED ? ACC_BK : ACC_PLAIN><<<b, 256, 0, s>>>(a); \
                 else if (G == 32) k_assemble<DIMV, DEG, MIXED, MODE_FUSED, 32, float><<<b, 256, 0, s>>>(a); \
                 else k_assemble<DIMV, DEG, MIXED, MODE_FUSED, 8, float><<<b, 256, 0, s>>>(a);  \
             }                                                                                 \

@@ -601,7 +601,7 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemb
     // Dense one-shot targets (warp per target, blocked compensation): about 3 in 4 candidates
     // are selected, so every lane accumulates its own candidate with the weight zeroed when it
     // is not selected, instead of compacting selected pairs through the shared-memory ring.
-    constexpr bool PRED = MODE == MODE_FUSED && ACC == ACC_BK;
+    constexpr bool PRED = MODE == MODE_FUSED && ACC == ACC_BK && G == 32;
 
     const int64_t ngroups = (int64_t)gridDim.x * (blockDim.x >> 5) * GPW;
     const int64_t gid = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * GPW + gi;

@@ -133,9 +133,10 @@ void cell_pyramid(const Grid& g, const SortedPoints& S, int levels, const int64_
                   float4* out, cudaStream_t s);
 
 // Stable LSD radix sort (8-bit digits) of (key, value) pairs with keys < nkeys; k1/v1 are
-// scratch of n entries. Returns the buffer (v0 or v1) holding the values in key order.
+// scratch of n entries. Returns the buffer (v0 or v1) holding the values in key order;
+// keys_out, if given, receives the buffer holding the sorted keys.
 uint32_t* radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t n,
-                           int64_t nkeys, cudaStream_t s);
+                           int64_t nkeys, cudaStream_t s, uint32_t** keys_out = nullptr);
 
 // exclusive scan of int32 counts into out[0..n] (out[n] = total); T = int32_t or int64_t
 template <typename T>

@@ -596,7 +596,8 @@ void cell_pyramid(const Grid& g, const SortedPoints& S, int levels, const int64_
 }
 
 uint32_t* radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t n,
-                           int64_t nkeys, cudaStream_t s) {
+                           int64_t nkeys, cudaStream_t s, uint32_t** keys_out) {
+    if (keys_out) *keys_out = k0;
     if (n <= 0) return v0;
     int bits = 1;
     while (bits < 32 && ((int64_t)1 << bits) < nkeys) bits++;
@@ -618,7 +619,37 @@ uint32_t* radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v
         std::swap(k0, k1);
         std::swap(v0, v1);
     }
+    if (keys_out) *keys_out = k0;
     return v0;
+}
+
+// cell_start[c] = the first sorted position whose key is >= c, for c = 0..ncell. Position
+// pos writes the cells (key[pos - 1], key[pos]] (position n: the cells after the last key),
+// so every entry is written exactly once, without atomics.
+__global__ void k_cell_starts(const uint32_t* __restrict__ skey, int64_t n, int64_t ncell,
+                              int32_t* __restrict__ start) {
+    for (int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pos <= n;
+         pos += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t lo = pos == 0 ? 0 : (int64_t)skey[pos - 1] + 1;
+        const int64_t hi = pos == n ? ncell : (int64_t)skey[pos];
+        for (int64_t c = lo; c <= hi; c++) start[c] = (int32_t)pos;
+    }
+}
+
+// The same by a binary search per cell, for grids with many more cells than points (long
+// runs of empty cells would serialise the kernel above).
+__global__ void k_cell_starts_search(const uint32_t* __restrict__ skey, int64_t n, int64_t ncell,
+                                     int32_t* __restrict__ start) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= ncell;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t a = 0, b = n;   // first position in [a, b) with key >= c
+        while (a < b) {
+            const int64_t m = (a + b) >> 1;
+            if ((int64_t)skey[m] < c) a = m + 1;
+            else b = m;
+        }
+        start[c] = (int32_t)a;
+    }
 }
 
 void sort_points(const Grid& g, const double* pts, int64_t n, bool with_start, bool with_hl,
@@ -627,17 +658,12 @@ void sort_points(const Grid& g, const double* pts, int64_t n, bool with_start, b
     out.n = n;
     const int dim = g.dim;
     const int64_t nn = std::max<int64_t>(n, 1);
-    // cell counts and starts only where they are needed (sources); targets are only ordered
-    DBuf count;
+    // cell starts only where they are needed (sources); targets are only ordered
     DBuf kv(sizeof(uint32_t) * 4 * nn, s);   // key, idx, key', idx'
     uint32_t* k0 = kv.as<uint32_t>();
     uint32_t* v0 = k0 + nn;
     uint32_t* k1 = v0 + nn;
     uint32_t* v1 = k1 + nn;
-    if (with_start) {
-        count.alloc(sizeof(int32_t) * (g.ncell + 1), s);
-        PCMS_CU(cudaMemsetAsync(count.p, 0, sizeof(int32_t) * (g.ncell + 1), s));
-    }
     out.perm.alloc(sizeof(int32_t) * nn, s);
     out.inv.alloc(sizeof(int32_t) * nn, s);
     out.x64.alloc(sizeof(double) * dim * nn, s);
@@ -653,14 +679,22 @@ void sort_points(const Grid& g, const double* pts, int64_t n, bool with_start, b
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8));
     if (n > 0) {
         PCMS_TRACE("grid_cell_keys", s);
-        k_cell_keys<<<blocks, 256, 0, s>>>(g, pts, n, k0, v0,
-                                           with_start ? count.as<int32_t>() : nullptr);
+        k_cell_keys<<<blocks, 256, 0, s>>>(g, pts, n, k0, v0, nullptr);
     }
     PCMS_LAUNCH_CHECK("cell_keys");
-    if (with_start)
-        exclusive_scan<int32_t>(count.as<int32_t>(), out.cell_start.as<int32_t>(), g.ncell, s);
+    uint32_t* skey = k0;
+    if (n > 0) v0 = radix_sort_pairs(k0, v0, k1, v1, n, g.ncell, s, &skey);
+    if (with_start) {
+        PCMS_TRACE("grid_cell_starts", s);
+        if (g.ncell <= 8 * n)
+            k_cell_starts<<<(int)std::max<int64_t>(1, std::min<int64_t>((n + 256) / 256, (int64_t)num_sms() * 8)),
+                            256, 0, s>>>(skey, n, g.ncell, out.cell_start.as<int32_t>());
+        else
+            k_cell_starts_search<<<(int)std::max<int64_t>(1, std::min<int64_t>((g.ncell + 256) / 256, (int64_t)num_sms() * 8)),
+                                   256, 0, s>>>(skey, n, g.ncell, out.cell_start.as<int32_t>());
+        PCMS_LAUNCH_CHECK("cell_starts");
+    }
     if (n > 0) {
-        v0 = radix_sort_pairs(k0, v0, k1, v1, n, g.ncell, s);
         PCMS_TRACE("grid_gather_sorted", s);
         k_gather_sorted<<<blocks, 256, 0, s>>>(dim, g, pts, n, v0, out.perm.as<int32_t>(),
                                                out.inv.as<int32_t>(), out.x64.as<double>(),
