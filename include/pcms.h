@@ -148,8 +148,11 @@ pcms_status pcms_apply_map(pcms_map map, const void* fields, int n_fields, void*
 
 /*
  * pcms_mls_transfer -- one-shot MLS transfer of n_fields fields without storing an
- *   operator (same selection, weights and fit as pcms_create_map; the per-target fit is
- *   evaluated directly as c_0 = e_1^T G^-1 g). Arguments as pcms_create_map plus fields
+ *   operator (same selection, weights and fit as pcms_create_map). One or two fields: the
+ *   per-target fit is evaluated directly as c_0 = e_1^T G^-1 g, one walk per field. Three or
+ *   more fields, PCMS_MIXED, 2D/3D: one walk builds each target's operator row, which is
+ *   applied to all fields as it is evaluated and not stored. FP64 with three or more fields,
+ *   and 4D/5D: a transient operator is built and applied. Arguments as pcms_create_map plus fields
  *   (device [n_fields][n_src], float64 for PCMS_FP64, float32 for PCMS_MIXED), out (device
  *   [n_fields][n_tgt], same dtype) and target_status (device int8 [n_tgt], may be NULL).
  *   1 <= n_fields <= 16. Syncs once for the bounding box unless opts->domain_known.

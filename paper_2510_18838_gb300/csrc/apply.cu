@@ -410,6 +410,30 @@ __global__ void k_export_status(int64_t nt, const int32_t* __restrict__ inv_t,
 
 }  // namespace
 
+int apply_fp_f32(int nf) {
+    int nvec = 1;
+    while (nvec * 4 < nf) nvec <<= 1;
+    return nf == 1 ? 1 : nvec * 4;
+}
+
+void fields_to_sorted_f32(const MapImpl& M, const float* fields, int nf, int fp, float* fs,
+                          cudaStream_t s) {
+    if (M.ns <= 0) return;
+    PCMS_TRACE("apply_fields_to_sorted", s);
+    k_fields_to_sorted<float><<<blocks_for(M.ns, 256), 256, 0, s>>>(fields, nf, fp, M.ns,
+                                                                    M.src.inv.as<int32_t>(), fs);
+    PCMS_LAUNCH_CHECK("fields_to_sorted");
+}
+
+void stage_to_caller_f32(const MapImpl& M, const float* stage, int fp, int nf, float* out,
+                         cudaStream_t s) {
+    if (M.nt <= 0) return;
+    PCMS_TRACE("apply_stage_to_caller", s);
+    k_stage_to_caller<float><<<blocks_for(M.nt, 256), 256, 0, s>>>(stage, fp, nf, M.nt,
+                                                                   M.tgt.inv.as<int32_t>(), out);
+    PCMS_LAUNCH_CHECK("stage_to_caller");
+}
+
 void mls_apply(MapImpl& M, const void* fields, int nf, void* out, cudaStream_t s) {
     if (M.P.prec == PCMS_MIXED) apply_t<float>(M, (const float*)fields, nf, (float*)out, s);
     else apply_t<double>(M, (const double*)fields, nf, (double*)out, s);

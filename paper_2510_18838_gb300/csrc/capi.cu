@@ -176,11 +176,13 @@ pcms_status pcms_mls_transfer(int dim, const double* src_pts, int64_t n_src,
         cudaStream_t s = (cudaStream_t)stream;
         pcms::MlsParams P = make_params(dim, basis_degree, radius, o);
         int64_t n_under = 0;
-        if (n_fields <= 2) {
+        if (n_fields <= 2 || (o.precision == PCMS_MIXED && dim <= 3)) {
+            // one or two fields: fused walks; several mixed fields: the operator's rows
+            // applied as they are evaluated, without storing them
             pcms::mls_transfer(P, src_pts, n_src, tgt_pts, n_tgt, o, fields, n_fields, out,
                                target_status, s, &n_under);
         } else {
-            // several fields: build a transient operator once and apply it
+            // several FP64 fields: build a transient operator once and apply it
             pcms::MapImpl M;
             M.P = P;
             M.ns = n_src;

@@ -490,7 +490,10 @@ int64_t MapImpl::device_bytes() const {
 // ------------------------------------------------------------------------------------
 // create map
 // ------------------------------------------------------------------------------------
-void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms_map_opts& o) {
+void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms_map_opts& o,
+                    const FusedApply* fused) {
+    if (fused && (M.P.dim >= 4 || M.P.prec != PCMS_MIXED))
+        fail(PCMS_ERR_INVALID_ARG, "internal: rows applied as evaluated need a mixed 2D/3D map");
     if (M.P.dim >= 4) return mls_nd_create_map(M, src, tgt);
     cudaStream_t s = M.stream;
     M.P = settle_growth(M.P, src, M.ns, tgt, M.nt, o, s);
@@ -596,7 +599,8 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
             assemble_any(dim, deg, mixed, MODE_MAP, G, plan.acc, false, a, asm_blocks(nt, G), s);
         }
         M.nnz = nnz;
-        M.vals.alloc((mixed ? sizeof(float) : sizeof(double)) * std::max<int64_t>(nnz, 1), s);
+        if (!fused)
+            M.vals.alloc((mixed ? sizeof(float) : sizeof(double)) * std::max<int64_t>(nnz, 1), s);
 
         SolveArgs sa{};
         bases.apply(sa);
@@ -632,7 +636,21 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
         sh.radius = P.radius;
         sh.weight = (int)P.weight;
         sh.vals = M.vals.p;
-        shape_any(dim, deg, mixed, G, sh, asm_blocks(nt, G), s);
+        if (fused) {
+            // each row is applied to the fields as it is evaluated: no values stored, no SpMM
+            const int fp = apply_fp_f32(fused->nf);
+            DBuf fsd(sizeof(float) * fp * std::max<int64_t>(ns, 1), s);
+            DBuf stage(sizeof(float) * fp * nt, s);
+            fields_to_sorted_f32(M, fused->fields, fused->nf, fp, fsd.as<float>(), s);
+            sh.fs = fsd.as<float>();
+            sh.fp = fp;
+            sh.status = M.status.as<int8_t>();
+            sh.stage = stage.as<float>();
+            shape_apply_any(dim, deg, G, sh, asm_blocks(nt, G), s);
+            stage_to_caller_f32(M, stage.as<float>(), fp, fused->nf, fused->out, s);
+        } else {
+            shape_any(dim, deg, mixed, G, sh, asm_blocks(nt, G), s);
+        }
         M.tgt.hl0.release();   // the targets' hi/lo coordinates only serve the assembly
         M.tgt.hl1.release();
 
@@ -717,6 +735,20 @@ void mls_transfer(const MlsParams& P0, const double* src, int64_t ns, const doub
     if (P0.dim >= 4)
         return mls_nd_transfer(P0, src, ns, tgt, nt, (const double*)fields, nf, (double*)out,
                                status, s, n_under);
+    if (P0.prec == PCMS_MIXED && nf >= 3) {
+        // several fields: one walk builds the operator's rows, which are applied to all the
+        // fields as they are evaluated, instead of one fused walk per field
+        MapImpl M;
+        M.P = P0;
+        M.ns = ns;
+        M.nt = nt;
+        M.stream = s;
+        const FusedApply fa{(const float*)fields, nf, (float*)out};
+        mls_create_map(M, src, tgt, o, &fa);
+        if (status && nt > 0) mls_export(M, nullptr, nullptr, nullptr, status, nullptr, s);
+        *n_under = M.n_under;
+        return;
+    }
     const MlsParams P = settle_growth(P0, src, ns, tgt, nt, o, s);
     const int dim = P.dim, deg = P.degree;
     const bool mixed = P.prec == PCMS_MIXED;

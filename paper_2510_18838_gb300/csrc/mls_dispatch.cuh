@@ -16,7 +16,9 @@ namespace pcms {
     void solve_dispatch_d##DIMV(int deg, int mode, int mom_kind, const SolveArgs& a,          \
                                 int blocks, cudaStream_t s);                                  \
     void shape_dispatch_d##DIMV(int deg, bool mixed, int G, const ShapeArgs& a, int blocks,   \
-                                cudaStream_t s);
+                                cudaStream_t s);                                              \
+    void shape_apply_dispatch_d##DIMV(int deg, int G, const ShapeArgs& a, int blocks,         \
+                                      cudaStream_t s);
 PCMS_DECLARE_MLS_DISPATCH(2)
 PCMS_DECLARE_MLS_DISPATCH(3)
 
@@ -53,6 +55,13 @@ inline void shape_any(int dim, int deg, bool mixed, int G, const ShapeArgs& a, i
     PCMS_TRACE(mixed ? "mls_shape_mixed" : "mls_shape_fp64", s);
     if (dim == 2) shape_dispatch_d2(deg, mixed, G, a, blocks, s);
     else shape_dispatch_d3(deg, mixed, G, a, blocks, s);
+}
+// mixed rows evaluated and applied at once (a.fs, a.fp, a.status, a.stage), nothing stored
+inline void shape_apply_any(int dim, int deg, int G, const ShapeArgs& a, int blocks,
+                            cudaStream_t s) {
+    PCMS_TRACE("mls_shape_apply_mixed", s);
+    if (dim == 2) shape_apply_dispatch_d2(deg, G, a, blocks, s);
+    else shape_apply_dispatch_d3(deg, G, a, blocks, s);
 }
 
 }  // namespace pcms
@@ -147,5 +156,18 @@ inline void shape_any(int dim, int deg, bool mixed, int G, const ShapeArgs& a, i
             }                                                                                 \
         }                                                                                     \
         PCMS_LAUNCH_CHECK("k_shape");                                                         \
+    }                                                                                         \
+    void shape_apply_dispatch_d##DIMV(int deg, int G, const ShapeArgs& a, int b,              \
+                                      cudaStream_t s) {                                       \
+        if (G == 32) {                                                                        \
+            if (deg == 0) k_shape<DIMV, 0, true, 32, true><<<b, 256, 0, s>>>(a);             \
+            else if (deg == 1) k_shape<DIMV, 1, true, 32, true><<<b, 256, 0, s>>>(a);        \
+            else k_shape<DIMV, 2, true, 32, true><<<b, 256, 0, s>>>(a);                      \
+        } else {                                                                              \
+            if (deg == 0) k_shape<DIMV, 0, true, 8, true><<<b, 256, 0, s>>>(a);              \
+            else if (deg == 1) k_shape<DIMV, 1, true, 8, true><<<b, 256, 0, s>>>(a);         \
+            else k_shape<DIMV, 2, true, 8, true><<<b, 256, 0, s>>>(a);                       \
+        }                                                                                     \
+        PCMS_LAUNCH_CHECK("k_shape_apply");                                                   \
     }                                                                                         \
     }

@@ -206,6 +206,13 @@ struct ShapeArgs {
     double radius;
     int weight;
     void* vals;
+    // k_shape<..., APPLY = true> (mixed): the rows are applied as they are evaluated instead of
+    // stored: stage[t][f] = sum_i N_ti fs[col_i][f] for f < fp (fields in sorted source order,
+    // fp = 1 or a multiple of 4 up to 16), NaN where status[t] is not OK
+    const float* fs;
+    int fp;
+    const int8_t* status;
+    float* stage;
 };
 
 // ------------------------------------------------------------------------------------
@@ -1417,9 +1424,10 @@ __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
 // ------------------------------------------------------------------------------------
 // k_shape: N_j = w_j a(u_j)^T y
 // ------------------------------------------------------------------------------------
-template <int DIM, int DEG, bool MIXED, int G>
+template <int DIM, int DEG, bool MIXED, int G, bool APPLY = false>
 __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
     static_assert(DEG <= 2, "operator rows: exact double-FP32 monomials need degree <= 2");
+    static_assert(!APPLY || MIXED, "fused rows and apply: mixed maps");
     using T = typename std::conditional<MIXED, float, double>::type;
     constexpr int M = mono_count(DIM, DEG);
     constexpr int GPW = 32 / G;
@@ -1467,6 +1475,46 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
         if constexpr (MIXED) inv_r = S.lv.inv_rf[kx];
         else inv_r = S.lv.inv_r[kx];
         const int64_t a = S.offsets[t], b = a + S.counts[t];
+        // APPLY: this lane's share of the row applied to the fields
+        float facc[16];
+#pragma unroll
+        for (int q = 0; q < 16; q++) facc[q] = 0.f;
+        const int nvf = APPLY ? S.fp / 4 : 0;
+        // APPLY: the pair's field row, loaded when the pair is taken up so that the gather
+        // overlaps the evaluation of its value
+        float4 fx[4];
+        float f1 = 0.f;
+        auto gather = [&](int j) {
+            if constexpr (APPLY) {
+                if (S.fp == 1) {
+                    f1 = S.fs[j];
+                } else {
+                    const float4* row = reinterpret_cast<const float4*>(S.fs + (int64_t)j * S.fp);
+#pragma unroll
+                    for (int q = 0; q < 4; q++)
+                        if (q < nvf) fx[q] = row[q];
+                }
+            }
+        };
+        auto emit = [&](int64_t i, int j, T v) {
+            if constexpr (APPLY) {
+                if (S.fp == 1) {
+                    facc[0] += (float)v * f1;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        if (q < nvf) {
+                            facc[4 * q] += (float)v * fx[q].x;
+                            facc[4 * q + 1] += (float)v * fx[q].y;
+                            facc[4 * q + 2] += (float)v * fx[q].z;
+                            facc[4 * q + 3] += (float)v * fx[q].w;
+                        }
+                    }
+                }
+            } else {
+                ((T*)S.vals)[i] = v;
+            }
+        };
         // Software pipeline over the row (mixed path): the column two pairs ahead and the
         // coordinates of the next pair are loaded before the current pair is evaluated, so
         // the gathers overlap the arithmetic instead of stalling on it.
@@ -1481,6 +1529,7 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
         }
         for (; i < b; i += G) {
             const int j = jc;
+            gather(j);
             const float4 cur0 = hc0;
             const float2 cur1 = hc1;
             if (MIXED && i + G < b) {
@@ -1509,7 +1558,7 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
                     am[p] = am[par] * uu[v];
                     s += am[p] * S.y[t * M + p];
                 });
-                ((T*)S.vals)[i] = (T)(w64 * s);
+                emit(i, j, (T)(w64 * s));
                 continue;
             }
             T dx[3] = {T(0), T(0), T(0)};
@@ -1568,7 +1617,7 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
                         sl = (sl + pl) + e2;
                         sh = s2;
                     }
-                    ((T*)S.vals)[i] = (T)(w * sh + w * sl);
+                    emit(i, j, (T)(w * sh + w * sl));
                     continue;
                 }
             }
@@ -1582,7 +1631,33 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
                 am[p] = am[par] * u[v];
                 s += am[p] * y[p];
             });
-            ((T*)S.vals)[i] = w * s;
+            emit(i, j, w * s);
+        }
+        if constexpr (APPLY) {
+            const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (gi * G));
+            const int nacc = S.fp == 1 ? 1 : 4 * nvf;
+#pragma unroll
+            for (int q = 0; q < 16; q++) {
+                if (q < nacc) {
+#pragma unroll
+                    for (int o = G / 2; o > 0; o >>= 1) facc[q] += __shfl_xor_sync(gmask, facc[q], o);
+                }
+            }
+            if (gl == 0) {
+                const bool ok = S.status[t] == PCMS_TARGET_OK;
+                const float nanf = __int_as_float(0x7fc00000);
+                if (S.fp == 1) {
+                    S.stage[t] = ok ? facc[0] : nanf;
+                } else {
+                    float4* dst = reinterpret_cast<float4*>(S.stage + t * S.fp);
+#pragma unroll
+                    for (int q = 0; q < 4; q++)
+                        if (q < nvf)
+                            dst[q] = ok ? make_float4(facc[4 * q], facc[4 * q + 1], facc[4 * q + 2],
+                                                      facc[4 * q + 3])
+                                        : make_float4(nanf, nanf, nanf, nanf);
+                }
+            }
         }
     }
 }

@@ -329,7 +329,23 @@ struct MapImpl {
     int64_t device_bytes() const;
 };
 
-void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms_map_opts& o);
+// fused: for a mixed map used once, evaluate its rows and apply them to these fields
+// (float [nf][ns] -> out float [nf][nt]) in one pass instead of storing the values; the map
+// then holds no values (M.vals empty) and is only fit to be destroyed
+struct FusedApply {
+    const float* fields;
+    int nf;
+    float* out;
+};
+void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms_map_opts& o,
+                    const FusedApply* fused = nullptr);
+// apply pieces shared with the fused path (float fields): padded row width, fields into
+// sorted order, staged rows back to caller order
+int apply_fp_f32(int nf);
+void fields_to_sorted_f32(const MapImpl& M, const float* fields, int nf, int fp, float* fs,
+                          cudaStream_t s);
+void stage_to_caller_f32(const MapImpl& M, const float* stage, int fp, int nf, float* out,
+                         cudaStream_t s);
 void mls_apply(MapImpl& M, const void* fields, int nf, void* out, cudaStream_t s);
 // apply with caller-provided scratch of apply_scratch_bytes(M, nf) bytes (256-aligned base);
 // allocates nothing, returns the launch status

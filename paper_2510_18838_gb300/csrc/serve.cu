@@ -276,7 +276,9 @@ void run_job(pcms_server_s* S, Job* j, cudaStream_t s, Bounce& bounce, pcms::Map
         pcms::mls_create_map(*M, r.src_pts, r.tgt_pts, r.opts);
         pcms::mls_apply(*M, r.fields, r.n_fields, r.out, s);
         *built = std::move(M);
-    } else if (r.n_fields <= 2) {
+    } else if (r.n_fields <= 2 || r.opts.precision == PCMS_MIXED) {
+        // one-shot: fused walks for one or two fields, else the operator's rows applied as
+        // they are evaluated (mixed)
         int64_t nu = 0;
         pcms::mls_transfer(P, r.src_pts, r.n_src, r.tgt_pts, r.n_tgt, r.opts, r.fields,
                            r.n_fields, r.out, nullptr, s, &nu);
@@ -323,20 +325,33 @@ void worker(pcms_server_s* S, int slot) {
                         S->cv_cache.wait(lk);
                         continue;
                     }
-                    if (reuse && it != S->cache.end()) {
+                    const bool hit = reuse && it != S->cache.end();
+                    if (hit) {
                         // only the apply scratch (and the staged fields) is new
                         need = (int64_t)(r.n_src + r.n_tgt) * std::max(r.n_fields, 1) * 8 * 2 +
                                (int64_t(1) << 20) + staged_bytes(r, false);
+                        // pinned across the eviction below: evicting the operator this request
+                        // is about to use would leave `it` (and the operator) freed
+                        it->second.pins++;
                     }
                     if (S->in_use + need > S->cap) evict_for(S, need);
+                    if (hit && S->in_use + need > S->cap) {   // not admitted
+                        it->second.pins--;
+                        if (it->second.pins == 0) {
+                            // no room beside its own operator, which no one else is using:
+                            // drop it, and the request (it carries its geometry) builds it again
+                            S->in_use -= it->second.bytes;
+                            S->cache.erase(it);
+                            continue;
+                        }
+                    }
                     if (S->in_use + need <= S->cap) {
                         S->queue.pop_front();
                         h->bytes = need;
                         S->in_use += need;
                         S->peak = std::max(S->peak, S->in_use);
                         h->t_start = S->now();
-                        if (reuse && it != S->cache.end()) {
-                            it->second.pins++;
+                        if (hit) {   // already pinned above
                             it->second.last_use = ++S->use_clock;
                             cached = it->second.map.get();
                             h->used_cached = 1;

@@ -203,6 +203,28 @@ def test_mixed_growth_gaussian_mixture(P):
     assert kx.max() >= 1
 
 
+@pytest.mark.parametrize("dim,deg,nf,n_src,r", [(3, 2, 5, 40000, 0.09), (2, 2, 16, 60000, 0.03),
+                                               (2, 1, 3, 30000, 0.016), (3, 1, 9, 30000, 0.08),
+                                               (2, 2, 4, 300000, 0.02)])
+def test_mixed_many_field_transfer_applies_rows_as_evaluated(P, dim, deg, nf, n_src, r):
+    """Three or more mixed fields: one walk, each operator row applied to all fields as it is
+    evaluated (8 and 32 lanes per target, 4 to 16 padded fields). Values against the oracle,
+    statuses equal, and the same numbers as the stored operator's apply."""
+    src = W.uniform_points(n_src, dim, 51 + nf)
+    tgt = W.uniform_points(6000, dim, 52 + nf)
+    f = W.trig_fields(src, n_fields=nf, max_deg=2, seed0=60 + nf).astype(np.float32)
+    out, st = P.mls_transfer(cu(src), cu(tgt), cu(f), deg, r, precision="mixed")
+    o = oracle.mls(src, tgt, f.astype(np.float64), deg, r, mode="grid")
+    assert np.array_equal(host(st), o["status"])
+    ok = o["status"] == 0
+    assert normwise_err(host(out), o["values"], ok) <= TOL_MIXED
+    m = P.create_map(cu(src), cu(tgt), deg, r, precision="mixed")
+    ref = host(m.apply(cu(f)))
+    m.destroy()
+    np.testing.assert_allclose(host(out)[:, ok], ref[:, ok], rtol=1e-5, atol=1e-5)
+    assert np.isnan(host(out)[:, ~ok]).all()
+
+
 def test_mixed_dense_targets_in_an_estimated_basis(P):
     """The blocked-compensation plan (mean count ~1250): one-sided targets (grown radii at the
     edge of a cluster, the domain boundary) are assembled in tier 1 in a re-centred basis

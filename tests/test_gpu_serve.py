@@ -88,6 +88,40 @@ def test_cache_reuse_and_capacity(env):
     s.close()
 
 
+def test_reuse_that_does_not_fit_beside_its_operator(env):
+    """Eviction must never free the operator that the request being admitted is about to use:
+    under a cap that holds the cached operator but not the reuse request's scratch beside it,
+    the request drops the operator, builds it again and returns the right values."""
+    torch, pcms, serve = env
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev).manual_seed(5)
+    src = torch.rand((2, 20000), dtype=torch.float64, device=dev, generator=g)
+    tgt = torch.rand((2, 5000), dtype=torch.float64, device=dev, generator=g)
+    f1 = torch.rand((3, 20000), dtype=torch.float32, device=dev, generator=g)
+    f2 = torch.rand((5, 20000), dtype=torch.float32, device=dev, generator=g)
+    o1 = torch.empty((3, 5000), dtype=torch.float32, device=dev)
+    o2 = torch.empty((5, 5000), dtype=torch.float32, device=dev)
+    s = pcms.Server(n_slots=1, mem_cap_bytes=2 << 30)
+    s.submit_mls(src, tgt, f1, o1, 2, 0.03, map_key=7)
+    s.drain(120)
+    op_bytes = s.memory()["in_use"]          # the cached operator alone
+    s.close()
+    assert op_bytes > 0
+    s = pcms.Server(n_slots=1, mem_cap_bytes=op_bytes + (2 << 20))
+    s.submit_mls(src, tgt, f1, o1, 2, 0.03, map_key=7, bytes_hint=op_bytes)
+    s.drain(120)
+    s.submit_mls(src, tgt, f2, o2, 2, 0.03, map_key=7, reuse=True, bytes_hint=op_bytes)
+    s.drain(120)
+    res = sorted(s.poll(8), key=lambda x: x["ticket"])
+    s.close()
+    assert [x["status"] for x in res] == [pcms.OK, pcms.OK]
+    assert not res[1]["cached"]               # rebuilt, not applied from a freed operator
+    m = pcms.create_map(src, tgt, 2, 0.03, precision="mixed")
+    assert normwise_err(o2.cpu().numpy(), m.apply(f2).cpu().numpy()) <= TOL_MIXED
+    assert normwise_err(o1.cpu().numpy(), m.apply(f1).cpu().numpy()) <= TOL_MIXED
+    m.destroy()
+
+
 def test_a_failing_request_does_not_disturb_the_others(env):
     """A request that fails while running (a non-finite source coordinate, found by the
     library's bounding-box pass) comes back with its error status; requests around it, in
