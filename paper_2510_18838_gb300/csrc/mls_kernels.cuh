@@ -471,12 +471,13 @@ using MomT = typename std::conditional<ACC == ACC_BK, float2, T>::type;
 
 // Two blocks per SM (at most 128 registers) except: the blocked 3D quadratic form, whose
 // three accumulator sets of 35-45 moments would spill heavily at that size (one block); and
-// plain sums of degree <= 1 (at most 15 moments), three blocks (80 registers): the walk is
-// latency-bound, and the extra warps cut the serving stream's assembly time by 6% despite a
-// few dozen bytes of spills.
+// plain sums of at most 15 moments (degree <= 1, or 2D), three blocks (80 registers): the
+// walk is latency-bound, and the extra warps cut the serving stream's assembly time by 9%
+// despite a few dozen bytes of spills.
 template <int DIM, int DEG, int ACC>
 constexpr int asm_min_blocks() {
-    return (ACC == ACC_BK && DIM == 3 && DEG == 2) ? 1 : ((ACC == ACC_PLAIN && DEG <= 1) ? 3 : 2);
+    return (ACC == ACC_BK && DIM == 3 && DEG == 2) ? 1
+                                                     : ((ACC == ACC_PLAIN && (DEG <= 1 || DIM == 2)) ? 3 : 2);
 }
 
 // Candidate row rho of a target (cell (ct) and position in it (fr), cell units): the cells
