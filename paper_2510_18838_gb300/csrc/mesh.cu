@@ -319,9 +319,11 @@ __global__ void __launch_bounds__(256) k_locate(Grid g, double bx0, double by0, 
                 const double x0 = xy[v0], y0 = xy[nv + v0];
                 const double x1 = xy[v1], y1 = xy[nv + v1];
                 const double x2 = xy[v2], y2 = xy[nv + v2];
-                const double area = orient_fp(x0, y0, x1, y1, x2, y2);
-                const double l0 = __ddiv_rn(orient_fp(px, py, x1, y1, x2, y2), area);
-                const double l1 = __ddiv_rn(orient_fp(x0, y0, px, py, x2, y2), area);
+                // one reciprocal of the doubled area for both coordinates (within 2 ulp of the
+                // quotients; the FP64 pipe is this kernel's bound)
+                const double rarea = recip64(orient_fp(x0, y0, x1, y1, x2, y2));
+                const double l0 = __dmul_rn(orient_fp(px, py, x1, y1, x2, y2), rarea);
+                const double l1 = __dmul_rn(orient_fp(x0, y0, px, py, x2, y2), rarea);
                 const double l2 = __dsub_rn(__dsub_rn(1.0, l0), l1);
                 v = __dadd_rn(__dadd_rn(__dmul_rn(l0, field[v0]), __dmul_rn(l1, field[v1])),
                               __dmul_rn(l2, field[v2]));

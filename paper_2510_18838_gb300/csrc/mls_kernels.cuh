@@ -970,23 +970,6 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemb
 // mom = [moments of degree <= 2k (graded-lex)] [g (FUSED only)]. Returns false when the
 // guard fails. Host-callable so the algebra can be checked without a GPU.
 // ------------------------------------------------------------------------------------
-// 1/x. On the device: Newton-Raphson from the FP32 reciprocal, two steps (2^-23 -> 2^-46 ->
-// below FP64 rounding), about half the FP64 instructions of an IEEE division; IEEE division
-// outside [1e-30, 1e30] and on the host.
-__host__ __device__ __forceinline__ double recip64(double x) {
-#ifdef __CUDA_ARCH__
-    const double ax = fabs(x);
-    if (ax > 1e-30 && ax < 1e30) {
-        double r = (double)__frcp_rn((float)x);
-        double e = fma(-x, r, 1.0);
-        r = fma(r, e, r);
-        e = fma(-x, r, 1.0);
-        return fma(r, e, r);
-    }
-#endif
-    return 1.0 / x;
-}
-
 template <int DIM, int DEG, int MODE>
 __host__ __device__ __forceinline__ bool solve_moments(const double* mom, double lambda,
                                                        double tau, double* out, double* c0,
