@@ -1115,8 +1115,10 @@ __host__ __device__ inline void basis_at_target(float4 b, double* at) {
 // a_t - G y is formed in double-FP32 arithmetic (TwoProduct by FMA, TwoSum) from the moments
 // as stored (plain FP32 sums are exact FP32 values; blocked sums are FP32 pairs), with y kept
 // as an FP32 pair. An error e in y moves c_0 (and an operator row's value) by about e amp, so
-// the refinement runs until a correction is below 2^-27 / amp of y, far below the moments'
-// own FP32 error (about 2^-24 amp). The attainable accuracy is about kappa 2^-48.
+// the refinement runs until a correction is below 2^-20 / amp of y: c_0 then moves by at most
+// 2^-20 of the field, 5% of the 2e-5 bound, next to the moments' own FP32 error that the
+// tiers' amp bounds keep below a third of it. The attainable accuracy is about
+// kappa amp 2^-48 (the residual's double-FP32 error relative to |G| |y|).
 // Returns
 //   1  solved: y = yh + yl, *c0 (FUSED) and *amp as solve_moments;
 //   2  not refined, because amp (from the FP32 solve) exceeds amp_accept, the tier's
@@ -1229,7 +1231,7 @@ __host__ __device__ __forceinline__ int solve_moments_refined(const MT* mt, cons
         *amp = (double)amp0;
         return 2;
     }
-    const float tol = 7.450580596923828e-09f / fmaxf(amp0, 1.f);   // 2^-27 / amp
+    const float tol = 9.5367431640625e-07f / fmaxf(amp0, 1.f);   // 2^-20 / amp
 #pragma unroll
     for (int k = 0; k < M; k++) yl[k] = 0.f;
     bool conv = false;

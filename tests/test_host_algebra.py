@@ -298,7 +298,7 @@ def _refined(hk, dim, deg, fused, pairs, mom, at=None, amp_accept=1e30):
 def test_refined_fp32_solve_reaches_the_exact_solution(hk, dim, deg, fused, pairs):
     """The mixed tiers solve the stored FP32 moments with an FP32 factorization and
     double-FP32 refinement. On well-spread neighbourhoods y must reach the exact solution of
-    that FP32-valued system to 2^-27 / amp relative (what moves c_0 by at most 2^-27 of the
+    that FP32-valued system to 2^-20 / amp relative (what moves c_0 by at most 2^-20 of the
     field; an FP32 solve alone is ~kappa 2^-24 off), c_0 likewise, amp the exact one's to
     FP32 rounding. With amp above the caller's acceptance bound it stops after the FP32 solve
     and reports amp (code 2)."""
@@ -317,11 +317,11 @@ def test_refined_fp32_solve_reaches_the_exact_solution(hk, dim, deg, fused, pair
     d = np.sqrt(np.diag(G))
     amp_ex = d[0] * np.sum(np.abs(y_ex) * d)
     assert amp == pytest.approx(amp_ex, rel=1e-5)
-    assert np.abs(y - y_ex).max() <= 2.0 ** -27 / max(amp_ex, 1.0) * np.abs(y_ex).max()
+    assert np.abs(y - y_ex).max() <= 2.0 ** -20 / max(amp_ex, 1.0) * np.abs(y_ex).max()
     y32 = np.linalg.solve(G.astype(np.float32), np.eye(m, dtype=np.float32)[0]).astype(np.float64)
     assert np.abs(y - y_ex).max() < np.abs(y32 - y_ex).max()        # better than FP32 alone
     if fused:
-        assert c0 == pytest.approx(y_ex @ stored[nm:nm + m], rel=1e-9, abs=1e-12)
+        assert c0 == pytest.approx(y_ex @ stored[nm:nm + m], rel=2e-6, abs=1e-12)
     rc2, _, _, amp2, _ = _refined(hk, dim, deg, fused, pairs, mom, amp_accept=amp_ex / 2)
     assert rc2 == 2 and amp2 == pytest.approx(amp_ex, rel=1e-3)
 
