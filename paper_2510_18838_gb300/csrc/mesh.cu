@@ -152,10 +152,22 @@ __device__ __forceinline__ double orient_fp(double ax, double ay, double bx, dou
 }
 
 // ---------------------------------------------------------------------- build kernels
+// Cell ranges in FP32 (use32): cell coordinates (hi + lo) * (1/h) of the vertices' hi/lo
+// pairs (relative to the grid origin), within about 2^-22 n < 0.005 cells of the exact ones
+// (n <= 16384 cells per axis); each range is widened by CELL_MARGIN, above twice that, so it
+// covers every cell that the FP64 cell of a point inside the triangle, or its FP32 cell in
+// k_locate, can be. Wider ranges only add candidates.
+constexpr float CELL_MARGIN = 1.f / 64.f;
+
+__device__ __forceinline__ int cell32(float c, int n) {
+    return min(max(__float2int_rd(c), 0), n - 1);
+}
+
 __global__ void k_tri_prep(int64_t nv, const double* __restrict__ xy, int64_t nt,
                            const int32_t* __restrict__ tri, Grid g, int32_t* __restrict__ count,
                            int8_t* __restrict__ tsign, int4* __restrict__ trect,
-                           unsigned long long* bad_ids) {
+                           unsigned long long* bad_ids, const float4* __restrict__ vhl,
+                           int use32, float delta, float ihf) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nt;
          k += (int64_t)gridDim.x * blockDim.x) {
         int32_t i0 = tri[k], i1 = tri[nt + k], i2 = tri[2 * nt + k];
@@ -165,18 +177,33 @@ __global__ void k_tri_prep(int64_t nv, const double* __restrict__ xy, int64_t nt
             trect[k] = make_int4(1, 1, 0, 0);   // empty
             continue;
         }
-        double x0 = xy[i0], y0 = xy[nv + i0], x1 = xy[i1], y1 = xy[nv + i1];
-        double x2 = xy[i2], y2 = xy[nv + i2];
-        int s = orient_sign(x0, y0, x1, y1, x2, y2);
+        int s = 0, cx0, cx1, cy0, cy1;
+        if (use32) {
+            // orientation: the FP32 filter of orient(v0, v1, v2), FP64 and exact when undecided
+            const float4 A = vhl[i0], B = vhl[i1], C = vhl[i2];
+            s = orient_filter32(A, B, C.x, C.y, C.z, C.w, delta);
+            if (s == 0)
+                s = orient_sign(xy[i0], xy[nv + i0], xy[i1], xy[nv + i1], xy[i2], xy[nv + i2]);
+            const float ax = (A.x + A.z) * ihf, bx = (B.x + B.z) * ihf, cx = (C.x + C.z) * ihf;
+            const float ay = (A.y + A.w) * ihf, by = (B.y + B.w) * ihf, cy = (C.y + C.w) * ihf;
+            cx0 = cell32(fminf(ax, fminf(bx, cx)) - CELL_MARGIN, g.n[0]);
+            cx1 = cell32(fmaxf(ax, fmaxf(bx, cx)) + CELL_MARGIN, g.n[0]);
+            cy0 = cell32(fminf(ay, fminf(by, cy)) - CELL_MARGIN, g.n[1]);
+            cy1 = cell32(fmaxf(ay, fmaxf(by, cy)) + CELL_MARGIN, g.n[1]);
+        } else {
+            double x0 = xy[i0], y0 = xy[nv + i0], x1 = xy[i1], y1 = xy[nv + i1];
+            double x2 = xy[i2], y2 = xy[nv + i2];
+            s = orient_sign(x0, y0, x1, y1, x2, y2);
+            cx0 = mesh_cell(fmin(x0, fmin(x1, x2)), g.lo[0], g.inv_h, g.n[0]);
+            cx1 = mesh_cell(fmax(x0, fmax(x1, x2)), g.lo[0], g.inv_h, g.n[0]);
+            cy0 = mesh_cell(fmin(y0, fmin(y1, y2)), g.lo[1], g.inv_h, g.n[1]);
+            cy1 = mesh_cell(fmax(y0, fmax(y1, y2)), g.lo[1], g.inv_h, g.n[1]);
+        }
         tsign[k] = (int8_t)s;
         if (s == 0) {
             trect[k] = make_int4(1, 1, 0, 0);
             continue;
         }
-        int cx0 = mesh_cell(fmin(x0, fmin(x1, x2)), g.lo[0], g.inv_h, g.n[0]);
-        int cx1 = mesh_cell(fmax(x0, fmax(x1, x2)), g.lo[0], g.inv_h, g.n[0]);
-        int cy0 = mesh_cell(fmin(y0, fmin(y1, y2)), g.lo[1], g.inv_h, g.n[1]);
-        int cy1 = mesh_cell(fmax(y0, fmax(y1, y2)), g.lo[1], g.inv_h, g.n[1]);
         trect[k] = make_int4(cx0, cy0, cx1, cy1);
         for (int cy = cy0; cy <= cy1; cy++)
             for (int cx = cx0; cx <= cx1; cx++) atomicAdd(&count[(int64_t)cy * g.n[0] + cx], 1);
@@ -260,7 +287,7 @@ __global__ void __launch_bounds__(256) k_locate(Grid g, double bx0, double by0, 
                                                 const int32_t* __restrict__ start,
                                                 const int32_t* __restrict__ items,
                                                 const float4* __restrict__ vhl, double ox,
-                                                double oy, float delta, int use32,
+                                                double oy, float delta, int use32, float ihf,
                                                 const double* __restrict__ pts, int64_t n,
                                                 const double* __restrict__ field,
                                                 int32_t* __restrict__ elem,
@@ -273,13 +300,17 @@ __global__ void __launch_bounds__(256) k_locate(Grid g, double bx0, double by0, 
         int nz = 0;
         int32_t v0 = 0, v1 = 0, v2 = 0;
         if (px >= bx0 && px <= bx1 && py >= by0 && py <= by1) {
-            const int64_t c = (int64_t)mesh_cell(py, g.lo[1], g.inv_h, g.n[1]) * g.n[0] +
-                              mesh_cell(px, g.lo[0], g.inv_h, g.n[0]);
-            const int a = start[c], b = start[c + 1];
-            // the point in the FP32 filter's frame
+            // the point in the FP32 filter's frame (the origin is the grid's)
             const double rx = px - ox, ry = py - oy;
             const float phx = (float)rx, phy = (float)ry;
             const float plx = (float)(rx - (double)phx), ply = (float)(ry - (double)phy);
+            // its cell: in FP32 when the triangles' ranges were (widened by CELL_MARGIN)
+            const int64_t c =
+                use32 ? (int64_t)cell32((phy + ply) * ihf, g.n[1]) * g.n[0] +
+                            cell32((phx + plx) * ihf, g.n[0])
+                      : (int64_t)mesh_cell(py, g.lo[1], g.inv_h, g.n[1]) * g.n[0] +
+                            mesh_cell(px, g.lo[0], g.inv_h, g.n[0]);
+            const int a = start[c], b = start[c + 1];
             for (int it = a; it < b; it++) {
                 const int32_t k = items[it];
                 const int s = tsign[k];
@@ -392,7 +423,9 @@ void mesh_create(MeshImpl& M, const double* xy, int64_t nv, const int32_t* tri, 
         k_tri_prep<<<blocks_for(ntri, 256), 256, 0, s>>>(nv, M.xy.as<double>(), ntri,
                                                          M.tri.as<int32_t>(), g, count.as<int32_t>(),
                                                          M.tsign.as<int8_t>(), trect.as<int4>(),
-                                                         badid.as<unsigned long long>());
+                                                         badid.as<unsigned long long>(),
+                                                         M.vhl.as<float4>(), M.use32 ? 1 : 0,
+                                                         M.delta, (float)g.inv_h);
     }
     PCMS_LAUNCH_CHECK("k_tri_prep");
     M.cell_start.alloc(sizeof(int32_t) * (g.ncell + 1), s);
@@ -520,7 +553,7 @@ void mesh_locate(const MeshImpl& M, const double* pts, int64_t n, const double* 
         M.g, M.bbox[0], M.bbox[1], M.bbox[2], M.bbox[3], M.nv, M.xy.as<double>(), M.ntri,
         M.tri.as<int32_t>(), M.tsign.as<int8_t>(), M.cell_start.as<int32_t>(),
         M.items.as<int32_t>(), M.vhl.as<float4>(), M.origin[0], M.origin[1], M.delta, M.use32,
-        pts, n, field, elem, edim, vals);
+        (float)M.g.inv_h, pts, n, field, elem, edim, vals);
     PCMS_LAUNCH_CHECK("k_locate");
 }
 
