@@ -1,5 +1,6 @@
 // util.cu -- errors, device memory, bounding box, prefix scan and the counting sort of
 // points into uniform-grid cells (the search structure of Sec. 3.3).
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -103,54 +104,65 @@ Grid make_grid(int dim, const double* lo, const double* hi, double radius, int64
 // number of non-finite coordinates it saw. One launch, no initialisation; the host combines
 // the partial boxes after its copy (bbox_combine). Each thread loads BB_UNROLL points per
 // coordinate plane before it reduces them, so that enough loads are in flight for the
-// kernel to stream at HBM speed with one block per SM.
+// kernel to stream at HBM speed with one block per SM. The comparisons run on the integer
+// pipe: a double's bits x map to the signed integer x ^ ((x >> 63) & 0x7fff...), which orders
+// like the values (-0 just below +0), so min and max need no FP64 instruction; a coordinate
+// is non-finite when its exponent bits are all set.
 constexpr int BB_UNROLL = 4;
+
+__device__ __forceinline__ long long order_key(long long b) {
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
 
 template <int DIM>
 __global__ void __launch_bounds__(256) k_bbox_partial(const double* __restrict__ pts, int64_t n,
                                                       double* __restrict__ part) {
     __shared__ double sh[8][7];
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    double nb = 0.0;
+    long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+    int nb = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const long long* bits = reinterpret_cast<const long long*>(pts);
     for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n;
          i0 += BB_UNROLL * stride) {
-        double x[DIM][BB_UNROLL];
+        long long x[DIM][BB_UNROLL];
 #pragma unroll
         for (int d = 0; d < DIM; d++)
 #pragma unroll
             for (int u = 0; u < BB_UNROLL; u++) {
                 const int64_t i = i0 + u * stride;
-                x[d][u] = i < n ? pts[d * n + i] : 0.0;
+                x[d][u] = i < n ? bits[d * n + i] : 0LL;
             }
 #pragma unroll
         for (int u = 0; u < BB_UNROLL; u++) {
             if (i0 + u * stride >= n) break;
 #pragma unroll
             for (int d = 0; d < DIM; d++) {
-                if (!isfinite(x[d][u])) {
-                    nb += 1.0;
+                const long long b = x[d][u];
+                if ((b & 0x7ff0000000000000LL) == 0x7ff0000000000000LL) {
+                    nb++;
                     continue;
                 }
-                lo[d] = fmin(lo[d], x[d][u]);
-                hi[d] = fmax(hi[d], x[d][u]);
+                const long long k = order_key(b);
+                lo[d] = min(lo[d], k);
+                hi[d] = max(hi[d], k);
             }
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
         for (int d = 0; d < 3; d++) {
-            lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
-            hi[d] = fmax(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+            lo[d] = min(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+            hi[d] = max(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
         }
         nb += __shfl_xor_sync(0xffffffffu, nb, o);
     }
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
         for (int d = 0; d < 3; d++) {
-            sh[w][d] = lo[d];
-            sh[w][3 + d] = hi[d];
+            // back to doubles; no finite coordinate on an axis gives (+inf, -inf)
+            sh[w][d] = lo[d] == LLONG_MAX ? INFINITY : __longlong_as_double(order_key(lo[d]));
+            sh[w][3 + d] = hi[d] == LLONG_MIN ? -INFINITY : __longlong_as_double(order_key(hi[d]));
         }
-        sh[w][6] = nb;
+        sh[w][6] = (double)nb;
     }
     __syncthreads();
     if (threadIdx.x < 7) {
