@@ -21,10 +21,15 @@ int mom_kind(bool mixed, int acc) {
 }
 size_t mom_elem_bytes(int kind) { return kind == MOM_F32 ? sizeof(float) : sizeof(double); }
 
-// Cell edge of the source grid: r/3 in 2D, r/2 in 3D. Smaller cells trim candidate rows
+// Cell edge of the source grid: r/3 in 2D, r/2 in 3D; r/6 in 2D for dense neighbourhoods
+// (expected count >= 1000, the blocked-compensation plan). Smaller cells trim candidate rows
 // closer to the ball at the price of more rows per target; measured on the 4M 2D and 8M 3D
-// transfers, r/3 is 5% faster in 2D and 6% slower in 3D than r/2.
-double cell_edge(int dim, double radius) { return (dim == 2 ? 1.0 / 3.0 : 0.5) * radius; }
+// transfers, r/3 is 5% faster in 2D and 6% slower in 3D than r/2, and with thousands of
+// candidates per row the rows of r/6 cells cost little beside the candidates they save.
+double cell_edge(int dim, double radius, double mean = 0.0) {
+    if (dim == 2) return (mean >= 1000.0 ? 1.0 / 6.0 : 1.0 / 3.0) * radius;
+    return 0.5 * radius;
+}
 
 int asm_blocks(int64_t nwork, int G) {
     int64_t groups_per_block = 8 * (32 / G);
@@ -409,7 +414,7 @@ MlsParams settle_growth(const MlsParams& P, const double* src, int64_t ns, const
     const int dim = P.dim;
     const bool mixed = P.prec == PCMS_MIXED;
     BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
-    Grid g = make_grid(dim, b.lo, b.hi, cell_edge(dim, P.radius), MAX_CELLS);
+    Grid g = make_grid(dim, b.lo, b.hi, cell_edge(dim, P.radius, choose_plan(dim, ns, P.radius, b.lo, b.hi, mixed).mean), MAX_CELLS);
     SortedPoints S, Tp;
     sort_points(g, src, ns, true, mixed, S, s);
     sort_points(g, tgt, nt, false, mixed, Tp, s, true);
@@ -502,7 +507,7 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
     const bool mixed = P.prec == PCMS_MIXED;
     const int64_t ns = M.ns, nt = M.nt;
     BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
-    M.g = make_grid(dim, b.lo, b.hi, cell_edge(dim, P.radius), MAX_CELLS);
+    M.g = make_grid(dim, b.lo, b.hi, cell_edge(dim, P.radius, choose_plan(dim, ns, P.radius, b.lo, b.hi, mixed).mean), MAX_CELLS);
     sort_points(M.g, src, ns, true, mixed, M.src, s);
     sort_points(M.g, tgt, nt, false, mixed, M.tgt, s, true);
     const AsmPlan plan = choose_plan(dim, ns, P.radius, b.lo, b.hi, mixed);
@@ -700,7 +705,7 @@ void mls_count(const MlsParams& P0, const double* src, int64_t ns, const double*
     const int dim = P.dim;
     const bool mixed = P.prec == PCMS_MIXED;
     BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
-    Grid g = make_grid(dim, b.lo, b.hi, cell_edge(dim, P.radius), MAX_CELLS);
+    Grid g = make_grid(dim, b.lo, b.hi, cell_edge(dim, P.radius, choose_plan(dim, ns, P.radius, b.lo, b.hi, mixed).mean), MAX_CELLS);
     SortedPoints S, Tp;
     sort_points(g, src, ns, true, mixed, S, s);
     sort_points(g, tgt, nt, false, mixed, Tp, s, true);
@@ -754,7 +759,7 @@ void mls_transfer(const MlsParams& P0, const double* src, int64_t ns, const doub
     const bool mixed = P.prec == PCMS_MIXED;
     *n_under = 0;
     BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
-    Grid g = make_grid(dim, b.lo, b.hi, cell_edge(dim, P.radius), MAX_CELLS);
+    Grid g = make_grid(dim, b.lo, b.hi, cell_edge(dim, P.radius, choose_plan(dim, ns, P.radius, b.lo, b.hi, mixed).mean), MAX_CELLS);
     SortedPoints S, Tp;
     sort_points(g, src, ns, true, mixed, S, s);
     sort_points(g, tgt, nt, false, mixed, Tp, s, true);
