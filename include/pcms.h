@@ -309,7 +309,10 @@ typedef struct {
      * map_key >= 0: keep the operator cached under this key; a later request with the same
      * key and reuse_map = 1 applies the cached operator to its own fields. A reuse request
      * still passes the same geometry (src/tgt): it is used to rebuild the operator if it was
-     * evicted. map_key < 0: nothing is cached. */
+     * evicted, or if the request's scratch does not fit under the cap beside it (the
+     * operator a request is admitted to apply is pinned before anything is evicted for it).
+     * The cached operator must have the request's n_src, n_tgt, dim and precision, else the
+     * request fails with PCMS_ERR_INVALID_ARG. map_key < 0: nothing is cached. */
     int dim, basis_degree;
     double radius;
     pcms_map_opts opts;
