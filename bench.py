@@ -300,7 +300,8 @@ class ServeWorkload:
         """The whole stream through the public serving API with host buffers: ordinary host
         inputs and outputs, submitted as host I/O requests, so the server copies each
         request's inputs in and its outputs back on the request's slot stream (overlapping
-        the other slots' kernels); every copy is inside the timed region."""
+        the other slots' kernels); every copy is inside the timed region. (Page-locked
+        buffers, copied directly, measured slower here than the server's bounce buffers.)"""
         torch = self.torch
         host = self.S.to_host(self.dreqs)
         torch.cuda.synchronize()
