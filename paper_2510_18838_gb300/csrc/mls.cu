@@ -260,14 +260,18 @@ void solve_tiers(int dim, int deg, int mode, bool mixed, AsmPlan plan, const Asm
     const int np = accp(dim, deg, mode);
     const int G = plan.G;
     const int mk1 = mom_kind(mixed, plan.acc);
-    DBuf lists(sizeof(int32_t) * (2 * nt + 3), s);
+    DBuf lists(sizeof(int32_t) * (3 * nt + 4), s);
     int32_t* list2 = lists.as<int32_t>();
     int32_t* list3 = list2 + nt;
-    int32_t* n2 = list2 + 2 * nt;
+    int32_t* fb = list3 + nt;   // the refined solve's declined work items (per mixed pass)
+    int32_t* n2 = fb + nt;
     int32_t* n3 = n2 + 1;
     int32_t* n_rc = n2 + 2;
+    int32_t* n_fb = n2 + 3;
     DBuf basis2(sizeof(float4) * nt, s);
-    PCMS_CU(cudaMemsetAsync(n2, 0, 3 * sizeof(int32_t), s));
+    PCMS_CU(cudaMemsetAsync(n2, 0, 4 * sizeof(int32_t), s));
+    sa.fb_list = fb;
+    sa.n_fb = n_fb;
     sa.list2 = list2;
     sa.n2 = n2;
     sa.list3 = list3;
@@ -321,9 +325,10 @@ void solve_tiers(int dim, int deg, int mode, bool mixed, AsmPlan plan, const Asm
         solve_any(dim, deg, mode, MOM_F64, s4, thread_blocks(n_ref, 128), s);
         return;
     }
-    int32_t cnt[3] = {0, 0, 0};
+    int32_t cnt[4] = {0, 0, 0, 0};
     PCMS_CU(cudaMemcpyAsync(cnt, n2, sizeof(cnt), cudaMemcpyDeviceToHost, s));
     PCMS_CU(cudaStreamSynchronize(s));
+    trace_count("mls_tier1_fp64_solves", cnt[3]);
     trace_count("mls_tier1_targets", nt - cnt[0] - cnt[1]);
     trace_count("mls_tier1_recentred_solves", cnt[2]);
     trace_count("mls_tier2_targets", cnt[0]);
@@ -349,6 +354,7 @@ void solve_tiers(int dim, int deg, int mode, bool mixed, AsmPlan plan, const Asm
         assemble_any(dim, deg, true, mode, G, ACC_BK, false, a2, asm_blocks(cnt[0], G), s);
         SolveArgs s2 = sa;
         s2.n_recentred = nullptr;
+        PCMS_CU(cudaMemsetAsync(n_fb, 0, sizeof(int32_t), s));   // tier 2's own declined items
         s2.list = list2;
         s2.n_list = n2;
         s2.mom = mom2.p;

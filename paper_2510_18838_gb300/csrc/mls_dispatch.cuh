@@ -115,9 +115,15 @@ inline void shape_apply_any(int dim, int deg, int G, const ShapeArgs& a, int blo
     }                                                                                         \
     template <int DEG, int MODE>                                                              \
     static void solve_deg(int mk, const SolveArgs& a, int b, cudaStream_t s) {                \
-        if (mk == MOM_F64) k_solve<DIMV, DEG, MODE, double><<<b, 128, 0, s>>>(a);            \
-        else if (mk == MOM_F32PAIR) k_solve<DIMV, DEG, MODE, float2><<<b, 128, 0, s>>>(a);   \
-        else k_solve<DIMV, DEG, MODE, float><<<b, 128, 0, s>>>(a);                           \
+        if (mk == MOM_F64) {                                                                  \
+            k_solve<DIMV, DEG, MODE, double><<<b, 128, 0, s>>>(a);                            \
+        } else if (mk == MOM_F32PAIR) {                                                       \
+            k_solve<DIMV, DEG, MODE, float2, 1><<<b, 128, 0, s>>>(a);                         \
+            k_solve<DIMV, DEG, MODE, float2, 2><<<b, 128, 0, s>>>(a);                         \
+        } else {                                                                              \
+            k_solve<DIMV, DEG, MODE, float, 1><<<b, 128, 0, s>>>(a);                          \
+            k_solve<DIMV, DEG, MODE, float, 2><<<b, 128, 0, s>>>(a);                          \
+        }                                                                                     \
     }                                                                                         \
     void solve_dispatch_d##DIMV(int deg, int mode, int mk, const SolveArgs& a, int b,           \
                               cudaStream_t s) {                                               \

@@ -170,6 +170,8 @@ struct SolveArgs {
     const float4* basis_in;   // basis of these moments: per list position (list mode), else
                               // per target (tier 1 with an estimated basis), or null
     int32_t* n_recentred;     // tier 1: targets solved in an estimated re-centred basis, or null
+    int32_t* fb_list;         // mixed tiers: work items (wk) the refined FP32 solve declined,
+    int32_t* n_fb;            // solved in FP64 by a second launch (k_solve<..., PASS 2>)
     float4* basis2;           // tier 1: basis for tier 2, per list2 position
     float4* rc;               // MAP: basis of the accepted tier-2 rows, per sorted target
     int32_t* list2;           // targets for tier 2 / tier 3
@@ -1300,15 +1302,20 @@ __host__ __device__ __forceinline__ double amp_bound(int acc, int n, int group) 
     return (double)((float)AMP_BK * sqrtf(nf));
 }
 
-template <int DIM, int DEG, int MODE, typename MT>
-__global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
+// PASS: 0 = FP64 moments (one FP64 solve); for FP32 moments (the mixed tiers) 1 = the refined
+// FP32 solve, whose declined work items go to fb_list, and 2 = the FP64 solve of those items.
+// Two launches keep the FP64 solve's registers out of the refined pass.
+template <int DIM, int DEG, int MODE, typename MT, int PASS = 0>
+__global__ void __launch_bounds__(128, PASS == 1 ? 3 : 1) k_solve(SolveArgs S) {
     constexpr int NM = mono_count(DIM, 2 * DEG);
     constexpr int M = mono_count(DIM, DEG);
     constexpr int NACC = MODE == MODE_FUSED ? NM + M : NM;
     constexpr int NACCP = round_up4(NACC);
-    const int64_t nwork = S.list ? (int64_t)(*S.n_list) : S.nt;
-    for (int64_t wk = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; wk < nwork;
-         wk += (int64_t)gridDim.x * blockDim.x) {
+    static_assert((PASS == 0) == std::is_same<MT, double>::value, "passes: FP32 moments only");
+    const int64_t nwork = PASS == 2 ? (int64_t)(*S.n_fb) : (S.list ? (int64_t)(*S.n_list) : S.nt);
+    for (int64_t ii = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ii < nwork;
+         ii += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t wk = PASS == 2 ? (int64_t)S.fb_list[ii] : ii;
         const int64_t t = S.list ? (int64_t)S.list[wk] : wk;
         const int cnt = S.counts[t];
         int st = PCMS_TARGET_OK;
@@ -1328,17 +1335,21 @@ __global__ void __launch_bounds__(128) k_solve(SolveArgs S) {
                 bas = S.basis_in[wk];
                 recentred = !is_target_centred(bas);
                 if (recentred) basis_at_target<DIM, DEG>(bas, at);
-                if (recentred && S.n_recentred) atomicAdd(S.n_recentred, 1);
+                if (PASS != 2 && recentred && S.n_recentred) atomicAdd(S.n_recentred, 1);
             }
-            if constexpr (!std::is_same<MT, double>::value) {
+            if constexpr (PASS == 1) {
+                int rs = 0;
                 if (S.lambda == 0.0) {
                     const double acc_amp = amp_bound(S.acc, cnt, S.group);
-                    const int rs = solve_moments_refined<DIM, DEG, MODE, MT>(
+                    rs = solve_moments_refined<DIM, DEG, MODE, MT>(
                         src, recentred ? at : nullptr, acc_amp, yh, yl, &val, &amp);
-                    refined = rs != 0;
                 }
-            }
-            if (!refined) {
+                if (rs == 0) {   // the FP64 pass solves it
+                    S.fb_list[atomicAdd(S.n_fb, 1)] = (int32_t)wk;
+                    continue;
+                }
+                refined = true;
+            } else {
 #pragma unroll
                 for (int i = 0; i < NACC; i++) mom[i] = mom_value(src[i]);
                 if (!solve_moments<DIM, DEG, MODE>(mom, S.lambda, S.tau, y, &val, &amp,
