@@ -407,8 +407,7 @@ __device__ __forceinline__ int cell_of(double x, double lo, double inv_h, int n)
 }
 
 __global__ void k_cell_keys(Grid g, const double* __restrict__ pts, int64_t n,
-                            uint32_t* __restrict__ key, uint32_t* __restrict__ idx,
-                            int32_t* __restrict__ count) {
+                            uint32_t* __restrict__ key, uint32_t* __restrict__ idx) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         int c = cell_of(pts[i], g.lo[0], g.inv_h, g.n[0]);
@@ -417,7 +416,6 @@ __global__ void k_cell_keys(Grid g, const double* __restrict__ pts, int64_t n,
             c += g.n[0] * g.n[1] * cell_of(pts[2 * n + i], g.lo[2], g.inv_h, g.n[2]);
         key[i] = (uint32_t)c;
         idx[i] = (uint32_t)i;
-        if (count) atomicAdd(&count[c], 1);
     }
 }
 
@@ -691,7 +689,7 @@ void sort_points(const Grid& g, const double* pts, int64_t n, bool with_start, b
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8));
     if (n > 0) {
         PCMS_TRACE("grid_cell_keys", s);
-        k_cell_keys<<<blocks, 256, 0, s>>>(g, pts, n, k0, v0, nullptr);
+        k_cell_keys<<<blocks, 256, 0, s>>>(g, pts, n, k0, v0);
     }
     PCMS_LAUNCH_CHECK("cell_keys");
     uint32_t* skey = k0;
