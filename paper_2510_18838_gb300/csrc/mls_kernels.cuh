@@ -1147,9 +1147,9 @@ constexpr float REFINE_PIVOT = 1e-4f;
 
 template <int DIM, int DEG, int MODE, typename MT>
 __host__ __device__ __forceinline__ int solve_moments_refined(const MT* mt, const double* at,
-                                                              double amp_accept, float* yh,
+                                                              float amp_accept, float* yh,
                                                               float* yl, double* c0,
-                                                              double* amp) {
+                                                              float* amp) {
     constexpr int NM = mono_count(DIM, 2 * DEG);
     constexpr int M = mono_count(DIM, DEG);
     constexpr int NP = M * (M + 1) / 2;
@@ -1229,8 +1229,8 @@ __host__ __device__ __forceinline__ int solve_moments_refined(const MT* mt, cons
     };
     const float amp0 = amp_of();
     if (!(amp0 <= 1e30f)) return 0;
-    if ((double)amp0 > 1.01 * amp_accept) {
-        *amp = (double)amp0;
+    if (amp0 > 1.01f * amp_accept) {
+        *amp = amp0;
         return 2;
     }
     const float tol = 9.5367431640625e-07f / fmaxf(amp0, 1.f);   // 2^-20 / amp
@@ -1287,19 +1287,19 @@ __host__ __device__ __forceinline__ int solve_moments_refined(const MT* mt, cons
         }
         *c0 = (double)ch + (double)cl;
     }
-    *amp = (double)amp_of();
+    *amp = amp_of();
     return 1;
 }
 
 // A tier's acceptance bound on amp for a target of n neighbours (the tier table above),
 // evaluated in FP32: the bound is a calibrated constant, not a precision-critical quantity.
-__host__ __device__ __forceinline__ double amp_bound(int acc, int n, int group) {
+__host__ __device__ __forceinline__ float amp_bound(int acc, int n, int group) {
     const float nf = (float)n;
     if (acc == ACC_PLAIN) {
         const float g = (float)group;
-        return (double)((float)AMP_T1 / (1.f + sqrtf(nf / (3.f * g * g))));
+        return (float)AMP_T1 / (1.f + sqrtf(nf / (3.f * g * g)));
     }
-    return (double)((float)AMP_BK * sqrtf(nf));
+    return (float)AMP_BK * sqrtf(nf);
 }
 
 // PASS: 0 = FP64 moments (one FP64 solve); for FP32 moments (the mixed tiers) 1 = the refined
@@ -1320,6 +1320,7 @@ __global__ void __launch_bounds__(128, PASS == 1 ? 3 : 1) k_solve(SolveArgs S) {
         const int cnt = S.counts[t];
         int st = PCMS_TARGET_OK;
         double val = 0.0, amp = 0.0;
+        float amp32 = 0.f;   // amp for routing and row flags (the refined pass works in FP32)
         double y[M];
         double mom[NACC];
         float yh[M], yl[M];   // the refined FP32 solve's y (mixed tiers), as pairs
@@ -1340,9 +1341,9 @@ __global__ void __launch_bounds__(128, PASS == 1 ? 3 : 1) k_solve(SolveArgs S) {
             if constexpr (PASS == 1) {
                 int rs = 0;
                 if (S.lambda == 0.0) {
-                    const double acc_amp = amp_bound(S.acc, cnt, S.group);
                     rs = solve_moments_refined<DIM, DEG, MODE, MT>(
-                        src, recentred ? at : nullptr, acc_amp, yh, yl, &val, &amp);
+                        src, recentred ? at : nullptr, amp_bound(S.acc, cnt, S.group), yh, yl,
+                        &val, &amp32);
                 }
                 if (rs == 0) {   // the FP64 pass solves it
                     S.fb_list[atomicAdd(S.n_fb, 1)] = (int32_t)wk;
@@ -1355,17 +1356,18 @@ __global__ void __launch_bounds__(128, PASS == 1 ? 3 : 1) k_solve(SolveArgs S) {
                 if (!solve_moments<DIM, DEG, MODE>(mom, S.lambda, S.tau, y, &val, &amp,
                                                    recentred ? at : nullptr))
                     st = PCMS_TARGET_ILL_CONDITIONED;
+                amp32 = (float)amp;
             }
         }
         if (S.tier == 4 && st != PCMS_TARGET_OK) continue;   // keep the first FP64 solve
-        if (S.tier == 3 && S.refine64 && st == PCMS_TARGET_OK && amp > AMP_FP64) {
+        if (S.tier == 3 && S.refine64 && st == PCMS_TARGET_OK && amp32 > (float)AMP_FP64) {
             const int pos = atomicAdd(S.n2, 1);
             S.list2[pos] = (int32_t)t;
             S.basis2[pos] = recentre_basis<DIM>(mom);
         }
         if (S.tier < 3 && st != PCMS_TARGET_UNDERDETERMINED) {
             bool ok = st == PCMS_TARGET_OK;
-            if (ok) ok = amp <= amp_bound(S.acc, cnt, S.group);
+            if (ok) ok = amp32 <= amp_bound(S.acc, cnt, S.group);
             if (!ok) {
                 // tier 2 only helps if it differs from this pass: a plain tier 1, or a
                 // re-centred basis
@@ -1391,8 +1393,8 @@ __global__ void __launch_bounds__(128, PASS == 1 ? 3 : 1) k_solve(SolveArgs S) {
         // 2 = everything in FP64 (tier 3: y belongs to the exact FP64 moments);
         // 3 = as 1 in the re-centred basis rc[t]; 4 = as 0 in the re-centred basis rc[t]
         if (MODE == MODE_MAP && S.flags) {
-            const int flag = recentred ? (amp > AMP_SHAPE ? 3 : 4)
-                                       : (S.tier == 3 ? 2 : (amp > AMP_SHAPE ? 1 : 0));
+            const int flag = recentred ? (amp32 > (float)AMP_SHAPE ? 3 : 4)
+                                       : (S.tier == 3 ? 2 : (amp32 > (float)AMP_SHAPE ? 1 : 0));
             S.flags[t] = (int8_t)flag;
             if (recentred && S.rc) S.rc[t] = bas;
         }

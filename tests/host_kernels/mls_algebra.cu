@@ -192,7 +192,11 @@ extern "C" void hk_recentre_basis(int dim, const double* mom, float* out) {
 template <int DIM, int DEG, int MODE, typename MT>
 static int refined_t(const MT* mt, const double* at, double amp_accept, float* yh, float* yl,
                      double* c0, double* amp) {
-    return solve_moments_refined<DIM, DEG, MODE, MT>(mt, at, amp_accept, yh, yl, c0, amp);
+    float a = 0.f;
+    const int rc = solve_moments_refined<DIM, DEG, MODE, MT>(mt, at, (float)amp_accept, yh, yl,
+                                                             c0, &a);
+    *amp = (double)a;
+    return rc;
 }
 
 extern "C" int hk_solve_refined(int dim, int deg, int fused, int pairs, int nacc,
