@@ -1112,7 +1112,7 @@ __host__ __device__ inline void basis_at_target(float4 b, double* at) {
     });
 }
 
-// The mixed tiers' solve without the FP64 pipe. G y = a_t is solved by iterative refinement:
+// The mixed tiers' solve without FP64 arithmetic. G y = a_t is solved by iterative refinement:
 // an FP32 LDL^T of G's leading FP32 parts gives each correction, and every residual
 // a_t - G y is formed in double-FP32 arithmetic (TwoProduct by FMA, TwoSum) from the moments
 // as stored (plain FP32 sums are exact FP32 values; blocked sums are FP32 pairs), with y kept
