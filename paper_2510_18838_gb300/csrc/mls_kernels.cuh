@@ -473,13 +473,14 @@ using MomT = typename std::conditional<ACC == ACC_BK, float2, T>::type;
 
 // Two blocks per SM (at most 128 registers) except: the blocked 3D quadratic form, whose
 // three accumulator sets of 35-45 moments would spill heavily at that size (one block); and
-// plain sums of at most 15 moments (degree <= 1, or 2D), three blocks (80 registers): the
+// plain FP32 sums of at most 15 moments (degree <= 1, or 2D), three blocks (80 registers): the
 // walk is latency-bound, and the extra warps cut the serving stream's assembly time by 9%
 // despite a few dozen bytes of spills.
-template <int DIM, int DEG, int ACC>
+template <int DIM, int DEG, int ACC, bool MIXED>
 constexpr int asm_min_blocks() {
-    return (ACC == ACC_BK && DIM == 3 && DEG == 2) ? 1
-                                                     : ((ACC == ACC_PLAIN && (DEG <= 1 || DIM == 2)) ? 3 : 2);
+    return (ACC == ACC_BK && DIM == 3 && DEG == 2)
+               ? 1
+               : ((MIXED && ACC == ACC_PLAIN && (DEG <= 1 || DIM == 2)) ? 3 : 2);
 }
 
 // Candidate row rho of a target (cell (ct) and position in it (fr), cell units): the cells
@@ -587,7 +588,7 @@ __device__ __forceinline__ float4 estimate_basis(const AsmArgs& A, const long lo
 }
 
 template <int DIM, int DEG, bool MIXED, int MODE, int G, typename FT, int ACC = ACC_PLAIN>
-__global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC>()) k_assemble(AsmArgs A) {
+__global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC, MIXED>()) k_assemble(AsmArgs A) {
     static_assert(ACC == ACC_PLAIN || (MIXED && MODE != MODE_COUNT), "blocked compensation: mixed moments only");
     using T = typename std::conditional<MIXED, float, double>::type;
     using MT = MomT<T, ACC>;
