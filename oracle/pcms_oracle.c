@@ -483,7 +483,7 @@ static int solve_target(int dim, int degree, int wkind, double lambda, const dou
     }
     /* values: back substitution R c = (Q^T rhs)[0:m]; value = c_0 */
     for (int f = 0; f < nf; f++) {
-        double c[10];
+        double c[ORC_MAX_TERMS];
         for (int k = m - 1; k >= 0; k--) {
             double s = rhs[f * rows + k];
             for (int l = k + 1; l < m; l++) s -= B[l * rows + k] * c[l];
