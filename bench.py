@@ -58,7 +58,7 @@ TRANSFER_NAME = ("transfer_mix: mesh 512x512 jittered (524,288 tri) 1M pts + MLS
 
 
 # ------------------------------------------------------------------------------------
-# algorithmic work models
+# algorithmic work models (per selected pair, per nonzero)
 # ------------------------------------------------------------------------------------
 def mono_count(dim, deg):
     return math.comb(dim + deg, deg)

@@ -193,7 +193,9 @@ pcms_status pcms_count_neighbors(int dim, const double* src_pts, int64_t n_src,
  *   call before any stream capture. Every call shares the one array and every element a
  *   call reads is written earlier by the same call, so nothing carries over between calls;
  *   calls whose work can overlap on the GPU (different streams, or host threads) race on
- *   the array and must be ordered by the caller. Arguments as pcms_apply_map.
+ *   the array and must be ordered by the caller. If a CUDA error from earlier work is
+ *   pending on the calling thread, the call launches nothing, returns PCMS_ERR_CUDA and
+ *   leaves that error pending for its owner. Arguments as pcms_apply_map.
  */
 pcms_status pcms_apply_map_noalloc(pcms_map map, const void* fields, int n_fields, void* out,
                                    void* stream);

@@ -330,36 +330,46 @@ void apply_t(MapImpl& M, const T* fields, int nf, T* out, cudaStream_t s) {
 }
 
 // The same three kernels as apply_t, with caller-provided scratch: fs needs ns*fp and stage
-// nt*fp elements. Launch errors are returned, nothing is allocated or traced.
+// nt*fp elements. Nothing is allocated or traced. Each launch is checked on its own, so an
+// error returned here is one of these launches; *where names it. The caller makes sure no
+// earlier error is pending on the thread before calling (it would otherwise surface here).
 template <typename T>
 cudaError_t apply_with_scratch_t(const MapImpl& M, const T* fields, int nf, T* out, T* fs,
-                                 T* stage, unsigned long long* next, cudaStream_t s) {
+                                 T* stage, unsigned long long* next, cudaStream_t s,
+                                 const char** where) {
     const int64_t ns = M.ns, nt = M.nt;
     constexpr int W = Vec<T>::W;
     int nvec = 1;
     while (nvec * W < nf) nvec <<= 1;
     const int fp = nf == 1 ? 1 : nvec * W;
-    if (ns > 0)
+    cudaError_t e = cudaSuccess;
+    if (ns > 0) {
         k_fields_to_sorted<T><<<blocks_for(ns, 256), 256, 0, s>>>(fields, nf, fp, ns,
                                                                   M.src.inv.as<int32_t>(), fs);
+        if ((e = cudaGetLastError()) != cudaSuccess) { *where = "k_fields_to_sorted"; return e; }
+    }
     if (nt > 0) {
         const int64_t* off = M.offsets.as<int64_t>();
         const int32_t* rc = M.counts.as<int32_t>();
         const int32_t* cols = M.cols.as<int32_t>();
         const T* vals = M.vals.as<T>();
         const int8_t* st = M.status.as<int8_t>();
-        const cudaError_t me = cudaMemsetAsync(next, 0, sizeof(unsigned long long), s);
-        if (me != cudaSuccess) return me;
+        if ((e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), s)) != cudaSuccess) {
+            *where = "cudaMemsetAsync (row-chunk counter)";
+            return e;
+        }
         const int nv = fp / W;
         if (fp == 1) k_spmm_1<T><<<spmm_blocks(k_spmm_1<T>, nt), 256, 0, s>>>(nt, off, rc, cols, vals, fs, st, stage, next);
         else if (nv == 1) k_spmm_vec<T, 1><<<spmm_blocks(k_spmm_vec<T, 1>, nt), 256, 0, s>>>(nt, off, rc, cols, vals, fs, st, stage, next);
         else if (nv == 2) k_spmm_vec<T, 2><<<spmm_blocks(k_spmm_vec<T, 2>, nt), 256, 0, s>>>(nt, off, rc, cols, vals, fs, st, stage, next);
         else if (nv == 4) k_spmm_vec<T, 4><<<spmm_blocks(k_spmm_vec<T, 4>, nt), 256, 0, s>>>(nt, off, rc, cols, vals, fs, st, stage, next);
         else k_spmm_vec<T, 8><<<spmm_blocks(k_spmm_vec<T, 8>, nt), 256, 0, s>>>(nt, off, rc, cols, vals, fs, st, stage, next);
+        if ((e = cudaGetLastError()) != cudaSuccess) { *where = "k_spmm"; return e; }
         k_stage_to_caller<T><<<blocks_for(nt, 256), 256, 0, s>>>(stage, fp, nf, nt,
                                                                  M.tgt.inv.as<int32_t>(), out);
+        if ((e = cudaGetLastError()) != cudaSuccess) { *where = "k_stage_to_caller"; return e; }
     }
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 // export: row lengths in caller order, scan, then a warp per row copies (col, val)
@@ -451,7 +461,7 @@ int64_t apply_scratch_bytes(const MapImpl& M, int nf) {
 }
 
 cudaError_t mls_apply_with_scratch(const MapImpl& M, const void* fields, int nf, void* out,
-                                   void* scratch, cudaStream_t s) {
+                                   void* scratch, cudaStream_t s, const char** where) {
     const int64_t elem = M.P.prec == PCMS_MIXED ? 4 : 8;
     const int W = M.P.prec == PCMS_MIXED ? 4 : 2;
     int nvec = 1;
@@ -462,9 +472,9 @@ cudaError_t mls_apply_with_scratch(const MapImpl& M, const void* fields, int nf,
     auto* next = (unsigned long long*)(stage + (M.nt * fp * elem + 255) / 256 * 256);
     if (M.P.prec == PCMS_MIXED)
         return apply_with_scratch_t<float>(M, (const float*)fields, nf, (float*)out, (float*)fs,
-                                           (float*)stage, next, s);
+                                           (float*)stage, next, s, where);
     return apply_with_scratch_t<double>(M, (const double*)fields, nf, (double*)out,
-                                        (double*)fs, (double*)stage, next, s);
+                                        (double*)fs, (double*)stage, next, s, where);
 }
 
 void mls_export(MapImpl& M, int64_t* offsets, int32_t* cols, double* vals, int8_t* status,

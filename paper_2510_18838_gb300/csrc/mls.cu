@@ -484,7 +484,10 @@ int64_t estimate_mls_bytes(const MlsParams& P, int64_t ns, int64_t nt, int nf, b
     b += nt * 33.0;                                                  // re-centred bases, row flags
     const double nnz = 1.3 * k * nt;
     if (keep_map || nf > 2) b += nnz * (4.0 + elem);                 // operator
-    b += (double)(ns + nt) * std::max(nf, 1) * elem * 2.0;           // apply/permute scratch
+    int fw = 1;                                                      // fields padded to the
+    while (fw * (mixed ? 4 : 2) < nf) fw <<= 1;                      // apply's vector width
+    const double fp = nf <= 1 ? 1.0 : (double)fw * (mixed ? 4 : 2);
+    b += (double)(ns + nt) * fp * elem * 2.0;                        // apply/permute scratch
     b += (mixed ? 26.0 : 4.0) * std::min<double>((double)(int64_t(1) << 24), 2.0 * ns + 64.0);
     // cell starts (and, mixed, the cell-sum pyramid of the tier-1 basis estimates)
     if (mixed) b += nt * 16.0;                                       // estimated bases

@@ -46,6 +46,14 @@ extern "C" pcms_status pcms_apply_map_noalloc(pcms_map map, const void* fields, 
                              " bytes of scratch, above the fixed " +
                              std::to_string(NOALLOC_SCRATCH_BYTES) +
                              " bytes; use pcms_apply_map");
+    // An error left pending on this thread by earlier, unrelated work would surface at this
+    // call's first launch check and be reported as this call's own. Leave it pending for its
+    // owner, launch nothing, and say so.
+    const cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess)
+        return fail_with(PCMS_ERR_CUDA,
+                         std::string("a CUDA error from earlier work is pending on this thread (") +
+                             cudaGetErrorString(pending) + "); nothing was launched");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
         cudaGetLastError();
@@ -68,12 +76,11 @@ extern "C" pcms_status pcms_apply_map_noalloc(pcms_map map, const void* fields, 
         }
         scratch = g_addr[dev];
     }
+    const char* where = "";
     const cudaError_t e = pcms::mls_apply_with_scratch(M, fields, n_fields, out, scratch,
-                                                       (cudaStream_t)stream);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail_with(PCMS_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
-    }
+                                                       (cudaStream_t)stream, &where);
+    if (e != cudaSuccess)
+        return fail_with(PCMS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
     pcms::set_last_error_message("");
     return PCMS_OK;
 }

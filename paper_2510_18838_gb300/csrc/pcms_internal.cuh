@@ -365,10 +365,10 @@ void stage_to_caller_f32(const MapImpl& M, const float* stage, int fp, int nf, f
                          cudaStream_t s);
 void mls_apply(MapImpl& M, const void* fields, int nf, void* out, cudaStream_t s);
 // apply with caller-provided scratch of apply_scratch_bytes(M, nf) bytes (256-aligned base);
-// allocates nothing, returns the launch status
+// allocates nothing, returns the first failing launch's status and names it in *where
 int64_t apply_scratch_bytes(const MapImpl& M, int nf);
 cudaError_t mls_apply_with_scratch(const MapImpl& M, const void* fields, int nf, void* out,
-                                   void* scratch, cudaStream_t s);
+                                   void* scratch, cudaStream_t s, const char** where);
 void mls_export(MapImpl& M, int64_t* offsets, int32_t* cols, double* vals, int8_t* status,
                 int32_t* kexp, cudaStream_t s);
 void mls_count(const MlsParams& P, const double* src, int64_t ns, const double* tgt, int64_t nt,

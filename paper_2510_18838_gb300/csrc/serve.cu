@@ -327,8 +327,9 @@ void worker(pcms_server_s* S, int slot) {
                     }
                     const bool hit = reuse && it != S->cache.end();
                     if (hit) {
-                        // only the apply scratch (and the staged fields) is new
-                        need = (int64_t)(r.n_src + r.n_tgt) * std::max(r.n_fields, 1) * 8 * 2 +
+                        // only the apply scratch (fields padded to the vector width, as the
+                        // apply allocates it) and the staged fields are new
+                        need = pcms::apply_scratch_bytes(*it->second.map, std::max(r.n_fields, 1)) +
                                (int64_t(1) << 20) + staged_bytes(r, false);
                         // pinned across the eviction below: evicting the operator this request
                         // is about to use would leave `it` (and the operator) freed

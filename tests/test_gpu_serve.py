@@ -169,3 +169,44 @@ def test_host_io_requests_match_device_requests(env, pin):
             if k in d.tensors:
                 a, b = d.tensors[k].cpu().numpy(), h.tensors[k].numpy()
                 assert np.array_equal(a, b, equal_nan=True), (d.req, k)
+
+
+def test_fp64_reuse_reserves_the_padded_apply_scratch(env):
+    """A float64 request that reuses a cached operator with 9 fields: the apply pads the
+    fields to 16 per row for its scratch (the fields in source order and the staged result,
+    16 * 8 bytes per source and per target). The server's reservation for the reuse, seen
+    in its peak above the cached operator, must cover that, and the values must equal a
+    fresh map's."""
+    torch, pcms, serve = env
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev).manual_seed(21)
+    ns, nt, nf = 30000, 12000, 9
+    src = torch.rand((2, ns), dtype=torch.float64, device=dev, generator=g)
+    tgt = torch.rand((2, nt), dtype=torch.float64, device=dev, generator=g)
+    f1 = torch.rand((1, ns), dtype=torch.float64, device=dev, generator=g)
+    f9 = torch.rand((nf, ns), dtype=torch.float64, device=dev, generator=g)
+    o1 = torch.empty((1, nt), dtype=torch.float64, device=dev)
+    o9 = torch.empty((nf, nt), dtype=torch.float64, device=dev)
+    s = pcms.Server(n_slots=1, mem_cap_bytes=2 << 30)
+    s.submit_mls(src, tgt, f1, o1, 1, 0.03, precision="fp64", map_key=3)
+    s.drain(120)
+    op_bytes = s.memory()["in_use"]
+    s.close()
+    s = pcms.Server(n_slots=1, mem_cap_bytes=2 << 30)
+    s.submit_mls(src, tgt, f1, o1, 1, 0.03, precision="fp64", map_key=3)
+    s.drain(120)
+    assert s.memory()["in_use"] == op_bytes
+    s.submit_mls(src, tgt, f9, o9, 1, 0.03, precision="fp64", map_key=3, reuse=True)
+    s.drain(120)
+    res = sorted(s.poll(8), key=lambda x: x["ticket"])
+    mem = s.memory()
+    s.close()
+    assert [x["status"] for x in res] == [pcms.OK, pcms.OK]
+    assert res[1]["cached"]
+    scratch = (ns + nt) * 16 * 8
+    assert mem["peak"] - op_bytes >= scratch, (mem, op_bytes, scratch)
+    m = pcms.create_map(src, tgt, 1, 0.03, precision="fp64")
+    ref = m.apply(f9).cpu().numpy()
+    m.destroy()
+    ok = np.isfinite(ref).all(axis=0)
+    assert normwise_err(o9.cpu().numpy(), ref, ok) <= TOL_FP64
