@@ -178,6 +178,58 @@ pcms_status pcms_count_neighbors(int dim, const double* src_pts, int64_t n_src,
                                  int32_t* radius_doublings, int64_t* total, void* stream);
 
 /*
+ * Batched one-shot MLS transfer of many small, independent problems (Sec. 3.2.1, Eq. 1:
+ * one local weighted fit per target, independent across targets and across problems).
+ *
+ * Each item is one transfer with its own sources, targets, radius, basis and fields, in
+ * the mixed precision of PCMS_MIXED with a user-given radius (min_neighbors = 0) and
+ * lambda = 0. Every item's selection, weights and fit are those of pcms_mls_transfer;
+ * what differs is the execution. The items are grouped by (dim, basis_degree, lanes per
+ * target); per group, one kernel sorts each item's sources into its own uniform grid (one
+ * thread block per item: bounding box, cell keys, counting sort, sorted FP64 and FP32
+ * hi/lo copies, fields in sorted order), and one persistent kernel takes (item, tile of
+ * targets) work units from a counter and runs, per target, the radius walk, the FP32
+ * moment assembly, the solve and the operator row applied to all fields, with the FP64
+ * assembly and solve in the same kernel for targets whose conditioning estimate rejects
+ * the FP32 moments. Neighbour counts from 10 to a few hundred per target, uneven across
+ * items, share the GPU through the work counter. Item results do not depend on the other
+ * items of the batch (bitwise).
+ *
+ *   src_pts/tgt_pts: device float64 [dim][n]; fields: device float32 [n_fields][n_src];
+ *   out: device float32 [n_fields][n_tgt], NaN where the target's status is not OK;
+ *   target_status: device int8 [n_tgt] or NULL (PCMS_TARGET_* codes).
+ *   Limits: dim 2 or 3; basis_degree 0..2; 1 <= n_fields <= 16; n_src, n_tgt <=
+ *   PCMS_BATCH_MAX_POINTS; radius finite and > 0; weight a pcms_weight.
+ *   result (host int32 [n_items], may be NULL): per item PCMS_OK, or
+ *   PCMS_ERR_INVALID_ARG when a point coordinate is not finite (that item's outputs are
+ *   then unspecified). The call returns PCMS_ERR_INVALID_ARG, enqueuing nothing, when an
+ *   item breaks a limit; otherwise it enqueues its work on `stream` and, when result is
+ *   non-NULL, syncs `stream` once to read the per-item flags. Device scratch (about
+ *   100 bytes per point plus 4 bytes per field and point) comes from cudaMallocAsync on
+ *   `stream`.
+ */
+#define PCMS_BATCH_MAX_POINTS 131072
+#define PCMS_BATCH_MAX_ITEMS 256
+
+typedef struct {
+    int dim;
+    int basis_degree;
+    double radius;
+    pcms_weight weight;
+    const double* src_pts;
+    int64_t n_src;
+    const double* tgt_pts;
+    int64_t n_tgt;
+    const float* fields;
+    int n_fields;
+    float* out;
+    int8_t* target_status;
+} pcms_batch_item;
+
+pcms_status pcms_mls_transfer_batch(const pcms_batch_item* items, int n_items,
+                                    int32_t* result, void* stream);
+
+/*
  * pcms_apply_map_noalloc -- the same result as pcms_apply_map, for callers that must not
  *   allocate device memory while they run (for example a solver's time-step loop that keeps
  *   a fixed device-memory footprint after set-up, or code sharing the GPU with an
@@ -361,6 +413,19 @@ pcms_status pcms_server_poll(pcms_server s, pcms_request_result* results, int ma
 pcms_status pcms_server_drain(pcms_server s, double timeout_s);
 /* Current time on the server's monotonic clock (seconds). */
 double pcms_server_now(pcms_server s);
+/* Batching of small requests (no counterpart in the paper; runtime). A request that is a
+ * one-shot PCMS_MIXED MLS transfer (map_key < 0, reuse_map = 0) with min_neighbors = 0,
+ * lambda = 0 and at most max_points sources and targets goes through the batched path of
+ * pcms_mls_transfer_batch: when a slot takes such a request from the head of the queue, it
+ * also takes the other queued requests of that kind that fit under the cap (up to
+ * PCMS_BATCH_MAX_ITEMS requests and 2^21 targets, in queue order) and runs them together,
+ * one CUDA graph replay per shape class. Results are those of pcms_mls_transfer_batch and do
+ * not depend on which requests share a batch. max_points = 0 turns batching off; values
+ * above PCMS_BATCH_MAX_POINTS are clamped. Default 8192. Takes effect for requests
+ * admitted after the call. */
+pcms_status pcms_server_set_batching(pcms_server s, int64_t max_points);
+/* Batches run so far and the requests they held. */
+pcms_status pcms_server_batch_stats(pcms_server s, int64_t* n_batches, int64_t* n_batched);
 /* Bytes currently reserved by admitted requests plus cached operators, and the peak. */
 pcms_status pcms_server_memory(pcms_server s, int64_t* in_use, int64_t* peak,
                                int64_t* cached_maps);

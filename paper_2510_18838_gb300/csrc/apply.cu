@@ -327,6 +327,10 @@ void apply_t(MapImpl& M, const T* fields, int nf, T* out, cudaStream_t s) {
                                                                  M.tgt.inv.as<int32_t>(), out);
     }
     PCMS_LAUNCH_CHECK("apply");
+    if (M.qr_n > 0) {
+        PCMS_TRACE("apply_qr_rows", s);
+        PCMS_CU(qr_apply(M, fields, nf, out, s));
+    }
 }
 
 // The same three kernels as apply_t, with caller-provided scratch: fs needs ns*fp and stage
@@ -368,6 +372,7 @@ cudaError_t apply_with_scratch_t(const MapImpl& M, const T* fields, int nf, T* o
         k_stage_to_caller<T><<<blocks_for(nt, 256), 256, 0, s>>>(stage, fp, nf, nt,
                                                                  M.tgt.inv.as<int32_t>(), out);
         if ((e = cudaGetLastError()) != cudaSuccess) { *where = "k_stage_to_caller"; return e; }
+        if ((e = qr_apply(M, fields, nf, out, s)) != cudaSuccess) { *where = "k_qr_apply"; return e; }
     }
     return cudaSuccess;
 }
@@ -506,6 +511,7 @@ void mls_export(MapImpl& M, int64_t* offsets, int32_t* cols, double* vals, int8_
                 nt, M.tgt.inv.as<int32_t>(), M.offsets.as<int64_t>(), M.counts.as<int32_t>(),
                 M.cols.as<int32_t>(), M.vals.as<double>(), M.src.perm.as<int32_t>(), M.status.as<int8_t>(),
                 M.kexp.as<int32_t>(), offsets, cols, vals, status, kexp, M.P.kbase);
+        qr_export(M, offsets, cols, vals, s);
     }
     PCMS_LAUNCH_CHECK("export");
 }

@@ -4,9 +4,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 
+#include "pcms_batch.cuh"
 #include "pcms_internal.cuh"
 #include "trace.cuh"
 
@@ -155,6 +157,30 @@ pcms_status pcms_apply_map(pcms_map map, const void* fields, int n_fields, void*
     REQUIRE(map->impl.nt == 0 || out != nullptr, "pcms_apply_map: out is NULL");
     return guarded("pcms_apply_map", [&]() -> pcms_status {
         pcms::mls_apply(map->impl, fields, n_fields, out, (cudaStream_t)stream);
+        return PCMS_OK;
+    });
+}
+
+pcms_status pcms_mls_transfer_batch(const pcms_batch_item* items, int n_items,
+                                    int32_t* result, void* stream) {
+    REQUIRE(n_items >= 0 && n_items <= PCMS_BATCH_MAX_ITEMS,
+            "pcms_mls_transfer_batch: n_items must be in 0..PCMS_BATCH_MAX_ITEMS");
+    REQUIRE(n_items == 0 || items != nullptr, "pcms_mls_transfer_batch: items is NULL");
+    for (int i = 0; i < n_items; i++) {
+        const std::string e = pcms::batch_check_item(items[i]);
+        if (!e.empty())
+            return set_error(PCMS_ERR_INVALID_ARG, "pcms_mls_transfer_batch: item " +
+                                                       std::to_string(i) + ": " + e);
+    }
+    return guarded("pcms_mls_transfer_batch", [&]() -> pcms_status {
+        // one executor per host thread and device (direct launches, table copied from
+        // pageable memory, so consecutive calls never wait on each other's table)
+        thread_local std::unique_ptr<pcms::BatchExec> ex[64];
+        int dev = 0;
+        PCMS_CU(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= 64) pcms::fail(PCMS_ERR_CUDA, "device ordinal above 63");
+        if (!ex[dev]) ex[dev].reset(new pcms::BatchExec(false));
+        ex[dev]->run(items, n_items, result, (cudaStream_t)stream);
         return PCMS_OK;
     });
 }

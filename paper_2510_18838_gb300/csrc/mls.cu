@@ -42,6 +42,24 @@ int thread_blocks(int64_t n, int threads) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 32));
 }
 
+// k_rows64_apply for the listed flag-2 targets (count on the device)
+void rows64_apply_any(int dim, int deg, int G, const ShapeArgs& sh, const int32_t* list,
+                      const int32_t* n, int64_t nmax, cudaStream_t s) {
+    if (nmax <= 0) return;
+    const int blocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>((nmax * G + 255) / 256, (int64_t)num_sms() * 8));
+#define PCMS_R64(D, K, GG) k_rows64_apply<D, K, GG><<<blocks, 256, 0, s>>>(sh, list, n)
+    if (dim == 2) {
+        if (G == 32) { if (deg == 0) PCMS_R64(2, 0, 32); else if (deg == 1) PCMS_R64(2, 1, 32); else PCMS_R64(2, 2, 32); }
+        else { if (deg == 0) PCMS_R64(2, 0, 8); else if (deg == 1) PCMS_R64(2, 1, 8); else PCMS_R64(2, 2, 8); }
+    } else {
+        if (G == 32) { if (deg == 0) PCMS_R64(3, 0, 32); else if (deg == 1) PCMS_R64(3, 1, 32); else PCMS_R64(3, 2, 32); }
+        else { if (deg == 0) PCMS_R64(3, 0, 8); else if (deg == 1) PCMS_R64(3, 1, 8); else PCMS_R64(3, 2, 8); }
+    }
+#undef PCMS_R64
+    PCMS_LAUNCH_CHECK("k_rows64_apply");
+}
+
 // Lanes per target and the first pass's accumulation, from the expected neighbour count
 // (ns * ball volume / box volume): 32 lanes from 160 neighbours on; blocked compensation
 // (mixed path) from 1000 on, where plain FP32 sums over n / 32 pairs per lane stop meeting
@@ -498,7 +516,8 @@ int64_t MapImpl::device_bytes() const {
     return (int64_t)(src.cell_start.bytes + src.perm.bytes + src.inv.bytes + src.x64.bytes +
                      src.hl0.bytes + src.hl1.bytes + tgt.perm.bytes + tgt.inv.bytes +
                      tgt.x64.bytes + counts.bytes + kexp.bytes + status.bytes + offsets.bytes +
-                     cols.bytes + vals.bytes);
+                     cols.bytes + vals.bytes + qr_list.bytes + qr_cols.bytes + qr_vals.bytes +
+                     qr_cnt.bytes);
 }
 
 // ------------------------------------------------------------------------------------
@@ -616,12 +635,26 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
         if (!fused)
             M.vals.alloc((mixed ? sizeof(float) : sizeof(double)) * std::max<int64_t>(nnz, 1), s);
 
+        DBuf qrl(sizeof(int32_t) * (nt + 1), s);   // targets for the QR pass, and their count
+        PCMS_CU(cudaMemsetAsync(qrl.as<int32_t>() + nt, 0, sizeof(int32_t), s));
+        // fused apply: the FP64-assembled targets, whose rows k_rows64_apply applies
+        DBuf l64(fused && mixed ? sizeof(int32_t) * (nt + 1) : 0, s);
+        if (fused && mixed) PCMS_CU(cudaMemsetAsync(l64.as<int32_t>() + nt, 0, sizeof(int32_t), s));
         SolveArgs sa{};
         bases.apply(sa);
         sa.nt = nt;
         sa.counts = M.counts.as<int32_t>();
         sa.mom = mom.p;
         sa.lambda = P.lambda;
+        if (deg >= 1) {
+            sa.qr_list = qrl.as<int32_t>();
+            sa.n_qr = qrl.as<int32_t>() + nt;
+            sa.amp_qr = mixed ? AMP_QR_MIXED : AMP_QR_FP64;
+        }
+        if (fused && mixed) {
+            sa.list64 = l64.as<int32_t>();
+            sa.n64 = l64.as<int32_t>() + nt;
+        }
         sa.y = y.as<double>();
         sa.yf = mixed ? yf.as<float2>() : nullptr;
         sa.flags = flags.as<int8_t>();
@@ -661,9 +694,24 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
             sh.status = M.status.as<int8_t>();
             sh.stage = stage.as<float>();
             shape_apply_any(dim, deg, G, sh, asm_blocks(nt, G), s);
+            {
+                PCMS_TRACE("mls_rows64_apply", s);
+                rows64_apply_any(dim, deg, G, sh, l64.as<int32_t>(), l64.as<int32_t>() + nt, nt, s);
+            }
             stage_to_caller_f32(M, stage.as<float>(), fp, fused->nf, fused->out, s);
         } else {
             shape_any(dim, deg, mixed, G, sh, asm_blocks(nt, G), s);
+        }
+        // the QR pass of the listed targets: an FP64 side table of their rows (rank failures
+        // become ill-conditioned before the status counts below)
+        if (deg >= 1) {
+            int32_t hq = 0;
+            PCMS_CU(cudaMemcpyAsync(&hq, qrl.as<int32_t>() + nt, sizeof(int32_t),
+                                    cudaMemcpyDeviceToHost, s));
+            PCMS_CU(cudaStreamSynchronize(s));
+            trace_count("mls_qr_rows", hq);
+            qr_fix_map(M, qrl.as<int32_t>(), hq, s);
+            if (fused) PCMS_CU(qr_apply(M, fused->fields, fused->nf, fused->out, s));
         }
         M.tgt.hl0.release();   // the targets' hi/lo coordinates only serve the assembly
         M.tgt.hl1.release();
@@ -782,6 +830,8 @@ void mls_transfer(const MlsParams& P0, const double* src, int64_t ns, const doub
     DBuf mom(mom_elem_bytes(mom_kind(mixed, plan.acc)) * np * std::max<int64_t>(nt, 1), s);
     BasisEstimate est;
     est.enable(mixed, plan, P, g, S, nt, s);
+    DBuf qrl(sizeof(int32_t) * (nt + 1), s);   // targets for the QR pass, and their count
+    PCMS_CU(cudaMemsetAsync(qrl.as<int32_t>() + nt, 0, sizeof(int32_t), s));
     for (int f = 0; f < nf; f++) {
         if (ns > 0) {
             PCMS_TRACE("mls_field_to_sorted", s);
@@ -811,8 +861,16 @@ void mls_transfer(const MlsParams& P0, const double* src, int64_t ns, const doub
         sa.out = (char*)out + fsz * (size_t)f * nt;
         sa.out_is_double = !mixed;
         sa.status = f == 0 ? status : nullptr;
+        if (f == 0 && deg >= 1) {   // the same targets for every field: listed once
+            sa.qr_list = qrl.as<int32_t>();
+            sa.n_qr = qrl.as<int32_t>() + nt;
+            sa.amp_qr = mixed ? AMP_QR_MIXED : AMP_QR_FP64;
+        }
         solve_tiers(dim, deg, MODE_FUSED, mixed, plan, a, sa, nt, nullptr, s);
     }
+    if (nt > 0 && deg >= 1)
+        qr_fix_transfer(dim, deg, !mixed, g, S, Tp, kexp.as<int32_t>(), P.radius, (int)P.weight,
+                        qrl.as<int32_t>(), qrl.as<int32_t>() + nt, fields, nf, out, status, s);
     if (status && P.min_neighbors == 0 && nt > 0) {
         DBuf st(sizeof(unsigned long long) * 4, s);
         PCMS_CU(cudaMemsetAsync(st.p, 0, st.bytes, s));

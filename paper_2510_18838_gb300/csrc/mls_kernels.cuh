@@ -172,6 +172,14 @@ struct SolveArgs {
     int32_t* n_recentred;     // tier 1: targets solved in an estimated re-centred basis, or null
     int32_t* fb_list;         // mixed tiers: work items (wk) the refined FP32 solve declined,
     int32_t* n_fb;            // solved in FP64 by a second launch (k_solve<..., PASS 2>)
+    // final FP64 solves (tier 3 not sent to the refine pass, tier 4) with amp / rho above
+    // amp_qr (rho: the smallest LDL^T pivot ratio), and refine solves that fail their guard:
+    // sorted targets for the Householder-QR pass (qr.cuh), or null
+    int32_t* qr_list;
+    int32_t* n_qr;
+    float amp_qr;
+    int32_t* list64;          // MAP: targets whose operator rows are FP64 (flag 2), or null
+    int32_t* n64;
     float4* basis2;           // tier 1: basis for tier 2, per list2 position
     float4* rc;               // MAP: basis of the accepted tier-2 rows, per sorted target
     int32_t* list2;           // targets for tier 2 / tier 3
@@ -973,10 +981,13 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC, MIXED>()) k
 // mom = [moments of degree <= 2k (graded-lex)] [g (FUSED only)]. Returns false when the
 // guard fails. Host-callable so the algebra can be checked without a GPU.
 // ------------------------------------------------------------------------------------
+// *rho (optional) = min_k d_k / G_kk, the smallest pivot ratio: about 1 / cond of the
+// diagonally scaled G. An error e in the moments moves c_0 by up to about e amp / rho.
 template <int DIM, int DEG, int MODE>
 __host__ __device__ __forceinline__ bool solve_moments(const double* mom, double lambda,
                                                        double tau, double* out, double* c0,
-                                                       double* amp, const double* at = nullptr) {
+                                                       double* amp, const double* at = nullptr,
+                                                       double* rho = nullptr) {
     constexpr int NM = mono_count(DIM, 2 * DEG);
     constexpr int M = mono_count(DIM, DEG);
     constexpr int NP = M * (M + 1) / 2;
@@ -1011,6 +1022,7 @@ __host__ __device__ __forceinline__ bool solve_moments(const double* mom, double
             dk -= lkj * lkj * L[j * (j + 1) / 2 + j];
         });
         ok = ok && (dk > tau * gkk);
+        if (rho) *rho = k == 0 ? dk / gkk : fmin(*rho, dk / gkk);
         L[k * (k + 1) / 2 + k] = dk;
         invd[k] = recip64(dk);
     });
@@ -1320,7 +1332,7 @@ __global__ void __launch_bounds__(128, PASS == 1 ? 3 : 1) k_solve(SolveArgs S) {
         const int64_t t = S.list ? (int64_t)S.list[wk] : wk;
         const int cnt = S.counts[t];
         int st = PCMS_TARGET_OK;
-        double val = 0.0, amp = 0.0;
+        double val = 0.0, amp = 0.0, rho = 1.0;
         float amp32 = 0.f;   // amp for routing and row flags (the refined pass works in FP32)
         double y[M];
         double mom[NACC];
@@ -1355,17 +1367,25 @@ __global__ void __launch_bounds__(128, PASS == 1 ? 3 : 1) k_solve(SolveArgs S) {
 #pragma unroll
                 for (int i = 0; i < NACC; i++) mom[i] = mom_value(src[i]);
                 if (!solve_moments<DIM, DEG, MODE>(mom, S.lambda, S.tau, y, &val, &amp,
-                                                   recentred ? at : nullptr))
+                                                   recentred ? at : nullptr, &rho))
                     st = PCMS_TARGET_ILL_CONDITIONED;
                 amp32 = (float)amp;
             }
         }
-        if (S.tier == 4 && st != PCMS_TARGET_OK) continue;   // keep the first FP64 solve
-        if (S.tier == 3 && S.refine64 && st == PCMS_TARGET_OK && amp32 > (float)AMP_FP64) {
+        if (S.tier == 4 && st != PCMS_TARGET_OK) {   // keep the first FP64 solve
+            if (S.qr_list) S.qr_list[atomicAdd(S.n_qr, 1)] = (int32_t)t;
+            continue;
+        }
+        const bool to_refine =
+            S.tier == 3 && S.refine64 && st == PCMS_TARGET_OK && amp32 > (float)AMP_FP64;
+        if (to_refine) {
             const int pos = atomicAdd(S.n2, 1);
             S.list2[pos] = (int32_t)t;
             S.basis2[pos] = recentre_basis<DIM>(mom);
         }
+        if (S.qr_list && S.tier >= 3 && !to_refine && st == PCMS_TARGET_OK &&
+            amp > (double)S.amp_qr * rho)
+            S.qr_list[atomicAdd(S.n_qr, 1)] = (int32_t)t;
         if (S.tier < 3 && st != PCMS_TARGET_UNDERDETERMINED) {
             bool ok = st == PCMS_TARGET_OK;
             if (ok) ok = amp32 <= amp_bound(S.acc, cnt, S.group);
@@ -1398,6 +1418,7 @@ __global__ void __launch_bounds__(128, PASS == 1 ? 3 : 1) k_solve(SolveArgs S) {
                                        : (S.tier == 3 ? 2 : (amp32 > (float)AMP_SHAPE ? 1 : 0));
             S.flags[t] = (int8_t)flag;
             if (recentred && S.rc) S.rc[t] = bas;
+            if (flag == 2 && S.list64) S.list64[atomicAdd(S.n64, 1)] = (int32_t)t;
         }
         const double nanv = __longlong_as_double(0x7ff8000000000000LL);
         if (MODE == MODE_FUSED) {
@@ -1479,8 +1500,11 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
         T inv_r;
         if constexpr (MIXED) inv_r = S.lv.inv_rf[kx];
         else inv_r = S.lv.inv_r[kx];
-        const int64_t a = S.offsets[t], b = a + S.counts[t];
-        // APPLY: this lane's share of the row applied to the fields
+        const int64_t a = S.offsets[t], b = (APPLY && flag == 2) ? a : a + S.counts[t];
+        // APPLY: this lane's share of the row applied to the fields. Rows of FP64-assembled
+        // targets (flag 2) are left to k_rows64_apply, which accumulates them in FP64: their
+        // operator values can be large with cancelling signs (extrapolating targets with
+        // about m neighbours: sum_j |N_j| up to amp), where FP32 sums would lose the bound.
         float facc[16];
 #pragma unroll
         for (int q = 0; q < 16; q++) facc[q] = 0.f;
@@ -1663,6 +1687,84 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
                                         : make_float4(nanf, nanf, nanf, nanf);
                 }
             }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// k_rows64_apply: the fused apply of the FP64-assembled targets (flag 2, listed by the
+// solve): each row evaluated in FP64 (exact offsets, weight, basis, the FP64 y) and applied
+// to the fields with FP64 sums; the result replaces the target's staged row. A group of G
+// lanes per listed target.
+// ------------------------------------------------------------------------------------
+template <int DIM, int DEG, int G>
+__global__ void __launch_bounds__(256) k_rows64_apply(ShapeArgs S, const int32_t* __restrict__ list,
+                                                      const int32_t* __restrict__ n_list) {
+    constexpr int M = mono_count(DIM, DEG);
+    constexpr int GPW = 32 / G;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int gi = lane / G, gl = lane % G;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (gi * G));
+    const int64_t ngroups = (int64_t)gridDim.x * (blockDim.x >> 5) * GPW;
+    const int64_t n = *n_list;
+    for (int64_t e = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * GPW + gi; e < n; e += ngroups) {
+        const int64_t t = list[e];
+        double tx[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int d = 0; d < DIM; d++) tx[d] = S.tx64[d * S.nt + t];
+        double y[M];
+#pragma unroll
+        for (int k = 0; k < M; k++) y[k] = S.y[t * M + k];
+        const double ir = S.lv.inv_r[S.kexp[t]];
+        const int64_t a = S.offsets[t], b = a + S.counts[t];
+        double acc[16];
+#pragma unroll
+        for (int q = 0; q < 16; q++) acc[q] = 0.0;
+        for (int64_t i = a + gl; i < b; i += G) {
+            const int j = S.cols[i];
+            double dx[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int d = 0; d < DIM; d++) dx[d] = S.sx64[d * S.ns + j] - tx[d];
+            double d2 = dx[0] * dx[0] + dx[1] * dx[1];
+            if (DIM == 3) d2 += dx[2] * dx[2];
+            const double w = weight_value<double>(S.weight, sqrt(d2) * ir);
+            const double u[3] = {dx[0] * ir, dx[1] * ir, dx[2] * ir};
+            double am[M];
+            am[0] = 1.0;
+            double sum = y[0];
+            sfor<M - 1>([&](auto I) {
+                constexpr int p = decltype(I)::value + 1;
+                am[p] = am[mono_parent(DIM, p)] * u[mono_var(DIM, p)];
+                sum += am[p] * y[p];
+            });
+            const double v = w * sum;
+            if (S.fp == 1) {
+                acc[0] += v * (double)S.fs[j];
+            } else {
+                const float4* row = reinterpret_cast<const float4*>(S.fs + (int64_t)j * S.fp);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    if (4 * q < S.fp) {
+                        const float4 x = row[q];
+                        acc[4 * q] += v * (double)x.x;
+                        acc[4 * q + 1] += v * (double)x.y;
+                        acc[4 * q + 2] += v * (double)x.z;
+                        acc[4 * q + 3] += v * (double)x.w;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 16; q++) {
+            if (q < S.fp) {
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(gmask, acc[q], o);
+            }
+        }
+        if (gl == 0 && S.status[t] == PCMS_TARGET_OK) {
+#pragma unroll
+            for (int q = 0; q < 16; q++)
+                if (q < S.fp) S.stage[t * S.fp + q] = (float)acc[q];
         }
     }
 }

@@ -343,6 +343,10 @@ struct MapImpl {
     DBuf cols;       // int32 [nnz] sorted source positions
     DBuf vals;       // float64 or float32 [nnz]
     int64_t n_under = 0, n_ill = 0, max_count = 0, max_k = 0;
+    // rows solved by Householder QR (qr_fix.cu): sorted targets, their (column, FP64 value)
+    // pairs, QR_MAX per row, and the pairs used (-1: the assembled row stands)
+    DBuf qr_list, qr_cols, qr_vals, qr_cnt;
+    int qr_n = 0;
     int64_t device_bytes() const;
 };
 
@@ -377,6 +381,25 @@ void mls_count(const MlsParams& P, const double* src, int64_t ns, const double* 
 void mls_transfer(const MlsParams& P, const double* src, int64_t ns, const double* tgt,
                   int64_t nt, const pcms_map_opts& o, const void* fields, int nf, void* out,
                   int8_t* status, cudaStream_t s, int64_t* n_under);
+
+// Householder-QR pass for targets whose FP64 normal equations are too ill-conditioned
+// (qr_fix.cu). One-shot: the listed sorted targets' values (all nf fields, caller order) and
+// statuses are replaced. Map: the listed rows go to the map's FP64 side table (a failed rank
+// test marks the target ill-conditioned); qr_apply then overwrites those targets' outputs
+// after an apply (NaN for ill-conditioned ones), qr_export their exported rows.
+void qr_fix_transfer(int dim, int deg, bool fp64, const Grid& g, const SortedPoints& S,
+                     const SortedPoints& Tp, const int32_t* kexp, double radius, int weight,
+                     const int32_t* list, const int32_t* n_list, const void* fields, int nf,
+                     void* out, int8_t* status, cudaStream_t s);
+void qr_fix_map(MapImpl& M, const int32_t* list, int n, cudaStream_t s);
+cudaError_t qr_apply(const MapImpl& M, const void* fields, int nf, void* out, cudaStream_t s);
+void qr_export(const MapImpl& M, const int64_t* off_out, int32_t* cols_out, double* vals_out,
+               cudaStream_t s);
+// Bounds on amp / rho (the error of an FP64 normal-equation solve is about amp / rho 2^-53
+// of the field) above which a final FP64 solve is redone by QR: a quarter of the mixed
+// path's 2e-5, a quarter of the FP64 path's 1e-12.
+constexpr float AMP_QR_MIXED = 4.5e10f;
+constexpr float AMP_QR_FP64 = 2.2e3f;
 
 // four and five dimensions, FP64 (mls_nd.cu); the MLS entry points above dispatch here
 void mls_nd_create_map(MapImpl& M, const double* src, const double* tgt);

@@ -21,6 +21,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "pcms_batch.cuh"
 #include "pcms_internal.cuh"
 
 namespace {
@@ -76,6 +77,11 @@ struct pcms_server_s {
     std::vector<std::thread> workers;
     std::vector<cudaStream_t> streams;
     std::vector<Bounce> bounce;   // per slot
+    // batched small MLS requests (batch.cu): requests with at most batch_max points per
+    // set go through one graph replay per shape class with the other queued ones; 0 = off
+    int64_t batch_max = 8192;
+    std::vector<std::unique_ptr<pcms::BatchExec>> batch;   // per slot, made by its worker
+    int64_t n_batches = 0, n_batched = 0;
 
     double now() const {
         return std::chrono::duration<double>(Clock::now() - t0).count();
@@ -105,6 +111,32 @@ int64_t request_bytes(const pcms_request& r) {
     const bool keep = r.map_key >= 0;
     return pcms::estimate_mls_bytes(P, r.n_src, r.n_tgt, r.n_fields, keep) +
            staged_bytes(r, true);
+}
+
+// A request the batched path takes: a one-shot mixed MLS transfer (no operator kept or
+// reused) with the user's radius, lambda = 0, and at most batch_max points per set.
+bool batchable(const pcms_server_s* S, const pcms_request& r) {
+    return S->batch_max > 0 && r.kind == PCMS_REQ_MLS && !r.reuse_map && r.map_key < 0 &&
+           r.opts.precision == PCMS_MIXED && r.opts.min_neighbors == 0 && r.opts.lambda == 0.0 &&
+           (r.dim == 2 || r.dim == 3) && r.n_src <= S->batch_max && r.n_tgt <= S->batch_max &&
+           r.n_src <= PCMS_BATCH_MAX_POINTS && r.n_tgt <= PCMS_BATCH_MAX_POINTS;
+}
+
+pcms_batch_item batch_item(const pcms_request& r) {
+    pcms_batch_item it{};
+    it.dim = r.dim;
+    it.basis_degree = r.basis_degree;
+    it.radius = r.radius;
+    it.weight = r.opts.weight;
+    it.src_pts = r.src_pts;
+    it.n_src = r.n_src;
+    it.tgt_pts = r.tgt_pts;
+    it.n_tgt = r.n_tgt;
+    it.fields = (const float*)r.fields;
+    it.n_fields = r.n_fields;
+    it.out = (float*)r.out;
+    it.target_status = nullptr;
+    return it;
 }
 
 bool page_locked(const void* p) {
@@ -295,12 +327,108 @@ void run_job(pcms_server_s* S, Job* j, cudaStream_t s, Bounce& bounce, pcms::Map
     PCMS_CU(cudaStreamSynchronize(s));
 }
 
+// Device bytes of a request on the batched path: its part of the batch's scratch arena and
+// its staged copies, plus 64 KiB for the batch's table and rounding.
+int64_t batch_bytes(const pcms_request& r) {
+    return pcms::batch_item_bytes(batch_item(r)) + staged_bytes(r, true) + (int64_t(1) << 16);
+}
+
+// Targets of one batch at most: bounds a batch's time, so that requests queued behind it
+// wait for a few milliseconds at most.
+constexpr int64_t BATCH_MAX_TARGETS = int64_t(1) << 21;
+
+// With the lock held and the head request batchable: take the head and the other queued
+// batchable requests that fit under the cap (at most PCMS_BATCH_MAX_ITEMS, at most
+// BATCH_MAX_TARGETS targets), in queue order, off the queue. Empty if the head does not fit.
+std::vector<Job*> take_batch(pcms_server_s* S) {
+    std::vector<Job*> b;
+    int64_t need = 0, targets = 0;
+    const int64_t head = batch_bytes(S->queue.front()->req);
+    if (S->in_use + head > S->cap) evict_for(S, head);
+    for (Job* x : S->queue) {
+        if ((int)b.size() >= PCMS_BATCH_MAX_ITEMS) break;
+        if (!batchable(S, x->req)) continue;
+        const int64_t xb = batch_bytes(x->req);
+        if (S->in_use + need + xb > S->cap) break;
+        if (!b.empty() && targets + x->req.n_tgt > BATCH_MAX_TARGETS) break;
+        b.push_back(x);
+        need += xb;
+        targets += x->req.n_tgt;
+        x->bytes = xb;
+    }
+    if (b.empty()) return b;
+    std::deque<Job*> rest;
+    size_t k = 0;
+    for (Job* x : S->queue) {
+        if (k < b.size() && x == b[k]) k++;
+        else rest.push_back(x);
+    }
+    S->queue.swap(rest);
+    S->in_use += need;
+    S->peak = std::max(S->peak, S->in_use);
+    const double t = S->now();
+    for (Job* x : b) x->t_start = t;
+    S->n_batches++;
+    S->n_batched += (int64_t)b.size();
+    return b;
+}
+
+// Runs a batch on the slot's stream (staging host-I/O requests' buffers) and completes its
+// requests.
+void run_batch(pcms_server_s* S, const std::vector<Job*>& b, int slot) {
+    cudaStream_t s = S->streams[slot];
+    std::vector<pcms_status> st(b.size(), PCMS_OK);
+    try {
+        if (!S->batch[slot]) S->batch[slot].reset(new pcms::BatchExec(true));
+        std::vector<Staging> stg(b.size());
+        std::vector<pcms_batch_item> items(b.size());
+        for (size_t i = 0; i < b.size(); i++) {
+            const pcms_request& r = b[i]->req;
+            if (r.host_io) {
+                stg[i].bounce = &S->bounce[slot];
+                stage(r, true, stg[i], s);
+                items[i] = batch_item(stg[i].d);
+            } else {
+                items[i] = batch_item(r);
+            }
+        }
+        std::vector<int32_t> res(b.size(), PCMS_OK);
+        S->batch[slot]->run(items.data(), (int)items.size(), res.data(), s);
+        for (size_t i = 0; i < b.size(); i++) {
+            st[i] = (pcms_status)res[i];
+            if (b[i]->req.host_io && st[i] == PCMS_OK) unstage(b[i]->req, stg[i], s);
+        }
+        PCMS_CU(cudaStreamSynchronize(s));
+    } catch (const pcms::PcmsError& e) {
+        if (e.status == PCMS_ERR_CUDA)
+            std::fprintf(stderr, "pcms server: a batch of %zu requests failed: %s\n", b.size(),
+                         e.msg.c_str());
+        for (auto& x : st) x = e.status;
+    } catch (...) {
+        for (auto& x : st) x = PCMS_ERR_CUDA;
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        const double t = S->now();
+        for (size_t i = 0; i < b.size(); i++) {
+            b[i]->st = st[i];
+            b[i]->t_end = t;
+            S->in_use -= b[i]->bytes;
+            S->finished.push_back(b[i]->ticket);
+            S->n_completed++;
+        }
+    }
+    S->cv_done.notify_all();
+    S->cv_work.notify_all();
+}
+
 void worker(pcms_server_s* S, int slot) {
     cudaSetDevice(S->device);
     cudaStream_t s = S->streams[slot];
     for (;;) {
         Job* j = nullptr;
         pcms::MapImpl* cached = nullptr;
+        std::vector<Job*> batch;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             for (;;) {
@@ -314,6 +442,12 @@ void worker(pcms_server_s* S, int slot) {
                         S->finished.push_back(h->ticket);
                         S->n_completed++;
                         S->cv_done.notify_all();
+                        continue;
+                    }
+                    if (batchable(S, h->req)) {
+                        batch = take_batch(S);
+                        if (!batch.empty()) break;
+                        S->cv_work.wait(lk);
                         continue;
                     }
                     // a reuse request whose operator is being built waits for it
@@ -369,6 +503,10 @@ void worker(pcms_server_s* S, int slot) {
                 }
                 S->cv_work.wait(lk);
             }
+        }
+        if (!batch.empty()) {
+            run_batch(S, batch, slot);
+            continue;
         }
         std::unique_ptr<pcms::MapImpl> built;
         pcms_status st = PCMS_OK;
@@ -447,6 +585,7 @@ pcms_status pcms_server_create(int n_slots, int64_t mem_cap_bytes, pcms_server* 
         S->streams.push_back(st);
     }
     S->bounce.resize(n_slots);
+    S->batch.resize(n_slots);
     for (int i = 0; i < n_slots; i++) S->workers.emplace_back(worker, S, i);
     *out = S;
     return PCMS_OK;
@@ -519,6 +658,21 @@ pcms_status pcms_server_drain(pcms_server S, double timeout_s) {
 
 double pcms_server_now(pcms_server S) { return S ? S->now() : 0.0; }
 
+pcms_status pcms_server_set_batching(pcms_server S, int64_t max_points) {
+    if (!S || max_points < 0) return PCMS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->batch_max = std::min<int64_t>(max_points, PCMS_BATCH_MAX_POINTS);
+    return PCMS_OK;
+}
+
+pcms_status pcms_server_batch_stats(pcms_server S, int64_t* n_batches, int64_t* n_batched) {
+    if (!S) return PCMS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (n_batches) *n_batches = S->n_batches;
+    if (n_batched) *n_batched = S->n_batched;
+    return PCMS_OK;
+}
+
 pcms_status pcms_server_memory(pcms_server S, int64_t* in_use, int64_t* peak,
                                int64_t* cached_maps) {
     if (!S) return PCMS_ERR_INVALID_ARG;
@@ -539,6 +693,7 @@ void pcms_server_destroy(pcms_server S) {
     S->cv_cache.notify_all();
     for (std::thread& t : S->workers) t.join();
     S->cache.clear();
+    S->batch.clear();
     for (cudaStream_t st : S->streams) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);

@@ -68,7 +68,7 @@ bool trace_timing() { return g_on.load(std::memory_order_relaxed) == 1; }
 
 TraceScope::TraceScope(const char* name, cudaStream_t s) : name_(name), s_(s) {
     const int mode = g_on.load(std::memory_order_relaxed);
-    if (!mode) return;
+    if (!mode || !name) return;   // a null name: not recorded
     std::lock_guard<std::mutex> lk(g_mu);
     if (mode == 2) {
         g_stats[name_].launches += 1;

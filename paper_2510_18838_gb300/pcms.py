@@ -72,6 +72,18 @@ class RequestResult(ctypes.Structure):
                 ("used_cached_map", ctypes.c_int)]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("basis_degree", ctypes.c_int),
+                ("radius", ctypes.c_double), ("weight", ctypes.c_int),
+                ("src_pts", ctypes.c_void_p), ("n_src", ctypes.c_int64),
+                ("tgt_pts", ctypes.c_void_p), ("n_tgt", ctypes.c_int64),
+                ("fields", ctypes.c_void_p), ("n_fields", ctypes.c_int),
+                ("out", ctypes.c_void_p), ("target_status", ctypes.c_void_p)]
+
+
+BATCH_MAX_POINTS = 131072
+BATCH_MAX_ITEMS = 256
+
 REQ_MLS, REQ_MESH = 0, 1
 
 _lib = None
@@ -87,6 +99,7 @@ SIGNATURES = {
     "pcms_apply_map_noalloc": (_I, [_P, _P, _I, _P, _P]),
     "pcms_mls_transfer": (_I, [_I, _P, _I64, _P, _I64, _I, _D, _P, _P, _I, _P, _P, _P]),
     "pcms_count_neighbors": (_I, [_I, _P, _I64, _P, _I64, _I, _D, _P, _P, _P, _P, _P]),
+    "pcms_mls_transfer_batch": (_I, [_P, _I, _P, _P]),
     "pcms_map_info": (_I, [_P, _P]),
     "pcms_map_export": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "pcms_map_destroy": (None, [_P, _P]),
@@ -101,6 +114,8 @@ SIGNATURES = {
     "pcms_server_poll": (_I, [_P, _P, _I, _D, _P]),
     "pcms_server_drain": (_I, [_P, _D]),
     "pcms_server_now": (_D, [_P]),
+    "pcms_server_set_batching": (_I, [_P, _I64]),
+    "pcms_server_batch_stats": (_I, [_P, _P, _P]),
     "pcms_server_memory": (_I, [_P, _P, _P, _P]),
     "pcms_server_destroy": (None, [_P]),
     "pcms_trace_enable": (_I, [_I]),
@@ -315,6 +330,42 @@ def mls_transfer(src, tgt, fields, degree, radius, precision="fp64", weight="wen
     return out, (status[:nt] if status is not None else None)
 
 
+def mls_transfer_batch(problems, with_status=True, stream=None):
+    """pcms_mls_transfer_batch: many small one-shot mixed-precision transfers in one call.
+    problems: list of dicts with src [dim, ns] and tgt [dim, nt] (float64, CUDA), fields
+    [F, ns] (float32, CUDA), degree, radius and optionally weight. Returns
+    (outs, statuses, results): per problem the values [F, nt] and the int8 target statuses
+    (or None), and the per-problem pcms_status codes."""
+    n = len(problems)
+    items = (BatchItem * max(n, 1))()
+    keep = []
+    outs, stats = [], []
+    for i, p in enumerate(problems):
+        src = _dev(p["src"], torch.float64, "src")
+        tgt = _dev(p["tgt"], torch.float64, "tgt")
+        f = _dev(p["fields"], torch.float32, "fields")
+        if f.dim() == 1:
+            f = f[None]
+        nt = tgt.shape[1]
+        out = torch.empty((f.shape[0], nt), dtype=torch.float32, device=src.device)
+        st = torch.empty(max(nt, 1), dtype=torch.int8, device=src.device) if with_status else None
+        it = items[i]
+        it.dim, it.basis_degree = src.shape[0], int(p["degree"])
+        it.radius = float(p["radius"])
+        it.weight = WEIGHTS[p.get("weight", "wendland_c2")]
+        it.src_pts, it.n_src = src.data_ptr(), src.shape[1]
+        it.tgt_pts, it.n_tgt = tgt.data_ptr(), nt
+        it.fields, it.n_fields = f.data_ptr(), f.shape[0]
+        it.out = out.data_ptr()
+        it.target_status = st.data_ptr() if st is not None else None
+        keep += [src, tgt, f]
+        outs.append(out)
+        stats.append(st[:nt] if st is not None else None)
+    res = (ctypes.c_int32 * max(n, 1))()
+    _check(lib().pcms_mls_transfer_batch(ctypes.byref(items), n, ctypes.byref(res), _stream(stream)))
+    return outs, stats, [int(res[i]) for i in range(n)]
+
+
 def count_neighbors(src, tgt, radius, degree=1, precision="fp64", weight="wendland_c2",
                     min_neighbors=0, domain=None, with_doublings=False, stream=None,
                     growth="target"):
@@ -498,6 +549,15 @@ class Server:
 
     def drain(self, timeout_s=600.0):
         _check(lib().pcms_server_drain(self.handle, float(timeout_s)))
+
+    def set_batching(self, max_points: int):
+        """Batch one-shot mixed MLS requests of at most max_points points per set (0: off)."""
+        _check(lib().pcms_server_set_batching(self.handle, int(max_points)))
+
+    def batch_stats(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().pcms_server_batch_stats(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return {"batches": a.value, "batched_requests": b.value}
 
     def memory(self):
         a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

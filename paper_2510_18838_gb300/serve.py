@@ -151,11 +151,16 @@ def submit(server: pcms.Server, d: DeviceRequest, reused_keys: set):
                              reuse=r.reuse_of >= 0)
 
 
-def run_served(dreqs, n_slots=8, mem_cap=40 << 30, arrivals=None, timeout_s=900.0):
+def run_served(dreqs, n_slots=8, mem_cap=40 << 30, arrivals=None, timeout_s=900.0,
+               batch_max=None):
     """Replay through a fresh server. arrivals=None: every request is submitted at once
-    (closed loop); else arrival offsets in seconds (open loop). Returns a stats dict."""
+    (closed loop); else arrival offsets in seconds (open loop). batch_max: the server's
+    batching bound in points (None: the library default, 0: no batching). Returns a stats
+    dict."""
     reused = {r.req.reuse_of for r in dreqs if r.req.kind == "mls" and r.req.reuse_of >= 0}
     server = pcms.Server(n_slots=n_slots, mem_cap_bytes=mem_cap)
+    if batch_max is not None:
+        server.set_batching(batch_max)
     torch.cuda.synchronize()
     t_begin = server.now()
     results = {}
@@ -175,6 +180,7 @@ def run_served(dreqs, n_slots=8, mem_cap=40 << 30, arrivals=None, timeout_s=900.
             raise TimeoutError("serving stream did not finish")
     t_end = max(r["t_end"] for r in results.values())
     mem = server.memory()
+    bst = server.batch_stats()
     server.close()
     lat = []
     bad = 0
@@ -189,7 +195,8 @@ def run_served(dreqs, n_slots=8, mem_cap=40 << 30, arrivals=None, timeout_s=900.
     return dict(points=pts, seconds=wall, points_per_s=pts / wall,
                 p50_ms=1e3 * statistics.median(lat), p99_ms=1e3 * _pct(lat, 99),
                 failed=bad, cached_hits=sum(1 for r in results.values() if r["cached"]),
-                peak_bytes=mem["peak"], results=[results[i] for i in range(n)])
+                peak_bytes=mem["peak"], batches=bst["batches"],
+                batched_requests=bst["batched_requests"], results=[results[i] for i in range(n)])
 
 
 def run_plain_fp64(dreqs, arrivals=None):

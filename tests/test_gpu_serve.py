@@ -107,7 +107,8 @@ def test_reuse_that_does_not_fit_beside_its_operator(env):
     op_bytes = s.memory()["in_use"]          # the cached operator alone
     s.close()
     assert op_bytes > 0
-    s = pcms.Server(n_slots=1, mem_cap_bytes=op_bytes + (2 << 20))
+    # room for the operator plus 1 MiB: less than the reuse's scratch and fixed 1 MiB slack
+    s = pcms.Server(n_slots=1, mem_cap_bytes=op_bytes + (1 << 20))
     s.submit_mls(src, tgt, f1, o1, 2, 0.03, map_key=7, bytes_hint=op_bytes)
     s.drain(120)
     s.submit_mls(src, tgt, f2, o2, 2, 0.03, map_key=7, reuse=True, bytes_hint=op_bytes)
@@ -210,3 +211,60 @@ def test_fp64_reuse_reserves_the_padded_apply_scratch(env):
     m.destroy()
     ok = np.isfinite(ref).all(axis=0)
     assert normwise_err(o9.cpu().numpy(), ref, ok) <= TOL_FP64
+
+
+def _batchable(d, reused):
+    r = d.req
+    return (r.kind == "mls" and r.reuse_of < 0 and r.rid not in reused
+            and r.n_src <= 8192 and r.n_tgt <= 8192)
+
+
+def test_batched_requests_are_bitwise_the_same_alone_and_match_the_oracle(env):
+    """Small one-shot MLS requests go through the batched path (several per graph replay).
+    Each one's result is bitwise the result of the same request served alone, and a sample
+    of them matches the FP64 oracle within the mixed tolerance."""
+    import oracle
+    torch, pcms, serve = env
+    reqs = W.request_stream(n_req=60, seed=79, pts_hi=50000, max_pts=50000)
+    dreqs = serve.materialize(reqs, torch.device("cuda", 0))
+    reused = {d.req.reuse_of for d in dreqs if d.req.kind == "mls" and d.req.reuse_of >= 0}
+    small = [i for i, d in enumerate(dreqs) if _batchable(d, reused)]
+    assert len(small) >= 8
+    st = serve.run_served(dreqs, n_slots=6, mem_cap=4 << 30)
+    assert st["failed"] == 0
+    assert st["batched_requests"] >= len(small) and st["batches"] < st["batched_requests"]
+    mix = {i: dreqs[i].tensors["out"].cpu().numpy().copy() for i in small}
+    for i in small[:6]:
+        one = serve.run_served([dreqs[i]], n_slots=1, mem_cap=4 << 30)
+        assert one["failed"] == 0 and one["batched_requests"] == 1
+        assert np.array_equal(dreqs[i].tensors["out"].cpu().numpy(), mix[i], equal_nan=True)
+    rng = np.random.default_rng(5)
+    for i in small[:4]:
+        d = dreqs[i]
+        t = {k: v.cpu().numpy() for k, v in d.tensors.items()}
+        sel = rng.choice(d.req.n_tgt, min(400, d.req.n_tgt), replace=False)
+        o = oracle.mls(t["src"], t["tgt"][:, sel], t["fields"].astype(np.float64), d.req.degree,
+                       d.req.radius, mode="grid")
+        ok = o["status"] == 0
+        assert np.array_equal(np.isfinite(mix[i][:, sel]).all(axis=0), ok)
+        assert normwise_err(mix[i][:, sel], o["values"], ok) <= TOL_MIXED
+
+
+def test_batching_off_gives_the_general_path(env):
+    """With batching off the same requests run one by one through the general path; the two
+    paths agree within the mixed tolerance, target by target status included."""
+    torch, pcms, serve = env
+    reqs = W.request_stream(n_req=40, seed=80, pts_hi=30000, max_pts=30000)
+    dreqs = serve.materialize(reqs, torch.device("cuda", 0))
+    a = serve.run_served(dreqs, n_slots=4, mem_cap=4 << 30)
+    outs = [d.tensors["out"].cpu().numpy().copy() if d.req.kind == "mls" else None for d in dreqs]
+    b = serve.run_served(dreqs, n_slots=4, mem_cap=4 << 30, batch_max=0)
+    assert a["failed"] == 0 and b["failed"] == 0
+    assert a["batched_requests"] > 0 and b["batched_requests"] == 0
+    for d, o in zip(dreqs, outs):
+        if o is None:
+            continue
+        g = d.tensors["out"].cpu().numpy()
+        ok = np.isfinite(g).all(axis=0)
+        assert np.array_equal(np.isfinite(o).all(axis=0), ok)
+        assert normwise_err(o, g, ok) <= TOL_MIXED
