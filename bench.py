@@ -145,12 +145,25 @@ def kernel_launches(trace):
 
 
 # ------------------------------------------------------------------------------------
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
+# of the kernel on the 1/8-size transfer case, and the factor to a full-size launch: the
+# assembly reads the sources and writes the moments once, which scale with the points (x 8).
+NCU_TRAFFIC = {
+    "mls_assemble_fused_bk": (
+        102.9e6, 8.0, "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_assemble<2, 2, "
+        "mixed, fused, 32, float, blocked> on the 500k -> 500k case (43.0 + 59.9 MB; "
+        "profiles/k_assemble_2d_quadratic_fused_bk_transfer_small.md) x 8 for the 4M -> 4M "
+        "launch (sources and targets scale by 8)"),
+}
+
+
 class TransferWorkload:
     name = TRANSFER_NAME
 
     def __init__(self, torch, pcms, W, device, small=False):
         import numpy as np
         self.torch, self.P, self.np = torch, pcms, np
+        self.small = small
         self.dev = device
         if small:   # the same three parts at 1/8 of the points, radii scaled so that the
             # neighbour counts per target match the full sizes (profiling captures)
@@ -174,6 +187,16 @@ class TransferWorkload:
         cnt = pcms.count_neighbors(self.d["s3"], self.d["t3"], c3.radius, degree=2,
                                    min_neighbors=c3.min_neighbors, precision="mixed")
         self.pairs3 = int(cnt.to(torch.int64).sum().item())
+        cnt4 = pcms.count_neighbors(self.d["s4"], self.d["t4"], c4.radius, degree=2,
+                                    precision="mixed")
+
+        def hist(x):
+            q = torch.quantile(x.to(torch.float64)[:: max(1, x.numel() // 1_000_000)],
+                               torch.tensor([0.5, 0.99], dtype=torch.float64, device=x.device))
+            return {"min": int(x.min().item()), "p50": float(q[0].item()),
+                    "p99": float(q[1].item()), "max": int(x.max().item()),
+                    "mean": float(x.to(torch.float64).mean().item())}
+        self.hist = {"mls2d_gauss": hist(cnt), "mls3d_slab": hist(cnt4)}
         self.parts = {}
         torch.cuda.synchronize()
 
@@ -222,6 +245,22 @@ class TransferWorkload:
         return n / dt, n, dt, (f"{n2} mesh points + {n3} MLS2D + {n4} MLS3D (16 fields) "
                                f"targets, seeded uniform sample, oracle grid mode")
 
+    def per_config_cpu(self, orc):
+        """The oracle on seeded target samples of the 4M 2D and 8M 3D cases alone (grid
+        mode, the host cores), as target points per second."""
+        np = self.np
+        rng = np.random.default_rng(9)
+        c3, c4 = self.cfg["c3"], self.cfg["c4"]
+        out = {}
+        for name, c, n, f in (("mls2d_gauss", c3, 1000, c3.fields),
+                              ("mls3d_slab", c4, 5000, c4.fields.astype(np.float64))):
+            sel = rng.choice(c.tgt.shape[1], n, replace=False)
+            t = time.perf_counter()
+            orc.mls(c.src, c.tgt[:, sel], f, 2, c.radius, min_neighbors=c.min_neighbors,
+                    mode="grid")
+            out[name] = {"targets": n, "points_per_s": n / (time.perf_counter() - t)}
+        return out
+
     def roofline(self, trace, peaks, kind):
         """The step's dominant kernel and its roofline entry. Work per launch comes from the
         workload (selected pairs, operator nonzeros) or from the library's work counts of the
@@ -263,6 +302,10 @@ class TransferWorkload:
             return {"kernel": name, "avg_launch_ms": ms / launches, "bound": None}
         r["frac"] = r["achieved"] / r["peak"]
         r["traffic"] = None
+        if name in NCU_TRAFFIC and not self.small:
+            b, scale, src = NCU_TRAFFIC[name]
+            r["traffic"] = b * scale
+            r["traffic_source"] = src
         r["kernel"] = name
         r["avg_launch_ms"] = ms / launches
         return r
@@ -279,6 +322,7 @@ class ServeWorkload:
         self.dreqs = serve.materialize(self.reqs, device)
         self.points_per_step = sum(d.points for d in self.dreqs)
         self.n_slots, self.cap = n_slots, cap
+        self.batch_max = 8192   # the server's default batching bound (points per set)
         self.last = None
 
     def step(self):
@@ -320,6 +364,106 @@ class ServeWorkload:
         return {"value": self.points_per_step / dt, "unit": "points/s",
                 "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": dt * 1e3,
                 "failed": st["failed"]}
+
+    def accuracy(self, orc, n_req=48, per_req=256):
+        """Served outputs of the last step against the FP64 oracle on a seeded sample: n_req
+        requests drawn per kind (mesh, batched one-shot MLS, other one-shot MLS, reuse of a
+        cached operator) and per_req seeded targets of each. MLS: norm-wise relative error
+        per field over the targets the oracle fits (Eq. 2's measure, L-inf); mesh: element
+        ids (bit-exact) and the interpolated values."""
+        import numpy as np
+        rng = np.random.default_rng(23)
+        reused = {d.req.reuse_of for d in self.dreqs if d.req.kind == "mls" and d.req.reuse_of >= 0}
+        kinds = {"mesh": [], "mls_batched": [], "mls_general": [], "mls_reuse": []}
+        for i, d in enumerate(self.dreqs):
+            r = d.req
+            if r.kind == "mesh":
+                kinds["mesh"].append(i)
+            elif r.reuse_of >= 0:
+                kinds["mls_reuse"].append(i)
+            elif r.rid not in reused and r.n_src <= self.batch_max and r.n_tgt <= self.batch_max:
+                kinds["mls_batched"].append(i)
+            else:
+                kinds["mls_general"].append(i)
+        per_kind = max(1, n_req // len(kinds))
+        worst = {"max_normwise_err": 0.0, "max_elem_id_mismatches": 0, "max_mesh_value_err": 0.0,
+                 "status_mismatches": 0}
+        counted = {}
+        for kind, idx in kinds.items():
+            pick = rng.choice(idx, min(per_kind, len(idx)), replace=False) if idx else []
+            counted[kind] = len(pick)
+            for i in pick:
+                d = self.dreqs[int(i)]
+                r, t = d.req, d.tensors
+                sel = np.sort(rng.choice(r.n_tgt, min(per_req, r.n_tgt), replace=False))
+                if r.kind == "mesh":
+                    pts = t["pts"].cpu().numpy()[:, sel]
+                    oe, _, ov = orc.locate(t["xy"].cpu().numpy(), t["tri"].cpu().numpy(), pts,
+                                           field=t["field"].cpu().numpy(), mode="grid")
+                    ge = t["elem"].cpu().numpy()[sel]
+                    gv = t["values"].cpu().numpy()[sel]
+                    worst["max_elem_id_mismatches"] = max(worst["max_elem_id_mismatches"],
+                                                          int((ge != oe).sum()))
+                    ins = oe >= 0
+                    if ins.any():
+                        e = float(np.abs(gv[ins] - ov[ins]).max() / np.abs(ov[ins]).max())
+                        worst["max_mesh_value_err"] = max(worst["max_mesh_value_err"], e)
+                    continue
+                src = t["src"].cpu().numpy()
+                tgt = t["tgt"].cpu().numpy()[:, sel]
+                f = t["fields"].cpu().numpy().astype(np.float64)
+                o = orc.mls(src, tgt, f, r.degree, r.radius, mode="grid")
+                g = t["out"].cpu().numpy()[:, sel]
+                ok = o["status"] == 0
+                worst["status_mismatches"] += int((np.isfinite(g).all(axis=0) != ok).sum())
+                if ok.any():
+                    den = np.abs(o["values"][:, ok]).max(axis=1)
+                    den[den == 0] = 1.0
+                    e = float((np.abs(g[:, ok] - o["values"][:, ok]).max(axis=1) / den).max())
+                    worst["max_normwise_err"] = max(worst["max_normwise_err"], e)
+        worst["sample"] = (f"{sum(counted.values())} requests of the served step ({counted}), "
+                           f"{per_req} seeded targets each, FP64 oracle in grid mode")
+        worst["tolerance"] = 2e-5
+        return worst
+
+    def breakdown(self):
+        """One more step on a single slot with event timing per kernel (no overlap, so the
+        times add up): serial kernel time, its largest kernels, and the roofline entry of
+        the dominant one from the library's work counts (selected pairs of the operator
+        assemblies per dimension and degree)."""
+        P, torch = self.P, self.torch
+        P.trace_enable(True)
+        st = self.S.run_served(self.dreqs, n_slots=1, mem_cap=self.cap, batch_max=self.batch_max)
+        torch.cuda.synchronize()
+        P.trace_enable(False)
+        tr = P.trace_read()
+        ker = kernel_launches(tr)
+        cnt = {k[6:]: v[0] for k, v in tr.items() if k.startswith("count:")}
+        total = sum(v[1] for v in ker.values())
+        top = sorted(ker.items(), key=lambda kv: -kv[1][1])[:12]
+        out = {"one_slot_wall_ms": st["seconds"] * 1e3, "serial_kernel_ms": total,
+               "launches": sum(v[0] for v in ker.values()),
+               "kernels_ms": {k: [v[0], round(v[1], 2)] for k, v in top}}
+        # the map assembly's algorithmic work: pairs of each (dim, degree) x flops per pair
+        flops = 0
+        pairs = 0
+        for dim in (2, 3):
+            for deg in (0, 1, 2):
+                n = cnt.get(f"mls_map_pairs_d{dim}k{deg}", 0)
+                pairs += n
+                flops += n * mls_pair_flops(dim, deg, 0)
+        name = "mls_assemble_map_mixed"
+        if name in ker and flops:
+            clk = measured_peaks()[0].get("sm_max_mhz", 2070.0)
+            peak = 152 * 128 * 2 * clk * 1e6 / 1e12
+            ach = flops / (ker[name][1] / 1e3) / 1e12
+            out["dominant_roofline"] = {
+                "kernel": name, "share_of_serial_kernel_time": ker[name][1] / total,
+                "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak,
+                "work": f"{pairs} selected pairs of operator assemblies x FP32 flops per pair "
+                        f"(dimension and degree of each request)"}
+        return out
 
     def cpu_sample(self, orc, per_req=1024, n_req=40):
         """the oracle as it stands on a bounded sample: n_req seeded requests, per_req seeded
@@ -406,6 +550,89 @@ def roundtrip_study(torch, W, iterations=100, n=553):
                                   "nnz": rt.v2c.info()["nnz"] + rt.c2v.info()["nnz"]}
         rt.destroy()
     return out
+
+
+def config1_leg(torch, pcms, W, orc, reps=50):
+    """The 10,000 -> 10,000 FP64 2D transfer (uniform points, linear basis, Wendland C2,
+    r = 0.03, one field sin(2 pi x) cos(2 pi y)) as one request at a time through
+    pcms_mls_transfer: latency per request with CUDA events (after warm-up; inputs resident),
+    every target checked against the oracle (brute force), and the oracle's own time on the
+    host cores in grid and brute-force mode."""
+    import numpy as np
+    c = W.mls_2d_small()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    s = torch.from_numpy(c.src).to(dev)
+    t = torch.from_numpy(c.tgt).to(dev)
+    f = torch.from_numpy(c.fields).to(dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(5):
+        pcms.mls_transfer(s, t, f, c.degree, c.radius, precision="fp64")
+    lat = []
+    out = None
+    for _ in range(reps):
+        (out, _), ms = timed(torch, lambda: pcms.mls_transfer(s, t, f, c.degree, c.radius,
+                                                              precision="fp64"), stream)
+        lat.append(ms * 1e3)
+    t0 = time.perf_counter()
+    o = orc.mls(c.src, c.tgt, c.fields, c.degree, c.radius, mode="grid")
+    cpu_grid = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    orc.mls(c.src, c.tgt, c.fields, c.degree, c.radius, mode="brute")
+    cpu_brute = time.perf_counter() - t0
+    ok = o["status"] == 0
+    g = out.cpu().numpy()
+    err = float(np.abs(g[:, ok] - o["values"][:, ok]).max() / np.abs(o["values"][:, ok]).max())
+    nt = c.tgt.shape[1]
+    return {"workload": c.name, "latency_us_p50": statistics.median(lat),
+            "latency_us_min": min(lat), "points_per_s": nt / (statistics.median(lat) / 1e6),
+            "oracle_max_normwise_err": err, "tolerance": 1e-12,
+            "status_equal": bool(np.array_equal(np.isfinite(g).all(axis=0), ok)),
+            "cpu_oracle_grid_points_per_s": nt / cpu_grid,
+            "cpu_oracle_brute_points_per_s": nt / cpu_brute, "cpu_cores": orc.get_threads()}
+
+
+def config2_leg(torch, pcms, W, orc, reps=10):
+    """The 512 x 512 jittered mesh (524,288 triangles) with 1,000,000 uniform points and the
+    nodal field x^2 + 3xy: the grid build and the query (location + interpolation) timed
+    separately with CUDA events (best of reps); element ids of 20,000 seeded points compared
+    bit-exactly with the oracle (grid mode) and values within 1e-12; the oracle's time on the
+    host cores for those points, and exhaustively for 2,000 of them (extrapolated to 1M)."""
+    import numpy as np
+    c = W.mesh_2d()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    xy = torch.from_numpy(c.xy).to(dev)
+    tri = torch.from_numpy(c.tri).to(dev)
+    fld = torch.from_numpy(c.field).to(dev)
+    pts = torch.from_numpy(c.pts).to(dev)
+    stream = torch.cuda.current_stream()
+    best_b = best_q = None
+    e = v = None
+    for _ in range(reps + 2):
+        mesh, mb = timed(torch, lambda: pcms.Mesh(xy, tri), stream)
+        (e, _, v), mq = timed(torch, lambda: mesh.locate_interp(pts, fld, with_dim=False), stream)
+        mesh.destroy()
+        best_b = mb if best_b is None else min(best_b, mb)
+        best_q = mq if best_q is None else min(best_q, mq)
+    rng = np.random.default_rng(31)
+    sel = np.sort(rng.choice(c.pts.shape[1], 20_000, replace=False))
+    t0 = time.perf_counter()
+    oe, _, ov = orc.locate(c.xy, c.tri, c.pts[:, sel], field=c.field, mode="grid")
+    cpu_grid = time.perf_counter() - t0
+    sel2 = sel[:2000]
+    t0 = time.perf_counter()
+    orc.locate(c.xy, c.tri, c.pts[:, sel2], field=c.field, mode="exhaustive")
+    cpu_ex = time.perf_counter() - t0
+    ge, gv = e.cpu().numpy()[sel], v.cpu().numpy()[sel]
+    ins = oe >= 0
+    n = c.pts.shape[1]
+    return {"workload": "mesh 512x512 jittered, 524288 triangles, 1M uniform points, f=x^2+3xy",
+            "build_ms": best_b, "query_ms": best_q, "points_per_s": n / (best_q / 1e3),
+            "points_per_s_with_build": n / ((best_b + best_q) / 1e3),
+            "elem_id_mismatches": int((ge != oe).sum()), "sample_points": int(len(sel)),
+            "max_value_err": float(np.abs(gv[ins] - ov[ins]).max() / np.abs(ov[ins]).max()),
+            "cpu_oracle_grid_points_per_s": len(sel) / cpu_grid,
+            "cpu_oracle_exhaustive_points_per_s_extrapolated": len(sel2) / cpu_ex,
+            "cpu_cores": orc.get_threads()}
 
 
 def mls5d_study(torch, pcms, W, reps=3):
@@ -613,6 +840,15 @@ def main():
                 "work": {"mls2d_pairs": tw.pairs3, "mls3d_nnz": tw.nnz4}}
     peaks, kind = measured_peaks()
     roof = tw.roofline(ttrace, peaks, kind)
+    configs = None
+    if args.workload == "serve" and rank == 0:
+        import oracle
+        oracle.build()
+        configs = {"mls2d_fp64_10k": config1_leg(torch, pcms, W, oracle),
+                   "mesh_512": config2_leg(torch, pcms, W, oracle),
+                   "neighbour_counts": tw.hist}
+        if not args.no_cpu_baseline:
+            configs["cpu_oracle_per_config"] = tw.per_config_cpu(oracle)
     study = roundtrip_study(torch, W) if args.workload == "serve" and rank == 0 else None
     study5 = mls5d_study(torch, pcms, W) if args.workload == "serve" and rank == 0 else None
     studyp = projection_study(torch, pcms, W) if args.workload == "serve" and rank == 0 else None
@@ -655,15 +891,13 @@ def main():
 
     extra = {}
     if args.workload == "serve":
-        # one more step with event timing: where the serving step spends device time
-        # (kernels overlap across slots, so these are summed busy times, not a partition)
-        pcms.trace_enable(True)
-        wl.step()
-        torch.cuda.synchronize()
-        pcms.trace_enable(False)
-        st = kernel_launches(pcms.trace_read())
-        extra["serve_kernels_ms"] = {k: [v[0], round(v[1], 2)] for k, v in sorted(
-            st.items(), key=lambda kv: -kv[1][1])[:16]}
+        if rank == 0:   # the last timed step's outputs against the oracle
+            import oracle
+            oracle.build()
+            extra["accuracy"] = wl.accuracy(oracle)
+        # where the serving step spends device time: one step on a single slot (no overlap)
+        extra["serving_breakdown"] = wl.breakdown()
+        extra["serving_breakdown"]["launches_per_step_16_slots"] = launches / args.steps
         ol = wl.open_loop(value / world)
         pf = wl.plain_fp64()
         extra.update({"latency_open_loop_0p8": {k: ol[k] for k in ("p50_ms", "p99_ms", "points_per_s",
@@ -679,7 +913,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        v, n, dt, sample = wl.cpu_sample(oracle)
+        v, n, dt, sample = (wl.cpu_sample(oracle, per_req=16384, n_req=400)
+                            if args.workload == "serve" else wl.cpu_sample(oracle))
         cpu = {"value": v, "unit": "points/s", "cores": oracle.get_threads(), "kind": "oracle",
                "sample": sample, "seconds": dt}
 
@@ -702,6 +937,8 @@ def main():
             "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
             "cpu_baseline": cpu, **extra, "transfer_pass": transfer,
         }
+        if configs is not None:
+            line["configs"] = configs
         if study is not None:
             line["roundtrip_study"] = study
         if study5 is not None:

@@ -736,6 +736,10 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
         M.max_count = (int64_t)hs[2];
         M.max_k = (int64_t)hs[3];
         M.nnz = (int64_t)hs[4];
+        static const char* pair_names[2][3] = {
+            {"mls_map_pairs_d2k0", "mls_map_pairs_d2k1", "mls_map_pairs_d2k2"},
+            {"mls_map_pairs_d3k0", "mls_map_pairs_d3k1", "mls_map_pairs_d3k2"}};
+        trace_count(pair_names[dim - 2][deg], M.nnz);   // the assembly's selected pairs
     }
 }
 
