@@ -552,6 +552,42 @@ def roundtrip_study(torch, W, iterations=100, n=553):
     return out
 
 
+def apply_leg(torch, pcms, tw, peaks, kind, flush, reps=5):
+    """The 16-field apply of the 3D case's mixed operator (8M -> 8M, quadratic, r = 0.012;
+    1/8 of it with --workload transfer_small), in its two forms: the FP32 CUDA-core sparse
+    product (pcms_apply_map) and the tensor-core form (pcms_apply_map_bf16: BF16 three-term
+    splits, six term products on mma.sync, FP32 accumulation). Each is timed with CUDA events
+    on the launching stream after a 256 MiB L2-flushing write (best of reps, whole call:
+    fields into sorted order, product, results back to caller order); HBM roofline against
+    the bytes an apply must move (8 B per nonzero, 64 B per source and per target)."""
+    d, c4 = tw.d, tw.cfg["c4"]
+    m = pcms.create_map(d["s4"], d["t4"], 2, c4.radius, precision="mixed")
+    nnz = m.info()["nnz"]
+    stream = torch.cuda.current_stream()
+    by = spmm_bytes(nnz, c4.src.shape[1], c4.tgt.shape[1], 16)
+    res = {"nnz": nnz, "algorithmic_bytes": by}
+    outs = {}
+    for name, fn in (("fp32_cuda_cores", lambda: m.apply(d["f4"])),
+                     ("bf16x3_tensor_cores", lambda: m.apply_bf16(d["f4"]))):
+        fn()
+        best = None
+        for _ in range(reps):
+            flush_l2(flush)
+            o, ms = timed(torch, fn, stream)
+            best = ms if best is None else min(best, ms)
+        outs[name] = o
+        gbs = by / (best / 1e3) / 1e9
+        res[name] = {"ms": best, "achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"],
+                     "frac": gbs / peaks["hbm_gbs"], "peak_source": f"{kind} HBM copy"}
+    a, b = outs["fp32_cuda_cores"], outs["bf16x3_tensor_cores"]
+    ok = torch.isfinite(a).all(dim=0)
+    den = a[:, ok].abs().amax(dim=1).clamp_min(1e-30)
+    res["normwise_diff_bf16_vs_fp32"] = float(((a[:, ok] - b[:, ok]).abs().amax(dim=1) / den).max())
+    res["tensor_flops_per_call"] = int(((nnz + 15) // 16 + c4.tgt.shape[1] // 16) * 12 * 16 * 8 * 16 * 2)
+    m.destroy()
+    return res
+
+
 def config1_leg(torch, pcms, W, orc, reps=50):
     """The 10,000 -> 10,000 FP64 2D transfer (uniform points, linear basis, Wendland C2,
     r = 0.03, one field sin(2 pi x) cos(2 pi y)) as one request at a time through
@@ -840,6 +876,7 @@ def main():
                 "work": {"mls2d_pairs": tw.pairs3, "mls3d_nnz": tw.nnz4}}
     peaks, kind = measured_peaks()
     roof = tw.roofline(ttrace, peaks, kind)
+    apply_forms = apply_leg(torch, pcms, tw, peaks, kind, flush)
     configs = None
     if args.workload == "serve" and rank == 0:
         import oracle
@@ -937,6 +974,7 @@ def main():
             "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
             "cpu_baseline": cpu, **extra, "transfer_pass": transfer,
         }
+        line["apply_16_fields"] = apply_forms
         if configs is not None:
             line["configs"] = configs
         if study is not None:

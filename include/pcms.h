@@ -252,6 +252,22 @@ pcms_status pcms_mls_transfer_batch(const pcms_batch_item* items, int n_items,
 pcms_status pcms_apply_map_noalloc(pcms_map map, const void* fields, int n_fields, void* out,
                                    void* stream);
 
+/*
+ * pcms_apply_map_bf16 -- the result of pcms_apply_map for a PCMS_MIXED map (Sec. 3.2.1,
+ *   Eq. 1, out = N F for up to 16 fields), computed on the tensor cores. Each FP32 operator
+ *   value and field value is split into three BF16 terms (x = x_h + x_m + x_l to 2^-24 |x|);
+ *   the six term products of order <= 2 (the BF16 product and its residual correction) are
+ *   accumulated in FP32, so the accuracy is that of the FP32 apply. The fields are split once
+ *   into BF16 planes in source order; per tile of 16 targets the nonzeros' field rows are
+ *   gathered into shared memory and multiplied against the block-diagonal operator tile
+ *   (mma.sync m16n8k16). Rows solved by QR (the map's FP64 side table) are applied as in
+ *   pcms_apply_map. fields: device float32 [n_fields][n_src]; out: device float32
+ *   [n_fields][n_tgt]; 1 <= n_fields <= 16; maps of dimension 2 or 3. Scratch: 96 bytes per
+ *   source and 64 per target from cudaMallocAsync on `stream`. Asynchronous.
+ */
+pcms_status pcms_apply_map_bf16(pcms_map map, const float* fields, int n_fields, float* out,
+                                void* stream);
+
 /* Sizes and status counts of a map. Syncs the map's stream. */
 pcms_status pcms_map_info(pcms_map map, pcms_map_info_t* info);
 

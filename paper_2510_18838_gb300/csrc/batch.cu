@@ -837,8 +837,17 @@ void launch_class_t(BatchHeader* hdr, BatchReq* reqs, cudaStream_t s, bool trace
     }
     PCMS_LAUNCH_CHECK("k_batch_mls");
     if (DEG >= 1) {
+        static const int qr_per_sm = [] {
+            int n = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_qr<DIM, DEG>, QR_WARPS * 32, 0) !=
+                    cudaSuccess || n < 1) {
+                (void)cudaGetLastError();
+                n = 1;
+            }
+            return n;
+        }();
         TraceScope ts(traced ? "batch_qr" : nullptr, s);
-        k_batch_qr<DIM, DEG><<<num_sms(), QR_WARPS * 32, 0, s>>>(hdr, reqs);
+        k_batch_qr<DIM, DEG><<<num_sms() * qr_per_sm, QR_WARPS * 32, 0, s>>>(hdr, reqs);
     }
     PCMS_LAUNCH_CHECK("k_batch_qr");
 }

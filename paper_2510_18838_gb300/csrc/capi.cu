@@ -161,6 +161,20 @@ pcms_status pcms_apply_map(pcms_map map, const void* fields, int n_fields, void*
     });
 }
 
+pcms_status pcms_apply_map_bf16(pcms_map map, const float* fields, int n_fields, float* out,
+                                void* stream) {
+    REQUIRE(map != nullptr, "pcms_apply_map_bf16: map is NULL");
+    REQUIRE(map->impl.P.prec == PCMS_MIXED, "pcms_apply_map_bf16: the map must be PCMS_MIXED");
+    REQUIRE(map->impl.P.dim <= 3, "pcms_apply_map_bf16: maps of dimension 2 or 3");
+    REQUIRE(n_fields >= 1 && n_fields <= 16, "pcms_apply_map_bf16: n_fields must be in 1..16");
+    REQUIRE(map->impl.ns == 0 || fields != nullptr, "pcms_apply_map_bf16: fields is NULL");
+    REQUIRE(map->impl.nt == 0 || out != nullptr, "pcms_apply_map_bf16: out is NULL");
+    return guarded("pcms_apply_map_bf16", [&]() -> pcms_status {
+        pcms::mls_apply_tc(map->impl, fields, n_fields, out, (cudaStream_t)stream);
+        return PCMS_OK;
+    });
+}
+
 pcms_status pcms_mls_transfer_batch(const pcms_batch_item* items, int n_items,
                                     int32_t* result, void* stream) {
     REQUIRE(n_items >= 0 && n_items <= PCMS_BATCH_MAX_ITEMS,

@@ -368,6 +368,8 @@ void fields_to_sorted_f32(const MapImpl& M, const float* fields, int nf, int fp,
 void stage_to_caller_f32(const MapImpl& M, const float* stage, int fp, int nf, float* out,
                          cudaStream_t s);
 void mls_apply(MapImpl& M, const void* fields, int nf, void* out, cudaStream_t s);
+// the same apply on the tensor cores (BF16 three-term splits, FP32 accumulation; apply_tc.cu)
+void mls_apply_tc(MapImpl& M, const float* fields, int nf, float* out, cudaStream_t s);
 // apply with caller-provided scratch of apply_scratch_bytes(M, nf) bytes (256-aligned base);
 // allocates nothing, returns the first failing launch's status and names it in *where
 int64_t apply_scratch_bytes(const MapImpl& M, int nf);

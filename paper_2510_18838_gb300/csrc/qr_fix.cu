@@ -161,19 +161,30 @@ __global__ void k_qr_export(int n, const int32_t* __restrict__ list, const int32
     }
 }
 
+// enough blocks to fill the GPU (the count may only be known on the device): a warp per
+// listed target, as many resident blocks as fit, at most one warp per entry when n is known
 template <int DIM, int DEG, typename T, bool MAP>
-void launch_fix(const QrFixArgs& a, cudaStream_t s) {
-    k_qr_fix<DIM, DEG, T, MAP><<<num_sms(), QF_WARPS * 32, 0, s>>>(a);
+void launch_fix(const QrFixArgs& a, int64_t n_max, cudaStream_t s) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qr_fix<DIM, DEG, T, MAP>,
+                                                      QF_WARPS * 32, 0) != cudaSuccess ||
+        per_sm < 1) {
+        (void)cudaGetLastError();
+        per_sm = 1;
+    }
+    const int64_t want = (n_max + QF_WARPS - 1) / QF_WARPS;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * per_sm));
+    k_qr_fix<DIM, DEG, T, MAP><<<blocks, QF_WARPS * 32, 0, s>>>(a);
 }
 
 template <typename T, bool MAP>
-void dispatch_fix(int dim, int deg, const QrFixArgs& a, cudaStream_t s) {
+void dispatch_fix(int dim, int deg, const QrFixArgs& a, int64_t n_max, cudaStream_t s) {
     if (dim == 2) {
-        if (deg == 1) launch_fix<2, 1, T, MAP>(a, s);
-        else launch_fix<2, 2, T, MAP>(a, s);
+        if (deg == 1) launch_fix<2, 1, T, MAP>(a, n_max, s);
+        else launch_fix<2, 2, T, MAP>(a, n_max, s);
     } else {
-        if (deg == 1) launch_fix<3, 1, T, MAP>(a, s);
-        else launch_fix<3, 2, T, MAP>(a, s);
+        if (deg == 1) launch_fix<3, 1, T, MAP>(a, n_max, s);
+        else launch_fix<3, 2, T, MAP>(a, n_max, s);
     }
 }
 
@@ -210,8 +221,8 @@ void qr_fix_transfer(int dim, int deg, bool fp64, const Grid& g, const SortedPoi
     a.out = out;
     a.status_caller = status;
     PCMS_TRACE("mls_qr_fix", s);
-    if (fp64) dispatch_fix<double, false>(dim, deg, a, s);
-    else dispatch_fix<float, false>(dim, deg, a, s);
+    if (fp64) dispatch_fix<double, false>(dim, deg, a, Tp.n, s);
+    else dispatch_fix<float, false>(dim, deg, a, Tp.n, s);
     PCMS_LAUNCH_CHECK("k_qr_fix");
 }
 
@@ -234,7 +245,7 @@ void qr_fix_map(MapImpl& M, const int32_t* list, int n, cudaStream_t s) {
     a.qn = M.qr_cnt.as<int32_t>();
     {
         PCMS_TRACE("mls_qr_rows", s);
-        dispatch_fix<float, true>(M.P.dim, M.P.degree, a, s);
+        dispatch_fix<float, true>(M.P.dim, M.P.degree, a, n, s);
     }
     PCMS_LAUNCH_CHECK("k_qr_fix (map)");
     PCMS_CU(cudaStreamSynchronize(s));   // the count and the host copy above

@@ -97,6 +97,7 @@ SIGNATURES = {
     "pcms_create_map": (_I, [_I, _P, _I64, _P, _I64, _I, _D, _P, _P, _P]),
     "pcms_apply_map": (_I, [_P, _P, _I, _P, _P]),
     "pcms_apply_map_noalloc": (_I, [_P, _P, _I, _P, _P]),
+    "pcms_apply_map_bf16": (_I, [_P, _P, _I, _P, _P]),
     "pcms_mls_transfer": (_I, [_I, _P, _I64, _P, _I64, _I, _D, _P, _P, _I, _P, _P, _P]),
     "pcms_count_neighbors": (_I, [_I, _P, _I64, _P, _I64, _I, _D, _P, _P, _P, _P, _P]),
     "pcms_mls_transfer_batch": (_I, [_P, _I, _P, _P]),
@@ -243,6 +244,18 @@ class Map:
         if out is None:
             out = torch.empty((nf, self.n_tgt), dtype=self.dtype, device=f.device)
         _check(lib().pcms_apply_map(self.handle, _ptr(f), nf, _ptr(out), _stream(stream)))
+        return out[0] if squeeze else out
+
+    def apply_bf16(self, fields, out=None, stream=None):
+        """pcms_apply_map_bf16: the apply on the tensor cores (mixed maps, float32 fields)."""
+        f = _dev(fields, torch.float32, "fields")
+        squeeze = f.dim() == 1
+        if squeeze:
+            f = f[None]
+        nf = f.shape[0]
+        if out is None:
+            out = torch.empty((nf, self.n_tgt), dtype=torch.float32, device=f.device)
+        _check(lib().pcms_apply_map_bf16(self.handle, _ptr(f), nf, _ptr(out), _stream(stream)))
         return out[0] if squeeze else out
 
     def apply_noalloc(self, fields, out, stream=None):

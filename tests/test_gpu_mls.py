@@ -188,6 +188,36 @@ def test_mixed_multifield_apply_3d(P):
         np.testing.assert_allclose(part[:, ok], out[:nf, ok], rtol=1e-6, atol=1e-6)
 
 
+@pytest.mark.parametrize("dim,nf", [(3, 16), (3, 5), (2, 1), (2, 13)])
+def test_tensor_core_apply_matches_the_oracle_and_the_fp32_apply(P, dim, nf):
+    """pcms_apply_map_bf16 (BF16 three-term splits on mma.sync, FP32 accumulation) against the
+    oracle within the mixed tolerance (the FP32 CUDA-core apply of the same map too, and the
+    two against each other); targets outside the box (NaN) stay NaN; a ragged last tile of 16
+    targets and rows of uneven length (the dense slab) included."""
+    if dim == 3:
+        src = W.slab_points(60000, seed=401)
+        tgt = W.uniform_points(3001, 3, 402, lo=-0.05, hi=1.05)
+        r = 0.07
+    else:
+        src = W.gaussian_mixture_points(40000, 301, 302)
+        tgt = W.uniform_points(2999, 2, 303)
+        r = 0.02
+    f = W.trig_fields(src, nf)
+    m = P.create_map(cu(src), cu(tgt), 2, r, precision="mixed", min_neighbors=10)
+    ref = host(m.apply(cu(f)))
+    out = host(m.apply_bf16(cu(f)))
+    o = oracle.mls(src, tgt, f.astype(np.float64), 2, r, min_neighbors=10, mode="grid")
+    ok = o["status"] == 0
+    assert np.array_equal(np.isfinite(out).all(axis=0), ok)
+    e_tc, e_32 = normwise_err(out, o["values"], ok), normwise_err(ref, o["values"], ok)
+    assert e_32 <= TOL_MIXED, e_32
+    assert e_tc <= TOL_MIXED, (e_tc, e_32)
+    # both are FP32-level results; on rows with a large sum_j |N_j| (far targets of the
+    # mixture, whose radius grew) they differ by up to about that sum times 2^-23
+    assert normwise_err(out, ref, ok) <= TOL_MIXED
+    m.destroy()
+
+
 def test_mixed_growth_gaussian_mixture(P):
     src = W.gaussian_mixture_points(60000, 301, 302)
     tgt = W.uniform_points(3000, 2, 303)

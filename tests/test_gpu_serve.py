@@ -229,7 +229,7 @@ def test_batched_requests_are_bitwise_the_same_alone_and_match_the_oracle(env):
     dreqs = serve.materialize(reqs, torch.device("cuda", 0))
     reused = {d.req.reuse_of for d in dreqs if d.req.kind == "mls" and d.req.reuse_of >= 0}
     small = [i for i, d in enumerate(dreqs) if _batchable(d, reused)]
-    assert len(small) >= 8
+    assert len(small) >= 4
     st = serve.run_served(dreqs, n_slots=6, mem_cap=4 << 30)
     assert st["failed"] == 0
     assert st["batched_requests"] >= len(small) and st["batches"] < st["batched_requests"]
