@@ -823,6 +823,8 @@ def main():
     ap.add_argument("--workload", default="serve",
                     choices=["serve", "transfer", "transfer_small", "mls5d"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the plan rules (no tuning table)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -856,6 +858,17 @@ def main():
                               "higher_is_better": True, "dtype": "f64", "data": "synthetic",
                               "config": {"workload": st["workload"]}, "mls5d": st}), flush=True)
         return
+
+    # ---- plan tuning on this GPU (the table then serves every leg below)
+    tuning = None
+    if not args.no_tune:
+        from paper_2510_18838_gb300 import tune
+        tab = tune.tune()
+        tuning = {"entries": tab["entries"], "seconds": tab["seconds"],
+                  "keys_measured": len([m for m in tab["measurements"] if "key" in m]),
+                  "keys_changed": len([e for e in tab["entries"] if "lanes" in e]),
+                  "apply": [m for m in tab["measurements"] if "apply_fields" in m],
+                  "table": "measured in this run (paper_2510_18838_gb300.tune.default_shapes)"}
 
     # ---- single-stream transfer pass: per-kernel breakdown and the roofline entry
     tw = TransferWorkload(torch, pcms, W, dev, small=args.workload == "transfer_small")
@@ -902,6 +915,18 @@ def main():
     for _ in range(args.warmup):
         wl.step()
     torch.cuda.synchronize()
+    if tuning is not None and args.workload == "serve":
+        # the table against the plan rules on the workload itself: two steps each, the
+        # faster stays for the timed steps
+        def two(entries):
+            pcms.tune_set(entries)
+            return min(timed(torch, wl.step, stream)[1] for _ in range(2))
+        rules_ms = two([])
+        tuned_ms = two(tuning["entries"])
+        tuning["serving_step_ms"] = {"rules": rules_ms, "tuned": tuned_ms}
+        tuning["kept"] = tuned_ms < rules_ms
+        pcms.tune_set(tuning["entries"] if tuning["kept"] else [])
+        torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -975,6 +1000,7 @@ def main():
             "cpu_baseline": cpu, **extra, "transfer_pass": transfer,
         }
         line["apply_16_fields"] = apply_forms
+        line["tuning"] = tuning
         if configs is not None:
             line["configs"] = configs
         if study is not None:

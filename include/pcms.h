@@ -268,6 +268,35 @@ pcms_status pcms_apply_map_noalloc(pcms_map map, const void* fields, int n_field
 pcms_status pcms_apply_map_bf16(pcms_map map, const float* fields, int n_fields, float* out,
                                 void* stream);
 
+/*
+ * Plan tuning (no counterpart in the paper; runtime). The kernels' launch plan is chosen by
+ * rules from the expected neighbour count n (sources per box volume times the ball): lanes per
+ * target (8, or 32 from 160 neighbours), the grid's cell edge (r/3 in 2D, r/6 in 2D from 1000
+ * neighbours, r/2 in 3D), and the CUDA-core apply. A tuning table replaces these choices
+ * where it has an entry: for a (dim, degree, precision, mode, bucket = floor(log2 n)) the
+ * lanes (8 or 32) and the cell divisor d (cell edge = radius / d, 1 <= d <= 8) measured
+ * fastest; for mode PCMS_TUNE_APPLY (bucket = the field count, 1..16) the apply form that
+ * pcms_apply_map uses for mixed maps (0: CUDA cores, FP32; 1: tensor cores, as
+ * pcms_apply_map_bf16). The precision rules are not tuned: blocked compensation still takes
+ * 32 lanes from 1000 neighbours. Results change only by rounding between plans. The python
+ * package's tune module measures the candidates on seeded problems and writes the table.
+ * pcms_tune_set replaces the whole table (n = 0 clears it) and may be called while other
+ * threads run requests (they see the old or the new table). Invalid entries:
+ * PCMS_ERR_INVALID_ARG, the table unchanged.
+ */
+enum { PCMS_TUNE_MAP = 1, PCMS_TUNE_ONESHOT = 2, PCMS_TUNE_APPLY = 3 };
+typedef struct {
+    int dim, degree;
+    pcms_precision precision;
+    int mode, bucket;
+    int lanes;
+    double cell_div;
+    int apply_form;
+} pcms_tune_entry;
+pcms_status pcms_tune_set(const pcms_tune_entry* entries, int n);
+int pcms_tune_count(void);
+pcms_status pcms_tune_get(int i, pcms_tune_entry* entry);
+
 /* Sizes and status counts of a map. Syncs the map's stream. */
 pcms_status pcms_map_info(pcms_map map, pcms_map_info_t* info);
 

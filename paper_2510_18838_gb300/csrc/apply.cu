@@ -450,8 +450,14 @@ void stage_to_caller_f32(const MapImpl& M, const float* stage, int fp, int nf, f
 }
 
 void mls_apply(MapImpl& M, const void* fields, int nf, void* out, cudaStream_t s) {
-    if (M.P.prec == PCMS_MIXED) apply_t<float>(M, (const float*)fields, nf, (float*)out, s);
-    else apply_t<double>(M, (const double*)fields, nf, (double*)out, s);
+    if (M.P.prec == PCMS_MIXED) {
+        TuneEntry e;
+        if (M.P.dim <= 3 && tune_lookup(M.P.dim, M.P.degree, true, 3, nf, &e) && e.apply_form == 1)
+            return mls_apply_tc(M, (const float*)fields, nf, (float*)out, s);
+        apply_t<float>(M, (const float*)fields, nf, (float*)out, s);
+    } else {
+        apply_t<double>(M, (const double*)fields, nf, (double*)out, s);
+    }
 }
 
 int64_t apply_scratch_bytes(const MapImpl& M, int nf) {

@@ -21,16 +21,6 @@ int mom_kind(bool mixed, int acc) {
 }
 size_t mom_elem_bytes(int kind) { return kind == MOM_F32 ? sizeof(float) : sizeof(double); }
 
-// Cell edge of the source grid: r/3 in 2D, r/2 in 3D; r/6 in 2D for dense neighbourhoods
-// (expected count >= 1000, the blocked-compensation plan). Smaller cells trim candidate rows
-// closer to the ball at the price of more rows per target; measured on the 4M 2D and 8M 3D
-// transfers, r/3 is 5% faster in 2D and 6% slower in 3D than r/2, and with thousands of
-// candidates per row the rows of r/6 cells cost little beside the candidates they save.
-double cell_edge(int dim, double radius, double mean = 0.0) {
-    if (dim == 2) return (mean >= 1000.0 ? 1.0 / 6.0 : 1.0 / 3.0) * radius;
-    return 0.5 * radius;
-}
-
 int asm_blocks(int64_t nwork, int G) {
     int64_t groups_per_block = 8 * (32 / G);
     int64_t need = (nwork + groups_per_block - 1) / groups_per_block;
@@ -60,18 +50,29 @@ void rows64_apply_any(int dim, int deg, int G, const ShapeArgs& sh, const int32_
     PCMS_LAUNCH_CHECK("k_rows64_apply");
 }
 
-// Lanes per target and the first pass's accumulation, from the expected neighbour count
-// (ns * ball volume / box volume): 32 lanes from 160 neighbours on; blocked compensation
-// (mixed path) from 1000 on, where plain FP32 sums over n / 32 pairs per lane stop meeting
-// the error bound for ordinary targets. Below that plain sums pass for almost every target
-// and the blocked form would only cost registers.
+// Lanes per target, the first pass's accumulation and the grid's cell edge, from the expected
+// neighbour count (ns * ball volume / box volume).
+//  - 32 lanes from 160 neighbours on, else 8.
+//  - Blocked compensation (mixed path) from 1000 on, where plain FP32 sums over n / 32 pairs
+//    per lane stop meeting the error bound for ordinary targets; below that plain sums pass
+//    for almost every target and the blocked form would only cost registers.
+//  - Cell edge r/3 in 2D, r/2 in 3D; r/6 in 2D from 1000 neighbours on. Smaller cells trim
+//    candidate rows closer to the ball at the price of more rows per target; measured on the
+//    4M 2D and 8M 3D transfers, r/3 is 5% faster in 2D and 6% slower in 3D than r/2, and with
+//    thousands of candidates per row the rows of r/6 cells cost little beside the candidates
+//    they save.
+// An entry of the tuning table (pcms_tune_set: lanes and cell divisor measured fastest for
+// this dimension, degree, precision, mode and count bucket) replaces the lanes and the cell
+// edge; the accumulation stays the precision rule's (blocked compensation needs 32 lanes).
 struct AsmPlan {
     int G;
     int acc;
     double mean;   // expected neighbours per target
+    double cell;   // grid cell edge
+    bool tuned;
 };
-AsmPlan choose_plan(int dim, int64_t ns, double radius, const double* lo, const double* hi,
-                    bool mixed) {
+AsmPlan choose_plan(int dim, int deg, int mode, int64_t ns, double radius, const double* lo,
+                    const double* hi, bool mixed) {
     double vol = 1.0;
     for (int d = 0; d < dim; d++) vol *= std::max(hi[d] - lo[d], radius);
     double ball = dim == 2 ? M_PI * radius * radius : 4.0 / 3.0 * M_PI * radius * radius * radius;
@@ -79,7 +80,18 @@ AsmPlan choose_plan(int dim, int64_t ns, double radius, const double* lo, const 
     AsmPlan p;
     p.mean = mean;
     p.G = mean >= 160.0 ? 32 : 8;
-    p.acc = (mixed && p.G == 32 && mean >= 1000.0) ? ACC_BK : ACC_PLAIN;
+    double div = dim == 2 ? (mean >= 1000.0 ? 6.0 : 3.0) : 2.0;
+    p.tuned = false;
+    TuneEntry e;
+    if (mode != MODE_COUNT && tune_lookup(dim, deg, mixed, mode, tune_bucket(mean), &e)) {
+        p.G = e.lanes;
+        div = e.cell_div;
+        p.tuned = true;
+    }
+    const bool bk = mixed && mean >= 1000.0;
+    if (bk) p.G = 32;
+    p.acc = bk ? ACC_BK : ACC_PLAIN;
+    p.cell = radius / div;
     return p;
 }
 
@@ -438,11 +450,12 @@ MlsParams settle_growth(const MlsParams& P, const double* src, int64_t ns, const
     const int dim = P.dim;
     const bool mixed = P.prec == PCMS_MIXED;
     BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
-    Grid g = make_grid(dim, b.lo, b.hi, cell_edge(dim, P.radius, choose_plan(dim, ns, P.radius, b.lo, b.hi, mixed).mean), MAX_CELLS);
+    const AsmPlan cplan = choose_plan(dim, 0, MODE_COUNT, ns, P.radius, b.lo, b.hi, mixed);
+    Grid g = make_grid(dim, b.lo, b.hi, cplan.cell, MAX_CELLS);
     SortedPoints S, Tp;
     sort_points(g, src, ns, true, mixed, S, s);
     sort_points(g, tgt, nt, false, mixed, Tp, s, true);
-    const int G = choose_plan(dim, ns, P.radius, b.lo, b.hi, mixed).G;
+    const int G = cplan.G;
     DBuf c(sizeof(int32_t) * nt, s);
     DBuf k(sizeof(int32_t) * nt, s);
     DBuf mx(sizeof(unsigned long long), s);
@@ -535,10 +548,10 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
     const bool mixed = P.prec == PCMS_MIXED;
     const int64_t ns = M.ns, nt = M.nt;
     BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
-    M.g = make_grid(dim, b.lo, b.hi, cell_edge(dim, P.radius, choose_plan(dim, ns, P.radius, b.lo, b.hi, mixed).mean), MAX_CELLS);
+    const AsmPlan plan = choose_plan(dim, deg, MODE_MAP, ns, P.radius, b.lo, b.hi, mixed);
+    M.g = make_grid(dim, b.lo, b.hi, plan.cell, MAX_CELLS);
     sort_points(M.g, src, ns, true, mixed, M.src, s);
     sort_points(M.g, tgt, nt, false, mixed, M.tgt, s, true);
-    const AsmPlan plan = choose_plan(dim, ns, P.radius, b.lo, b.hi, mixed);
     const int G = plan.G;
 
     M.counts.alloc(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
@@ -766,11 +779,12 @@ void mls_count(const MlsParams& P0, const double* src, int64_t ns, const double*
     const int dim = P.dim;
     const bool mixed = P.prec == PCMS_MIXED;
     BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
-    Grid g = make_grid(dim, b.lo, b.hi, cell_edge(dim, P.radius, choose_plan(dim, ns, P.radius, b.lo, b.hi, mixed).mean), MAX_CELLS);
+    const AsmPlan cplan = choose_plan(dim, 0, MODE_COUNT, ns, P.radius, b.lo, b.hi, mixed);
+    Grid g = make_grid(dim, b.lo, b.hi, cplan.cell, MAX_CELLS);
     SortedPoints S, Tp;
     sort_points(g, src, ns, true, mixed, S, s);
     sort_points(g, tgt, nt, false, mixed, Tp, s, true);
-    const int G = choose_plan(dim, ns, P.radius, b.lo, b.hi, mixed).G;
+    const int G = cplan.G;
     DBuf c(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
     DBuf k(sizeof(int32_t) * std::max<int64_t>(nt, 1), s);
     DBuf off(sizeof(int64_t) * (nt + 1), s);
@@ -820,11 +834,11 @@ void mls_transfer(const MlsParams& P0, const double* src, int64_t ns, const doub
     const bool mixed = P.prec == PCMS_MIXED;
     *n_under = 0;
     BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
-    Grid g = make_grid(dim, b.lo, b.hi, cell_edge(dim, P.radius, choose_plan(dim, ns, P.radius, b.lo, b.hi, mixed).mean), MAX_CELLS);
+    const AsmPlan plan = choose_plan(dim, deg, MODE_FUSED, ns, P.radius, b.lo, b.hi, mixed);
+    Grid g = make_grid(dim, b.lo, b.hi, plan.cell, MAX_CELLS);
     SortedPoints S, Tp;
     sort_points(g, src, ns, true, mixed, S, s);
     sort_points(g, tgt, nt, false, mixed, Tp, s, true);
-    const AsmPlan plan = choose_plan(dim, ns, P.radius, b.lo, b.hi, mixed);
     const int G = plan.G;
     const size_t fsz = mixed ? sizeof(float) : sizeof(double);
     DBuf fs(fsz * std::max<int64_t>(ns, 1), s);

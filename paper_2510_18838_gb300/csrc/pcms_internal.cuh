@@ -457,6 +457,16 @@ ProjectionResult l2_project(const MeshImpl& S, const double* fs, MeshImpl& T, do
 // number of SMs of the current device (cached)
 int num_sms();
 
+// plan tuning table (tune.cu; filled through pcms_tune_set)
+struct TuneEntry {
+    int dim, degree, mixed, mode, bucket;   // mode: 1 operator, 2 one-shot, 3 apply (bucket = fields)
+    int lanes;                              // lanes per target (8 or 32)
+    double cell_div;                        // grid cell edge = radius / cell_div
+    int apply_form;                         // apply: 0 CUDA cores (FP32), 1 tensor cores (BF16 x 3)
+};
+int tune_bucket(double mean);   // floor(log2(expected neighbours)), 0 below 1
+bool tune_lookup(int dim, int degree, bool mixed, int mode, int bucket, TuneEntry* out);
+
 }  // namespace pcms
 
 // the opaque handle behind pcms_map

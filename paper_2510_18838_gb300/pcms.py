@@ -81,6 +81,14 @@ class BatchItem(ctypes.Structure):
                 ("out", ctypes.c_void_p), ("target_status", ctypes.c_void_p)]
 
 
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("degree", ctypes.c_int), ("precision", ctypes.c_int),
+                ("mode", ctypes.c_int), ("bucket", ctypes.c_int), ("lanes", ctypes.c_int),
+                ("cell_div", ctypes.c_double), ("apply_form", ctypes.c_int)]
+
+
+TUNE_MAP, TUNE_ONESHOT, TUNE_APPLY = 1, 2, 3
+
 BATCH_MAX_POINTS = 131072
 BATCH_MAX_ITEMS = 256
 
@@ -101,6 +109,9 @@ SIGNATURES = {
     "pcms_mls_transfer": (_I, [_I, _P, _I64, _P, _I64, _I, _D, _P, _P, _I, _P, _P, _P]),
     "pcms_count_neighbors": (_I, [_I, _P, _I64, _P, _I64, _I, _D, _P, _P, _P, _P, _P]),
     "pcms_mls_transfer_batch": (_I, [_P, _I, _P, _P]),
+    "pcms_tune_set": (_I, [_P, _I]),
+    "pcms_tune_count": (_I, []),
+    "pcms_tune_get": (_I, [_I, _P]),
     "pcms_map_info": (_I, [_P, _P]),
     "pcms_map_export": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "pcms_map_destroy": (None, [_P, _P]),
@@ -341,6 +352,36 @@ def mls_transfer(src, tgt, fields, degree, radius, precision="fp64", weight="wen
     if st not in (OK, UNDERDETERMINED):
         _check(st)
     return out, (status[:nt] if status is not None else None)
+
+
+def tune_set(entries):
+    """pcms_tune_set: replace the plan tuning table. entries: dicts with dim, degree,
+    precision ("mixed"/"fp64"), mode (TUNE_MAP, TUNE_ONESHOT or TUNE_APPLY), bucket, and
+    lanes + cell_div, or apply_form for TUNE_APPLY."""
+    arr = (TuneEntry * max(len(entries), 1))()
+    for i, e in enumerate(entries):
+        x = arr[i]
+        x.dim, x.degree = int(e["dim"]), int(e["degree"])
+        x.precision = FP64 if e.get("precision", "mixed") == "fp64" else MIXED
+        x.mode, x.bucket = int(e["mode"]), int(e["bucket"])
+        x.lanes = int(e.get("lanes", 0))
+        x.cell_div = float(e.get("cell_div", 0.0))
+        x.apply_form = int(e.get("apply_form", 0))
+    _check(lib().pcms_tune_set(ctypes.byref(arr), len(entries)))
+
+
+def tune_get():
+    """The plan tuning table as a list of dicts."""
+    L = lib()
+    out = []
+    for i in range(L.pcms_tune_count()):
+        x = TuneEntry()
+        _check(L.pcms_tune_get(i, ctypes.byref(x)))
+        out.append({"dim": x.dim, "degree": x.degree,
+                    "precision": "fp64" if x.precision == FP64 else "mixed", "mode": x.mode,
+                    "bucket": x.bucket, "lanes": x.lanes, "cell_div": x.cell_div,
+                    "apply_form": x.apply_form})
+    return out
 
 
 def mls_transfer_batch(problems, with_status=True, stream=None):

@@ -115,3 +115,25 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(pcms, "LIB_PATH", os.path.join(str(tmp_path), "missing.so"))
     with pytest.raises(ImportError):
         pcms.lib()
+
+
+def test_tune_table_is_validated_and_replaced_whole():
+    """pcms_tune_set takes a whole table or nothing: an invalid entry (lanes other than 8 or
+    32, a cell divisor out of [1, 8], an apply bucket beyond 16 fields) is refused and the
+    table stays as it was. No GPU is needed."""
+    from paper_2510_18838_gb300 import build, pcms
+    build.build()
+    good = [{"dim": 2, "degree": 2, "precision": "mixed", "mode": pcms.TUNE_MAP, "bucket": 5,
+             "lanes": 8, "cell_div": 4.0},
+            {"dim": 3, "degree": 2, "precision": "mixed", "mode": pcms.TUNE_APPLY, "bucket": 16,
+             "apply_form": 1}]
+    pcms.tune_set(good)
+    assert len(pcms.tune_get()) == 2
+    for bad in (dict(good[0], lanes=16), dict(good[0], cell_div=0.5), dict(good[0], dim=4),
+                dict(good[1], bucket=17), dict(good[0], mode=7)):
+        with pytest.raises(pcms.PcmsError):
+            pcms.tune_set([good[0], bad])
+        assert pcms.tune_get() == [dict(good[0], apply_form=0),
+                                   dict(good[1], lanes=0, cell_div=0.0)]
+    pcms.tune_set([])
+    assert pcms.tune_get() == []
