@@ -41,6 +41,11 @@ enum { MODE_COUNT = 0, MODE_MAP = 1, MODE_FUSED = 2 };
 //              the rounding of the individual terms, which averages out like 1/sqrt(n).
 enum { ACC_PLAIN = 0, ACC_BK = 1 };
 constexpr int BK_BLOCK = 4;
+// Tier 1 of dense 2D one-shot targets (32 lanes per target, every lane adding its own
+// candidate) uses blocks of BK_BLOCK_DENSE pairs: a quarter of the Kahan updates, calibrated
+// with its own acceptance bound AMP_BK_DENSE (below). Tier 2, and 3D, keep BK_BLOCK.
+constexpr int BK_BLOCK_DENSE = 16;
+constexpr int DENSE_UNROLL = 4;   // candidates per lane per step of the dense form's walk
 
 constexpr float MIX_BAND = 1.52587890625e-05f;   // 2^-16 relative band around r^2
 constexpr int MAX_DOUBLINGS = 60;
@@ -133,6 +138,13 @@ struct AsmArgs {
 //   plain sums          err ~ amp * 6e-8 * (1 + sqrt(n / 3G^2));
 //   blocked compensated err <= 3.4 * amp * 6e-8 / sqrt(n) (largest over 500 targets with
 //                       up to 5e5 neighbours), so AMP_BK = 32 leaves a factor 3.
+// A second emulation (600 uniform targets of the same case, up to 4.9e5 neighbours, lanes
+// fed in stream order with unselected candidates as exact zeros) put the largest constant at
+// 5.8 for blocks of 4 pairs and 8.3 for blocks of 16, the rounding of the terms alone at 4.9.
+// Dense one-shot tier 1 (blocks of BK_BLOCK_DENSE = 16) therefore accepts amp <=
+// AMP_BK_DENSE * sqrt(n) with AMP_BK_DENSE = 32 * 5.8 / 8.3 = 22: the same error bound as
+// blocks of 4 under AMP_BK. In that sample 0.01% of the pairs belong to targets between the
+// two bounds, which go to tier 2.
 //
 // Re-centred basis. Far targets (radius doubled until min_neighbors sources are inside)
 // often see their neighbours on one side, at offsets u = (s - t)/r of size ~1 with a small
@@ -151,6 +163,7 @@ struct AsmArgs {
 // targets this cuts amp and the error by factors of 50 to 300.
 constexpr double AMP_T1 = 64.0;
 constexpr double AMP_BK = 32.0;
+constexpr double AMP_BK_DENSE = 22.0;
 constexpr double AMP_SHAPE = 32.0;   // operator rows above this are evaluated in FP64
 constexpr double AMP_FP64 = 256.0;   // FP64 path: above this the error may pass 4e-13
 
@@ -375,7 +388,8 @@ __host__ __device__ __forceinline__ void basis_offsets(const T* dx, T inv_r, con
 // Adds one selected pair to the running sums: moments w u^p of degree <= 2k, and in fused
 // mode the right-hand side w b u^p of degree <= k. dx = target-relative offsets (the weight
 // is always a function of |dx| / r), b = field value, bc = re-centred basis or null.
-template <int DIM, int DEG, int MODE, typename T, int NACC>
+// WK >= 0 fixes the weight kind at compile time (the runtime kind is then ignored).
+template <int DIM, int DEG, int MODE, typename T, int NACC, int WK = -1>
 __host__ __device__ __forceinline__ void accumulate(T (&acc)[NACC > 0 ? NACC : 1], const T* dx,
                                                     T b, int kind, T inv_r, const T* bc,
                                                     bool selected = true) {
@@ -390,7 +404,7 @@ __host__ __device__ __forceinline__ void accumulate(T (&acc)[NACC > 0 ? NACC : 1
 #else
     q = sqrt(d2) * inv_r;
 #endif
-    T w = weight_value<T>(kind, q);
+    T w = weight_value<T>(WK >= 0 ? WK : kind, q);
     if (!selected) w = T(0);   // adds exact zeros: an unselected candidate leaves the sums as they are
     T u[3];
     basis_offsets<DIM, T>(dx, inv_r, bc, u);
@@ -429,6 +443,45 @@ __host__ __device__ __forceinline__ void bk_flush(float (&acc)[NACC], float (&su
         acc[i] = 0.f;
     }
 }
+
+// A lane's Kahan totals of blocked compensation: (sum, cmp) per running sum, the true total
+// being sum - cmp. Kept in registers, or (SMEM) in the block's shared memory at
+// base[i * 256] (one float2 per sum, 256 threads per block), which frees 2 NA registers
+// for the dense one-shot form, whose block flushes are rare.
+template <int NA, bool SMEM>
+struct KahanTotals {
+    float sum[NA], cmp[NA];
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int i = 0; i < NA; i++) {
+            sum[i] = 0.f;
+            cmp[i] = 0.f;
+        }
+    }
+    __device__ __forceinline__ void flush(float (&acc)[NA]) { bk_flush<NA>(acc, sum, cmp); }
+    __device__ __forceinline__ float2 pair(int i) const { return make_float2(sum[i], -cmp[i]); }
+};
+template <int NA>
+struct KahanTotals<NA, true> {
+    float2* base;
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int i = 0; i < NA; i++) base[i * 256] = make_float2(0.f, 0.f);
+    }
+    __device__ __forceinline__ void flush(float (&acc)[NA]) {
+#pragma unroll
+        for (int i = 0; i < NA; i++) {
+            float2 v = base[i * 256];
+            kahan_add(v.x, v.y, acc[i]);
+            base[i * 256] = v;
+            acc[i] = 0.f;
+        }
+    }
+    __device__ __forceinline__ float2 pair(int i) const {
+        const float2 v = base[i * 256];
+        return make_float2(v.x, -v.y);
+    }
+};
 
 // ------------------------------------------------------------------------------------
 // k_assemble
@@ -481,14 +534,18 @@ using MomT = typename std::conditional<ACC == ACC_BK, float2, T>::type;
 
 // Two blocks per SM (at most 128 registers) except: the blocked 3D quadratic form, whose
 // three accumulator sets of 35-45 moments would spill heavily at that size (one block); and
-// plain FP32 sums of at most 15 moments (degree <= 1, or 2D), three blocks (80 registers): the
-// walk is latency-bound, and the extra warps cut the serving stream's assembly time by 9%
-// despite a few dozen bytes of spills.
-template <int DIM, int DEG, int ACC, bool MIXED>
+// three blocks (80 registers) for plain FP32 sums of at most 15 moments (degree <= 1, or 2D)
+// and for the dense 2D one-shot form (its Kahan totals in shared memory): the walk is
+// latency-bound, and the extra warps cut the serving stream's assembly time by 9% and the
+// dense 2D transfer's by 2%, despite a few dozen bytes of spills.
+template <int DIM, int DEG, int ACC, bool MIXED, int MODE, int G>
 constexpr int asm_min_blocks() {
     return (ACC == ACC_BK && DIM == 3 && DEG == 2)
                ? 1
-               : ((MIXED && ACC == ACC_PLAIN && (DEG <= 1 || DIM == 2)) ? 3 : 2);
+               : ((MIXED && ACC == ACC_PLAIN && (DEG <= 1 || DIM == 2)) ||
+                          (ACC == ACC_BK && MODE == MODE_FUSED && G == 32 && DIM == 2)
+                      ? 3
+                      : 2);
 }
 
 // Candidate row rho of a target (cell (ct) and position in it (fr), cell units): the cells
@@ -596,7 +653,7 @@ __device__ __forceinline__ float4 estimate_basis(const AsmArgs& A, const long lo
 }
 
 template <int DIM, int DEG, bool MIXED, int MODE, int G, typename FT, int ACC = ACC_PLAIN>
-__global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC, MIXED>()) k_assemble(AsmArgs A) {
+__global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC, MIXED, MODE, G>()) k_assemble(AsmArgs A) {
     static_assert(ACC == ACC_PLAIN || (MIXED && MODE != MODE_COUNT), "blocked compensation: mixed moments only");
     using T = typename std::conditional<MIXED, float, double>::type;
     using MT = MomT<T, ACC>;
@@ -626,6 +683,11 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC, MIXED>()) k
     // are selected, so every lane accumulates its own candidate with the weight zeroed when it
     // is not selected, instead of compacting selected pairs through the shared-memory ring.
     constexpr bool PRED = MODE == MODE_FUSED && ACC == ACC_BK && G == 32;
+    const int bk_block = (PRED && DIM == 2 && !A.list) ? BK_BLOCK_DENSE : BK_BLOCK;
+    // the dense form's Kahan totals live in shared memory where they fit the static limit
+    constexpr int NA = NACC > 0 ? NACC : 1;
+    constexpr bool SMEM_TOT = PRED && NA * 256 * 8 <= 44 * 1024;
+    __shared__ float2 tot_s[SMEM_TOT ? NA * 256 : 1];
 
     const int64_t ngroups = (int64_t)gridDim.x * (blockDim.x >> 5) * GPW;
     const int64_t gid = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * GPW + gi;
@@ -678,10 +740,10 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC, MIXED>()) k
                 bc = bcv;
             }
         }
-        constexpr int NA = NACC > 0 ? NACC : 1;
         constexpr int NB = ACC == ACC_BK ? NA : 1;   // Kahan totals (blocked compensation)
         T acc[NA];
-        float sum[NB], cmp[NB];
+        KahanTotals<NB, SMEM_TOT> tot;
+        if constexpr (SMEM_TOT) tot.base = &tot_s[threadIdx.x];
         int pops = 0;
         for (;;) {
             const double r = A.lv.r[k];
@@ -732,11 +794,7 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC, MIXED>()) k
             }
 #pragma unroll
             for (int i = 0; i < NA; i++) acc[i] = T(0);
-#pragma unroll
-            for (int i = 0; i < NB; i++) {
-                sum[i] = 0.f;
-                cmp[i] = 0.f;
-            }
+            if constexpr (ACC == ACC_BK) tot.clear();
             pops = 0;
             cnt = 0;
             int qn = 0, head = 0;
@@ -766,34 +824,37 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC, MIXED>()) k
                 rA[gl] = ra;
                 rE[gl] = incl;
                 __syncwarp(gmask);
-                // stream position p -> source index; positions only grow, so the row cursor
-                // only moves forward (p < total keeps it inside the G rows)
-                int rcur = 0;
-                auto locate = [&](int p) -> int {
-                    while (rE[rcur] <= p) ++rcur;
-                    return rA[rcur] + (p - (rcur ? rE[rcur - 1] : 0));
-                };
-                CandT cn;
-                int jn = 0;
-                bool vn = gl < total;
-                if (vn) {
-                    jn = locate(gl);
-                    cn.load(A, jn);
-                }
-                for (int p0 = 0; p0 < total; p0 += G) {
-                    const bool v = vn;
-                    const int j = jn;
-                    const CandT c = cn;
-                    const int pn = p0 + G + gl;
-                    vn = pn < total;
-                    if (vn) {
-                        jn = locate(pn);
-                        cn.load(A, jn);
-                    }
-                    bool in = false;
-                    T dx[3] = {T(0), T(0), T(0)};
-                    if (v) {
-                        if constexpr (MIXED) {
+                if constexpr (PRED) {
+                    // Each lane keeps its own cursor into the G rows: its stream position
+                    // advances by G per step, and within a row the source index does too,
+                    // so the row table is read only where a lane crosses into a later row.
+                    // Steps are taken DU at a time while DU full steps remain (one row check,
+                    // one check for FP32-undecided pairs and one block-flush check per DU
+                    // candidates of a lane), then one at a time. Each lane counts its own
+                    // selected pairs; the group's count is reduced after the walk.
+                    auto stream = [&](auto wkc) {
+                        constexpr int WK = decltype(wkc)::value;
+                        constexpr int DU = DENSE_UNROLL;
+                        int rcur = 0, pos = gl, pend = 0, jc = 0;   // jc: source at pos
+                        if (pos < total) {
+                            while (rE[rcur] <= pos) ++rcur;
+                            pend = rE[rcur];
+                            jc = rA[rcur] + pos - (rcur ? rE[rcur - 1] : 0);
+                        }
+                        // move the cursor one step (pos < total before the step)
+                        auto step = [&]() {
+                            pos += G;
+                            if (pos < pend) {
+                                jc += G;
+                            } else if (pos < total) {   // the loop moves rcur at least once
+                                while (rE[rcur] <= pos) ++rcur;
+                                pend = rE[rcur];
+                                jc = rA[rcur] + pos - rE[rcur - 1];
+                            }
+                        };
+                        // offsets and FP32 classification of one candidate: 1 in, 0 out,
+                        // -1 undecided in FP32
+                        auto classify = [&](const CandT& c, T* dx) -> int {
                             float ddx, ddy, ddz = 0.f;
                             if (DIM == 2) {
                                 ddx = (c.h0.x - thi[0]) + (c.h0.z - tlo[0]);
@@ -805,84 +866,214 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC, MIXED>()) k
                             }
                             float d2f = ddx * ddx + ddy * ddy;
                             if (DIM == 3) d2f += ddz * ddz;
-                            int cl = classify32(A.weight, d2f, r2f);
-                            if (cl < 0) {
-                                double te[3] = {0.0, 0.0, 0.0};
+                            dx[0] = ddx;
+                            dx[1] = ddy;
+                            dx[2] = ddz;
+                            if constexpr (WK == PCMS_WENDLAND_C2)   // classify32 for this kind
+                                return d2f > r2f * (1.0f + MIX_BAND)
+                                           ? 0
+                                           : (d2f < r2f * (1.0f - MIX_BAND) ? 1 : -1);
+                            else
+                                return classify32(A.weight, d2f, r2f);
+                        };
+                        auto exact = [&](int j) -> bool {
+                            double te[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-                                for (int d = 0; d < DIM; d++) te[d] = A.tx64[d * A.nt + t];
-                                cl = select_exact(A.weight, dist2_exact<DIM>(A.sx64, A.ns, j, te), r, r2);
+                            for (int d = 0; d < DIM; d++) te[d] = A.tx64[d * A.nt + t];
+                            return select_exact(A.weight, dist2_exact<DIM>(A.sx64, A.ns, j, te), r,
+                                                r2) != 0;
+                        };
+                        int p0 = 0;
+                        for (; p0 + DU * G <= total; p0 += DU * G) {
+                            int jj[DU];
+                            CandT cc[DU];
+#pragma unroll
+                            for (int u = 0; u < DU; u++) {
+                                jj[u] = jc;
+                                cc[u].load(A, jc);
+                                if (u + 1 < DU) step();
                             }
-                            in = cl != 0;
-                            dx[0] = (T)ddx;
-                            dx[1] = (T)ddy;
-                            dx[2] = (T)ddz;
-                        } else {
-                            const double e0 = __dsub_rn(c.x[0], tx[0]);
-                            const double e1 = __dsub_rn(c.x[1], tx[1]);
-                            double d2 = __dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1));
-                            double e2 = 0.0;
-                            if (DIM == 3) {
-                                e2 = __dsub_rn(c.x[2], tx[2]);
-                                d2 = __dadd_rn(d2, __dmul_rn(e2, e2));
+                            step();
+                            T dx[DU][3];
+                            int cl[DU];
+                            bool und = false;
+#pragma unroll
+                            for (int u = 0; u < DU; u++) {
+                                cl[u] = classify(cc[u], dx[u]);
+                                und = und || cl[u] < 0;
                             }
-                            in = select64(A.weight, d2, r, r2, r2_in);
-                            dx[0] = (T)e0;
-                            dx[1] = (T)e1;
-                            dx[2] = (T)e2;
-                        }
-                    }
-                    const unsigned bal = __ballot_sync(gmask, in) & gmask;
-                    const int nin = __popc(bal);
-                    if (MODE == MODE_COUNT) {
-                        cnt += nin;
-                        continue;
-                    }
-                    if constexpr (PRED) {
-                        cnt += nin;
-                        if (nin == 0) continue;
-                        accumulate<DIM, DEG, MODE, T, NACC>(acc, dx, v ? (T)c.f : T(0), A.weight,
-                                                            inv_r, bc, in);
-                        if (++pops == BK_BLOCK) {
-                            bk_flush<NA>(acc, sum, cmp);
-                            pops = 0;
-                        }
-                        continue;
-                    }
-                    if (in) {
-                        T pay;
-                        if constexpr (MODE == MODE_MAP) pay = pack_index(j, T(0));
-                        else pay = (T)c.f;
-                        const int pos = (head + qn + __popc(bal & lt)) & (QCAP - 1);
-                        q[pos] = make_entry<T>(dx[0], dx[1], dx[2], pay);
-                    }
-                    qn += nin;
-                    cnt += nin;
-                    __syncwarp(gmask);
-                    if (qn >= G) {
-                        QE e = q[(head + gl) & (QCAP - 1)];
-                        T edx[3] = {e.x, e.y, e.z};
-                        accumulate<DIM, DEG, MODE, T, NACC>(acc, edx, e.w, A.weight, inv_r, bc);
-                        if constexpr (ACC == ACC_BK) {
-                            if (++pops == BK_BLOCK) {
-                                bk_flush<NA>(acc, sum, cmp);
+                            if (und) {
+#pragma unroll
+                                for (int u = 0; u < DU; u++)
+                                    if (cl[u] < 0) cl[u] = exact(jj[u]) ? 1 : 0;
+                            }
+#pragma unroll
+                            for (int u = 0; u < DU; u++) {
+                                cnt += cl[u];
+                                accumulate<DIM, DEG, MODE, T, NACC, WK>(acc, dx[u], (T)cc[u].f,
+                                                                        A.weight, inv_r, bc,
+                                                                        cl[u] != 0);
+                            }
+                            pops += DU;
+                            if (pops >= bk_block) {
+                                tot.flush(acc);
                                 pops = 0;
                             }
                         }
-                        if (MODE == MODE_MAP) {
-                            if (one_pass) {
-                                if (written + gl < STG) stg[written + gl] = unpack_index(e.w);
-                            } else if (A.cols && written + gl < row_len) {
-                                A.cols[row_off + written + gl] = unpack_index(e.w);
+                        for (; p0 < total; p0 += G) {
+                            const bool v = pos < total;
+                            const int j = jc;
+                            CandT c;
+                            if (v) {
+                                c.load(A, j);
+                                step();
                             }
-                            written += G;
+                            T dx[3] = {T(0), T(0), T(0)};
+                            int cl = 0;
+                            if (v) {
+                                cl = classify(c, dx);
+                                if (cl < 0) cl = exact(j) ? 1 : 0;
+                            }
+                            cnt += cl;
+                            accumulate<DIM, DEG, MODE, T, NACC, WK>(acc, dx, v ? (T)c.f : T(0),
+                                                                    A.weight, inv_r, bc, cl != 0);
+                            if (++pops >= bk_block) {
+                                tot.flush(acc);
+                                pops = 0;
+                            }
                         }
-                        head = (head + G) & (QCAP - 1);
-                        qn -= G;
-                        __syncwarp(gmask);
-                    }
+                    };
+                    if (A.weight == PCMS_WENDLAND_C2)
+                        stream(std::integral_constant<int, PCMS_WENDLAND_C2>{});
+                    else
+                        stream(std::integral_constant<int, -1>{});
+                    __syncwarp(gmask);   // the row table is rewritten by the next G rows
+                    continue;
                 }
+                // Selected pairs are compacted through the group's ring so that accumulation
+                // runs on full lanes. Lane cursors as in the dense form above.
+                auto stream = [&](auto wkc) {
+                    constexpr int WK = decltype(wkc)::value;
+                    int rcur = 0, pos = gl, pend = 0, jn = 0;
+                    CandT cn;
+                    bool vn = pos < total;
+                    if (vn) {
+                        while (rE[rcur] <= pos) ++rcur;
+                        pend = rE[rcur];
+                        jn = rA[rcur] + pos - (rcur ? rE[rcur - 1] : 0);
+                        cn.load(A, jn);
+                    }
+                    for (int p0 = 0; p0 < total; p0 += G) {
+                        const bool v = vn;
+                        const int j = jn;
+                        const CandT c = cn;
+                        pos += G;
+                        vn = pos < total;
+                        if (vn) {
+                            if (pos < pend) {
+                                jn += G;
+                            } else {   // pos >= rE[rcur]: the loop moves rcur at least once
+                                while (rE[rcur] <= pos) ++rcur;
+                                pend = rE[rcur];
+                                jn = rA[rcur] + pos - rE[rcur - 1];
+                            }
+                            cn.load(A, jn);
+                        }
+                        bool in = false;
+                        T dx[3] = {T(0), T(0), T(0)};
+                        if (v) {
+                            if constexpr (MIXED) {
+                                float ddx, ddy, ddz = 0.f;
+                                if (DIM == 2) {
+                                    ddx = (c.h0.x - thi[0]) + (c.h0.z - tlo[0]);
+                                    ddy = (c.h0.y - thi[1]) + (c.h0.w - tlo[1]);
+                                } else {
+                                    ddx = (c.h0.x - thi[0]) + (c.h0.w - tlo[0]);
+                                    ddy = (c.h0.y - thi[1]) + (c.h1.x - tlo[1]);
+                                    ddz = (c.h0.z - thi[2]) + (c.h1.y - tlo[2]);
+                                }
+                                float d2f = ddx * ddx + ddy * ddy;
+                                if (DIM == 3) d2f += ddz * ddz;
+                                int cl;
+                                if constexpr (WK == PCMS_WENDLAND_C2)   // classify32 for this kind
+                                    cl = d2f > r2f * (1.0f + MIX_BAND)
+                                             ? 0
+                                             : (d2f < r2f * (1.0f - MIX_BAND) ? 1 : -1);
+                                else
+                                    cl = classify32(A.weight, d2f, r2f);
+                                if (cl < 0) {
+                                    double te[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+                                    for (int d = 0; d < DIM; d++) te[d] = A.tx64[d * A.nt + t];
+                                    cl = select_exact(A.weight, dist2_exact<DIM>(A.sx64, A.ns, j, te),
+                                                      r, r2);
+                                }
+                                in = cl != 0;
+                                dx[0] = (T)ddx;
+                                dx[1] = (T)ddy;
+                                dx[2] = (T)ddz;
+                            } else {
+                                const double e0 = __dsub_rn(c.x[0], tx[0]);
+                                const double e1 = __dsub_rn(c.x[1], tx[1]);
+                                double d2 = __dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1));
+                                double e2 = 0.0;
+                                if (DIM == 3) {
+                                    e2 = __dsub_rn(c.x[2], tx[2]);
+                                    d2 = __dadd_rn(d2, __dmul_rn(e2, e2));
+                                }
+                                in = select64(A.weight, d2, r, r2, r2_in);
+                                dx[0] = (T)e0;
+                                dx[1] = (T)e1;
+                                dx[2] = (T)e2;
+                            }
+                        }
+                        const unsigned bal = __ballot_sync(gmask, in) & gmask;
+                        const int nin = __popc(bal);
+                        if (MODE == MODE_COUNT) {
+                            cnt += nin;
+                            continue;
+                        }
+                        if (in) {
+                            T pay;
+                            if constexpr (MODE == MODE_MAP) pay = pack_index(j, T(0));
+                            else pay = (T)c.f;
+                            const int qp = (head + qn + __popc(bal & lt)) & (QCAP - 1);
+                            q[qp] = make_entry<T>(dx[0], dx[1], dx[2], pay);
+                        }
+                        qn += nin;
+                        cnt += nin;
+                        __syncwarp(gmask);
+                        if (qn >= G) {
+                            QE e = q[(head + gl) & (QCAP - 1)];
+                            T edx[3] = {e.x, e.y, e.z};
+                            accumulate<DIM, DEG, MODE, T, NACC, WK>(acc, edx, e.w, A.weight, inv_r, bc);
+                            if constexpr (ACC == ACC_BK) {
+                                if (++pops == BK_BLOCK) {
+                                    tot.flush(acc);
+                                    pops = 0;
+                                }
+                            }
+                            if (MODE == MODE_MAP) {
+                                if (one_pass) {
+                                    if (written + gl < STG) stg[written + gl] = unpack_index(e.w);
+                                } else if (A.cols && written + gl < row_len) {
+                                    A.cols[row_off + written + gl] = unpack_index(e.w);
+                                }
+                                written += G;
+                            }
+                            head = (head + G) & (QCAP - 1);
+                            qn -= G;
+                            __syncwarp(gmask);
+                        }
+                    }
+                };
+                if (MIXED && MODE != MODE_COUNT && A.weight == PCMS_WENDLAND_C2)
+                    stream(std::integral_constant<int, PCMS_WENDLAND_C2>{});
+                else
+                    stream(std::integral_constant<int, -1>{});
                 __syncwarp(gmask);   // the row table is rewritten by the next G rows
             }
+            if constexpr (PRED) cnt = __reduce_add_sync(gmask, (unsigned)cnt);   // lanes' counts
             if (MODE != MODE_COUNT && qn > 0) {
                 if (gl < qn) {
                     QE e = q[(head + gl) & (QCAP - 1)];
@@ -905,13 +1096,38 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC, MIXED>()) k
             break;
         }
         MT red[NA];
-        if constexpr (ACC == ACC_BK) {
+        if constexpr (SMEM_TOT) {
+            // The totals are in shared memory: lane i reduces running sum i over the warp's 32
+            // lanes (TwoSum on the leading parts, plain sums of the trailing parts), starting
+            // at lane i so that the lanes' reads fall in different banks, and stores it.
+            tot.flush(acc);
+            __syncwarp();
+            if (NACC > 0 && gl < NACCP) {
+                MT* dst = (MT*)A.mom + (A.list ? wk : t) * NACCP;   // list mode: by list position
+                if (gl < NACC) {
+                    const float2* col = &tot_s[gl * 256 + (threadIdx.x & ~31)];
+                    float hi = 0.f, lo = 0.f;
+                    for (int m = 0; m < 32; m++) {
+                        const float2 v = col[(m + gl) & 31];   // a lane's total is v.x - v.y
+                        float sm, e;
+                        two_sum32(hi, v.x, sm, e);
+                        lo = (lo - v.y) + e;
+                        hi = sm;
+                    }
+                    dst[gl] = make_float2(hi, lo);
+                } else {
+                    dst[gl] = MT{};
+                }
+            }
+            __syncwarp();   // the next target clears the totals
+        } else if constexpr (ACC == ACC_BK) {
             // the lane's total is sum - cmp; reduce the pairs (hi, lo) = (sum, -cmp) with
             // TwoSum on the leading parts and plain sums of the trailing parts
-            bk_flush<NA>(acc, sum, cmp);
+            tot.flush(acc);
 #pragma unroll
             for (int i = 0; i < NA; i++) {
-                float hi = sum[i], lo = -cmp[i];
+                const float2 hl = tot.pair(i);
+                float hi = hl.x, lo = hl.y;
 #pragma unroll
                 for (int o = G / 2; o > 0; o >>= 1) {
                     const float ho = __shfl_xor_sync(gmask, hi, o);
@@ -934,7 +1150,7 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC, MIXED>()) k
             }
         }
         if (gl == 0) {
-            if (NACC > 0) {
+            if (NACC > 0 && !SMEM_TOT) {
                 MT* dst = (MT*)A.mom + (A.list ? wk : t) * NACCP;   // list mode: by list position
 #pragma unroll
                 for (int i = 0; i < NACCP; i++) {
@@ -1306,13 +1522,14 @@ __host__ __device__ __forceinline__ int solve_moments_refined(const MT* mt, cons
 
 // A tier's acceptance bound on amp for a target of n neighbours (the tier table above),
 // evaluated in FP32: the bound is a calibrated constant, not a precision-critical quantity.
-__host__ __device__ __forceinline__ float amp_bound(int acc, int n, int group) {
+// dense: tier 1 of a dense one-shot plan (blocks of BK_BLOCK_DENSE pairs).
+__host__ __device__ __forceinline__ float amp_bound(int acc, int n, int group, bool dense = false) {
     const float nf = (float)n;
     if (acc == ACC_PLAIN) {
         const float g = (float)group;
         return (float)AMP_T1 / (1.f + sqrtf(nf / (3.f * g * g)));
     }
-    return (float)AMP_BK * sqrtf(nf);
+    return (float)(dense ? AMP_BK_DENSE : AMP_BK) * sqrtf(nf);
 }
 
 // PASS: 0 = FP64 moments (one FP64 solve); for FP32 moments (the mixed tiers) 1 = the refined
@@ -1326,6 +1543,9 @@ __global__ void __launch_bounds__(128, PASS == 1 ? 3 : 1) k_solve(SolveArgs S) {
     constexpr int NACCP = round_up4(NACC);
     static_assert((PASS == 0) == std::is_same<MT, double>::value, "passes: FP32 moments only");
     const int64_t nwork = PASS == 2 ? (int64_t)(*S.n_fb) : (S.list ? (int64_t)(*S.n_list) : S.nt);
+    // tier 1 of a dense one-shot plan was assembled in blocks of BK_BLOCK_DENSE pairs
+    const bool dense =
+        DIM == 2 && MODE == MODE_FUSED && S.tier == 1 && S.acc == ACC_BK && S.group == 32;
     for (int64_t ii = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ii < nwork;
          ii += (int64_t)gridDim.x * blockDim.x) {
         const int64_t wk = PASS == 2 ? (int64_t)S.fb_list[ii] : ii;
@@ -1355,7 +1575,7 @@ __global__ void __launch_bounds__(128, PASS == 1 ? 3 : 1) k_solve(SolveArgs S) {
                 int rs = 0;
                 if (S.lambda == 0.0) {
                     rs = solve_moments_refined<DIM, DEG, MODE, MT>(
-                        src, recentred ? at : nullptr, amp_bound(S.acc, cnt, S.group), yh, yl,
+                        src, recentred ? at : nullptr, amp_bound(S.acc, cnt, S.group, dense), yh, yl,
                         &val, &amp32);
                 }
                 if (rs == 0) {   // the FP64 pass solves it
@@ -1388,7 +1608,7 @@ __global__ void __launch_bounds__(128, PASS == 1 ? 3 : 1) k_solve(SolveArgs S) {
             S.qr_list[atomicAdd(S.n_qr, 1)] = (int32_t)t;
         if (S.tier < 3 && st != PCMS_TARGET_UNDERDETERMINED) {
             bool ok = st == PCMS_TARGET_OK;
-            if (ok) ok = amp32 <= amp_bound(S.acc, cnt, S.group);
+            if (ok) ok = amp32 <= amp_bound(S.acc, cnt, S.group, dense);
             if (!ok) {
                 // tier 2 only helps if it differs from this pass: a plain tier 1, or a
                 // re-centred basis
