@@ -69,6 +69,7 @@ struct AsmPlan {
     int acc;
     double mean;   // expected neighbours per target
     double cell;   // grid cell edge
+    int xs;        // x cells per cell edge (choose_xs)
     bool tuned;
 };
 AsmPlan choose_plan(int dim, int deg, int mode, int64_t ns, double radius, const double* lo,
@@ -92,6 +93,7 @@ AsmPlan choose_plan(int dim, int deg, int mode, int64_t ns, double radius, const
     if (bk) p.G = 32;
     p.acc = bk ? ACC_BK : ACC_PLAIN;
     p.cell = radius / div;
+    p.xs = choose_xs(dim, lo, hi, p.cell, MAX_CELLS, ns);
     return p;
 }
 
@@ -451,7 +453,7 @@ MlsParams settle_growth(const MlsParams& P, const double* src, int64_t ns, const
     const bool mixed = P.prec == PCMS_MIXED;
     BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
     const AsmPlan cplan = choose_plan(dim, 0, MODE_COUNT, ns, P.radius, b.lo, b.hi, mixed);
-    Grid g = make_grid(dim, b.lo, b.hi, cplan.cell, MAX_CELLS);
+    Grid g = make_grid(dim, b.lo, b.hi, cplan.cell, MAX_CELLS, cplan.xs);
     SortedPoints S, Tp;
     sort_points(g, src, ns, true, mixed, S, s);
     sort_points(g, tgt, nt, false, mixed, Tp, s, true);
@@ -549,7 +551,7 @@ void mls_create_map(MapImpl& M, const double* src, const double* tgt, const pcms
     const int64_t ns = M.ns, nt = M.nt;
     BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
     const AsmPlan plan = choose_plan(dim, deg, MODE_MAP, ns, P.radius, b.lo, b.hi, mixed);
-    M.g = make_grid(dim, b.lo, b.hi, plan.cell, MAX_CELLS);
+    M.g = make_grid(dim, b.lo, b.hi, plan.cell, MAX_CELLS, plan.xs);
     sort_points(M.g, src, ns, true, mixed, M.src, s);
     sort_points(M.g, tgt, nt, false, mixed, M.tgt, s, true);
     const int G = plan.G;
@@ -780,7 +782,7 @@ void mls_count(const MlsParams& P0, const double* src, int64_t ns, const double*
     const bool mixed = P.prec == PCMS_MIXED;
     BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
     const AsmPlan cplan = choose_plan(dim, 0, MODE_COUNT, ns, P.radius, b.lo, b.hi, mixed);
-    Grid g = make_grid(dim, b.lo, b.hi, cplan.cell, MAX_CELLS);
+    Grid g = make_grid(dim, b.lo, b.hi, cplan.cell, MAX_CELLS, cplan.xs);
     SortedPoints S, Tp;
     sort_points(g, src, ns, true, mixed, S, s);
     sort_points(g, tgt, nt, false, mixed, Tp, s, true);
@@ -835,7 +837,7 @@ void mls_transfer(const MlsParams& P0, const double* src, int64_t ns, const doub
     *n_under = 0;
     BoxResult b = source_box(dim, src, ns, tgt, nt, o, s);
     const AsmPlan plan = choose_plan(dim, deg, MODE_FUSED, ns, P.radius, b.lo, b.hi, mixed);
-    Grid g = make_grid(dim, b.lo, b.hi, plan.cell, MAX_CELLS);
+    Grid g = make_grid(dim, b.lo, b.hi, plan.cell, MAX_CELLS, plan.xs);
     SortedPoints S, Tp;
     sort_points(g, src, ns, true, mixed, S, s);
     sort_points(g, tgt, nt, false, mixed, Tp, s, true);

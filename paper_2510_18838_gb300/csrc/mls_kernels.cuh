@@ -550,8 +550,9 @@ constexpr int asm_min_blocks() {
 
 // Candidate row rho of a target (cell (ct) and position in it (fr), cell units): the cells
 // (dz, dy) in row-major order over [z0, z0 + nz) x [y0, y0 + ny), trimmed in x to the chord of
-// the ball of radius RR (which includes the margin mg). Returns false for an empty row, else
-// the row's first cell index and its x range [x0, x1], clamped to the grid.
+// the ball of radius RR (which includes the margin mg; y and z units, g.xs x cells per unit).
+// Returns false for an empty row, else the row's first cell index and its x range [x0, x1],
+// clamped to the grid.
 template <int DIM>
 __device__ __forceinline__ bool row_chord(const Grid& g, const long long* ct, const float* fr,
                                           float RR, float mg, long long y0, long long z0,
@@ -573,7 +574,7 @@ __device__ __forceinline__ bool row_chord(const Grid& g, const long long* ct, co
     const float remz = RR * RR - ez * ez;
     const float rem = remz - ey * ey;
     if (!(remz > 0.f && rem > 0.f)) return false;
-    const float hx = sqrtf(rem) + mg;
+    const float hx = (sqrtf(rem) + mg) * (float)g.xs;
     x0 = max((long long)__float2int_rd(fr[0] - hx) + ct[0], 0LL);
     x1 = min((long long)__float2int_rd(fr[0] + hx) + ct[0], (long long)g.n[0] - 1);
     if (x0 > x1) return false;
@@ -602,8 +603,10 @@ __device__ __forceinline__ float4 estimate_basis(const AsmArgs& A, const long lo
     bool empty = false;
 #pragma unroll
     for (int d = 0; d < DIM; d++) {
-        nb[d] = (int)(((long long)A.g.n[d] + (1LL << j) - 1) >> j);
-        const float p = (float)ct[d] + fr[d];
+        // the pyramid is over h-wide cells: x positions in x cells are divided by xs
+        const long long nd = d == 0 ? A.g.ncoarse_x() : A.g.n[d];
+        nb[d] = (int)((nd + (1LL << j) - 1) >> j);
+        const float p = d == 0 ? ((float)ct[0] + fr[0]) / (float)A.g.xs : (float)ct[d] + fr[d];
         // floor(x / 2^j) of the floored cell coordinates (arithmetic shifts floor negatives)
         const int a = max(__float2int_rd(p - RR) >> j, 0);
         const int b = min(__float2int_rd(p + RR) >> j, nb[d] - 1);
@@ -665,15 +668,21 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC, MIXED, MODE
     constexpr int GPW = 32 / G;
     constexpr int QCAP = 2 * G;
     __shared__ QE qbuf[8][64];
-    __shared__ int rowa_s[8][32], rowe_s[8][32];   // per group: G rows' source start, stream end
+    // Rows are set up RB = G * RPL at a time, RPL consecutive rows per lane: for the 8-lane 3D
+    // walks (25 rows at the start radius) one batch instead of four, so the cell-start loads
+    // of all rows are in flight together.
+    constexpr int RPL = (DIM == 3 && G == 8) ? 4 : 1;
+    constexpr int RB = G * RPL;
+    __shared__ int rowa_s[8][32 * RPL], rowe_s[8][32 * RPL];   // per group: RB rows' source
+                                                                // start, stream end
 
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int gi = lane / G, gl = lane % G;
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (gi * G));
     const unsigned lt = (1u << lane) - 1u;
     QE* q = &qbuf[wib][gi * QCAP];
-    int* rA = &rowa_s[wib][gi * G];
-    int* rE = &rowe_s[wib][gi * G];
+    int* rA = &rowa_s[wib][gi * RB];
+    int* rE = &rowe_s[wib][gi * RB];
     // one-pass MAP: staged column indices, STG per group (24 KB per block)
     constexpr int STG = MODE == MODE_MAP ? (G == 32 ? 768 : 192) : 1;
     __shared__ int32_t stg_s[MODE == MODE_MAP ? 8 * GPW * STG : 1];
@@ -778,7 +787,8 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC, MIXED, MODE
 #pragma unroll
                 for (int d = 0; d < DIM; d++) {
                     const float p = (float)ct[d] + fr[d];
-                    want = want || p - RR < 0.f || p + RR > (float)g.n[d];
+                    const float rd = d == 0 ? RR * (float)g.xs : RR;
+                    want = want || p - rd < 0.f || p + rd > (float)g.n[d];
                 }
                 if (A.cpyr && !A.list) {
                     const float4 eb =
@@ -804,28 +814,43 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC, MIXED, MODE
             // group lays those ranges end to end, and the group streams the concatenated
             // candidates G per step, so steps are full across row ends. The loads of the
             // next step are issued before the current one is classified.
-            for (long long row0 = 0; row0 < nrows; row0 += G) {
-                int ra = 0, rlen = 0;
-                const long long rho = row0 + gl;
-                int64_t rowbase;
-                long long x0, x1;
-                if (rho < nrows &&
-                    row_chord<DIM>(g, ct, fr, RR, mg, y0, z0, ny, rho, rowbase, x0, x1)) {
-                    ra = A.cell_start[rowbase + x0];
-                    rlen = A.cell_start[rowbase + x1 + 1] - ra;
+            for (long long row0 = 0; row0 < nrows; row0 += RB) {
+                int64_t cs0[RPL], cs1[RPL];   // cell-start indices of each row's x range
+                bool live[RPL];
+#pragma unroll
+                for (int i = 0; i < RPL; i++) {
+                    const long long rho = row0 + gl * RPL + i;
+                    int64_t rowbase = 0;
+                    long long x0 = 0, x1 = 0;
+                    live[i] = rho < nrows &&
+                              row_chord<DIM>(g, ct, fr, RR, mg, y0, z0, ny, rho, rowbase, x0, x1);
+                    cs0[i] = rowbase + x0;
+                    cs1[i] = rowbase + x1 + 1;
                 }
-                int incl = rlen;
+                int ra[RPL], rl[RPL], lsum = 0;
+#pragma unroll
+                for (int i = 0; i < RPL; i++) {
+                    ra[i] = live[i] ? A.cell_start[cs0[i]] : 0;
+                    rl[i] = live[i] ? A.cell_start[cs1[i]] - ra[i] : 0;
+                    lsum += rl[i];
+                }
+                int incl = lsum;
 #pragma unroll
                 for (int o = 1; o < G; o <<= 1) {
                     const int v = __shfl_up_sync(gmask, incl, o, G);
                     if (gl >= o) incl += v;
                 }
                 const int total = __shfl_sync(gmask, incl, G - 1, G);
-                rA[gl] = ra;
-                rE[gl] = incl;
+                int e = incl - lsum;
+#pragma unroll
+                for (int i = 0; i < RPL; i++) {
+                    e += rl[i];
+                    rA[gl * RPL + i] = ra[i];
+                    rE[gl * RPL + i] = e;
+                }
                 __syncwarp(gmask);
                 if constexpr (PRED) {
-                    // Each lane keeps its own cursor into the G rows: its stream position
+                    // Each lane keeps its own cursor into the batch of rows: its stream position
                     // advances by G per step, and within a row the source index does too,
                     // so the row table is read only where a lane crosses into a later row.
                     // Steps are taken DU at a time while DU full steps remain (one row check,
@@ -947,7 +972,7 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC, MIXED, MODE
                         stream(std::integral_constant<int, PCMS_WENDLAND_C2>{});
                     else
                         stream(std::integral_constant<int, -1>{});
-                    __syncwarp(gmask);   // the row table is rewritten by the next G rows
+                    __syncwarp(gmask);   // the row table is rewritten by the next RB rows
                     continue;
                 }
                 // Selected pairs are compacted through the group's ring so that accumulation
@@ -1071,7 +1096,7 @@ __global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC, MIXED, MODE
                     stream(std::integral_constant<int, PCMS_WENDLAND_C2>{});
                 else
                     stream(std::integral_constant<int, -1>{});
-                __syncwarp(gmask);   // the row table is rewritten by the next G rows
+                __syncwarp(gmask);   // the row table is rewritten by the next RB rows
             }
             if constexpr (PRED) cnt = __reduce_add_sync(gmask, (unsigned)cnt);   // lanes' counts
             if (MODE != MODE_COUNT && qn > 0) {

@@ -77,18 +77,30 @@ struct DBuf {
 // ------------------------------------------------------------------------------------
 // uniform grid (Sec. 3.3 search structure)
 // ------------------------------------------------------------------------------------
+// Cells are h wide in y and z and h / xs wide in x (xs = 1, 2 or 4): finer x cells trim the
+// x-rows of a ball's cells closer to its chords at the same number of rows. The x cells
+// nest exactly in the h-wide columns: x / (h / xs) = xs * (x / h), a power-of-2 scaling.
 struct Grid {
     int dim;
-    int n[3];         // cells per axis (1 for unused axes)
+    int n[3];         // cells per axis (1 for unused axes); n[0] counts the h / xs cells
     int64_t ncell;
     double lo[3];     // origin (bounding-box minimum)
-    double h, inv_h;  // cell edge and its reciprocal
+    double h, inv_h;  // cell edge (y, z) and its reciprocal
+    int xs = 1;       // x cells per h
+
+    __host__ __device__ double inv_hd(int d) const { return d == 0 ? inv_h * xs : inv_h; }
+    __host__ __device__ int ncoarse_x() const { return (n[0] + xs - 1) / xs; }
 };
 
 // Cell edge h = r (1 + 2^-20) and cells per axis from a bounding box; h doubles until the
 // grid has at most max_cells cells. Every point within r of a target lies in a cell at
-// most 2^k cells away (per axis) from the target's cell, for radius r 2^k.
-Grid make_grid(int dim, const double* lo, const double* hi, double radius, int64_t max_cells);
+// most 2^k cells away (per axis, in units of h) from the target's cell, for radius r 2^k.
+Grid make_grid(int dim, const double* lo, const double* hi, double radius, int64_t max_cells,
+               int xs = 1);
+// The largest x subdivision in {4, 2, 1} whose grid (cell edge `cell`) has at most
+// min(max_cells, 2 ns + 64) cells, so that the cell starts stay small next to the points.
+int choose_xs(int dim, const double* lo, const double* hi, double cell, int64_t max_cells,
+              int64_t ns);
 
 // Where a point sits in the grid, in cell units: the cell coordinates (the floor, clamped
 // to +-2^30, points outside the box included) and the FP32 position inside that cell. The
@@ -99,7 +111,7 @@ __device__ __forceinline__ void point_cell(const Grid& g, int dim, const double*
     int c[3] = {0, 0, 0};
     float f[3] = {0.f, 0.f, 0.f};
     for (int d = 0; d < dim; d++) {
-        const double u = (x[d] - g.lo[d]) * g.inv_h;
+        const double u = (x[d] - g.lo[d]) * g.inv_hd(d);
         double fl = floor(u);
         fl = fmin(fmax(fl, -1073741824.0), 1073741824.0);
         c[d] = (int)fl;

@@ -40,10 +40,11 @@ __device__ __forceinline__ int qr_collect(const Grid& g, const int32_t* __restri
     if (!(R < 12.0)) return -1;
 #pragma unroll
     for (int d = 0; d < DIM; d++) {
-        const double u = (tx[d] - g.lo[d]) * g.inv_h;
+        const double u = (tx[d] - g.lo[d]) * g.inv_hd(d);
+        const double Rd = r * g.inv_hd(d);
         // one cell of margin each side covers the rounding of u and of the cells' keys
-        const double a = fmax(floor(u - R) - 1.0, 0.0);
-        const double b = fmin(floor(u + R) + 1.0, (double)(g.n[d] - 1));
+        const double a = fmax(floor(u - Rd) - 1.0, 0.0);
+        const double b = fmin(floor(u + Rd) + 1.0, (double)(g.n[d] - 1));
         c0[d] = (long long)a;
         c1[d] = (long long)b;
         if (b < a) return 0;

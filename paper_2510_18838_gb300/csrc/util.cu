@@ -68,33 +68,43 @@ int num_sms() {
     return n;
 }
 
-Grid make_grid(int dim, const double* lo, const double* hi, double radius, int64_t max_cells) {
+static double grid_cells(int dim, const double* lo, const double* hi, double h, int xs) {
+    double tot = 1.0;
+    for (int d = 0; d < dim; d++)
+        tot *= std::floor((hi[d] - lo[d]) / h * (d == 0 ? xs : 1)) + 1.0;
+    return tot;
+}
+
+Grid make_grid(int dim, const double* lo, const double* hi, double radius, int64_t max_cells,
+               int xs) {
     Grid g;
     g.dim = dim;
+    g.xs = dim >= 2 ? xs : 1;
     double h = radius * (1.0 + std::ldexp(1.0, -20));
     for (int d = 0; d < 3; d++) {
         g.lo[d] = d < dim ? lo[d] : 0.0;
         g.n[d] = 1;
     }
-    for (;;) {
-        double tot = 1.0;
-        for (int d = 0; d < dim; d++) {
-            double ext = hi[d] - lo[d];
-            double nd = std::floor(ext / h) + 1.0;
-            tot *= nd;
-        }
-        if (tot <= (double)max_cells) break;
-        h *= 2.0;
-    }
+    while (grid_cells(dim, lo, hi, h, g.xs) > (double)max_cells) h *= 2.0;
     int64_t ncell = 1;
     for (int d = 0; d < dim; d++) {
-        g.n[d] = (int)(std::floor((hi[d] - lo[d]) / h) + 1.0);
+        g.n[d] = (int)(std::floor((hi[d] - lo[d]) / h * (d == 0 ? g.xs : 1)) + 1.0);
         ncell *= g.n[d];
     }
     g.ncell = ncell;
     g.h = h;
     g.inv_h = 1.0 / h;
     return g;
+}
+
+int choose_xs(int dim, const double* lo, const double* hi, double cell, int64_t max_cells,
+              int64_t ns) {
+    if (dim < 2) return 1;
+    const double h = cell * (1.0 + std::ldexp(1.0, -20));
+    const double cap = (double)std::min<int64_t>(max_cells, 2 * ns + 64);
+    for (int xs = 4; xs > 1; xs >>= 1)
+        if (grid_cells(dim, lo, hi, h, xs) <= cap) return xs;
+    return 1;
 }
 
 // ------------------------------------------------------------------------------------
@@ -410,7 +420,7 @@ __global__ void k_cell_keys(Grid g, const double* __restrict__ pts, int64_t n,
                             uint32_t* __restrict__ key, uint32_t* __restrict__ idx) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        int c = cell_of(pts[i], g.lo[0], g.inv_h, g.n[0]);
+        int c = cell_of(pts[i], g.lo[0], g.inv_hd(0), g.n[0]);
         if (g.dim >= 2) c += g.n[0] * cell_of(pts[n + i], g.lo[1], g.inv_h, g.n[1]);
         if (g.dim == 3)
             c += g.n[0] * g.n[1] * cell_of(pts[2 * n + i], g.lo[2], g.inv_h, g.n[2]);
@@ -519,15 +529,19 @@ __global__ void k_gather_sorted(int dim, Grid g, const double* __restrict__ pts,
     }
 }
 
-// one warp per cell: lanes take the cell's sources in strides of 32, then a fixed
-// butterfly reduction
-__global__ void k_cell_sums(int dim, int64_t ncell, const int32_t* __restrict__ start,
+// one warp per h-wide cell (xs adjacent x cells of the grid, contiguous in the sorted
+// order): lanes take the cell's sources in strides of 32, then a fixed butterfly reduction
+__global__ void k_cell_sums(int dim, int64_t ncell, int nx, int xs, const int32_t* __restrict__ start,
                             const float4* __restrict__ hl0, float4* __restrict__ out) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int ncx = (nx + xs - 1) / xs;
     for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < ncell;
          c += nwarps) {
-        const int a = start[c], b = start[c + 1];
+        const int64_t row = c / ncx;
+        const int cx = (int)(c - row * ncx);
+        const int64_t base = row * nx;
+        const int a = start[base + (int64_t)cx * xs], b = start[base + min((cx + 1) * xs, nx)];
         float sx = 0.f, sy = 0.f, sz = 0.f;
         for (int i = a + lane; i < b; i += 32) {
             const float4 h = hl0[i];
@@ -566,8 +580,9 @@ __global__ void k_pyr_up(int dim, int64_t nx, int64_t ny, int64_t nz, int64_t mx
     }
 }
 
+// The pyramid is built over h-wide cells (xs x cells merged).
 int pyramid_levels(const Grid& g) {
-    int64_t m = std::max<int64_t>(g.n[0], std::max<int64_t>(g.n[1], g.n[2]));
+    int64_t m = std::max<int64_t>(g.ncoarse_x(), std::max<int64_t>(g.n[1], g.n[2]));
     int L = 1;
     while (L < PYR_MAX && m > 1) {
         m = (m + 1) / 2;
@@ -577,7 +592,7 @@ int pyramid_levels(const Grid& g) {
 }
 
 int64_t pyramid_size(const Grid& g, int levels, int64_t* off) {
-    int64_t n[3] = {g.n[0], g.n[1], g.n[2]}, tot = 0;
+    int64_t n[3] = {g.ncoarse_x(), g.n[1], g.n[2]}, tot = 0;
     for (int j = 0; j < levels; j++) {
         if (off) off[j] = tot;
         tot += n[0] * n[1] * n[2];
@@ -590,10 +605,11 @@ void cell_pyramid(const Grid& g, const SortedPoints& S, int levels, const int64_
                   float4* out, cudaStream_t s) {
     if (g.ncell <= 0) return;
     PCMS_TRACE("grid_cell_pyramid", s);
-    const int64_t blocks = std::min<int64_t>((g.ncell + 7) / 8, (int64_t)num_sms() * 16);
+    const int64_t ncoarse = g.ncell / g.n[0] * g.ncoarse_x();
+    const int64_t blocks = std::min<int64_t>((ncoarse + 7) / 8, (int64_t)num_sms() * 16);
     k_cell_sums<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(
-        g.dim, g.ncell, S.cell_start.as<int32_t>(), S.hl0.as<float4>(), out);
-    int64_t n[3] = {g.n[0], g.n[1], g.n[2]};
+        g.dim, ncoarse, g.n[0], g.xs, S.cell_start.as<int32_t>(), S.hl0.as<float4>(), out);
+    int64_t n[3] = {g.ncoarse_x(), g.n[1], g.n[2]};
     for (int j = 1; j < levels; j++) {
         int64_t m[3] = {n[0], n[1], n[2]};
         for (int d = 0; d < g.dim; d++) m[d] = (n[d] + 1) / 2;
