@@ -73,6 +73,18 @@ def mls_pair_flops(dim, deg, fused_fields):
     return (2 * dim - 1) + 2 + 6 + dim + (2 * nm - 1) + fused_fields * (2 * m + 1)
 
 
+def entry_pair_flops(dim, deg, fused_fields):
+    """FP32 flops per selected pair of the plain normal-equation formulation, the
+    algorithmic work the roofline entries are quoted on: the distance filter over the
+    candidates a uniform grid of cell edge r yields (2.9 per selected pair in 2D, 6.4 in 3D,
+    about 6 flops each), the weight (about 10), the basis (m - 1 products), the m(m+1)/2
+    distinct entries of w a a^T (a multiply-add each) and, in one-shot mode, the right-hand
+    side w b a (m multiply-adds per field)."""
+    m = mono_count(dim, deg)
+    cand = 2.9 if dim == 2 else 6.4
+    return cand * 6 + 10 + (m - 1) + m * (m + 1) + fused_fields * 2 * m
+
+
 def spmm_bytes(nnz, ns, nt, nf, elem=4):
     """HBM bytes one apply must move at least: column + value per nonzero, each source's
     field row once, each target's output row once."""
@@ -275,7 +287,7 @@ class TransferWorkload:
         clk = peaks.get("sm_max_mhz", 2070.0)
         fp32 = 152 * 128 * 2 * clk * 1e6 / 1e12      # FFMA lanes x 2 flops
         fp64 = 152 * 2 * 2 * clk * 1e6 / 1e12        # DFMA lanes x 2 flops
-        f2, f3 = mls_pair_flops(2, 2, 1), mls_pair_flops(3, 2, 0)
+        f2, f3 = entry_pair_flops(2, 2, 1), entry_pair_flops(3, 2, 0)
         flops = {   # kernel: (units in the traced step, flops per unit, peak TFLOP/s, peak name)
             "mls_assemble_fused_mixed": (self.pairs3, f2, fp32, "FP32"),
             "mls_assemble_fused_bk": (self.pairs3, f2, fp32, "FP32"),
@@ -292,7 +304,10 @@ class TransferWorkload:
                  "unit": "TFLOP/s",
                  "peak_source": f"derived: 152 SM x {128 if pk == 'FP32' else 2} {pk} FMA lanes "
                                 f"x 2 flops x {clk:.0f} MHz ({kind} max SM clock)",
-                 "work": f"{units} selected pairs x {per} flops"}
+                 "work": f"{units} selected pairs x {per:.1f} flops (normal-equation "
+                         f"entries, weight and candidate filter per selected pair)",
+                 "achieved_moment_form": units * (mls_pair_flops(2, 2, 1) if per == f2 else
+                                                  mls_pair_flops(3, 2, 0)) / (ms / 1e3) / 1e12}
         elif name == "apply_spmm":
             by = spmm_bytes(self.nnz4, c4.src.shape[1], c4.tgt.shape[1], 16) * launches
             r = {"bound": "hbm", "achieved": by / (ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
@@ -451,7 +466,7 @@ class ServeWorkload:
             for deg in (0, 1, 2):
                 n = cnt.get(f"mls_map_pairs_d{dim}k{deg}", 0)
                 pairs += n
-                flops += n * mls_pair_flops(dim, deg, 0)
+                flops += n * entry_pair_flops(dim, deg, 0)
         name = "mls_assemble_map_mixed"
         if name in ker and flops:
             clk = measured_peaks()[0].get("sm_max_mhz", 2070.0)
@@ -462,6 +477,7 @@ class ServeWorkload:
                 "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak,
                 "work": f"{pairs} selected pairs of operator assemblies x FP32 flops per pair "
+                        f"of the normal-equation entries, weight and candidate filter "
                         f"(dimension and degree of each request)"}
         return out
 
