@@ -188,6 +188,40 @@ def test_mixed_multifield_apply_3d(P):
         np.testing.assert_allclose(part[:, ok], out[:nf, ok], rtol=1e-6, atol=1e-6)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_mixed_map_rows_longer_than_the_stage(P, dim):
+    """Sparse sources plus one dense cluster: the mean neighbour count picks 8 lanes per
+    target, while the targets at the cluster see thousands of sources, more than a group
+    stages during its walk (192 columns). Their rows are reserved after the walk and walked
+    a second time. Lists bit-exact, statuses equal, values within the mixed tolerance, and
+    the second walk must have run."""
+    rng = np.random.default_rng(730 + dim)
+    n_bg, n_cl, r = (20000, 2500, 0.02) if dim == 2 else (30000, 3000, 0.07)
+    bg = W.uniform_points(n_bg, dim, 731 + dim)
+    cl = 0.5 + 0.02 * (rng.random((dim, n_cl)) - 0.5)   # a cube of side 0.02 at the centre
+    src = np.ascontiguousarray(np.concatenate([bg, cl], axis=1))
+    tgt = np.ascontiguousarray(np.concatenate(
+        [W.uniform_points(1500, dim, 733 + dim), 0.5 + 0.06 * (rng.random((dim, 300)) - 0.5)],
+        axis=1))
+    f = np.sin(2 * np.pi * src[0]) * np.cos(2 * np.pi * src[1])
+    P.trace_enable(True, count_only=True)
+    m = P.create_map(cu(src), cu(tgt), 2, r, precision="mixed")
+    out = host(m.apply(cu(f.astype(np.float32))))
+    P.trace_enable(False)
+    walked_again = P.trace_read().get("count:mls_map_rows_walked_again", (0, 0.0))[0]
+    off, cols, _, st, _ = (host(x) for x in m.export())
+    o = oracle.mls(src, tgt, f, 2, r, shape=True)
+    assert walked_again > 0
+    assert np.diff(off).max() > 192
+    assert np.array_equal(st, o["status"])
+    for a, b in zip(rows_as_sets(off, cols), rows_as_sets(o["offsets"], o["cols"])):
+        assert np.array_equal(a, b)
+    ok = o["status"] == 0
+    assert ok.mean() > 0.95
+    assert normwise_err(out, o["values"], ok) <= TOL_MIXED
+    m.destroy()
+
+
 @pytest.mark.parametrize("dim,nf", [(3, 16), (3, 5), (2, 1), (2, 13)])
 def test_tensor_core_apply_matches_the_oracle_and_the_fp32_apply(P, dim, nf):
     """pcms_apply_map_bf16 (BF16 three-term splits on mma.sync, FP32 accumulation) against the
