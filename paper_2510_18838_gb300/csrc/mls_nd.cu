@@ -260,6 +260,10 @@ struct NdArgs {
     int32_t* cols;
     const double* field;  // FUSED: sorted field
     double* mom;          // [nt][NACCP]
+    double* wvals;        // MAP: each row's weights w_j beside its columns (in the
+                          // operator-value buffer, which k_shape_nd overwrites with the rows):
+                          // written by the column walk when it assembles the moments, else by
+                          // the first pass of k_moments_nd
 };
 
 // Calls f(j, d2) for every source j selected at radius level k of target t (coordinates tt),
@@ -274,7 +278,14 @@ struct NdArgs {
 // sum e_f^2 < (r + sqrt(D) eta)^2 (Minkowski) and d2f <= (1 + D 2^-23)(r + sqrt(D) eta)^2.
 // band is that bound relative to r^2, and r2 (1 + band) is rounded up by a further 2^-20.
 // The screen is off (band > 1/4) when the FP32 offsets are too coarse for the radius.
-template <int D, typename F>
+//
+// The same bound read the other way accepts without the FP64 test: a candidate with
+// d2f < r^2 (1 - 2 band) (1 - 2^-20) lies within r (1 - 2^-21), so its FP64 squared distance
+// is below r^2 (1 - 2^-40) and it is selected for every weight that is positive on the whole
+// support (all but TPS and cubic, which keep the exact test). With NEED_D2 the callback gets
+// the FP64 squared distance of every selected pair; without it, d2 is passed only where the
+// exact test computed it (0 otherwise).
+template <int D, bool NEED_D2 = true, typename F>
 __device__ __forceinline__ void walk_nd(const NdArgs& A, const double* tt, int k, F&& f) {
     const GridN& g = A.g;
     const double r = A.lv.r[k], r2 = A.lv.r2[k];
@@ -287,7 +298,7 @@ __device__ __forceinline__ void walk_nd(const NdArgs& A, const double* tt, int k
         tf[d] = (float)(tt[d] - g.lo[d]);
         tmax = fmaxf(tmax, fabsf(tf[d]));
     }
-    float r2hi = INFINITY;
+    float r2hi = INFINITY, r2lo = -1.f;
     if (A.sxf) {
         const float rf = A.lv.r2f[k] > 0.f ? sqrtf(A.lv.r2f[k]) : 0.f;
         const float ds = 5.9604645e-08f * A.src_extent * (1.f + 1e-6f);
@@ -295,27 +306,63 @@ __device__ __forceinline__ void walk_nd(const NdArgs& A, const double* tt, int k
         const float eta = (ds + dt) * (1.f + 5.9604645e-08f) + 5.9604645e-08f * rf;
         const float grow = 1.f + sqrtf((float)D) * eta / rf;
         const float band = (1.f + (float)D * 1.1920929e-07f) * grow * grow - 1.f;
-        if (rf > 0.f && band < 0.25f) r2hi = A.lv.r2f[k] * (1.f + band) * (1.f + 9.5367432e-07f);
+        if (rf > 0.f && band < 0.25f) {
+            r2hi = A.lv.r2f[k] * (1.f + band) * (1.f + 9.5367432e-07f);
+            if (A.weight != PCMS_TPS && A.weight != PCMS_CUBIC)
+                r2lo = A.lv.r2f[k] * (1.f - 2.f * band) * (1.f - 9.5367432e-07f);
+        }
     }
-    int lo_c[D], hi_c[D], idx[D];
+    // The box's rows of cells (contiguous in x) are walked in order. A row whose cells lie
+    // farther than r from the target in the other D - 1 coordinates is skipped, and the x
+    // range of the others is trimmed to the ball's chord at the row's nearest point. Both
+    // are computed in cell units in FP32 with a margin mg far above the FP32 error (the
+    // positions inside the cell are exact to 2^-24, the cells' own coordinates are exact
+    // integers), so they only ever over-cover: every source within r keeps its candidacy.
+    int lo_c[D], hi_c[D], idx[D], cc[D];
+    float fr[D];
 #pragma unroll
     for (int d = 0; d < D; d++) {
-        double fl = floor((tt[d] - g.lo[d]) * g.inv_h);
+        const double p = (tt[d] - g.lo[d]) * g.inv_h;
+        double fl = floor(p);
         fl = fmin(fmax(fl, -1073741824.0), 1073741824.0);
         const long long c = (long long)fl;
+        cc[d] = (int)c;
+        fr[d] = (float)(p - fl);
         lo_c[d] = (int)max(c - R, 0LL);
         hi_c[d] = (int)min(c + R, (long long)g.n[d] - 1);
         if (lo_c[d] > hi_c[d]) return;   // the box misses the grid
         idx[d] = lo_c[d];
     }
+    const float R0 = A.lv.rcell[k];
+    const float mg = 1e-3f + R0 * 1e-6f;
+    const float RR = R0 + mg;
     for (;;) {
-        int64_t base = 0, stride = g.n[0];
+        // the row's squared distance from the target over the coordinates d >= 1, less mg each
+        float rem = RR * RR;
 #pragma unroll
         for (int d = 1; d < D; d++) {
-            base += stride * idx[d];
-            stride *= g.n[d];
+            const float dd = (float)(idx[d] - cc[d]);
+            float e = fmaxf(fmaxf(dd - fr[d], fr[d] - dd - 1.f), 0.f);
+            e = fmaxf(e - mg, 0.f);
+            rem -= e * e;
         }
-        const int a = A.cell_start[base + lo_c[0]], b = A.cell_start[base + hi_c[0] + 1];
+        int x0 = 1, x1 = 0;   // empty unless the row reaches into the ball
+        if (rem > 0.f) {
+            const float hx = sqrtf(rem) + mg;
+            x0 = (int)max((long long)__float2int_rd(fr[0] - hx) + cc[0], (long long)lo_c[0]);
+            x1 = (int)min((long long)__float2int_rd(fr[0] + hx) + cc[0], (long long)hi_c[0]);
+        }
+        int a = 0, b = 0;
+        if (x0 <= x1) {
+            int64_t base = 0, stride = g.n[0];
+#pragma unroll
+            for (int d = 1; d < D; d++) {
+                base += stride * idx[d];
+                stride *= g.n[d];
+            }
+            a = A.cell_start[base + x0];
+            b = A.cell_start[base + x1 + 1];
+        }
         for (int j = a; j < b; j++) {
             if (A.sxf) {
                 float d2f = 0.f;
@@ -325,6 +372,10 @@ __device__ __forceinline__ void walk_nd(const NdArgs& A, const double* tt, int k
                     d2f = fmaf(e, e, d2f);
                 }
                 if (d2f > r2hi) continue;
+                if (!NEED_D2 && d2f < r2lo) {
+                    f(j, 0.0);
+                    continue;
+                }
             }
             double e = __dsub_rn(A.sx64[j], tt[0]);
             double d2 = __dmul_rn(e, e);
@@ -364,7 +415,7 @@ __global__ void __launch_bounds__(ND_THREADS) k_count_nd(NdArgs A, const int32_t
         int cnt = 0;
         for (;;) {
             cnt = 0;
-            walk_nd<D>(A, tt, k, [&](int, double) { ++cnt; });
+            walk_nd<D, false>(A, tt, k, [&](int, double) { ++cnt; });
             if (A.need > 0 && cnt < A.need && k < MAX_DOUBLINGS && cnt < A.ns) {
                 ++k;
                 continue;
@@ -434,15 +485,19 @@ __global__ void __launch_bounds__(ND_THREADS) k_assemble_nd(NdArgs A) {
         for (int i = 0; i < NACC; i++) acc[i] = 0.0;
         int64_t w_at = MODE == MODE_MAP ? A.offsets[t] : 0;
         const int64_t w_end = MODE == MODE_MAP ? w_at + A.counts[t] : 0;
-        walk_nd<D>(A, tt, k, [&](int j, double d2) {
+        walk_nd<D, MOMENTS>(A, tt, k, [&](int j, double d2) {
+            double w = 0.0;
             if constexpr (MOMENTS) {
+                w = weight_value<double>(A.weight, sqrt(d2) * inv_r);
                 double u[D];
 #pragma unroll
                 for (int d = 0; d < D; d++) u[d] = (A.sx64[d * A.ns + j] - tt[d]) * inv_r;
-                const double w = weight_value<double>(A.weight, sqrt(d2) * inv_r);
                 accumulate_nd<D, DEG, MODE, NACC>(acc, u, w, MODE == MODE_FUSED ? A.field[j] : 0.0);
             }
-            if (MODE == MODE_MAP && w_at < w_end) A.cols[w_at++] = j;
+            if (MODE == MODE_MAP && w_at < w_end) {
+                if (MOMENTS && A.wvals) A.wvals[w_at] = w;   // else k_moments_nd writes it
+                A.cols[w_at++] = j;
+            }
         });
         if constexpr (MOMENTS) {
             double* dst = A.mom + t * NACCP;
@@ -494,9 +549,14 @@ constexpr SplitTab<D> make_split_tab() {
 constexpr int ND_PASS = 64;   // moments accumulated per pass over a row
 
 // Moments of a quadratic basis from the operator's row: the 126 (5D) accumulators do not fit
-// one thread's registers, so the row is read in passes of ND_PASS moments. Per pair and pass:
-// squared distance, weight and offsets, the degree <= 2 monomials a2 of u, then for each
-// moment one FMA, (w a2[alpha]) a2[beta], with w a2[alpha] formed once per alpha group.
+// one thread's registers, so the row is read in passes of ND_PASS moments. A warp per target:
+// its lanes take the row's pairs 32 apart (rows of uneven length then cost a warp only their
+// own length, where a thread per target made each warp wait for its longest row), and the
+// lanes' partial sums are added by a butterfly of shuffles at the end of each pass (5 adds
+// per moment, against one multiply-add per moment and pair). Per pair and pass: the offsets,
+// the weight (computed in the first pass and kept in the operator-value buffer, where the
+// rows find it), the degree <= 2 monomials a2 of u, then for each moment one FMA,
+// (w a2[alpha]) a2[beta], with w a2[alpha] formed once per alpha group.
 template <int D>
 __global__ void __launch_bounds__(ND_THREADS) k_moments_nd(NdArgs A) {
     constexpr int NM = mono_count(D, 4);
@@ -504,8 +564,10 @@ __global__ void __launch_bounds__(ND_THREADS) k_moments_nd(NdArgs A) {
     constexpr int NACCP = round_up4(NM);
     constexpr int NPASS = (NM + ND_PASS - 1) / ND_PASS;
     constexpr SplitTab<D> tab = make_split_tab<D>();
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < A.nt;
-         t += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < A.nt;
+         t += nwarps) {
         double tt[D];
         load_target_nd<D>(A, t, tt);
         const int k = A.kexp[t];
@@ -518,19 +580,30 @@ __global__ void __launch_bounds__(ND_THREADS) k_moments_nd(NdArgs A) {
             double acc[nq];
 #pragma unroll
             for (int q = 0; q < nq; q++) acc[q] = 0.0;
-            for (int64_t i = a; i < b; i++) {
+            for (int64_t i = a + lane; i < b; i += 32) {
                 const int j = A.cols[i];
                 double u[D];
-                double e = __dsub_rn(A.sx64[j], tt[0]);
-                double d2 = __dmul_rn(e, e);
-                u[0] = e * inv_r;
+                double w;
+                if constexpr (decltype(PI)::value == 0) {
+                    // the first pass forms the weight from the squared distance as the walk's
+                    // exact test does, and keeps it for the later passes and the rows (the
+                    // same lane reads it back)
+                    double e = __dsub_rn(A.sx64[j], tt[0]);
+                    double d2 = __dmul_rn(e, e);
+                    u[0] = e * inv_r;
 #pragma unroll
-                for (int d = 1; d < D; d++) {
-                    e = __dsub_rn(A.sx64[d * A.ns + j], tt[d]);
-                    d2 = __dadd_rn(d2, __dmul_rn(e, e));
-                    u[d] = e * inv_r;
+                    for (int d = 1; d < D; d++) {
+                        e = __dsub_rn(A.sx64[d * A.ns + j], tt[d]);
+                        d2 = __dadd_rn(d2, __dmul_rn(e, e));
+                        u[d] = e * inv_r;
+                    }
+                    w = weight_value<double>(A.weight, sqrt(d2) * inv_r);
+                    A.wvals[i] = w;
+                } else {
+                    w = A.wvals[i];
+#pragma unroll
+                    for (int d = 0; d < D; d++) u[d] = __dsub_rn(A.sx64[d * A.ns + j], tt[d]) * inv_r;
                 }
-                const double w = weight_value<double>(A.weight, sqrt(d2) * inv_r);
                 double a2[M2];
                 a2[0] = 1.0;
                 sfor<M2 - 1>([&](auto I) {
@@ -551,12 +624,14 @@ __global__ void __launch_bounds__(ND_THREADS) k_moments_nd(NdArgs A) {
                 });
             }
             sfor<nq>([&](auto Q) {
+                double v = acc[decltype(Q)::value];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                 constexpr int p = tab.order[q0 + decltype(Q)::value];
-                dst[p] = acc[decltype(Q)::value];
+                if (lane == (decltype(Q)::value & 31)) dst[p] = v;
             });
         });
-#pragma unroll
-        for (int i = NM; i < NACCP; i++) dst[i] = 0.0;
+        if (lane < NACCP - NM) dst[NM + lane] = 0.0;
     }
 }
 
@@ -603,13 +678,16 @@ __global__ void __launch_bounds__(ND_THREADS) k_solve_nd(NdSolveArgs S) {
     }
 }
 
-// operator rows N_j = w_j a(u_j)^T y
+// operator rows N_j = w_j a(u_j)^T y, with w_j as the column walk wrote it into vals (the
+// same buffer); a warp per target, its lanes over the row's pairs 32 apart
 template <int D, int DEG>
 __global__ void __launch_bounds__(ND_THREADS) k_shape_nd(NdArgs A, const double* __restrict__ yv,
                                                          double* __restrict__ vals) {
     constexpr int M = mono_count(D, DEG);
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < A.nt;
-         t += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < A.nt;
+         t += nwarps) {
         double tt[D], y[M];
         load_target_nd<D>(A, t, tt);
 #pragma unroll
@@ -617,19 +695,12 @@ __global__ void __launch_bounds__(ND_THREADS) k_shape_nd(NdArgs A, const double*
         const int k = A.kexp[t];
         const double inv_r = A.lv.inv_r[k];
         const int64_t a = A.offsets[t], b = a + A.counts[t];
-        for (int64_t i = a; i < b; i++) {
+        for (int64_t i = a + lane; i < b; i += 32) {
             const int j = A.cols[i];
+            const double w = vals[i];
             double u[D];
-            double e = __dsub_rn(A.sx64[j], tt[0]);
-            double d2 = __dmul_rn(e, e);
-            u[0] = e * inv_r;
 #pragma unroll
-            for (int d = 1; d < D; d++) {
-                e = __dsub_rn(A.sx64[d * A.ns + j], tt[d]);
-                d2 = __dadd_rn(d2, __dmul_rn(e, e));
-                u[d] = e * inv_r;
-            }
-            const double w = weight_value<double>(A.weight, sqrt(d2) * inv_r);
+            for (int d = 0; d < D; d++) u[d] = __dsub_rn(A.sx64[d * A.ns + j], tt[d]) * inv_r;
             double am[M];
             am[0] = 1.0;
             double s = y[0];
@@ -778,6 +849,7 @@ void create_map_nd(MapImpl& M, const double* src, const double* tgt) {
         a.offsets = M.offsets.as<int64_t>();
         a.cols = M.cols.as<int32_t>();
         a.mom = mom.as<double>();
+        a.wvals = M.vals.as<double>();   // the rows' weights until k_shape_nd replaces them
         if constexpr (DEG == 2) {   // columns first, then the moments in passes over the rows
             {
                 PCMS_TRACE("nd_assemble_map", s);
@@ -785,7 +857,7 @@ void create_map_nd(MapImpl& M, const double* src, const double* tgt) {
             }
             {
                 PCMS_TRACE("nd_moments", s);
-                k_moments_nd<D><<<nd_blocks(nt), ND_THREADS, 0, s>>>(a);
+                k_moments_nd<D><<<nd_blocks(32 * nt), ND_THREADS, 0, s>>>(a);   // warp per target
             }
         } else {
             PCMS_TRACE("nd_assemble_map", s);
@@ -806,7 +878,8 @@ void create_map_nd(MapImpl& M, const double* src, const double* tgt) {
         PCMS_LAUNCH_CHECK("nd_solve");
         {
             PCMS_TRACE("nd_shape", s);
-            k_shape_nd<D, DEG><<<nd_blocks(nt), ND_THREADS, 0, s>>>(a, y.as<double>(), M.vals.as<double>());
+            k_shape_nd<D, DEG><<<nd_blocks(32 * nt), ND_THREADS, 0, s>>>(a, y.as<double>(),
+                                                                     M.vals.as<double>());
         }
         PCMS_LAUNCH_CHECK("nd_shape");
         DBuf st(sizeof(unsigned long long) * 5, s);
