@@ -263,7 +263,7 @@ struct NdArgs {
     double* wvals;        // MAP: each row's weights w_j beside its columns (in the
                           // operator-value buffer, which k_shape_nd overwrites with the rows):
                           // written by the column walk when it assembles the moments, else by
-                          // the first pass of k_moments_nd
+                          // k_moments_nd
 };
 
 // Calls f(j, d2) for every source j selected at radius level k of target t (coordinates tt),
@@ -336,6 +336,10 @@ __device__ __forceinline__ void walk_nd(const NdArgs& A, const double* tt, int k
     const float R0 = A.lv.rcell[k];
     const float mg = 1e-3f + R0 * 1e-6f;
     const float RR = R0 + mg;
+    int64_t stride_c[D];   // cells per step of coordinate d in the linear cell index
+    stride_c[0] = 1;
+#pragma unroll
+    for (int d = 1; d < D; d++) stride_c[d] = stride_c[d - 1] * g.n[d - 1];
     for (;;) {
         // the row's squared distance from the target over the coordinates d >= 1, less mg each
         float rem = RR * RR;
@@ -354,12 +358,9 @@ __device__ __forceinline__ void walk_nd(const NdArgs& A, const double* tt, int k
         }
         int a = 0, b = 0;
         if (x0 <= x1) {
-            int64_t base = 0, stride = g.n[0];
+            int64_t base = 0;
 #pragma unroll
-            for (int d = 1; d < D; d++) {
-                base += stride * idx[d];
-                stride *= g.n[d];
-            }
+            for (int d = 1; d < D; d++) base += stride_c[d] * idx[d];
             a = A.cell_start[base + x0];
             b = A.cell_start[base + x1 + 1];
         }
@@ -388,13 +389,21 @@ __device__ __forceinline__ void walk_nd(const NdArgs& A, const double* tt, int k
             }
             if (select64(A.weight, d2, r, r2, r2_in)) f(j, d2);
         }
-        int d = 1;
-        while (d < D) {
-            if (++idx[d] <= hi_c[d]) break;
-            idx[d] = lo_c[d];
-            ++d;
+        // next row: an odometer over d = 1 .. D-1 with compile-time indices, so that the
+        // indices stay in registers
+        bool carry = true;
+#pragma unroll
+        for (int d = 1; d < D; d++) {
+            if (carry) {
+                if (idx[d] < hi_c[d]) {
+                    ++idx[d];
+                    carry = false;
+                } else {
+                    idx[d] = lo_c[d];
+                }
+            }
         }
-        if (d >= D) break;
+        if (carry) break;
     }
 }
 
@@ -546,25 +555,42 @@ constexpr SplitTab<D> make_split_tab() {
     return t;
 }
 
-constexpr int ND_PASS = 64;   // moments accumulated per pass over a row
+constexpr int ND_REG = 64;   // moments accumulated in registers; the rest in shared memory
 
-// Moments of a quadratic basis from the operator's row: the 126 (5D) accumulators do not fit
-// one thread's registers, so the row is read in passes of ND_PASS moments. A warp per target:
-// its lanes take the row's pairs 32 apart (rows of uneven length then cost a warp only their
-// own length, where a thread per target made each warp wait for its longest row), and the
-// lanes' partial sums are added by a butterfly of shuffles at the end of each pass (5 adds
-// per moment, against one multiply-add per moment and pair). Per pair and pass: the offsets,
-// the weight (computed in the first pass and kept in the operator-value buffer, where the
-// rows find it), the degree <= 2 monomials a2 of u, then for each moment one FMA,
-// (w a2[alpha]) a2[beta], with w a2[alpha] formed once per alpha group.
+// Shared-memory accumulators of k_moments_nd per block: the moments past ND_REG, one double
+// per moment and lane ([moment][lane]: a warp's loads and stores hit distinct banks).
+template <int D>
+constexpr int nd_smem_moments() {
+    return mono_count(D, 4) > ND_REG ? mono_count(D, 4) - ND_REG : 0;
+}
+template <int D>
+constexpr size_t nd_moments_smem_bytes() {
+    return sizeof(double) * (size_t)nd_smem_moments<D>() * ND_THREADS;
+}
+
+// Moments of a quadratic basis from the operator's row, in one pass over it. The 126 (5D)
+// accumulators do not fit one thread's registers: ND_REG of them are registers, the others
+// live in shared memory, one slot per lane (a load, a multiply-add and a store per pair).
+// The shared-memory traffic runs beside the FP64 pipe, the bound, which then carries each
+// pair's offsets, weight and monomials once. A warp per target: its lanes take the row's
+// pairs 32 apart (rows of uneven length cost a warp only their own length, where a thread per
+// target made each warp wait for its longest row), and the lanes' partial sums are added by a
+// butterfly of shuffles at the end (5 adds per moment, against one multiply-add per moment
+// and pair). Per pair: the offsets and the squared distance as the walk's exact test forms
+// them, the weight (kept in the operator-value buffer, where the rows find it), the degree
+// <= 2 monomials a2 of u, then for each moment one FMA, (w a2[alpha]) a2[beta], with
+// w a2[alpha] formed once per alpha group.
 template <int D>
 __global__ void __launch_bounds__(ND_THREADS) k_moments_nd(NdArgs A) {
     constexpr int NM = mono_count(D, 4);
     constexpr int M2 = mono_count(D, 2);
     constexpr int NACCP = round_up4(NM);
-    constexpr int NPASS = (NM + ND_PASS - 1) / ND_PASS;
+    constexpr int NR = NM < ND_REG ? NM : ND_REG;
+    constexpr int NS = nd_smem_moments<D>();
     constexpr SplitTab<D> tab = make_split_tab<D>();
+    extern __shared__ double nd_sacc[];
     const int lane = threadIdx.x & 31;
+    volatile double* sacc = nd_sacc + (threadIdx.x >> 5) * 32 * NS + lane;   // [NS][32]
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < A.nt;
          t += nwarps) {
@@ -574,62 +600,53 @@ __global__ void __launch_bounds__(ND_THREADS) k_moments_nd(NdArgs A) {
         const double inv_r = A.lv.inv_r[k];
         const int64_t a = A.offsets[t], b = a + A.counts[t];
         double* dst = A.mom + t * NACCP;
-        sfor<NPASS>([&](auto PI) {
-            constexpr int q0 = decltype(PI)::value * ND_PASS;
-            constexpr int nq = NM - q0 < ND_PASS ? NM - q0 : ND_PASS;
-            double acc[nq];
+        double acc[NR];
 #pragma unroll
-            for (int q = 0; q < nq; q++) acc[q] = 0.0;
-            for (int64_t i = a + lane; i < b; i += 32) {
-                const int j = A.cols[i];
-                double u[D];
-                double w;
-                if constexpr (decltype(PI)::value == 0) {
-                    // the first pass forms the weight from the squared distance as the walk's
-                    // exact test does, and keeps it for the later passes and the rows (the
-                    // same lane reads it back)
-                    double e = __dsub_rn(A.sx64[j], tt[0]);
-                    double d2 = __dmul_rn(e, e);
-                    u[0] = e * inv_r;
+        for (int q = 0; q < NR; q++) acc[q] = 0.0;
 #pragma unroll
-                    for (int d = 1; d < D; d++) {
-                        e = __dsub_rn(A.sx64[d * A.ns + j], tt[d]);
-                        d2 = __dadd_rn(d2, __dmul_rn(e, e));
-                        u[d] = e * inv_r;
-                    }
-                    w = weight_value<double>(A.weight, sqrt(d2) * inv_r);
-                    A.wvals[i] = w;
-                } else {
-                    w = A.wvals[i];
+        for (int q = 0; q < NS; q++) sacc[32 * q] = 0.0;
+        for (int64_t i = a + lane; i < b; i += 32) {
+            const int j = A.cols[i];
+            double u[D];
+            double e = __dsub_rn(A.sx64[j], tt[0]);
+            double d2 = __dmul_rn(e, e);
+            u[0] = e * inv_r;
 #pragma unroll
-                    for (int d = 0; d < D; d++) u[d] = __dsub_rn(A.sx64[d * A.ns + j], tt[d]) * inv_r;
-                }
-                double a2[M2];
-                a2[0] = 1.0;
-                sfor<M2 - 1>([&](auto I) {
-                    constexpr int p = decltype(I)::value + 1;
-                    constexpr int par = mono_parent_nd<D>(p);
-                    constexpr int v = mono_var_nd<D>(p);
-                    a2[p] = a2[par] * u[v];
-                });
-                double wa = 0.0;
-                sfor<nq>([&](auto Q) {
-                    constexpr int q = q0 + decltype(Q)::value;
-                    constexpr int p = tab.order[q];
-                    constexpr int al = tab.alpha[p];
-                    constexpr int be = tab.beta[p];
-                    constexpr bool fresh = decltype(Q)::value == 0 || tab.alpha[tab.order[q - 1]] != al;
-                    if constexpr (fresh) wa = w * a2[al];
-                    acc[decltype(Q)::value] = fma(wa, a2[be], acc[decltype(Q)::value]);
-                });
+            for (int d = 1; d < D; d++) {
+                e = __dsub_rn(A.sx64[d * A.ns + j], tt[d]);
+                d2 = __dadd_rn(d2, __dmul_rn(e, e));
+                u[d] = e * inv_r;
             }
-            sfor<nq>([&](auto Q) {
-                double v = acc[decltype(Q)::value];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                constexpr int p = tab.order[q0 + decltype(Q)::value];
-                if (lane == (decltype(Q)::value & 31)) dst[p] = v;
+            const double w = weight_value<double>(A.weight, sqrt(d2) * inv_r);
+            A.wvals[i] = w;
+            double a2[M2];
+            a2[0] = 1.0;
+            sfor<M2 - 1>([&](auto I) {
+                constexpr int p = decltype(I)::value + 1;
+                constexpr int par = mono_parent_nd<D>(p);
+                constexpr int v = mono_var_nd<D>(p);
+                a2[p] = a2[par] * u[v];
             });
+            double wa = 0.0;
+            sfor<NM>([&](auto Q) {
+                constexpr int q = decltype(Q)::value;
+                constexpr int p = tab.order[q];
+                constexpr int al = tab.alpha[p];
+                constexpr int be = tab.beta[p];
+                constexpr bool fresh = q == 0 || tab.alpha[tab.order[q - 1]] != al;
+                if constexpr (fresh) wa = w * a2[al];
+                if constexpr (q < NR) acc[q] = fma(wa, a2[be], acc[q]);
+                else sacc[32 * (q - NR)] = fma(wa, a2[be], sacc[32 * (q - NR)]);
+            });
+        }
+        sfor<NM>([&](auto Q) {
+            constexpr int q = decltype(Q)::value;
+            double v;
+            if constexpr (q < NR) v = acc[q];
+            else v = sacc[32 * (q - NR)];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == (q & 31)) dst[tab.order[q]] = v;
         });
         if (lane < NACCP - NM) dst[NM + lane] = 0.0;
     }
@@ -857,7 +874,12 @@ void create_map_nd(MapImpl& M, const double* src, const double* tgt) {
             }
             {
                 PCMS_TRACE("nd_moments", s);
-                k_moments_nd<D><<<nd_blocks(32 * nt), ND_THREADS, 0, s>>>(a);   // warp per target
+                constexpr size_t smem = nd_moments_smem_bytes<D>();
+                if (smem > 48 * 1024)
+                    PCMS_CU(cudaFuncSetAttribute(k_moments_nd<D>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem));
+                k_moments_nd<D><<<nd_blocks(32 * nt), ND_THREADS, smem, s>>>(a);   // warp per target
             }
         } else {
             PCMS_TRACE("nd_assemble_map", s);
