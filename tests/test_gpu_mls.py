@@ -492,6 +492,49 @@ def test_nd_map_matches_oracle(P, dim, deg, min_nb):
     m.destroy()
 
 
+@pytest.mark.parametrize("weight", ["wendland_c2", "tps"])
+def test_nd_selection_exact_at_the_radius(P, weight):
+    """5D: sources exactly at distance r (dyadic offsets along an axis and along
+    (1, 2, 2, 4, 0)/32, |.| = 5/32 = r) are excluded; one ulp inside, and inside by 2^-21
+    and 2^-19 of r (around the FP32 screen's accept bound), are included; among uniform
+    background sources. Both walks (counts and columns) against the oracle's brute force."""
+    r = 5.0 / 32
+    g = np.array([0.25, 0.75])
+    tgt = np.stack(np.meshgrid(*([g] * 5), indexing="ij")).reshape(5, -1)   # 32 dyadic targets
+    offs = []
+    for d in range(5):
+        for sgn in (1.0, -1.0):
+            e = np.zeros(5)
+            e[d] = sgn * r
+            offs.append(e)                                   # exactly at r
+    offs.append(np.array([1.0, 2.0, 2.0, 4.0, 0.0]) / 32)    # exactly at r, off the axes
+    src = [tgt + o[:, None] for o in offs]
+    for d, f in [(0, None), (3, None), (1, 1 - 2.0 ** -21), (4, 1 - 2.0 ** -19)]:
+        p = tgt.copy()
+        if f is None:                                        # one ulp inside
+            p[d] = np.nextafter(tgt[d] + r, tgt[d])
+        else:
+            p[d] = tgt[d] - r * f
+        src.append(p)
+    src.append(W.uniform_points(3000, 5, 991))
+    src = np.ascontiguousarray(np.concatenate(src, axis=1))
+    m = P.create_map(cu(src), cu(tgt), 0, r, weight=weight)
+    off, cols, *_ = (host(x) for x in m.export())
+    o_off, o_cols, _ = oracle.neighbors(src, tgt, r, weight=weight, degree=0)
+    for a, b in zip(rows_as_sets(off, cols), rows_as_sets(o_off, o_cols)):
+        assert np.array_equal(a, b)
+    nt = tgt.shape[1]
+    exact = set(range(11 * nt))                              # the sources at exactly r
+    assert not exact.intersection(np.asarray(cols).tolist())
+    inside = [set(range((11 + k) * nt, (12 + k) * nt)) for k in range(4)]
+    got = set(np.asarray(cols).tolist())
+    if weight == "wendland_c2":
+        assert all(s <= got for s in inside)
+    c = P.count_neighbors(cu(src), cu(tgt), r, degree=0, weight=weight)
+    assert np.array_equal(host(c), np.diff(o_off))
+    m.destroy()
+
+
 @pytest.mark.parametrize("dim,weight,lam", [(4, "wendland_c2", 0.0), (5, "c4", 0.0),
                                             (5, "gaussian", 1e-3), (4, "imq", 0.0)])
 def test_nd_one_shot_transfer(P, dim, weight, lam):
