@@ -419,15 +419,11 @@ __host__ __device__ __forceinline__ void accumulate(T (&acc)[NACC > 0 ? NACC : 1
         acc[p] += wm[p];
     });
     if constexpr (MODE == MODE_FUSED) {
-        T wb[M];
-        wb[0] = w * b;
-        acc[NM] += wb[0];
-        sfor<M - 1>([&](auto I) {
-            constexpr int p = decltype(I)::value + 1;
-            constexpr int par = mono_parent(DIM, p);
-            constexpr int v = mono_var(DIM, p);
-            wb[p] = wb[par] * u[v];
-            acc[NM + p] += wb[p];
+        // the basis monomials come first in the graded order, so w u^p of degree <= k is
+        // already among the moment terms: one multiply-add per right-hand-side entry
+        sfor<M>([&](auto I) {
+            constexpr int p = decltype(I)::value;
+            acc[NM + p] += wm[p] * b;
         });
     }
 }
