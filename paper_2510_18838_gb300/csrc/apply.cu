@@ -230,7 +230,10 @@ __global__ void __launch_bounds__(256) k_spmm_vec(int64_t nt, const int64_t* __r
 // them; steps are unrolled four times, so four field-row gathers per lane are in flight.
 // 32 registers: eight blocks (64 warps) per SM. (Loading the next row's (col, val) pairs
 // behind the current row's gathers took 48 registers and measured slower: 3.0 against 2.5
-// ms on the 8M 3D operator with 16 fields.)
+// ms on the 8M 3D operator with 16 fields. So did staging each row's pairs in shared memory
+// by cp.async two rows ahead, the row offsets a row before that: 40 registers, 48 warps per
+// SM, 3.3 ms. The field-row gathers and the warps in flight decide the time, not the chain
+// of loads that leads to them.)
 // At the row's end the lanes holding the same vector position are summed (xor shuffles
 // over the 32 / NV nonzero slots) and lanes 0 .. NV-1 store the row. One warp per row,
 // rows in chunks from the counter as k_spmm_vec.
