@@ -163,13 +163,12 @@ def kernel_launches(trace):
 NCU_TRAFFIC = {
     "mls_assemble_fused_bk": (
         107.3e6, 8.0, "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_assemble<2, 2, "
-        "mixed, fused, 32, float, blocked> on the 500k -> 500k case (43.1 + 64.1 MB; "
-        "profiles/k_assemble_2d_quadratic_fused_bk_transfer_small.md) x 8 for the 4M -> 4M "
+        "mixed, fused, 32, float, blocked> on the 500k -> 500k case (43.1 + 64.1 MB) "
+        "x 8 for the 4M -> 4M "
         "launch (sources and targets scale by 8)"),
     "mls_assemble_map_mixed": (
         459.9e6, 8.0, "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_assemble_map8<3, 2> "
-        "on the 1M -> 1M case (129.9 + 330.0 MB; "
-        "profiles/k_assemble_map8_3d_quadratic_transfer_small.md) x 8 for the 8M -> 8M launch "
+        "on the 1M -> 1M case (129.9 + 330.0 MB) x 8 for the 8M -> 8M launch "
         "(sources, targets and the operator's columns scale by 8)"),
 }
 
