@@ -172,6 +172,29 @@ def test_mixed_values(P, dim, deg):
     assert normwise_err(out2, o["values"], ok) <= TOL_MIXED
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("weight", ["gaussian", "c4", "const", "noop", "mq", "imq", "tps",
+                                    "cubic"])
+def test_mixed_map_every_weight(P, dim, weight):
+    """Mixed operators with every weight of Table 1 besides Wendland C2 (the walk with the
+    weight kind read at run time), 8 lanes per target: lists bit-exact, statuses equal,
+    values within the mixed tolerance."""
+    ns, nt, r = (6000, 800, 0.05) if dim == 2 else (20000, 600, 0.09)
+    src, tgt = _case(dim, ns, nt, 610 + 10 * dim)
+    f = np.sin(5 * src[0]) + src[1]
+    m = P.create_map(cu(src), cu(tgt), 1, r, precision="mixed", weight=weight)
+    out = host(m.apply(cu(f.astype(np.float32))))
+    off, cols, _, st, _ = (host(x) for x in m.export())
+    o = oracle.mls(src, tgt, f, 1, r, weight=weight, shape=True)
+    assert np.array_equal(st, o["status"])
+    for a, b in zip(rows_as_sets(off, cols), rows_as_sets(o["offsets"], o["cols"])):
+        assert np.array_equal(a, b)
+    ok = o["status"] == 0
+    assert ok.mean() > 0.9
+    assert normwise_err(out, o["values"], ok) <= TOL_MIXED
+    m.destroy()
+
+
 def test_mixed_multifield_apply_3d(P):
     src = W.slab_points(60000, seed=401)
     tgt = W.uniform_points(3000, 3, 402)
