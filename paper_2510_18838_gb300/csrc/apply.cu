@@ -233,7 +233,8 @@ __global__ void __launch_bounds__(256) k_spmm_vec(int64_t nt, const int64_t* __r
 // ms on the 8M 3D operator with 16 fields. So did staging each row's pairs in shared memory
 // by cp.async two rows ahead, the row offsets a row before that: 40 registers, 48 warps per
 // SM, 3.3 ms. The field-row gathers and the warps in flight decide the time, not the chain
-// of loads that leads to them.)
+// of loads that leads to them. Handing each SM its own contiguous range of row chunks, so
+// that its blocks share neighbouring sources in L1, measured 3.1 ms.)
 // At the row's end the lanes holding the same vector position are summed (xor shuffles
 // over the 32 / NV nonzero slots) and lanes 0 .. NV-1 store the row. One warp per row,
 // rows in chunks from the counter as k_spmm_vec.
