@@ -42,7 +42,8 @@ def _case(dim, ns, nt, seed, outside=0.0):
 
 # ------------------------------------------------------------------ neighbour lists
 @pytest.mark.parametrize("dim,prec,min_nb", [(2, "fp64", 0), (2, "mixed", 0), (3, "fp64", 0),
-                                              (3, "mixed", 0), (2, "mixed", 12), (3, "fp64", 15)])
+                                              (3, "mixed", 0), (2, "mixed", 12), (3, "fp64", 15),
+                                              (3, "mixed", 15)])
 def test_neighbor_lists_bit_exact(P, dim, prec, min_nb):
     ns, nt, r = (6000, 1700, 0.03) if dim == 2 else (20000, 1300, 0.06)
     src, tgt = _case(dim, ns, nt, 100 + dim, outside=0.05)
