@@ -1691,8 +1691,11 @@ __global__ void __launch_bounds__(128, PASS == 1 ? 3 : 1) k_solve(SolveArgs S) {
 // ------------------------------------------------------------------------------------
 // k_shape: N_j = w_j a(u_j)^T y
 // ------------------------------------------------------------------------------------
+// Rows applied as evaluated of degree <= 1 run three blocks per SM (80 registers, a few dozen
+// bytes of spills for degree 1; 2D linear, 16 fields: 0.217 -> 0.164 ms per 1M targets); the
+// quadratic forms keep two (at 80 registers their spills cost more than the warps gain).
 template <int DIM, int DEG, bool MIXED, int G, bool APPLY = false>
-__global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
+__global__ void __launch_bounds__(256, (APPLY && DEG <= 1) ? 3 : 1) k_shape(ShapeArgs S) {
     static_assert(DEG <= 2, "operator rows: exact double-FP32 monomials need degree <= 2");
     static_assert(!APPLY || MIXED, "fused rows and apply: mixed maps");
     using T = typename std::conditional<MIXED, float, double>::type;
@@ -1711,20 +1714,22 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
         if constexpr (MIXED) load_hilo<DIM>(S.thl0, S.thl1, t, thi, tlo);
         // y as T, and for mixed maps also as an unevaluated FP32 pair (y = yh + yl to ~2^-48)
         T y[M];
-        float yl[M];
+        float yl[M];   // rows applied as evaluated read the trailing parts where they need them
 #pragma unroll
         for (int k = 0; k < M; k++) {
             if constexpr (MIXED) {
                 const float2 v = S.yf[t * M + k];
                 y[k] = v.x;
-                yl[k] = v.y;
+                yl[k] = APPLY ? 0.f : v.y;
             } else {
                 y[k] = S.y[t * M + k];
                 yl[k] = 0.f;
             }
         }
         const int flag = S.flags ? S.flags[t] : 0;
-        if (!MIXED || flag == 2) {
+        // FP64 target coordinates: FP64 paths, and the FP64-assembled rows (flag 2) of mixed
+        // maps, which rows applied as evaluated leave to k_rows64_apply
+        if (!MIXED || (!APPLY && flag == 2)) {
 #pragma unroll
             for (int d = 0; d < DIM; d++) tx[d] = S.tx64[d * S.nt + t];
         }
@@ -1881,7 +1886,8 @@ __global__ void __launch_bounds__(256) k_shape(ShapeArgs S) {
 #pragma unroll
                     for (int k = 0; k < M; k++) {
                         const float ph = __fmul_rn(ah[k], y[k]);
-                        const float pl = __fmaf_rn(ah[k], y[k], -ph) + (ah[k] * yl[k] + al[k] * y[k]);
+                        const float ylk = APPLY ? S.yf[t * M + k].y : yl[k];
+                        const float pl = __fmaf_rn(ah[k], y[k], -ph) + (ah[k] * ylk + al[k] * y[k]);
                         float s2, e2;
                         two_sum32(sh, ph, s2, e2);
                         sl = (sl + pl) + e2;
