@@ -1691,11 +1691,12 @@ __global__ void __launch_bounds__(128, PASS == 1 ? 3 : 1) k_solve(SolveArgs S) {
 // ------------------------------------------------------------------------------------
 // k_shape: N_j = w_j a(u_j)^T y
 // ------------------------------------------------------------------------------------
-// Rows applied as evaluated of degree <= 1 run three blocks per SM (80 registers, a few dozen
-// bytes of spills for degree 1; 2D linear, 16 fields: 0.217 -> 0.164 ms per 1M targets); the
-// quadratic forms keep two (at 80 registers their spills cost more than the warps gain).
+// Three blocks per SM (80 registers) for the stored mixed rows (3D quadratic: 20 bytes of
+// spills, 3.9 -> 3.3 ms on the 8M operator) and for rows applied as evaluated of degree <= 1
+// (2D linear, 16 fields: 0.217 -> 0.164 ms per 1M targets); quadratic rows applied as
+// evaluated keep two (at 80 registers their spills cost more than the warps gain).
 template <int DIM, int DEG, bool MIXED, int G, bool APPLY = false>
-__global__ void __launch_bounds__(256, (APPLY && DEG <= 1) ? 3 : 1) k_shape(ShapeArgs S) {
+__global__ void __launch_bounds__(256, (APPLY && DEG <= 1) || (!APPLY && MIXED) ? 3 : 1) k_shape(ShapeArgs S) {
     static_assert(DEG <= 2, "operator rows: exact double-FP32 monomials need degree <= 2");
     static_assert(!APPLY || MIXED, "fused rows and apply: mixed maps");
     using T = typename std::conditional<MIXED, float, double>::type;
