@@ -83,8 +83,7 @@ inline void shape_apply_any(int dim, int deg, int G, const ShapeArgs& a, int blo
             else if (MIXED && acc == ACC_BK)                                                  \
                 k_assemble<DIMV, DEG, MIXED, MODE_MAP, 8, float, MIXED ? ACC_BK : ACC_PLAIN><<<b, 256, 0, s>>>(a); \
             else if (G == 32) k_assemble<DIMV, DEG, MIXED, MODE_MAP, 32, float><<<b, 256, 0, s>>>(a); \
-            else if constexpr (MIXED) k_assemble_map8<DIMV, DEG><<<b, 256, 0, s>>>(a);         \
-            else k_assemble<DIMV, DEG, MIXED, MODE_MAP, 8, float><<<b, 256, 0, s>>>(a);       \
+            else launch_map8<DIMV, DEG, MIXED>(a, b, s);                                       \
         } else {                                                                              \
             if (fd) {                                                                         \
                 if constexpr (!MIXED) {                                                       \

@@ -1,6 +1,6 @@
-// mls_map8.cuh -- the operator walk of small neighbourhoods on the mixed path with the four
-// 8-lane groups of a warp stepping together (Sec. 3.2.1, Eq. 1: the moments of G and the
-// columns of the operator rows).
+// mls_map8.cuh -- the operator walk of small neighbourhoods (mixed path, FP64 path and the
+// mixed path's FP64 tier) with the four 8-lane groups of a warp stepping together (Sec.
+// 3.2.1, Eq. 1: the moments of G and the columns of the operator rows).
 //
 // k_assemble with G = 8 lets each group run its own walk: a group pops its compaction ring
 // (and runs the moment update, the costly part of a selected pair) as soon as it holds 8
@@ -13,8 +13,12 @@
 //
 // Pairs reach the lanes exactly as in k_assemble (ring entry i of a target to lane i mod 8,
 // in stream order), so the per-lane sums, the moments and the columns are the same bit for
-// bit; only the schedule of the pops differs. Plain FP32 sums, MODE_MAP, one pass or a
-// given row (the second walk of rows that did not fit the stage), optional target list.
+// bit; only the schedule of the pops differs. Plain sums (FP32 on the mixed path, FP64
+// otherwise, where a warp's FP64 instructions take the narrow FP64 pipe whatever their
+// active lanes, so the divergent pops cost even more), MODE_MAP, one pass or a given row (the
+// second walk of rows that did not fit the stage), optional target list and, for the FP64
+// form, the list's re-centred bases. Measured on 1M -> 1M operators, FP64: 3D quadratic
+// 22.5 -> 16.4 ms, 3D linear 9.1 -> 7.2 ms.
 #pragma once
 
 #include "mls_kernels.cuh"
@@ -30,17 +34,21 @@ struct Map8 {
     static constexpr int RPL = DIM == 3 ? 4 : 1;   // rows set up per lane and batch
 };
 
-// Shared memory of one block (one copy for both weight instantiations of the body)
-template <int DIM>
+// Shared memory of one block (one copy for both weight instantiations of the body). Ring
+// entries are (offsets, payload) as float4 (mixed) or double4 (FP64).
+template <int DIM, bool MIXED>
 struct Map8Smem {
-    float4 q[8][Map8::GPW * Map8::QCAP];
+    using QE = typename QEntry<typename std::conditional<MIXED, float, double>::type>::type;
+    QE q[8][Map8::GPW * Map8::QCAP];
     int rowa[8][Map8::GPW * Map8::G * Map8::RPL<DIM>];
     int rowe[8][Map8::GPW * Map8::G * Map8::RPL<DIM>];
     int32_t stg[8 * Map8::GPW * Map8::STG];
 };
 
-template <int DIM, int DEG, int WK>
-__device__ __forceinline__ void map8_body(const AsmArgs& A, Map8Smem<DIM>& S) {
+template <int DIM, int DEG, bool MIXED, int WK>
+__device__ __forceinline__ void map8_body(const AsmArgs& A, Map8Smem<DIM, MIXED>& S) {
+    using T = typename std::conditional<MIXED, float, double>::type;
+    using QE = typename Map8Smem<DIM, MIXED>::QE;
     constexpr int G = Map8::G, GPW = Map8::GPW, QCAP = Map8::QCAP, STG = Map8::STG;
     constexpr int NM = mono_count(DIM, 2 * DEG);
     constexpr int NACCP = round_up4(NM);
@@ -52,7 +60,7 @@ __device__ __forceinline__ void map8_body(const AsmArgs& A, Map8Smem<DIM>& S) {
     const int gi = lane >> 3, gl = lane & 7;
     const unsigned gmask = 0xffu << (gi * G);
     const unsigned lt = (1u << lane) - 1u;
-    float4* q = &S.q[wib][gi * QCAP];
+    QE* q = &S.q[wib][gi * QCAP];
     int* rA = &S.rowa[wib][gi * RB];
     int* rE = &S.rowe[wib][gi * RB];
     int32_t* stg = &S.stg[(wib * GPW + gi) * STG];
@@ -69,9 +77,24 @@ __device__ __forceinline__ void map8_body(const AsmArgs& A, Map8Smem<DIM>& S) {
         long long ct[3] = {0, 0, 0};
         float fr[3] = {0.f, 0.f, 0.f};
         float thi[3] = {0.f, 0.f, 0.f}, tlo[3] = {0.f, 0.f, 0.f};
+        double tx[3] = {0.0, 0.0, 0.0};   // FP64 walk: the target's coordinates
+        T bcv[4] = {T(0), T(0), T(0), T(1)};
+        bool recentred = false;           // FP64 list mode: a re-centred basis per entry
         int k = 0;
         int64_t row_off = 0, row_len = 0;
         if (act) {
+            if constexpr (!MIXED) {
+#pragma unroll
+                for (int d = 0; d < DIM; d++) tx[d] = A.tx64[d * A.nt + t];
+                if (A.basis) {
+                    const float4 bb = A.basis[wk];
+                    bcv[0] = bb.x;
+                    bcv[1] = bb.y;
+                    bcv[2] = bb.z;
+                    bcv[3] = bb.w;
+                    recentred = true;
+                }
+            }
             const int4 c4 = A.tcell[t];
             const float4 f4 = A.tfrac[t];
             ct[0] = c4.x;
@@ -80,7 +103,7 @@ __device__ __forceinline__ void map8_body(const AsmArgs& A, Map8Smem<DIM>& S) {
             fr[0] = f4.x;
             fr[1] = f4.y;
             fr[2] = f4.z;
-            load_hilo<DIM>(A.thl0, A.thl1, t, thi, tlo);
+            if constexpr (MIXED) load_hilo<DIM>(A.thl0, A.thl1, t, thi, tlo);
             k = A.kexp_in ? A.kexp_in[t] : 0;
             if (!one_pass && A.cols) {   // the first walk fixed the row
                 row_off = A.offsets[t];
@@ -89,8 +112,9 @@ __device__ __forceinline__ void map8_body(const AsmArgs& A, Map8Smem<DIM>& S) {
         }
         const double r = A.lv.r[k];
         const double r2 = A.lv.r2[k];
+        const double r2_in = r2 * (1.0 - 9.094947017729282e-13);
         const float r2f = A.lv.r2f[k];
-        const float inv_r = A.lv.inv_rf[k];
+        const T inv_r = MIXED ? (T)A.lv.inv_rf[k] : (T)A.lv.inv_r[k];
         const float R0 = A.lv.rcell[k];
         const float mg = 1e-3f + R0 * 1e-6f;
         const float RR = R0 + mg;
@@ -106,19 +130,19 @@ __device__ __forceinline__ void map8_body(const AsmArgs& A, Map8Smem<DIM>& S) {
         long long nrows = ny * (DIM == 3 ? (z1 >= z0 ? z1 - z0 + 1 : 0) : 1);
         if (!act) nrows = 0;
 
-        float acc[NM];
+        T acc[NM];
 #pragma unroll
-        for (int i = 0; i < NM; i++) acc[i] = 0.f;
+        for (int i = 0; i < NM; i++) acc[i] = T(0);
         int qn = 0, head = 0, cnt = 0;
         int64_t written = 0;
 
         // pops G ring entries into the lanes' sums and the row's columns
         auto pop = [&](int n) {
             if (gl < n) {
-                const float4 e = q[(head + gl) & (QCAP - 1)];
-                const float edx[3] = {e.x, e.y, e.z};
-                accumulate<DIM, DEG, MODE_MAP, float, NM, WK>(acc, edx, e.w, A.weight, inv_r,
-                                                              nullptr);
+                const QE e = q[(head + gl) & (QCAP - 1)];
+                const T edx[3] = {e.x, e.y, e.z};
+                accumulate<DIM, DEG, MODE_MAP, T, NM, WK>(acc, edx, e.w, A.weight, inv_r,
+                                                          recentred ? bcv : nullptr);
                 const int32_t j = unpack_index(e.w);
                 if (one_pass) {
                     if (written + gl < STG) stg[written + gl] = j;
@@ -171,21 +195,18 @@ __device__ __forceinline__ void map8_body(const AsmArgs& A, Map8Smem<DIM>& S) {
             const int tmax = __reduce_max_sync(FULL, total);
 
             int rcur = 0, pos = gl, pend = 0, jn = 0;
-            float4 h0n = make_float4(0.f, 0.f, 0.f, 0.f);
-            float2 h1n = make_float2(0.f, 0.f);
+            Cand<MIXED, DIM, float, false> cn{};
             bool vn = pos < total;
             if (vn) {
                 while (rE[rcur] <= pos) ++rcur;
                 pend = rE[rcur];
                 jn = rA[rcur] + pos - (rcur ? rE[rcur - 1] : 0);
-                h0n = A.hl0[jn];
-                if (DIM == 3) h1n = A.hl1[jn];
+                cn.load(A, jn);
             }
             for (int p0 = 0; p0 < tmax; p0 += G) {
                 const bool v = vn;
                 const int j = jn;
-                const float4 h0 = h0n;
-                const float2 h1 = h1n;
+                const Cand<MIXED, DIM, float, false> c = cn;
                 pos += G;
                 vn = pos < total;
                 if (vn) {
@@ -196,12 +217,27 @@ __device__ __forceinline__ void map8_body(const AsmArgs& A, Map8Smem<DIM>& S) {
                         pend = rE[rcur];
                         jn = rA[rcur] + pos - rE[rcur - 1];
                     }
-                    h0n = A.hl0[jn];
-                    if (DIM == 3) h1n = A.hl1[jn];
+                    cn.load(A, jn);
                 }
                 bool in = false;
-                float ddx = 0.f, ddy = 0.f, ddz = 0.f;
-                if (v) {
+                T ddx = T(0), ddy = T(0), ddz = T(0);
+                if (!MIXED && v) {   // FP64 walk: the definition's squared distance
+                    const double e0 = __dsub_rn(c.x[0], tx[0]);
+                    const double e1 = __dsub_rn(c.x[1], tx[1]);
+                    double d2 = __dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1));
+                    double e2 = 0.0;
+                    if (DIM == 3) {
+                        e2 = __dsub_rn(c.x[2], tx[2]);
+                        d2 = __dadd_rn(d2, __dmul_rn(e2, e2));
+                    }
+                    in = select64(A.weight, d2, r, r2, r2_in);
+                    ddx = (T)e0;
+                    ddy = (T)e1;
+                    ddz = (T)e2;
+                }
+                if (MIXED && v) {
+                    const float4 h0 = c.h0;
+                    const float2 h1 = c.h1;
                     if (DIM == 2) {
                         ddx = (h0.x - thi[0]) + (h0.z - tlo[0]);
                         ddy = (h0.y - thi[1]) + (h0.w - tlo[1]);
@@ -231,7 +267,7 @@ __device__ __forceinline__ void map8_body(const AsmArgs& A, Map8Smem<DIM>& S) {
                 const int nin = __popc(gb);
                 if (in) {
                     const int qp = (head + qn + __popc(gb & lt)) & (QCAP - 1);
-                    q[qp] = make_float4(ddx, ddy, ddz, pack_index(j, 0.f));
+                    q[qp] = make_entry<T>(ddx, ddy, ddz, pack_index(j, T(0)));
                 }
                 qn += nin;
                 cnt += nin;
@@ -260,9 +296,9 @@ __device__ __forceinline__ void map8_body(const AsmArgs& A, Map8Smem<DIM>& S) {
             for (int o = G / 2; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(FULL, acc[i], o);
         }
         if (act && gl == 0) {
-            float* dst = (float*)A.mom + (A.list ? wk : t) * NACCP;
+            T* dst = (T*)A.mom + (A.list ? wk : t) * NACCP;
 #pragma unroll
-            for (int i = 0; i < NACCP; i++) dst[i] = i < NM ? acc[i < NM ? i : 0] : 0.f;
+            for (int i = 0; i < NACCP; i++) dst[i] = i < NM ? acc[i < NM ? i : 0] : T(0);
             A.counts[t] = cnt;
             if (A.kexp_out) A.kexp_out[t] = k;
             if (!one_pass && A.cols && cnt != row_len) atomicOr(A.err, 1u);
@@ -284,12 +320,24 @@ __device__ __forceinline__ void map8_body(const AsmArgs& A, Map8Smem<DIM>& S) {
     }
 }
 
-template <int DIM, int DEG>
-__global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC_PLAIN, true, MODE_MAP, 8>())
+// The block's Map8Smem is dynamic shared memory (the FP64 form's 32-byte ring entries take it
+// past the 48 KB of static shared memory).
+template <int DIM, int DEG, bool MIXED>
+__global__ void __launch_bounds__(256, asm_min_blocks<DIM, DEG, ACC_PLAIN, MIXED, MODE_MAP, 8>())
     k_assemble_map8(AsmArgs A) {
-    __shared__ Map8Smem<DIM> S;
-    if (A.weight == PCMS_WENDLAND_C2) map8_body<DIM, DEG, PCMS_WENDLAND_C2>(A, S);
-    else map8_body<DIM, DEG, -1>(A, S);
+    extern __shared__ __align__(32) unsigned char map8_smem[];
+    Map8Smem<DIM, MIXED>& S = *reinterpret_cast<Map8Smem<DIM, MIXED>*>(map8_smem);
+    if (A.weight == PCMS_WENDLAND_C2) map8_body<DIM, DEG, MIXED, PCMS_WENDLAND_C2>(A, S);
+    else map8_body<DIM, DEG, MIXED, -1>(A, S);
+}
+
+template <int DIM, int DEG, bool MIXED>
+void launch_map8(const AsmArgs& a, int blocks, cudaStream_t s) {
+    constexpr size_t smem = sizeof(Map8Smem<DIM, MIXED>);
+    if (smem > 48 * 1024)
+        PCMS_CU(cudaFuncSetAttribute(k_assemble_map8<DIM, DEG, MIXED>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_assemble_map8<DIM, DEG, MIXED><<<blocks, 256, smem, s>>>(a);
 }
 
 }  // namespace pcms
