@@ -843,6 +843,44 @@ def run_reference(args, rank, world):
                 "d2h_bytes_per_step": 0}}), flush=True)
 
 
+def transfer_and_studies(torch, pcms, W, dev, args, rank, stream, flush):
+    """The single-stream transfer pass (per-kernel breakdown, roofline entry, apply leg) and,
+    for the full serving line, the configuration legs and the studies."""
+    tw = TransferWorkload(torch, pcms, W, dev, small=args.workload == "transfer_small")
+    for _ in range(2):
+        tw.step()
+    torch.cuda.synchronize()
+    pcms.trace_enable(True)
+    flush_l2(flush)
+    _, tms = timed(torch, tw.step, stream)
+    pcms.trace_enable(False)
+    ttrace = pcms.trace_read()
+    tw.step(timed_parts=True)
+    transfer = {"workload": tw.name, "ms": tms, "points": tw.points_per_step,
+                "points_per_s": tw.points_per_step / (tms / 1e3), "parts_ms": tw.parts,
+                "kernels_ms": {k: round(v[1], 3) for k, v in sorted(
+                    kernel_launches(ttrace).items(), key=lambda kv: -kv[1][1])[:14]},
+                "tiers": {k[6:]: v[0] for k, v in ttrace.items() if k.startswith("count:")},
+                "work": {"mls2d_pairs": tw.pairs3, "mls3d_nnz": tw.nnz4}}
+    peaks, kind = measured_peaks()
+    roof = tw.roofline(ttrace, peaks, kind)
+    apply_forms = apply_leg(torch, pcms, tw, peaks, kind, flush)
+    configs = None
+    if args.workload == "serve" and rank == 0:
+        import oracle
+        oracle.build()
+        configs = {"mls2d_fp64_10k": config1_leg(torch, pcms, W, oracle),
+                   "mesh_512": config2_leg(torch, pcms, W, oracle),
+                   "neighbour_counts": tw.hist}
+        if not args.no_cpu_baseline:
+            configs["cpu_oracle_per_config"] = tw.per_config_cpu(oracle)
+    study = roundtrip_study(torch, W) if args.workload == "serve" and rank == 0 else None
+    study5 = mls5d_study(torch, pcms, W) if args.workload == "serve" and rank == 0 else None
+    studyp = projection_study(torch, pcms, W) if args.workload == "serve" and rank == 0 else None
+
+    return transfer, roof, apply_forms, configs, study, study5, studyp, tw
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -850,7 +888,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="serve",
-                    choices=["serve", "transfer", "transfer_small", "mls5d"])
+                    choices=["serve", "serve_only", "transfer", "transfer_small", "mls5d"],
+                    help="serve: the full line; serve_only: the serving steps alone (no transfer "
+                         "pass, studies or extra legs; a profiling helper)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the plan rules (no tuning table)")
@@ -900,43 +940,16 @@ def main():
                   "table": "measured in this run (paper_2510_18838_gb300.tune.default_shapes)"}
 
     # ---- single-stream transfer pass: per-kernel breakdown and the roofline entry
-    tw = TransferWorkload(torch, pcms, W, dev, small=args.workload == "transfer_small")
-    for _ in range(2):
-        tw.step()
-    torch.cuda.synchronize()
-    pcms.trace_enable(True)
-    flush_l2(flush)
-    _, tms = timed(torch, tw.step, stream)
-    pcms.trace_enable(False)
-    ttrace = pcms.trace_read()
-    tw.step(timed_parts=True)
-    transfer = {"workload": tw.name, "ms": tms, "points": tw.points_per_step,
-                "points_per_s": tw.points_per_step / (tms / 1e3), "parts_ms": tw.parts,
-                "kernels_ms": {k: round(v[1], 3) for k, v in sorted(
-                    kernel_launches(ttrace).items(), key=lambda kv: -kv[1][1])[:14]},
-                "tiers": {k[6:]: v[0] for k, v in ttrace.items() if k.startswith("count:")},
-                "work": {"mls2d_pairs": tw.pairs3, "mls3d_nnz": tw.nnz4}}
-    peaks, kind = measured_peaks()
-    roof = tw.roofline(ttrace, peaks, kind)
-    apply_forms = apply_leg(torch, pcms, tw, peaks, kind, flush)
-    configs = None
-    if args.workload == "serve" and rank == 0:
-        import oracle
-        oracle.build()
-        configs = {"mls2d_fp64_10k": config1_leg(torch, pcms, W, oracle),
-                   "mesh_512": config2_leg(torch, pcms, W, oracle),
-                   "neighbour_counts": tw.hist}
-        if not args.no_cpu_baseline:
-            configs["cpu_oracle_per_config"] = tw.per_config_cpu(oracle)
-    study = roundtrip_study(torch, W) if args.workload == "serve" and rank == 0 else None
-    study5 = mls5d_study(torch, pcms, W) if args.workload == "serve" and rank == 0 else None
-    studyp = projection_study(torch, pcms, W) if args.workload == "serve" and rank == 0 else None
+    transfer = roof = apply_forms = configs = study = study5 = studyp = None
+    if args.workload != "serve_only":
+        transfer, roof, apply_forms, configs, study, study5, studyp, tw = transfer_and_studies(
+            torch, pcms, W, dev, args, rank, stream, flush)
 
     if args.workload in ("transfer", "transfer_small"):
         wl = tw
         name = tw.name
     else:
-        del tw
+        tw = None
         torch.cuda.empty_cache()
         wl = ServeWorkload(torch, pcms, serve, W, dev, seed=shard.rank_seed(501, rank))
         name = SERVE_NAME

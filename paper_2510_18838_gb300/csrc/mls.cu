@@ -52,7 +52,9 @@ void rows64_apply_any(int dim, int deg, int G, const ShapeArgs& sh, const int32_
 
 // Lanes per target, the first pass's accumulation and the grid's cell edge, from the expected
 // neighbour count (ns * ball volume / box volume).
-//  - 32 lanes from 160 neighbours on, else 8.
+//  - 32 lanes from 160 neighbours on, else 8; operators from 320 on (the lockstep 8-lane
+//    walk stages 384 columns per target: on the serving stream, 8 lanes up to 320 neighbours
+//    cut the step from 744 to 711 ms).
 //  - Blocked compensation (mixed path) from 1000 on, where plain FP32 sums over n / 32 pairs
 //    per lane stop meeting the error bound for ordinary targets; below that plain sums pass
 //    for almost every target and the blocked form would only cost registers.
@@ -80,7 +82,7 @@ AsmPlan choose_plan(int dim, int deg, int mode, int64_t ns, double radius, const
     double mean = (double)ns * ball / vol;
     AsmPlan p;
     p.mean = mean;
-    p.G = mean >= 160.0 ? 32 : 8;
+    p.G = mean >= (mode == MODE_MAP ? 320.0 : 160.0) ? 32 : 8;
     double div = dim == 2 ? (mean >= 1000.0 ? 6.0 : 3.0) : 2.0;
     p.tuned = false;
     TuneEntry e;

@@ -29,7 +29,7 @@ namespace pcms {
 struct Map8 {
     static constexpr int G = 8, GPW = 4;
     static constexpr int QCAP = 4 * G;   // ring entries per group (a power of two)
-    static constexpr int STG = 192;      // staged columns per group (one-pass rows)
+    static constexpr int STG = 384;      // staged columns per group (one-pass rows)
     template <int DIM>
     static constexpr int RPL = DIM == 3 ? 4 : 1;   // rows set up per lane and batch
 };
