@@ -212,12 +212,12 @@ def test_mixed_multifield_apply_3d(P):
         np.testing.assert_allclose(part[:, ok], out[:nf, ok], rtol=1e-6, atol=1e-6)
 
 
-@pytest.mark.parametrize("dim", [2, 3])
-def test_mixed_map_rows_longer_than_the_stage(P, dim):
+@pytest.mark.parametrize("dim,prec", [(2, "mixed"), (3, "mixed"), (2, "fp64"), (3, "fp64")])
+def test_map_rows_longer_than_the_stage(P, dim, prec):
     """Sparse sources plus one dense cluster: the mean neighbour count picks 8 lanes per
     target, while the targets at the cluster see thousands of sources, more than a group
-    stages during its walk (192 columns). Their rows are reserved after the walk and walked
-    a second time. Lists bit-exact, statuses equal, values within the mixed tolerance, and
+    stages during its walk (384 columns). Their rows are reserved after the walk and walked
+    a second time. Lists bit-exact, statuses equal, values within the path's tolerance, and
     the second walk must have run."""
     rng = np.random.default_rng(730 + dim)
     n_bg, n_cl, r = (20000, 2500, 0.02) if dim == 2 else (30000, 3000, 0.07)
@@ -229,20 +229,20 @@ def test_mixed_map_rows_longer_than_the_stage(P, dim):
         axis=1))
     f = np.sin(2 * np.pi * src[0]) * np.cos(2 * np.pi * src[1])
     P.trace_enable(True, count_only=True)
-    m = P.create_map(cu(src), cu(tgt), 2, r, precision="mixed")
-    out = host(m.apply(cu(f.astype(np.float32))))
+    m = P.create_map(cu(src), cu(tgt), 2, r, precision=prec)
+    out = host(m.apply(cu(f.astype(np.float32) if prec == "mixed" else f)))
     P.trace_enable(False)
     walked_again = P.trace_read().get("count:mls_map_rows_walked_again", (0, 0.0))[0]
     off, cols, _, st, _ = (host(x) for x in m.export())
     o = oracle.mls(src, tgt, f, 2, r, shape=True)
     assert walked_again > 0
-    assert np.diff(off).max() > 192
+    assert np.diff(off).max() > 384
     assert np.array_equal(st, o["status"])
     for a, b in zip(rows_as_sets(off, cols), rows_as_sets(o["offsets"], o["cols"])):
         assert np.array_equal(a, b)
     ok = o["status"] == 0
     assert ok.mean() > 0.95
-    assert normwise_err(out, o["values"], ok) <= TOL_MIXED
+    assert normwise_err(out, o["values"], ok) <= (TOL_MIXED if prec == "mixed" else TOL_FP64)
     m.destroy()
 
 
