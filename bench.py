@@ -162,13 +162,13 @@ def kernel_launches(trace):
 # assembly reads the sources and writes the moments once, which scale with the points (x 8).
 NCU_TRAFFIC = {
     "mls_assemble_fused_bk": (
-        107.3e6, 8.0, "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_assemble<2, 2, "
-        "mixed, fused, 32, float, blocked> on the 500k -> 500k case (43.1 + 64.1 MB) "
+        107.8e6, 8.0, "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_assemble<2, 2, "
+        "mixed, fused, 32, float, blocked> on the 500k -> 500k case (43.1 + 64.7 MB) "
         "x 8 for the 4M -> 4M "
         "launch (sources and targets scale by 8)"),
     "mls_assemble_map_mixed": (
-        459.9e6, 8.0, "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_assemble_map8<3, 2> "
-        "on the 1M -> 1M case (129.9 + 330.0 MB) x 8 for the 8M -> 8M launch "
+        460.5e6, 8.0, "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_assemble_map8<3, 2> "
+        "on the 1M -> 1M case (130.0 + 330.5 MB) x 8 for the 8M -> 8M launch "
         "(sources, targets and the operator's columns scale by 8)"),
 }
 
