@@ -244,3 +244,23 @@ extern "C" int hk_mono(int dim, int p, int* e) {
 extern "C" int hk_mono_prod(int dim, int k, int l) { return mono_prod(dim, k, l); }
 
 extern "C" double hk_weight(int kind, double q) { return weight_value<double>(kind, q); }
+
+// the compile-time pairing of the FP32 moment terms (two-lane FP32 instructions)
+template <int DIM, int MDEG>
+static int pair_plan(int* partner, int* first, int* packed) {
+    constexpr PairPlan<DIM, MDEG> P = PairPlanOf<DIM, MDEG>::v;
+    for (int p = 0; p < P.N; ++p) {
+        partner[p] = P.partner[p];
+        first[p] = P.first[p] ? 1 : 0;
+        packed[p] = P.packed[p] ? 1 : 0;
+    }
+    return P.N;
+}
+
+extern "C" int hk_pair_plan(int dim, int mdeg, int* partner, int* first, int* packed) {
+    if (dim == 2 && mdeg == 2) return pair_plan<2, 2>(partner, first, packed);
+    if (dim == 2 && mdeg == 4) return pair_plan<2, 4>(partner, first, packed);
+    if (dim == 3 && mdeg == 2) return pair_plan<3, 2>(partner, first, packed);
+    if (dim == 3 && mdeg == 4) return pair_plan<3, 4>(partner, first, packed);
+    return -1;
+}

@@ -43,6 +43,8 @@ def hk(tmp_path_factory):
     L.hk_mono_prod.argtypes = [I, I, I]
     L.hk_weight.restype = D
     L.hk_weight.argtypes = [I, D]
+    L.hk_pair_plan.restype = I
+    L.hk_pair_plan.argtypes = [I, I, P, P, P]
     return L
 
 
@@ -467,3 +469,56 @@ def test_fp64_refine_pass_on_extrapolating_targets(hk, t):
     assert amp_rc < amp_tc / 50
     assert err_rc <= 1e-12
     assert err_rc < err_tc / 50
+
+
+@pytest.mark.parametrize("dim,mdeg,expect", [(2, 2, 6), (2, 4, 16), (3, 2, 11), (3, 4, 33)])
+def test_pairing_of_the_fp32_moment_terms(hk, dim, mdeg, expect):
+    """The compile-time pairing of the FP32 moment terms for two-lane FP32 instructions. The
+    scalar chain forms each term w u^e as its parent (e with its first positive exponent
+    lowered by one) times u of that variable. A packed pair (p, q) is one two-lane product of
+    the parent pair, so p and q must share that variable and their parents must be partners,
+    p's parent in lane 0. Pairs hold terms of one degree; w (degree 0) is alone. The count of
+    instructions for the terms and their sums (a packed pair: product + sum, or one fused
+    multiply-add at the top degree; an unpacked pair: two products + one packed sum, or two
+    fused multiply-adds at the top degree; a single: product + sum, or one fused multiply-add)
+    is fixed per shape (the scalar chain takes 2 per term, 1 at the top degree)."""
+    n = _n_moments(dim, mdeg // 2)
+    partner = np.zeros(n, np.int32)
+    first = np.zeros(n, np.int32)
+    packed = np.zeros(n, np.int32)
+    assert hk.hk_pair_plan(dim, mdeg, _p(partner), _p(first), _p(packed)) == n
+    ex = exps(hk, dim, n)
+    deg = [sum(e) for e in ex]
+    index = {e: i for i, e in enumerate(ex)}
+
+    def var(e):
+        return next(d for d in range(dim) if e[d] > 0)
+
+    def parent(e):
+        v = var(e)
+        return index[tuple(x - (d == v) for d, x in enumerate(e))]
+
+    assert partner[0] == -1
+    count = 1   # w into its sum
+    for p in range(1, n):
+        q = partner[p]
+        top = deg[p] == mdeg
+        if q < 0:
+            assert not first[p] and not packed[p]
+            count += 1 if top else 2
+            continue
+        assert partner[q] == p and q != p and deg[q] == deg[p]
+        assert first[p] + first[q] == 1
+        if not first[p]:
+            assert not packed[p]
+            continue
+        if packed[p]:
+            assert var(ex[p]) == var(ex[q])
+            a, b = parent(ex[p]), parent(ex[q])
+            assert partner[a] == b and first[a] == 1
+            count += 1 if top else 2
+        else:
+            count += 2 if top else 3
+    assert count == expect
+    scalar = 1 + sum(1 if deg[p] == mdeg else 2 for p in range(1, n))
+    assert count < scalar
