@@ -27,6 +27,19 @@ def normwise_err(got, ref, mask=None):
     return float(np.max(np.max(np.abs(got - ref), axis=1) / den))
 
 
+def table1_cases():
+    """(kind, q, value) rows of tests/golden/table1_weights.txt: the weights of Table 1
+    (Sec. 3.2.1) at points where each formula has a closed form, evaluated by hand (the
+    derivation is on each row)."""
+    rows = []
+    for line in open(os.path.join(ROOT, "tests", "golden", "table1_weights.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        kind, q, value = line.split()[:3]
+        rows.append((kind, float(q), float(value)))
+    return rows
+
+
 def header_functions():
     txt = open(HEADER).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)

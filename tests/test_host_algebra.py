@@ -11,6 +11,8 @@ import subprocess
 import numpy as np
 import pytest
 
+from tests._helpers import table1_cases
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "tests", "host_kernels", "mls_algebra.cu")
 
@@ -75,9 +77,12 @@ def test_monomial_order_is_graded_lex(hk):
             assert ex[hk.hk_mono_prod(dim, k, l)] == prod
 
 
-def test_wendland_value(hk):
-    for q, v in [(0.0, 1.0), (0.5, 0.1875), (0.25, 0.6328125)]:
-        assert hk.hk_weight(0, q) == pytest.approx(v, rel=1e-15)
+@pytest.mark.parametrize("kind,q,expect", table1_cases())
+def test_weight_values_of_table1(hk, kind, q, expect):
+    """The library's weight function (compiled for the host in FP64) at the closed-form
+    points of Table 1, the same fixture the oracle's weights are pinned to."""
+    from paper_2510_18838_gb300.pcms import WEIGHTS
+    assert hk.hk_weight(WEIGHTS[kind], q) == pytest.approx(expect, rel=1e-15, abs=1e-300)
 
 
 def _system(dim, deg, n, seed):

@@ -12,30 +12,13 @@ import numpy as np
 import pytest
 
 from paper_2510_18838_gb300 import workloads as W
+from tests._helpers import table1_cases
 
 pytestmark = pytest.mark.filterwarnings("ignore")
 
 
 # ---------------------------------------------------------------- weights (Table 1)
-@pytest.mark.parametrize("kind,q,expect", [
-    ("wendland_c2", 0.0, 1.0),
-    ("wendland_c2", 0.5, 0.1875),              # (1/2)^4 * 3
-    ("wendland_c2", 0.25, 0.6328125),          # (3/4)^4 * 2
-    ("wendland_c2", 1.0, 0.0),
-    ("gaussian", 0.5, math.exp(-1.0)),        # exp(-(2*0.5)^2)
-    ("gaussian", 0.0, 1.0),
-    ("c4", 0.0, 6.0),                          # constant term of the polynomial, (1-0)^6
-    ("c4", 0.5, (5 / 32 + 30 / 16 + 72 / 8 + 82 / 4 + 18 + 6) / 64.0),
-    ("c4", 1.0, 0.0),
-    ("const", 0.7, 1.0),
-    ("noop", 0.7, 1.0),
-    ("mq", 0.5, math.sqrt(2.0)),
-    ("imq", 0.5, 1.0 / math.sqrt(2.0)),
-    ("tps", 0.5, 0.0),                         # (2*0.5)^2 ln(1) = 0
-    ("tps", 0.25, 0.25 * math.log(0.5)),
-    ("cubic", 0.5, 1.0),
-    ("cubic", 0.25, 0.125),
-])
+@pytest.mark.parametrize("kind,q,expect", table1_cases())
 def test_weight_table_values(orc, kind, q, expect):
     assert orc.weight(kind, q) == pytest.approx(expect, rel=1e-15, abs=1e-300)
 
