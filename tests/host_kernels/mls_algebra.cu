@@ -1,6 +1,9 @@
 // Host-compiled harness for the CPU tests: exposes the library's per-target MLS algebra
 // (the moment accumulation and the guarded LDL^T solve from mls_kernels.cuh, compiled for
 // the host with T = double) so its arithmetic can be checked against numpy without a GPU.
+// The FP32 form compiled here forms the moment terms one at a time; the device build forms
+// the same products on two-lane FP32 instructions, with one fused multiply-add for each
+// term of the top degree, which changes roundings but not the error model checked here.
 #include "mls_kernels.cuh"
 
 using namespace pcms;
